@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Bidomain time steps per second at PCG relative residual 1e-8.
+
+Workload (one GPU): the 2D torso slice at 2049 x 2049 nodes (N = 4 198 401,
+N_H = 792 653), dt = 0.1 ms, seeded stimulus disc inside the elliptic heart,
+Mitchell-Schaeffer reaction term.  A step is one pass of the resolution
+algorithm: fused Step 1 + Step 3 kernel, PCG on Lambda with the block-LU /
+monodomain preconditioner (hierarchical Cholesky factors), normalisation.
+
+The chosen form (eps-truncated factors stored in reduced precision) is the
+headline; the plain form (exact FP64 factors) is timed on the same GPU.  The
+factor and matrix working set (GBs) is far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (pinned sparse direct solve of
+every step) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bidomain steps/s at PCG rel-res 1e-8 (chosen form); HBM GB/s of the factor solve"
+
+
+def parse():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=20)
+    a.add_argument("--warmup", type=int, default=3)
+    a.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    a.add_argument("--n", type=int, default=2049)
+    a.add_argument("--eps", type=float, default=1e-3)
+    a.add_argument("--precision", default="fp32")
+    a.add_argument("--tol", type=float, default=1e-8)
+    a.add_argument("--cpu-seconds", type=float, default=20.0)
+    a.add_argument("--no-plain", action="store_true")
+    a.add_argument("--no-cpu", action="store_true")
+    return a.parse_args()
+
+
+def workload(n, seed):
+    from workloads import torso_square_2d, params_2d, stimulus_seeded_disc
+    mesh = torso_square_2d(n)
+    p = params_2d(0.1)
+    stim = stimulus_seeded_disc(mesh, seed=seed)
+    return mesh, p, stim
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def cpu_baseline(n, budget_s, seed=0):
+    """The oracle as it stands, timed on the host cores: steps of the same
+    workload (pinned sparse direct solve per step), as many as fit the budget
+    (at least one)."""
+    from oracle import bidomain as ob
+    mesh, p, stim = workload(n, seed)
+    s = ob.build_system(mesh, p)
+    ist = ob.heart_stimulus(s, stim)
+    U, V, h = ob.initial_state(s)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        U, V, h = ob.time_step(s, U, V, h, ist, steps * p["dt"], p["dt"], solver="direct")
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 50:
+            break
+    cores = len(os.sched_getaffinity(0))
+    return {"value": steps / el, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} oracle time steps of the {n}^2 workload from rest "
+                      f"(pinned sparse direct solve, FP64), {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.n, args.cpu_seconds)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"2D torso slice {args.n}^2, dt 0.1 ms, seeded stimulus",
+                       "solver": "oracle pinned sparse direct"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_08708_gb300 import bid
+
+    dev = torch.device("cuda", local)
+    mesh, p, stim = workload(args.n, seed=rank)
+    S = bid.System(mesh, p)
+    NH, N = S.NH, S.N
+    ist_h = stim[S.perm[:NH]]
+
+    def state():
+        U = torch.zeros(N, dtype=torch.float64, device=dev)
+        V = torch.full((NH,), p["v_rest"], dtype=torch.float64, device=dev)
+        h = torch.ones(NH, dtype=torch.float64, device=dev)
+        return U, V, h
+
+    I = torch.tensor(ist_h, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+
+    def time_form(P, label):
+        U, V, h = state()
+        t = 0.0
+        iters = []
+        for _ in range(args.warmup):
+            iters += list(P.step(U, V, h, I, t, 1, tol=args.tol))
+            t += p["dt"]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        it0 = len(iters)
+        l0 = bid.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as ck:
+            e0.record(st)
+            for _ in range(args.steps):
+                iters += list(P.step(U, V, h, I, t, 1, tol=args.tol))
+                t += p["dt"]
+            e1.record(st)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = bid.kernel_launches() - l0
+        if dist:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return dict(ms=ms, iters=iters[it0:], launches=launches, clocks=ck.summary(), U=U, V=V, h=h)
+
+    # ---- chosen form
+    P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision)
+    chosen_stats = dict(P.stats)
+    chosen = time_form(P, "chosen")
+
+    # ---- roofline of the dominant kernel family: the P_1 triangular pair
+    # (k_hfwd + k_hbwd over all tree levels), timed alone with CUDA events
+    b = torch.randn(N, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    for _ in range(3):
+        P.apply_factor(1, b, x)
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        P.apply_factor(1, b, x)
+    e1.record(st)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1) / reps
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6780.7)
+    # algorithmic bytes of one P_1 application: the factor read twice (stored
+    # bytes_p1 already counts both passes) + input gather, y and x vectors
+    alg_bytes = P.stats["bytes_p1"] + 8 * 4 * N
+    achieved = alg_bytes / (solve_ms * 1e-3) / 1e9
+
+    # ---- e2e through the public API with host buffers
+    U0, V0, h0 = state()
+    hU = torch.zeros(N, dtype=torch.float64).pin_memory()
+    hV = torch.full((NH,), p["v_rest"], dtype=torch.float64).pin_memory()
+    hh = torch.ones(NH, dtype=torch.float64).pin_memory()
+    t = args.warmup * p["dt"]
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        U0.copy_(hU, non_blocking=True)
+        V0.copy_(hV, non_blocking=True)
+        h0.copy_(hh, non_blocking=True)
+        P.step(U0, V0, h0, I, t, 1, tol=args.tol)
+        hU.copy_(U0, non_blocking=True)
+        hV.copy_(V0, non_blocking=True)
+        hh.copy_(h0, non_blocking=True)
+        t += p["dt"]
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    io_bytes = 8 * (N + 2 * NH)
+
+    # ---- plain form on the same GPU
+    plain = None
+    if not args.no_plain:
+        del P
+        torch.cuda.empty_cache()
+        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64")
+        plain = time_form(Pp, "plain")
+        plain_stats = Pp.stats
+        del Pp
+
+    ms_step = chosen["ms"] / args.steps
+    value = world * args.steps / (chosen["ms"] * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"2D torso slice {args.n}^2 (N={N}, N_H={NH}), dt 0.1 ms, "
+                        "seeded stimulus disc, PCG rel-res 1e-8",
+            "form": {"eps": args.eps, "factor_precision": args.precision},
+            "mean_pcg_iters": float(np.mean(chosen["iters"])),
+            "l2": "inputs larger than L2 (factor + matrices several GB)",
+            "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+            "precond_stats": {k: chosen_stats[k] for k in (
+                "factor_bytes", "bytes_p1", "bytes_pk", "levels1", "levelsk", "dense_entries",
+                "lowrank_entries", "build_seconds")},
+            "plain": None if plain is None else {
+                "steps_per_s": world * args.steps / (plain["ms"] * 1e-3),
+                "mean_pcg_iters": float(np.mean(plain["iters"])),
+                "factor_bytes": plain_stats["factor_bytes"],
+            },
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "k_hfwd+k_hbwd (one P_1 triangular pair)",
+                     "ms": solve_ms, "algorithmic_bytes": alg_bytes,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
+        "e2e": {"value": world / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": chosen["launches"],
+        "clocks": chosen["clocks"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

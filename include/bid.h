@@ -1,0 +1,225 @@
+/*
+ * bid.h -- C ABI of the GB300 bidomain time-step library.
+ *
+ * The library solves, at every time step, the linear system of the coupled
+ * heart-and-torso bidomain model of C. Pierre, "Preconditioning the bidomain
+ * model with almost linear complexity" (arXiv 1711.08708):
+ *
+ *   Lambda X = Y,  Lambda = [[S_1, Pi^T S_i], [S_i Pi, gamma M_H + S_i]],
+ *   int_Omega U = 0                                      (Sec. 3.2, eq. system)
+ *
+ * by FP64 preconditioned conjugate gradients with the block-LU preconditioner
+ * P_Lambda = L_P U_P (Def. 5.1, eq. prec-def / prec2), P_1 built from S_1 and
+ * P_K from the monodomain matrix K_m = gamma M_H + S_m (Sec. 5.2), both as
+ * hierarchical (nested-dissection, low-rank compressed) Cholesky factors with
+ * accuracy eps (Sec. 5.3).  The reaction term is the Mitchell-Schaeffer model.
+ *
+ * Conventions for every entry point:
+ *  - Vectors passed to the solver calls are DEVICE pointers (cudaMalloc'd or
+ *    torch tensors' data), FP64, in the library's node numbering: heart nodes
+ *    first (hypothesis H1, Sec. 3.1), so U = X[0:N], V = X[N:N+N_H] and
+ *    Pi U = U[0:N_H].  bid_get_perm gives library index -> mesh node.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls documented as blocking synchronise it before return.
+ *  - Every function returns BID_OK or an error code and never aborts; a
+ *    message for the last error of the calling thread is at bid_last_error().
+ *  - Handles own their device memory and free it in bid_destroy_*.  Nothing is
+ *    allocated per solve or per step: work vectors live in the preconditioner.
+ *  - Handles are not thread safe: one thread (and one stream at a time) per
+ *    preconditioner handle.
+ */
+#ifndef BID_H
+#define BID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BID_OK 0
+#define BID_EINVAL 1     /* bad argument: size, NULL pointer, non-positive parameter */
+#define BID_ENOCONV 2    /* max_iter reached; X holds the last iterate */
+#define BID_ESTAGNATE 3  /* residual not finite (NaN/Inf in the data) */
+#define BID_ECUDA 4      /* a CUDA runtime call failed */
+#define BID_ETIMEOUT 5   /* a bounded device wait expired */
+#define BID_ENOMEM 6     /* host or device allocation failed */
+
+/* storage precision of the hierarchical factors (Sec. 5.3 precision form) */
+#define BID_FP64 0
+#define BID_FP32 1
+#define BID_BF16 2
+
+/* Mesh of Omega with the heart sub-mesh (Sec. 3.1, hypothesis H1).  All arrays
+ * are HOST memory, borrowed for the duration of bid_assemble only. */
+typedef struct bid_mesh {
+    int32_t dim;              /* 2 or 3 */
+    int64_t n_nodes;
+    int64_t n_elems;
+    const double* coords;     /* [n_nodes * dim], cm */
+    const int32_t* elems;     /* [n_elems * (dim+1)] P1 simplices, mesh node ids */
+    const int32_t* region;    /* [n_elems]: 1 heart (T_H), 0 torso (T) */
+    const double* fibre;      /* [n_elems * dim * dim] row-major frame whose
+                                 columns are the local axes (fibre, sheet, normal) */
+} bid_mesh;
+
+/* Model parameters (Sec. 2; Mitchell-Schaeffer reaction term). */
+typedef struct bid_params {
+    double sigma_i[3];        /* g_i^l, g_i^t, g_i^n  (mS/cm; n unused in 2D) */
+    double sigma_e[3];        /* g_e^l, g_e^t, g_e^n */
+    double sigma_T;           /* isotropic torso conductivity k (mS/cm) */
+    double chi;               /* membrane surface-to-volume ratio A_m (cm^-1) */
+    double Cm;                /* membrane capacitance (uF/cm^2) */
+    double tau_in, tau_out, tau_open, tau_close, v_gate;   /* ms, v_gate normalised */
+    double v_rest, v_peak;    /* mV: w = (v - v_rest)/(v_peak - v_rest) */
+    double stim_t_on, stim_t_off;  /* stimulus window [on, off) in ms */
+    int32_t mass_lumped;      /* must be 1: row-sum (diagonal) mass matrices */
+} bid_params;
+
+typedef struct bid_system bid_system;    /* assembled S_1, S_i, M, M_H on the device */
+typedef struct bid_precond bid_precond;  /* P_1, P_K factors + PCG work vectors */
+
+/* Options of the preconditioner build (defaults via bid_precond_opts_default). */
+typedef struct bid_precond_opts {
+    double dt;                /* time step (ms); gamma = chi * Cm / dt (Sec. 3.2) */
+    double eps;               /* low-rank truncation accuracy (Sec. 5.3); 0 = exact */
+    int32_t precision;        /* BID_FP64 | BID_FP32 | BID_BF16 factor storage */
+    int32_t leaf_size;        /* nested-dissection leaf: max nodes per leaf cluster */
+    int32_t block;            /* row/column block of the factor tiles (16..128) */
+    int32_t n_threads;        /* host threads for the build (0 = all) */
+} bid_precond_opts;
+
+typedef struct bid_precond_stats {
+    int64_t n1, nk;                    /* sizes of the S_1 and K_m factors */
+    int64_t supernodes1, supernodesk;
+    int32_t levels1, levelsk;          /* tree heights (launches per triangular pass) */
+    int64_t dense_entries, lowrank_entries;  /* stored factor entries, both factors */
+    int64_t factor_bytes;              /* bytes read by one forward+backward pass of
+                                          P_1 plus one of P_K (algorithmic) */
+    int64_t bytes_p1, bytes_pk;        /* per single triangular-pair solve */
+    int64_t lowrank_blocks, dense_blocks;
+    double build_seconds;
+} bid_precond_stats;
+
+typedef struct bid_solve_info {
+    int32_t iters;            /* P_Lambda^-1 applications after the initial one */
+    int32_t status;           /* BID_OK / BID_ENOCONV / BID_ESTAGNATE */
+    int32_t restarts;         /* true-residual restarts (at most 1) */
+    double relres;            /* recurrence residual ||r||/||Y|| at exit */
+    double relres_true;       /* ||Y - Lambda X||/||Y|| recomputed at exit */
+} bid_solve_info;
+
+/* Assemble S_1 (sigma_1 = sigma_i + sigma_e on H, sigma_T on T), S_i, lumped
+ * M and M_H with P1 elements (Sec. 3.1) and S_m (sigma_m, Sec. 5.2); reorder the
+ * nodes heart-first; upload to the current CUDA device.  Blocking.
+ * Errors: BID_EINVAL (dim, sizes, node ids out of range, no heart element,
+ * non-positive conductivity, mass_lumped != 1), BID_ENOMEM, BID_ECUDA. */
+int bid_assemble(const bid_mesh* mesh, const bid_params* params, bid_system** out);
+
+/* Sizes: N, N_H and stored non-zeros of S_1 and S_i (any pointer may be NULL). */
+int bid_system_sizes(const bid_system* s, int64_t* N, int64_t* NH,
+                     int64_t* nnz_s1, int64_t* nnz_si);
+
+/* perm[k] = mesh node of library index k (host array of N entries). */
+int bid_get_perm(const bid_system* s, int64_t* perm);
+
+/* Lumped mass diagonals (host arrays, N and N_H entries; either may be NULL). */
+int bid_get_mass(const bid_system* s, double* m, double* mH);
+
+void bid_precond_opts_default(bid_precond_opts* o);
+
+/* Build P_Lambda for time step dt (Def. 5.1 with Sec. 5.2-5.3): the nested-
+ * dissection Cholesky factors of S_1 (the last U unknown pinned, which makes
+ * the factor an exact pseudo-inverse solver on 1^perp) and of K_m, in explicit
+ * inverse-block form with eps-truncated low-rank blocks, stored in `precision`.
+ * Host build (OpenMP), then upload.  Blocking.
+ * Errors: BID_EINVAL (dt <= 0, eps < 0, bad precision/leaf/block), BID_ENOMEM,
+ * BID_ECUDA. */
+int bid_precond_build(bid_system* s, double dt, double eps, int precision,
+                      bid_precond** out);
+int bid_precond_build_ex(bid_system* s, const bid_precond_opts* opts,
+                         bid_precond** out);
+int bid_precond_get_stats(const bid_precond* P, bid_precond_stats* st);
+
+/* y = Lambda(gamma) x (eq. system); x, y device, N + N_H each, distinct. */
+int bid_apply_lambda(const bid_system* s, double gamma, const double* x, double* y,
+                     void* stream);
+
+/* z = P_Lambda^-1 r (eq. prec2): Z1 = P_1^-1 p r_U, T = r_V - S_i Pi Z1,
+ * Z2 = P_K^-1 T, Z1 -= P_1^-1 Pi^T S_i Z2, where p projects onto 1^perp.  r and
+ * z device, N + N_H each, distinct.  The U block of z is defined up to an
+ * additive constant (Lambda annihilates constants, Prop. 1). */
+int bid_apply_precond(bid_precond* P, const double* r, double* z, void* stream);
+
+/* Solve x = P_1^-1 (b - mean(b)) (which = 1: S_1 factor, N entries) or
+ * x = P_K^-1 b (which = 2: K_m factor, N_H entries).  Device vectors. */
+int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void* stream);
+
+/* Step 2 (eq. system): PCG on Lambda from the guess in X, stopping when the
+ * recurrence residual ||r||_2/||Y||_2 < tol (Sec. 6.2); the true residual is
+ * then recomputed and PCG restarted once if it is above tol; X is finally
+ * normalised so that (M U, 1) = 0 (proof of Prop. 1).  Y must lie in
+ * Ran(Lambda) (U block summing to zero); the U block of every residual is
+ * projected onto 1^perp.  Y and X device (N + N_H), distinct.  Blocking: info
+ * (may be NULL) is filled before return.  Returns BID_ENOCONV after max_iter. */
+int bid_solve(bid_system* s, bid_precond* P, const double* Y, double* X,
+              double tol, int max_iter, bid_solve_info* info, void* stream);
+
+/* The resolution algorithm (Sec. 3.2) for n_steps steps from time t0:
+ * Step 1 and Step 3 fused (Y from (V^n, W^n); W^{n+1} = W^n + dt g(V^n, W^n)),
+ * Step 2 by bid_solve with guess (U^n, V^n).  U (N), V (N_H), h (N_H) device,
+ * updated in place.  Ist: device per-heart-node stimulus amplitude (uA/cm^2)
+ * applied while t in [stim_t_on, stim_t_off), or NULL.  iters_out: host array
+ * of n_steps PCG iteration counts, or NULL.  Blocking. */
+int bid_step(bid_system* s, bid_precond* P, double* U, double* V, double* h,
+             const double* Ist, double t0, int n_steps, double tol, int max_iter,
+             int* iters_out, void* stream);
+
+/* Step 1 + Step 3 only: Y[0:N] = 0, Y[N:] = M_H (gamma V - chi (I_ion - I_st)),
+ * h += dt g(V, h), with the stimulus on iff stim_on != 0.  Device pointers. */
+int bid_rhs_gate(bid_precond* P, const double* V, double* h, const double* Ist,
+                 int stim_on, double* Y, void* stream);
+
+/* U <- U - (M U, 1)/(M 1, 1) on the U block of X (device, N + N_H or N). */
+int bid_normalise(bid_precond* P, double* X, void* stream);
+
+void bid_destroy_system(bid_system* s);
+void bid_destroy_precond(bid_precond* P);
+const char* bid_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads; used to report launches inside a timed region). */
+int64_t bid_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------
+ * Host-only entry points (no GPU needed).  They expose the host half of the
+ * library -- the P1 assembly and the hierarchical factor build -- together
+ * with a sequential host replay of the factor's level-by-level triangular
+ * passes over exactly the packed blocks and tiles that the GPU kernels read.
+ * They exist so that the host logic can be checked on machines without a GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct bid_host_system bid_host_system;
+
+/* Assemble on the host only (same arguments and errors as bid_assemble). */
+int bid_host_assemble(const bid_mesh* mesh, const bid_params* params, bid_host_system** out);
+/* Sizes of matrix `which` (0: S_1, 1: S_i, 2: S_m): rows and stored entries. */
+int bid_host_csr_size(const bid_host_system* h, int which, int64_t* n, int64_t* nnz);
+/* Copy matrix `which` in CSR form (ptr: n+1 entries, col/val: nnz entries),
+ * library numbering; perm (N entries, may be NULL) and the lumped masses m
+ * (N) and mH (N_H) (may be NULL) are copied too. */
+int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col, double* val,
+                 int64_t* perm, double* m, double* mH);
+/* Build the factor of S_1 (which = 1, last U unknown pinned) or of
+ * K_m = gamma M_H + S_m (which = 2) with the given eps / leaf / block, and
+ * apply it on the host: x = P^-1 (b - mean(b)) for which = 1, x = P^-1 b for
+ * which = 2.  b and x are host arrays (N or N_H).  stats may be NULL. */
+int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps,
+                          int leaf, int block, const double* b, double* x,
+                          bid_precond_stats* stats);
+void bid_host_destroy(bid_host_system* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BID_H */

@@ -1,0 +1,284 @@
+"""Python binding of libbid.so (ctypes): argument marshalling only.
+
+Every computation runs in the C/CUDA library; this module converts numpy
+arrays and torch tensors to the plain pointers and sizes of the C ABI
+(include/bid.h) and raises ``BidError`` on a non-zero status.  There is no
+fallback path: importing it without the built library raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbid.so")
+
+OK, EINVAL, ENOCONV, ESTAGNATE, ECUDA, ETIMEOUT, ENOMEM = range(7)
+FP64, FP32, BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+
+
+class BidError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bid error {code}: {msg}")
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_nodes", C.c_int64), ("n_elems", C.c_int64),
+                ("coords", C.c_void_p), ("elems", C.c_void_p), ("region", C.c_void_p),
+                ("fibre", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("sigma_i", C.c_double * 3), ("sigma_e", C.c_double * 3), ("sigma_T", C.c_double),
+                ("chi", C.c_double), ("Cm", C.c_double), ("tau_in", C.c_double),
+                ("tau_out", C.c_double), ("tau_open", C.c_double), ("tau_close", C.c_double),
+                ("v_gate", C.c_double), ("v_rest", C.c_double), ("v_peak", C.c_double),
+                ("stim_t_on", C.c_double), ("stim_t_off", C.c_double), ("mass_lumped", C.c_int32)]
+
+
+class PrecondOpts(C.Structure):
+    _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("precision", C.c_int32),
+                ("leaf_size", C.c_int32), ("block", C.c_int32), ("n_threads", C.c_int32)]
+
+
+class PrecondStats(C.Structure):
+    _fields_ = [("n1", C.c_int64), ("nk", C.c_int64), ("supernodes1", C.c_int64),
+                ("supernodesk", C.c_int64), ("levels1", C.c_int32), ("levelsk", C.c_int32),
+                ("dense_entries", C.c_int64), ("lowrank_entries", C.c_int64),
+                ("factor_bytes", C.c_int64), ("bytes_p1", C.c_int64), ("bytes_pk", C.c_int64),
+                ("lowrank_blocks", C.c_int64), ("dense_blocks", C.c_int64),
+                ("build_seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("restarts", C.c_int32),
+                ("relres", C.c_double), ("relres_true", C.c_double)]
+
+
+_VP, _I, _D, _I64P = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_int64)
+
+# name -> (restype, argtypes); every symbol include/bid.h declares
+SIGNATURES = {
+    "bid_assemble": (_I, [C.POINTER(Mesh), C.POINTER(Params), C.POINTER(_VP)]),
+    "bid_system_sizes": (_I, [_VP, _I64P, _I64P, _I64P, _I64P]),
+    "bid_get_perm": (_I, [_VP, _VP]),
+    "bid_get_mass": (_I, [_VP, _VP, _VP]),
+    "bid_precond_opts_default": (None, [C.POINTER(PrecondOpts)]),
+    "bid_precond_build": (_I, [_VP, _D, _D, _I, C.POINTER(_VP)]),
+    "bid_precond_build_ex": (_I, [_VP, C.POINTER(PrecondOpts), C.POINTER(_VP)]),
+    "bid_precond_get_stats": (_I, [_VP, C.POINTER(PrecondStats)]),
+    "bid_apply_lambda": (_I, [_VP, _D, _VP, _VP, _VP]),
+    "bid_apply_precond": (_I, [_VP, _VP, _VP, _VP]),
+    "bid_apply_factor": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "bid_solve": (_I, [_VP, _VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo), _VP]),
+    "bid_step": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _D, _I, _D, _I, _VP, _VP]),
+    "bid_rhs_gate": (_I, [_VP, _VP, _VP, _VP, _I, _VP, _VP]),
+    "bid_normalise": (_I, [_VP, _VP, _VP]),
+    "bid_destroy_system": (None, [_VP]),
+    "bid_destroy_precond": (None, [_VP]),
+    "bid_last_error": (C.c_char_p, []),
+    "bid_kernel_launches": (C.c_int64, []),
+    "bid_host_assemble": (_I, [C.POINTER(Mesh), C.POINTER(Params), C.POINTER(_VP)]),
+    "bid_host_csr_size": (_I, [_VP, _I, _I64P, _I64P]),
+    "bid_host_csr": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "bid_host_factor_solve": (_I, [_VP, _I, _D, _D, _I, _I, _VP, _VP, C.POINTER(PrecondStats)]),
+    "bid_host_destroy": (None, [_VP]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != OK:
+        raise BidError(rc, lib.bid_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(a):
+    """Plain pointer of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def kernel_launches() -> int:
+    return int(lib.bid_kernel_launches())
+
+
+def make_params(p: dict) -> Params:
+    q = Params()
+    si = list(p["sigma_i"]) + [p["sigma_i"][-1]] * (3 - len(p["sigma_i"]))
+    se = list(p["sigma_e"]) + [p["sigma_e"][-1]] * (3 - len(p["sigma_e"]))
+    q.sigma_i = (C.c_double * 3)(*si)
+    q.sigma_e = (C.c_double * 3)(*se)
+    for k in ("sigma_T", "chi", "Cm", "tau_in", "tau_out", "tau_open", "tau_close", "v_gate",
+              "v_rest", "v_peak"):
+        setattr(q, k, float(p[k]))
+    q.stim_t_on, q.stim_t_off = (float(t) for t in p.get("stim_t", (0.0, 1.0)))
+    q.mass_lumped = 1
+    return q
+
+
+class _MeshArrays:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, mesh):
+        self.coords = np.ascontiguousarray(mesh.coords, dtype=np.float64)
+        self.elems = np.ascontiguousarray(mesh.elems, dtype=np.int32)
+        self.region = np.ascontiguousarray(mesh.region, dtype=np.int32)
+        self.fibre = np.ascontiguousarray(mesh.fibre, dtype=np.float64)
+        self.s = Mesh(mesh.dim, self.coords.shape[0], self.elems.shape[0], self.coords.ctypes.data,
+                      self.elems.ctypes.data, self.region.ctypes.data, self.fibre.ctypes.data)
+
+
+class System:
+    """bid_system: S_1, S_i, M, M_H assembled and resident on the current GPU."""
+
+    def __init__(self, mesh, params: dict):
+        self.params = dict(params)
+        m = _MeshArrays(mesh)
+        h = _VP()
+        _check(lib.bid_assemble(C.byref(m.s), C.byref(make_params(params)), C.byref(h)))
+        self.h = h
+        N, NH, n1, ni = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.bid_system_sizes(h, C.byref(N), C.byref(NH), C.byref(n1), C.byref(ni)))
+        self.N, self.NH, self.nnz_s1, self.nnz_si = N.value, NH.value, n1.value, ni.value
+        self.perm = np.empty(self.N, dtype=np.int64)
+        _check(lib.bid_get_perm(h, _ptr(self.perm)))
+        self.m = np.empty(self.N)
+        self.mH = np.empty(self.NH)
+        _check(lib.bid_get_mass(h, _ptr(self.m), _ptr(self.mH)))
+
+    def apply_lambda(self, gamma, x, y, stream=None):
+        _check(lib.bid_apply_lambda(self.h, float(gamma), _ptr(x), _ptr(y), _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bid_destroy_system(self.h)
+            self.h = None
+
+
+class Precond:
+    """bid_precond: P_Lambda for one time step dt, plus the PCG work vectors."""
+
+    def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=64, block=64,
+                 threads=0):
+        o = PrecondOpts()
+        lib.bid_precond_opts_default(C.byref(o))
+        o.dt, o.eps = float(dt), float(eps)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.leaf_size, o.block, o.n_threads = int(leaf), int(block), int(threads)
+        h = _VP()
+        _check(lib.bid_precond_build_ex(system.h, C.byref(o), C.byref(h)))
+        self.h, self.system, self.dt = h, system, float(dt)
+        st = PrecondStats()
+        _check(lib.bid_precond_get_stats(h, C.byref(st)))
+        self.stats = st.as_dict()
+
+    def apply(self, r, z, stream=None):
+        _check(lib.bid_apply_precond(self.h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def apply_factor(self, which, b, x, stream=None):
+        _check(lib.bid_apply_factor(self.h, int(which), _ptr(b), _ptr(x), _stream(stream)))
+
+    def solve(self, Y, X, tol=1e-8, max_iter=200, stream=None, check=True):
+        info = SolveInfo()
+        rc = lib.bid_solve(self.system.h, self.h, _ptr(Y), _ptr(X), float(tol), int(max_iter),
+                           C.byref(info), _stream(stream))
+        if check:
+            _check(rc)
+        return dict(iters=info.iters, status=info.status, restarts=info.restarts,
+                    relres=info.relres, relres_true=info.relres_true, rc=rc)
+
+    def step(self, U, V, h, Ist, t0, n_steps, tol=1e-8, max_iter=200, stream=None):
+        iters = np.zeros(max(n_steps, 1), dtype=np.int32)
+        _check(lib.bid_step(self.system.h, self.h, _ptr(U), _ptr(V), _ptr(h), _ptr(Ist),
+                            float(t0), int(n_steps), float(tol), int(max_iter), _ptr(iters),
+                            _stream(stream)))
+        return iters[:n_steps]
+
+    def rhs_gate(self, V, h, Ist, stim_on, Y, stream=None):
+        _check(lib.bid_rhs_gate(self.h, _ptr(V), _ptr(h), _ptr(Ist), int(bool(stim_on)), _ptr(Y),
+                                _stream(stream)))
+
+    def normalise(self, X, stream=None):
+        _check(lib.bid_normalise(self.h, _ptr(X), _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bid_destroy_precond(self.h)
+            self.h = None
+
+
+class HostSystem:
+    """Host-only assembly and factor replay (no GPU needed)."""
+
+    def __init__(self, mesh, params: dict):
+        m = _MeshArrays(mesh)
+        h = _VP()
+        _check(lib.bid_host_assemble(C.byref(m.s), C.byref(make_params(params)), C.byref(h)))
+        self.h = h
+
+    def csr(self, which):
+        n, nnz = C.c_int64(), C.c_int64()
+        _check(lib.bid_host_csr_size(self.h, which, C.byref(n), C.byref(nnz)))
+        ptr = np.empty(n.value + 1, dtype=np.int64)
+        col = np.empty(nnz.value, dtype=np.int32)
+        val = np.empty(nnz.value)
+        _check(lib.bid_host_csr(self.h, which, _ptr(ptr), _ptr(col), _ptr(val), None, None, None))
+        return ptr, col, val
+
+    def perm_and_mass(self):
+        n0, _ = C.c_int64(), C.c_int64()
+        n1 = C.c_int64()
+        _check(lib.bid_host_csr_size(self.h, 0, C.byref(n0), None))
+        _check(lib.bid_host_csr_size(self.h, 1, C.byref(n1), None))
+        perm = np.empty(n0.value, dtype=np.int64)
+        m = np.empty(n0.value)
+        mH = np.empty(n1.value)
+        _check(lib.bid_host_csr(self.h, 0, None, None, None, _ptr(perm), _ptr(m), _ptr(mH)))
+        return perm, m, mH
+
+    def factor_solve(self, which, b, gamma=0.0, eps=0.0, leaf=64, block=64):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        st = PrecondStats()
+        _check(lib.bid_host_factor_solve(self.h, int(which), float(gamma), float(eps), int(leaf),
+                                         int(block), _ptr(b), _ptr(x), C.byref(st)))
+        return x, st.as_dict()
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bid_host_destroy(self.h)
+            self.h = None

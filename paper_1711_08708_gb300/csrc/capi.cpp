@@ -1,0 +1,475 @@
+// C ABI entry points (include/bid.h): argument checks, device buffers, and the
+// host side of the PCG loop and of the resolution algorithm.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include <omp.h>
+
+#include "internal.h"
+
+namespace bid {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+namespace {
+
+int upload_sell(const CsrHost& A, SellDev* d) {
+    const int64_t n = A.n;
+    const int32_t ns = (int32_t)((n + 31) / 32);
+    std::vector<int32_t> sptr(ns + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) {
+        int64_t w = 0;
+        for (int64_t r = (int64_t)s * 32; r < std::min<int64_t>(n, (int64_t)s * 32 + 32); ++r)
+            w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
+        if ((int64_t)sptr[s] + w * 32 > INT32_MAX) return set_error(BID_EINVAL, "matrix too large");
+        sptr[s + 1] = sptr[s] + (int32_t)(w * 32);
+    }
+    std::vector<int32_t> col(sptr[ns], 0);
+    std::vector<double> val(sptr[ns], 0.0);
+    for (int32_t s = 0; s < ns; ++s) {
+        const int32_t w = (sptr[s + 1] - sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t r = (int64_t)s * 32 + l;
+            const int64_t len = r < n ? A.ptr[r + 1] - A.ptr[r] : 0;
+            for (int k = 0; k < w; ++k) {
+                const int64_t idx = sptr[s] + (int64_t)k * 32 + l;
+                if (k < len) {
+                    col[idx] = A.col[A.ptr[r] + k];
+                    val[idx] = A.val[A.ptr[r] + k];
+                } else {
+                    col[idx] = r < n ? (int32_t)r : 0;
+                }
+            }
+        }
+    }
+    d->n = (int32_t)n;
+    d->nslices = ns;
+    d->stored = sptr[ns];
+    BID_CUDA_TRY(cudaMalloc(&d->sptr, sizeof(int32_t) * (ns + 1)));
+    BID_CUDA_TRY(cudaMalloc(&d->col, sizeof(int32_t) * std::max<int64_t>(1, col.size())));
+    BID_CUDA_TRY(cudaMalloc(&d->val, sizeof(double) * std::max<int64_t>(1, val.size())));
+    BID_CUDA_TRY(cudaMemcpy(d->sptr, sptr.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice));
+    if (!col.empty()) {
+        BID_CUDA_TRY(cudaMemcpy(d->col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice));
+        BID_CUDA_TRY(cudaMemcpy(d->val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice));
+    }
+    return BID_OK;
+}
+
+void free_sell(SellDev* d) {
+    cudaFree(d->sptr);
+    cudaFree(d->col);
+    cudaFree(d->val);
+    *d = SellDev();
+}
+
+template <typename T>
+int dalloc(T** p, int64_t n) {
+    *p = nullptr;
+    if (cudaMalloc(p, sizeof(T) * std::max<int64_t>(n, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(BID_ENOMEM, "cudaMalloc of %lld bytes failed", (long long)(sizeof(T) * n));
+    }
+    return BID_OK;
+}
+
+Launch launch_of(const bid_system* s, void* stream) {
+    Launch L;
+    L.sms = s->sms;
+    L.st = (cudaStream_t)stream;
+    return L;
+}
+
+// z = P_Lambda^-1 r (eq. prec2).  The shift of the first P_1 input is
+// sc->sumr / N (sum of r_U), of the second sc->sum_b / N.
+int precond_apply(bid_precond* P, const Launch& L, const double* r, double* z) {
+    bid_system* s = P->sys;
+    const int64_t N = s->host.N, NH = s->host.NH;
+    const double invN = 1.0 / (double)N;
+    // Z1 = P_1^-1 p r_U
+    BID_TRY(launch_hsolve(L, P->F1, r, &P->sc->sumr, invN, P->ybuf, P->ubuf, z));
+    // T = r_V - S_i Pi Z1
+    BID_TRY(launch_si_residual(L, NH, s->Si, r + N, z, P->t));
+    // Z2 = P_K^-1 T
+    BID_TRY(launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->ybuf, P->ubuf, z + N));
+    // W = Pi^T S_i Z2 (zero on the torso), sum(W)
+    BID_TRY(launch_si_apply_sum(L, N, NH, s->Si, z + N, P->w, P->sc, P->partials));
+    // Z1 -= P_1^-1 p W
+    BID_TRY(launch_hsolve(L, P->F1, P->w, &P->sc->sum_b, invN, P->ybuf, P->ubuf, P->z1b));
+    BID_TRY(launch_axpy_sub(L, N, z, P->z1b));
+    return BID_OK;
+}
+
+int read_scalars(bid_precond* P, cudaStream_t st, DevScalars* out) {
+    BID_CUDA_TRY(cudaMemcpyAsync(P->host_pinned, P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    BID_CUDA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(out, P->host_pinned, sizeof(DevScalars));
+    return BID_OK;
+}
+
+int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_iter,
+               bid_solve_info* info, cudaStream_t st) {
+    bid_system* s = P->sys;
+    const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
+    Launch L = launch_of(s, st);
+    const int flexible = P->opts.precision != BID_FP64;
+    bid_solve_info inf{};
+    inf.status = BID_OK;
+    DevScalars h{};
+    int iters = 0;
+    // attempt 0: PCG from the guess; attempt 1 (only if the recurrence converged
+    // but the recomputed true residual is above tol): one restart from X.
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        // r = Y - Lambda X, U block projected onto 1^perp
+        BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, X, P->r, Y, P->sc, P->partials));
+        BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+        BID_TRY(read_scalars(P, st, &h));
+        if (!std::isfinite(h.yy) || !std::isfinite(h.rr)) {
+            inf.status = BID_ESTAGNATE;
+            break;
+        }
+        const double ny = std::sqrt(h.yy);
+        if (ny == 0.0) {
+            BID_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * n, st));
+            inf.relres = inf.relres_true = 0.0;
+            break;
+        }
+        const double rel_true = std::sqrt(h.rr) / ny;
+        inf.relres_true = rel_true;
+        if (attempt == 0) inf.relres = rel_true;
+        if (rel_true < tol || attempt == 2) break;
+        if (attempt == 1) inf.restarts = 1;
+        BID_TRY(precond_apply(P, L, P->r, P->z));
+        BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, 1, P->sc, P->partials));
+        BID_TRY(launch_pupdate(L, n, P->p, P->z, 1, P->sc));
+        bool conv = false;
+        while (iters < max_iter) {
+            BID_TRY(launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc, P->partials));
+            BID_TRY(launch_update(L, N, NH, X, P->r, P->p, P->q, P->sc, P->partials));
+            ++iters;
+            BID_TRY(read_scalars(P, st, &h));
+            if (!std::isfinite(h.rr)) {
+                inf.status = BID_ESTAGNATE;
+                break;
+            }
+            inf.relres = std::sqrt(h.rr) / ny;
+            if (inf.relres < tol) {
+                conv = true;
+                break;
+            }
+            BID_TRY(precond_apply(P, L, P->r, P->z));
+            BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, 0, P->sc, P->partials));
+            BID_TRY(launch_pupdate(L, n, P->p, P->z, 0, P->sc));
+        }
+        if (inf.status != BID_OK) break;
+        if (!conv) {
+            inf.status = BID_ENOCONV;
+            BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, X, P->r, Y, P->sc, P->partials));
+            BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+            BID_TRY(read_scalars(P, st, &h));
+            inf.relres_true = std::sqrt(h.rr) / ny;
+            break;
+        }
+    }
+    BID_TRY(launch_normalise(L, N, X, s->m, s->msum, P->sc, P->partials));
+    inf.iters = iters;
+    if (info) *info = inf;
+    if (inf.status == BID_ENOCONV)
+        return set_error(BID_ENOCONV, "PCG did not converge in %d iterations (relres %.3e)",
+                         max_iter, inf.relres);
+    if (inf.status == BID_ESTAGNATE) return set_error(BID_ESTAGNATE, "residual is not finite");
+    return BID_OK;
+}
+
+}  // namespace
+}  // namespace bid
+
+using namespace bid;
+
+extern "C" {
+
+const char* bid_last_error(void) { return g_err; }
+
+int64_t bid_kernel_launches(void) { return g_launches.load(); }
+
+int bid_assemble(const bid_mesh* mesh, const bid_params* params, bid_system** out) {
+    if (!out) return set_error(BID_EINVAL, "out is NULL");
+    *out = nullptr;
+    bid_system* s = new (std::nothrow) bid_system();
+    if (!s) return set_error(BID_ENOMEM, "host allocation failed");
+    int rc = assemble_host(mesh, params, &s->host);
+    if (rc != BID_OK) {
+        delete s;
+        return rc;
+    }
+    s->params = *params;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (s->sms <= 0) s->sms = 152;
+    rc = upload_sell(s->host.S1, &s->S1);
+    if (rc == BID_OK) rc = upload_sell(s->host.Si, &s->Si);
+    if (rc == BID_OK) rc = dalloc(&s->m, s->host.N);
+    if (rc == BID_OK) rc = dalloc(&s->mH, s->host.NH);
+    if (rc == BID_OK &&
+        (cudaMemcpy(s->m, s->host.m.data(), sizeof(double) * s->host.N, cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(s->mH, s->host.mH.data(), sizeof(double) * s->host.NH, cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = set_error(BID_ECUDA, "upload of the mass matrices failed");
+    if (rc != BID_OK) {
+        bid_destroy_system(s);
+        return rc;
+    }
+    double ms = 0.0;
+    for (double v : s->host.m) ms += v;
+    s->msum = ms;
+    *out = s;
+    return BID_OK;
+}
+
+int bid_system_sizes(const bid_system* s, int64_t* N, int64_t* NH, int64_t* nnz_s1, int64_t* nnz_si) {
+    if (!s) return set_error(BID_EINVAL, "NULL system");
+    if (N) *N = s->host.N;
+    if (NH) *NH = s->host.NH;
+    if (nnz_s1) *nnz_s1 = s->host.S1.nnz();
+    if (nnz_si) *nnz_si = s->host.Si.nnz();
+    return BID_OK;
+}
+
+int bid_get_perm(const bid_system* s, int64_t* perm) {
+    if (!s || !perm) return set_error(BID_EINVAL, "NULL argument");
+    std::memcpy(perm, s->host.perm.data(), sizeof(int64_t) * s->host.N);
+    return BID_OK;
+}
+
+int bid_get_mass(const bid_system* s, double* m, double* mH) {
+    if (!s) return set_error(BID_EINVAL, "NULL system");
+    if (m) std::memcpy(m, s->host.m.data(), sizeof(double) * s->host.N);
+    if (mH) std::memcpy(mH, s->host.mH.data(), sizeof(double) * s->host.NH);
+    return BID_OK;
+}
+
+void bid_precond_opts_default(bid_precond_opts* o) {
+    if (!o) return;
+    o->dt = 0.1;
+    o->eps = 0.0;
+    o->precision = BID_FP64;
+    o->leaf_size = 64;
+    o->block = 64;
+    o->n_threads = 0;
+}
+
+int bid_precond_build(bid_system* s, double dt, double eps, int precision, bid_precond** out) {
+    bid_precond_opts o;
+    bid_precond_opts_default(&o);
+    o.dt = dt;
+    o.eps = eps;
+    o.precision = precision;
+    return bid_precond_build_ex(s, &o, out);
+}
+
+int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond** out) {
+    if (!s || !o || !out) return set_error(BID_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (!(o->dt > 0.0)) return set_error(BID_EINVAL, "dt must be positive");
+    if (!(o->eps >= 0.0) || o->eps >= 1.0) return set_error(BID_EINVAL, "eps must be in [0, 1)");
+    if (o->precision < BID_FP64 || o->precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
+    if (o->block < 8 || o->block > 64) return set_error(BID_EINVAL, "block must be in 8..64");
+    if (o->leaf_size < 4 || o->leaf_size > 4096) return set_error(BID_EINVAL, "leaf_size must be in 4..4096");
+    auto t0 = std::chrono::steady_clock::now();
+    BID_TRY(hsolve_prepare());
+    const AssembledHost& H = s->host;
+    const double gamma = s->params.chi * s->params.Cm / o->dt;
+    HBuildOpts bo;
+    bo.eps = o->eps;
+    bo.leaf = o->leaf_size;
+    bo.block = o->block;
+    bo.threads = o->n_threads;
+    HFactorHost h1, hk;
+    // P_1: S_1 with the last U unknown pinned (pseudo-inverse on 1^perp)
+    BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, (int)(H.N - 1), bo, &h1));
+    // P_K: K_m = gamma M_H + S_m (Sec. 5.2)
+    CsrHost Km = H.Sm;
+    for (int64_t r = 0; r < Km.n; ++r)
+        for (int64_t q = Km.ptr[r]; q < Km.ptr[r + 1]; ++q)
+            if (Km.col[q] == r) Km.val[q] += gamma * H.mH[r];
+    BID_TRY(build_hfactor(Km, H.coords.data(), H.dim, -1, bo, &hk));
+    bid_precond* P = new (std::nothrow) bid_precond();
+    if (!P) return set_error(BID_ENOMEM, "host allocation failed");
+    P->sys = s;
+    P->opts = *o;
+    P->gamma = gamma;
+    int rc = upload_hfactor(h1, o->precision, &P->F1);
+    if (rc == BID_OK) rc = upload_hfactor(hk, o->precision, &P->FK);
+    const int64_t N = H.N, NH = H.NH, n = N + NH;
+    if (rc == BID_OK) rc = dalloc(&P->r, n);
+    if (rc == BID_OK) rc = dalloc(&P->z, n);
+    if (rc == BID_OK) rc = dalloc(&P->p, n);
+    if (rc == BID_OK) rc = dalloc(&P->q, n);
+    if (rc == BID_OK) rc = dalloc(&P->xs, n);
+    if (rc == BID_OK) rc = dalloc(&P->ytmp, n);
+    if (rc == BID_OK) rc = dalloc(&P->z1b, N);
+    if (rc == BID_OK) rc = dalloc(&P->t, NH);
+    if (rc == BID_OK) rc = dalloc(&P->w, N);
+    if (rc == BID_OK) rc = dalloc(&P->ybuf, N);
+    if (rc == BID_OK) rc = dalloc(&P->ubuf, std::max(h1.ubuf, hk.ubuf));
+    if (rc == BID_OK) rc = dalloc(&P->partials, (int64_t)s->sms * 8 * 4);
+    if (rc == BID_OK) rc = dalloc(&P->sc, 1);
+    if (rc == BID_OK && cudaMallocHost(&P->host_pinned, sizeof(DevScalars)) != cudaSuccess)
+        rc = set_error(BID_ENOMEM, "pinned host allocation failed");
+    if (rc == BID_OK && (cudaMemset(P->w, 0, sizeof(double) * N) != cudaSuccess ||
+                         cudaMemset(P->sc, 0, sizeof(DevScalars)) != cudaSuccess ||
+                         cudaMemset(P->p, 0, sizeof(double) * n) != cudaSuccess ||
+                         cudaMemset(P->q, 0, sizeof(double) * n) != cudaSuccess))
+        rc = set_error(BID_ECUDA, "cudaMemset failed");
+    if (rc != BID_OK) {
+        bid_destroy_precond(P);
+        return rc;
+    }
+    bid_precond_stats& st = P->stats;
+    st.n1 = h1.n;
+    st.nk = hk.n;
+    st.supernodes1 = (int64_t)h1.sn.size();
+    st.supernodesk = (int64_t)hk.sn.size();
+    st.levels1 = h1.height;
+    st.levelsk = hk.height;
+    st.dense_entries = h1.dense_entries + hk.dense_entries;
+    st.lowrank_entries = h1.lowrank_entries + hk.lowrank_entries;
+    st.dense_blocks = h1.dense_blocks + hk.dense_blocks;
+    st.lowrank_blocks = h1.lowrank_blocks + hk.lowrank_blocks;
+    st.bytes_p1 = P->F1.bytes_pass;
+    st.bytes_pk = P->FK.bytes_pass;
+    st.factor_bytes = 2 * st.bytes_p1 + st.bytes_pk;   // one P_Lambda^-1: 2 P_1 + 1 P_K
+    st.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return BID_OK;
+}
+
+int bid_precond_get_stats(const bid_precond* P, bid_precond_stats* st) {
+    if (!P || !st) return set_error(BID_EINVAL, "NULL argument");
+    *st = P->stats;
+    return BID_OK;
+}
+
+int bid_apply_lambda(const bid_system* s, double gamma, const double* x, double* y, void* stream) {
+    if (!s || !x || !y || x == y) return set_error(BID_EINVAL, "bad argument");
+    // a private scalar block: Lambda alone needs no PCG state
+    DevScalars* sc = nullptr;
+    double* partials = nullptr;
+    BID_TRY(dalloc(&sc, 1));
+    int rc = dalloc(&partials, (int64_t)s->sms * 8 * 4);
+    if (rc == BID_OK && cudaMemsetAsync(sc, 0, sizeof(DevScalars), (cudaStream_t)stream) != cudaSuccess)
+        rc = set_error(BID_ECUDA, "memset failed");
+    if (rc == BID_OK)
+        rc = launch_lambda(launch_of(s, stream), 0, s->host.N, s->host.NH, s->S1, s->Si, s->mH, gamma, x,
+                           y, nullptr, sc, partials);
+    if (rc == BID_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        rc = set_error(BID_ECUDA, "stream synchronize failed");
+    cudaFree(sc);
+    cudaFree(partials);
+    return rc;
+}
+
+int bid_apply_precond(bid_precond* P, const double* r, double* z, void* stream) {
+    if (!P || !r || !z || r == z) return set_error(BID_EINVAL, "bad argument");
+    Launch L = launch_of(P->sys, stream);
+    BID_TRY(launch_sum(L, P->sys->host.N, r, &P->sc->sumr, &P->sc->ticket[5], P->partials));
+    return precond_apply(P, L, r, z);
+}
+
+int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void* stream) {
+    if (!P || !b || !x || b == x) return set_error(BID_EINVAL, "bad argument");
+    Launch L = launch_of(P->sys, stream);
+    if (which == 1) {
+        BID_TRY(launch_sum(L, P->sys->host.N, b, &P->sc->sum_a, &P->sc->ticket[5], P->partials));
+        return launch_hsolve(L, P->F1, b, &P->sc->sum_a, 1.0 / (double)P->sys->host.N, P->ybuf,
+                             P->ubuf, x);
+    }
+    if (which == 2) return launch_hsolve(L, P->FK, b, nullptr, 0.0, P->ybuf, P->ubuf, x);
+    return set_error(BID_EINVAL, "which must be 1 or 2");
+}
+
+int bid_solve(bid_system* s, bid_precond* P, const double* Y, double* X, double tol, int max_iter,
+              bid_solve_info* info, void* stream) {
+    if (!s || !P || P->sys != s || !Y || !X || Y == X) return set_error(BID_EINVAL, "bad argument");
+    if (!(tol > 0.0) || max_iter < 1) return set_error(BID_EINVAL, "tol must be > 0, max_iter >= 1");
+    return solve_impl(P, Y, X, tol, max_iter, info, (cudaStream_t)stream);
+}
+
+int bid_rhs_gate(bid_precond* P, const double* V, double* h, const double* Ist, int stim_on, double* Y,
+                 void* stream) {
+    if (!P || !V || !h || !Y) return set_error(BID_EINVAL, "bad argument");
+    bid_system* s = P->sys;
+    return launch_rhs_gate(launch_of(s, stream), s->host.N, s->host.NH, V, h, Ist, stim_on, s->mH,
+                           s->params, P->opts.dt, Y);
+}
+
+int bid_normalise(bid_precond* P, double* X, void* stream) {
+    if (!P || !X) return set_error(BID_EINVAL, "bad argument");
+    bid_system* s = P->sys;
+    return launch_normalise(launch_of(s, stream), s->host.N, X, s->m, s->msum, P->sc, P->partials);
+}
+
+int bid_step(bid_system* s, bid_precond* P, double* U, double* V, double* h, const double* Ist,
+             double t0, int n_steps, double tol, int max_iter, int* iters_out, void* stream) {
+    if (!s || !P || P->sys != s || !U || !V || !h) return set_error(BID_EINVAL, "bad argument");
+    if (n_steps < 0 || !(tol > 0.0) || max_iter < 1) return set_error(BID_EINVAL, "bad step arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = s->host.N, NH = s->host.NH;
+    const double dt = P->opts.dt;
+    BID_CUDA_TRY(cudaMemcpyAsync(P->xs, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    BID_CUDA_TRY(cudaMemcpyAsync(P->xs + N, V, sizeof(double) * NH, cudaMemcpyDeviceToDevice, st));
+    int rc = BID_OK;
+    for (int k = 0; k < n_steps; ++k) {
+        const double t = t0 + k * dt;
+        const int on = (t >= s->params.stim_t_on && t < s->params.stim_t_off) ? 1 : 0;
+        rc = launch_rhs_gate(launch_of(s, stream), N, NH, P->xs + N, h, Ist, on, s->mH, s->params, dt, P->ytmp);
+        if (rc != BID_OK) break;
+        bid_solve_info inf{};
+        rc = solve_impl(P, P->ytmp, P->xs, tol, max_iter, &inf, st);
+        if (iters_out) iters_out[k] = inf.iters;
+        if (rc != BID_OK) break;
+    }
+    BID_CUDA_TRY(cudaMemcpyAsync(U, P->xs, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    BID_CUDA_TRY(cudaMemcpyAsync(V, P->xs + N, sizeof(double) * NH, cudaMemcpyDeviceToDevice, st));
+    BID_CUDA_TRY(cudaStreamSynchronize(st));
+    return rc;
+}
+
+void bid_destroy_system(bid_system* s) {
+    if (!s) return;
+    free_sell(&s->S1);
+    free_sell(&s->Si);
+    cudaFree(s->m);
+    cudaFree(s->mH);
+    delete s;
+}
+
+void bid_destroy_precond(bid_precond* P) {
+    if (!P) return;
+    free_hfactor(&P->F1);
+    free_hfactor(&P->FK);
+    for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->ybuf, P->ubuf, P->partials})
+        cudaFree(p);
+    cudaFree(P->sc);
+    if (P->host_pinned) cudaFreeHost(P->host_pinned);
+    delete P;
+}
+
+}  // extern "C"

@@ -1,0 +1,230 @@
+// Internal declarations of the bidomain library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bid.h"
+
+namespace bid {
+
+// ---------------------------------------------------------------- errors
+int set_error(int code, const char* fmt, ...);
+#define BID_CUDA_TRY(expr)                                                         \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return ::bid::set_error(BID_ECUDA, "%s failed: %s (%s:%d)", #expr,     \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);   \
+    } while (0)
+#define BID_TRY(expr)                      \
+    do {                                   \
+        int rc_ = (expr);                  \
+        if (rc_ != BID_OK) return rc_;     \
+    } while (0)
+
+// Count of kernel launches issued by this library (bid_kernel_launches).
+void count_launches(int n);
+
+// ---------------------------------------------------------------- host sparse
+struct CsrHost {
+    int64_t n = 0;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// Sliced ELLPACK with 32-row slices: element k of row r = 32*s + l lives at
+// sptr[s] + 32*k + l (column-major inside a slice, so a warp reads a slice
+// coalesced).  Padding entries have value 0 and column = the row itself.
+struct SellDev {
+    int32_t n = 0;
+    int32_t nslices = 0;
+    int32_t* sptr = nullptr;   // nslices + 1 offsets (elements)
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    int64_t stored = 0;        // stored entries including padding
+};
+
+// ---------------------------------------------------------------- assembly
+struct AssembledHost {
+    int dim = 0;
+    int64_t N = 0, NH = 0;
+    std::vector<int64_t> perm;     // library index -> mesh node
+    std::vector<double> coords;    // library order, N * dim
+    CsrHost S1, Si, Sm;            // Sm: sigma_m stiffness on the heart (Sec. 5.2)
+    std::vector<double> m, mH;     // lumped mass diagonals
+};
+int assemble_host(const bid_mesh* mesh, const bid_params* p, AssembledHost* out);
+
+// ---------------------------------------------------------------- H-factor
+// Factor of an SPD matrix A (n x n) in nested-dissection supernodal form.  For
+// supernode s with pivot set I_s (ni entries, contiguous in the elimination
+// order starting at `first`) and boundary set B_s (nb ancestor entries), the
+// stored block is M_s = [L_ss^-1 ; L_Bs L_ss^-1], (ni + nb) x ni, tiled in
+// blocks that are dense (row-major m x n) or low rank (U m x k row-major,
+// Vt k x n row-major, block = U Vt).
+struct HSnode {
+    int32_t first, ni, nb;
+    int32_t bidx_off;   // B_s entries (vector indices) at bidx[bidx_off ...]
+    int32_t u_off;      // update vector of s in the scratch buffer
+    int32_t inc_off;    // 2 ints per frontal row: children's update entries or -1
+    int32_t height;
+    int32_t pad;
+};
+struct HBlock {
+    int32_t type;       // 0 dense, 1 low rank
+    int32_t row0, col0; // position inside M_s
+    int32_t m, n, k;
+    int64_t off;        // element offset in the factor data
+};
+struct HTile {
+    int32_t s;          // supernode
+    int32_t r0, len;    // fwd: rows [r0, r0+len) of M_s; bwd: columns
+    int32_t blk_begin, blk_end;   // range in the tile's block list
+    int32_t tsum;       // sum of ranks of the tile's low-rank blocks
+};
+
+struct HFactorHost {
+    int64_t n = 0;
+    int32_t pin = -1;                  // vector index fixed to zero, or -1
+    int32_t block = 64;
+    int32_t height = 0;                // number of levels
+    std::vector<int32_t> pidx;         // elimination position -> vector index
+    std::vector<HSnode> sn;
+    std::vector<int32_t> bidx;
+    std::vector<int32_t> inc;
+    std::vector<HBlock> blk;
+    std::vector<double> data;
+    std::vector<HTile> tf, tb;         // tiles sorted by level
+    std::vector<int32_t> lf, lb;       // tile block lists
+    std::vector<int32_t> tf_ptr, tb_ptr;   // level -> tile range
+    std::vector<int32_t> ni_max;       // level -> max ni (shared memory for w)
+    std::vector<int32_t> tsum_max_f, tsum_max_b;
+    int64_t ubuf = 0;                  // update-vector scratch entries
+    int64_t dense_entries = 0, lowrank_entries = 0;
+    int64_t dense_blocks = 0, lowrank_blocks = 0;
+};
+
+struct HBuildOpts {
+    double eps = 0.0;
+    int leaf = 64;
+    int block = 64;
+    int threads = 0;
+};
+// A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
+// the unknowns, used by the nested dissection).  pin >= 0 replaces row and
+// column `pin` by the identity (pseudo-inverse of a singular Neumann matrix).
+int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin,
+                  const HBuildOpts& o, HFactorHost* F);
+
+// ---------------------------------------------------------------- device factor
+struct HFactorDev {
+    int64_t n = 0;
+    int32_t pin = -1;
+    int32_t precision = BID_FP64;
+    int32_t height = 0;
+    int32_t* pidx = nullptr;
+    int32_t* bidx = nullptr;
+    int32_t* inc = nullptr;
+    HSnode* sn = nullptr;
+    HBlock* blk = nullptr;
+    HTile* tf = nullptr;
+    HTile* tb = nullptr;
+    int32_t* lf = nullptr;
+    int32_t* lb = nullptr;
+    void* data = nullptr;               // double / float / __nv_bfloat16
+    int64_t data_elems = 0;
+    std::vector<int32_t> tf_ptr, tb_ptr, ni_max, tsum_max_f, tsum_max_b;
+    int64_t ubuf_entries = 0;
+    int64_t bytes_pass = 0;             // factor bytes read by fwd + bwd
+    int32_t block = 64;
+};
+int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
+void free_hfactor(HFactorDev* d);
+
+// ---------------------------------------------------------------- device scalars
+// Scalars of the PCG recurrences, kept on the device so that no kernel needs a
+// host round trip.  Reductions are deterministic (fixed order).
+struct DevScalars {
+    double pq, sumq, alpha;
+    double rr, sumr;
+    double rz, rz_new, qz, beta;
+    double yy, sum_a, sum_b;
+    double shift1, shift2;
+    double gen[4];
+    unsigned int ticket[16];
+};
+
+// ---------------------------------------------------------------- kernels (device entry)
+struct Launch {
+    int sms = 152;
+    cudaStream_t st = nullptr;
+};
+
+// Lambda product / residual (fused): mode 0: q = Lambda p, sums <p,q>, sum(q_U)
+// and sets alpha = rz / <p,q>; mode 1: r = Y - Lambda x, sums ||Y||^2, sum(r_U).
+int launch_lambda(const Launch& L, int mode, int64_t N, int64_t NH, const SellDev& S1,
+                  const SellDev& Si, const double* mH, double gamma, const double* x,
+                  double* out, const double* Y, DevScalars* sc, double* partials);
+int launch_project(const Launch& L, int64_t N, int64_t NH, double* r, DevScalars* sc,
+                   double* partials);
+int launch_update(const Launch& L, int64_t N, int64_t NH, double* x, double* r,
+                  const double* p, const double* q, DevScalars* sc, double* partials);
+int launch_dot_rz(const Launch& L, int64_t n, int64_t N, const double* r, const double* z,
+                  const double* q, int flexible, int first, DevScalars* sc,
+                  double* partials);
+int launch_pupdate(const Launch& L, int64_t n, double* p, const double* z, int first,
+                   const DevScalars* sc);
+int launch_si_residual(const Launch& L, int64_t NH, const SellDev& Si, const double* rV,
+                       const double* z1, double* t);
+int launch_si_apply_sum(const Launch& L, int64_t N, int64_t NH, const SellDev& Si,
+                        const double* z2, double* w, DevScalars* sc, double* partials);
+int launch_sum(const Launch& L, int64_t n, const double* x, double* dst_sum,
+               unsigned int* ticket, double* partials);
+int launch_axpy_sub(const Launch& L, int64_t n, double* a, const double* b);
+int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, double* h,
+                    const double* Ist, int stim_on, const double* mH, const bid_params& p,
+                    double dt, double* Y);
+int launch_normalise(const Launch& L, int64_t N, double* U, const double* m,
+                     double msum, DevScalars* sc, double* partials);
+// x = P^-1 b over a hierarchical factor: forward pass level by level (leaves
+// first), then backward pass.  The input entries are b[i] - shift_sum*inv_n
+// (shift_sum may be NULL), with the pinned entry set to zero.
+int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in,
+                  const double* shift_sum, double inv_n, double* ybuf, double* ubuf,
+                  double* out);
+int hsolve_prepare();   // raise the dynamic shared-memory limit of the kernels
+
+// ---------------------------------------------------------------- handles
+}  // namespace bid
+
+struct bid_system {
+    bid::AssembledHost host;
+    bid_params params{};
+    bid::SellDev S1, Si;
+    double* m = nullptr;      // device lumped mass (N)
+    double* mH = nullptr;     // device lumped heart mass (N_H)
+    double msum = 0.0;
+    int sms = 152;
+};
+
+struct bid_precond {
+    bid_system* sys = nullptr;
+    bid_precond_opts opts{};
+    double gamma = 0.0;
+    bid::HFactorDev F1, FK;
+    // work vectors (device)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double *z1b = nullptr, *t = nullptr, *w = nullptr, *ytmp = nullptr, *xs = nullptr;
+    double *ybuf = nullptr, *ubuf = nullptr;
+    double* partials = nullptr;
+    bid::DevScalars* sc = nullptr;
+    bid::DevScalars* host_pinned = nullptr;   // pinned host mirror of the scalars
+    bid_precond_stats stats{};
+};

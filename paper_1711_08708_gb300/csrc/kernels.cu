@@ -1,0 +1,466 @@
+// FP64 vector kernels of the PCG on Lambda (Sec. 5.1, 6.2), the fused
+// Lambda product (eq. system), the S_i products of the block-LU chain
+// (eq. prec2), the fused Step 1 + Step 3 kernel (Sec. 3.2) and the
+// normalisation (proof of Prop. 1).
+//
+// All reductions are deterministic: each CTA reduces in a fixed tree, writes
+// its partial, and the last CTA to finish (ticket counter) sums the partials
+// in index order and updates the PCG scalars in device memory.  No kernel
+// needs a host round trip.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace bid {
+
+namespace {
+
+constexpr int TPB = 256;
+
+struct SellView {
+    int32_t n, nslices;
+    const int32_t* __restrict__ sptr;
+    const int32_t* __restrict__ col;
+    const double* __restrict__ val;
+};
+SellView view(const SellDev& s) { return SellView{s.n, s.nslices, s.sptr, s.col, s.val}; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-wide deterministic reduction of NV values.  Returns true in thread 0 of
+// the last CTA, with the totals in `tot`.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
+                                            unsigned int* ticket, double (&tot)[NV]) {
+    __shared__ double sh[TPB / 32][NV];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[wid][i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[w][i];
+            partials[(size_t)blockIdx.x * NV + i] = s;
+        }
+        __threadfence();
+        const unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(&partials[(size_t)b * NV + i]);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = warp_sum(acc[i]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[wid][i] = acc[i];
+    __syncthreads();
+    if (threadIdx.x != 0) return false;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[w][i];
+        tot[i] = s;
+    }
+    *ticket = 0u;
+    return true;
+}
+
+int grid_for(const Launch& L, int64_t work_items) {
+    int64_t g = (work_items + TPB - 1) / TPB;
+    int64_t cap = (int64_t)L.sms * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// tickets (one per kernel kind)
+enum { TK_LAMBDA = 0, TK_PROJECT, TK_UPDATE, TK_DOT, TK_SIAPPLY, TK_SUM, TK_NORM };
+
+// ------------------------------------------------------------ Lambda product
+// mode 0: out = Lambda x; sums <x, out> and sum(out_U); alpha = rz / <x, out>.
+// mode 1: out = Y - Lambda x; sums ||Y||^2 and sum(out_U).
+// Row r of the U block: (S_1 x_U)_r + [r < N_H] (S_i x_V)_r.
+// Row r of the V block: (S_i (x_U[0:N_H] + x_V))_r + gamma m_r x_V[r].
+// One warp per 32-row slice; S_1 and S_i rows of a heart node are read in
+// the same pass.
+__global__ void __launch_bounds__(TPB) k_lambda(int mode, int N, int NH, SellView S1,
+                                                SellView Si, const double* __restrict__ mH,
+                                                double gamma, const double* __restrict__ x,
+                                                double* __restrict__ out,
+                                                const double* __restrict__ Y, DevScalars* sc,
+                                                double* partials) {
+    const double* xU = x;
+    const double* xV = x + N;
+    double* oU = out;
+    double* oV = out + N;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    double a0 = 0.0, a1 = 0.0;
+    for (int sl = gw; sl < S1.nslices; sl += nwarps) {
+        const int r = sl * 32 + lane;
+        const int b1 = S1.sptr[sl], w1 = (S1.sptr[sl + 1] - b1) >> 5;
+        double a = 0.0;
+        for (int k = 0; k < w1; ++k) {
+            const int idx = b1 + k * 32 + lane;
+            a += S1.val[idx] * xU[S1.col[idx]];
+        }
+        double qu = a, qv = 0.0;
+        bool heart = false;
+        if (sl < Si.nslices) {
+            const int b2 = Si.sptr[sl], w2 = (Si.sptr[sl + 1] - b2) >> 5;
+            double bv = 0.0, cu = 0.0;
+            for (int k = 0; k < w2; ++k) {
+                const int idx = b2 + k * 32 + lane;
+                const double v = Si.val[idx];
+                const int j = Si.col[idx];
+                bv += v * xV[j];
+                cu += v * xU[j];
+            }
+            if (r < NH) {
+                heart = true;
+                const double xv = xV[r];
+                qu = a + bv;
+                qv = cu + bv + gamma * mH[r] * xv;
+            }
+        }
+        if (r >= N) continue;
+        if (mode == 0) {
+            oU[r] = qu;
+            a0 += xU[r] * qu;
+            a1 += qu;
+            if (heart) {
+                oV[r] = qv;
+                a0 += xV[r] * qv;
+            }
+        } else {
+            const double yu = Y[r];
+            oU[r] = yu - qu;
+            a0 += yu * yu;
+            a1 += yu - qu;
+            if (heart) {
+                const double yv = Y[N + r];
+                oV[r] = yv - qv;
+                a0 += yv * yv;
+            }
+        }
+    }
+    double v[2] = {a0, a1}, tot[2];
+    if (grid_reduce<2>(v, partials, &sc->ticket[TK_LAMBDA], tot)) {
+        if (mode == 0) {
+            sc->pq = tot[0];
+            sc->sumq = tot[1];
+            sc->alpha = sc->rz / tot[0];
+        } else {
+            sc->yy = tot[0];
+            sc->sumr = tot[1];
+        }
+    }
+}
+
+// r_U <- r_U - sum(r_U)/N; then ||r||^2 and the new sum(r_U).
+__global__ void __launch_bounds__(TPB) k_project(int N, int NH, double* __restrict__ r,
+                                                 DevScalars* sc, double* partials) {
+    const double mean = sc->sumr / N;
+    double rr = 0.0, s = 0.0;
+    const int n = N + NH;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v = r[i];
+        if (i < N) {
+            v -= mean;
+            r[i] = v;
+            s += v;
+        }
+        rr += v * v;
+    }
+    double v2[2] = {rr, s}, tot[2];
+    if (grid_reduce<2>(v2, partials, &sc->ticket[TK_PROJECT], tot)) {
+        sc->rr = tot[0];
+        sc->sumr = tot[1];
+    }
+}
+
+// x += alpha p; r -= alpha q; r_U projected onto 1^perp in the same pass (the
+// new mean is known from the tracked sums); ||r||^2 and sum(r_U).
+__global__ void __launch_bounds__(TPB) k_update(int N, int NH, double* __restrict__ x,
+                                                double* __restrict__ r,
+                                                const double* __restrict__ p,
+                                                const double* __restrict__ q, DevScalars* sc,
+                                                double* partials) {
+    const double alpha = sc->alpha;
+    const double mean = (sc->sumr - alpha * sc->sumq) / N;
+    double rr = 0.0, s = 0.0;
+    const int n = N + NH;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        double v = r[i] - alpha * q[i];
+        if (i < N) {
+            v -= mean;
+            s += v;
+        }
+        r[i] = v;
+        rr += v * v;
+    }
+    double v2[2] = {rr, s}, tot[2];
+    if (grid_reduce<2>(v2, partials, &sc->ticket[TK_UPDATE], tot)) {
+        sc->rr = tot[0];
+        sc->sumr = tot[1];
+    }
+}
+
+// rz_new = <r, z>; qz = <q, p z> (q against the U-projected z).  first: rz = rz_new.
+// otherwise beta = rz_new / rz (standard) or -alpha qz / rz (flexible,
+// Polak-Ribiere form, since r_{k+1} - r_k = -alpha p q_k).
+__global__ void __launch_bounds__(TPB) k_dot_rz(int n, int N, const double* __restrict__ r,
+                                                const double* __restrict__ z,
+                                                const double* __restrict__ q, int flexible,
+                                                int first, DevScalars* sc, double* partials) {
+    double rz = 0.0, qz = 0.0, sz = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double zi = z[i];
+        rz += r[i] * zi;
+        if (flexible && !first) {
+            qz += q[i] * zi;
+            if (i < N) sz += zi;
+        }
+    }
+    double v[3] = {rz, qz, sz}, tot[3];
+    if (grid_reduce<3>(v, partials, &sc->ticket[TK_DOT], tot)) {
+        if (first) {
+            sc->beta = 0.0;
+        } else if (flexible) {
+            const double qzp = tot[1] - sc->sumq * tot[2] / N;
+            sc->beta = -sc->alpha * qzp / sc->rz;
+        } else {
+            sc->beta = tot[0] / sc->rz;
+        }
+        sc->rz_new = tot[0];
+        sc->qz = tot[1];
+        sc->rz = tot[0];
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_pupdate(int n, double* __restrict__ p,
+                                                 const double* __restrict__ z, int first,
+                                                 const DevScalars* sc) {
+    const double beta = first ? 0.0 : sc->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+// t = r_V - S_i z1[0:N_H]
+__global__ void __launch_bounds__(TPB) k_si_residual(int NH, SellView Si,
+                                                     const double* __restrict__ rV,
+                                                     const double* __restrict__ z1,
+                                                     double* __restrict__ t) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int sl = gw; sl < Si.nslices; sl += nwarps) {
+        const int r = sl * 32 + lane;
+        const int b = Si.sptr[sl], w = (Si.sptr[sl + 1] - b) >> 5;
+        double a = 0.0;
+        for (int k = 0; k < w; ++k) {
+            const int idx = b + k * 32 + lane;
+            a += Si.val[idx] * z1[Si.col[idx]];
+        }
+        if (r < NH) t[r] = rV[r] - a;
+    }
+}
+
+// w[0:N_H] = S_i z2 (w[N_H:N] stays 0); sum(w) -> sc->sum_b
+__global__ void __launch_bounds__(TPB) k_si_apply_sum(int NH, SellView Si,
+                                                      const double* __restrict__ z2,
+                                                      double* __restrict__ w, DevScalars* sc,
+                                                      double* partials) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    double s = 0.0;
+    for (int sl = gw; sl < Si.nslices; sl += nwarps) {
+        const int r = sl * 32 + lane;
+        const int b = Si.sptr[sl], wd = (Si.sptr[sl + 1] - b) >> 5;
+        double a = 0.0;
+        for (int k = 0; k < wd; ++k) {
+            const int idx = b + k * 32 + lane;
+            a += Si.val[idx] * z2[Si.col[idx]];
+        }
+        if (r < NH) {
+            w[r] = a;
+            s += a;
+        }
+    }
+    double v[1] = {s}, tot[1];
+    if (grid_reduce<1>(v, partials, &sc->ticket[TK_SIAPPLY], tot)) sc->sum_b = tot[0];
+}
+
+__global__ void __launch_bounds__(TPB) k_sum(int n, const double* __restrict__ x, double* dst,
+                                             unsigned int* ticket, double* partials) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s += x[i];
+    double v[1] = {s}, tot[1];
+    if (grid_reduce<1>(v, partials, ticket, tot)) *dst = tot[0];
+}
+
+__global__ void __launch_bounds__(TPB) k_axpy_sub(int n, double* __restrict__ a,
+                                                  const double* __restrict__ b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        a[i] -= b[i];
+}
+
+// Step 1 + Step 3 (Sec. 3.2) with the Mitchell-Schaeffer model:
+//   w = (v - v_rest)/(v_peak - v_rest)
+//   I_ion = -Cm (v_peak - v_rest) (h w^2 (1-w)/tau_in - w/tau_out)
+//   Y_V = m_H (gamma v - chi (I_ion - I_st)),  Y_U = 0
+//   h <- h + dt ((1-h)/tau_open  if w < v_gate  else  -h/tau_close)
+struct MsParams {
+    double v_rest, span, tau_in, tau_out, tau_open, tau_close, v_gate, Cm, chi, gamma, dt;
+};
+__global__ void __launch_bounds__(TPB) k_rhs_gate(int N, int NH, const double* __restrict__ V,
+                                                  double* __restrict__ h,
+                                                  const double* __restrict__ Ist, int stim_on,
+                                                  const double* __restrict__ mH, MsParams P,
+                                                  double* __restrict__ Y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N + NH;
+         i += gridDim.x * blockDim.x) {
+        if (i < N) {
+            Y[i] = 0.0;
+            continue;
+        }
+        const int j = i - N;
+        const double v = V[j], hj = h[j];
+        const double w = (v - P.v_rest) / P.span;
+        const double jin = hj * w * w * (1.0 - w) / P.tau_in;
+        const double jout = -w / P.tau_out;
+        const double iion = -P.Cm * P.span * (jin + jout);
+        const double ist = (stim_on && Ist) ? Ist[j] : 0.0;
+        Y[i] = mH[j] * (P.gamma * v - P.chi * (iion - ist));
+        const double g = (w < P.v_gate) ? (1.0 - hj) / P.tau_open : -hj / P.tau_close;
+        h[j] = hj + P.dt * g;
+    }
+}
+
+// alpha = (M U, 1) / (M 1, 1) (lumped M), then U -= alpha.
+__global__ void __launch_bounds__(TPB) k_mass_dot(int N, const double* __restrict__ U,
+                                                  const double* __restrict__ m, double msum,
+                                                  DevScalars* sc, double* partials) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        s += m[i] * U[i];
+    double v[1] = {s}, tot[1];
+    if (grid_reduce<1>(v, partials, &sc->ticket[TK_NORM], tot)) sc->gen[0] = tot[0] / msum;
+}
+__global__ void __launch_bounds__(TPB) k_sub_scalar(int N, double* __restrict__ U,
+                                                    const DevScalars* sc) {
+    const double a = sc->gen[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        U[i] -= a;
+}
+
+int check_launch(const char* what) {
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(BID_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return BID_OK;
+}
+
+}  // namespace
+
+int launch_lambda(const Launch& L, int mode, int64_t N, int64_t NH, const SellDev& S1,
+                  const SellDev& Si, const double* mH, double gamma, const double* x,
+                  double* out, const double* Y, DevScalars* sc, double* partials) {
+    const int g = grid_for(L, (int64_t)S1.nslices * 32);
+    k_lambda<<<g, TPB, 0, L.st>>>(mode, (int)N, (int)NH, view(S1), view(Si), mH, gamma, x, out,
+                                  Y, sc, partials);
+    return check_launch("lambda");
+}
+int launch_project(const Launch& L, int64_t N, int64_t NH, double* r, DevScalars* sc,
+                   double* partials) {
+    k_project<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, r, sc, partials);
+    return check_launch("project");
+}
+int launch_update(const Launch& L, int64_t N, int64_t NH, double* x, double* r, const double* p,
+                  const double* q, DevScalars* sc, double* partials) {
+    k_update<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, x, r, p, q, sc, partials);
+    return check_launch("update");
+}
+int launch_dot_rz(const Launch& L, int64_t n, int64_t N, const double* r, const double* z,
+                    const double* q, int flexible, int first, DevScalars* sc, double* partials) {
+    k_dot_rz<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, (int)N, r, z, q, flexible, first, sc,
+                                               partials);
+    return check_launch("dot_rz");
+}
+int launch_pupdate(const Launch& L, int64_t n, double* p, const double* z, int first,
+                   const DevScalars* sc) {
+    k_pupdate<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, p, z, first, sc);
+    return check_launch("pupdate");
+}
+int launch_si_residual(const Launch& L, int64_t NH, const SellDev& Si, const double* rV,
+                       const double* z1, double* t) {
+    k_si_residual<<<grid_for(L, (int64_t)Si.nslices * 32), TPB, 0, L.st>>>((int)NH, view(Si), rV,
+                                                                            z1, t);
+    return check_launch("si_residual");
+}
+int launch_si_apply_sum(const Launch& L, int64_t N, int64_t NH, const SellDev& Si,
+                        const double* z2, double* w, DevScalars* sc, double* partials) {
+    (void)N;
+    k_si_apply_sum<<<grid_for(L, (int64_t)Si.nslices * 32), TPB, 0, L.st>>>((int)NH, view(Si),
+                                                                             z2, w, sc, partials);
+    return check_launch("si_apply_sum");
+}
+int launch_sum(const Launch& L, int64_t n, const double* x, double* dst, unsigned int* ticket,
+               double* partials) {
+    k_sum<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, x, dst, ticket, partials);
+    return check_launch("sum");
+}
+int launch_axpy_sub(const Launch& L, int64_t n, double* a, const double* b) {
+    k_axpy_sub<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, a, b);
+    return check_launch("axpy_sub");
+}
+int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, double* h,
+                    const double* Ist, int stim_on, const double* mH, const bid_params& p,
+                    double dt, double* Y) {
+    MsParams P;
+    P.v_rest = p.v_rest;
+    P.span = p.v_peak - p.v_rest;
+    P.tau_in = p.tau_in;
+    P.tau_out = p.tau_out;
+    P.tau_open = p.tau_open;
+    P.tau_close = p.tau_close;
+    P.v_gate = p.v_gate;
+    P.Cm = p.Cm;
+    P.chi = p.chi;
+    P.gamma = p.chi * p.Cm / dt;
+    P.dt = dt;
+    k_rhs_gate<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, V, h, Ist, stim_on, mH, P,
+                                                      Y);
+    return check_launch("rhs_gate");
+}
+int launch_normalise(const Launch& L, int64_t N, double* U, const double* m, double msum,
+                     DevScalars* sc, double* partials) {
+    k_mass_dot<<<grid_for(L, N), TPB, 0, L.st>>>((int)N, U, m, msum, sc, partials);
+    BID_TRY(check_launch("mass_dot"));
+    k_sub_scalar<<<grid_for(L, N), TPB, 0, L.st>>>((int)N, U, sc);
+    return check_launch("sub_scalar");
+}
+
+}  // namespace bid

@@ -1,0 +1,254 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 element-wise results (Lambda product, Step 1 + Step 3) within
+1e-13 relative to the largest entry (rounding order only); solves compared
+after a PCG run to relative residual 1e-13, where the solution error is at
+most cond * 1e-13, within 1e-9 relative (the bound stated for the
+transmembrane and extracellular potentials); every factor precision (FP64,
+FP32, BF16, eps > 0) reaches the same bound because PCG stops on the FP64
+residual.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import bidomain as ob
+from workloads import (torso_square_2d, slab_3d, params_2d, params_3d, stimulus_left_apex,
+                       stimulus_seeded_disc)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def bid():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_08708_gb300 import bid as b
+    return b
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def H(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+CASES = {
+    "2d65": lambda: (torso_square_2d(65), params_2d(0.25)),
+    "2d97": lambda: (torso_square_2d(97), params_2d(0.1)),
+    "3d": lambda: (slab_3d(13, 11, 7), params_3d(0.05)),
+}
+
+
+def _setup(bid, case, **kw):
+    mesh, p = CASES[case]()
+    S = bid.System(mesh, p)
+    P = bid.Precond(S, p["dt"], **kw)
+    o = ob.build_system(mesh, p)
+    assert (S.perm == o.order).all()
+    return mesh, p, S, P, o
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_lambda_matches_oracle(bid, case):
+    mesh, p, S, P, o = _setup(bid, case)
+    g = ob.gamma_of(p, p["dt"])
+    x = np.random.default_rng(0).normal(size=o.N + o.NH)
+    y = torch.zeros(o.N + o.NH, dtype=torch.float64, device=DEV)
+    S.apply_lambda(g, T(x), y)
+    ref = ob.system_matrix(o, g) @ x
+    assert np.abs(H(y) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("stim", [0, 1])
+def test_rhs_gate_matches_oracle(bid, stim):
+    mesh, p, S, P, o = _setup(bid, "2d65")
+    rng = np.random.default_rng(1 + stim)
+    V = rng.uniform(p["v_rest"] - 5, p["v_peak"] + 5, size=o.NH)
+    w = (V - p["v_rest"]) / (p["v_peak"] - p["v_rest"])
+    assert np.abs(w - p["v_gate"]).min() > 1e-9          # no gate decision at a tie
+    h = rng.uniform(0, 1, size=o.NH)
+    ist = ob.heart_stimulus(o, stimulus_left_apex(mesh))
+    Yg = torch.zeros(o.N + o.NH, dtype=torch.float64, device=DEV)
+    hg = T(h)
+    P.rhs_gate(T(V), hg, T(ist), stim, Yg)
+    t = 0.5 if stim else 5.0
+    Yo = ob.rhs(o, V, h, ist, t, p["dt"])
+    ho = ob.gate_update(o, V, h, p["dt"])
+    assert np.abs(H(Yg) - Yo).max() <= 1e-13 * np.abs(Yo).max()
+    assert np.abs(H(hg) - ho).max() <= 1e-15
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_exact_factors_match_oracle(bid, case):
+    mesh, p, S, P, o = _setup(bid, case, eps=0.0)
+    g = ob.gamma_of(p, p["dt"])
+    rng = np.random.default_rng(2)
+    b = rng.normal(size=o.N)
+    x = torch.zeros(o.N, dtype=torch.float64, device=DEV)
+    P.apply_factor(1, T(b), x)
+    xg = H(x)
+    xg -= xg.mean()
+    xo = ob.s1_pseudo_inverse_apply(o, b)
+    assert np.abs(xg - xo).max() <= 1e-10 * np.abs(xo).max()
+    b2 = rng.normal(size=o.NH)
+    x2 = torch.zeros(o.NH, dtype=torch.float64, device=DEV)
+    P.apply_factor(2, T(b2), x2)
+    xo2 = spla.spsolve(ob.monodomain_matrix(o, g).tocsc(), b2)
+    assert np.abs(H(x2) - xo2).max() <= 1e-12 * np.abs(xo2).max()
+
+
+@pytest.mark.parametrize("case", ["2d65", "3d"])
+def test_exact_preconditioner_matches_oracle(bid, case):
+    mesh, p, S, P, o = _setup(bid, case, eps=0.0)
+    g = ob.gamma_of(p, p["dt"])
+    r = np.random.default_rng(3).normal(size=o.N + o.NH)
+    r[:o.N] -= r[:o.N].mean()
+    z = torch.zeros_like(T(r))
+    P.apply(T(r), z)
+    zg = H(z)
+    zo = ob.precond_apply_exact(o, g, r)
+    zg[:o.N] -= zg[:o.N].mean()
+    zo[:o.N] -= zo[:o.N].mean()
+    assert np.abs(zg - zo).max() <= 1e-10 * np.abs(zo).max()
+
+
+def test_equal_anisotropy_converges_in_one_iteration(bid):
+    # isolated heart, sigma_e = lam sigma_i: K_m = K, so exact P_1 and P_K make
+    # P_Lambda = Lambda on its range (Sec. 5.2, P_Lambda exact as eps -> 0)
+    mesh = slab_3d(13, 12, 7)
+    p = params_3d(0.05)
+    p["sigma_e"] = tuple(0.7 * np.array(p["sigma_i"]))
+    S = bid.System(mesh, p)
+    P = bid.Precond(S, p["dt"], eps=0.0)
+    o = ob.build_system(mesh, p)
+    V = p["v_rest"] + 100 * np.random.default_rng(4).random(o.NH)
+    Y = np.concatenate([np.zeros(o.N), o.MH @ V])
+    X = torch.zeros(o.N + o.NH, dtype=torch.float64, device=DEV)
+    info = P.solve(T(Y), X, tol=1e-10, max_iter=20)
+    assert info["iters"] == 1, info
+
+
+SOLVE_FORMS = [("2d65", dict(eps=0.0)), ("2d97", dict(eps=0.0)), ("3d", dict(eps=0.0)),
+               ("2d97", dict(eps=1e-3)), ("2d97", dict(eps=1e-2, precision="fp32")),
+               ("2d97", dict(eps=1e-3, precision="bf16")), ("3d", dict(eps=1e-2, precision="bf16")),
+               ("2d97", dict(eps=0.0, leaf=16, block=16))]
+
+
+@pytest.mark.parametrize("case,kw", SOLVE_FORMS)
+def test_solve_matches_oracle(bid, case, kw):
+    mesh, p, S, P, o = _setup(bid, case, **kw)
+    g = ob.gamma_of(p, p["dt"])
+    rng = np.random.default_rng(5)
+    V = p["v_rest"] + 100 * rng.random(o.NH)
+    h = rng.random(o.NH)
+    Y = ob.rhs(o, V, h, np.zeros(o.NH), 5.0, p["dt"])
+    X = T(np.concatenate([np.zeros(o.N), V]))
+    info = P.solve(T(Y), X, tol=1e-13, max_iter=400)
+    Xo = ob.solve_direct(o, g, Y)
+    Xg = H(X)
+    err = np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)
+    assert err <= 1e-9, (err, info)
+    assert info["relres_true"] < 1e-13
+    assert abs(Xg[:o.N] @ o.M.diagonal()) <= 1e-12 * np.abs(Xg).max() * o.M.sum()
+
+
+def test_step_trajectory_matches_oracle(bid):
+    # 65^2 torso, 20 steps of 0.25 ms with the corner stimulus: per step, the
+    # oracle is fed the GPU's state; at the end the two trajectories agree too
+    mesh, p, S, P, o = _setup(bid, "2d65", eps=1e-3)
+    ist = ob.heart_stimulus(o, stimulus_left_apex(mesh))
+    U0, V0, h0 = ob.initial_state(o)
+    U, V, h, I = T(U0), T(V0), T(h0), T(ist)
+    Uo, Vo, ho = U0.copy(), V0.copy(), h0.copy()
+    dt = p["dt"]
+    for k in range(20):
+        Ug, Vg, hg = H(U), H(V), H(h)
+        its = P.step(U, V, h, I, k * dt, 1, tol=1e-13, max_iter=400)
+        U1, V1, h1 = ob.time_step(o, Ug, Vg, hg, ist, k * dt, dt)
+        Xg = np.concatenate([H(U), H(V)])
+        X1 = np.concatenate([U1, V1])
+        assert np.linalg.norm(Xg - X1) <= 1e-9 * np.linalg.norm(X1), k
+        assert np.abs(H(h) - h1).max() <= 1e-13
+        Uo, Vo, ho = ob.time_step(o, Uo, Vo, ho, ist, k * dt, dt)
+        assert its[0] >= 1
+    Xo = np.concatenate([Uo, Vo])
+    Xg = np.concatenate([H(U), H(V)])
+    assert np.linalg.norm(Xg - Xo) <= 1e-8 * np.linalg.norm(Xo)
+    assert H(V).max() > -60.0                # the stimulus depolarised the site
+
+
+def test_solve_is_deterministic(bid):
+    mesh, p, S, P, o = _setup(bid, "2d97", eps=1e-3)
+    Y = ob.rhs(o, p["v_rest"] + 100 * np.random.default_rng(6).random(o.NH), np.ones(o.NH),
+               np.zeros(o.NH), 5.0, p["dt"])
+    outs = []
+    for _ in range(2):
+        X = torch.zeros(o.N + o.NH, dtype=torch.float64, device=DEV)
+        P.solve(T(Y), X, tol=1e-10)
+        outs.append(H(X))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_edge_cases(bid):
+    mesh, p, S, P, o = _setup(bid, "2d65")
+    n = o.N + o.NH
+    X = torch.ones(n, dtype=torch.float64, device=DEV)
+    info = P.solve(torch.zeros(n, dtype=torch.float64, device=DEV), X)
+    assert info["iters"] == 0 and not H(X).any()
+    Y = ob.rhs(o, p["v_rest"] + 50 * np.random.default_rng(7).random(o.NH), np.ones(o.NH),
+               np.zeros(o.NH), 5.0, p["dt"])
+    X = torch.zeros(n, dtype=torch.float64, device=DEV)
+    info = P.solve(T(Y), X, tol=1e-30, max_iter=2, check=False)
+    assert info["rc"] == bid.ENOCONV and info["iters"] == 2
+    Yn = Y.copy()
+    Yn[3] = np.nan
+    info = P.solve(T(Yn), X, check=False)
+    assert info["rc"] == bid.ESTAGNATE
+    Yt = T(Y)
+    with pytest.raises(bid.BidError) as e:
+        P.solve(Yt, Yt)
+    assert e.value.code == bid.EINVAL
+    with pytest.raises(bid.BidError):
+        bid.Precond(S, -1.0)
+
+
+def _full_size_properties(bid, n, steps, eps, precision):
+    mesh = torso_square_2d(n)
+    p = params_2d(0.1)
+    S = bid.System(mesh, p)
+    P = bid.Precond(S, p["dt"], eps=eps, precision=precision)
+    o = ob.build_system(mesh, p)
+    assert (S.perm == o.order).all()
+    ist = ob.heart_stimulus(o, stimulus_seeded_disc(mesh, seed=0))
+    U0, V0, h0 = ob.initial_state(o)
+    U, V, h, I = T(U0), T(V0), T(h0), T(ist)
+    g = ob.gamma_of(p, p["dt"])
+    L = ob.system_matrix(o, g)
+    rng = np.random.default_rng(8)
+    for k in range(steps):
+        Vb, hb = H(V), H(h)
+        P.step(U, V, h, I, k * p["dt"], 1, tol=1e-8, max_iter=100)
+        Y = ob.rhs(o, Vb, hb, ist, k * p["dt"], p["dt"])
+        X = np.concatenate([H(U), H(V)])
+        assert np.linalg.norm(L @ X - Y) <= 1e-8 * np.linalg.norm(Y) * 1.0001
+        assert abs(H(U) @ o.M.diagonal()) <= 1e-10 * np.abs(X).max() * o.M.sum()
+        idx = rng.choice(o.NH, 2000, replace=False)
+        _, gg = ob.ms_reaction(Vb[idx], hb[idx], p)
+        np.testing.assert_allclose(H(h)[idx], hb[idx] + p["dt"] * gg, rtol=0, atol=1e-15)
+
+
+def test_full_size_513_properties(bid):
+    _full_size_properties(bid, 513, 3, 1e-3, "fp64")
+
+
+def test_full_size_2049_properties(bid):
+    _full_size_properties(bid, 2049, 2, 1e-3, "fp32")

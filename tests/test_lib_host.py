@@ -1,0 +1,131 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol include/bid.h
+declares, and its host half (P1 assembly and the packed hierarchical factor,
+replayed on the host over the very blocks and tiles the GPU kernels read)
+agrees with the FP64 oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import bidomain as ob
+from workloads import torso_square_2d, slab_3d, params_2d, params_3d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bid():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_08708_gb300 import bid as b
+    return b
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bid.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bid_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(bid):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(bid.lib, n), n
+        assert n in bid.SIGNATURES, n
+
+
+def test_library_is_the_in_tree_build(bid):
+    assert os.path.dirname(bid.LIB_PATH) == os.path.join(ROOT, "paper_1711_08708_gb300")
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_host_assembly_matches_oracle(bid, case):
+    if case == "2d":
+        m, p = torso_square_2d(33), params_2d(0.25)
+    else:
+        m, p = slab_3d(9, 8, 5), params_3d(0.05)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    perm, mm, mH = hs.perm_and_mass()
+    assert (perm == s.order).all()
+    np.testing.assert_allclose(mm, s.M.diagonal(), rtol=1e-13)
+    np.testing.assert_allclose(mH, s.MH.diagonal(), rtol=1e-13)
+    for which, A in ((0, s.S1), (1, s.Si), (2, s.Sm)):
+        ptr, col, val = hs.csr(which)
+        B = sp.csr_matrix((val, col, ptr), shape=A.shape)
+        assert abs(B - A).max() <= 1e-14 * abs(A).max()
+
+
+@pytest.mark.parametrize("leaf,block", [(64, 64), (16, 16), (24, 32)])
+def test_host_factor_exact_equals_pseudo_inverse(bid, leaf, block):
+    m, p = torso_square_2d(41), params_2d(0.25)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    rng = np.random.default_rng(leaf)
+    b = rng.normal(size=s.N)
+    x, st = hs.factor_solve(1, b, leaf=leaf, block=block)
+    xo = ob.s1_pseudo_inverse_apply(s, b)
+    x -= x.mean()
+    assert np.abs(x - xo).max() <= 1e-11 * np.abs(xo).max()
+    g = ob.gamma_of(p, 0.25)
+    b2 = rng.normal(size=s.NH)
+    x2, _ = hs.factor_solve(2, b2, gamma=g, leaf=leaf, block=block)
+    xo2 = spla.spsolve(ob.monodomain_matrix(s, g).tocsc(), b2)
+    assert np.abs(x2 - xo2).max() <= 1e-12 * np.abs(xo2).max()
+    assert st["levels1"] >= 3 and st["lowrank_blocks"] == 0
+
+
+def test_host_factor_3d_exact():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_08708_gb300 import bid
+    m, p = slab_3d(11, 10, 6), params_3d(0.05)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    b = np.random.default_rng(7).normal(size=s.N)
+    x, _ = hs.factor_solve(1, b, leaf=32, block=32)
+    x -= x.mean()
+    xo = ob.s1_pseudo_inverse_apply(s, b)
+    assert np.abs(x - xo).max() <= 1e-11 * np.abs(xo).max()
+
+
+def test_host_factor_truncation_error_tracks_eps(bid):
+    m, p = torso_square_2d(129), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    b = np.random.default_rng(3).normal(size=s.N)
+    x0, _ = hs.factor_solve(1, b)
+    x0 -= x0.mean()
+    errs = []
+    for eps in (1e-2, 1e-4, 1e-6):
+        x, st = hs.factor_solve(1, b, eps=eps, leaf=32, block=32)
+        x -= x.mean()
+        errs.append(np.abs(x - x0).max() / np.abs(x0).max())
+        assert st["lowrank_blocks"] > 0
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-3
+
+
+def test_host_errors(bid):
+    m, p = torso_square_2d(9), params_2d(0.25)
+    bad = dict(p)
+    bad["sigma_T"] = -1.0
+    with pytest.raises(bid.BidError) as e:
+        bid.HostSystem(m, bad)
+    assert e.value.code == bid.EINVAL
+    m2 = torso_square_2d(9)
+    m2.region[:] = 0
+    with pytest.raises(bid.BidError) as e:
+        bid.HostSystem(m2, p)
+    assert e.value.code == bid.EINVAL
+    m3 = torso_square_2d(9)
+    m3.elems[0, 0] = 10 ** 6
+    with pytest.raises(bid.BidError):
+        bid.HostSystem(m3, p)
+    hs = bid.HostSystem(m, p)
+    with pytest.raises(bid.BidError):
+        hs.factor_solve(1, np.zeros(hs.perm_and_mass()[0].size), block=4)
