@@ -192,7 +192,7 @@ class System:
 class Precond:
     """bid_precond: P_Lambda for one time step dt, plus the PCG work vectors."""
 
-    def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=64, block=64,
+    def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=16, block=128,
                  threads=0):
         o = PrecondOpts()
         lib.bid_precond_opts_default(C.byref(o))
@@ -270,7 +270,7 @@ class HostSystem:
         _check(lib.bid_host_csr(self.h, 0, None, None, None, _ptr(perm), _ptr(m), _ptr(mH)))
         return perm, m, mH
 
-    def factor_solve(self, which, b, gamma=0.0, eps=0.0, leaf=64, block=64):
+    def factor_solve(self, which, b, gamma=0.0, eps=0.0, leaf=16, block=128):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         st = PrecondStats()

@@ -104,15 +104,15 @@ int precond_apply(bid_precond* P, const Launch& L, const double* r, double* z) {
     const int64_t N = s->host.N, NH = s->host.NH;
     const double invN = 1.0 / (double)N;
     // Z1 = P_1^-1 p r_U
-    BID_TRY(launch_hsolve(L, P->F1, r, &P->sc->sumr, invN, P->ybuf, P->ubuf, z));
+    BID_TRY(launch_hsolve(L, P->F1, r, &P->sc->sumr, invN, P->hs, z));
     // T = r_V - S_i Pi Z1
     BID_TRY(launch_si_residual(L, NH, s->Si, r + N, z, P->t));
     // Z2 = P_K^-1 T
-    BID_TRY(launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->ybuf, P->ubuf, z + N));
+    BID_TRY(launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->hs, z + N));
     // W = Pi^T S_i Z2 (zero on the torso), sum(W)
     BID_TRY(launch_si_apply_sum(L, N, NH, s->Si, z + N, P->w, P->sc, P->partials));
     // Z1 -= P_1^-1 p W
-    BID_TRY(launch_hsolve(L, P->F1, P->w, &P->sc->sum_b, invN, P->ybuf, P->ubuf, P->z1b));
+    BID_TRY(launch_hsolve(L, P->F1, P->w, &P->sc->sum_b, invN, P->hs, P->z1b));
     BID_TRY(launch_axpy_sub(L, N, z, P->z1b));
     return BID_OK;
 }
@@ -270,8 +270,8 @@ void bid_precond_opts_default(bid_precond_opts* o) {
     o->dt = 0.1;
     o->eps = 0.0;
     o->precision = BID_FP64;
-    o->leaf_size = 64;
-    o->block = 64;
+    o->leaf_size = 16;
+    o->block = 128;
     o->n_threads = 0;
 }
 
@@ -290,7 +290,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (!(o->dt > 0.0)) return set_error(BID_EINVAL, "dt must be positive");
     if (!(o->eps >= 0.0) || o->eps >= 1.0) return set_error(BID_EINVAL, "eps must be in [0, 1)");
     if (o->precision < BID_FP64 || o->precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
-    if (o->block < 8 || o->block > 64) return set_error(BID_EINVAL, "block must be in 8..64");
+    if (o->block < 8 || o->block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o->leaf_size < 4 || o->leaf_size > 4096) return set_error(BID_EINVAL, "leaf_size must be in 4..4096");
     auto t0 = std::chrono::steady_clock::now();
     BID_TRY(hsolve_prepare());
@@ -327,8 +327,13 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (rc == BID_OK) rc = dalloc(&P->z1b, N);
     if (rc == BID_OK) rc = dalloc(&P->t, NH);
     if (rc == BID_OK) rc = dalloc(&P->w, N);
-    if (rc == BID_OK) rc = dalloc(&P->ybuf, N);
-    if (rc == BID_OK) rc = dalloc(&P->ubuf, std::max(h1.ubuf, hk.ubuf));
+    if (rc == BID_OK) rc = dalloc(&P->hs.ybuf, N);
+    if (rc == BID_OK) rc = dalloc(&P->hs.ubuf, std::max(h1.ubuf, hk.ubuf));
+    if (rc == BID_OK) rc = dalloc(&P->hs.tbuf, std::max(h1.tbuf, hk.tbuf));
+    if (rc == BID_OK) rc = dalloc(&P->hs.pbuf, std::max(h1.pbuf, hk.pbuf));
+    if (rc == BID_OK) rc = dalloc(&P->hs.tickets, std::max(h1.ntickets, hk.ntickets));
+    if (rc == BID_OK && cudaMemset(P->hs.tickets, 0, sizeof(unsigned int) * std::max(1, std::max(h1.ntickets, hk.ntickets))) != cudaSuccess)
+        rc = set_error(BID_ECUDA, "cudaMemset failed");
     if (rc == BID_OK) rc = dalloc(&P->partials, (int64_t)s->sms * 8 * 4);
     if (rc == BID_OK) rc = dalloc(&P->sc, 1);
     if (rc == BID_OK && cudaMallocHost(&P->host_pinned, sizeof(DevScalars)) != cudaSuccess)
@@ -347,12 +352,12 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.nk = hk.n;
     st.supernodes1 = (int64_t)h1.sn.size();
     st.supernodesk = (int64_t)hk.sn.size();
-    st.levels1 = h1.height;
-    st.levelsk = hk.height;
+    st.levels1 = h1.height + (h1.nsub > 0 ? 1 : 0);
+    st.levelsk = hk.height + (hk.nsub > 0 ? 1 : 0);
     st.dense_entries = h1.dense_entries + hk.dense_entries;
     st.lowrank_entries = h1.lowrank_entries + hk.lowrank_entries;
-    st.dense_blocks = h1.dense_blocks + hk.dense_blocks;
-    st.lowrank_blocks = h1.lowrank_blocks + hk.lowrank_blocks;
+    st.dense_blocks = h1.nsub + hk.nsub;
+    st.lowrank_blocks = h1.nlr + hk.nlr;
     st.bytes_p1 = P->F1.bytes_pass;
     st.bytes_pk = P->FK.bytes_pass;
     st.factor_bytes = 2 * st.bytes_p1 + st.bytes_pk;   // one P_Lambda^-1: 2 P_1 + 1 P_K
@@ -398,10 +403,9 @@ int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void
     Launch L = launch_of(P->sys, stream);
     if (which == 1) {
         BID_TRY(launch_sum(L, P->sys->host.N, b, &P->sc->sum_a, &P->sc->ticket[5], P->partials));
-        return launch_hsolve(L, P->F1, b, &P->sc->sum_a, 1.0 / (double)P->sys->host.N, P->ybuf,
-                             P->ubuf, x);
+        return launch_hsolve(L, P->F1, b, &P->sc->sum_a, 1.0 / (double)P->sys->host.N, P->hs, x);
     }
-    if (which == 2) return launch_hsolve(L, P->FK, b, nullptr, 0.0, P->ybuf, P->ubuf, x);
+    if (which == 2) return launch_hsolve(L, P->FK, b, nullptr, 0.0, P->hs, x);
     return set_error(BID_EINVAL, "which must be 1 or 2");
 }
 
@@ -465,8 +469,10 @@ void bid_destroy_precond(bid_precond* P) {
     if (!P) return;
     free_hfactor(&P->F1);
     free_hfactor(&P->FK);
-    for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->ybuf, P->ubuf, P->partials})
+    for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->hs.ybuf,
+                      P->hs.ubuf, P->hs.tbuf, P->hs.pbuf, P->partials})
         cudaFree(p);
+    cudaFree(P->hs.tickets);
     cudaFree(P->sc);
     if (P->host_pinned) cudaFreeHost(P->host_pinned);
     delete P;

@@ -150,9 +150,12 @@ struct NDBuilder {
 struct SnWork {
     std::vector<int32_t> B;          // boundary positions (sorted)
     std::vector<double> Ustore;      // update matrix (nb x nb, lower), consumed by parent
-    std::vector<HBlock> blocks;      // offsets local to `data`
-    std::vector<double> data;
-    int64_t dense_e = 0, lr_e = 0, nd = 0, nl = 0;
+    std::vector<double> data;        // low-rank groups, then the packed dense columns
+    std::vector<HLr> lr;             // offsets local to `data`
+    std::vector<int32_t> drows;      // M_s rows of the dense boundary rows
+    int64_t dense_off = 0;
+    int nd = 0;
+    int64_t dense_e = 0, lr_e = 0;
 };
 
 }  // namespace
@@ -161,7 +164,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                   HFactorHost* F) {
     const int64_t n = A.n;
     if (n <= 0) return set_error(BID_EINVAL, "empty matrix");
-    if (o.block < 8 || o.block > 128) return set_error(BID_EINVAL, "block must be in 8..128");
+    if (o.block < 8 || o.block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o.leaf < 4 || o.leaf > 4096) return set_error(BID_EINVAL, "leaf must be in 4..4096");
     const int nthreads = o.threads > 0 ? o.threads : omp_get_max_threads();
 
@@ -196,7 +199,6 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
 
     F->n = n;
     F->pin = pin;
-    F->block = o.block;
     F->pidx.resize(n);
     F->sn.resize(nt);
     std::vector<int32_t> posof(n);
@@ -291,9 +293,37 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         }
     }
 
+    // ---------------- bottom subtrees (small clusters, one CTA per subtree)
+    std::vector<int> sub_begin(nt);
+    for (int s = 0; s < nt; ++s) {
+        int b = s;
+        for (int k = 0; k < nch[s]; ++k) b = std::min(b, sub_begin[ch[s][k]]);
+        sub_begin[s] = b;
+    }
+    std::vector<char> elig(nt, 0);
+    std::vector<int64_t> subpiv(nt, 0);
+    for (int s = 0; s < nt; ++s) {
+        const HSnode& h = F->sn[s];
+        bool ok = h.ni + h.nb <= SUB_ROWS && h.ni <= SUB_NI;
+        int64_t piv = h.ni;
+        for (int k = 0; k < nch[s]; ++k) {
+            ok = ok && elig[ch[s][k]];
+            piv += subpiv[ch[s][k]];
+        }
+        subpiv[s] = piv;
+        elig[s] = ok && piv <= SUB_PIV;
+    }
+    std::vector<int> sub_roots;
+    for (int s = 0; s < nt; ++s) {
+        F->sn[s].sub = -1;
+        if (elig[s] && (parent[s] < 0 || !elig[parent[s]])) sub_roots.push_back(s);
+    }
+    for (size_t t = 0; t < sub_roots.size(); ++t)
+        for (int s = sub_begin[sub_roots[t]]; s <= sub_roots[t]; ++s) F->sn[s].sub = (int32_t)t;
+
     // ---------------- numeric factorisation
-    const int bsz = o.block;
     const double eps = o.eps;
+    const int lrows = std::max(16, o.block);
     int fail = 0;
     auto factor_one = [&](int s, bool par) -> int {
         HSnode& h = F->sn[s];
@@ -332,8 +362,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             int bad = dense::potrf_partial(nf, ni, Fm.data(), nf, par);
             if (bad) return bad;
         }
-        // update matrix for the parent
-        if (nb > 0) {
+        if (nb > 0) {   // update matrix for the parent
             w.Ustore.assign((size_t)nb * nb, 0.0);
             for (int i = 0; i < nb; ++i)
                 std::memcpy(&w.Ustore[(size_t)i * nb], &Fm[(size_t)(ni + i) * nf + ni],
@@ -341,99 +370,86 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             if (ni > 0)
                 dense::syrk_lower_sub(nb, ni, &Fm[(size_t)ni * nf], nf, w.Ustore.data(), nb, par);
         }
-        if (ni == 0) return 0;
-        // M_s = [L_ss^-1 ; L_Bs L_ss^-1]
+        if (ni == 0) {
+            w.nd = 0;
+            return 0;
+        }
+        // M_s = [L_ss^-1 ; L_Bs L_ss^-1]  (nf x ni, row-major)
         std::vector<double> M((size_t)nf * ni);
         dense::trtri_lower(ni, Fm.data(), nf, M.data(), ni, par);
         if (nb > 0)
             dense::trmm_right_lower(nb, ni, &Fm[(size_t)ni * nf], nf, M.data(), ni,
                                     &M[(size_t)ni * ni], ni, par);
         std::vector<double>().swap(Fm);
-        // row blocks: L^-1 part by `bsz`, boundary part split at ancestor changes
-        std::vector<int> rb{0};
-        for (int r = bsz; r < ni; r += bsz) rb.push_back(r);
-        {
-            int start = ni;
-            int owner = -1;
-            for (int j = 0; j < nb; ++j) {
-                // owner cluster of boundary position: walk ancestors of s
-                int32_t pos = w.B[j];
+        // low-rank groups: boundary rows of an upper cluster, in runs owned by one
+        // ancestor separator, chunked to `lrows` rows; kept when the truncated
+        // rank-revealing QR reaches eps with k (m + ni) <= m ni / 2
+        std::vector<char> in_lr(nb, 0);
+        if (eps > 0.0 && h.sub < 0 && ni >= 16) {
+            int j = 0;
+            while (j < nb) {
                 int a = parent[s];
+                const int32_t pos = w.B[j];
                 while (a >= 0 && !(pos >= F->sn[a].first && pos < F->sn[a].first + F->sn[a].ni))
                     a = parent[a];
-                if (j == 0 || a != owner || ni + j - start >= bsz) {
-                    rb.push_back(ni + j);
-                    start = ni + j;
+                int e = j + 1;
+                while (e < nb && e - j < lrows && w.B[e] < F->sn[a].first + F->sn[a].ni) ++e;
+                const int m = e - j;
+                if (m >= 16) {
+                    const int kmax = std::min(LR_KMAX, (m * ni) / (2 * (m + ni)));
+                    std::vector<double> Ub, Vt;
+                    int k = dense::rrqr(m, ni, &M[(size_t)(ni + j) * ni], ni, eps, kmax, Ub, Vt);
+                    if (k >= 0) {
+                        HLr g{};
+                        g.s = s;
+                        g.row0 = ni + j;
+                        g.m = m;
+                        g.k = k;
+                        g.off_u = (int64_t)w.data.size();
+                        w.data.insert(w.data.end(), Ub.begin(), Ub.end());
+                        g.off_v = (int64_t)w.data.size();
+                        for (int c = 0; c < ni; ++c)          // V = Vt^T, row-major ni x k
+                            for (int l = 0; l < k; ++l) w.data.push_back(Vt[(size_t)l * ni + c]);
+                        w.lr.push_back(g);
+                        w.lr_e += (int64_t)k * (m + ni);
+                        for (int r = j; r < e; ++r) in_lr[r] = 1;
+                    }
                 }
-                owner = a;
+                j = e;
             }
         }
-        rb.push_back(nf);
-        rb.erase(std::unique(rb.begin(), rb.end()), rb.end());
-        std::vector<double> blk, Ub, Vb;
-        for (size_t R = 0; R + 1 < rb.size(); ++R) {
-            const int r0 = rb[R], r1 = rb[R + 1];
-            for (int c0 = 0; c0 < ni; c0 += bsz) {
-                const int c1 = std::min(ni, c0 + bsz);
-                if (r1 <= ni && c0 >= r1) continue;   // strictly upper part of L^-1
-                const int m = r1 - r0, nn = c1 - c0;
-                const bool diag = r0 < ni && c0 < r1 && r0 < c1;
-                HBlock b{};
-                b.row0 = r0;
-                b.col0 = c0;
-                b.m = m;
-                b.n = nn;
-                int k = -1;
-                if (eps > 0.0 && !diag && m >= 8 && nn >= 8) {
-                    const int kmax = (m * nn) / (2 * (m + nn));
-                    k = dense::rrqr(m, nn, &M[(size_t)r0 * ni + c0], ni, eps, kmax, Ub, Vb);
-                }
-                if (k == 0) continue;   // numerically zero block
-                b.off = (int64_t)w.data.size();
-                if (k > 0) {
-                    b.type = 1;
-                    b.k = k;
-                    w.data.insert(w.data.end(), Ub.begin(), Ub.end());
-                    w.data.insert(w.data.end(), Vb.begin(), Vb.end());
-                    w.lr_e += (int64_t)k * (m + nn);
-                    w.nl++;
-                } else {
-                    b.type = 0;
-                    b.k = 0;
-                    for (int i = 0; i < m; ++i)
-                        w.data.insert(w.data.end(), &M[(size_t)(r0 + i) * ni + c0],
-                                      &M[(size_t)(r0 + i) * ni + c1]);
-                    w.dense_e += (int64_t)m * nn;
-                    w.nd++;
-                }
-                w.blocks.push_back(b);
-            }
-        }
+        // packed dense columns over the dense rows
+        std::vector<int32_t> rows;
+        rows.reserve(nf);
+        for (int r = 0; r < ni; ++r) rows.push_back(r);
+        for (int r = 0; r < nb; ++r)
+            if (!in_lr[r]) rows.push_back(ni + r);
+        const int nd = (int)rows.size();
+        w.nd = nd;
+        w.drows.assign(rows.begin() + ni, rows.end());
+        w.dense_off = (int64_t)w.data.size();
+        for (int c = 0; c < ni; ++c)
+            for (int q = c; q < nd; ++q) w.data.push_back(M[(size_t)rows[q] * ni + c]);
+        w.dense_e += col_offset(nd, ni);
         return 0;
     };
 
     // subtrees below a cut depth run in parallel; the clusters above it run in
     // order with parallel dense kernels
+    const int nthreads_eff = nthreads;
     int cut = 0;
     {
         std::vector<int> cnt(64, 0);
         for (int s = 0; s < nt; ++s)
             if (depth[s] < 64) cnt[depth[s]]++;
-        while (cut < 63 && cnt[cut] < 4 * nthreads && cnt[cut + 1] > cnt[cut]) ++cut;
+        while (cut < 63 && cnt[cut] < 4 * nthreads_eff && cnt[cut + 1] > cnt[cut]) ++cut;
     }
     std::vector<int> roots, upper;
     for (int s = 0; s < nt; ++s) {
         if (depth[s] == cut || (depth[s] < cut && nch[s] == 0)) roots.push_back(s);
         else if (depth[s] < cut) upper.push_back(s);
     }
-    // subtree of s = contiguous post-order range ending at s
-    std::vector<int> sub_begin(nt);
-    for (int s = 0; s < nt; ++s) {
-        int b = s;
-        for (int k = 0; k < nch[s]; ++k) b = std::min(b, sub_begin[ch[s][k]]);
-        sub_begin[s] = b;
-    }
-    omp_set_num_threads(nthreads);
+    omp_set_num_threads(nthreads_eff);
     std::atomic<int> pfail{0};
 #pragma omp parallel for schedule(dynamic, 1)
     for (size_t i = 0; i < roots.size(); ++i) {
@@ -454,122 +470,151 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         }
     if (fail) return set_error(BID_EINVAL, "factorisation: non-positive pivot (matrix not SPD)");
 
-    // ---------------- pack blocks and tiles
-    int64_t total = 0;
-    for (int s = 0; s < nt; ++s) total += (int64_t)W[s].data.size();
-    F->data.resize(total);
-    F->dense_entries = F->lowrank_entries = F->dense_blocks = F->lowrank_blocks = 0;
-    std::vector<int64_t> blk_first(nt + 1, 0);
+    // ---------------- pack
     {
+        int64_t total = 0, nd_rows = 0;
+        for (int s = 0; s < nt; ++s) {
+            total += (int64_t)W[s].data.size();
+            nd_rows += (int64_t)W[s].drows.size();
+        }
+        F->data.resize(total);
+        F->drows.reserve(nd_rows);
         int64_t off = 0;
         for (int s = 0; s < nt; ++s) {
             SnWork& w = W[s];
+            HSnode& h = F->sn[s];
             std::memcpy(F->data.data() + off, w.data.data(), w.data.size() * sizeof(double));
-            blk_first[s] = (int64_t)F->blk.size();
-            for (HBlock b : w.blocks) {
-                b.off += off;
-                F->blk.push_back(b);
+            h.nd = w.nd;
+            h.data_off = off + w.dense_off;
+            h.drow_off = (int32_t)F->drows.size();
+            F->drows.insert(F->drows.end(), w.drows.begin(), w.drows.end());
+            h.lr_begin = h.lr_end = 0;   // set below (groups ordered by level)
+            for (HLr& g : w.lr) {
+                g.off_u += off;
+                g.off_v += off;
             }
             off += (int64_t)w.data.size();
             F->dense_entries += w.dense_e;
             F->lowrank_entries += w.lr_e;
-            F->dense_blocks += w.nd;
-            F->lowrank_blocks += w.nl;
             std::vector<double>().swap(w.data);
         }
-        blk_first[nt] = (int64_t)F->blk.size();
     }
-    const int H = F->height;
-    std::vector<std::vector<HTile>> tfl(H), tbl(H);
-    std::vector<std::vector<std::vector<int32_t>>> lfl(H), lbl(H);
-    F->ni_max.assign(H, 0);
-    for (int s = 0; s < nt; ++s) {
-        const HSnode& h = F->sn[s];
-        const int lev = h.height;
-        F->ni_max[lev] = std::max(F->ni_max[lev], h.ni);
-        const int nf = h.ni + h.nb;
-        if (nf == 0) continue;
-        // forward: row panels of `bsz` rows following the block partition
-        std::vector<std::pair<int, int>> rows;   // distinct (row0, m) of the blocks
-        for (int64_t b = blk_first[s]; b < blk_first[s + 1]; ++b)
-            rows.push_back({F->blk[b].row0, F->blk[b].m});
-        if (h.ni == 0)
-            for (int r = 0; r < nf; r += bsz) rows.push_back({r, std::min(bsz, nf - r)});
-        std::sort(rows.begin(), rows.end());
-        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
-        for (auto [r0, m] : rows) {
-            HTile t{};
-            t.s = s;
-            t.r0 = r0;
-            t.len = m;
-            std::vector<int32_t> list;
-            for (int64_t b = blk_first[s]; b < blk_first[s + 1]; ++b)
-                if (F->blk[b].row0 == r0) {
-                    list.push_back((int32_t)b);
-                    if (F->blk[b].type == 1) t.tsum += F->blk[b].k;
+    // bottom subtree tasks
+    const int nsub = (int)sub_roots.size();
+    F->nsub = nsub;
+    F->sub_lev.resize(nsub);
+    F->sub_nlev.resize(nsub);
+    for (int t = 0; t < nsub; ++t) {
+        const int r = sub_roots[t];
+        const int nlev = F->sn[r].height + 1;
+        F->sub_lev[t] = (int32_t)F->sfp.size();
+        F->sub_nlev[t] = nlev;
+        for (int lev = 0; lev < nlev; ++lev) {
+            F->sfp.push_back((int32_t)F->sft.size());
+            F->sbp.push_back((int32_t)F->sbt.size());
+            for (int s = sub_begin[r]; s <= r; ++s) {
+                const HSnode& h = F->sn[s];
+                if (h.height != lev || h.ni + h.nb == 0) continue;
+                const int rows = h.ni + h.nb;   // no low-rank groups in bottom clusters
+                for (int a = 0; a < rows; a += SUB_ROWS) {
+                    HTask k{};
+                    k.s = s;
+                    k.a0 = a;
+                    k.a1 = std::min(rows, a + SUB_ROWS);
+                    F->sft.push_back(k);
                 }
-            tfl[lev].push_back(t);
-            lfl[lev].push_back(std::move(list));
-        }
-        // rows of M_s not covered by any block (all blocks numerically zero)
-        // still need their outputs written: add empty panels for them
-        {
-            std::vector<char> cov(nf, 0);
-            for (auto [r0, m] : rows)
-                for (int i = 0; i < m; ++i) cov[r0 + i] = 1;
-            for (int r = 0; r < nf;) {
-                if (cov[r]) { ++r; continue; }
-                int e = r;
-                while (e < nf && !cov[e] && e - r < bsz) ++e;
-                HTile t{};
-                t.s = s;
-                t.r0 = r;
-                t.len = e - r;
-                tfl[lev].push_back(t);
-                lfl[lev].push_back({});
-                r = e;
+                const int cpw = 4;
+                for (int a = 0; a < h.ni; a += cpw) {
+                    HTask k{};
+                    k.s = s;
+                    k.a0 = a;
+                    k.a1 = std::min<int>(h.ni, a + cpw);
+                    F->sbt.push_back(k);
+                }
             }
         }
-        // backward: column panels
-        for (int c0 = 0; c0 < h.ni; c0 += bsz) {
-            HTile t{};
-            t.s = s;
-            t.r0 = c0;
-            t.len = std::min(bsz, h.ni - c0);
-            std::vector<int32_t> list;
-            for (int64_t b = blk_first[s]; b < blk_first[s + 1]; ++b)
-                if (F->blk[b].col0 == c0) {
-                    list.push_back((int32_t)b);
-                    if (F->blk[b].type == 1) t.tsum += F->blk[b].k;
+        F->sfp.push_back((int32_t)F->sft.size());
+        F->sbp.push_back((int32_t)F->sbt.size());
+    }
+    // upper levels, ascending height
+    std::vector<int> ulev;
+    for (int s = 0; s < nt; ++s)
+        if (F->sn[s].sub < 0) ulev.push_back(F->sn[s].height);
+    std::sort(ulev.begin(), ulev.end());
+    ulev.erase(std::unique(ulev.begin(), ulev.end()), ulev.end());
+    const int nul = (int)ulev.size();
+    F->height = nul;
+    F->ulr_ptr.assign(1, 0);
+    F->uf_ptr.assign(1, 0);
+    F->ub_ptr.assign(1, 0);
+    int64_t tbuf = 0, pbuf = 0;
+    int32_t tickets = 0;
+    for (int L = 0; L < nul; ++L) {
+        int ni_max = 0, nd_max = 0;
+        for (int s = 0; s < nt; ++s) {
+            HSnode& h = F->sn[s];
+            if (h.sub >= 0 || h.height != ulev[L]) continue;
+            ni_max = std::max(ni_max, h.ni);
+            nd_max = std::max(nd_max, h.nd);
+            h.lr_begin = (int32_t)F->lr.size();
+            for (HLr g : W[s].lr) {
+                g.t_off = (int32_t)tbuf;
+                tbuf += g.k;
+                F->lr.push_back(g);
+            }
+            h.lr_end = (int32_t)F->lr.size();
+            // forward dense row chunks
+            for (int a = 0; a < h.nd; a += UP_ROWS) {
+                const int a1 = std::min(h.nd, a + UP_ROWS);
+                const int cols = a1 <= h.ni ? a1 : h.ni;
+                const int np = (cols + UP_COLS - 1) / UP_COLS;
+                int32_t part = -1, tk = -1;
+                if (np > 1) {
+                    part = (int32_t)pbuf;
+                    pbuf += (int64_t)np * (a1 - a);
+                    tk = tickets++;
                 }
-            tbl[lev].push_back(t);
-            lbl[lev].push_back(std::move(list));
+                for (int c = 0; c < np; ++c) {
+                    HTask k{};
+                    k.s = s;
+                    k.a0 = a;
+                    k.a1 = a1;
+                    k.b0 = c * UP_COLS;
+                    k.b1 = std::min(cols, (c + 1) * UP_COLS);
+                    k.part = part;
+                    k.ticket = tk;
+                    k.nparts = np;
+                    F->uft.push_back(k);
+                }
+            }
+            for (int g = h.lr_begin; g < h.lr_end; ++g)
+                for (int a = 0; a < F->lr[g].m; a += UP_ROWS) {
+                    HTask k{};
+                    k.s = -1 - g;
+                    k.a0 = a;
+                    k.a1 = std::min(F->lr[g].m, a + UP_ROWS);
+                    k.nparts = 1;
+                    k.part = k.ticket = -1;
+                    F->uft.push_back(k);
+                }
+            for (int a = 0; a < h.ni; a += UP_BCOLS) {
+                HTask k{};
+                k.s = s;
+                k.a0 = a;
+                k.a1 = std::min(h.ni, a + UP_BCOLS);
+                F->ubt.push_back(k);
+            }
         }
+        F->u_ni_max.push_back(ni_max);
+        F->u_nd_max.push_back(nd_max);
+        F->ulr_ptr.push_back((int32_t)F->lr.size());
+        F->uf_ptr.push_back((int32_t)F->uft.size());
+        F->ub_ptr.push_back((int32_t)F->ubt.size());
     }
-    F->tf_ptr.assign(H + 1, 0);
-    F->tb_ptr.assign(H + 1, 0);
-    F->tsum_max_f.assign(H, 0);
-    F->tsum_max_b.assign(H, 0);
-    for (int lev = 0; lev < H; ++lev) {
-        for (size_t i = 0; i < tfl[lev].size(); ++i) {
-            HTile t = tfl[lev][i];
-            t.blk_begin = (int32_t)F->lf.size();
-            F->lf.insert(F->lf.end(), lfl[lev][i].begin(), lfl[lev][i].end());
-            t.blk_end = (int32_t)F->lf.size();
-            F->tsum_max_f[lev] = std::max(F->tsum_max_f[lev], t.tsum);
-            F->tf.push_back(t);
-        }
-        for (size_t i = 0; i < tbl[lev].size(); ++i) {
-            HTile t = tbl[lev][i];
-            t.blk_begin = (int32_t)F->lb.size();
-            F->lb.insert(F->lb.end(), lbl[lev][i].begin(), lbl[lev][i].end());
-            t.blk_end = (int32_t)F->lb.size();
-            F->tsum_max_b[lev] = std::max(F->tsum_max_b[lev], t.tsum);
-            F->tb.push_back(t);
-        }
-        F->tf_ptr[lev + 1] = (int32_t)F->tf.size();
-        F->tb_ptr[lev + 1] = (int32_t)F->tb.size();
-    }
+    F->tbuf = tbuf;
+    F->pbuf = pbuf;
+    F->ntickets = tickets;
+    F->nlr = (int64_t)F->lr.size();
     return BID_OK;
 }
 

@@ -16,81 +16,127 @@ struct bid_host_system {
 namespace bid {
 namespace {
 
-// x = P^-1 (b - shift) with the pinned entry zeroed: forward over tiles of
-// each level (leaves first), then backward (root first).
+// x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
+// the same order, as the GPU launches (bottom subtrees, then upper levels).
 void replay(const HFactorHost& F, const double* b, double shift, double* x) {
     std::vector<double> y(F.n, 0.0), u(std::max<int64_t>(F.ubuf, 1), 0.0);
+    std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
-    for (int lev = 0; lev < F.height; ++lev)
-        for (int ti = F.tf_ptr[lev]; ti < F.tf_ptr[lev + 1]; ++ti) {
-            const HTile& t = F.tf[ti];
-            const HSnode& s = F.sn[t.s];
-            std::vector<double> w(s.ni);
-            for (int i = 0; i < s.ni; ++i) {
-                const int v = F.pidx[s.first + i];
-                double val = v == F.pin ? 0.0 : b[v] - shift;
-                const int c0 = F.inc[s.inc_off + 2 * i], c1 = F.inc[s.inc_off + 2 * i + 1];
-                if (c0 >= 0) val += u[c0];
-                if (c1 >= 0) val += u[c1];
-                w[i] = val;
+    auto gather = [&](const HSnode& s, int i) {
+        const int v = F.pidx[s.first + i];
+        double val = v == F.pin ? 0.0 : b[v] - shift;
+        const int c0 = F.inc[s.inc_off + 2 * i], c1 = F.inc[s.inc_off + 2 * i + 1];
+        if (c0 >= 0) val += u[c0];
+        if (c1 >= 0) val += u[c1];
+        return val;
+    };
+    auto finish = [&](const HSnode& s, int R, double acc) {
+        if (R < s.ni) {
+            y[s.first + R] = acc;
+        } else {
+            double in = 0.0;
+            const int c0 = F.inc[s.inc_off + 2 * R], c1 = F.inc[s.inc_off + 2 * R + 1];
+            if (c0 >= 0) in += u[c0];
+            if (c1 >= 0) in += u[c1];
+            u[s.u_off + R - s.ni] = in - acc;
+        }
+    };
+    auto drow = [&](const HSnode& s, int q) { return q < s.ni ? q : F.drows[s.drow_off + q - s.ni]; };
+    auto elem = [&](const HSnode& s, int q, int j) { return D[s.data_off + col_offset(s.nd, j) + q - j]; };
+    // dense forward rows [a0,a1) over columns [b0,b1)
+    auto fwd_rows = [&](const HSnode& s, int a0, int a1, int b0, int b1, std::vector<double>& acc) {
+        for (int q = a0; q < a1; ++q) {
+            const int jend = q < s.ni ? std::min(b1, q + 1) : b1;
+            for (int j = b0; j < jend; ++j) acc[q - a0] += elem(s, q, j) * gather(s, j);
+        }
+    };
+    for (int64_t st = 0; st < F.nsub; ++st)
+        for (int lev = 0; lev < F.sub_nlev[st]; ++lev)
+            for (int ti = F.sfp[F.sub_lev[st] + lev]; ti < F.sfp[F.sub_lev[st] + lev + 1]; ++ti) {
+                const HTask& k = F.sft[ti];
+                const HSnode& s = F.sn[k.s];
+                std::vector<double> acc(k.a1 - k.a0, 0.0);
+                fwd_rows(s, k.a0, k.a1, 0, s.ni, acc);
+                for (int q = k.a0; q < k.a1; ++q) finish(s, drow(s, q), acc[q - k.a0]);
             }
-            std::vector<double> acc(t.len, 0.0);
-            for (int bi = t.blk_begin; bi < t.blk_end; ++bi) {
-                const HBlock& B = F.blk[F.lf[bi]];
-                if (B.type == 0) {
-                    for (int i = 0; i < B.m; ++i)
-                        for (int j = 0; j < B.n; ++j)
-                            acc[i] += D[B.off + (int64_t)i * B.n + j] * w[B.col0 + j];
-                } else {
-                    const double* U = D + B.off;
-                    const double* Vt = U + (int64_t)B.m * B.k;
-                    for (int l = 0; l < B.k; ++l) {
-                        double tl = 0.0;
-                        for (int j = 0; j < B.n; ++j) tl += Vt[(int64_t)l * B.n + j] * w[B.col0 + j];
-                        for (int i = 0; i < B.m; ++i) acc[i] += U[(int64_t)i * B.k + l] * tl;
-                    }
-                }
-            }
-            for (int i = 0; i < t.len; ++i) {
-                const int row = t.r0 + i;
-                if (row < s.ni) {
-                    y[s.first + row] = acc[i];
-                } else {
-                    double in = 0.0;
-                    const int c0 = F.inc[s.inc_off + 2 * row], c1 = F.inc[s.inc_off + 2 * row + 1];
-                    if (c0 >= 0) in += u[c0];
-                    if (c1 >= 0) in += u[c1];
-                    u[s.u_off + row - s.ni] = in - acc[i];
-                }
+    const int nul = (int)F.uf_ptr.size() - 1;
+    for (int lev = 0; lev < nul; ++lev) {
+        for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
+            const HLr& G = F.lr[g];
+            const HSnode& s = F.sn[G.s];
+            for (int l = 0; l < G.k; ++l) {
+                double a = 0.0;
+                for (int j = 0; j < s.ni; ++j) a += D[G.off_v + (int64_t)j * G.k + l] * gather(s, j);
+                t[G.t_off + l] = a;
             }
         }
-    for (int lev = F.height - 1; lev >= 0; --lev)
-        for (int ti = F.tb_ptr[lev]; ti < F.tb_ptr[lev + 1]; ++ti) {
-            const HTile& t = F.tb[ti];
-            const HSnode& s = F.sn[t.s];
-            std::vector<double> acc(t.len, 0.0);
-            for (int bi = t.blk_begin; bi < t.blk_end; ++bi) {
-                const HBlock& B = F.blk[F.lb[bi]];
-                std::vector<double> v(B.m);
-                for (int i = 0; i < B.m; ++i) {
-                    const int R = B.row0 + i;
-                    v[i] = R < s.ni ? y[s.first + R] : -x[F.bidx[s.bidx_off + R - s.ni]];
+        // row chunks may be split over column chunks: sum the chunks in order
+        std::vector<std::pair<int, int>> done;
+        for (int ti = F.uf_ptr[lev]; ti < F.uf_ptr[lev + 1]; ++ti) {
+            const HTask& k = F.uft[ti];
+            if (k.s < 0) {
+                const HLr& G = F.lr[-1 - k.s];
+                const HSnode& s = F.sn[G.s];
+                for (int i = k.a0; i < k.a1; ++i) {
+                    double a = 0.0;
+                    for (int l = 0; l < G.k; ++l) a += D[G.off_u + (int64_t)i * G.k + l] * t[G.t_off + l];
+                    finish(s, G.row0 + i, a);
                 }
-                if (B.type == 0) {
-                    for (int i = 0; i < B.m; ++i)
-                        for (int j = 0; j < B.n; ++j) acc[j] += D[B.off + (int64_t)i * B.n + j] * v[i];
-                } else {
-                    const double* U = D + B.off;
-                    const double* Vt = U + (int64_t)B.m * B.k;
-                    for (int l = 0; l < B.k; ++l) {
-                        double tl = 0.0;
-                        for (int i = 0; i < B.m; ++i) tl += U[(int64_t)i * B.k + l] * v[i];
-                        for (int j = 0; j < B.n; ++j) acc[j] += Vt[(int64_t)l * B.n + j] * tl;
-                    }
+                continue;
+            }
+            if (k.b0 != 0) continue;   // the first chunk task finishes the whole row chunk
+            const HSnode& s = F.sn[k.s];
+            std::vector<double> acc(k.a1 - k.a0, 0.0);
+            for (int c = 0; c < k.nparts; ++c) {
+                std::vector<double> part(k.a1 - k.a0, 0.0);
+                const HTask& kc = F.uft[ti + c];
+                fwd_rows(s, kc.a0, kc.a1, kc.b0, kc.b1, part);
+                for (size_t i = 0; i < part.size(); ++i) acc[i] += part[i];
+            }
+            for (int q = k.a0; q < k.a1; ++q) finish(s, drow(s, q), acc[q - k.a0]);
+        }
+    }
+    auto vrow = [&](const HSnode& s, int q) {
+        return q < s.ni ? y[s.first + q] : -x[F.bidx[s.bidx_off + drow(s, q) - s.ni]];
+    };
+    for (int lev = nul - 1; lev >= 0; --lev) {
+        for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
+            const HLr& G = F.lr[g];
+            const HSnode& s = F.sn[G.s];
+            for (int l = 0; l < G.k; ++l) {
+                double a = 0.0;
+                for (int i = 0; i < G.m; ++i)
+                    a += D[G.off_u + (int64_t)i * G.k + l] * -x[F.bidx[s.bidx_off + G.row0 + i - s.ni]];
+                t[G.t_off + l] = a;
+            }
+        }
+        for (int ti = F.ub_ptr[lev]; ti < F.ub_ptr[lev + 1]; ++ti) {
+            const HTask& k = F.ubt[ti];
+            const HSnode& s = F.sn[k.s];
+            std::vector<double> vv(s.nd);
+            for (int q = 0; q < s.nd; ++q) vv[q] = vrow(s, q);
+            for (int j = k.a0; j < k.a1; ++j) {
+                double a = 0.0;
+                for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vv[q];
+                for (int g = s.lr_begin; g < s.lr_end; ++g) {
+                    const HLr& G = F.lr[g];
+                    for (int l = 0; l < G.k; ++l) a += D[G.off_v + (int64_t)j * G.k + l] * t[G.t_off + l];
+                }
+                x[F.pidx[s.first + j]] = a;
+            }
+        }
+    }
+    for (int64_t st = 0; st < F.nsub; ++st)
+        for (int lev = F.sub_nlev[st] - 1; lev >= 0; --lev)
+            for (int ti = F.sbp[F.sub_lev[st] + lev]; ti < F.sbp[F.sub_lev[st] + lev + 1]; ++ti) {
+                const HTask& k = F.sbt[ti];
+                const HSnode& s = F.sn[k.s];
+                for (int j = k.a0; j < k.a1; ++j) {
+                    double a = 0.0;
+                    for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
+                    x[F.pidx[s.first + j]] = a;
                 }
             }
-            for (int j = 0; j < t.len; ++j) x[F.pidx[s.first + t.r0 + j]] = acc[j];
-        }
 }
 
 }  // namespace
@@ -144,7 +190,7 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps, int leaf,
                           int block, const double* b, double* x, bid_precond_stats* stats) {
     if (!h || !b || !x || (which != 1 && which != 2)) return set_error(BID_EINVAL, "bad argument");
-    if (!(eps >= 0.0) || block < 8 || block > 64) return set_error(BID_EINVAL, "bad eps/block");
+    if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
     HBuildOpts o;
     o.eps = eps;
     o.leaf = leaf;
@@ -168,11 +214,11 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
         std::memset(stats, 0, sizeof(*stats));
         stats->n1 = F.n;
         stats->supernodes1 = (int64_t)F.sn.size();
-        stats->levels1 = F.height;
+        stats->levels1 = F.height + (F.nsub > 0 ? 1 : 0);
         stats->dense_entries = F.dense_entries;
         stats->lowrank_entries = F.lowrank_entries;
-        stats->dense_blocks = F.dense_blocks;
-        stats->lowrank_blocks = F.lowrank_blocks;
+        stats->dense_blocks = F.nsub;
+        stats->lowrank_blocks = F.nlr;
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
     }
     return BID_OK;

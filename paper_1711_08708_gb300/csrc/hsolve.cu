@@ -1,17 +1,24 @@
-// Triangular solves with the hierarchical Cholesky factors (the P_1^-1 and
-// P_K^-1 applications of eq. prec2; factor layout described in hfactor.cpp).
+// Triangular solves with the hierarchical Cholesky factors: the P_1^-1 and
+// P_K^-1 applications of eq. prec2 (factor layout in internal.h / hfactor.cpp).
 //
-// Forward pass, one launch per tree level (leaves first), one CTA per row
-// panel ("tile") of a cluster's block M_s = [L_ss^-1; L_Bs L_ss^-1]:
-//   w_s = b[I_s] - shift + children's update entries        (gathered)
-//   rows of L_ss^-1:  y_s = L_ss^-1 w_s                      -> ybuf
-//   rows of L_Bs L_ss^-1: u_s = children's entries on B_s - (L_Bs L_ss^-1) w_s
-// Backward pass, one launch per level (root first), one CTA per column panel:
-//   x_s = (L_ss^-1)^T y_s - (L_Bs L_ss^-1)^T x_B              -> out[I_s]
-// Every block is dense (row-major) or low rank (U Vt).  The factor is stored
-// in FP64, FP32 or BF16; FP32/BF16 factors accumulate in FP32 (precision
-// form), FP64 factors in FP64.  Reductions run in a fixed order, so results
-// are bitwise reproducible.
+// Forward pass (leaves first), for each cluster s with gathered input
+//   w_s = b[I_s] - shift + children's update entries,
+// computes y_s = L_ss^-1 w_s (rows q < ni of M_s) and the update vector
+//   u_s = children's entries on B_s - (L_Bs L_ss^-1) w_s (boundary rows).
+// Backward pass (root first): x_s = (L_ss^-1)^T y_s - (L_Bs L_ss^-1)^T x_B.
+//
+// Launches of one solve:
+//   k_sub_fwd   one CTA per bottom subtree, all its levels (warp tasks, CTA
+//               barrier between levels);
+//   per upper level: k_lr_fwd (V^T w of the low-rank groups, if any) and
+//               k_up_fwd (thread per dense row over a column chunk; chunks of
+//               a row are combined in a fixed order by the last CTA);
+//   per upper level, root first: k_lr_bwd (U^T v) and k_up_bwd (warp per
+//               column over the packed column, v staged in shared memory);
+//   k_sub_bwd   one CTA per bottom subtree.
+// Factors are stored in FP64, FP32 or BF16; FP32/BF16 accumulate in FP32 (the
+// precision form), FP64 in FP64.  All reductions have a fixed order, so the
+// result is bitwise reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -23,14 +30,13 @@ namespace bid {
 
 namespace {
 
-constexpr int HT = 256;          // threads per CTA
-constexpr int MAX_TILE_BLOCKS = 256;
+constexpr int HT = 256;   // threads per CTA
+constexpr int NW = HT / 32;
+constexpr int RPL = SUB_ROWS / 32;   // rows per lane in the bottom kernels
 
 __device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
-__device__ __forceinline__ float ldv(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p)));
-}
+__device__ __forceinline__ float ldv(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
 template <typename A>
 __device__ __forceinline__ A wsum(A v) {
@@ -44,143 +50,287 @@ struct HView {
     const int32_t* __restrict__ pidx;
     const int32_t* __restrict__ bidx;
     const int32_t* __restrict__ inc;
+    const int32_t* __restrict__ drows;
     const HSnode* __restrict__ sn;
-    const HBlock* __restrict__ blk;
-    const HTile* __restrict__ tf;
-    const HTile* __restrict__ tb;
-    const int32_t* __restrict__ lf;
-    const int32_t* __restrict__ lb;
+    const HLr* __restrict__ lr;
+    const int32_t* __restrict__ sub_lev;
+    const int32_t* __restrict__ sub_nlev;
+    const int32_t* __restrict__ sfp;
+    const int32_t* __restrict__ sbp;
+    const HTask* __restrict__ sft;
+    const HTask* __restrict__ sbt;
+    const HTask* __restrict__ uft;
+    const HTask* __restrict__ ubt;
 };
 
-template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_hfwd(HView v, const T* __restrict__ data, int tile0,
-                                             const double* __restrict__ in,
-                                             const double* shift_sum, double inv_n,
-                                             double* __restrict__ ybuf,
-                                             double* __restrict__ ubuf) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    HBlock* bl = reinterpret_cast<HBlock*>(smem);
-    const HTile t = v.tf[tile0 + blockIdx.x];
-    const HSnode sn = v.sn[t.s];
-    const int nblk = t.blk_end - t.blk_begin;
-    A* w = reinterpret_cast<A*>(smem + sizeof(HBlock) * MAX_TILE_BLOCKS);
-    A* tb = w + ((sn.ni + 1) & ~1);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = HT / 32;
+// gathered forward input entry i of cluster sn (ubuf holds finished children)
+__device__ __forceinline__ double gather_w(const HView& v, const HSnode& sn, int i,
+                                           const double* __restrict__ in, double shift,
+                                           const double* ubuf) {
+    const int vi = v.pidx[sn.first + i];
+    double val = (vi == v.pin) ? 0.0 : in[vi] - shift;
+    const int c0 = v.inc[sn.inc_off + 2 * i], c1 = v.inc[sn.inc_off + 2 * i + 1];
+    if (c0 >= 0) val += ubuf[c0];
+    if (c1 >= 0) val += ubuf[c1];
+    return val;
+}
 
-    for (int i = tid; i < nblk; i += HT) bl[i] = v.blk[v.lf[t.blk_begin + i]];
-    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
-    for (int i = tid; i < sn.ni; i += HT) {
-        const int vi = v.pidx[sn.first + i];
-        double val = (vi == v.pin) ? 0.0 : in[vi] - shift;
-        const int c0 = v.inc[sn.inc_off + 2 * i], c1 = v.inc[sn.inc_off + 2 * i + 1];
-        if (c0 >= 0) val += ubuf[c0];
-        if (c1 >= 0) val += ubuf[c1];
-        w[i] = (A)val;
-    }
-    __syncthreads();
-    // low-rank blocks: t_l = Vt[l,:] . w[col0 : col0+n]
-    {
-        int tofs = 0;
-        for (int b = 0; b < nblk; ++b) {
-            const HBlock B = bl[b];
-            if (B.type != 1) continue;
-            const T* Vt = data + B.off + (int64_t)B.m * B.k;
-            for (int l = warp; l < B.k; l += nw) {
-                A s = 0;
-                for (int j = lane; j < B.n; j += 32) s += (A)ldv(Vt + (int64_t)l * B.n + j) * w[B.col0 + j];
-                s = wsum(s);
-                if (lane == 0) tb[tofs + l] = s;
-            }
-            tofs += B.k;
-        }
-    }
-    __syncthreads();
-    for (int i = warp; i < t.len; i += nw) {
-        const int row = t.r0 + i;
-        A acc = 0;
-        int tofs = 0;
-        for (int b = 0; b < nblk; ++b) {
-            const HBlock B = bl[b];
-            const int li = row - B.row0;
-            if (B.type == 0) {
-                const T* D = data + B.off + (int64_t)li * B.n;
-                const A* wc = w + B.col0;
-                for (int j = lane; j < B.n; j += 32) acc += (A)ldv(D + j) * wc[j];
-            } else {
-                const T* U = data + B.off + (int64_t)li * B.k;
-                for (int l = lane; l < B.k; l += 32) acc += (A)ldv(U + l) * tb[tofs + l];
-                tofs += B.k;
-            }
-        }
-        acc = wsum(acc);
-        if (lane == 0) {
-            if (row < sn.ni) {
-                ybuf[sn.first + row] = (double)acc;
-            } else {
-                double u = 0.0;
-                const int c0 = v.inc[sn.inc_off + 2 * row], c1 = v.inc[sn.inc_off + 2 * row + 1];
-                if (c0 >= 0) u += ubuf[c0];
-                if (c1 >= 0) u += ubuf[c1];
-                ubuf[sn.u_off + row - sn.ni] = u - (double)acc;
-            }
-        }
+// store the forward result of M_s row R
+__device__ __forceinline__ void finish_row(const HView& v, const HSnode& sn, int R, double acc,
+                                           double* ybuf, double* ubuf) {
+    if (R < sn.ni) {
+        ybuf[sn.first + R] = acc;
+    } else {
+        double u = 0.0;
+        const int c0 = v.inc[sn.inc_off + 2 * R], c1 = v.inc[sn.inc_off + 2 * R + 1];
+        if (c0 >= 0) u += ubuf[c0];
+        if (c1 >= 0) u += ubuf[c1];
+        ubuf[sn.u_off + R - sn.ni] = u - acc;
     }
 }
 
-// Backward pass: CTA = column panel [r0, r0+len) of M_s (len <= 64); thread
-// (g, j) with g = tid / 64 accumulates rows g, g+4, ... of every block.
+__device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q) {
+    return q < sn.ni ? q : v.drows[sn.drow_off + q - sn.ni];
+}
+
+// ------------------------------------------------------------ bottom subtrees
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_hbwd(HView v, const T* __restrict__ data, int tile0,
-                                             const double* __restrict__ ybuf,
-                                             double* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    HBlock* bl = reinterpret_cast<HBlock*>(smem);
-    A* vseg = reinterpret_cast<A*>(smem + sizeof(HBlock) * MAX_TILE_BLOCKS);   // 128 entries
-    A* part = vseg + 128;                                                       // 4 x 64
-    A* tb = part + 4 * 64;                                                      // ranks
-    const HTile t = v.tb[tile0 + blockIdx.x];
-    const HSnode sn = v.sn[t.s];
-    const int nblk = t.blk_end - t.blk_begin;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = HT / 32;
-    const int j = tid & 63, g = tid >> 6;
-    for (int i = tid; i < nblk; i += HT) bl[i] = v.blk[v.lb[t.blk_begin + i]];
-    __syncthreads();
-    A acc = 0;
-    for (int b = 0; b < nblk; ++b) {
-        const HBlock B = bl[b];
-        for (int i = tid; i < B.m; i += HT) {
-            const int R = B.row0 + i;
-            double val = R < sn.ni ? ybuf[sn.first + R] : -out[v.bidx[sn.bidx_off + R - sn.ni]];
-            vseg[i] = (A)val;
-        }
-        __syncthreads();
-        if (B.type == 0) {
-            if (j < B.n) {
-                const T* D = data + B.off + j;
-                for (int i = g; i < B.m; i += 4) acc += (A)ldv(D + (int64_t)i * B.n) * vseg[i];
+__global__ void __launch_bounds__(HT) k_sub_fwd(HView v, const T* __restrict__ data,
+                                                const double* __restrict__ in,
+                                                const double* shift_sum, double inv_n,
+                                                double* ybuf, double* ubuf) {
+    __shared__ A wsh[NW][SUB_NI];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = v.sub_lev[blockIdx.x], nlev = v.sub_nlev[blockIdx.x];
+    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
+    A* w = wsh[warp];
+    for (int lev = 0; lev < nlev; ++lev) {
+        const int t0 = v.sfp[base + lev], t1 = v.sfp[base + lev + 1];
+        for (int ti = t0 + warp; ti < t1; ti += NW) {
+            const HTask t = v.sft[ti];
+            const HSnode sn = v.sn[t.s];
+            for (int i = lane; i < sn.ni; i += 32) w[i] = (A)gather_w(v, sn, i, in, shift, ubuf);
+            __syncwarp();
+            A acc[RPL];
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) acc[r] = 0;
+            const T* col = data + sn.data_off;
+            for (int j = 0; j < sn.ni; ++j) {
+                const A wj = w[j];
+                const T* cj = col + col_offset(sn.nd, j) - j;   // element q of column j at cj[q]
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int q = t.a0 + lane + 32 * r;
+                    if (q < t.a1 && q >= j) acc[r] += (A)ldv(cj + q) * wj;
+                }
             }
-        } else {
-            const T* U = data + B.off;
-            const T* Vt = U + (int64_t)B.m * B.k;
-            for (int l = warp; l < B.k; l += nw) {
-                A s = 0;
-                for (int i = lane; i < B.m; i += 32) s += (A)ldv(U + (int64_t)i * B.k + l) * vseg[i];
-                s = wsum(s);
-                if (lane == 0) tb[l] = s;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int q = t.a0 + lane + 32 * r;
+                if (q < t.a1) finish_row(v, sn, q, (double)acc[r], ybuf, ubuf);
             }
-            __syncthreads();
-            if (j < B.n)
-                for (int l = g; l < B.k; l += 4) acc += (A)ldv(Vt + (int64_t)l * B.n + j) * tb[l];
+            __syncwarp();
         }
         __syncthreads();
     }
-    part[g * 64 + j] = acc;
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_sub_bwd(HView v, const T* __restrict__ data,
+                                                const double* __restrict__ ybuf, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = v.sub_lev[blockIdx.x], nlev = v.sub_nlev[blockIdx.x];
+    for (int lev = nlev - 1; lev >= 0; --lev) {
+        const int t0 = v.sbp[base + lev], t1 = v.sbp[base + lev + 1];
+        for (int ti = t0 + warp; ti < t1; ti += NW) {
+            const HTask t = v.sbt[ti];
+            const HSnode sn = v.sn[t.s];
+            A vv[RPL];
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int q = lane + 32 * r;
+                double x = 0.0;
+                if (q < sn.nd)
+                    x = q < sn.ni ? ybuf[sn.first + q]
+                                  : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
+                vv[r] = (A)x;
+            }
+            const T* col = data + sn.data_off;
+            for (int j = t.a0; j < t.a1; ++j) {
+                const T* cj = col + col_offset(sn.nd, j) - j;
+                A acc = 0;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int q = lane + 32 * r;
+                    if (q >= j && q < sn.nd) acc += (A)ldv(cj + q) * vv[r];
+                }
+                acc = wsum(acc);
+                if (lane == 0) out[v.pidx[sn.first + j]] = (double)acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ upper levels
+// t_g = V_g^T w_s for every low-rank group g of the level (one CTA per group)
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_lr_fwd(HView v, const T* __restrict__ data, int g0,
+                                               const double* __restrict__ in,
+                                               const double* shift_sum, double inv_n,
+                                               const double* ubuf, double* tbuf) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const HLr g = v.lr[g0 + blockIdx.x];
+    const HSnode sn = v.sn[g.s];
+    A* w = reinterpret_cast<A*>(smem);
+    A* red = w + ((sn.ni + 1) & ~1);
+    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
+    for (int i = threadIdx.x; i < sn.ni; i += HT) w[i] = (A)gather_w(v, sn, i, in, shift, ubuf);
     __syncthreads();
-    if (tid < t.len) {
-        A s = part[tid] + part[64 + tid];
-        s += part[128 + tid];
-        s += part[192 + tid];
-        out[v.pidx[sn.first + t.r0 + tid]] = (double)s;
+    const int kp = g.k <= 32 ? 32 : 64, ng = HT / kp;
+    const int l = threadIdx.x % kp, grp = threadIdx.x / kp;
+    A acc = 0;
+    if (l < g.k) {
+        const T* V = data + g.off_v;
+        for (int j = grp; j < sn.ni; j += ng) acc += (A)ldv(V + (int64_t)j * g.k + l) * w[j];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < g.k) {
+        A s = 0;
+        for (int q = 0; q < ng; ++q) s += red[q * kp + threadIdx.x];
+        tbuf[g.t_off + threadIdx.x] = (double)s;
+    }
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ data, int task0,
+                                               const double* __restrict__ in,
+                                               const double* shift_sum, double inv_n,
+                                               double* ybuf, double* ubuf, const double* tbuf,
+                                               double* pbuf, unsigned int* tickets) {
+    __shared__ A w[UP_COLS];
+    __shared__ bool last;
+    const HTask t = v.uft[task0 + blockIdx.x];
+    const int tid = threadIdx.x;
+    if (t.s < 0) {   // rows of a low-rank group: u = inc - U t
+        const HLr g = v.lr[-1 - t.s];
+        const HSnode sn = v.sn[g.s];
+        const int i = t.a0 + tid;
+        if (i < t.a1) {
+            const T* U = data + g.off_u + (int64_t)i * g.k;
+            A acc = 0;
+            for (int l = 0; l < g.k; ++l) acc += (A)ldv(U + l) * (A)tbuf[g.t_off + l];
+            finish_row(v, sn, g.row0 + i, (double)acc, ybuf, ubuf);
+        }
+        return;
+    }
+    const HSnode sn = v.sn[t.s];
+    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
+    for (int j = t.b0 + tid; j < t.b1; j += HT) w[j - t.b0] = (A)gather_w(v, sn, j, in, shift, ubuf);
+    __syncthreads();
+    const int q = t.a0 + tid;
+    A acc = 0;
+    if (q < t.a1) {
+        const T* col = data + sn.data_off;
+        const int jend = q < sn.ni ? min(t.b1, q + 1) : t.b1;
+        int j = t.b0;
+        for (; j + 4 <= jend; j += 4) {
+            const T* c0 = col + col_offset(sn.nd, j) - j;
+            const T* c1 = col + col_offset(sn.nd, j + 1) - (j + 1);
+            const T* c2 = col + col_offset(sn.nd, j + 2) - (j + 2);
+            const T* c3 = col + col_offset(sn.nd, j + 3) - (j + 3);
+            const A x0 = (A)ldv(c0 + q), x1 = (A)ldv(c1 + q), x2 = (A)ldv(c2 + q),
+                    x3 = (A)ldv(c3 + q);
+            acc += x0 * w[j - t.b0];
+            acc += x1 * w[j + 1 - t.b0];
+            acc += x2 * w[j + 2 - t.b0];
+            acc += x3 * w[j + 3 - t.b0];
+        }
+        for (; j < jend; ++j) acc += (A)ldv(col + col_offset(sn.nd, j) - j + q) * w[j - t.b0];
+    }
+    if (t.nparts == 1) {
+        if (q < t.a1) finish_row(v, sn, dense_row(v, sn, q), (double)acc, ybuf, ubuf);
+        return;
+    }
+    const int rows = t.a1 - t.a0;
+    const int c = t.b0 / UP_COLS;
+    if (q < t.a1) pbuf[t.part + (int64_t)c * rows + tid] = (double)acc;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&tickets[t.ticket], 1u) == (unsigned)(t.nparts - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (q < t.a1) {
+        double s = 0.0;
+        for (int p = 0; p < t.nparts; ++p) s += __ldcg(&pbuf[t.part + (int64_t)p * rows + tid]);
+        finish_row(v, sn, dense_row(v, sn, q), s, ybuf, ubuf);
+    }
+    if (tid == 0) tickets[t.ticket] = 0u;
+}
+
+// t_g = U_g^T v_g with v = -x on the group's boundary rows (one CTA per group)
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_lr_bwd(HView v, const T* __restrict__ data, int g0,
+                                               const double* out, double* tbuf) {
+    __shared__ A vv[UP_ROWS];
+    __shared__ A red[HT];
+    const HLr g = v.lr[g0 + blockIdx.x];
+    const HSnode sn = v.sn[g.s];
+    for (int i = threadIdx.x; i < g.m; i += HT)
+        vv[i] = (A)(-out[v.bidx[sn.bidx_off + g.row0 + i - sn.ni]]);
+    __syncthreads();
+    const int kp = g.k <= 32 ? 32 : 64, ng = HT / kp;
+    const int l = threadIdx.x % kp, grp = threadIdx.x / kp;
+    A acc = 0;
+    if (l < g.k) {
+        const T* U = data + g.off_u;
+        for (int i = grp; i < g.m; i += ng) acc += (A)ldv(U + (int64_t)i * g.k + l) * vv[i];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < g.k) {
+        A s = 0;
+        for (int q = 0; q < ng; ++q) s += red[q * kp + threadIdx.x];
+        tbuf[g.t_off + threadIdx.x] = (double)s;
+    }
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ data, int task0,
+                                               const double* __restrict__ ybuf,
+                                               const double* tbuf, double* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    A* vv = reinterpret_cast<A*>(smem);
+    const HTask t = v.ubt[task0 + blockIdx.x];
+    const HSnode sn = v.sn[t.s];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < sn.nd; q += HT)
+        vv[q] = (A)(q < sn.ni ? ybuf[sn.first + q]
+                              : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]]);
+    __syncthreads();
+    const T* col = data + sn.data_off;
+    for (int j = t.a0 + warp; j < t.a1; j += NW) {
+        const T* cj = col + col_offset(sn.nd, j) - j;
+        A acc = 0;
+        int q = j + lane;
+        for (; q + 96 < sn.nd; q += 128) {
+            const A x0 = (A)ldv(cj + q), x1 = (A)ldv(cj + q + 32), x2 = (A)ldv(cj + q + 64),
+                    x3 = (A)ldv(cj + q + 96);
+            acc += x0 * vv[q];
+            acc += x1 * vv[q + 32];
+            acc += x2 * vv[q + 64];
+            acc += x3 * vv[q + 96];
+        }
+        for (; q < sn.nd; q += 32) acc += (A)ldv(cj + q) * vv[q];
+        for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
+            const HLr G = v.lr[g];
+            const T* V = data + G.off_v + (int64_t)j * G.k;
+            for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)tbuf[G.t_off + l];
+        }
+        acc = wsum(acc);
+        if (lane == 0) out[v.pidx[sn.first + j]] = (double)acc;
     }
 }
 
@@ -190,36 +340,65 @@ HView view_of(const HFactorDev& F) {
     v.pidx = F.pidx;
     v.bidx = F.bidx;
     v.inc = F.inc;
+    v.drows = F.drows;
     v.sn = F.sn;
-    v.blk = F.blk;
-    v.tf = F.tf;
-    v.tb = F.tb;
-    v.lf = F.lf;
-    v.lb = F.lb;
+    v.lr = F.lr;
+    v.sub_lev = F.sub_lev;
+    v.sub_nlev = F.sub_nlev;
+    v.sfp = F.sfp;
+    v.sbp = F.sbp;
+    v.sft = F.sft;
+    v.sbt = F.sbt;
+    v.uft = F.uft;
+    v.ubt = F.ubt;
     return v;
 }
 
 template <typename T, typename A>
 int run(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
-        double inv_n, double* ybuf, double* ubuf, double* out) {
+        double inv_n, const HScratch& S, double* out) {
     const HView v = view_of(F);
     const T* data = reinterpret_cast<const T*>(F.data);
-    for (int lev = 0; lev < F.height; ++lev) {
-        const int nt = F.tf_ptr[lev + 1] - F.tf_ptr[lev];
-        if (nt == 0) continue;
-        size_t sm = sizeof(HBlock) * MAX_TILE_BLOCKS +
-                    sizeof(A) * (((F.ni_max[lev] + 1) & ~1) + F.tsum_max_f[lev] + 2);
-        k_hfwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.tf_ptr[lev], in, shift_sum, inv_n, ybuf,
-                                           ubuf);
-        count_launches(1);
+    int launches = 0;
+    if (F.nsub > 0) {
+        k_sub_fwd<T, A><<<(unsigned)F.nsub, HT, 0, L.st>>>(v, data, in, shift_sum, inv_n, S.ybuf,
+                                                           S.ubuf);
+        ++launches;
     }
-    for (int lev = F.height - 1; lev >= 0; --lev) {
-        const int nt = F.tb_ptr[lev + 1] - F.tb_ptr[lev];
-        if (nt == 0) continue;
-        size_t sm = sizeof(HBlock) * MAX_TILE_BLOCKS + sizeof(A) * (128 + 256 + F.tsum_max_b[lev] + 2);
-        k_hbwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.tb_ptr[lev], ybuf, out);
-        count_launches(1);
+    const int nul = (int)F.uf_ptr.size() - 1;
+    for (int lev = 0; lev < nul; ++lev) {
+        const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
+        if (ng > 0) {
+            const size_t sm = sizeof(A) * (((F.u_ni_max[lev] + 1) & ~1) + HT);
+            k_lr_fwd<T, A><<<ng, HT, sm, L.st>>>(v, data, F.ulr_ptr[lev], in, shift_sum, inv_n,
+                                                 S.ubuf, S.tbuf);
+            ++launches;
+        }
+        const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
+        if (nt > 0) {
+            k_up_fwd<T, A><<<nt, HT, 0, L.st>>>(v, data, F.uf_ptr[lev], in, shift_sum, inv_n,
+                                                S.ybuf, S.ubuf, S.tbuf, S.pbuf, S.tickets);
+            ++launches;
+        }
     }
+    for (int lev = nul - 1; lev >= 0; --lev) {
+        const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
+        if (ng > 0) {
+            k_lr_bwd<T, A><<<ng, HT, 0, L.st>>>(v, data, F.ulr_ptr[lev], out, S.tbuf);
+            ++launches;
+        }
+        const int nt = F.ub_ptr[lev + 1] - F.ub_ptr[lev];
+        if (nt > 0) {
+            const size_t sm = sizeof(A) * (F.u_nd_max[lev] + 2);
+            k_up_bwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.ub_ptr[lev], S.ybuf, S.tbuf, out);
+            ++launches;
+        }
+    }
+    if (F.nsub > 0) {
+        k_sub_bwd<T, A><<<(unsigned)F.nsub, HT, 0, L.st>>>(v, data, S.ybuf, out);
+        ++launches;
+    }
+    count_launches(launches);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(BID_ECUDA, "hsolve launch: %s", cudaGetErrorString(e));
     return BID_OK;
@@ -233,25 +412,29 @@ uint16_t to_bf16(float f) {   // round to nearest even
     return (uint16_t)(u >> 16);
 }
 
+template <typename T, typename A>
+int prepare_one() {
+    const int lim = 200 * 1024;
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_lr_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_up_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return BID_OK;
+}
+
 }  // namespace
 
 int hsolve_prepare() {
-    const int lim = 200 * 1024;
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_hfwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_hfwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_hfwd<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_hbwd<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_hbwd<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_hbwd<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    BID_TRY((prepare_one<double, double>()));
+    BID_TRY((prepare_one<float, float>()));
+    BID_TRY((prepare_one<__nv_bfloat16, float>()));
     return BID_OK;
 }
 
 int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
-                  double inv_n, double* ybuf, double* ubuf, double* out) {
+                  double inv_n, const HScratch& S, double* out) {
     switch (F.precision) {
-        case BID_FP64: return run<double, double>(L, F, in, shift_sum, inv_n, ybuf, ubuf, out);
-        case BID_FP32: return run<float, float>(L, F, in, shift_sum, inv_n, ybuf, ubuf, out);
-        case BID_BF16: return run<__nv_bfloat16, float>(L, F, in, shift_sum, inv_n, ybuf, ubuf, out);
+        case BID_FP64: return run<double, double>(L, F, in, shift_sum, inv_n, S, out);
+        case BID_FP32: return run<float, float>(L, F, in, shift_sum, inv_n, S, out);
+        case BID_BF16: return run<__nv_bfloat16, float>(L, F, in, shift_sum, inv_n, S, out);
         default: return set_error(BID_EINVAL, "bad factor precision");
     }
 }
@@ -266,39 +449,40 @@ static int upload_vec(const std::vector<V>& h, V** d) {
 }
 
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
+    const int esz_acc = precision == BID_FP64 ? 8 : 4;
+    for (size_t L = 0; L < h.u_nd_max.size(); ++L)
+        if ((int64_t)(h.u_nd_max[L] + 2) * esz_acc > 200 * 1024 ||
+            (int64_t)(h.u_ni_max[L] + 2 + HT) * esz_acc > 200 * 1024)
+            return set_error(BID_EINVAL, "cluster too large for shared memory (nd=%d)", h.u_nd_max[L]);
+    for (const HLr& g : h.lr)
+        if (g.k > 64 || g.m > UP_ROWS) return set_error(BID_EINVAL, "low-rank group out of range");
     d->n = h.n;
     d->pin = h.pin;
     d->precision = precision;
-    d->height = h.height;
-    d->block = h.block;
-    for (int lev = 0; lev < h.height; ++lev) {
-        const int esz = precision == BID_FP64 ? 8 : 4;
-        if ((int64_t)(h.ni_max[lev] + h.tsum_max_f[lev] + 4) * esz + 8192 > 200 * 1024)
-            return set_error(BID_EINVAL, "cluster too large for shared memory (ni=%d)", h.ni_max[lev]);
-        if (h.tsum_max_b[lev] * esz + 8192 + 384 * esz > 200 * 1024)
-            return set_error(BID_EINVAL, "tile rank sum too large (%d)", h.tsum_max_b[lev]);
-    }
-    for (const HTile& t : h.tf)
-        if (t.blk_end - t.blk_begin > MAX_TILE_BLOCKS)
-            return set_error(BID_EINVAL, "too many blocks in a factor tile");
-    for (const HTile& t : h.tb)
-        if (t.blk_end - t.blk_begin > MAX_TILE_BLOCKS)
-            return set_error(BID_EINVAL, "too many blocks in a factor tile");
+    d->nsub = h.nsub;
     BID_TRY(upload_vec(h.pidx, &d->pidx));
     BID_TRY(upload_vec(h.bidx, &d->bidx));
     BID_TRY(upload_vec(h.inc, &d->inc));
+    BID_TRY(upload_vec(h.drows, &d->drows));
     BID_TRY(upload_vec(h.sn, &d->sn));
-    BID_TRY(upload_vec(h.blk, &d->blk));
-    BID_TRY(upload_vec(h.tf, &d->tf));
-    BID_TRY(upload_vec(h.tb, &d->tb));
-    BID_TRY(upload_vec(h.lf, &d->lf));
-    BID_TRY(upload_vec(h.lb, &d->lb));
-    d->tf_ptr = h.tf_ptr;
-    d->tb_ptr = h.tb_ptr;
-    d->ni_max = h.ni_max;
-    d->tsum_max_f = h.tsum_max_f;
-    d->tsum_max_b = h.tsum_max_b;
+    BID_TRY(upload_vec(h.lr, &d->lr));
+    BID_TRY(upload_vec(h.sub_lev, &d->sub_lev));
+    BID_TRY(upload_vec(h.sub_nlev, &d->sub_nlev));
+    BID_TRY(upload_vec(h.sfp, &d->sfp));
+    BID_TRY(upload_vec(h.sbp, &d->sbp));
+    BID_TRY(upload_vec(h.sft, &d->sft));
+    BID_TRY(upload_vec(h.sbt, &d->sbt));
+    BID_TRY(upload_vec(h.uft, &d->uft));
+    BID_TRY(upload_vec(h.ubt, &d->ubt));
+    d->ulr_ptr = h.ulr_ptr;
+    d->uf_ptr = h.uf_ptr;
+    d->ub_ptr = h.ub_ptr;
+    d->u_ni_max = h.u_ni_max;
+    d->u_nd_max = h.u_nd_max;
     d->ubuf_entries = h.ubuf;
+    d->tbuf_entries = h.tbuf;
+    d->pbuf_entries = h.pbuf;
+    d->ntickets = h.ntickets;
     d->data_elems = (int64_t)h.data.size();
     const size_t n = h.data.size();
     int esz = 8;
@@ -320,16 +504,9 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 void free_hfactor(HFactorDev* d) {
-    cudaFree(d->pidx);
-    cudaFree(d->bidx);
-    cudaFree(d->inc);
-    cudaFree(d->sn);
-    cudaFree(d->blk);
-    cudaFree(d->tf);
-    cudaFree(d->tb);
-    cudaFree(d->lf);
-    cudaFree(d->lb);
-    cudaFree(d->data);
+    void* ptrs[] = {d->pidx, d->bidx, d->inc, d->drows, d->sn, d->lr, d->sub_lev, d->sub_nlev,
+                    d->sfp, d->sbp, d->sft, d->sbt, d->uft, d->ubt, d->data};
+    for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }
 

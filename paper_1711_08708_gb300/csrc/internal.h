@@ -63,57 +63,78 @@ struct AssembledHost {
 int assemble_host(const bid_mesh* mesh, const bid_params* p, AssembledHost* out);
 
 // ---------------------------------------------------------------- H-factor
+#ifdef __CUDACC__
+#define BID_HD __host__ __device__ __forceinline__
+#else
+#define BID_HD inline
+#endif
+
 // Factor of an SPD matrix A (n x n) in nested-dissection supernodal form.  For
-// supernode s with pivot set I_s (ni entries, contiguous in the elimination
-// order starting at `first`) and boundary set B_s (nb ancestor entries), the
-// stored block is M_s = [L_ss^-1 ; L_Bs L_ss^-1], (ni + nb) x ni, tiled in
-// blocks that are dense (row-major m x n) or low rank (U m x k row-major,
-// Vt k x n row-major, block = U Vt).
+// cluster s with pivot set I_s (ni entries, contiguous in the elimination
+// order from `first`) and boundary set B_s (nb ancestor entries), the stored
+// block is M_s = [L_ss^-1 ; L_Bs L_ss^-1], (ni + nb) x ni.  Its "dense rows"
+// (the ni rows of L_ss^-1 and the boundary rows not in a low-rank group, nd in
+// all) are stored packed, lower-trapezoidal and column-major: column j holds
+// dense rows q = j .. nd-1, contiguous.  A low-rank group replaces m boundary
+// rows by U (m x k, row-major) times V^T (V: ni x k, row-major).
 struct HSnode {
-    int32_t first, ni, nb;
+    int32_t first, ni, nb, nd;
     int32_t bidx_off;   // B_s entries (vector indices) at bidx[bidx_off ...]
-    int32_t u_off;      // update vector of s in the scratch buffer
+    int32_t u_off;      // update vector of s in the ubuf scratch
     int32_t inc_off;    // 2 ints per frontal row: children's update entries or -1
     int32_t height;
-    int32_t pad;
+    int64_t data_off;   // packed dense columns
+    int32_t drow_off;   // M_s row index of dense boundary row q (q >= ni) at drows[drow_off + q - ni]
+    int32_t lr_begin, lr_end;
+    int32_t sub;        // bottom subtree id, or -1 for an upper cluster
 };
-struct HBlock {
-    int32_t type;       // 0 dense, 1 low rank
-    int32_t row0, col0; // position inside M_s
-    int32_t m, n, k;
-    int64_t off;        // element offset in the factor data
+BID_HD int64_t col_offset(int64_t nd, int64_t j) { return j * nd - j * (j - 1) / 2; }
+
+struct HLr {
+    int32_t s, row0, m, k;      // rows [row0, row0+m) of M_s (boundary rows)
+    int64_t off_u, off_v;
+    int32_t t_off, pad;         // slot of V^T w (forward) / U^T v (backward) in tbuf
 };
-struct HTile {
-    int32_t s;          // supernode
-    int32_t r0, len;    // fwd: rows [r0, r0+len) of M_s; bwd: columns
-    int32_t blk_begin, blk_end;   // range in the tile's block list
-    int32_t tsum;       // sum of ranks of the tile's low-rank blocks
+// Work item of a triangular-pass kernel.
+//  bottom forward:  cluster s, dense rows [a0, a1)
+//  bottom backward: cluster s, columns [a0, a1)
+//  upper forward:   s >= 0: dense rows [a0, a1) x columns [b0, b1); when the
+//                   row chunk is split over nparts column chunks, partial sums
+//                   go to pbuf[part + c*(a1-a0) + row] and the last CTA of
+//                   ticket `ticket` finishes the rows;  s < 0: low-rank group
+//                   g = -1 - s, rows [a0, a1) of the group
+//  upper backward:  cluster s, columns [a0, a1)
+struct HTask {
+    int32_t s, a0, a1, b0, b1, part, ticket, nparts;
 };
 
 struct HFactorHost {
     int64_t n = 0;
     int32_t pin = -1;                  // vector index fixed to zero, or -1
-    int32_t block = 64;
-    int32_t height = 0;                // number of levels
+    int32_t height = 0;
     std::vector<int32_t> pidx;         // elimination position -> vector index
     std::vector<HSnode> sn;
-    std::vector<int32_t> bidx;
-    std::vector<int32_t> inc;
-    std::vector<HBlock> blk;
+    std::vector<int32_t> bidx, inc, drows;
+    std::vector<HLr> lr;
     std::vector<double> data;
-    std::vector<HTile> tf, tb;         // tiles sorted by level
-    std::vector<int32_t> lf, lb;       // tile block lists
-    std::vector<int32_t> tf_ptr, tb_ptr;   // level -> tile range
-    std::vector<int32_t> ni_max;       // level -> max ni (shared memory for w)
-    std::vector<int32_t> tsum_max_f, tsum_max_b;
-    int64_t ubuf = 0;                  // update-vector scratch entries
+    // bottom subtrees: one CTA each, levels processed inside the CTA
+    std::vector<int32_t> sub_lev, sub_nlev;   // per subtree: base into sfp/sbp, levels
+    std::vector<int32_t> sfp, sbp;             // level -> task ranges
+    std::vector<HTask> sft, sbt;
+    // upper levels (ascending height)
+    std::vector<int32_t> ulr_ptr;              // level -> low-rank groups [ptr, ptr+1)
+    std::vector<int32_t> uf_ptr, ub_ptr;       // level -> task ranges
+    std::vector<HTask> uft, ubt;
+    std::vector<int32_t> u_ni_max, u_nd_max;   // level -> max ni / nd (shared memory)
+    int64_t ubuf = 0, tbuf = 0, pbuf = 0;
+    int32_t ntickets = 0;
     int64_t dense_entries = 0, lowrank_entries = 0;
-    int64_t dense_blocks = 0, lowrank_blocks = 0;
+    int64_t nsub = 0, nlr = 0;
 };
 
 struct HBuildOpts {
     double eps = 0.0;
-    int leaf = 64;
+    int leaf = 16;
     int block = 64;
     int threads = 0;
 };
@@ -123,30 +144,53 @@ struct HBuildOpts {
 int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin,
                   const HBuildOpts& o, HFactorHost* F);
 
+// Limits shared by the build and the kernels.
+constexpr int SUB_ROWS = 256;    // max ni + nb of a bottom cluster (8 rows per lane)
+constexpr int SUB_NI = 128;      // max ni of a bottom cluster
+constexpr int SUB_PIV = 4096;    // max pivots of a bottom subtree
+constexpr int UP_ROWS = 256;     // rows of an upper forward task (one per thread)
+constexpr int UP_COLS = 256;     // columns of an upper forward task
+constexpr int UP_BCOLS = 64;     // columns of an upper backward task
+constexpr int LR_KMAX = 64;      // largest rank kept in a low-rank group
+
 // ---------------------------------------------------------------- device factor
 struct HFactorDev {
     int64_t n = 0;
     int32_t pin = -1;
     int32_t precision = BID_FP64;
-    int32_t height = 0;
     int32_t* pidx = nullptr;
     int32_t* bidx = nullptr;
     int32_t* inc = nullptr;
+    int32_t* drows = nullptr;
     HSnode* sn = nullptr;
-    HBlock* blk = nullptr;
-    HTile* tf = nullptr;
-    HTile* tb = nullptr;
-    int32_t* lf = nullptr;
-    int32_t* lb = nullptr;
+    HLr* lr = nullptr;
+    int32_t* sub_lev = nullptr;
+    int32_t* sub_nlev = nullptr;
+    int32_t* sfp = nullptr;
+    int32_t* sbp = nullptr;
+    HTask* sft = nullptr;
+    HTask* sbt = nullptr;
+    HTask* uft = nullptr;
+    HTask* ubt = nullptr;
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
-    std::vector<int32_t> tf_ptr, tb_ptr, ni_max, tsum_max_f, tsum_max_b;
-    int64_t ubuf_entries = 0;
+    int64_t nsub = 0;
+    std::vector<int32_t> ulr_ptr, uf_ptr, ub_ptr, u_ni_max, u_nd_max;
+    int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0;
+    int32_t ntickets = 0;
     int64_t bytes_pass = 0;             // factor bytes read by fwd + bwd
-    int32_t block = 64;
 };
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
 void free_hfactor(HFactorDev* d);
+
+// Scratch of one triangular solve (sized by the factor; reused by every solve).
+struct HScratch {
+    double* ybuf = nullptr;
+    double* ubuf = nullptr;
+    double* tbuf = nullptr;
+    double* pbuf = nullptr;
+    unsigned int* tickets = nullptr;    // zero between solves
+};
 
 // ---------------------------------------------------------------- device scalars
 // Scalars of the PCG recurrences, kept on the device so that no kernel needs a
@@ -197,8 +241,7 @@ int launch_normalise(const Launch& L, int64_t N, double* U, const double* m,
 // first), then backward pass.  The input entries are b[i] - shift_sum*inv_n
 // (shift_sum may be NULL), with the pinned entry set to zero.
 int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in,
-                  const double* shift_sum, double inv_n, double* ybuf, double* ubuf,
-                  double* out);
+                  const double* shift_sum, double inv_n, const HScratch& S, double* out);
 int hsolve_prepare();   // raise the dynamic shared-memory limit of the kernels
 
 // ---------------------------------------------------------------- handles
@@ -222,7 +265,7 @@ struct bid_precond {
     // work vectors (device)
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double *z1b = nullptr, *t = nullptr, *w = nullptr, *ytmp = nullptr, *xs = nullptr;
-    double *ybuf = nullptr, *ubuf = nullptr;
+    bid::HScratch hs;
     double* partials = nullptr;
     bid::DevScalars* sc = nullptr;
     bid::DevScalars* host_pinned = nullptr;   // pinned host mirror of the scalars

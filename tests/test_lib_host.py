@@ -76,7 +76,22 @@ def test_host_factor_exact_equals_pseudo_inverse(bid, leaf, block):
     x2, _ = hs.factor_solve(2, b2, gamma=g, leaf=leaf, block=block)
     xo2 = spla.spsolve(ob.monodomain_matrix(s, g).tocsc(), b2)
     assert np.abs(x2 - xo2).max() <= 1e-12 * np.abs(xo2).max()
-    assert st["levels1"] >= 3 and st["lowrank_blocks"] == 0
+    assert st["levels1"] >= 1 and st["lowrank_blocks"] == 0
+
+
+@pytest.mark.parametrize("n,leaf,block", [(161, 16, 128), (129, 32, 64), (129, 8, 16)])
+def test_host_factor_exact_with_upper_levels(bid, n, leaf, block):
+    # large enough that clusters above the bottom subtrees exist (upper levels,
+    # column-chunked row tasks)
+    m, p = torso_square_2d(n), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    b = np.random.default_rng(n).normal(size=s.N)
+    x, st = hs.factor_solve(1, b, leaf=leaf, block=block)
+    x -= x.mean()
+    xo = ob.s1_pseudo_inverse_apply(s, b)
+    assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
+    assert st["levels1"] >= 3 and st["dense_blocks"] >= 2
 
 
 def test_host_factor_3d_exact():
