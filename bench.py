@@ -235,7 +235,7 @@ def main():
     hbm = pk.get("hbm_gbs", 6780.7)
     # algorithmic bytes of one P_1 application: the factor read twice (stored
     # bytes_p1 already counts both passes) + input gather, y and x vectors
-    alg_bytes = P.stats["bytes_p1"] + 8 * 4 * N
+    alg_bytes = P.stats["alg_bytes_p1"] + 8 * 4 * N
     achieved = alg_bytes / (solve_ms * 1e-3) / 1e9
 
     # ---- e2e through the public API with host buffers

@@ -85,8 +85,8 @@ typedef struct bid_precond_opts {
     double dt;                /* time step (ms); gamma = chi * Cm / dt (Sec. 3.2) */
     double eps;               /* low-rank truncation accuracy (Sec. 5.3); 0 = exact */
     int32_t precision;        /* BID_FP64 | BID_FP32 | BID_BF16 factor storage */
-    int32_t leaf_size;        /* nested-dissection leaf: max nodes per leaf cluster */
-    int32_t block;            /* row/column block of the factor tiles (16..128) */
+    int32_t leaf_size;        /* nested-dissection leaf: max nodes per leaf cluster (4..4096) */
+    int32_t block;            /* rows of a low-rank boundary group (8..256) */
     int32_t n_threads;        /* host threads for the build (0 = all) */
 } bid_precond_opts;
 
@@ -95,9 +95,12 @@ typedef struct bid_precond_stats {
     int64_t supernodes1, supernodesk;
     int32_t levels1, levelsk;          /* tree heights (launches per triangular pass) */
     int64_t dense_entries, lowrank_entries;  /* stored factor entries, both factors */
-    int64_t factor_bytes;              /* bytes read by one forward+backward pass of
-                                          P_1 plus one of P_K (algorithmic) */
-    int64_t bytes_p1, bytes_pk;        /* per single triangular-pair solve */
+    int64_t factor_bytes;              /* algorithmic factor bytes of one P_Lambda^-1:
+                                          two P_1 solves and one P_K solve */
+    int64_t bytes_p1, bytes_pk;        /* stored bytes read by one forward+backward
+                                          pair (including alignment padding) */
+    int64_t alg_bytes_p1, alg_bytes_pk;  /* the same without padding (nonzero
+                                          dense entries and low-rank factors) */
     int64_t lowrank_blocks, dense_blocks;
     double build_seconds;
 } bid_precond_stats;
@@ -213,9 +216,10 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
 /* Build the factor of S_1 (which = 1, last U unknown pinned) or of
  * K_m = gamma M_H + S_m (which = 2) with the given eps / leaf / block, and
  * apply it on the host: x = P^-1 (b - mean(b)) for which = 1, x = P^-1 b for
- * which = 2.  b and x are host arrays (N or N_H).  stats may be NULL. */
+ * which = 2.  The stored layout is the one built for `precision`; the replay
+ * computes in FP64.  b and x are host arrays (N or N_H).  stats may be NULL. */
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps,
-                          int leaf, int block, const double* b, double* x,
+                          int leaf, int block, int precision, const double* b, double* x,
                           bid_precond_stats* stats);
 void bid_host_destroy(bid_host_system* h);
 

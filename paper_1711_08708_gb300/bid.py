@@ -50,6 +50,7 @@ class PrecondStats(C.Structure):
                 ("supernodesk", C.c_int64), ("levels1", C.c_int32), ("levelsk", C.c_int32),
                 ("dense_entries", C.c_int64), ("lowrank_entries", C.c_int64),
                 ("factor_bytes", C.c_int64), ("bytes_p1", C.c_int64), ("bytes_pk", C.c_int64),
+                ("alg_bytes_p1", C.c_int64), ("alg_bytes_pk", C.c_int64),
                 ("lowrank_blocks", C.c_int64), ("dense_blocks", C.c_int64),
                 ("build_seconds", C.c_double)]
 
@@ -88,7 +89,7 @@ SIGNATURES = {
     "bid_host_assemble": (_I, [C.POINTER(Mesh), C.POINTER(Params), C.POINTER(_VP)]),
     "bid_host_csr_size": (_I, [_VP, _I, _I64P, _I64P]),
     "bid_host_csr": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
-    "bid_host_factor_solve": (_I, [_VP, _I, _D, _D, _I, _I, _VP, _VP, C.POINTER(PrecondStats)]),
+    "bid_host_factor_solve": (_I, [_VP, _I, _D, _D, _I, _I, _I, _VP, _VP, C.POINTER(PrecondStats)]),
     "bid_host_destroy": (None, [_VP]),
 }
 
@@ -270,12 +271,13 @@ class HostSystem:
         _check(lib.bid_host_csr(self.h, 0, None, None, None, _ptr(perm), _ptr(m), _ptr(mH)))
         return perm, m, mH
 
-    def factor_solve(self, which, b, gamma=0.0, eps=0.0, leaf=16, block=128):
+    def factor_solve(self, which, b, gamma=0.0, eps=0.0, leaf=16, block=128, precision="fp64"):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         st = PrecondStats()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(lib.bid_host_factor_solve(self.h, int(which), float(gamma), float(eps), int(leaf),
-                                         int(block), _ptr(b), _ptr(x), C.byref(st)))
+                                         int(block), prec, _ptr(b), _ptr(x), C.byref(st)))
         return x, st.as_dict()
 
     def __del__(self):

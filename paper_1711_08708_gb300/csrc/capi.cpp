@@ -301,6 +301,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     bo.leaf = o->leaf_size;
     bo.block = o->block;
     bo.threads = o->n_threads;
+    bo.vec = o->precision == BID_FP64 ? 2 : o->precision == BID_FP32 ? 4 : 8;
     HFactorHost h1, hk;
     // P_1: S_1 with the last U unknown pinned (pseudo-inverse on 1^perp)
     BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, (int)(H.N - 1), bo, &h1));
@@ -360,7 +361,9 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.lowrank_blocks = h1.nlr + hk.nlr;
     st.bytes_p1 = P->F1.bytes_pass;
     st.bytes_pk = P->FK.bytes_pass;
-    st.factor_bytes = 2 * st.bytes_p1 + st.bytes_pk;   // one P_Lambda^-1: 2 P_1 + 1 P_K
+    st.alg_bytes_p1 = P->F1.alg_bytes_pass;
+    st.alg_bytes_pk = P->FK.alg_bytes_pass;
+    st.factor_bytes = 2 * st.alg_bytes_p1 + st.alg_bytes_pk;   // one P_Lambda^-1: 2 P_1 + 1 P_K
     st.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = P;
     return BID_OK;

@@ -166,6 +166,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
     if (n <= 0) return set_error(BID_EINVAL, "empty matrix");
     if (o.block < 8 || o.block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o.leaf < 4 || o.leaf > 4096) return set_error(BID_EINVAL, "leaf must be in 4..4096");
+    if (o.vec != 2 && o.vec != 4 && o.vec != 8) return set_error(BID_EINVAL, "vec must be 2, 4 or 8");
     const int nthreads = o.threads > 0 ? o.threads : omp_get_max_threads();
 
     // ---------------- cluster tree
@@ -323,7 +324,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
 
     // ---------------- numeric factorisation
     const double eps = o.eps;
-    const int lrows = std::max(16, o.block);
+    const int lrows = std::min(LR_ROWS, std::max(16, o.block));
+    const int vec = o.vec;
+    F->vec = vec;
     int fail = 0;
     auto factor_one = [&](int s, bool par) -> int {
         HSnode& h = F->sn[s];
@@ -427,9 +430,13 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         const int nd = (int)rows.size();
         w.nd = nd;
         w.drows.assign(rows.begin() + ni, rows.end());
+        while (w.data.size() % vec) w.data.push_back(0.0);   // aligned dense start
         w.dense_off = (int64_t)w.data.size();
-        for (int c = 0; c < ni; ++c)
+        for (int c = 0; c < ni; ++c) {
             for (int q = c; q < nd; ++q) w.data.push_back(M[(size_t)rows[q] * ni + c]);
+            const int pad = ((1 - (nd - c)) % vec + vec) % vec;
+            for (int z = 0; z < pad; ++z) w.data.push_back(0.0);
+        }
         w.dense_e += col_offset(nd, ni);
         return 0;
     };
@@ -472,17 +479,21 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
 
     // ---------------- pack
     {
+        // every cluster starts on a vec boundary; vec trailing zeros let the last
+        // vector load of the last column stay inside the array
+        auto up = [vec](int64_t x) { return (x + vec - 1) / vec * vec; };
         int64_t total = 0, nd_rows = 0;
         for (int s = 0; s < nt; ++s) {
-            total += (int64_t)W[s].data.size();
+            total += up((int64_t)W[s].data.size());
             nd_rows += (int64_t)W[s].drows.size();
         }
-        F->data.resize(total);
+        F->data.assign(total + 2 * vec, 0.0);
         F->drows.reserve(nd_rows);
         int64_t off = 0;
         for (int s = 0; s < nt; ++s) {
             SnWork& w = W[s];
             HSnode& h = F->sn[s];
+            off = up(off);
             std::memcpy(F->data.data() + off, w.data.data(), w.data.size() * sizeof(double));
             h.nd = w.nd;
             h.data_off = off + w.dense_off;
@@ -564,8 +575,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             }
             h.lr_end = (int32_t)F->lr.size();
             // forward dense row chunks
-            for (int a = 0; a < h.nd; a += UP_ROWS) {
-                const int a1 = std::min(h.nd, a + UP_ROWS);
+            const int up_rows = UP_THREADS * vec;   // a thread owns vec consecutive rows
+            for (int a = 0; a < h.nd; a += up_rows) {
+                const int a1 = std::min(h.nd, a + up_rows);
                 const int cols = a1 <= h.ni ? a1 : h.ni;
                 const int np = (cols + UP_COLS - 1) / UP_COLS;
                 int32_t part = -1, tk = -1;
@@ -588,11 +600,11 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                 }
             }
             for (int g = h.lr_begin; g < h.lr_end; ++g)
-                for (int a = 0; a < F->lr[g].m; a += UP_ROWS) {
+                for (int a = 0; a < F->lr[g].m; a += UP_THREADS) {
                     HTask k{};
                     k.s = -1 - g;
                     k.a0 = a;
-                    k.a1 = std::min(F->lr[g].m, a + UP_ROWS);
+                    k.a1 = std::min(F->lr[g].m, a + UP_THREADS);
                     k.nparts = 1;
                     k.part = k.ticket = -1;
                     F->uft.push_back(k);

@@ -42,7 +42,9 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x) {
         }
     };
     auto drow = [&](const HSnode& s, int q) { return q < s.ni ? q : F.drows[s.drow_off + q - s.ni]; };
-    auto elem = [&](const HSnode& s, int q, int j) { return D[s.data_off + col_offset(s.nd, j) + q - j]; };
+    auto elem = [&](const HSnode& s, int q, int j) {
+        return D[s.data_off + col_start(s.nd, j, F.vec) + q - j];
+    };
     // dense forward rows [a0,a1) over columns [b0,b1)
     auto fwd_rows = [&](const HSnode& s, int a0, int a1, int b0, int b1, std::vector<double>& acc) {
         for (int q = a0; q < a1; ++q) {
@@ -188,13 +190,16 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
 }
 
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps, int leaf,
-                          int block, const double* b, double* x, bid_precond_stats* stats) {
+                          int block, int precision, const double* b, double* x,
+                          bid_precond_stats* stats) {
     if (!h || !b || !x || (which != 1 && which != 2)) return set_error(BID_EINVAL, "bad argument");
+    if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
     if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
     HBuildOpts o;
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
+    o.vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
     HFactorHost F;
     const AssembledHost& a = h->a;
     double shift = 0.0;
@@ -220,6 +225,7 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
         stats->dense_blocks = F.nsub;
         stats->lowrank_blocks = F.nlr;
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
+        stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
     }
     return BID_OK;
 }

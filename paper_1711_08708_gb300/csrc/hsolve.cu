@@ -38,6 +38,34 @@ __device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
+// 16-byte aligned vector of the storage type, widened to the accumulation type
+__device__ __forceinline__ void ld16(const double* p, double (&o)[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+}
+__device__ __forceinline__ void ld16(const float* p, float (&o)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ void ld16(const __nv_bfloat16* p, float (&o)[8]) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[2 * i] = __uint_as_float(w[i] << 16);
+        o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+template <typename T>
+struct VecOf {
+    static constexpr int N = 16 / sizeof(T);
+};
+
 template <typename A>
 __device__ __forceinline__ A wsum(A v) {
 #pragma unroll
@@ -94,11 +122,16 @@ __device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q
 }
 
 // ------------------------------------------------------------ bottom subtrees
+// Forward: a warp task covers <= SUB_ROWS dense rows of one cluster; lane l
+// owns the aligned row groups a0 + VEC*(l + 32 g).  Columns are consumed four
+// at a time so that 4*G vector loads per lane are in flight.
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_sub_fwd(HView v, const T* __restrict__ data,
                                                 const double* __restrict__ in,
                                                 const double* shift_sum, double inv_n,
                                                 double* ybuf, double* ubuf) {
+    constexpr int VEC = VecOf<T>::N;
+    constexpr int G = SUB_ROWS / (32 * VEC);
     __shared__ A wsh[NW][SUB_NI];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = v.sub_lev[blockIdx.x], nlev = v.sub_nlev[blockIdx.x];
@@ -111,62 +144,108 @@ __global__ void __launch_bounds__(HT) k_sub_fwd(HView v, const T* __restrict__ d
             const HSnode sn = v.sn[t.s];
             for (int i = lane; i < sn.ni; i += 32) w[i] = (A)gather_w(v, sn, i, in, shift, ubuf);
             __syncwarp();
-            A acc[RPL];
+            A acc[G][VEC];
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) acc[r] = 0;
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) acc[g][e] = 0;
             const T* col = data + sn.data_off;
-            for (int j = 0; j < sn.ni; ++j) {
-                const A wj = w[j];
-                const T* cj = col + col_offset(sn.nd, j) - j;   // element q of column j at cj[q]
+            for (int j0 = 0; j0 < sn.ni; j0 += 4) {
+                A val[4][G][VEC];
 #pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int q = t.a0 + lane + 32 * r;
-                    if (q < t.a1 && q >= j) acc[r] += (A)ldv(cj + q) * wj;
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    const T* cj = col + col_start(sn.nd, j, VEC) - j;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int q0 = t.a0 + VEC * (lane + 32 * g);
+                        if (j < sn.ni && q0 < t.a1 && q0 + VEC > j) {
+                            ld16(cj + q0, val[u][g]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) val[u][g][e] = 0;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    const A wj = j < sn.ni ? w[j] : (A)0;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int q0 = t.a0 + VEC * (lane + 32 * g);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (q0 + e >= j) acc[g][e] += val[u][g][e] * wj;
+                    }
                 }
             }
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) {
-                const int q = t.a0 + lane + 32 * r;
-                if (q < t.a1) finish_row(v, sn, q, (double)acc[r], ybuf, ubuf);
-            }
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int q = t.a0 + VEC * (lane + 32 * g) + e;
+                    if (q < t.a1) finish_row(v, sn, q, (double)acc[g][e], ybuf, ubuf);
+                }
             __syncwarp();
         }
         __syncthreads();
     }
 }
 
+// Backward: a warp task covers <= 4 columns of one cluster; the cluster's
+// v = [y_s; -x_B] is staged in the warp's shared memory; the four columns are
+// read together as aligned vectors and reduced across the warp.
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_sub_bwd(HView v, const T* __restrict__ data,
                                                 const double* __restrict__ ybuf, double* out) {
+    constexpr int VEC = VecOf<T>::N;
+    __shared__ A vsh[NW][SUB_ROWS + 8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = v.sub_lev[blockIdx.x], nlev = v.sub_nlev[blockIdx.x];
+    A* vv = vsh[warp];
     for (int lev = nlev - 1; lev >= 0; --lev) {
         const int t0 = v.sbp[base + lev], t1 = v.sbp[base + lev + 1];
         for (int ti = t0 + warp; ti < t1; ti += NW) {
             const HTask t = v.sbt[ti];
             const HSnode sn = v.sn[t.s];
-            A vv[RPL];
-#pragma unroll
-            for (int r = 0; r < RPL; ++r) {
-                const int q = lane + 32 * r;
+            for (int q = lane; q < sn.nd + VEC; q += 32) {
                 double x = 0.0;
                 if (q < sn.nd)
                     x = q < sn.ni ? ybuf[sn.first + q]
                                   : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
-                vv[r] = (A)x;
+                vv[q] = (A)x;
             }
+            __syncwarp();
             const T* col = data + sn.data_off;
-            for (int j = t.a0; j < t.a1; ++j) {
-                const T* cj = col + col_offset(sn.nd, j) - j;
-                A acc = 0;
+            A acc[4] = {0, 0, 0, 0};
+            const int qa = t.a0 & ~(VEC - 1);   // first aligned group of the first column
+            for (int q0 = qa + VEC * lane; q0 < sn.nd; q0 += 32 * VEC) {
+                A val[4][VEC];
 #pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int q = lane + 32 * r;
-                    if (q >= j && q < sn.nd) acc += (A)ldv(cj + q) * vv[r];
+                for (int u = 0; u < 4; ++u) {
+                    const int j = t.a0 + u;
+                    if (j < t.a1 && q0 + VEC > j) {
+                        ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) val[u][e] = 0;
+                    }
                 }
-                acc = wsum(acc);
-                if (lane == 0) out[v.pidx[sn.first + j]] = (double)acc;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = t.a0 + u;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e)
+                        if (q0 + e >= j && q0 + e < sn.nd) acc[u] += val[u][e] * vv[q0 + e];
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const A s = wsum(acc[u]);
+                if (lane == 0 && t.a0 + u < t.a1) out[v.pidx[sn.first + t.a0 + u]] = (double)s;
+            }
+            __syncwarp();
         }
         __syncthreads();
     }
@@ -209,11 +288,12 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
                                                const double* shift_sum, double inv_n,
                                                double* ybuf, double* ubuf, const double* tbuf,
                                                double* pbuf, unsigned int* tickets) {
-    __shared__ A w[UP_COLS];
+    constexpr int VEC = VecOf<T>::N;
+    __shared__ A w[UP_COLS + 4];
     __shared__ bool last;
     const HTask t = v.uft[task0 + blockIdx.x];
     const int tid = threadIdx.x;
-    if (t.s < 0) {   // rows of a low-rank group: u = inc - U t
+    if (t.s < 0) {   // rows of a low-rank group: u = inc - U t (thread per row)
         const HLr g = v.lr[-1 - t.s];
         const HSnode sn = v.sn[g.s];
         const int i = t.a0 + tid;
@@ -229,43 +309,60 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
     const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
     for (int j = t.b0 + tid; j < t.b1; j += HT) w[j - t.b0] = (A)gather_w(v, sn, j, in, shift, ubuf);
     __syncthreads();
-    const int q = t.a0 + tid;
-    A acc = 0;
-    if (q < t.a1) {
+    const int q0 = t.a0 + VEC * tid;   // this thread's aligned row group
+    A acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0;
+    if (q0 < t.a1) {
         const T* col = data + sn.data_off;
-        const int jend = q < sn.ni ? min(t.b1, q + 1) : t.b1;
-        int j = t.b0;
-        for (; j + 4 <= jend; j += 4) {
-            const T* c0 = col + col_offset(sn.nd, j) - j;
-            const T* c1 = col + col_offset(sn.nd, j + 1) - (j + 1);
-            const T* c2 = col + col_offset(sn.nd, j + 2) - (j + 2);
-            const T* c3 = col + col_offset(sn.nd, j + 3) - (j + 3);
-            const A x0 = (A)ldv(c0 + q), x1 = (A)ldv(c1 + q), x2 = (A)ldv(c2 + q),
-                    x3 = (A)ldv(c3 + q);
-            acc += x0 * w[j - t.b0];
-            acc += x1 * w[j + 1 - t.b0];
-            acc += x2 * w[j + 2 - t.b0];
-            acc += x3 * w[j + 3 - t.b0];
+        const int jend = (q0 + VEC - 1 < sn.ni) ? min(t.b1, q0 + VEC) : t.b1;
+        for (int j0 = t.b0; j0 < jend; j0 += 4) {
+            A val[4][VEC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                if (j < jend) {
+                    ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) val[u][e] = 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                const A wj = j < jend ? w[j - t.b0] : (A)0;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (q0 + e >= j) acc[e] += val[u][e] * wj;
+            }
         }
-        for (; j < jend; ++j) acc += (A)ldv(col + col_offset(sn.nd, j) - j + q) * w[j - t.b0];
     }
     if (t.nparts == 1) {
-        if (q < t.a1) finish_row(v, sn, dense_row(v, sn, q), (double)acc, ybuf, ubuf);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (q0 + e < t.a1) finish_row(v, sn, dense_row(v, sn, q0 + e), (double)acc[e], ybuf, ubuf);
         return;
     }
     const int rows = t.a1 - t.a0;
     const int c = t.b0 / UP_COLS;
-    if (q < t.a1) pbuf[t.part + (int64_t)c * rows + tid] = (double)acc;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+        if (q0 + e < t.a1) pbuf[t.part + (int64_t)c * rows + (q0 + e - t.a0)] = (double)acc[e];
     __threadfence();
     __syncthreads();
     if (tid == 0) last = atomicAdd(&tickets[t.ticket], 1u) == (unsigned)(t.nparts - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (q < t.a1) {
-        double s = 0.0;
-        for (int p = 0; p < t.nparts; ++p) s += __ldcg(&pbuf[t.part + (int64_t)p * rows + tid]);
-        finish_row(v, sn, dense_row(v, sn, q), s, ybuf, ubuf);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        const int q = q0 + e;
+        if (q < t.a1) {
+            double s = 0.0;
+            for (int p = 0; p < t.nparts; ++p) s += __ldcg(&pbuf[t.part + (int64_t)p * rows + (q - t.a0)]);
+            finish_row(v, sn, dense_row(v, sn, q), s, ybuf, ubuf);
+        }
     }
     if (tid == 0) tickets[t.ticket] = 0u;
 }
@@ -274,7 +371,7 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_lr_bwd(HView v, const T* __restrict__ data, int g0,
                                                const double* out, double* tbuf) {
-    __shared__ A vv[UP_ROWS];
+    __shared__ A vv[LR_ROWS];
     __shared__ A red[HT];
     const HLr g = v.lr[g0 + blockIdx.x];
     const HSnode sn = v.sn[g.s];
@@ -301,37 +398,55 @@ template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ data, int task0,
                                                const double* __restrict__ ybuf,
                                                const double* tbuf, double* out) {
+    constexpr int VEC = VecOf<T>::N;
     extern __shared__ __align__(16) unsigned char smem[];
     A* vv = reinterpret_cast<A*>(smem);
     const HTask t = v.ubt[task0 + blockIdx.x];
     const HSnode sn = v.sn[t.s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < sn.nd; q += HT)
-        vv[q] = (A)(q < sn.ni ? ybuf[sn.first + q]
-                              : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]]);
+    for (int q = threadIdx.x; q < sn.nd + VEC; q += HT) {
+        double x = 0.0;
+        if (q < sn.nd)
+            x = q < sn.ni ? ybuf[sn.first + q]
+                          : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
+        vv[q] = (A)x;
+    }
     __syncthreads();
     const T* col = data + sn.data_off;
-    for (int j = t.a0 + warp; j < t.a1; j += NW) {
-        const T* cj = col + col_offset(sn.nd, j) - j;
-        A acc = 0;
-        int q = j + lane;
-        for (; q + 96 < sn.nd; q += 128) {
-            const A x0 = (A)ldv(cj + q), x1 = (A)ldv(cj + q + 32), x2 = (A)ldv(cj + q + 64),
-                    x3 = (A)ldv(cj + q + 96);
-            acc += x0 * vv[q];
-            acc += x1 * vv[q + 32];
-            acc += x2 * vv[q + 64];
-            acc += x3 * vv[q + 96];
-        }
-        for (; q < sn.nd; q += 32) acc += (A)ldv(cj + q) * vv[q];
-        for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
-            const HLr G = v.lr[g];
-            const T* V = data + G.off_v + (int64_t)j * G.k;
-            for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)tbuf[G.t_off + l];
-        }
-        acc = wsum(acc);
-        if (lane == 0) out[v.pidx[sn.first + j]] = (double)acc;
+    const int j = t.a0 + warp;   // one column per warp
+    if (j >= t.a1) return;
+    const T* cj = col + col_start(sn.nd, j, VEC) - j;
+    A acc = 0;
+    const int qa = j & ~(VEC - 1);
+    int q0 = qa + VEC * lane;
+    for (; q0 + 3 * 32 * VEC < sn.nd; q0 += 4 * 32 * VEC) {
+        A val[4][VEC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * 32 * VEC, val[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int q = q0 + u * 32 * VEC + e;
+                if (q >= j) acc += val[u][e] * vv[q];
+            }
     }
+    for (; q0 < sn.nd; q0 += 32 * VEC) {
+        A val[VEC];
+        ld16(cj + q0, val);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const int q = q0 + e;
+            if (q >= j && q < sn.nd) acc += val[e] * vv[q];
+        }
+    }
+    for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
+        const HLr G = v.lr[g];
+        const T* V = data + G.off_v + (int64_t)j * G.k;
+        for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)tbuf[G.t_off + l];
+    }
+    acc = wsum(acc);
+    if (lane == 0) out[v.pidx[sn.first + j]] = (double)acc;
 }
 
 HView view_of(const HFactorDev& F) {
@@ -389,7 +504,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const double* sh
         }
         const int nt = F.ub_ptr[lev + 1] - F.ub_ptr[lev];
         if (nt > 0) {
-            const size_t sm = sizeof(A) * (F.u_nd_max[lev] + 2);
+            const size_t sm = sizeof(A) * (F.u_nd_max[lev] + 16);
             k_up_bwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.ub_ptr[lev], S.ybuf, S.tbuf, out);
             ++launches;
         }
@@ -451,11 +566,13 @@ static int upload_vec(const std::vector<V>& h, V** d) {
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     const int esz_acc = precision == BID_FP64 ? 8 : 4;
     for (size_t L = 0; L < h.u_nd_max.size(); ++L)
-        if ((int64_t)(h.u_nd_max[L] + 2) * esz_acc > 200 * 1024 ||
+        if ((int64_t)(h.u_nd_max[L] + 16) * esz_acc > 200 * 1024 ||
             (int64_t)(h.u_ni_max[L] + 2 + HT) * esz_acc > 200 * 1024)
             return set_error(BID_EINVAL, "cluster too large for shared memory (nd=%d)", h.u_nd_max[L]);
     for (const HLr& g : h.lr)
-        if (g.k > 64 || g.m > UP_ROWS) return set_error(BID_EINVAL, "low-rank group out of range");
+        if (g.k > LR_KMAX || g.m > LR_ROWS) return set_error(BID_EINVAL, "low-rank group out of range");
+    const int want_vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
+    if (h.vec != want_vec) return set_error(BID_EINVAL, "factor layout built for another precision");
     d->n = h.n;
     d->pin = h.pin;
     d->precision = precision;
@@ -500,6 +617,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
         esz = 2;
     }
     d->bytes_pass = 2 * (int64_t)n * esz;
+    d->alg_bytes_pass = 2 * (h.dense_entries + h.lowrank_entries) * esz;
+    d->vec = h.vec;
     return BID_OK;
 }
 

@@ -88,7 +88,21 @@ struct HSnode {
     int32_t lr_begin, lr_end;
     int32_t sub;        // bottom subtree id, or -1 for an upper cluster
 };
+// Number of stored (nonzero) entries of columns 0 .. j-1 of the dense part.
 BID_HD int64_t col_offset(int64_t nd, int64_t j) { return j * nd - j * (j - 1) / 2; }
+// Start of column j inside the cluster's dense data.  Column c holds rows
+// c .. nd-1 followed by p_c zeros, p_c = (1 - (nd - c)) mod vec, so that
+// start(j) - j is a multiple of vec: row q of every column then sits at an
+// address congruent to q modulo vec, and a thread can read rows q .. q+vec-1
+// (q a multiple of vec) of any column as one aligned 16-byte vector.
+BID_HD int64_t col_start(int64_t nd, int64_t j, int64_t vec) {
+    const int64_t r0 = ((1 - nd) % vec + vec) % vec;
+    const int64_t m = j % vec;
+    const int64_t wrap = m - (vec - r0);
+    const int64_t pad = (j / vec) * (vec * (vec - 1) / 2) + m * r0 + m * (m - 1) / 2 -
+                        vec * (wrap > 0 ? wrap : 0);
+    return col_offset(nd, j) + pad;
+}
 
 struct HLr {
     int32_t s, row0, m, k;      // rows [row0, row0+m) of M_s (boundary rows)
@@ -128,7 +142,8 @@ struct HFactorHost {
     std::vector<int32_t> u_ni_max, u_nd_max;   // level -> max ni / nd (shared memory)
     int64_t ubuf = 0, tbuf = 0, pbuf = 0;
     int32_t ntickets = 0;
-    int64_t dense_entries = 0, lowrank_entries = 0;
+    int32_t vec = 2;
+    int64_t dense_entries = 0, lowrank_entries = 0;   // algorithmic (no padding)
     int64_t nsub = 0, nlr = 0;
 };
 
@@ -137,6 +152,7 @@ struct HBuildOpts {
     int leaf = 16;
     int block = 64;
     int threads = 0;
+    int vec = 2;        // elements per 16-byte vector of the storage precision
 };
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  pin >= 0 replaces row and
@@ -148,9 +164,10 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin,
 constexpr int SUB_ROWS = 256;    // max ni + nb of a bottom cluster (8 rows per lane)
 constexpr int SUB_NI = 128;      // max ni of a bottom cluster
 constexpr int SUB_PIV = 4096;    // max pivots of a bottom subtree
-constexpr int UP_ROWS = 256;     // rows of an upper forward task (one per thread)
-constexpr int UP_COLS = 256;     // columns of an upper forward task
-constexpr int UP_BCOLS = 64;     // columns of an upper backward task
+constexpr int UP_THREADS = 256;  // threads of an upper forward task (vec rows each)
+constexpr int UP_COLS = 64;      // columns of an upper forward task
+constexpr int UP_BCOLS = 8;      // columns of an upper backward task (one per warp)
+constexpr int LR_ROWS = 256;     // max rows of a low-rank group
 constexpr int LR_KMAX = 64;      // largest rank kept in a low-rank group
 
 // ---------------------------------------------------------------- device factor
@@ -178,7 +195,9 @@ struct HFactorDev {
     std::vector<int32_t> ulr_ptr, uf_ptr, ub_ptr, u_ni_max, u_nd_max;
     int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0;
     int32_t ntickets = 0;
-    int64_t bytes_pass = 0;             // factor bytes read by fwd + bwd
+    int64_t bytes_pass = 0;             // stored factor bytes read by fwd + bwd
+    int64_t alg_bytes_pass = 0;         // nonzero entries only (no padding)
+    int32_t vec = 2;
 };
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
 void free_hfactor(HFactorDev* d);

@@ -79,15 +79,17 @@ def test_host_factor_exact_equals_pseudo_inverse(bid, leaf, block):
     assert st["levels1"] >= 1 and st["lowrank_blocks"] == 0
 
 
-@pytest.mark.parametrize("n,leaf,block", [(161, 16, 128), (129, 32, 64), (129, 8, 16)])
-def test_host_factor_exact_with_upper_levels(bid, n, leaf, block):
+@pytest.mark.parametrize("n,leaf,block,precision", [(161, 16, 128, "fp64"), (129, 32, 64, "fp32"),
+                                                   (129, 8, 16, "bf16"), (161, 16, 128, "bf16")])
+def test_host_factor_exact_with_upper_levels(bid, n, leaf, block, precision):
     # large enough that clusters above the bottom subtrees exist (upper levels,
-    # column-chunked row tasks)
+    # column-chunked row tasks); the layout padding of each storage precision
+    # (16-byte vectors of 2, 4 or 8 entries) is replayed in FP64
     m, p = torso_square_2d(n), params_2d(0.1)
     hs = bid.HostSystem(m, p)
     s = ob.build_system(m, p)
     b = np.random.default_rng(n).normal(size=s.N)
-    x, st = hs.factor_solve(1, b, leaf=leaf, block=block)
+    x, st = hs.factor_solve(1, b, leaf=leaf, block=block, precision=precision)
     x -= x.mean()
     xo = ob.s1_pseudo_inverse_apply(s, b)
     assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
