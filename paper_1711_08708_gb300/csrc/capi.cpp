@@ -353,11 +353,11 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.nk = hk.n;
     st.supernodes1 = (int64_t)h1.sn.size();
     st.supernodesk = (int64_t)hk.sn.size();
-    st.levels1 = h1.height + (h1.nsub > 0 ? 1 : 0);
-    st.levelsk = hk.height + (hk.nsub > 0 ? 1 : 0);
+    st.levels1 = h1.height;
+    st.levelsk = hk.height;
     st.dense_entries = h1.dense_entries + hk.dense_entries;
     st.lowrank_entries = h1.lowrank_entries + hk.lowrank_entries;
-    st.dense_blocks = h1.nsub + hk.nsub;
+    st.dense_blocks = h1.nlarge + hk.nlarge;
     st.lowrank_blocks = h1.nlr + hk.nlr;
     st.bytes_p1 = P->F1.bytes_pass;
     st.bytes_pk = P->FK.bytes_pass;

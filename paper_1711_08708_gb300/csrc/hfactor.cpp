@@ -294,33 +294,17 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         }
     }
 
-    // ---------------- bottom subtrees (small clusters, one CTA per subtree)
-    std::vector<int> sub_begin(nt);
+    // ---------------- small / large clusters
+    std::vector<int> sub_begin(nt);   // subtree of s = post-order range [sub_begin, s]
     for (int s = 0; s < nt; ++s) {
         int b = s;
         for (int k = 0; k < nch[s]; ++k) b = std::min(b, sub_begin[ch[s][k]]);
         sub_begin[s] = b;
     }
-    std::vector<char> elig(nt, 0);
-    std::vector<int64_t> subpiv(nt, 0);
     for (int s = 0; s < nt; ++s) {
-        const HSnode& h = F->sn[s];
-        bool ok = h.ni + h.nb <= SUB_ROWS && h.ni <= SUB_NI;
-        int64_t piv = h.ni;
-        for (int k = 0; k < nch[s]; ++k) {
-            ok = ok && elig[ch[s][k]];
-            piv += subpiv[ch[s][k]];
-        }
-        subpiv[s] = piv;
-        elig[s] = ok && piv <= SUB_PIV;
+        HSnode& h = F->sn[s];
+        h.large = (h.ni > SMALL_NI || h.ni + h.nb > SMALL_NF) ? 1 : 0;
     }
-    std::vector<int> sub_roots;
-    for (int s = 0; s < nt; ++s) {
-        F->sn[s].sub = -1;
-        if (elig[s] && (parent[s] < 0 || !elig[parent[s]])) sub_roots.push_back(s);
-    }
-    for (size_t t = 0; t < sub_roots.size(); ++t)
-        for (int s = sub_begin[sub_roots[t]]; s <= sub_roots[t]; ++s) F->sn[s].sub = (int32_t)t;
 
     // ---------------- numeric factorisation
     const double eps = o.eps;
@@ -388,7 +372,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         // ancestor separator, chunked to `lrows` rows; kept when the truncated
         // rank-revealing QR reaches eps with k (m + ni) <= m ni / 2
         std::vector<char> in_lr(nb, 0);
-        if (eps > 0.0 && h.sub < 0 && ni >= 16) {
+        if (eps > 0.0 && h.large && ni >= 16) {
             int j = 0;
             while (j < nb) {
                 int a = parent[s];
@@ -510,76 +494,90 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             std::vector<double>().swap(w.data);
         }
     }
-    // bottom subtree tasks
-    const int nsub = (int)sub_roots.size();
-    F->nsub = nsub;
-    F->sub_lev.resize(nsub);
-    F->sub_nlev.resize(nsub);
-    for (int t = 0; t < nsub; ++t) {
-        const int r = sub_roots[t];
-        const int nlev = F->sn[r].height + 1;
-        F->sub_lev[t] = (int32_t)F->sfp.size();
-        F->sub_nlev[t] = nlev;
-        for (int lev = 0; lev < nlev; ++lev) {
-            F->sfp.push_back((int32_t)F->sft.size());
-            F->sbp.push_back((int32_t)F->sbt.size());
-            for (int s = sub_begin[r]; s <= r; ++s) {
-                const HSnode& h = F->sn[s];
-                if (h.height != lev || h.ni + h.nb == 0) continue;
-                const int rows = h.ni + h.nb;   // no low-rank groups in bottom clusters
-                for (int a = 0; a < rows; a += SUB_ROWS) {
-                    HTask k{};
-                    k.s = s;
-                    k.a0 = a;
-                    k.a1 = std::min(rows, a + SUB_ROWS);
-                    F->sft.push_back(k);
-                }
-                const int cpw = 4;
-                for (int a = 0; a < h.ni; a += cpw) {
-                    HTask k{};
-                    k.s = s;
-                    k.a0 = a;
-                    k.a1 = std::min<int>(h.ni, a + cpw);
-                    F->sbt.push_back(k);
-                }
-            }
-        }
-        F->sfp.push_back((int32_t)F->sft.size());
-        F->sbp.push_back((int32_t)F->sbt.size());
-    }
-    // upper levels, ascending height
-    std::vector<int> ulev;
-    for (int s = 0; s < nt; ++s)
-        if (F->sn[s].sub < 0) ulev.push_back(F->sn[s].height);
-    std::sort(ulev.begin(), ulev.end());
-    ulev.erase(std::unique(ulev.begin(), ulev.end()), ulev.end());
-    const int nul = (int)ulev.size();
-    F->height = nul;
+    // per-level work: flat items of the small clusters, chunked tasks of the
+    // large ones
+    const int H = maxh + 1;
+    F->height = H;
+    std::vector<std::vector<int>> bylev(H);
+    for (int s = 0; s < nt; ++s) bylev[F->sn[s].height].push_back(s);
+    F->ff_ptr.assign(1, 0);
+    F->fb_ptr.assign(1, 0);
     F->ulr_ptr.assign(1, 0);
     F->uf_ptr.assign(1, 0);
     F->ub_ptr.assign(1, 0);
     int64_t tbuf = 0, pbuf = 0;
     int32_t tickets = 0;
-    for (int L = 0; L < nul; ++L) {
+    // pack the items of one level into CTAs: <= FLAT_ITEMS items and
+    // <= STAGE_MAX staged values; items of one cluster are consecutive
+    auto pack = [&](const std::vector<int>& cl, bool fwd, std::vector<FCta>& ctas,
+                    std::vector<FItem>& items, std::vector<FStage>& stages) {
+        FCta c{};
+        c.it0 = c.it1 = (int32_t)items.size();
+        c.st0 = c.st1 = (int32_t)stages.size();
+        auto flush = [&]() {
+            if (c.it1 > c.it0) ctas.push_back(c);
+            c = FCta{};
+            c.it0 = c.it1 = (int32_t)items.size();
+            c.st0 = c.st1 = (int32_t)stages.size();
+        };
+        for (int s : cl) {
+            const HSnode& h = F->sn[s];
+            if (h.ni == 0 && h.nb == 0) continue;
+            const int stage = fwd ? h.ni : h.nd + vec;          // values staged per cluster
+            const int nitems = fwd ? (h.nd + vec - 1) / vec : h.ni;
+            for (int k = 0; k < nitems;) {
+                if (c.it1 - c.it0 == FLAT_ITEMS || c.total + stage > STAGE_MAX) flush();
+                // stage the cluster in this CTA
+                FStage g{s, c.total};
+                stages.push_back(g);
+                c.st1 = (int32_t)stages.size();
+                c.total += stage;
+                while (k < nitems && c.it1 - c.it0 < FLAT_ITEMS) {
+                    FItem it{};
+                    it.s = s;
+                    it.q = fwd ? k * vec : k;
+                    it.woff = g.woff;
+                    items.push_back(it);
+                    c.it1 = (int32_t)items.size();
+                    ++k;
+                }
+            }
+        }
+        flush();
+    };
+    for (int L = 0; L < H; ++L) {
+        std::vector<int> small;
         int ni_max = 0, nd_max = 0;
-        for (int s = 0; s < nt; ++s) {
+        for (int s : bylev[L]) {
             HSnode& h = F->sn[s];
-            if (h.sub >= 0 || h.height != ulev[L]) continue;
+            h.lr_begin = h.lr_end = (int32_t)F->lr.size();
+            if (!h.large) {
+                small.push_back(s);
+                F->nsmall++;
+                continue;
+            }
+            F->nlarge++;
             ni_max = std::max(ni_max, h.ni);
             nd_max = std::max(nd_max, h.nd);
-            h.lr_begin = (int32_t)F->lr.size();
             for (HLr g : W[s].lr) {
                 g.t_off = (int32_t)tbuf;
                 tbuf += g.k;
                 F->lr.push_back(g);
             }
             h.lr_end = (int32_t)F->lr.size();
-            // forward dense row chunks
+        }
+        pack(small, true, F->ffc, F->ffi, F->ffs);
+        pack(small, false, F->fbc, F->fbi, F->fbs);
+        F->ff_ptr.push_back((int32_t)F->ffc.size());
+        F->fb_ptr.push_back((int32_t)F->fbc.size());
+        for (int s : bylev[L]) {
+            const HSnode& h = F->sn[s];
+            if (!h.large) continue;
             const int up_rows = UP_THREADS * vec;   // a thread owns vec consecutive rows
             for (int a = 0; a < h.nd; a += up_rows) {
                 const int a1 = std::min(h.nd, a + up_rows);
                 const int cols = a1 <= h.ni ? a1 : h.ni;
-                const int np = (cols + UP_COLS - 1) / UP_COLS;
+                const int np = std::max(1, (cols + UP_COLS - 1) / UP_COLS);
                 int32_t part = -1, tk = -1;
                 if (np > 1) {
                     part = (int32_t)pbuf;

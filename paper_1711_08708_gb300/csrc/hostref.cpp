@@ -52,17 +52,17 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x) {
             for (int j = b0; j < jend; ++j) acc[q - a0] += elem(s, q, j) * gather(s, j);
         }
     };
-    for (int64_t st = 0; st < F.nsub; ++st)
-        for (int lev = 0; lev < F.sub_nlev[st]; ++lev)
-            for (int ti = F.sfp[F.sub_lev[st] + lev]; ti < F.sfp[F.sub_lev[st] + lev + 1]; ++ti) {
-                const HTask& k = F.sft[ti];
-                const HSnode& s = F.sn[k.s];
-                std::vector<double> acc(k.a1 - k.a0, 0.0);
-                fwd_rows(s, k.a0, k.a1, 0, s.ni, acc);
-                for (int q = k.a0; q < k.a1; ++q) finish(s, drow(s, q), acc[q - k.a0]);
-            }
     const int nul = (int)F.uf_ptr.size() - 1;
     for (int lev = 0; lev < nul; ++lev) {
+        for (int c = F.ff_ptr[lev]; c < F.ff_ptr[lev + 1]; ++c)
+            for (int it = F.ffc[c].it0; it < F.ffc[c].it1; ++it) {
+                const FItem& f = F.ffi[it];
+                const HSnode& s = F.sn[f.s];
+                const int q1 = std::min(s.nd, f.q + F.vec);
+                std::vector<double> acc(q1 - f.q, 0.0);
+                fwd_rows(s, f.q, q1, 0, s.ni, acc);
+                for (int q = f.q; q < q1; ++q) finish(s, drow(s, q), acc[q - f.q]);
+            }
         for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
             const HLr& G = F.lr[g];
             const HSnode& s = F.sn[G.s];
@@ -127,18 +127,15 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x) {
                 x[F.pidx[s.first + j]] = a;
             }
         }
-    }
-    for (int64_t st = 0; st < F.nsub; ++st)
-        for (int lev = F.sub_nlev[st] - 1; lev >= 0; --lev)
-            for (int ti = F.sbp[F.sub_lev[st] + lev]; ti < F.sbp[F.sub_lev[st] + lev + 1]; ++ti) {
-                const HTask& k = F.sbt[ti];
-                const HSnode& s = F.sn[k.s];
-                for (int j = k.a0; j < k.a1; ++j) {
-                    double a = 0.0;
-                    for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
-                    x[F.pidx[s.first + j]] = a;
-                }
+        for (int c = F.fb_ptr[lev]; c < F.fb_ptr[lev + 1]; ++c)
+            for (int it = F.fbc[c].it0; it < F.fbc[c].it1; ++it) {
+                const FItem& f = F.fbi[it];
+                const HSnode& s = F.sn[f.s];
+                double a = 0.0;
+                for (int q = f.q; q < s.nd; ++q) a += elem(s, q, f.q) * vrow(s, q);
+                x[F.pidx[s.first + f.q]] = a;
             }
+    }
 }
 
 }  // namespace
@@ -219,10 +216,10 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
         std::memset(stats, 0, sizeof(*stats));
         stats->n1 = F.n;
         stats->supernodes1 = (int64_t)F.sn.size();
-        stats->levels1 = F.height + (F.nsub > 0 ? 1 : 0);
+        stats->levels1 = F.height;
         stats->dense_entries = F.dense_entries;
         stats->lowrank_entries = F.lowrank_entries;
-        stats->dense_blocks = F.nsub;
+        stats->dense_blocks = F.nlarge;
         stats->lowrank_blocks = F.nlr;
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;

@@ -8,14 +8,14 @@
 // Backward pass (root first): x_s = (L_ss^-1)^T y_s - (L_Bs L_ss^-1)^T x_B.
 //
 // Launches of one solve:
-//   k_sub_fwd   one CTA per bottom subtree, all its levels (warp tasks, CTA
-//               barrier between levels);
-//   per upper level: k_lr_fwd (V^T w of the low-rank groups, if any) and
-//               k_up_fwd (thread per dense row over a column chunk; chunks of
-//               a row are combined in a fixed order by the last CTA);
-//   per upper level, root first: k_lr_bwd (U^T v) and k_up_bwd (warp per
-//               column over the packed column, v staged in shared memory);
-//   k_sub_bwd   one CTA per bottom subtree.
+//   per level, leaves first: k_flat_fwd (small clusters: thread per aligned
+//               row group, the CTA's cluster inputs staged in shared memory),
+//               k_lr_fwd (V^T w of the low-rank groups, if any) and k_up_fwd
+//               (large clusters: thread per row group over a column chunk;
+//               chunks of a row are combined in a fixed order by the last CTA);
+//   per level, root first: k_lr_bwd (U^T v), k_up_bwd (large clusters: warp
+//               per column, v staged in shared memory) and k_flat_bwd (small
+//               clusters: thread per column).
 // Factors are stored in FP64, FP32 or BF16; FP32/BF16 accumulate in FP32 (the
 // precision form), FP64 in FP64.  All reductions have a fixed order, so the
 // result is bitwise reproducible.
@@ -32,7 +32,6 @@ namespace {
 
 constexpr int HT = 256;   // threads per CTA
 constexpr int NW = HT / 32;
-constexpr int RPL = SUB_ROWS / 32;   // rows per lane in the bottom kernels
 
 __device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
@@ -81,12 +80,12 @@ struct HView {
     const int32_t* __restrict__ drows;
     const HSnode* __restrict__ sn;
     const HLr* __restrict__ lr;
-    const int32_t* __restrict__ sub_lev;
-    const int32_t* __restrict__ sub_nlev;
-    const int32_t* __restrict__ sfp;
-    const int32_t* __restrict__ sbp;
-    const HTask* __restrict__ sft;
-    const HTask* __restrict__ sbt;
+    const FCta* __restrict__ ffc;
+    const FCta* __restrict__ fbc;
+    const FItem* __restrict__ ffi;
+    const FItem* __restrict__ fbi;
+    const FStage* __restrict__ ffs;
+    const FStage* __restrict__ fbs;
     const HTask* __restrict__ uft;
     const HTask* __restrict__ ubt;
 };
@@ -121,134 +120,133 @@ __device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q
     return q < sn.ni ? q : v.drows[sn.drow_off + q - sn.ni];
 }
 
-// ------------------------------------------------------------ bottom subtrees
-// Forward: a warp task covers <= SUB_ROWS dense rows of one cluster; lane l
-// owns the aligned row groups a0 + VEC*(l + 32 g).  Columns are consumed four
-// at a time so that 4*G vector loads per lane are in flight.
-template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_sub_fwd(HView v, const T* __restrict__ data,
-                                                const double* __restrict__ in,
-                                                const double* shift_sum, double inv_n,
-                                                double* ybuf, double* ubuf) {
-    constexpr int VEC = VecOf<T>::N;
-    constexpr int G = SUB_ROWS / (32 * VEC);
-    __shared__ A wsh[NW][SUB_NI];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int base = v.sub_lev[blockIdx.x], nlev = v.sub_nlev[blockIdx.x];
-    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
-    A* w = wsh[warp];
-    for (int lev = 0; lev < nlev; ++lev) {
-        const int t0 = v.sfp[base + lev], t1 = v.sfp[base + lev + 1];
-        for (int ti = t0 + warp; ti < t1; ti += NW) {
-            const HTask t = v.sft[ti];
-            const HSnode sn = v.sn[t.s];
-            for (int i = lane; i < sn.ni; i += 32) w[i] = (A)gather_w(v, sn, i, in, shift, ubuf);
-            __syncwarp();
-            A acc[G][VEC];
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[g][e] = 0;
-            const T* col = data + sn.data_off;
-            for (int j0 = 0; j0 < sn.ni; j0 += 4) {
-                A val[4][G][VEC];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    const T* cj = col + col_start(sn.nd, j, VEC) - j;
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int q0 = t.a0 + VEC * (lane + 32 * g);
-                        if (j < sn.ni && q0 < t.a1 && q0 + VEC > j) {
-                            ld16(cj + q0, val[u][g]);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < VEC; ++e) val[u][g][e] = 0;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    const A wj = j < sn.ni ? w[j] : (A)0;
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int q0 = t.a0 + VEC * (lane + 32 * g);
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e)
-                            if (q0 + e >= j) acc[g][e] += val[u][g][e] * wj;
-                    }
-                }
-            }
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const int q = t.a0 + VEC * (lane + 32 * g) + e;
-                    if (q < t.a1) finish_row(v, sn, q, (double)acc[g][e], ybuf, ubuf);
-                }
-            __syncwarp();
-        }
-        __syncthreads();
+// ------------------------------------------------------------ small clusters
+// Stage the inputs of a flat CTA's clusters: entry f belongs to the last
+// FStage with woff <= f (binary search over the CTA's stage list).
+__device__ __forceinline__ int stage_owner(const int2* st, int nst, int f) {
+    int lo = 0, hi = nst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (st[mid].y <= f) lo = mid;
+        else hi = mid - 1;
     }
+    return lo;
 }
 
-// Backward: a warp task covers <= 4 columns of one cluster; the cluster's
-// v = [y_s; -x_B] is staged in the warp's shared memory; the four columns are
-// read together as aligned vectors and reduced across the warp.
+// Forward: thread = aligned row group q .. q+VEC-1 of a small cluster over all
+// its columns (four columns per step, 16-byte vector loads).
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_sub_bwd(HView v, const T* __restrict__ data,
-                                                const double* __restrict__ ybuf, double* out) {
+__global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ data, int cta0,
+                                                 const double* __restrict__ in,
+                                                 const double* shift_sum, double inv_n,
+                                                 double* ybuf, double* ubuf) {
     constexpr int VEC = VecOf<T>::N;
-    __shared__ A vsh[NW][SUB_ROWS + 8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int base = v.sub_lev[blockIdx.x], nlev = v.sub_nlev[blockIdx.x];
-    A* vv = vsh[warp];
-    for (int lev = nlev - 1; lev >= 0; --lev) {
-        const int t0 = v.sbp[base + lev], t1 = v.sbp[base + lev + 1];
-        for (int ti = t0 + warp; ti < t1; ti += NW) {
-            const HTask t = v.sbt[ti];
-            const HSnode sn = v.sn[t.s];
-            for (int q = lane; q < sn.nd + VEC; q += 32) {
-                double x = 0.0;
-                if (q < sn.nd)
-                    x = q < sn.ni ? ybuf[sn.first + q]
-                                  : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
-                vv[q] = (A)x;
-            }
-            __syncwarp();
-            const T* col = data + sn.data_off;
-            A acc[4] = {0, 0, 0, 0};
-            const int qa = t.a0 & ~(VEC - 1);   // first aligned group of the first column
-            for (int q0 = qa + VEC * lane; q0 < sn.nd; q0 += 32 * VEC) {
-                A val[4][VEC];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = t.a0 + u;
-                    if (j < t.a1 && q0 + VEC > j) {
-                        ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) val[u][e] = 0;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = t.a0 + u;
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if (q0 + e >= j && q0 + e < sn.nd) acc[u] += val[u][e] * vv[q0 + e];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const A s = wsum(acc[u]);
-                if (lane == 0 && t.a0 + u < t.a1) out[v.pidx[sn.first + t.a0 + u]] = (double)s;
-            }
-            __syncwarp();
-        }
-        __syncthreads();
+    __shared__ A w[STAGE_MAX];
+    __shared__ int2 st[FLAT_ITEMS];
+    const FCta c = v.ffc[cta0 + blockIdx.x];
+    const int nst = c.st1 - c.st0;
+    for (int k = threadIdx.x; k < nst; k += HT) {
+        const FStage g = v.ffs[c.st0 + k];
+        st[k] = make_int2(g.s, g.woff);
     }
+    __syncthreads();
+    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
+    for (int f = threadIdx.x; f < c.total; f += HT) {
+        const int2 g = st[stage_owner(st, nst, f)];
+        const HSnode sn = v.sn[g.x];
+        w[f] = (A)gather_w(v, sn, f - g.y, in, shift, ubuf);
+    }
+    __syncthreads();
+    const int it = c.it0 + threadIdx.x;
+    if (it >= c.it1) return;
+    const FItem item = v.ffi[it];
+    const HSnode sn = v.sn[item.s];
+    const int q0 = item.q;
+    const A* ws = w + item.woff;
+    const T* col = data + sn.data_off;
+    const int jend = (q0 + VEC - 1 < sn.ni) ? q0 + VEC : sn.ni;
+    A acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0;
+    for (int j0 = 0; j0 < jend; j0 += 4) {
+        A val[4][VEC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            if (j < jend) {
+                ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) val[u][e] = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            const A wj = j < jend ? ws[j] : (A)0;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (q0 + e >= j) acc[e] += val[u][e] * wj;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+        if (q0 + e < sn.nd) finish_row(v, sn, dense_row(v, sn, q0 + e), (double)acc[e], ybuf, ubuf);
+}
+
+// Backward: thread = column j of a small cluster: x_j = sum_{q >= j} M[q][j] v[q]
+// over the packed column (aligned vectors, v staged in shared memory).
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_flat_bwd(HView v, const T* __restrict__ data, int cta0,
+                                                 const double* __restrict__ ybuf, double* out) {
+    constexpr int VEC = VecOf<T>::N;
+    __shared__ A vs[STAGE_MAX];
+    __shared__ int2 st[FLAT_ITEMS];
+    const FCta c = v.fbc[cta0 + blockIdx.x];
+    const int nst = c.st1 - c.st0;
+    for (int k = threadIdx.x; k < nst; k += HT) {
+        const FStage g = v.fbs[c.st0 + k];
+        st[k] = make_int2(g.s, g.woff);
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < c.total; f += HT) {
+        const int2 g = st[stage_owner(st, nst, f)];
+        const HSnode sn = v.sn[g.x];
+        const int q = f - g.y;
+        double x = 0.0;
+        if (q < sn.nd)
+            x = q < sn.ni ? ybuf[sn.first + q]
+                          : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
+        vs[f] = (A)x;
+    }
+    __syncthreads();
+    const int it = c.it0 + threadIdx.x;
+    if (it >= c.it1) return;
+    const FItem item = v.fbi[it];
+    const HSnode sn = v.sn[item.s];
+    const int j = item.q;
+    const A* vv = vs + item.woff;
+    const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
+    A acc = 0;
+    int q0 = j & ~(VEC - 1);
+    for (; q0 + 3 * VEC < sn.nd; q0 += 4 * VEC) {
+        A val[4][VEC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * VEC, val[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (q0 + u * VEC + e >= j) acc += val[u][e] * vv[q0 + u * VEC + e];
+    }
+    for (; q0 < sn.nd; q0 += VEC) {
+        A val[VEC];
+        ld16(cj + q0, val);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (q0 + e >= j && q0 + e < sn.nd) acc += val[e] * vv[q0 + e];
+    }
+    out[v.pidx[sn.first + j]] = (double)acc;
 }
 
 // ------------------------------------------------------------ upper levels
@@ -458,12 +456,12 @@ HView view_of(const HFactorDev& F) {
     v.drows = F.drows;
     v.sn = F.sn;
     v.lr = F.lr;
-    v.sub_lev = F.sub_lev;
-    v.sub_nlev = F.sub_nlev;
-    v.sfp = F.sfp;
-    v.sbp = F.sbp;
-    v.sft = F.sft;
-    v.sbt = F.sbt;
+    v.ffc = F.ffc;
+    v.fbc = F.fbc;
+    v.ffi = F.ffi;
+    v.fbi = F.fbi;
+    v.ffs = F.ffs;
+    v.fbs = F.fbs;
     v.uft = F.uft;
     v.ubt = F.ubt;
     return v;
@@ -475,13 +473,14 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const double* sh
     const HView v = view_of(F);
     const T* data = reinterpret_cast<const T*>(F.data);
     int launches = 0;
-    if (F.nsub > 0) {
-        k_sub_fwd<T, A><<<(unsigned)F.nsub, HT, 0, L.st>>>(v, data, in, shift_sum, inv_n, S.ybuf,
-                                                           S.ubuf);
-        ++launches;
-    }
-    const int nul = (int)F.uf_ptr.size() - 1;
-    for (int lev = 0; lev < nul; ++lev) {
+    const int H = (int)F.uf_ptr.size() - 1;
+    for (int lev = 0; lev < H; ++lev) {
+        const int nf = F.ff_ptr[lev + 1] - F.ff_ptr[lev];
+        if (nf > 0) {
+            k_flat_fwd<T, A><<<nf, HT, 0, L.st>>>(v, data, F.ff_ptr[lev], in, shift_sum, inv_n,
+                                                  S.ybuf, S.ubuf);
+            ++launches;
+        }
         const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
         if (ng > 0) {
             const size_t sm = sizeof(A) * (((F.u_ni_max[lev] + 1) & ~1) + HT);
@@ -496,7 +495,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const double* sh
             ++launches;
         }
     }
-    for (int lev = nul - 1; lev >= 0; --lev) {
+    for (int lev = H - 1; lev >= 0; --lev) {
         const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
         if (ng > 0) {
             k_lr_bwd<T, A><<<ng, HT, 0, L.st>>>(v, data, F.ulr_ptr[lev], out, S.tbuf);
@@ -508,10 +507,11 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const double* sh
             k_up_bwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.ub_ptr[lev], S.ybuf, S.tbuf, out);
             ++launches;
         }
-    }
-    if (F.nsub > 0) {
-        k_sub_bwd<T, A><<<(unsigned)F.nsub, HT, 0, L.st>>>(v, data, S.ybuf, out);
-        ++launches;
+        const int nf = F.fb_ptr[lev + 1] - F.fb_ptr[lev];
+        if (nf > 0) {
+            k_flat_bwd<T, A><<<nf, HT, 0, L.st>>>(v, data, F.fb_ptr[lev], S.ybuf, out);
+            ++launches;
+        }
     }
     count_launches(launches);
     cudaError_t e = cudaGetLastError();
@@ -576,19 +576,21 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     d->n = h.n;
     d->pin = h.pin;
     d->precision = precision;
-    d->nsub = h.nsub;
+
     BID_TRY(upload_vec(h.pidx, &d->pidx));
     BID_TRY(upload_vec(h.bidx, &d->bidx));
     BID_TRY(upload_vec(h.inc, &d->inc));
     BID_TRY(upload_vec(h.drows, &d->drows));
     BID_TRY(upload_vec(h.sn, &d->sn));
     BID_TRY(upload_vec(h.lr, &d->lr));
-    BID_TRY(upload_vec(h.sub_lev, &d->sub_lev));
-    BID_TRY(upload_vec(h.sub_nlev, &d->sub_nlev));
-    BID_TRY(upload_vec(h.sfp, &d->sfp));
-    BID_TRY(upload_vec(h.sbp, &d->sbp));
-    BID_TRY(upload_vec(h.sft, &d->sft));
-    BID_TRY(upload_vec(h.sbt, &d->sbt));
+    BID_TRY(upload_vec(h.ffc, &d->ffc));
+    BID_TRY(upload_vec(h.fbc, &d->fbc));
+    BID_TRY(upload_vec(h.ffi, &d->ffi));
+    BID_TRY(upload_vec(h.fbi, &d->fbi));
+    BID_TRY(upload_vec(h.ffs, &d->ffs));
+    BID_TRY(upload_vec(h.fbs, &d->fbs));
+    d->ff_ptr = h.ff_ptr;
+    d->fb_ptr = h.fb_ptr;
     BID_TRY(upload_vec(h.uft, &d->uft));
     BID_TRY(upload_vec(h.ubt, &d->ubt));
     d->ulr_ptr = h.ulr_ptr;
@@ -623,8 +625,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 void free_hfactor(HFactorDev* d) {
-    void* ptrs[] = {d->pidx, d->bidx, d->inc, d->drows, d->sn, d->lr, d->sub_lev, d->sub_nlev,
-                    d->sfp, d->sbp, d->sft, d->sbt, d->uft, d->ubt, d->data};
+    void* ptrs[] = {d->pidx, d->bidx, d->inc, d->drows, d->sn, d->lr, d->ffc, d->fbc, d->ffi,
+                    d->fbi, d->ffs, d->fbs, d->uft, d->ubt, d->data};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

@@ -86,7 +86,7 @@ struct HSnode {
     int64_t data_off;   // packed dense columns
     int32_t drow_off;   // M_s row index of dense boundary row q (q >= ni) at drows[drow_off + q - ni]
     int32_t lr_begin, lr_end;
-    int32_t sub;        // bottom subtree id, or -1 for an upper cluster
+    int32_t large;      // 1: chunked upper-level tasks (may hold low-rank groups); 0: flat items
 };
 // Number of stored (nonzero) entries of columns 0 .. j-1 of the dense part.
 BID_HD int64_t col_offset(int64_t nd, int64_t j) { return j * nd - j * (j - 1) / 2; }
@@ -109,9 +109,23 @@ struct HLr {
     int64_t off_u, off_v;
     int32_t t_off, pad;         // slot of V^T w (forward) / U^T v (backward) in tbuf
 };
-// Work item of a triangular-pass kernel.
-//  bottom forward:  cluster s, dense rows [a0, a1)
-//  bottom backward: cluster s, columns [a0, a1)
+// Flat work of the small clusters of one level: one thread per item.
+//  forward item:  rows q .. q+vec-1 (q a multiple of vec) of cluster s over all
+//                 its columns, input w_s staged at woff in shared memory;
+//  backward item: column q of cluster s, v_s = [y_s; -x_B] staged at woff.
+// A CTA holds up to FLAT_ITEMS items and stages the inputs of its clusters
+// (FStage entries sorted by woff, `total` values in all).
+struct FItem {
+    int32_t s, q, woff, pad;
+};
+struct FStage {
+    int32_t s, woff;
+};
+struct FCta {
+    int32_t it0, it1, st0, st1, total, pad;
+};
+
+// Work item of a large-cluster kernel.
 //  upper forward:   s >= 0: dense rows [a0, a1) x columns [b0, b1); when the
 //                   row chunk is split over nparts column chunks, partial sums
 //                   go to pbuf[part + c*(a1-a0) + row] and the last CTA of
@@ -131,11 +145,12 @@ struct HFactorHost {
     std::vector<int32_t> bidx, inc, drows;
     std::vector<HLr> lr;
     std::vector<double> data;
-    // bottom subtrees: one CTA each, levels processed inside the CTA
-    std::vector<int32_t> sub_lev, sub_nlev;   // per subtree: base into sfp/sbp, levels
-    std::vector<int32_t> sfp, sbp;             // level -> task ranges
-    std::vector<HTask> sft, sbt;
-    // upper levels (ascending height)
+    // small clusters: flat items per level
+    std::vector<FCta> ffc, fbc;
+    std::vector<FItem> ffi, fbi;
+    std::vector<FStage> ffs, fbs;
+    std::vector<int32_t> ff_ptr, fb_ptr;       // level -> CTA ranges
+    // large clusters, per level
     std::vector<int32_t> ulr_ptr;              // level -> low-rank groups [ptr, ptr+1)
     std::vector<int32_t> uf_ptr, ub_ptr;       // level -> task ranges
     std::vector<HTask> uft, ubt;
@@ -144,7 +159,7 @@ struct HFactorHost {
     int32_t ntickets = 0;
     int32_t vec = 2;
     int64_t dense_entries = 0, lowrank_entries = 0;   // algorithmic (no padding)
-    int64_t nsub = 0, nlr = 0;
+    int64_t nsmall = 0, nlarge = 0, nlr = 0;
 };
 
 struct HBuildOpts {
@@ -161,9 +176,10 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin,
                   const HBuildOpts& o, HFactorHost* F);
 
 // Limits shared by the build and the kernels.
-constexpr int SUB_ROWS = 256;    // max ni + nb of a bottom cluster (8 rows per lane)
-constexpr int SUB_NI = 128;      // max ni of a bottom cluster
-constexpr int SUB_PIV = 4096;    // max pivots of a bottom subtree
+constexpr int SMALL_NI = 64;     // a cluster is small when ni <= SMALL_NI and
+constexpr int SMALL_NF = 320;    // ni + nb <= SMALL_NF (before compression)
+constexpr int FLAT_ITEMS = 256;  // items (threads) of a flat CTA
+constexpr int STAGE_MAX = 4096;  // staged input values of a flat CTA
 constexpr int UP_THREADS = 256;  // threads of an upper forward task (vec rows each)
 constexpr int UP_COLS = 64;      // columns of an upper forward task
 constexpr int UP_BCOLS = 8;      // columns of an upper backward task (one per warp)
@@ -181,18 +197,17 @@ struct HFactorDev {
     int32_t* drows = nullptr;
     HSnode* sn = nullptr;
     HLr* lr = nullptr;
-    int32_t* sub_lev = nullptr;
-    int32_t* sub_nlev = nullptr;
-    int32_t* sfp = nullptr;
-    int32_t* sbp = nullptr;
-    HTask* sft = nullptr;
-    HTask* sbt = nullptr;
+    FCta* ffc = nullptr;
+    FCta* fbc = nullptr;
+    FItem* ffi = nullptr;
+    FItem* fbi = nullptr;
+    FStage* ffs = nullptr;
+    FStage* fbs = nullptr;
     HTask* uft = nullptr;
     HTask* ubt = nullptr;
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
-    int64_t nsub = 0;
-    std::vector<int32_t> ulr_ptr, uf_ptr, ub_ptr, u_ni_max, u_nd_max;
+    std::vector<int32_t> ff_ptr, fb_ptr, ulr_ptr, uf_ptr, ub_ptr, u_ni_max, u_nd_max;
     int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0;
     int32_t ntickets = 0;
     int64_t bytes_pass = 0;             // stored factor bytes read by fwd + bwd

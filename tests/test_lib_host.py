@@ -93,7 +93,7 @@ def test_host_factor_exact_with_upper_levels(bid, n, leaf, block, precision):
     x -= x.mean()
     xo = ob.s1_pseudo_inverse_apply(s, b)
     assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
-    assert st["levels1"] >= 3 and st["dense_blocks"] >= 2
+    assert st["levels1"] >= 3 and st["dense_blocks"] >= 1   # some large clusters
 
 
 def test_host_factor_3d_exact():
@@ -111,7 +111,7 @@ def test_host_factor_3d_exact():
 
 
 def test_host_factor_truncation_error_tracks_eps(bid):
-    m, p = torso_square_2d(129), params_2d(0.1)
+    m, p = torso_square_2d(257), params_2d(0.1)
     hs = bid.HostSystem(m, p)
     s = ob.build_system(m, p)
     b = np.random.default_rng(3).normal(size=s.N)
@@ -119,7 +119,7 @@ def test_host_factor_truncation_error_tracks_eps(bid):
     x0 -= x0.mean()
     errs = []
     for eps in (1e-2, 1e-4, 1e-6):
-        x, st = hs.factor_solve(1, b, eps=eps, leaf=32, block=32)
+        x, st = hs.factor_solve(1, b, eps=eps, leaf=16, block=64)
         x -= x.mean()
         errs.append(np.abs(x - x0).max() / np.abs(x0).max())
         assert st["lowrank_blocks"] > 0
