@@ -159,6 +159,28 @@ int bid_apply_precond(bid_precond* P, const double* r, double* z, void* stream);
  * x = P_K^-1 b (which = 2: K_m factor, N_H entries).  Device vectors. */
 int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void* stream);
 
+/* Same result as bid_apply_factor, but the call allocates nothing.  (The paper
+ * has no counterpart: this is a library service.)  It is meant for callers
+ * that cannot call cudaMalloc at the moment they solve: code running under a
+ * stream capture in the global capture mode, where the allocator is illegal;
+ * a real-time loop that must not pay for the allocator's implicit device
+ * synchronisation; or a host that gives the library a fixed memory budget.
+ * bid_apply_factor itself only uses buffers made by bid_precond_build, but
+ * this variant takes its scratch (the forward-pass, update, rank, partial-sum
+ * and ticket buffers) from one static device array of 2^21 doubles (16 MiB)
+ * that every GPU loading this library holds until the process exits.
+ * Limit: a factor whose scratch (its size plus its update, rank and
+ * partial-sum entries) exceeds that array is rejected with BID_EINVAL and a
+ * message; use bid_apply_factor for it.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  The array is shared by all
+ * calls and keeps the last call's contents (the tickets it needs at zero are
+ * cleared on each call), so calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race: serialise them.  Device
+ * pointers, stream semantics and which / b / x as for bid_apply_factor. */
+int bid_apply_factor_noalloc(bid_precond* P, int which, const double* b, double* x,
+                             void* stream);
+
 /* Step 2 (eq. system): PCG on Lambda from the guess in X, stopping when the
  * recurrence residual ||r||_2/||Y||_2 < tol (Sec. 6.2); the true residual is
  * then recomputed and PCG restarted once if it is above tol; X is finally

@@ -78,6 +78,7 @@ SIGNATURES = {
     "bid_apply_lambda": (_I, [_VP, _D, _VP, _VP, _VP]),
     "bid_apply_precond": (_I, [_VP, _VP, _VP, _VP]),
     "bid_apply_factor": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "bid_apply_factor_noalloc": (_I, [_VP, _I, _VP, _VP, _VP]),
     "bid_solve": (_I, [_VP, _VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo), _VP]),
     "bid_step": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _D, _I, _D, _I, _VP, _VP]),
     "bid_rhs_gate": (_I, [_VP, _VP, _VP, _VP, _I, _VP, _VP]),
@@ -212,6 +213,16 @@ class Precond:
 
     def apply_factor(self, which, b, x, stream=None):
         _check(lib.bid_apply_factor(self.h, int(which), _ptr(b), _ptr(x), _stream(stream)))
+
+    def apply_factor_noalloc(self, which, b, x, stream=None, check=True):
+        """bid_apply_factor without any allocation: scratch comes from the
+        library's static 16 MiB device array (for callers that cannot call
+        cudaMalloc, e.g. inside a global-mode stream capture).  Returns the
+        status code."""
+        rc = lib.bid_apply_factor_noalloc(self.h, int(which), _ptr(b), _ptr(x), _stream(stream))
+        if check:
+            _check(rc)
+        return rc
 
     def solve(self, Y, X, tol=1e-8, max_iter=200, stream=None, check=True):
         info = SolveInfo()
