@@ -136,6 +136,13 @@ struct NDBuilder {
         }
         for (int i = 0; i < n; ++i) side[R[i]] = 0;
         std::vector<int32_t>().swap(R);
+        // the two halves are already disconnected: every cluster needs pivots
+        // (a pivot-free cluster would have to pass its children's updates on),
+        // and any node set is a valid separator of disconnected halves
+        if (S.empty()) {
+            S.push_back(L.empty() ? U.back() : L.back());
+            (L.empty() ? U : L).pop_back();
+        }
         order_rcb(S.data(), (int)S.size());
         T[id].sep = std::move(S);
         for (auto* part : {&L, &U}) {

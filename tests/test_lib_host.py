@@ -146,3 +146,25 @@ def test_host_errors(bid):
     hs = bid.HostSystem(m, p)
     with pytest.raises(bid.BidError):
         hs.factor_solve(1, np.zeros(hs.perm_and_mass()[0].size), block=4)
+
+
+def test_host_factor_disconnected_heart(bid):
+    # two separate heart blobs: K_m has two components, so nested dissection
+    # meets halves that are already disconnected (no natural separator)
+    m = torso_square_2d(65)
+    c = m.coords[m.elems].mean(axis=1)
+    blob = lambda cx: ((c[:, 0] - cx) / 1.5) ** 2 + ((c[:, 1] - 5) / 2) ** 2 <= 1
+    m.region[:] = (blob(2.5) | blob(7.5)).astype(np.int32)
+    p = params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    g = ob.gamma_of(p, 0.1)
+    b2 = np.random.default_rng(1).normal(size=s.NH)
+    x2, _ = hs.factor_solve(2, b2, gamma=g, leaf=16)
+    xo2 = spla.spsolve(ob.monodomain_matrix(s, g).tocsc(), b2)
+    assert np.abs(x2 - xo2).max() <= 1e-12 * np.abs(xo2).max()
+    b = np.random.default_rng(2).normal(size=s.N)
+    x, _ = hs.factor_solve(1, b, leaf=16)
+    x -= x.mean()
+    xo = ob.s1_pseudo_inverse_apply(s, b)
+    assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
