@@ -329,7 +329,9 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (rc == BID_OK) rc = dalloc(&P->t, NH);
     if (rc == BID_OK) rc = dalloc(&P->w, N);
     if (rc == BID_OK) rc = dalloc(&P->hs.ybuf, N);
-    if (rc == BID_OK) rc = dalloc(&P->hs.ubuf, std::max(h1.ubuf, hk.ubuf));
+    if (rc == BID_OK) rc = dalloc(&P->hs.xp, N);
+    if (rc == BID_OK) rc = dalloc(&P->hs.inb, std::max(h1.nslots, hk.nslots));
+    if (rc == BID_OK) rc = dalloc(&P->hs.vbuf, std::max(h1.vbuf, hk.vbuf));
     if (rc == BID_OK) rc = dalloc(&P->hs.tbuf, std::max(h1.tbuf, hk.tbuf));
     if (rc == BID_OK) rc = dalloc(&P->hs.pbuf, std::max(h1.pbuf, hk.pbuf));
     if (rc == BID_OK) rc = dalloc(&P->hs.tickets, std::max(h1.ntickets, hk.ntickets));
@@ -473,7 +475,7 @@ void bid_destroy_precond(bid_precond* P) {
     free_hfactor(&P->F1);
     free_hfactor(&P->FK);
     for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->hs.ybuf,
-                      P->hs.ubuf, P->hs.tbuf, P->hs.pbuf, P->partials})
+                      P->hs.xp, P->hs.inb, P->hs.vbuf, P->hs.tbuf, P->hs.pbuf, P->partials})
         cudaFree(p);
     cudaFree(P->hs.tickets);
     cudaFree(P->sc);

@@ -277,7 +277,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             return set_error(BID_EINVAL, "factor index space exceeds 2^31");
         F->bidx.resize(boff);
         F->inc.assign(ioff, -1);
+        F->uout.assign(uoff, -1);
         F->ubuf = uoff;
+        F->nslots = ioff;
         for (int s = 0; s < nt; ++s) {
             const HSnode& h = F->sn[s];
             for (int32_t j = 0; j < h.nb; ++j) F->bidx[h.bidx_off + j] = F->pidx[W[s].B[j]];
@@ -295,8 +297,10 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             const int c = ch[s][k];
             const HSnode& hc = F->sn[c];
             for (int32_t j = 0; j < hc.nb; ++j) {
-                int32_t f = front_index(s, W[c].B[j]);
-                F->inc[F->sn[s].inc_off + 2 * f + k] = hc.u_off + j;
+                const int32_t f = front_index(s, W[c].B[j]);
+                const int32_t slot = F->sn[s].inc_off + 2 * f + k;
+                F->inc[slot] = slot;
+                F->uout[hc.u_off + j] = slot;
             }
         }
     }
@@ -509,13 +513,15 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
     for (int s = 0; s < nt; ++s) bylev[F->sn[s].height].push_back(s);
     F->ff_ptr.assign(1, 0);
     F->fb_ptr.assign(1, 0);
+    F->vg_ptr.assign(1, 0);
     F->ulr_ptr.assign(1, 0);
     F->uf_ptr.assign(1, 0);
     F->ub_ptr.assign(1, 0);
     int64_t tbuf = 0, pbuf = 0;
     int32_t tickets = 0;
     // pack the items of one level into CTAs: <= FLAT_ITEMS items and
-    // <= STAGE_MAX staged values; items of one cluster are consecutive
+    // <= STAGE_MAX staged values; the splits of one row group (column) sit
+    // in the same CTA, `stride` threads apart
     auto pack = [&](const std::vector<int>& cl, bool fwd, std::vector<FCta>& ctas,
                     std::vector<FItem>& items, std::vector<FStage>& stages) {
         FCta c{};
@@ -529,25 +535,47 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         };
         for (int s : cl) {
             const HSnode& h = F->sn[s];
-            if (h.ni == 0 && h.nb == 0) continue;
-            const int stage = fwd ? h.ni : h.nd + vec;          // values staged per cluster
-            const int nitems = fwd ? (h.nd + vec - 1) / vec : h.ni;
-            for (int k = 0; k < nitems;) {
-                if (c.it1 - c.it0 == FLAT_ITEMS || c.total + stage > STAGE_MAX) flush();
-                // stage the cluster in this CTA
-                FStage g{s, c.total};
-                stages.push_back(g);
-                c.st1 = (int32_t)stages.size();
-                c.total += stage;
-                while (k < nitems && c.it1 - c.it0 < FLAT_ITEMS) {
-                    FItem it{};
-                    it.s = s;
-                    it.q = fwd ? k * vec : k;
-                    it.woff = g.woff;
-                    items.push_back(it);
-                    c.it1 = (int32_t)items.size();
-                    ++k;
+            if (h.ni == 0) continue;
+            const int stage = fwd ? h.ni : h.nd + vec;   // values staged per cluster
+            const int units = fwd ? (h.nd + vec - 1) / vec : h.ni;   // row groups / columns
+            // splits: forward over columns (<= FWD_COLS each), backward over rows
+            const int span = fwd ? h.ni : h.nd;
+            const int per = fwd ? FWD_COLS : BWD_ROWS;
+            const int P = std::min(8, std::max(1, (span + per - 1) / per));
+            int chunk = (span + P - 1) / P;
+            chunk = (chunk + vec - 1) / vec * vec;      // split bounds on vector boundaries
+            const int umax = FLAT_ITEMS / P;             // units per CTA block
+            bool staged = false;
+            int woff = 0;
+            for (int u0 = 0; u0 < units; u0 += umax) {
+                const int u1 = std::min(units, u0 + umax);
+                const int need = P * (u1 - u0);
+                if (c.it1 - c.it0 + need > FLAT_ITEMS || (!staged && c.total + stage > STAGE_MAX)) {
+                    flush();
+                    staged = false;
                 }
+                if (!staged) {
+                    FStage g{s, c.total};
+                    stages.push_back(g);
+                    c.st1 = (int32_t)stages.size();
+                    woff = c.total;
+                    c.total += stage;
+                    staged = true;
+                }
+                for (int p = 0; p < P; ++p)
+                    for (int u = u0; u < u1; ++u) {
+                        FItem it{};
+                        it.s = s;
+                        it.q = fwd ? u * vec : u;
+                        it.woff = woff;
+                        it.c0 = std::min(span, p * chunk);
+                        it.c1 = std::min(span, (p + 1) * chunk);
+                        it.nsplit = P;
+                        it.stride = u1 - u0;
+                        it.lead = p == 0;
+                        items.push_back(it);
+                    }
+                c.it1 = (int32_t)items.size();
             }
         }
         flush();
@@ -580,7 +608,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         for (int s : bylev[L]) {
             const HSnode& h = F->sn[s];
             if (!h.large) continue;
-            const int up_rows = UP_THREADS * vec;   // a thread owns vec consecutive rows
+            const int up_rows = UP_GROUPS * vec;   // a thread owns vec consecutive rows
             for (int a = 0; a < h.nd; a += up_rows) {
                 const int a1 = std::min(h.nd, a + up_rows);
                 const int cols = a1 <= h.ni ? a1 : h.ni;
@@ -604,16 +632,15 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                     F->uft.push_back(k);
                 }
             }
-            for (int g = h.lr_begin; g < h.lr_end; ++g)
-                for (int a = 0; a < F->lr[g].m; a += UP_THREADS) {
-                    HTask k{};
-                    k.s = -1 - g;
-                    k.a0 = a;
-                    k.a1 = std::min(F->lr[g].m, a + UP_THREADS);
-                    k.nparts = 1;
-                    k.part = k.ticket = -1;
-                    F->uft.push_back(k);
-                }
+            for (int g = h.lr_begin; g < h.lr_end; ++g) {   // one CTA per low-rank group
+                HTask k{};
+                k.s = -1 - g;
+                k.a0 = 0;
+                k.a1 = F->lr[g].m;
+                k.nparts = 1;
+                k.part = k.ticket = -1;
+                F->uft.push_back(k);
+            }
             for (int a = 0; a < h.ni; a += UP_BCOLS) {
                 HTask k{};
                 k.s = s;
@@ -621,6 +648,18 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                 k.a1 = std::min(h.ni, a + UP_BCOLS);
                 F->ubt.push_back(k);
             }
+        }
+        {
+            int64_t voff = 0;
+            for (int s : bylev[L]) {
+                HSnode& h = F->sn[s];
+                if (!h.large || h.ni == 0) continue;
+                h.v_off = (int32_t)voff;
+                voff += h.nd + 2 * vec;
+                F->vgl.push_back(s);
+            }
+            F->vbuf = std::max(F->vbuf, voff);
+            F->vg_ptr.push_back((int32_t)F->vgl.size());
         }
         F->u_ni_max.push_back(ni_max);
         F->u_nd_max.push_back(nd_max);

@@ -17,68 +17,62 @@ namespace bid {
 namespace {
 
 // x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
-// the same order, as the GPU launches (bottom subtrees, then upper levels).
+// the same order, as the GPU launches (permuted input, per-level flat items
+// with their splits, large-cluster tasks, parent input slots).
 void replay(const HFactorHost& F, const double* b, double shift, double* x) {
-    std::vector<double> y(F.n, 0.0), u(std::max<int64_t>(F.ubuf, 1), 0.0);
+    std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
-    auto gather = [&](const HSnode& s, int i) {
-        const int v = F.pidx[s.first + i];
-        double val = v == F.pin ? 0.0 : b[v] - shift;
-        const int c0 = F.inc[s.inc_off + 2 * i], c1 = F.inc[s.inc_off + 2 * i + 1];
-        if (c0 >= 0) val += u[c0];
-        if (c1 >= 0) val += u[c1];
-        return val;
+    for (int64_t i = 0; i < F.n; ++i) xp[i] = F.pidx[i] == F.pin ? 0.0 : b[F.pidx[i]] - shift;
+    auto incoming = [&](const HSnode& s, int f) {
+        const int o = s.inc_off + 2 * f;
+        return (F.inc[o] >= 0 ? inb[o] : 0.0) + (F.inc[o + 1] >= 0 ? inb[o + 1] : 0.0);
     };
+    auto gather = [&](const HSnode& s, int i) { return xp[s.first + i] + incoming(s, i); };
     auto finish = [&](const HSnode& s, int R, double acc) {
-        if (R < s.ni) {
-            y[s.first + R] = acc;
-        } else {
-            double in = 0.0;
-            const int c0 = F.inc[s.inc_off + 2 * R], c1 = F.inc[s.inc_off + 2 * R + 1];
-            if (c0 >= 0) in += u[c0];
-            if (c1 >= 0) in += u[c1];
-            u[s.u_off + R - s.ni] = in - acc;
-        }
+        if (R < s.ni) y[s.first + R] = acc;
+        else inb[F.uout[s.u_off + R - s.ni]] = incoming(s, R) - acc;
     };
     auto drow = [&](const HSnode& s, int q) { return q < s.ni ? q : F.drows[s.drow_off + q - s.ni]; };
     auto elem = [&](const HSnode& s, int q, int j) {
         return D[s.data_off + col_start(s.nd, j, F.vec) + q - j];
     };
-    // dense forward rows [a0,a1) over columns [b0,b1)
-    auto fwd_rows = [&](const HSnode& s, int a0, int a1, int b0, int b1, std::vector<double>& acc) {
-        for (int q = a0; q < a1; ++q) {
-            const int jend = q < s.ni ? std::min(b1, q + 1) : b1;
-            for (int j = b0; j < jend; ++j) acc[q - a0] += elem(s, q, j) * gather(s, j);
-        }
+    // forward partial of dense row q over columns [c0, c1)
+    auto fwd_part = [&](const HSnode& s, int q, int c0, int c1) {
+        const int jend = q < s.ni ? std::min(c1, q + 1) : c1;
+        double a = 0.0;
+        for (int j = c0; j < jend; ++j) a += elem(s, q, j) * gather(s, j);
+        return a;
     };
-    const int nul = (int)F.uf_ptr.size() - 1;
-    for (int lev = 0; lev < nul; ++lev) {
+    const int H = (int)F.uf_ptr.size() - 1;
+    for (int lev = 0; lev < H; ++lev) {
+        // flat items first (all reads of this level's inputs precede the writes
+        // into the parents' slots, as on the GPU where parents sit higher up)
+        std::vector<std::pair<int, double>> rows_out;   // not needed: parents are later levels
         for (int c = F.ff_ptr[lev]; c < F.ff_ptr[lev + 1]; ++c)
             for (int it = F.ffc[c].it0; it < F.ffc[c].it1; ++it) {
                 const FItem& f = F.ffi[it];
+                if (!f.lead) continue;
                 const HSnode& s = F.sn[f.s];
-                const int q1 = std::min(s.nd, f.q + F.vec);
-                std::vector<double> acc(q1 - f.q, 0.0);
-                fwd_rows(s, f.q, q1, 0, s.ni, acc);
-                for (int q = f.q; q < q1; ++q) finish(s, drow(s, q), acc[q - f.q]);
+                for (int e = 0; e < F.vec && f.q + e < s.nd; ++e) {
+                    double a = 0.0;
+                    for (int p = 0; p < f.nsplit; ++p) {
+                        const FItem& g = F.ffi[it + p * f.stride];
+                        a += fwd_part(s, f.q + e, g.c0, g.c1);
+                    }
+                    finish(s, drow(s, f.q + e), a);
+                }
             }
-        for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
-            const HLr& G = F.lr[g];
-            const HSnode& s = F.sn[G.s];
-            for (int l = 0; l < G.k; ++l) {
-                double a = 0.0;
-                for (int j = 0; j < s.ni; ++j) a += D[G.off_v + (int64_t)j * G.k + l] * gather(s, j);
-                t[G.t_off + l] = a;
-            }
-        }
-        // row chunks may be split over column chunks: sum the chunks in order
-        std::vector<std::pair<int, int>> done;
         for (int ti = F.uf_ptr[lev]; ti < F.uf_ptr[lev + 1]; ++ti) {
             const HTask& k = F.uft[ti];
             if (k.s < 0) {
                 const HLr& G = F.lr[-1 - k.s];
                 const HSnode& s = F.sn[G.s];
+                for (int l = 0; l < G.k; ++l) {
+                    double a = 0.0;
+                    for (int j = 0; j < s.ni; ++j) a += D[G.off_v + (int64_t)j * G.k + l] * gather(s, j);
+                    t[G.t_off + l] = a;
+                }
                 for (int i = k.a0; i < k.a1; ++i) {
                     double a = 0.0;
                     for (int l = 0; l < G.k; ++l) a += D[G.off_u + (int64_t)i * G.k + l] * t[G.t_off + l];
@@ -86,22 +80,22 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x) {
                 }
                 continue;
             }
-            if (k.b0 != 0) continue;   // the first chunk task finishes the whole row chunk
+            if (k.b0 != 0) continue;   // the first column chunk stands for the row chunk
             const HSnode& s = F.sn[k.s];
-            std::vector<double> acc(k.a1 - k.a0, 0.0);
-            for (int c = 0; c < k.nparts; ++c) {
-                std::vector<double> part(k.a1 - k.a0, 0.0);
-                const HTask& kc = F.uft[ti + c];
-                fwd_rows(s, kc.a0, kc.a1, kc.b0, kc.b1, part);
-                for (size_t i = 0; i < part.size(); ++i) acc[i] += part[i];
+            for (int q = k.a0; q < k.a1; ++q) {
+                double a = 0.0;
+                for (int c = 0; c < k.nparts; ++c) {
+                    const HTask& kc = F.uft[ti + c];
+                    a += fwd_part(s, q, kc.b0, kc.b1);
+                }
+                finish(s, drow(s, q), a);
             }
-            for (int q = k.a0; q < k.a1; ++q) finish(s, drow(s, q), acc[q - k.a0]);
         }
     }
     auto vrow = [&](const HSnode& s, int q) {
         return q < s.ni ? y[s.first + q] : -x[F.bidx[s.bidx_off + drow(s, q) - s.ni]];
     };
-    for (int lev = nul - 1; lev >= 0; --lev) {
+    for (int lev = H - 1; lev >= 0; --lev) {
         for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
             const HLr& G = F.lr[g];
             const HSnode& s = F.sn[G.s];
@@ -112,29 +106,33 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x) {
                 t[G.t_off + l] = a;
             }
         }
+        std::vector<std::pair<int32_t, double>> xs;   // outputs of this level, written after
         for (int ti = F.ub_ptr[lev]; ti < F.ub_ptr[lev + 1]; ++ti) {
             const HTask& k = F.ubt[ti];
             const HSnode& s = F.sn[k.s];
-            std::vector<double> vv(s.nd);
-            for (int q = 0; q < s.nd; ++q) vv[q] = vrow(s, q);
             for (int j = k.a0; j < k.a1; ++j) {
                 double a = 0.0;
-                for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vv[q];
+                for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
                 for (int g = s.lr_begin; g < s.lr_end; ++g) {
                     const HLr& G = F.lr[g];
                     for (int l = 0; l < G.k; ++l) a += D[G.off_v + (int64_t)j * G.k + l] * t[G.t_off + l];
                 }
-                x[F.pidx[s.first + j]] = a;
+                xs.push_back({F.pidx[s.first + j], a});
             }
         }
         for (int c = F.fb_ptr[lev]; c < F.fb_ptr[lev + 1]; ++c)
             for (int it = F.fbc[c].it0; it < F.fbc[c].it1; ++it) {
                 const FItem& f = F.fbi[it];
+                if (!f.lead) continue;
                 const HSnode& s = F.sn[f.s];
                 double a = 0.0;
-                for (int q = f.q; q < s.nd; ++q) a += elem(s, q, f.q) * vrow(s, q);
-                x[F.pidx[s.first + f.q]] = a;
+                for (int p = 0; p < f.nsplit; ++p) {
+                    const FItem& g = F.fbi[it + p * f.stride];
+                    for (int q = std::max(g.c0, f.q); q < g.c1; ++q) a += elem(s, q, f.q) * vrow(s, q);
+                }
+                xs.push_back({F.pidx[s.first + f.q], a});
             }
+        for (auto& pr : xs) x[pr.first] = pr.second;
     }
 }
 

@@ -1,21 +1,27 @@
 // Triangular solves with the hierarchical Cholesky factors: the P_1^-1 and
 // P_K^-1 applications of eq. prec2 (factor layout in internal.h / hfactor.cpp).
 //
-// Forward pass (leaves first), for each cluster s with gathered input
+// Forward pass (leaves first), for each cluster s with input
 //   w_s = b[I_s] - shift + children's update entries,
 // computes y_s = L_ss^-1 w_s (rows q < ni of M_s) and the update vector
-//   u_s = children's entries on B_s - (L_Bs L_ss^-1) w_s (boundary rows).
-// Backward pass (root first): x_s = (L_ss^-1)^T y_s - (L_Bs L_ss^-1)^T x_B.
+//   u_s = children's entries on B_s - (L_Bs L_ss^-1) w_s (boundary rows),
+// written straight into the parent's input slots.  Backward pass (root first):
+//   x_s = (L_ss^-1)^T y_s - (L_Bs L_ss^-1)^T x_B.
 //
 // Launches of one solve:
-//   per level, leaves first: k_flat_fwd (small clusters: thread per aligned
-//               row group, the CTA's cluster inputs staged in shared memory),
-//               k_lr_fwd (V^T w of the low-rank groups, if any) and k_up_fwd
-//               (large clusters: thread per row group over a column chunk;
-//               chunks of a row are combined in a fixed order by the last CTA);
-//   per level, root first: k_lr_bwd (U^T v), k_up_bwd (large clusters: warp
-//               per column, v staged in shared memory) and k_flat_bwd (small
-//               clusters: thread per column).
+//   k_permute     b (vector order) -> xp (elimination order), shifted, pin zeroed;
+//   per level, leaves first:
+//     k_flat_fwd  small clusters: a thread owns an aligned row group over a
+//                 split of the columns; splits are summed in a fixed order;
+//     k_up_fwd    large clusters: 64 row groups x 4 column splits per CTA over
+//                 64 columns; column chunks of a row are combined in a fixed
+//                 order by the last CTA (ticket); low-rank groups: one CTA each
+//                 (t = V^T w, then U t);
+//   per level, root first:
+//     k_bwd_prep  U^T v of the low-rank groups; staging of the large
+//                 clusters' v = [y_s; -x_B] in vbuf;
+//     k_up_bwd    large clusters: 4 warps per column over row quarters;
+//     k_flat_bwd  small clusters: a thread owns a column over a split of rows.
 // Factors are stored in FP64, FP32 or BF16; FP32/BF16 accumulate in FP32 (the
 // precision form), FP64 in FP64.  All reductions have a fixed order, so the
 // result is bitwise reproducible.
@@ -78,6 +84,8 @@ struct HView {
     const int32_t* __restrict__ bidx;
     const int32_t* __restrict__ inc;
     const int32_t* __restrict__ drows;
+    const int32_t* __restrict__ uout;
+    const int32_t* __restrict__ vgl;
     const HSnode* __restrict__ sn;
     const HLr* __restrict__ lr;
     const FCta* __restrict__ ffc;
@@ -90,29 +98,33 @@ struct HView {
     const HTask* __restrict__ ubt;
 };
 
-// gathered forward input entry i of cluster sn (ubuf holds finished children)
-__device__ __forceinline__ double gather_w(const HView& v, const HSnode& sn, int i,
-                                           const double* __restrict__ in, double shift,
-                                           const double* ubuf) {
-    const int vi = v.pidx[sn.first + i];
-    double val = (vi == v.pin) ? 0.0 : in[vi] - shift;
-    const int c0 = v.inc[sn.inc_off + 2 * i], c1 = v.inc[sn.inc_off + 2 * i + 1];
-    if (c0 >= 0) val += ubuf[c0];
-    if (c1 >= 0) val += ubuf[c1];
-    return val;
+// sum of the (up to two) children's contributions to frontal row f
+__device__ __forceinline__ double incoming(const HView& v, const HSnode& sn, int f,
+                                           const double* inb) {
+    const int o = sn.inc_off + 2 * f;
+    const int2 flags = *reinterpret_cast<const int2*>(v.inc + o);
+    const double2 val = *reinterpret_cast<const double2*>(inb + o);
+    double s = 0.0;
+    if (flags.x >= 0) s += val.x;
+    if (flags.y >= 0) s += val.y;
+    return s;
 }
 
-// store the forward result of M_s row R
+// forward input entry i of cluster sn
+__device__ __forceinline__ double gather_w(const HView& v, const HSnode& sn, int i,
+                                           const double* xp, const double* inb) {
+    return xp[sn.first + i] + incoming(v, sn, i, inb);
+}
+
+// store the forward result of M_s row R: y (pivot rows) or the update entry,
+// written into the parent's input slot
 __device__ __forceinline__ void finish_row(const HView& v, const HSnode& sn, int R, double acc,
-                                           double* ybuf, double* ubuf) {
+                                           double* ybuf, double* inb) {
     if (R < sn.ni) {
         ybuf[sn.first + R] = acc;
     } else {
-        double u = 0.0;
-        const int c0 = v.inc[sn.inc_off + 2 * R], c1 = v.inc[sn.inc_off + 2 * R + 1];
-        if (c0 >= 0) u += ubuf[c0];
-        if (c1 >= 0) u += ubuf[c1];
-        ubuf[sn.u_off + R - sn.ni] = u - acc;
+        const double u = incoming(v, sn, R, inb) - acc;
+        inb[v.uout[sn.u_off + R - sn.ni]] = u;
     }
 }
 
@@ -120,9 +132,25 @@ __device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q
     return q < sn.ni ? q : v.drows[sn.drow_off + q - sn.ni];
 }
 
+// backward input of dense row q of cluster sn
+__device__ __forceinline__ double vrow(const HView& v, const HSnode& sn, int q,
+                                       const double* ybuf, const double* out) {
+    return q < sn.ni ? ybuf[sn.first + q] : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
+}
+
+// xp[pos] = b[pidx[pos]] - shift, pinned entry 0
+__global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict__ pidx, int pin,
+                                                const double* __restrict__ b,
+                                                const double* shift_sum, double inv_n,
+                                                double* __restrict__ xp) {
+    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int vi = pidx[i];
+        xp[i] = vi == pin ? 0.0 : b[vi] - shift;
+    }
+}
+
 // ------------------------------------------------------------ small clusters
-// Stage the inputs of a flat CTA's clusters: entry f belongs to the last
-// FStage with woff <= f (binary search over the CTA's stage list).
 __device__ __forceinline__ int stage_owner(const int2* st, int nst, int f) {
     int lo = 0, hi = nst - 1;
     while (lo < hi) {
@@ -133,15 +161,12 @@ __device__ __forceinline__ int stage_owner(const int2* st, int nst, int f) {
     return lo;
 }
 
-// Forward: thread = aligned row group q .. q+VEC-1 of a small cluster over all
-// its columns (four columns per step, 16-byte vector loads).
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ data, int cta0,
-                                                 const double* __restrict__ in,
-                                                 const double* shift_sum, double inv_n,
-                                                 double* ybuf, double* ubuf) {
+                                                 const double* xp, double* ybuf, double* inb) {
     constexpr int VEC = VecOf<T>::N;
     __shared__ A w[STAGE_MAX];
+    __shared__ A red[HT][VEC];
     __shared__ int2 st[FLAT_ITEMS];
     const FCta c = v.ffc[cta0 + blockIdx.x];
     const int nst = c.st1 - c.st0;
@@ -150,57 +175,67 @@ __global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ 
         st[k] = make_int2(g.s, g.woff);
     }
     __syncthreads();
-    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
     for (int f = threadIdx.x; f < c.total; f += HT) {
         const int2 g = st[stage_owner(st, nst, f)];
         const HSnode sn = v.sn[g.x];
-        w[f] = (A)gather_w(v, sn, f - g.y, in, shift, ubuf);
+        w[f] = (A)gather_w(v, sn, f - g.y, xp, inb);
     }
     __syncthreads();
     const int it = c.it0 + threadIdx.x;
-    if (it >= c.it1) return;
-    const FItem item = v.ffi[it];
-    const HSnode sn = v.sn[item.s];
-    const int q0 = item.q;
-    const A* ws = w + item.woff;
-    const T* col = data + sn.data_off;
-    const int jend = (q0 + VEC - 1 < sn.ni) ? q0 + VEC : sn.ni;
+    FItem item;
+    item.lead = 0;
     A acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0;
-    for (int j0 = 0; j0 < jend; j0 += 4) {
-        A val[4][VEC];
+    HSnode sn;
+    if (it < c.it1) {
+        item = v.ffi[it];
+        sn = v.sn[item.s];
+        const int q0 = item.q;
+        const A* ws = w + item.woff;
+        const T* col = data + sn.data_off;
+        const int jend = (q0 + VEC - 1 < sn.ni) ? min(item.c1, q0 + VEC) : item.c1;
+        for (int j0 = item.c0; j0 < jend; j0 += 4) {
+            A val[4][VEC];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int j = j0 + u;
-            if (j < jend) {
-                ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
-            } else {
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                if (j < jend) {
+                    ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
+                } else {
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) val[u][e] = 0;
+                    for (int e = 0; e < VEC; ++e) val[u][e] = 0;
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int j = j0 + u;
-            const A wj = j < jend ? ws[j] : (A)0;
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u;
+                const A wj = j < jend ? ws[j] : (A)0;
 #pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                if (q0 + e >= j) acc[e] += val[u][e] * wj;
+                for (int e = 0; e < VEC; ++e)
+                    if (q0 + e >= j) acc[e] += val[u][e] * wj;
+            }
         }
     }
 #pragma unroll
+    for (int e = 0; e < VEC; ++e) red[threadIdx.x][e] = acc[e];
+    __syncthreads();
+    if (it >= c.it1 || !item.lead) return;
+    for (int p = 1; p < item.nsplit; ++p)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] += red[threadIdx.x + p * item.stride][e];
+#pragma unroll
     for (int e = 0; e < VEC; ++e)
-        if (q0 + e < sn.nd) finish_row(v, sn, dense_row(v, sn, q0 + e), (double)acc[e], ybuf, ubuf);
+        if (item.q + e < sn.nd)
+            finish_row(v, sn, dense_row(v, sn, item.q + e), (double)acc[e], ybuf, inb);
 }
 
-// Backward: thread = column j of a small cluster: x_j = sum_{q >= j} M[q][j] v[q]
-// over the packed column (aligned vectors, v staged in shared memory).
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_flat_bwd(HView v, const T* __restrict__ data, int cta0,
                                                  const double* __restrict__ ybuf, double* out) {
     constexpr int VEC = VecOf<T>::N;
     __shared__ A vs[STAGE_MAX];
+    __shared__ A red[HT];
     __shared__ int2 st[FLAT_ITEMS];
     const FCta c = v.fbc[cta0 + blockIdx.x];
     const int nst = c.st1 - c.st0;
@@ -213,108 +248,116 @@ __global__ void __launch_bounds__(HT) k_flat_bwd(HView v, const T* __restrict__ 
         const int2 g = st[stage_owner(st, nst, f)];
         const HSnode sn = v.sn[g.x];
         const int q = f - g.y;
-        double x = 0.0;
-        if (q < sn.nd)
-            x = q < sn.ni ? ybuf[sn.first + q]
-                          : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
-        vs[f] = (A)x;
+        vs[f] = (A)(q < sn.nd ? vrow(v, sn, q, ybuf, out) : 0.0);
     }
     __syncthreads();
     const int it = c.it0 + threadIdx.x;
-    if (it >= c.it1) return;
-    const FItem item = v.fbi[it];
-    const HSnode sn = v.sn[item.s];
-    const int j = item.q;
-    const A* vv = vs + item.woff;
-    const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
+    FItem item;
+    item.lead = 0;
     A acc = 0;
-    int q0 = j & ~(VEC - 1);
-    for (; q0 + 3 * VEC < sn.nd; q0 += 4 * VEC) {
-        A val[4][VEC];
+    HSnode sn;
+    if (it < c.it1) {
+        item = v.fbi[it];
+        sn = v.sn[item.s];
+        const int j = item.q;
+        const A* vv = vs + item.woff;
+        const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
+        const int qbeg = max(item.c0, j & ~(VEC - 1));   // both multiples of VEC
+        const int qend = item.c1;
+        int q0 = qbeg;
+        for (; q0 + 3 * VEC < qend; q0 += 4 * VEC) {
+            A val[4][VEC];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * VEC, val[u]);
+            for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * VEC, val[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int e = 0; e < VEC; ++e)
-                if (q0 + u * VEC + e >= j) acc += val[u][e] * vv[q0 + u * VEC + e];
-    }
-    for (; q0 < sn.nd; q0 += VEC) {
-        A val[VEC];
-        ld16(cj + q0, val);
+                for (int e = 0; e < VEC; ++e) {
+                    const int q = q0 + u * VEC + e;
+                    if (q >= j && q < qend) acc += val[u][e] * vv[q];
+                }
+        }
+        for (; q0 < qend; q0 += VEC) {
+            A val[VEC];
+            ld16(cj + q0, val);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e)
-            if (q0 + e >= j && q0 + e < sn.nd) acc += val[e] * vv[q0 + e];
-    }
-    out[v.pidx[sn.first + j]] = (double)acc;
-}
-
-// ------------------------------------------------------------ upper levels
-// t_g = V_g^T w_s for every low-rank group g of the level (one CTA per group)
-template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_lr_fwd(HView v, const T* __restrict__ data, int g0,
-                                               const double* __restrict__ in,
-                                               const double* shift_sum, double inv_n,
-                                               const double* ubuf, double* tbuf) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const HLr g = v.lr[g0 + blockIdx.x];
-    const HSnode sn = v.sn[g.s];
-    A* w = reinterpret_cast<A*>(smem);
-    A* red = w + ((sn.ni + 1) & ~1);
-    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
-    for (int i = threadIdx.x; i < sn.ni; i += HT) w[i] = (A)gather_w(v, sn, i, in, shift, ubuf);
-    __syncthreads();
-    const int kp = g.k <= 32 ? 32 : 64, ng = HT / kp;
-    const int l = threadIdx.x % kp, grp = threadIdx.x / kp;
-    A acc = 0;
-    if (l < g.k) {
-        const T* V = data + g.off_v;
-        for (int j = grp; j < sn.ni; j += ng) acc += (A)ldv(V + (int64_t)j * g.k + l) * w[j];
+            for (int e = 0; e < VEC; ++e) {
+                const int q = q0 + e;
+                if (q >= j && q < qend) acc += val[e] * vv[q];
+            }
+        }
     }
     red[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x < g.k) {
-        A s = 0;
-        for (int q = 0; q < ng; ++q) s += red[q * kp + threadIdx.x];
-        tbuf[g.t_off + threadIdx.x] = (double)s;
-    }
+    if (it >= c.it1 || !item.lead) return;
+    for (int p = 1; p < item.nsplit; ++p) acc += red[threadIdx.x + p * item.stride];
+    out[v.pidx[sn.first + item.q]] = (double)acc;
 }
 
+// ------------------------------------------------------------ large clusters
+// Forward.  Dense task: rows [a0, a1) (64 groups of VEC rows) x columns
+// [b0, b1) (4 splits of 16); the 4 splits of a row group are summed in
+// order; split column chunks of a row chunk are combined by the last CTA.
+// Low-rank task: one CTA per group: t = V^T w_s (all ni columns), then
+// u = incoming - U t for the group's rows.
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ data, int task0,
-                                               const double* __restrict__ in,
-                                               const double* shift_sum, double inv_n,
-                                               double* ybuf, double* ubuf, const double* tbuf,
-                                               double* pbuf, unsigned int* tickets) {
+                                               const double* xp, double* ybuf, double* inb,
+                                               double* tbuf, double* pbuf,
+                                               unsigned int* tickets) {
     constexpr int VEC = VecOf<T>::N;
-    __shared__ A w[UP_COLS + 4];
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ A red[HT][VEC];
     __shared__ bool last;
     const HTask t = v.uft[task0 + blockIdx.x];
     const int tid = threadIdx.x;
-    if (t.s < 0) {   // rows of a low-rank group: u = inc - U t (thread per row)
+    if (t.s < 0) {
         const HLr g = v.lr[-1 - t.s];
         const HSnode sn = v.sn[g.s];
+        A* w = reinterpret_cast<A*>(smem);
+        A* tl = w + ((sn.ni + 1) & ~1);
+        for (int i = tid; i < sn.ni; i += HT) w[i] = (A)gather_w(v, sn, i, xp, inb);
+        __syncthreads();
+        const int kp = g.k <= 32 ? 32 : 64, ng = HT / kp;
+        const int l = tid % kp, grp = tid / kp;
+        A a = 0;
+        if (l < g.k) {
+            const T* V = data + g.off_v;
+            for (int j = grp; j < sn.ni; j += ng) a += (A)ldv(V + (int64_t)j * g.k + l) * w[j];
+        }
+        red[tid][0] = a;
+        __syncthreads();
+        if (tid < g.k) {
+            A s = 0;
+            for (int q = 0; q < ng; ++q) s += red[q * kp + tid][0];
+            tl[tid] = s;
+            tbuf[g.t_off + tid] = (double)s;
+        }
+        __syncthreads();
         const int i = t.a0 + tid;
         if (i < t.a1) {
             const T* U = data + g.off_u + (int64_t)i * g.k;
             A acc = 0;
-            for (int l = 0; l < g.k; ++l) acc += (A)ldv(U + l) * (A)tbuf[g.t_off + l];
-            finish_row(v, sn, g.row0 + i, (double)acc, ybuf, ubuf);
+            for (int q = 0; q < g.k; ++q) acc += (A)ldv(U + q) * tl[q];
+            finish_row(v, sn, g.row0 + i, (double)acc, ybuf, inb);
         }
         return;
     }
     const HSnode sn = v.sn[t.s];
-    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
-    for (int j = t.b0 + tid; j < t.b1; j += HT) w[j - t.b0] = (A)gather_w(v, sn, j, in, shift, ubuf);
+    A* w = reinterpret_cast<A*>(smem);
+    for (int j = t.b0 + tid; j < t.b1; j += HT) w[j - t.b0] = (A)gather_w(v, sn, j, xp, inb);
     __syncthreads();
-    const int q0 = t.a0 + VEC * tid;   // this thread's aligned row group
+    const int p = tid / UP_GROUPS, gi = tid % UP_GROUPS;
+    const int q0 = t.a0 + VEC * gi;
     A acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0;
     if (q0 < t.a1) {
         const T* col = data + sn.data_off;
-        const int jend = (q0 + VEC - 1 < sn.ni) ? min(t.b1, q0 + VEC) : t.b1;
-        for (int j0 = t.b0; j0 < jend; j0 += 4) {
+        const int c0 = t.b0 + p * (UP_COLS / UP_SPLIT);
+        const int c1 = min(t.b1, c0 + UP_COLS / UP_SPLIT);
+        const int jend = (q0 + VEC - 1 < sn.ni) ? min(c1, q0 + VEC) : c1;
+        for (int j0 = c0; j0 < jend; j0 += 4) {
             A val[4][VEC];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -336,115 +379,145 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
             }
         }
     }
-    if (t.nparts == 1) {
 #pragma unroll
-        for (int e = 0; e < VEC; ++e)
-            if (q0 + e < t.a1) finish_row(v, sn, dense_row(v, sn, q0 + e), (double)acc[e], ybuf, ubuf);
+    for (int e = 0; e < VEC; ++e) red[tid][e] = acc[e];
+    __syncthreads();
+    if (p == 0) {
+        for (int s = 1; s < UP_SPLIT; ++s)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[e] += red[tid + s * UP_GROUPS][e];
+    }
+    if (t.nparts == 1) {
+        if (p == 0)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (q0 + e < t.a1)
+                    finish_row(v, sn, dense_row(v, sn, q0 + e), (double)acc[e], ybuf, inb);
         return;
     }
     const int rows = t.a1 - t.a0;
     const int c = t.b0 / UP_COLS;
+    if (p == 0)
 #pragma unroll
-    for (int e = 0; e < VEC; ++e)
-        if (q0 + e < t.a1) pbuf[t.part + (int64_t)c * rows + (q0 + e - t.a0)] = (double)acc[e];
+        for (int e = 0; e < VEC; ++e)
+            if (q0 + e < t.a1) pbuf[t.part + (int64_t)c * rows + (q0 + e - t.a0)] = (double)acc[e];
     __threadfence();
     __syncthreads();
     if (tid == 0) last = atomicAdd(&tickets[t.ticket], 1u) == (unsigned)(t.nparts - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
+    if (p == 0) {
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-        const int q = q0 + e;
-        if (q < t.a1) {
-            double s = 0.0;
-            for (int p = 0; p < t.nparts; ++p) s += __ldcg(&pbuf[t.part + (int64_t)p * rows + (q - t.a0)]);
-            finish_row(v, sn, dense_row(v, sn, q), s, ybuf, ubuf);
+        for (int e = 0; e < VEC; ++e) {
+            const int q = q0 + e;
+            if (q < t.a1) {
+                double s = 0.0;
+                for (int k = 0; k < t.nparts; ++k) s += __ldcg(&pbuf[t.part + (int64_t)k * rows + (q - t.a0)]);
+                finish_row(v, sn, dense_row(v, sn, q), s, ybuf, inb);
+            }
         }
     }
     if (tid == 0) tickets[t.ticket] = 0u;
 }
 
-// t_g = U_g^T v_g with v = -x on the group's boundary rows (one CTA per group)
+// Backward preparation of one level.  CTAs [0, ng): t_g = U_g^T v_g for the
+// low-rank groups; CTAs [ng, ng + nv): staging v = [y_s; -x_B] of a large
+// cluster into vbuf.
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_lr_bwd(HView v, const T* __restrict__ data, int g0,
-                                               const double* out, double* tbuf) {
+__global__ void __launch_bounds__(HT) k_bwd_prep(HView v, const T* __restrict__ data, int g0,
+                                                 int ng, int vg0, const double* __restrict__ ybuf,
+                                                 const double* out, double* tbuf, double* vbuf) {
     __shared__ A vv[LR_ROWS];
     __shared__ A red[HT];
+    if ((int)blockIdx.x >= ng) {
+        const HSnode sn = v.sn[v.vgl[vg0 + blockIdx.x - ng]];
+        for (int q = threadIdx.x; q < sn.nd + 2 * VecOf<T>::N; q += HT)
+            vbuf[sn.v_off + q] = q < sn.nd ? vrow(v, sn, q, ybuf, out) : 0.0;
+        return;
+    }
     const HLr g = v.lr[g0 + blockIdx.x];
     const HSnode sn = v.sn[g.s];
     for (int i = threadIdx.x; i < g.m; i += HT)
         vv[i] = (A)(-out[v.bidx[sn.bidx_off + g.row0 + i - sn.ni]]);
     __syncthreads();
-    const int kp = g.k <= 32 ? 32 : 64, ng = HT / kp;
+    const int kp = g.k <= 32 ? 32 : 64, nq = HT / kp;
     const int l = threadIdx.x % kp, grp = threadIdx.x / kp;
     A acc = 0;
     if (l < g.k) {
         const T* U = data + g.off_u;
-        for (int i = grp; i < g.m; i += ng) acc += (A)ldv(U + (int64_t)i * g.k + l) * vv[i];
+        for (int i = grp; i < g.m; i += nq) acc += (A)ldv(U + (int64_t)i * g.k + l) * vv[i];
     }
     red[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < g.k) {
         A s = 0;
-        for (int q = 0; q < ng; ++q) s += red[q * kp + threadIdx.x];
+        for (int q = 0; q < nq; ++q) s += red[q * kp + threadIdx.x];
         tbuf[g.t_off + threadIdx.x] = (double)s;
     }
 }
 
+// Backward, large clusters: CTA = UP_BCOLS columns, 4 warps per column, warp w
+// of a column covers a quarter of the column's rows (aligned vectors, v from
+// vbuf); the 4 partials are summed in order, plus the low-rank terms.
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ data, int task0,
-                                               const double* __restrict__ ybuf,
-                                               const double* tbuf, double* out) {
+                                               const double* vbuf, const double* tbuf,
+                                               double* out) {
     constexpr int VEC = VecOf<T>::N;
-    extern __shared__ __align__(16) unsigned char smem[];
-    A* vv = reinterpret_cast<A*>(smem);
+    __shared__ A red[NW];
     const HTask t = v.ubt[task0 + blockIdx.x];
     const HSnode sn = v.sn[t.s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < sn.nd + VEC; q += HT) {
-        double x = 0.0;
-        if (q < sn.nd)
-            x = q < sn.ni ? ybuf[sn.first + q]
-                          : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
-        vv[q] = (A)x;
-    }
-    __syncthreads();
-    const T* col = data + sn.data_off;
-    const int j = t.a0 + warp;   // one column per warp
-    if (j >= t.a1) return;
-    const T* cj = col + col_start(sn.nd, j, VEC) - j;
+    const int j = t.a0 + warp / 4, part = warp % 4;
     A acc = 0;
-    const int qa = j & ~(VEC - 1);
-    int q0 = qa + VEC * lane;
-    for (; q0 + 3 * 32 * VEC < sn.nd; q0 += 4 * 32 * VEC) {
-        A val[4][VEC];
+    if (j < t.a1) {
+        const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
+        const double* vv = vbuf + sn.v_off;
+        const int qa = j & ~(VEC - 1);
+        int rs = (sn.nd - qa + 3) / 4;
+        rs = (rs + VEC - 1) / VEC * VEC;
+        const int r0 = qa + part * rs, r1 = min(sn.nd, r0 + rs);
+        int q0 = r0 + VEC * lane;
+        for (; q0 + 3 * 32 * VEC < r1; q0 += 4 * 32 * VEC) {
+            A val[4][VEC];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * 32 * VEC, val[u]);
+            for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * 32 * VEC, val[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int q = q0 + u * 32 * VEC + e;
+                    if (q >= j && q < r1) acc += val[u][e] * (A)vv[q];
+                }
+        }
+        for (; q0 < r1; q0 += 32 * VEC) {
+            A val[VEC];
+            ld16(cj + q0, val);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                const int q = q0 + u * 32 * VEC + e;
-                if (q >= j) acc += val[u][e] * vv[q];
+                const int q = q0 + e;
+                if (q >= j && q < r1) acc += val[e] * (A)vv[q];
+            }
+        }
+        if (part == 0)
+            for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
+                const HLr G = v.lr[g];
+                const T* V = data + G.off_v + (int64_t)j * G.k;
+                for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)tbuf[G.t_off + l];
             }
     }
-    for (; q0 < sn.nd; q0 += 32 * VEC) {
-        A val[VEC];
-        ld16(cj + q0, val);
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            const int q = q0 + e;
-            if (q >= j && q < sn.nd) acc += val[e] * vv[q];
+    acc = wsum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x < UP_BCOLS) {
+        const int jj = t.a0 + threadIdx.x;
+        if (jj < t.a1) {
+            const A s = red[4 * threadIdx.x] + red[4 * threadIdx.x + 1] + red[4 * threadIdx.x + 2] +
+                        red[4 * threadIdx.x + 3];
+            out[v.pidx[sn.first + jj]] = (double)s;
         }
     }
-    for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
-        const HLr G = v.lr[g];
-        const T* V = data + G.off_v + (int64_t)j * G.k;
-        for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)tbuf[G.t_off + l];
-    }
-    acc = wsum(acc);
-    if (lane == 0) out[v.pidx[sn.first + j]] = (double)acc;
 }
 
 HView view_of(const HFactorDev& F) {
@@ -454,6 +527,8 @@ HView view_of(const HFactorDev& F) {
     v.bidx = F.bidx;
     v.inc = F.inc;
     v.drows = F.drows;
+    v.uout = F.uout;
+    v.vgl = F.vgl;
     v.sn = F.sn;
     v.lr = F.lr;
     v.ffc = F.ffc;
@@ -472,39 +547,40 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const double* sh
         double inv_n, const HScratch& S, double* out) {
     const HView v = view_of(F);
     const T* data = reinterpret_cast<const T*>(F.data);
-    int launches = 0;
+    int launches = 1;
+    {
+        int64_t g = (F.n + HT - 1) / HT;
+        if (g > (int64_t)L.sms * 8) g = (int64_t)L.sms * 8;
+        k_permute<<<(unsigned)g, HT, 0, L.st>>>((int)F.n, F.pidx, F.pin, in, shift_sum, inv_n, S.xp);
+    }
     const int H = (int)F.uf_ptr.size() - 1;
     for (int lev = 0; lev < H; ++lev) {
         const int nf = F.ff_ptr[lev + 1] - F.ff_ptr[lev];
         if (nf > 0) {
-            k_flat_fwd<T, A><<<nf, HT, 0, L.st>>>(v, data, F.ff_ptr[lev], in, shift_sum, inv_n,
-                                                  S.ybuf, S.ubuf);
-            ++launches;
-        }
-        const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
-        if (ng > 0) {
-            const size_t sm = sizeof(A) * (((F.u_ni_max[lev] + 1) & ~1) + HT);
-            k_lr_fwd<T, A><<<ng, HT, sm, L.st>>>(v, data, F.ulr_ptr[lev], in, shift_sum, inv_n,
-                                                 S.ubuf, S.tbuf);
+            k_flat_fwd<T, A><<<nf, HT, 0, L.st>>>(v, data, F.ff_ptr[lev], S.xp, S.ybuf, S.inb);
             ++launches;
         }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
         if (nt > 0) {
-            k_up_fwd<T, A><<<nt, HT, 0, L.st>>>(v, data, F.uf_ptr[lev], in, shift_sum, inv_n,
-                                                S.ybuf, S.ubuf, S.tbuf, S.pbuf, S.tickets);
+            const int has_lr = F.ulr_ptr[lev + 1] > F.ulr_ptr[lev];
+            const size_t sm = sizeof(A) * (has_lr ? (((F.u_ni_max[lev] + 1) & ~1) + LR_KMAX + 2)
+                                                  : (size_t)UP_COLS);
+            k_up_fwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.uf_ptr[lev], S.xp, S.ybuf, S.inb,
+                                                 S.tbuf, S.pbuf, S.tickets);
             ++launches;
         }
     }
     for (int lev = H - 1; lev >= 0; --lev) {
         const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
-        if (ng > 0) {
-            k_lr_bwd<T, A><<<ng, HT, 0, L.st>>>(v, data, F.ulr_ptr[lev], out, S.tbuf);
+        const int nv = F.vg_ptr[lev + 1] - F.vg_ptr[lev];
+        if (ng + nv > 0) {
+            k_bwd_prep<T, A><<<ng + nv, HT, 0, L.st>>>(v, data, F.ulr_ptr[lev], ng, F.vg_ptr[lev],
+                                                       S.ybuf, out, S.tbuf, S.vbuf);
             ++launches;
         }
         const int nt = F.ub_ptr[lev + 1] - F.ub_ptr[lev];
         if (nt > 0) {
-            const size_t sm = sizeof(A) * (F.u_nd_max[lev] + 16);
-            k_up_bwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.ub_ptr[lev], S.ybuf, S.tbuf, out);
+            k_up_bwd<T, A><<<nt, HT, 0, L.st>>>(v, data, F.ub_ptr[lev], S.vbuf, S.tbuf, out);
             ++launches;
         }
         const int nf = F.fb_ptr[lev + 1] - F.fb_ptr[lev];
@@ -530,8 +606,7 @@ uint16_t to_bf16(float f) {   // round to nearest even
 template <typename T, typename A>
 int prepare_one() {
     const int lim = 200 * 1024;
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_lr_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_up_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_up_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     return BID_OK;
 }
 
@@ -565,10 +640,9 @@ static int upload_vec(const std::vector<V>& h, V** d) {
 
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     const int esz_acc = precision == BID_FP64 ? 8 : 4;
-    for (size_t L = 0; L < h.u_nd_max.size(); ++L)
-        if ((int64_t)(h.u_nd_max[L] + 16) * esz_acc > 200 * 1024 ||
-            (int64_t)(h.u_ni_max[L] + 2 + HT) * esz_acc > 200 * 1024)
-            return set_error(BID_EINVAL, "cluster too large for shared memory (nd=%d)", h.u_nd_max[L]);
+    for (size_t L = 0; L < h.u_ni_max.size(); ++L)
+        if ((int64_t)(h.u_ni_max[L] + LR_KMAX + 4) * esz_acc > 200 * 1024)
+            return set_error(BID_EINVAL, "cluster too large for shared memory (ni=%d)", h.u_ni_max[L]);
     for (const HLr& g : h.lr)
         if (g.k > LR_KMAX || g.m > LR_ROWS) return set_error(BID_EINVAL, "low-rank group out of range");
     const int want_vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
@@ -576,11 +650,12 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     d->n = h.n;
     d->pin = h.pin;
     d->precision = precision;
-
     BID_TRY(upload_vec(h.pidx, &d->pidx));
     BID_TRY(upload_vec(h.bidx, &d->bidx));
     BID_TRY(upload_vec(h.inc, &d->inc));
     BID_TRY(upload_vec(h.drows, &d->drows));
+    BID_TRY(upload_vec(h.uout, &d->uout));
+    BID_TRY(upload_vec(h.vgl, &d->vgl));
     BID_TRY(upload_vec(h.sn, &d->sn));
     BID_TRY(upload_vec(h.lr, &d->lr));
     BID_TRY(upload_vec(h.ffc, &d->ffc));
@@ -589,18 +664,21 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.fbi, &d->fbi));
     BID_TRY(upload_vec(h.ffs, &d->ffs));
     BID_TRY(upload_vec(h.fbs, &d->fbs));
-    d->ff_ptr = h.ff_ptr;
-    d->fb_ptr = h.fb_ptr;
     BID_TRY(upload_vec(h.uft, &d->uft));
     BID_TRY(upload_vec(h.ubt, &d->ubt));
+    d->ff_ptr = h.ff_ptr;
+    d->fb_ptr = h.fb_ptr;
     d->ulr_ptr = h.ulr_ptr;
     d->uf_ptr = h.uf_ptr;
     d->ub_ptr = h.ub_ptr;
+    d->vg_ptr = h.vg_ptr;
     d->u_ni_max = h.u_ni_max;
     d->u_nd_max = h.u_nd_max;
     d->ubuf_entries = h.ubuf;
     d->tbuf_entries = h.tbuf;
     d->pbuf_entries = h.pbuf;
+    d->nslots = h.nslots;
+    d->vbuf_entries = h.vbuf;
     d->ntickets = h.ntickets;
     d->data_elems = (int64_t)h.data.size();
     const size_t n = h.data.size();
@@ -625,8 +703,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 void free_hfactor(HFactorDev* d) {
-    void* ptrs[] = {d->pidx, d->bidx, d->inc, d->drows, d->sn, d->lr, d->ffc, d->fbc, d->ffi,
-                    d->fbi, d->ffs, d->fbs, d->uft, d->ubt, d->data};
+    void* ptrs[] = {d->pidx, d->bidx, d->inc, d->drows, d->uout, d->vgl, d->sn, d->lr, d->ffc,
+                    d->fbc, d->ffi, d->fbi, d->ffs, d->fbs, d->uft, d->ubt, d->data};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

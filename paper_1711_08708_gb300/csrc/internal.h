@@ -80,13 +80,16 @@ int assemble_host(const bid_mesh* mesh, const bid_params* p, AssembledHost* out)
 struct HSnode {
     int32_t first, ni, nb, nd;
     int32_t bidx_off;   // B_s entries (vector indices) at bidx[bidx_off ...]
-    int32_t u_off;      // update vector of s in the ubuf scratch
-    int32_t inc_off;    // 2 ints per frontal row: children's update entries or -1
+    int32_t u_off;      // uout[u_off + j]: slot of update row j in the parent's inputs
+    int32_t inc_off;    // 2 input slots per frontal row at inb[inc_off + 2f + k]
+                        // (child k's contribution), valid iff inc[...] >= 0
     int32_t height;
     int64_t data_off;   // packed dense columns
     int32_t drow_off;   // M_s row index of dense boundary row q (q >= ni) at drows[drow_off + q - ni]
     int32_t lr_begin, lr_end;
     int32_t large;      // 1: chunked upper-level tasks (may hold low-rank groups); 0: flat items
+    int32_t v_off;      // large clusters: backward input staged at vbuf[v_off ...]
+    int32_t pad2;
 };
 // Number of stored (nonzero) entries of columns 0 .. j-1 of the dense part.
 BID_HD int64_t col_offset(int64_t nd, int64_t j) { return j * nd - j * (j - 1) / 2; }
@@ -110,13 +113,16 @@ struct HLr {
     int32_t t_off, pad;         // slot of V^T w (forward) / U^T v (backward) in tbuf
 };
 // Flat work of the small clusters of one level: one thread per item.
-//  forward item:  rows q .. q+vec-1 (q a multiple of vec) of cluster s over all
-//                 its columns, input w_s staged at woff in shared memory;
-//  backward item: column q of cluster s, v_s = [y_s; -x_B] staged at woff.
-// A CTA holds up to FLAT_ITEMS items and stages the inputs of its clusters
-// (FStage entries sorted by woff, `total` values in all).
+//  forward item:  rows q .. q+vec-1 (q a multiple of vec) of cluster s over its
+//                 columns [c0, c1); input w_s staged at woff in shared memory;
+//  backward item: column q of cluster s over the rows [c0, c1) of the column;
+//                 v_s = [y_s; -x_B] staged at woff.
+// A row group (or column) is split over nsplit items placed stride threads
+// apart in the same CTA; the split with c0 == lowest (the first) sums the
+// partial results in split order.  A CTA holds up to FLAT_ITEMS items and
+// stages the inputs of its clusters (FStage entries sorted by woff).
 struct FItem {
-    int32_t s, q, woff, pad;
+    int32_t s, q, woff, c0, c1, nsplit, stride, lead;
 };
 struct FStage {
     int32_t s, woff;
@@ -142,7 +148,7 @@ struct HFactorHost {
     int32_t height = 0;
     std::vector<int32_t> pidx;         // elimination position -> vector index
     std::vector<HSnode> sn;
-    std::vector<int32_t> bidx, inc, drows;
+    std::vector<int32_t> bidx, inc, drows, uout;
     std::vector<HLr> lr;
     std::vector<double> data;
     // small clusters: flat items per level
@@ -152,10 +158,11 @@ struct HFactorHost {
     std::vector<int32_t> ff_ptr, fb_ptr;       // level -> CTA ranges
     // large clusters, per level
     std::vector<int32_t> ulr_ptr;              // level -> low-rank groups [ptr, ptr+1)
+    std::vector<int32_t> vg_ptr, vgl;          // level -> large clusters (backward staging)
     std::vector<int32_t> uf_ptr, ub_ptr;       // level -> task ranges
     std::vector<HTask> uft, ubt;
     std::vector<int32_t> u_ni_max, u_nd_max;   // level -> max ni / nd (shared memory)
-    int64_t ubuf = 0, tbuf = 0, pbuf = 0;
+    int64_t ubuf = 0, tbuf = 0, pbuf = 0, nslots = 0, vbuf = 0;
     int32_t ntickets = 0;
     int32_t vec = 2;
     int64_t dense_entries = 0, lowrank_entries = 0;   // algorithmic (no padding)
@@ -180,9 +187,13 @@ constexpr int SMALL_NI = 64;     // a cluster is small when ni <= SMALL_NI and
 constexpr int SMALL_NF = 320;    // ni + nb <= SMALL_NF (before compression)
 constexpr int FLAT_ITEMS = 256;  // items (threads) of a flat CTA
 constexpr int STAGE_MAX = 4096;  // staged input values of a flat CTA
-constexpr int UP_THREADS = 256;  // threads of an upper forward task (vec rows each)
+constexpr int UP_GROUPS = 64;    // row groups (of vec rows) of an upper forward task
+constexpr int UP_SPLIT = 4;      // column splits of an upper forward task (16 columns each)
 constexpr int UP_COLS = 64;      // columns of an upper forward task
-constexpr int UP_BCOLS = 8;      // columns of an upper backward task (one per warp)
+constexpr int UP_BCOLS = 2;      // columns of an upper backward task (4 warps each)
+constexpr int UP_THREADS = 256;  // threads of a low-rank group task (one per row)
+constexpr int FWD_COLS = 16;     // columns per flat forward split
+constexpr int BWD_ROWS = 64;     // rows per flat backward split
 constexpr int LR_ROWS = 256;     // max rows of a low-rank group
 constexpr int LR_KMAX = 64;      // largest rank kept in a low-rank group
 
@@ -195,6 +206,8 @@ struct HFactorDev {
     int32_t* bidx = nullptr;
     int32_t* inc = nullptr;
     int32_t* drows = nullptr;
+    int32_t* uout = nullptr;
+    int32_t* vgl = nullptr;
     HSnode* sn = nullptr;
     HLr* lr = nullptr;
     FCta* ffc = nullptr;
@@ -207,8 +220,8 @@ struct HFactorDev {
     HTask* ubt = nullptr;
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
-    std::vector<int32_t> ff_ptr, fb_ptr, ulr_ptr, uf_ptr, ub_ptr, u_ni_max, u_nd_max;
-    int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0;
+    std::vector<int32_t> ff_ptr, fb_ptr, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max, u_nd_max;
+    int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0, nslots = 0, vbuf_entries = 0;
     int32_t ntickets = 0;
     int64_t bytes_pass = 0;             // stored factor bytes read by fwd + bwd
     int64_t alg_bytes_pass = 0;         // nonzero entries only (no padding)
@@ -219,10 +232,12 @@ void free_hfactor(HFactorDev* d);
 
 // Scratch of one triangular solve (sized by the factor; reused by every solve).
 struct HScratch {
-    double* ybuf = nullptr;
-    double* ubuf = nullptr;
-    double* tbuf = nullptr;
-    double* pbuf = nullptr;
+    double* xp = nullptr;      // permuted, shifted input (n)
+    double* ybuf = nullptr;    // forward result (n)
+    double* inb = nullptr;     // children's update slots (nslots)
+    double* tbuf = nullptr;    // low-rank products
+    double* pbuf = nullptr;    // partial sums of split row chunks
+    double* vbuf = nullptr;    // staged backward inputs of the large clusters of a level
     unsigned int* tickets = nullptr;    // zero between solves
 };
 

@@ -56,7 +56,8 @@ extern "C" int bid_apply_factor_noalloc(bid_precond* P, int which, const double*
     const HFactorDev& F = which == 1 ? P->F1 : P->FK;
     const int64_t red = (int64_t)P->sys->sms * 8 + 2;      // block partials + sum + ticket
     const int64_t tick = (F.ntickets + 2) / 2;              // tickets packed two per double
-    const int64_t need = F.n + F.ubuf_entries + F.tbuf_entries + F.pbuf_entries + tick + red;
+    const int64_t need = 2 * F.n + F.nslots + F.vbuf_entries + F.tbuf_entries + F.pbuf_entries +
+                         tick + red;
     if (need > (int64_t)NOALLOC_DOUBLES)
         return set_error(BID_EINVAL,
                          "factor needs %lld scratch values; the static scratch holds %lld "
@@ -66,8 +67,10 @@ extern "C" int bid_apply_factor_noalloc(bid_precond* P, int which, const double*
     BID_TRY(scratch_address(&base));
     HScratch S;
     S.ybuf = base;
-    S.ubuf = S.ybuf + F.n;
-    S.tbuf = S.ubuf + F.ubuf_entries;
+    S.xp = S.ybuf + F.n;
+    S.inb = S.xp + F.n;
+    S.vbuf = S.inb + F.nslots;
+    S.tbuf = S.vbuf + F.vbuf_entries;
     S.pbuf = S.tbuf + F.tbuf_entries;
     S.tickets = reinterpret_cast<unsigned int*>(S.pbuf + F.pbuf_entries);
     double* partials = S.pbuf + F.pbuf_entries + tick;
