@@ -546,11 +546,12 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
             chunk = (chunk + vec - 1) / vec * vec;      // split bounds on vector boundaries
             const int umax = FLAT_ITEMS / P;             // units per CTA block
             bool staged = false;
-            int woff = 0;
+            int woff = 0, sk = 0;
             for (int u0 = 0; u0 < units; u0 += umax) {
                 const int u1 = std::min(units, u0 + umax);
                 const int need = P * (u1 - u0);
-                if (c.it1 - c.it0 + need > FLAT_ITEMS || (!staged && c.total + stage > STAGE_MAX)) {
+                if (c.it1 - c.it0 + need > FLAT_ITEMS ||
+                    (!staged && (c.total + stage > STAGE_MAX || c.st1 - c.st0 == STAGE_CL))) {
                     flush();
                     staged = false;
                 }
@@ -558,6 +559,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                     FStage g{s, c.total};
                     stages.push_back(g);
                     c.st1 = (int32_t)stages.size();
+                    sk = c.st1 - c.st0 - 1;
                     woff = c.total;
                     c.total += stage;
                     staged = true;
@@ -568,6 +570,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                         it.s = s;
                         it.q = fwd ? u * vec : u;
                         it.woff = woff;
+                        it.sk = sk;
                         it.c0 = std::min(span, p * chunk);
                         it.c1 = std::min(span, (p + 1) * chunk);
                         it.nsplit = P;
@@ -641,11 +644,17 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
                 k.part = k.ticket = -1;
                 F->uft.push_back(k);
             }
-            for (int a = 0; a < h.ni; a += UP_BCOLS) {
+            // backward: a column is shared by wpc warps so that each warp reads
+            // about UP_BROWS rows; a CTA holds 8 / wpc columns
+            int wpc = 1;
+            while (wpc < 8 && (int64_t)wpc * UP_BROWS < h.nd) wpc *= 2;
+            const int cpc = 8 / wpc;
+            for (int a = 0; a < h.ni; a += cpc) {
                 HTask k{};
                 k.s = s;
                 k.a0 = a;
-                k.a1 = std::min(h.ni, a + UP_BCOLS);
+                k.a1 = std::min(h.ni, a + cpc);
+                k.b0 = wpc;
                 F->ubt.push_back(k);
             }
         }

@@ -161,44 +161,49 @@ __device__ __forceinline__ int stage_owner(const int2* st, int nst, int f) {
     return lo;
 }
 
+// Small clusters carry no low-rank groups, so their dense rows are the rows
+// of M_s (dense_row(q) = q).  A CTA first stages the descriptors and inputs of
+// its clusters in shared memory; the item loop then touches global memory only
+// for the factor data, the update slots of its rows and the result.
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ data, int cta0,
                                                  const double* xp, double* ybuf, double* inb) {
     constexpr int VEC = VecOf<T>::N;
+    constexpr int U = VEC == 8 ? 4 : 8;   // columns per load round
     __shared__ A w[STAGE_MAX];
     __shared__ A red[HT][VEC];
-    __shared__ int2 st[FLAT_ITEMS];
+    __shared__ int2 st[STAGE_CL];
+    __shared__ HSnode ssn[STAGE_CL];
     const FCta c = v.ffc[cta0 + blockIdx.x];
     const int nst = c.st1 - c.st0;
-    for (int k = threadIdx.x; k < nst; k += HT) {
-        const FStage g = v.ffs[c.st0 + k];
-        st[k] = make_int2(g.s, g.woff);
-    }
-    __syncthreads();
-    for (int f = threadIdx.x; f < c.total; f += HT) {
-        const int2 g = st[stage_owner(st, nst, f)];
-        const HSnode sn = v.sn[g.x];
-        w[f] = (A)gather_w(v, sn, f - g.y, xp, inb);
-    }
-    __syncthreads();
     const int it = c.it0 + threadIdx.x;
     FItem item;
     item.lead = 0;
+    if (it < c.it1) item = v.ffi[it];   // issued early, used after the barrier
+    for (int k = threadIdx.x; k < nst; k += HT) {
+        const FStage g = v.ffs[c.st0 + k];
+        st[k] = make_int2(g.s, g.woff);
+        ssn[k] = v.sn[g.s];
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < c.total; f += HT) {
+        const int k = stage_owner(st, nst, f);
+        w[f] = (A)gather_w(v, ssn[k], f - st[k].y, xp, inb);
+    }
+    __syncthreads();
     A acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0;
-    HSnode sn;
     if (it < c.it1) {
-        item = v.ffi[it];
-        sn = v.sn[item.s];
+        const HSnode sn = ssn[item.sk];
         const int q0 = item.q;
         const A* ws = w + item.woff;
         const T* col = data + sn.data_off;
         const int jend = (q0 + VEC - 1 < sn.ni) ? min(item.c1, q0 + VEC) : item.c1;
-        for (int j0 = item.c0; j0 < jend; j0 += 4) {
-            A val[4][VEC];
+        for (int j0 = item.c0; j0 < jend; j0 += U) {
+            A val[U][VEC];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int j = j0 + u;
                 if (j < jend) {
                     ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ 
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int j = j0 + u;
                 const A wj = j < jend ? ws[j] : (A)0;
 #pragma unroll
@@ -221,76 +226,77 @@ __global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ 
     for (int e = 0; e < VEC; ++e) red[threadIdx.x][e] = acc[e];
     __syncthreads();
     if (it >= c.it1 || !item.lead) return;
+    const HSnode sn = ssn[item.sk];
     for (int p = 1; p < item.nsplit; ++p)
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc[e] += red[threadIdx.x + p * item.stride][e];
 #pragma unroll
     for (int e = 0; e < VEC; ++e)
-        if (item.q + e < sn.nd)
-            finish_row(v, sn, dense_row(v, sn, item.q + e), (double)acc[e], ybuf, inb);
+        if (item.q + e < sn.nd) finish_row(v, sn, item.q + e, (double)acc[e], ybuf, inb);
 }
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_flat_bwd(HView v, const T* __restrict__ data, int cta0,
                                                  const double* __restrict__ ybuf, double* out) {
     constexpr int VEC = VecOf<T>::N;
+    constexpr int U = VEC == 8 ? 4 : 8;   // vectors per load round
     __shared__ A vs[STAGE_MAX];
     __shared__ A red[HT];
-    __shared__ int2 st[FLAT_ITEMS];
+    __shared__ int2 st[STAGE_CL];
+    __shared__ HSnode ssn[STAGE_CL];
     const FCta c = v.fbc[cta0 + blockIdx.x];
     const int nst = c.st1 - c.st0;
-    for (int k = threadIdx.x; k < nst; k += HT) {
-        const FStage g = v.fbs[c.st0 + k];
-        st[k] = make_int2(g.s, g.woff);
-    }
-    __syncthreads();
-    for (int f = threadIdx.x; f < c.total; f += HT) {
-        const int2 g = st[stage_owner(st, nst, f)];
-        const HSnode sn = v.sn[g.x];
-        const int q = f - g.y;
-        vs[f] = (A)(q < sn.nd ? vrow(v, sn, q, ybuf, out) : 0.0);
-    }
-    __syncthreads();
     const int it = c.it0 + threadIdx.x;
     FItem item;
     item.lead = 0;
+    if (it < c.it1) item = v.fbi[it];
+    for (int k = threadIdx.x; k < nst; k += HT) {
+        const FStage g = v.fbs[c.st0 + k];
+        st[k] = make_int2(g.s, g.woff);
+        ssn[k] = v.sn[g.s];
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < c.total; f += HT) {
+        const int k = stage_owner(st, nst, f);
+        const HSnode& sn = ssn[k];
+        const int q = f - st[k].y;
+        double x = 0.0;
+        if (q < sn.nd) x = q < sn.ni ? ybuf[sn.first + q] : -out[v.bidx[sn.bidx_off + q - sn.ni]];
+        vs[f] = (A)x;
+    }
+    __syncthreads();
     A acc = 0;
-    HSnode sn;
     if (it < c.it1) {
-        item = v.fbi[it];
-        sn = v.sn[item.s];
+        const HSnode sn = ssn[item.sk];
         const int j = item.q;
         const A* vv = vs + item.woff;
         const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
-        const int qbeg = max(item.c0, j & ~(VEC - 1));   // both multiples of VEC
         const int qend = item.c1;
-        int q0 = qbeg;
-        for (; q0 + 3 * VEC < qend; q0 += 4 * VEC) {
-            A val[4][VEC];
+        for (int q0 = max(item.c0, j & ~(VEC - 1)); q0 < qend; q0 += U * VEC) {
+            A val[U][VEC];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) ld16(cj + q0 + u * VEC, val[u]);
+            for (int u = 0; u < U; ++u) {
+                if (q0 + u * VEC < qend) {
+                    ld16(cj + q0 + u * VEC, val[u]);
+                } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+                    for (int e = 0; e < VEC; ++e) val[u][e] = 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     const int q = q0 + u * VEC + e;
                     if (q >= j && q < qend) acc += val[u][e] * vv[q];
                 }
         }
-        for (; q0 < qend; q0 += VEC) {
-            A val[VEC];
-            ld16(cj + q0, val);
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                const int q = q0 + e;
-                if (q >= j && q < qend) acc += val[e] * vv[q];
-            }
-        }
     }
     red[threadIdx.x] = acc;
     __syncthreads();
     if (it >= c.it1 || !item.lead) return;
     for (int p = 1; p < item.nsplit; ++p) acc += red[threadIdx.x + p * item.stride];
+    const HSnode& sn = ssn[item.sk];
     out[v.pidx[sn.first + item.q]] = (double)acc;
 }
 
@@ -457,9 +463,10 @@ __global__ void __launch_bounds__(HT) k_bwd_prep(HView v, const T* __restrict__ 
     }
 }
 
-// Backward, large clusters: CTA = UP_BCOLS columns, 4 warps per column, warp w
-// of a column covers a quarter of the column's rows (aligned vectors, v from
-// vbuf); the 4 partials are summed in order, plus the low-rank terms.
+// Backward, large clusters: a column is shared by wpc = t.b0 warps (1..8, from
+// the column length), a CTA holds 8 / wpc columns; warp w of a column covers
+// a 1/wpc share of its rows (aligned vectors, v from vbuf).  The wpc partials
+// are summed in order, plus the low-rank terms.
 template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ data, int task0,
                                                const double* vbuf, const double* tbuf,
@@ -469,13 +476,14 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
     const HTask t = v.ubt[task0 + blockIdx.x];
     const HSnode sn = v.sn[t.s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = t.a0 + warp / 4, part = warp % 4;
+    const int wpc = t.b0;
+    const int j = t.a0 + warp / wpc, part = warp % wpc;
     A acc = 0;
     if (j < t.a1) {
         const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
         const double* vv = vbuf + sn.v_off;
         const int qa = j & ~(VEC - 1);
-        int rs = (sn.nd - qa + 3) / 4;
+        int rs = (sn.nd - qa + wpc - 1) / wpc;
         rs = (rs + VEC - 1) / VEC * VEC;
         const int r0 = qa + part * rs, r1 = min(sn.nd, r0 + rs);
         int q0 = r0 + VEC * lane;
@@ -510,11 +518,12 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
     acc = wsum(acc);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
-    if (threadIdx.x < UP_BCOLS) {
+    const int ncol = NW / wpc;
+    if ((int)threadIdx.x < ncol) {
         const int jj = t.a0 + threadIdx.x;
         if (jj < t.a1) {
-            const A s = red[4 * threadIdx.x] + red[4 * threadIdx.x + 1] + red[4 * threadIdx.x + 2] +
-                        red[4 * threadIdx.x + 3];
+            A s = 0;
+            for (int w = 0; w < wpc; ++w) s += red[threadIdx.x * wpc + w];
             out[v.pidx[sn.first + jj]] = (double)s;
         }
     }

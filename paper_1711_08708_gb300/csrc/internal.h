@@ -123,6 +123,7 @@ struct HLr {
 // stages the inputs of its clusters (FStage entries sorted by woff).
 struct FItem {
     int32_t s, q, woff, c0, c1, nsplit, stride, lead;
+    int32_t sk;         // index of the cluster in its CTA's stage list
 };
 struct FStage {
     int32_t s, woff;
@@ -137,7 +138,7 @@ struct FCta {
 //                   go to pbuf[part + c*(a1-a0) + row] and the last CTA of
 //                   ticket `ticket` finishes the rows;  s < 0: low-rank group
 //                   g = -1 - s, rows [a0, a1) of the group
-//  upper backward:  cluster s, columns [a0, a1)
+//  upper backward:  cluster s, columns [a0, a1), b0 warps per column
 struct HTask {
     int32_t s, a0, a1, b0, b1, part, ticket, nparts;
 };
@@ -187,10 +188,11 @@ constexpr int SMALL_NI = 64;     // a cluster is small when ni <= SMALL_NI and
 constexpr int SMALL_NF = 320;    // ni + nb <= SMALL_NF (before compression)
 constexpr int FLAT_ITEMS = 256;  // items (threads) of a flat CTA
 constexpr int STAGE_MAX = 4096;  // staged input values of a flat CTA
+constexpr int STAGE_CL = 128;    // staged clusters of a flat CTA
 constexpr int UP_GROUPS = 64;    // row groups (of vec rows) of an upper forward task
 constexpr int UP_SPLIT = 4;      // column splits of an upper forward task (16 columns each)
 constexpr int UP_COLS = 64;      // columns of an upper forward task
-constexpr int UP_BCOLS = 2;      // columns of an upper backward task (4 warps each)
+constexpr int UP_BROWS = 512;    // target rows per warp of an upper backward task
 constexpr int UP_THREADS = 256;  // threads of a low-rank group task (one per row)
 constexpr int FWD_COLS = 16;     // columns per flat forward split
 constexpr int BWD_ROWS = 64;     // rows per flat backward split
