@@ -124,71 +124,119 @@ int read_scalars(bid_precond* P, cudaStream_t st, DevScalars* out) {
     return BID_OK;
 }
 
+// Device-resident PCG (Sec. 5.1 with the stopping rule of Sec. 6.2) on the
+// preconditioner's own vectors xs (X) and ytmp (Y), as one CUDA graph:
+//   prologue: r = Y - Lambda X, projection, check (sets the loop condition)
+//   WHILE (condition): z = P^-1 r, beta, p = z + beta p, q = Lambda p,
+//                      x += alpha p, r -= alpha q (projected), check.
+// The check sits at the end of the body, so no preconditioner application is
+// spent after convergence; no host round trip happens inside the loop.
+int build_graph(bid_precond* P) {
+    if (P->gexec) return BID_OK;
+    bid_system* s = P->sys;
+    const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
+    const int flexible = P->opts.precision != BID_FP64;
+    BID_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+    BID_CUDA_TRY(cudaGraphCreate(&P->graph, 0));
+    cudaGraphConditionalHandle h;
+    BID_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, P->graph, 0, 0));
+    Launch L = launch_of(s, P->cap);
+    // prologue, captured into a graph of its own and added as a child node
+    cudaGraph_t pro = nullptr;
+    const int64_t l0 = bid_kernel_launches();
+    BID_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp, P->sc,
+                           P->partials);
+    if (rc == BID_OK) rc = launch_project(L, N, NH, P->r, P->sc, P->partials);
+    if (rc == BID_OK) rc = launch_check(L, P->sc, h, 1);
+    cudaError_t e = cudaStreamEndCapture(P->cap, &pro);
+    if (rc != BID_OK) return rc;
+    if (e != cudaSuccess) return set_error(BID_ECUDA, "prologue capture: %s", cudaGetErrorString(e));
+    P->g_prologue = (int)(bid_kernel_launches() - l0);
+    cudaGraphNode_t npro, nwhile;
+    BID_CUDA_TRY(cudaGraphAddChildGraphNode(&npro, P->graph, nullptr, 0, pro));
+    cudaGraphDestroy(pro);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    BID_CUDA_TRY(cudaGraphAddNode(&nwhile, P->graph, &npro, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const int64_t l1 = bid_kernel_launches();
+    BID_CUDA_TRY(cudaStreamBeginCaptureToGraph(P->cap, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+    rc = precond_apply(P, L, P->r, P->z);
+    if (rc == BID_OK) rc = launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, -1, P->sc, P->partials);
+    if (rc == BID_OK) rc = launch_pupdate(L, n, P->p, P->z, -1, P->sc);
+    if (rc == BID_OK)
+        rc = launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc,
+                           P->partials);
+    if (rc == BID_OK) rc = launch_update(L, N, NH, P->xs, P->r, P->p, P->q, P->sc, P->partials);
+    if (rc == BID_OK) rc = launch_check(L, P->sc, h, 0);
+    cudaGraph_t body_out = nullptr;
+    e = cudaStreamEndCapture(P->cap, &body_out);
+    if (rc != BID_OK) return rc;
+    if (e != cudaSuccess) return set_error(BID_ECUDA, "loop body capture: %s", cudaGetErrorString(e));
+    P->g_body = (int)(bid_kernel_launches() - l1);
+    // captures are not launches: remove them from the count
+    count_launches(-(P->g_prologue + P->g_body));
+    BID_CUDA_TRY(cudaGraphInstantiate(&P->gexec, P->graph, 0));
+    return BID_OK;
+}
+
+// Step 2 on X (in: guess, out: solution) for right-hand side Y; X and Y may be
+// the preconditioner's own xs / ytmp (no copy then).
 int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_iter,
                bid_solve_info* info, cudaStream_t st) {
     bid_system* s = P->sys;
     const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
     Launch L = launch_of(s, st);
-    const int flexible = P->opts.precision != BID_FP64;
+    BID_TRY(build_graph(P));
+    if (Y != P->ytmp) BID_CUDA_TRY(cudaMemcpyAsync(P->ytmp, Y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if (X != P->xs) BID_CUDA_TRY(cudaMemcpyAsync(P->xs, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     bid_solve_info inf{};
     inf.status = BID_OK;
     DevScalars h{};
     int iters = 0;
-    // attempt 0: PCG from the guess; attempt 1 (only if the recurrence converged
-    // but the recomputed true residual is above tol): one restart from X.
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        // r = Y - Lambda X, U block projected onto 1^perp
-        BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, X, P->r, Y, P->sc, P->partials));
-        BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+    // attempt 0: PCG from the guess; attempt 1 only if the recurrence residual
+    // converged but the recomputed true residual is above tol (one restart).
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        struct {
+            double tol2;
+            int iter, max_iter;
+        } lim{tol * tol, 0, max_iter - iters};
+        BID_CUDA_TRY(cudaMemcpyAsync(&P->sc->tol2, &lim, sizeof(lim), cudaMemcpyHostToDevice, st));
+        BID_CUDA_TRY(cudaGraphLaunch(P->gexec, st));
         BID_TRY(read_scalars(P, st, &h));
+        count_launches(P->g_prologue + P->g_body * h.iter);
+        iters += h.iter;
+        if (attempt == 0) inf.relres_true = h.yy > 0 ? std::sqrt(h.rr / h.yy) : 0.0;
         if (!std::isfinite(h.yy) || !std::isfinite(h.rr)) {
             inf.status = BID_ESTAGNATE;
             break;
         }
-        const double ny = std::sqrt(h.yy);
-        if (ny == 0.0) {
-            BID_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * n, st));
+        if (h.yy == 0.0) {
+            BID_CUDA_TRY(cudaMemsetAsync(P->xs, 0, sizeof(double) * n, st));
             inf.relres = inf.relres_true = 0.0;
             break;
         }
-        const double rel_true = std::sqrt(h.rr) / ny;
-        inf.relres_true = rel_true;
-        if (attempt == 0) inf.relres = rel_true;
-        if (rel_true < tol || attempt == 2) break;
-        if (attempt == 1) inf.restarts = 1;
-        BID_TRY(precond_apply(P, L, P->r, P->z));
-        BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, 1, P->sc, P->partials));
-        BID_TRY(launch_pupdate(L, n, P->p, P->z, 1, P->sc));
-        bool conv = false;
-        while (iters < max_iter) {
-            BID_TRY(launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc, P->partials));
-            BID_TRY(launch_update(L, N, NH, X, P->r, P->p, P->q, P->sc, P->partials));
-            ++iters;
-            BID_TRY(read_scalars(P, st, &h));
-            if (!std::isfinite(h.rr)) {
-                inf.status = BID_ESTAGNATE;
-                break;
-            }
-            inf.relres = std::sqrt(h.rr) / ny;
-            if (inf.relres < tol) {
-                conv = true;
-                break;
-            }
-            BID_TRY(precond_apply(P, L, P->r, P->z));
-            BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, 0, P->sc, P->partials));
-            BID_TRY(launch_pupdate(L, n, P->p, P->z, 0, P->sc));
-        }
-        if (inf.status != BID_OK) break;
-        if (!conv) {
+        const double ny = std::sqrt(h.yy);
+        inf.relres = std::sqrt(h.rr) / ny;
+        if (inf.relres >= tol) {   // stopped on max_iter
             inf.status = BID_ENOCONV;
-            BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, X, P->r, Y, P->sc, P->partials));
-            BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
-            BID_TRY(read_scalars(P, st, &h));
-            inf.relres_true = std::sqrt(h.rr) / ny;
-            break;
         }
+        // true residual
+        BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp, P->sc,
+                              P->partials));
+        BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+        BID_TRY(read_scalars(P, st, &h));
+        inf.relres_true = std::sqrt(h.rr) / ny;
+        if (inf.status != BID_OK || inf.relres_true < tol || attempt == 1 || iters >= max_iter) break;
+        inf.restarts = 1;
     }
-    BID_TRY(launch_normalise(L, N, X, s->m, s->msum, P->sc, P->partials));
+    BID_TRY(launch_normalise(L, N, P->xs, s->m, s->msum, P->sc, P->partials));
+    if (X != P->xs) BID_CUDA_TRY(cudaMemcpyAsync(X, P->xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     inf.iters = iters;
     if (info) *info = inf;
     if (inf.status == BID_ENOCONV)
@@ -480,6 +528,9 @@ void bid_destroy_precond(bid_precond* P) {
     cudaFree(P->hs.tickets);
     cudaFree(P->sc);
     if (P->host_pinned) cudaFreeHost(P->host_pinned);
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->cap) cudaStreamDestroy(P->cap);
     delete P;
 }
 

@@ -253,6 +253,8 @@ struct DevScalars {
     double yy, sum_a, sum_b;
     double shift1, shift2;
     double gen[4];
+    double tol2;            // tol^2 of the running solve (device-resident loop)
+    int iter, max_iter;     // iterations done / allowed
     unsigned int ticket[16];
 };
 
@@ -288,6 +290,11 @@ int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, dou
                     double dt, double* Y);
 int launch_normalise(const Launch& L, int64_t N, double* U, const double* m,
                      double msum, DevScalars* sc, double* partials);
+// One-thread convergence check of the device-resident PCG loop: first != 0
+// resets the iteration count, otherwise it is incremented; the WHILE
+// condition `h` is set to continue iff ||r||^2 > tol^2 ||Y||^2, the residual is
+// finite and fewer than max_iter iterations are done.
+int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int first);
 // x = P^-1 b over a hierarchical factor: forward pass level by level (leaves
 // first), then backward pass.  The input entries are b[i] - shift_sum*inv_n
 // (shift_sum may be NULL), with the pinned entry set to zero.
@@ -321,4 +328,9 @@ struct bid_precond {
     bid::DevScalars* sc = nullptr;
     bid::DevScalars* host_pinned = nullptr;   // pinned host mirror of the scalars
     bid_precond_stats stats{};
+    // device-resident PCG loop: one graph per preconditioner (built on first use)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;               // private stream used for capture only
+    int g_prologue = 0, g_body = 0;           // kernels per prologue / per iteration
 };

@@ -232,7 +232,10 @@ __global__ void __launch_bounds__(TPB) k_update(int N, int NH, double* __restric
 __global__ void __launch_bounds__(TPB) k_dot_rz(int n, int N, const double* __restrict__ r,
                                                 const double* __restrict__ z,
                                                 const double* __restrict__ q, int flexible,
-                                                int first, DevScalars* sc, double* partials) {
+                                                int first_arg, DevScalars* sc, double* partials) {
+    // first_arg < 0: inside the device-resident loop, the first iteration is
+    // the one that starts with no iteration done
+    const bool first = first_arg < 0 ? sc->iter == 0 : first_arg != 0;
     double rz = 0.0, qz = 0.0, sz = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double zi = z[i];
@@ -259,8 +262,9 @@ __global__ void __launch_bounds__(TPB) k_dot_rz(int n, int N, const double* __re
 }
 
 __global__ void __launch_bounds__(TPB) k_pupdate(int n, double* __restrict__ p,
-                                                 const double* __restrict__ z, int first,
+                                                 const double* __restrict__ z, int first_arg,
                                                  const DevScalars* sc) {
+    const bool first = first_arg < 0 ? sc->iter == 0 : first_arg != 0;
     const double beta = first ? 0.0 : sc->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         p[i] = first ? z[i] : z[i] + beta * p[i];
@@ -376,6 +380,14 @@ __global__ void __launch_bounds__(TPB) k_sub_scalar(int N, double* __restrict__ 
         U[i] -= a;
 }
 
+__global__ void k_check(DevScalars* sc, cudaGraphConditionalHandle h, int first) {
+    const int it = first ? 0 : sc->iter + 1;
+    sc->iter = it;
+    const double rr = sc->rr, yy = sc->yy;
+    const bool go = yy > 0.0 && isfinite(rr) && rr > sc->tol2 * yy && it < sc->max_iter;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 int check_launch(const char* what) {
     count_launches(1);
     cudaError_t e = cudaGetLastError();
@@ -454,6 +466,10 @@ int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, dou
     k_rhs_gate<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, V, h, Ist, stim_on, mH, P,
                                                       Y);
     return check_launch("rhs_gate");
+}
+int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int first) {
+    k_check<<<1, 1, 0, L.st>>>(sc, (cudaGraphConditionalHandle)h, first);
+    return check_launch("check");
 }
 int launch_normalise(const Launch& L, int64_t N, double* U, const double* m, double msum,
                      DevScalars* sc, double* partials) {
