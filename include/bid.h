@@ -218,6 +218,67 @@ const char* bid_last_error(void);
 int64_t bid_kernel_launches(void);
 
 /* ---------------------------------------------------------------------------
+ * Batched form: many independent problems ("slices", each assembled by
+ * bid_assemble on its own mesh) advanced together, with the semantics of one
+ * bid_solve / bid_step per slice.  Each phase of the method (Lambda product,
+ * P_1 and P_K solves, vector updates, convergence test) is one kernel launch
+ * over all slices, and the PCG loop of all slices is one CUDA graph whose
+ * device-side WHILE condition runs until every slice has converged; a slice
+ * that has converged is frozen (its iterate no longer changes).
+ *
+ * Combined layout: slice s owns entries [off[s], off[s+1]) of every combined
+ * vector, laid out as that slice's own X ([U_s | V_s], N_s + N_H,s entries,
+ * heart nodes first), so X_s = X + off[s]; its heart-indexed arrays (gates h,
+ * stimulus Ist) are entries [hoff[s], hoff[s+1]) of the combined heart
+ * arrays.  bid_batch_layout returns off and hoff.
+ * ------------------------------------------------------------------------- */
+typedef struct bid_batch bid_batch;
+
+/* Build the batch: the factors of every slice (one nested-dissection tree per
+ * slice; leaf[s] its leaf size, or opts->leaf_size for all when leaf is NULL;
+ * dt, eps, precision, block, n_threads from opts) and the combined device
+ * layout.  The systems are borrowed and must outlive the batch.  All slices
+ * share the reaction and stimulus parameters (chi, Cm, Mitchell-Schaeffer
+ * constants, stimulus window) and the dimension; conductivities and meshes
+ * may differ.  Blocking.
+ * Errors: BID_EINVAL (nslices < 1 or > 32767, NULL system, differing reaction
+ * parameters or dimension, bad opts or leaf, more than 2^31 unknowns in
+ * all), BID_ENOMEM, BID_ECUDA. */
+int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_opts* opts,
+                     const int32_t* leaf, bid_batch** out);
+/* off, hoff: host arrays of nslices + 1 entries (either may be NULL). */
+int bid_batch_layout(const bid_batch* B, int64_t* off, int64_t* hoff);
+/* Factor statistics of the batch (both forests, all slices together). */
+int bid_batch_get_stats(const bid_batch* B, bid_precond_stats* st);
+/* bid_apply_factor for every slice at once on combined device vectors:
+ * which = 1: x_U,s = P_1,s^-1 (b_U,s - mean(b_U,s)), which = 2:
+ * x_V,s = P_K,s^-1 b_V,s; the other entries of x are not written. */
+int bid_batch_apply_factor(bid_batch* B, int which, const double* b, double* x, void* stream);
+/* bid_apply_precond for every slice (combined device vectors r, z). */
+int bid_batch_apply_precond(bid_batch* B, const double* r, double* z, void* stream);
+/* bid_solve for every slice: Y, X combined device vectors (distinct); info:
+ * host array of nslices entries or NULL.  Returns the first error of any
+ * slice (BID_ESTAGNATE before BID_ENOCONV); info tells which.  Blocking. */
+int bid_batch_solve(bid_batch* B, const double* Y, double* X, double tol, int max_iter,
+                    bid_solve_info* info, void* stream);
+/* bid_step for every slice: X (combined state, U_s and V_s of each slice), h
+ * (combined gates) and Ist (combined stimulus amplitudes or NULL) device,
+ * updated in place; iters_out: host array of n_steps * nslices counts (step
+ * major) or NULL.  Blocking. */
+int bid_batch_step(bid_batch* B, double* X, double* h, const double* Ist, double t0,
+                   int n_steps, double tol, int max_iter, int* iters_out, void* stream);
+void bid_batch_destroy(bid_batch* B);
+
+/* Leaf-size tuner: builds the preconditioner of s with each leaf size in
+ * cands (other options from opts), times `reps` applications of
+ * P_Lambda^-1 with CUDA events, and returns the fastest in *best and the mean
+ * milliseconds per application of every candidate in ms_out (ncands entries,
+ * may be NULL).  Results are cached in the process, keyed by the system's
+ * sizes and the options: a repeated query returns at once.  Blocking. */
+int bid_tune_leaf(bid_system* s, const bid_precond_opts* opts, const int32_t* cands,
+                  int ncands, int reps, int32_t* best, double* ms_out);
+
+/* ---------------------------------------------------------------------------
  * Host-only entry points (no GPU needed).  They expose the host half of the
  * library -- the P1 assembly and the hierarchical factor build -- together
  * with a sequential host replay of the factor's level-by-level triangular
@@ -243,6 +304,16 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps,
                           int leaf, int block, int precision, const double* b, double* x,
                           bid_precond_stats* stats);
+/* The batched factors on the host: the forest over nslices host systems
+ * (combined layout as for bid_batch_create, leaf per slice or NULL for
+ * `leaf_default`), replayed in FP64: which = 1 writes x_U,s = P_1,s^-1
+ * (b_U,s - mean(b_U,s)), which = 2 writes x_V,s = P_K,s^-1 b_V,s (gamma as
+ * given); other entries of x are left as they are.  b, x host arrays of the
+ * combined length.  stats may be NULL. */
+int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, int which,
+                                double gamma, double eps, const int32_t* leaf, int leaf_default,
+                                int block, int precision, const double* b, double* x,
+                                bid_precond_stats* stats);
 void bid_host_destroy(bid_host_system* h);
 
 #ifdef __cplusplus

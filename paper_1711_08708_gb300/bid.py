@@ -92,6 +92,17 @@ SIGNATURES = {
     "bid_host_csr": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "bid_host_factor_solve": (_I, [_VP, _I, _D, _D, _I, _I, _I, _VP, _VP, C.POINTER(PrecondStats)]),
     "bid_host_destroy": (None, [_VP]),
+    "bid_batch_create": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, C.POINTER(_VP)]),
+    "bid_batch_layout": (_I, [_VP, _VP, _VP]),
+    "bid_batch_get_stats": (_I, [_VP, C.POINTER(PrecondStats)]),
+    "bid_batch_apply_factor": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "bid_batch_apply_precond": (_I, [_VP, _VP, _VP, _VP]),
+    "bid_batch_solve": (_I, [_VP, _VP, _VP, _D, _I, _VP, _VP]),
+    "bid_batch_step": (_I, [_VP, _VP, _VP, _VP, _D, _I, _D, _I, _VP, _VP]),
+    "bid_batch_destroy": (None, [_VP]),
+    "bid_tune_leaf": (_I, [_VP, C.POINTER(PrecondOpts), _VP, _I, _I, _VP, _VP]),
+    "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _VP, _VP,
+                                         C.POINTER(PrecondStats)]),
 }
 
 
@@ -191,16 +202,21 @@ class System:
             self.h = None
 
 
+def _opts(dt, eps, precision, leaf, block, threads):
+    o = PrecondOpts()
+    lib.bid_precond_opts_default(C.byref(o))
+    o.dt, o.eps = float(dt), float(eps)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.leaf_size, o.block, o.n_threads = int(leaf), int(block), int(threads)
+    return o
+
+
 class Precond:
     """bid_precond: P_Lambda for one time step dt, plus the PCG work vectors."""
 
     def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=16, block=128,
                  threads=0):
-        o = PrecondOpts()
-        lib.bid_precond_opts_default(C.byref(o))
-        o.dt, o.eps = float(dt), float(eps)
-        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        o.leaf_size, o.block, o.n_threads = int(leaf), int(block), int(threads)
+        o = _opts(dt, eps, precision, leaf, block, threads)
         h = _VP()
         _check(lib.bid_precond_build_ex(system.h, C.byref(o), C.byref(h)))
         self.h, self.system, self.dt = h, system, float(dt)
@@ -253,6 +269,72 @@ class Precond:
             self.h = None
 
 
+def tune_leaf(system: System, dt, eps=0.0, precision="fp64", block=128,
+              candidates=(8, 16, 32, 64), reps=5):
+    """bid_tune_leaf: the fastest leaf size of `system` among `candidates`
+    (timed P_Lambda^-1 applications; cached per system size and options).
+    Returns (best, {leaf: ms})."""
+    o = _opts(dt, eps, precision, 16, block, 0)
+    c = np.ascontiguousarray(candidates, dtype=np.int32)
+    ms = np.zeros(c.size)
+    best = np.zeros(1, dtype=np.int32)
+    _check(lib.bid_tune_leaf(system.h, C.byref(o), _ptr(c), int(c.size), int(reps), _ptr(best),
+                             _ptr(ms)))
+    return int(best[0]), {int(k): float(v) for k, v in zip(c, ms)}
+
+
+class Batch:
+    """bid_batch: independent slices advanced together (combined layout:
+    slice s owns X[off[s]:off[s+1]] = [U_s | V_s] and h[hoff[s]:hoff[s+1]])."""
+
+    def __init__(self, systems, dt, eps=0.0, precision="fp64", leaf=16, block=128, threads=0):
+        self.systems = list(systems)
+        S = len(self.systems)
+        o = _opts(dt, eps, precision, leaf if np.isscalar(leaf) else 16, block, threads)
+        arr = (_VP * S)(*[s.h.value for s in self.systems])
+        lf = None if np.isscalar(leaf) else np.ascontiguousarray(leaf, dtype=np.int32)
+        h = _VP()
+        _check(lib.bid_batch_create(arr, S, C.byref(o), _ptr(lf), C.byref(h)))
+        self.h, self.S, self.dt = h, S, float(dt)
+        self.leaf = [int(leaf)] * S if lf is None else [int(v) for v in lf]
+        self.off = np.zeros(S + 1, dtype=np.int64)
+        self.hoff = np.zeros(S + 1, dtype=np.int64)
+        _check(lib.bid_batch_layout(h, _ptr(self.off), _ptr(self.hoff)))
+        st = PrecondStats()
+        _check(lib.bid_batch_get_stats(h, C.byref(st)))
+        self.stats = st.as_dict()
+
+    @property
+    def n(self):
+        return int(self.off[-1])
+
+    def apply_factor(self, which, b, x, stream=None):
+        _check(lib.bid_batch_apply_factor(self.h, int(which), _ptr(b), _ptr(x), _stream(stream)))
+
+    def apply_precond(self, r, z, stream=None):
+        _check(lib.bid_batch_apply_precond(self.h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def solve(self, Y, X, tol=1e-8, max_iter=200, stream=None, check=True):
+        info = (SolveInfo * self.S)()
+        rc = lib.bid_batch_solve(self.h, _ptr(Y), _ptr(X), float(tol), int(max_iter),
+                                 C.cast(info, _VP), _stream(stream))
+        if check:
+            _check(rc)
+        return [dict(iters=i.iters, status=i.status, restarts=i.restarts, relres=i.relres,
+                     relres_true=i.relres_true) for i in info], rc
+
+    def step(self, X, h, Ist, t0, n_steps, tol=1e-8, max_iter=200, stream=None):
+        iters = np.zeros((max(n_steps, 1), self.S), dtype=np.int32)
+        _check(lib.bid_batch_step(self.h, _ptr(X), _ptr(h), _ptr(Ist), float(t0), int(n_steps),
+                                  float(tol), int(max_iter), _ptr(iters), _stream(stream)))
+        return iters[:n_steps]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bid_batch_destroy(self.h)
+            self.h = None
+
+
 class HostSystem:
     """Host-only assembly and factor replay (no GPU needed)."""
 
@@ -295,3 +377,20 @@ class HostSystem:
         if getattr(self, "h", None):
             lib.bid_host_destroy(self.h)
             self.h = None
+
+
+def host_batch_factor_solve(systems, which, b, gamma=0.0, eps=0.0, leaf=16, block=128,
+                            precision="fp64"):
+    """bid_host_batch_factor_solve over HostSystems (combined layout); the
+    entries of the result outside the factor's block are zero."""
+    S = len(systems)
+    arr = (_VP * S)(*[s.h.value for s in systems])
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    lf = None if np.isscalar(leaf) else np.ascontiguousarray(leaf, dtype=np.int32)
+    st = PrecondStats()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib.bid_host_batch_factor_solve(arr, S, int(which), float(gamma), float(eps), _ptr(lf),
+                                           int(leaf) if lf is None else 16, int(block), prec,
+                                           _ptr(b), _ptr(x), C.byref(st)))
+    return x, st.as_dict()

@@ -352,13 +352,13 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     bo.vec = o->precision == BID_FP64 ? 2 : o->precision == BID_FP32 ? 4 : 8;
     HFactorHost h1, hk;
     // P_1: S_1 with the last U unknown pinned (pseudo-inverse on 1^perp)
-    BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, (int)(H.N - 1), bo, &h1));
+    BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, {(int32_t)(H.N - 1)}, bo, &h1));
     // P_K: K_m = gamma M_H + S_m (Sec. 5.2)
     CsrHost Km = H.Sm;
     for (int64_t r = 0; r < Km.n; ++r)
         for (int64_t q = Km.ptr[r]; q < Km.ptr[r + 1]; ++q)
             if (Km.col[q] == r) Km.val[q] += gamma * H.mH[r];
-    BID_TRY(build_hfactor(Km, H.coords.data(), H.dim, -1, bo, &hk));
+    BID_TRY(build_hfactor(Km, H.coords.data(), H.dim, {}, bo, &hk));
     bid_precond* P = new (std::nothrow) bid_precond();
     if (!P) return set_error(BID_ENOMEM, "host allocation failed");
     P->sys = s;

@@ -167,30 +167,55 @@ struct SnWork {
 
 }  // namespace
 
-int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, const HBuildOpts& o,
-                  HFactorHost* F) {
+int build_hfactor(const CsrHost& A, const double* coords, int dim,
+                  const std::vector<int32_t>& pins, const HBuildOpts& o, HFactorHost* F) {
     const int64_t n = A.n;
     if (n <= 0) return set_error(BID_EINVAL, "empty matrix");
     if (o.block < 8 || o.block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o.leaf < 4 || o.leaf > 4096) return set_error(BID_EINVAL, "leaf must be in 4..4096");
     if (o.vec != 2 && o.vec != 4 && o.vec != 8) return set_error(BID_EINVAL, "vec must be 2, 4 or 8");
     const int nthreads = o.threads > 0 ? o.threads : omp_get_max_threads();
+    std::vector<int64_t> gptr = o.group_ptr;
+    if (gptr.empty()) gptr = {0, n};
+    const int ngroups = (int)gptr.size() - 1;
+    if (ngroups < 1 || gptr[0] != 0 || gptr[ngroups] != n)
+        return set_error(BID_EINVAL, "group boundaries must cover the matrix");
+    for (int g = 0; g < ngroups; ++g) {
+        if (gptr[g + 1] <= gptr[g]) return set_error(BID_EINVAL, "empty group %d", g);
+        const int lf = (int)o.group_leaf.size() == ngroups ? o.group_leaf[g] : o.leaf;
+        if (lf < 4 || lf > 4096) return set_error(BID_EINVAL, "leaf must be in 4..4096");
+    }
+    if (!o.group_leaf.empty() && (int)o.group_leaf.size() != ngroups)
+        return set_error(BID_EINVAL, "one leaf size per group");
+    if (!o.vmap.empty()) {
+        if ((int64_t)o.vmap.size() != n) return set_error(BID_EINVAL, "vmap size");
+        for (int32_t v : o.vmap)
+            if (v < 0 || v >= o.vn) return set_error(BID_EINVAL, "vmap entry out of range");
+    }
+    for (int64_t r = 0; r < n; ++r) {   // block-diagonal structure
+        const int g = (int)(std::upper_bound(gptr.begin(), gptr.end(), r) - gptr.begin()) - 1;
+        for (int64_t q = A.ptr[r]; q < A.ptr[r + 1]; ++q)
+            if (A.col[q] < gptr[g] || A.col[q] >= gptr[g + 1])
+                return set_error(BID_EINVAL, "matrix couples groups %d and another", g);
+    }
 
-    // ---------------- cluster tree
+    // ---------------- cluster tree (one per group)
     NDBuilder nd(A, coords, dim, o.leaf);
-    {
-        std::vector<int32_t> all(n);
-        for (int64_t i = 0; i < n; ++i) all[i] = (int32_t)i;
-        nd.build(all, 0);
+    std::vector<int> troots;
+    for (int g = 0; g < ngroups; ++g) {
+        nd.leaf = (int)o.group_leaf.size() == ngroups ? o.group_leaf[g] : o.leaf;
+        std::vector<int32_t> all(gptr[g + 1] - gptr[g]);
+        for (int64_t i = gptr[g]; i < gptr[g + 1]; ++i) all[i - gptr[g]] = (int32_t)i;
+        troots.push_back(nd.build(all, 0));
     }
     std::vector<TNode>& T = nd.T;
     const int nt = (int)T.size();
 
-    // post-order
+    // post-order, tree after tree
     std::vector<int> post;
     post.reserve(nt);
-    {
-        std::vector<std::pair<int, int>> st{{0, 0}};
+    for (int root : troots) {
+        std::vector<std::pair<int, int>> st{{root, 0}};
         while (!st.empty()) {
             auto& [t, k] = st.back();
             if (k < T[t].nchild) {
@@ -206,7 +231,13 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
     for (int s = 0; s < nt; ++s) sid[post[s]] = s;
 
     F->n = n;
-    F->pin = pin;
+    std::vector<char> pinned(n, 0);
+    for (int32_t p : pins) {
+        if (p < 0 || p >= n) return set_error(BID_EINVAL, "pinned index out of range");
+        pinned[p] = 1;
+    }
+    F->pin = pins.size() == 1 ? pins[0] : -1;
+    if (pins.size() > 1) F->pinflag.assign(pinned.begin(), pinned.end());
     F->pidx.resize(n);
     F->sn.resize(nt);
     std::vector<int32_t> posof(n);
@@ -332,13 +363,13 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         for (int32_t p = h.first; p < lim; ++p) {
             const int32_t v = F->pidx[p];
             const int fp = p - h.first;
-            if (v == pin) {
+            if (pinned[v]) {
                 Fm[(size_t)fp * nf + fp] = 1.0;
                 continue;
             }
             for (int64_t q = A.ptr[v]; q < A.ptr[v + 1]; ++q) {
                 const int32_t u = A.col[q];
-                if (u == pin) continue;
+                if (pinned[u]) continue;
                 const int32_t pq = posof[u];
                 if (pq < h.first) continue;   // assembled in a descendant's front
                 const int fq = front_index(s, pq);
@@ -451,6 +482,12 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
         if (depth[s] == cut || (depth[s] < cut && nch[s] == 0)) roots.push_back(s);
         else if (depth[s] < cut) upper.push_back(s);
     }
+    // largest subtrees first (the loop below takes them from the back)
+    std::stable_sort(roots.begin(), roots.end(), [&](int a, int b) {
+        const int64_t wa = F->sn[a].first + F->sn[a].ni - F->sn[sub_begin[a]].first;
+        const int64_t wb = F->sn[b].first + F->sn[b].ni - F->sn[sub_begin[b]].first;
+        return wa < wb;
+    });
     omp_set_num_threads(nthreads_eff);
     std::atomic<int> pfail{0};
 #pragma omp parallel for schedule(dynamic, 1)
@@ -680,6 +717,16 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin, cons
     F->pbuf = pbuf;
     F->ntickets = tickets;
     F->nlr = (int64_t)F->lr.size();
+    if (!o.vmap.empty()) {   // matrix rows -> vector indices of the solve
+        for (int32_t& v : F->pidx) v = o.vmap[v];
+        for (int32_t& v : F->bidx) v = o.vmap[v];
+        if (F->pin >= 0) F->pin = o.vmap[F->pin];
+        if (!F->pinflag.empty()) {
+            std::vector<uint8_t> pf(o.vn, 0);
+            for (int64_t i = 0; i < n; ++i) pf[o.vmap[i]] = F->pinflag[i];
+            F->pinflag.swap(pf);
+        }
+    }
     return BID_OK;
 }
 

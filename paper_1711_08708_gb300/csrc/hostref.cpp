@@ -19,11 +19,16 @@ namespace {
 // x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
 // the same order, as the GPU launches (permuted input, per-level flat items
 // with their splits, large-cluster tasks, parent input slots).
-void replay(const HFactorHost& F, const double* b, double shift, double* x) {
+void replay(const HFactorHost& F, const double* b, double shift, double* x,
+            const std::vector<double>* vshift = nullptr) {
     std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
-    for (int64_t i = 0; i < F.n; ++i) xp[i] = F.pidx[i] == F.pin ? 0.0 : b[F.pidx[i]] - shift;
+    for (int64_t i = 0; i < F.n; ++i) {
+        const int v = F.pidx[i];
+        const bool pinned = v == F.pin || (!F.pinflag.empty() && F.pinflag[v]);
+        xp[i] = pinned ? 0.0 : b[v] - (vshift ? (*vshift)[v] : shift);
+    }
     auto incoming = [&](const HSnode& s, int f) {
         const int o = s.inc_off + 2 * f;
         return (F.inc[o] >= 0 ? inb[o] : 0.0) + (F.inc[o + 1] >= 0 ? inb[o + 1] : 0.0);
@@ -199,7 +204,7 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
     const AssembledHost& a = h->a;
     double shift = 0.0;
     if (which == 1) {
-        BID_TRY(build_hfactor(a.S1, a.coords.data(), a.dim, (int)(a.N - 1), o, &F));
+        BID_TRY(build_hfactor(a.S1, a.coords.data(), a.dim, {(int32_t)(a.N - 1)}, o, &F));
         for (int64_t i = 0; i < a.N; ++i) shift += b[i];
         shift /= (double)a.N;
     } else {
@@ -207,7 +212,7 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
         for (int64_t r = 0; r < K.n; ++r)
             for (int64_t q = K.ptr[r]; q < K.ptr[r + 1]; ++q)
                 if (K.col[q] == r) K.val[q] += gamma * a.mH[r];
-        BID_TRY(build_hfactor(K, a.coords.data(), a.dim, -1, o, &F));
+        BID_TRY(build_hfactor(K, a.coords.data(), a.dim, {}, o, &F));
     }
     replay(F, b, shift, x);
     if (stats) {
@@ -221,6 +226,58 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
         stats->lowrank_blocks = F.nlr;
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
+    }
+    return BID_OK;
+}
+
+int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, int which,
+                                double gamma, double eps, const int32_t* leaf, int leaf_default,
+                                int block, int precision, const double* b, double* x,
+                                bid_precond_stats* stats) {
+    if (!hs || nslices < 1 || !b || !x || (which != 1 && which != 2))
+        return set_error(BID_EINVAL, "bad argument");
+    if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
+    if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
+    std::vector<const AssembledHost*> A;
+    BatchHost lay;
+    lay.S = nslices;
+    lay.off.assign(1, 0);
+    lay.hoff.assign(1, 0);
+    for (int s = 0; s < nslices; ++s) {
+        if (!hs[s]) return set_error(BID_EINVAL, "NULL system %d", s);
+        A.push_back(&hs[s]->a);
+        lay.N.push_back(hs[s]->a.N);
+        lay.NH.push_back(hs[s]->a.NH);
+        lay.off.push_back(lay.off.back() + hs[s]->a.N + hs[s]->a.NH);
+        lay.hoff.push_back(lay.hoff.back() + hs[s]->a.NH);
+    }
+    HBuildOpts o;
+    o.eps = eps;
+    o.leaf = leaf_default;
+    o.block = block;
+    o.vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
+    std::vector<int32_t> lf(nslices, leaf_default);
+    if (leaf) lf.assign(leaf, leaf + nslices);
+    HFactorHost F;
+    BID_TRY(build_batch_factor(A, lay, which, gamma, o, lf, &F));
+    std::vector<double> vshift(lay.off[nslices], 0.0);
+    if (which == 1)
+        for (int s = 0; s < nslices; ++s) {
+            double m = 0.0;
+            for (int64_t i = 0; i < lay.N[s]; ++i) m += b[lay.off[s] + i];
+            m /= (double)lay.N[s];
+            for (int64_t i = 0; i < lay.N[s]; ++i) vshift[lay.off[s] + i] = m;
+        }
+    replay(F, b, 0.0, x, &vshift);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->n1 = F.n;
+        stats->supernodes1 = (int64_t)F.sn.size();
+        stats->levels1 = F.height;
+        stats->dense_entries = F.dense_entries;
+        stats->lowrank_entries = F.lowrank_entries;
+        stats->dense_blocks = F.nlarge;
+        stats->lowrank_blocks = F.nlr;
     }
     return BID_OK;
 }

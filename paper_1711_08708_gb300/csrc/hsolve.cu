@@ -138,15 +138,30 @@ __device__ __forceinline__ double vrow(const HView& v, const HSnode& sn, int q,
     return q < sn.ni ? ybuf[sn.first + q] : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
 }
 
-// xp[pos] = b[pidx[pos]] - shift, pinned entry 0
+// Input shift of a solve: one scalar mean, or one mean per segment.
+struct HShift {
+    const double* sum = nullptr;     // scalar sum (times inv_n) ...
+    double inv_n = 0.0;
+    const int16_t* seg = nullptr;    // ... or per-segment sums seg_sum[seg[i]] * seg_inv_n[seg[i]]
+    const double* seg_sum = nullptr;
+    const double* seg_inv_n = nullptr;
+};
+
+// xp[pos] = b[pidx[pos]] - shift, pinned entries 0
 __global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict__ pidx, int pin,
-                                                const double* __restrict__ b,
-                                                const double* shift_sum, double inv_n,
+                                                const uint8_t* __restrict__ pinflag,
+                                                const double* __restrict__ b, HShift sh,
                                                 double* __restrict__ xp) {
-    const double shift = shift_sum ? (*shift_sum) * inv_n : 0.0;
+    const double shift = sh.sum ? (*sh.sum) * sh.inv_n : 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int vi = pidx[i];
-        xp[i] = vi == pin ? 0.0 : b[vi] - shift;
+        const bool pinned = vi == pin || (pinflag && pinflag[vi]);
+        double sv = shift;
+        if (sh.seg) {
+            const int g = sh.seg[vi];
+            sv = sh.seg_sum[g] * sh.seg_inv_n[g];
+        }
+        xp[i] = pinned ? 0.0 : b[vi] - sv;
     }
 }
 
@@ -552,15 +567,15 @@ HView view_of(const HFactorDev& F) {
 }
 
 template <typename T, typename A>
-int run(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
-        double inv_n, const HScratch& S, double* out) {
+int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh,
+        const HScratch& S, double* out) {
     const HView v = view_of(F);
     const T* data = reinterpret_cast<const T*>(F.data);
     int launches = 1;
     {
         int64_t g = (F.n + HT - 1) / HT;
         if (g > (int64_t)L.sms * 8) g = (int64_t)L.sms * 8;
-        k_permute<<<(unsigned)g, HT, 0, L.st>>>((int)F.n, F.pidx, F.pin, in, shift_sum, inv_n, S.xp);
+        k_permute<<<(unsigned)g, HT, 0, L.st>>>((int)F.n, F.pidx, F.pin, F.pinflag, in, sh, S.xp);
     }
     const int H = (int)F.uf_ptr.size() - 1;
     for (int lev = 0; lev < H; ++lev) {
@@ -628,14 +643,32 @@ int hsolve_prepare() {
     return BID_OK;
 }
 
-int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
-                  double inv_n, const HScratch& S, double* out) {
+static int dispatch(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh,
+                    const HScratch& S, double* out) {
     switch (F.precision) {
-        case BID_FP64: return run<double, double>(L, F, in, shift_sum, inv_n, S, out);
-        case BID_FP32: return run<float, float>(L, F, in, shift_sum, inv_n, S, out);
-        case BID_BF16: return run<__nv_bfloat16, float>(L, F, in, shift_sum, inv_n, S, out);
+        case BID_FP64: return run<double, double>(L, F, in, sh, S, out);
+        case BID_FP32: return run<float, float>(L, F, in, sh, S, out);
+        case BID_BF16: return run<__nv_bfloat16, float>(L, F, in, sh, S, out);
         default: return set_error(BID_EINVAL, "bad factor precision");
     }
+}
+
+int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
+                  double inv_n, const HScratch& S, double* out) {
+    HShift sh;
+    sh.sum = shift_sum;
+    sh.inv_n = inv_n;
+    return dispatch(L, F, in, sh, S, out);
+}
+
+int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in, const int16_t* seg,
+                      const double* seg_sum, const double* seg_inv_n, const HScratch& S,
+                      double* out) {
+    HShift sh;
+    sh.seg = seg;
+    sh.seg_sum = seg_sum;
+    sh.seg_inv_n = seg_inv_n;
+    return dispatch(L, F, in, sh, S, out);
 }
 
 template <typename V>
@@ -659,6 +692,7 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     d->n = h.n;
     d->pin = h.pin;
     d->precision = precision;
+    BID_TRY(upload_vec(h.pinflag, &d->pinflag));
     BID_TRY(upload_vec(h.pidx, &d->pidx));
     BID_TRY(upload_vec(h.bidx, &d->bidx));
     BID_TRY(upload_vec(h.inc, &d->inc));
@@ -712,7 +746,7 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 void free_hfactor(HFactorDev* d) {
-    void* ptrs[] = {d->pidx, d->bidx, d->inc, d->drows, d->uout, d->vgl, d->sn, d->lr, d->ffc,
+    void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout, d->vgl, d->sn, d->lr, d->ffc,
                     d->fbc, d->ffi, d->fbi, d->ffs, d->fbs, d->uft, d->ubt, d->data};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();

@@ -146,6 +146,7 @@ struct HTask {
 struct HFactorHost {
     int64_t n = 0;
     int32_t pin = -1;                  // vector index fixed to zero, or -1
+    std::vector<uint8_t> pinflag;      // several pinned indices (block-diagonal systems)
     int32_t height = 0;
     std::vector<int32_t> pidx;         // elimination position -> vector index
     std::vector<HSnode> sn;
@@ -176,12 +177,22 @@ struct HBuildOpts {
     int block = 64;
     int threads = 0;
     int vec = 2;        // elements per 16-byte vector of the storage precision
+    // Block-diagonal matrices (several independent problems): rows
+    // [group_ptr[g], group_ptr[g+1]) form block g, which gets a cluster tree
+    // of its own (leaf size group_leaf[g], or `leaf`); the factor is a forest.
+    std::vector<int64_t> group_ptr;
+    std::vector<int32_t> group_leaf;
+    // Vector index of matrix row i in the vectors the solve reads and writes
+    // (vmap[i] < vn); empty: the identity.
+    std::vector<int32_t> vmap;
+    int64_t vn = 0;
 };
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
-// the unknowns, used by the nested dissection).  pin >= 0 replaces row and
-// column `pin` by the identity (pseudo-inverse of a singular Neumann matrix).
-int build_hfactor(const CsrHost& A, const double* coords, int dim, int pin,
-                  const HBuildOpts& o, HFactorHost* F);
+// the unknowns, used by the nested dissection).  Every index in `pins` has its
+// row and column replaced by the identity and its input entry set to zero
+// (pseudo-inverse of a singular Neumann matrix, one pin per component).
+int build_hfactor(const CsrHost& A, const double* coords, int dim,
+                  const std::vector<int32_t>& pins, const HBuildOpts& o, HFactorHost* F);
 
 // Limits shared by the build and the kernels.
 constexpr int SMALL_NI = 64;     // a cluster is small when ni <= SMALL_NI and
@@ -203,6 +214,7 @@ constexpr int LR_KMAX = 64;      // largest rank kept in a low-rank group
 struct HFactorDev {
     int64_t n = 0;
     int32_t pin = -1;
+    uint8_t* pinflag = nullptr;         // set when more than one index is pinned
     int32_t precision = BID_FP64;
     int32_t* pidx = nullptr;
     int32_t* bidx = nullptr;
@@ -300,7 +312,83 @@ int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int firs
 // (shift_sum may be NULL), with the pinned entry set to zero.
 int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in,
                   const double* shift_sum, double inv_n, const HScratch& S, double* out);
+// Same with one shift per segment (block-diagonal systems): input entry of
+// vector index i is b[i] - seg_sum[seg[i]] * seg_inv_n[seg[i]].
+int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in,
+                      const int16_t* seg, const double* seg_sum, const double* seg_inv_n,
+                      const HScratch& S, double* out);
 int hsolve_prepare();   // raise the dynamic shared-memory limit of the kernels
+
+// ---------------------------------------------------------------- batched form
+// Slice s of a batch owns the combined-vector segment [off[s], off[s+1]) laid
+// out as a single system ([U_s | V_s]); its heart-indexed arrays (gates,
+// stimulus) sit at [hoff[s], hoff[s+1]).
+struct BatchHost {
+    int S = 0;
+    std::vector<int64_t> off, hoff, N, NH;
+};
+// Factor of a batch: which = 1: the S_1 of every slice (last U unknown of each
+// pinned), which = 2: K_m = gamma M_H + S_m of every slice; one cluster tree
+// per slice (leaf size leaf[s]), vector indices in the combined layout.
+int build_batch_factor(const std::vector<const AssembledHost*>& A, const BatchHost& lay, int which,
+                       double gamma, const HBuildOpts& base, const std::vector<int32_t>& leaf,
+                       HFactorHost* F);
+
+struct BCta {              // CTA task: slice s, range [a, b) (elements or tiles)
+    int32_t s, a, b, pad;
+};
+struct BTasks {
+    const BCta* t;
+    const int32_t* ptr;    // slice s owns tasks [ptr[s], ptr[s+1])
+    int n;
+};
+struct BGeom {
+    int S;
+    const int32_t *off, *N, *NH, *hoff;
+    const double *invN, *msum;
+    const double* mdiag;   // lumped m at U positions, m_H at V positions
+};
+// 32-row SELL tiles of every slice's S_1 (sp1/col1/val1) and S_i (sp2/...;
+// empty beyond the heart rows); tile t of slice s covers local rows
+// 32 (t - tile0[s]) ...; columns are local to the slice.
+struct BSell {
+    const int32_t *sp1, *sp2, *tile0, *col1, *col2;
+    const double *val1, *val2;
+};
+// Per-slice PCG scalars (device arrays of S entries).
+struct BScal {
+    double *pq, *sumq, *alpha, *rr, *sumr, *rz, *beta, *yy, *sumb, *gen, *suma;
+    double* tol2;          // one value
+    int32_t *iter, *active, *mask, *maxit;
+    unsigned int* ticket;  // one per kernel kind
+};
+struct MsParamsB {
+    double v_rest, span, tau_in, tau_out, tau_open, tau_close, v_gate, Cm, chi, gamma, dt;
+};
+int blaunch_lambda(const Launch& L, int mode, const BGeom& g, const BSell& A, const BTasks& T,
+                   double gamma, const double* x, double* out, const double* Y, const BScal& c,
+                   double* partials);
+int blaunch_project(const Launch& L, const BGeom& g, const BTasks& T, double* r, const BScal& c,
+                    double* partials);
+int blaunch_update(const Launch& L, const BGeom& g, const BTasks& T, double* x, double* r,
+                   const double* p, const double* q, const BScal& c, double* partials);
+int blaunch_dot_rz(const Launch& L, const BGeom& g, const BTasks& T, const double* r,
+                   const double* z, const double* q, int flexible, const BScal& c,
+                   double* partials);
+int blaunch_pupdate(const Launch& L, const BTasks& T, double* p, const double* z, const BScal& c);
+int blaunch_si_residual(const Launch& L, const BGeom& g, const BSell& A, const BTasks& T,
+                        const double* r, const double* z, double* t);
+int blaunch_si_apply_sum(const Launch& L, const BGeom& g, const BSell& A, const BTasks& T,
+                         const double* z, double* w, const BScal& c, double* partials);
+int blaunch_sum_u(const Launch& L, const BGeom& g, const BTasks& T, const double* x, double* dst,
+                  const BScal& c, double* partials);
+int blaunch_axpy_sub_u(const Launch& L, const BGeom& g, const BTasks& T, double* z,
+                       const double* b);
+int blaunch_rhs_gate(const Launch& L, const BGeom& g, const BTasks& T, const double* X, double* h,
+                     const double* Ist, int stim_on, const bid_params& p, double dt, double* Y);
+int blaunch_normalise(const Launch& L, const BGeom& g, const BTasks& T, double* X, const BScal& c,
+                      double* partials);
+int blaunch_check(const Launch& L, int S, const BScal& c, unsigned long long h, int first);
 
 // ---------------------------------------------------------------- handles
 }  // namespace bid
@@ -333,4 +421,45 @@ struct bid_precond {
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap = nullptr;               // private stream used for capture only
     int g_prologue = 0, g_body = 0;           // kernels per prologue / per iteration
+};
+
+struct bid_batch {
+    int S = 0;
+    std::vector<bid_system*> sys;
+    bid::BatchHost lay;
+    bid_precond_opts opts{};
+    std::vector<int32_t> leaf;
+    double gamma = 0.0;
+    int sms = 152;
+    bid::HFactorDev F1, FK;
+    bid::HScratch hs;
+    // device geometry, tiles and tasks
+    int32_t *d_off = nullptr, *d_N = nullptr, *d_NH = nullptr, *d_hoff = nullptr;
+    double *d_invN = nullptr, *d_msum = nullptr, *mdiag = nullptr;
+    int16_t* seg = nullptr;
+    int32_t *sp1 = nullptr, *sp2 = nullptr, *tile0 = nullptr, *col1 = nullptr, *col2 = nullptr;
+    double *val1 = nullptr, *val2 = nullptr;
+    bid::BCta *vt = nullptr, *lt = nullptr, *ht = nullptr;
+    int32_t *vptr = nullptr, *lptr = nullptr, *hptr = nullptr;
+    int nvt = 0, nlt = 0, nht = 0;
+    // work vectors (combined layout)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xs = nullptr, *ytmp = nullptr;
+    double *z1b = nullptr, *t = nullptr, *w = nullptr, *partials = nullptr;
+    double* dscal = nullptr;       // per-slice double scalars
+    int32_t* iscal = nullptr;      // per-slice int scalars
+    unsigned int* tickets = nullptr;
+    void* host_pinned = nullptr;   // mirror of dscal + iscal
+    bid::BScal sc{};
+    bid_precond_stats stats{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    int g_prologue = 0, g_body = 0;
+    bid::BGeom geom() const {
+        return bid::BGeom{S, d_off, d_N, d_NH, d_hoff, d_invN, d_msum, mdiag};
+    }
+    bid::BSell sell() const { return bid::BSell{sp1, sp2, tile0, col1, col2, val1, val2}; }
+    bid::BTasks vtasks() const { return bid::BTasks{vt, vptr, nvt}; }
+    bid::BTasks ltasks() const { return bid::BTasks{lt, lptr, nlt}; }
+    bid::BTasks htasks() const { return bid::BTasks{ht, hptr, nht}; }
 };

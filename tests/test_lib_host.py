@@ -168,3 +168,52 @@ def test_host_factor_disconnected_heart(bid):
     x -= x.mean()
     xo = ob.s1_pseudo_inverse_apply(s, b)
     assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
+
+
+def _slices(count, seed, min_k, max_k, step, dt=0.1):
+    from workloads import batched_slices
+    out = []
+    for d in batched_slices(count, seed, min_k, max_k, step):
+        m = torso_square_2d(d["n"], semi_axes=d["semi_axes"], fibre_deg=d["fibre_deg"])
+        out.append((m, params_2d(dt)))
+    return out
+
+
+@pytest.mark.parametrize("precision,leaf", [("fp64", 16), ("fp32", [8, 16, 32, 16]),
+                                            ("bf16", [32, 8, 16, 64])])
+def test_host_batch_factor_forest(bid, precision, leaf):
+    # the forest factor of several slices (one tree per slice, its own leaf
+    # size, vector indices in the combined layout, one pin per slice) replays
+    # to each slice's own P_1 pseudo-inverse and K_m solve
+    sl = _slices(4, 11, 3, 9, 8)
+    hs = [bid.HostSystem(m, p) for m, p in sl]
+    ss = [ob.build_system(m, p) for m, p in sl]
+    off = np.cumsum([0] + [s.N + s.NH for s in ss])
+    rng = np.random.default_rng(5)
+    b = rng.normal(size=off[-1])
+    g = ob.gamma_of(sl[0][1], 0.1)
+    x1, st1 = bid.host_batch_factor_solve(hs, 1, b, gamma=g, leaf=leaf, precision=precision)
+    x2, _ = bid.host_batch_factor_solve(hs, 2, b, gamma=g, leaf=leaf, precision=precision)
+    assert st1["levels1"] >= 3
+    for k, s in enumerate(ss):
+        o = off[k]
+        bu, bv = b[o:o + s.N], b[o + s.N:off[k + 1]]
+        xu = x1[o:o + s.N] - x1[o:o + s.N].mean()
+        xo = ob.s1_pseudo_inverse_apply(s, bu)
+        assert np.abs(xu - xo).max() <= 1e-10 * np.abs(xo).max()
+        assert not x1[o + s.N:off[k + 1]].any()          # V entries untouched
+        xo2 = spla.spsolve(ob.monodomain_matrix(s, g).tocsc(), bv)
+        assert np.abs(x2[o + s.N:off[k + 1]] - xo2).max() <= 1e-12 * np.abs(xo2).max()
+        assert not x2[o:o + s.N].any()
+
+
+def test_host_batch_factor_errors(bid):
+    sl = _slices(2, 3, 3, 4, 8)
+    hs = [bid.HostSystem(m, p) for m, p in sl]
+    n = sum(bid.HostSystem(m, p).perm_and_mass()[0].size + bid.HostSystem(m, p).perm_and_mass()[2].size
+            for m, p in sl)
+    with pytest.raises(bid.BidError) as e:
+        bid.host_batch_factor_solve(hs, 1, np.zeros(n), leaf=[16, 2])
+    assert e.value.code == bid.EINVAL
+    with pytest.raises(bid.BidError):
+        bid.host_batch_factor_solve(hs, 3, np.zeros(n))

@@ -159,15 +159,16 @@ def stimulus_centre_ball(mesh: Mesh, radius: float = 0.1, amp: float = 50.0) -> 
     return np.where(d <= radius, amp, 0.0)
 
 
-def batched_slices(count: int = 64, seed: int = 2026, min_k: int = 4, max_k: int = 32):
-    """Seeded uneven 2D torso slices: side 1 + 32*k nodes, k ~ U{min_k..max_k},
+def batched_slices(count: int = 64, seed: int = 2026, min_k: int = 4, max_k: int = 32,
+                   step: int = 32):
+    """Seeded uneven 2D torso slices: side 1 + step*k nodes, k ~ U{min_k..max_k},
     ellipse semi-axes ~ U(1.5, 3.5) cm clipped to fit the 10 cm box with a
     0.5 cm margin, fibre angle ~ U(0, 90) deg, stimulus disc seeded per slice."""
     rng = np.random.default_rng(seed)
     out = []
     for s in range(count):
         k = int(rng.integers(min_k, max_k + 1))
-        n = 1 + 32 * k
+        n = 1 + step * k
         a = float(min(rng.uniform(1.5, 3.5), 4.5))
         b = float(min(rng.uniform(1.5, 3.5), 4.5))
         fib = float(rng.uniform(0.0, 90.0))
