@@ -12,8 +12,13 @@ headline; the plain form (exact FP64 factors) is timed on the same GPU.  The
 factor and matrix working set (GBs) is far larger than the 129 MB L2, so no
 flush is needed between steps.
 
---impl reference times the FP64 CPU oracle (pinned sparse direct solve of
-every step) on the host cores instead.
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload (see cpu_baseline).
+
+--workload batched times the batched form instead: 64 seeded torso slices
+(sides 129 ... 1025 nodes, seed 2026) advanced together, one graph launch of
+the PCG loop per step for all slices, leaf sizes from the tuner; its line
+also gives the same slices stepped one at a time for comparison.
 """
 from __future__ import annotations
 
@@ -46,6 +51,9 @@ def parse():
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
+    a.add_argument("--workload", default="slice", choices=["slice", "batched"])
+    a.add_argument("--slices", type=int, default=64)
+    a.add_argument("--no-sequential", action="store_true")
     return a.parse_args()
 
 
@@ -171,10 +179,179 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args):
+    """The batched form on one GPU (replicas of the whole batch for N > 1)."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_08708_gb300 import bid
+    from workloads import batched_slices, torso_square_2d, params_2d, stimulus_seeded_disc
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    dt = 0.1
+    p = params_2d(dt)
+    specs = batched_slices(args.slices, 2026)
+    meshes = [torso_square_2d(d["n"], semi_axes=d["semi_axes"], fibre_deg=d["fibre_deg"])
+              for d in specs]
+    systems = [bid.System(m, p) for m in meshes]
+    t0 = time.perf_counter()
+    leaf = bid.tune_batch_leaf(systems, dt, eps=args.eps, precision=args.precision,
+                               candidates=(8, 16, 32), reps=5)
+    tune_s = time.perf_counter() - t0
+    B = bid.Batch(systems, dt, eps=args.eps, precision=args.precision, leaf=leaf)
+    S = B.S
+    n, nh = B.n, int(B.hoff[-1])
+    X0 = np.zeros(n)
+    h0 = np.ones(nh)
+    ist = np.zeros(nh)
+    for k, (m, d, sy) in enumerate(zip(meshes, specs, systems)):
+        X0[B.off[k] + sy.N:B.off[k + 1]] = p["v_rest"]
+        ist[B.hoff[k]:B.hoff[k + 1]] = stimulus_seeded_disc(m, seed=d["stim_seed"])[sy.perm[:sy.NH]]
+    I = torch.tensor(ist, dtype=torch.float64, device=dev)
+
+    def timed(step_fn, nsteps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0.record(st)
+        out = [step_fn(k) for k in range(nsteps)]
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, out
+
+    X = torch.tensor(X0, dtype=torch.float64, device=dev)
+    h = torch.tensor(h0, dtype=torch.float64, device=dev)
+    tcur = [0.0]
+
+    def bstep(_):
+        its = B.step(X, h, I, tcur[0], 1, tol=args.tol)
+        tcur[0] += dt
+        return its[0]
+
+    timed(bstep, args.warmup)
+    l0 = bid.kernel_launches()
+    with Clocks(local) as ck:
+        ms, its = timed(bstep, args.steps)
+    launches = bid.kernel_launches() - l0
+    its = np.array(its)
+
+    # roofline: the P_1 forest solve of all slices, timed alone
+    b = torch.randn(n, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        B.apply_factor(1, b, x)
+    reps = 10
+    solve_ms, _ = timed(lambda k: B.apply_factor(1, b, x), reps)
+    solve_ms /= reps
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6780.7)
+    Ntot = int(sum(sy.N for sy in systems))
+    alg_bytes = B.stats["alg_bytes_p1"] + 8 * 4 * Ntot
+    achieved = alg_bytes / (solve_ms * 1e-3) / 1e9
+
+    # e2e: combined state from / to pinned host memory every step
+    hX = torch.tensor(X0, dtype=torch.float64).pin_memory()
+    hh = torch.tensor(h0, dtype=torch.float64).pin_memory()
+    Xe = torch.empty_like(X)
+    he = torch.empty_like(h)
+
+    tcur[0] = 0.0      # the same steps as the device-timed run, from the initial state
+
+    def estep(_):
+        Xe.copy_(hX, non_blocking=True)
+        he.copy_(hh, non_blocking=True)
+        B.step(Xe, he, I, tcur[0], 1, tol=args.tol)
+        hX.copy_(Xe, non_blocking=True)
+        hh.copy_(he, non_blocking=True)
+        tcur[0] += dt
+
+    e2e_ms, _ = timed(estep, args.steps)
+    io_bytes = 8 * (n + nh)
+
+    seq = None
+    if not args.no_sequential:
+        # the same slices one at a time through the single-system path
+        Ps = [bid.Precond(sy, dt, eps=args.eps, precision=args.precision, leaf=lf)
+              for sy, lf in zip(systems, leaf)]
+        Us = [torch.zeros(sy.N, dtype=torch.float64, device=dev) for sy in systems]
+        Vs = [torch.full((sy.NH,), p["v_rest"], dtype=torch.float64, device=dev) for sy in systems]
+        hs = [torch.ones(sy.NH, dtype=torch.float64, device=dev) for sy in systems]
+        Is = [I[B.hoff[k]:B.hoff[k + 1]].contiguous() for k in range(S)]
+        ts = [0.0]
+
+        def sstep(_):
+            for k in range(S):
+                Ps[k].step(Us[k], Vs[k], hs[k], Is[k], ts[0], 1, tol=args.tol)
+            ts[0] += dt
+
+        timed(sstep, args.warmup)
+        sms, _ = timed(sstep, args.steps)
+        seq = {"steps_per_s": world * args.steps / (sms * 1e-3),
+               "note": "the same slices and leaf sizes stepped one at a time (bid_step per slice)"}
+        del Ps
+
+    value = world * args.steps / (ms * 1e-3)
+    line = {
+        "metric": "bidomain batch steps/s at PCG rel-res 1e-8 (batched form, every slice "
+                  "advanced per step); HBM GB/s of the factor solve",
+        "value": value, "unit": "batch steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {
+            "workload": f"batched form: {S} torso slices, sides "
+                        f"{min(d['n'] for d in specs)}..{max(d['n'] for d in specs)} "
+                        f"(seed 2026), N total {Ntot}, N_H total {nh}, dt 0.1 ms, "
+                        "seeded stimulus discs, PCG rel-res 1e-8 per slice",
+            "form": {"eps": args.eps, "factor_precision": args.precision},
+            "slice_steps_per_s": S * value,
+            "mean_pcg_iters": float(its.mean()), "max_pcg_iters": int(its.max()),
+            "leaf": {str(v): leaf.count(v) for v in sorted(set(leaf))},
+            "tune_seconds": tune_s,
+            "l2": "inputs larger than L2 (factors and matrices several GB)",
+            "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+            "precond_stats": {k: B.stats[k] for k in (
+                "factor_bytes", "alg_bytes_p1", "alg_bytes_pk", "levels1", "levelsk",
+                "build_seconds")},
+            "sequential": seq,
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "P_1 forest solve of all slices (k_permute, k_flat_fwd, k_up_fwd, "
+                               "k_bwd_prep, k_up_bwd, k_flat_bwd over all levels)",
+                     "ms": solve_ms, "algorithmic_bytes": alg_bytes,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
+        "e2e": {"value": world / (e2e_ms / args.steps * 1e-3), "unit": "batch steps/s",
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": launches,
+        "clocks": ck.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -314,7 +491,8 @@ def main():
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "kernel": "k_hfwd+k_hbwd (one P_1 triangular pair)",
+                     "kernel": "P_1 solve: k_permute, k_flat_fwd, k_up_fwd, k_bwd_prep, "
+                               "k_up_bwd, k_flat_bwd over all tree levels",
                      "ms": solve_ms, "algorithmic_bytes": alg_bytes,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
         "e2e": {"value": world / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": io_bytes,

@@ -277,6 +277,12 @@ void bid_batch_destroy(bid_batch* B);
  * sizes and the options: a repeated query returns at once.  Blocking. */
 int bid_tune_leaf(bid_system* s, const bid_precond_opts* opts, const int32_t* cands,
                   int ncands, int reps, int32_t* best, double* ms_out);
+/* Leaf sizes for a batch: the slices are grouped in classes of half an octave
+ * of N; bid_tune_leaf runs on the slice of median N of each class and its
+ * answer is given to the whole class.  leaf_out: host array of nslices
+ * entries, ready for bid_batch_create.  Blocking. */
+int bid_tune_batch_leaf(bid_system* const* systems, int nslices, const bid_precond_opts* opts,
+                        const int32_t* cands, int ncands, int reps, int32_t* leaf_out);
 
 /* ---------------------------------------------------------------------------
  * Host-only entry points (no GPU needed).  They expose the host half of the

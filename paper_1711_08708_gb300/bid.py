@@ -101,6 +101,7 @@ SIGNATURES = {
     "bid_batch_step": (_I, [_VP, _VP, _VP, _VP, _D, _I, _D, _I, _VP, _VP]),
     "bid_batch_destroy": (None, [_VP]),
     "bid_tune_leaf": (_I, [_VP, C.POINTER(PrecondOpts), _VP, _I, _I, _VP, _VP]),
+    "bid_tune_batch_leaf": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, _I, _I, _VP]),
     "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _VP, _VP,
                                          C.POINTER(PrecondStats)]),
 }
@@ -281,6 +282,19 @@ def tune_leaf(system: System, dt, eps=0.0, precision="fp64", block=128,
     _check(lib.bid_tune_leaf(system.h, C.byref(o), _ptr(c), int(c.size), int(reps), _ptr(best),
                              _ptr(ms)))
     return int(best[0]), {int(k): float(v) for k, v in zip(c, ms)}
+
+
+def tune_batch_leaf(systems, dt, eps=0.0, precision="fp64", block=128,
+                    candidates=(8, 16, 32, 64), reps=5):
+    """bid_tune_batch_leaf: one tuned leaf size per slice (size classes of
+    half an octave, median slice of each class timed)."""
+    S = len(systems)
+    arr = (_VP * S)(*[s.h.value for s in systems])
+    o = _opts(dt, eps, precision, 16, block, 0)
+    c = np.ascontiguousarray(candidates, dtype=np.int32)
+    out = np.zeros(S, dtype=np.int32)
+    _check(lib.bid_tune_batch_leaf(arr, S, C.byref(o), _ptr(c), int(c.size), int(reps), _ptr(out)))
+    return [int(v) for v in out]
 
 
 class Batch:

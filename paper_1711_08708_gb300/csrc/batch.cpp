@@ -639,4 +639,25 @@ int bid_tune_leaf(bid_system* s, const bid_precond_opts* o, const int32_t* cands
     return BID_OK;
 }
 
+int bid_tune_batch_leaf(bid_system* const* systems, int nslices, const bid_precond_opts* o,
+                        const int32_t* cands, int ncands, int reps, int32_t* leaf_out) {
+    if (!systems || nslices < 1 || !o || !leaf_out) return set_error(BID_EINVAL, "bad argument");
+    // size classes of half an octave in N; the slice of median N in a class
+    // stands for the class
+    std::map<int, std::vector<int>> cls;
+    for (int s = 0; s < nslices; ++s) {
+        if (!systems[s]) return set_error(BID_EINVAL, "NULL system %d", s);
+        cls[(int)std::floor(2.0 * std::log2((double)systems[s]->host.N))].push_back(s);
+    }
+    for (auto& kv : cls) {
+        std::vector<int>& m = kv.second;
+        std::stable_sort(m.begin(), m.end(),
+                         [&](int a, int b) { return systems[a]->host.N < systems[b]->host.N; });
+        int32_t best = 0;
+        BID_TRY(bid_tune_leaf(systems[m[m.size() / 2]], o, cands, ncands, reps, &best, nullptr));
+        for (int s : m) leaf_out[s] = best;
+    }
+    return BID_OK;
+}
+
 }  // extern "C"

@@ -258,3 +258,17 @@ def test_full_size_batch_properties(bid):
             L = ob.system_matrix(o, g)
             assert np.linalg.norm(L @ Xa[a:e] - Y) <= 1.0001e-8 * np.linalg.norm(Y), (step, k)
             assert abs(Xa[a:a + o.N] @ o.M.diagonal()) <= 1e-10 * np.abs(Xa[a:e]).max() * o.M.sum()
+
+
+def test_tune_batch_leaf_per_size_class(bid, small):
+    sl, systems = small
+    leaf = bid.tune_batch_leaf(systems, 0.1, eps=1e-3, precision="fp32", candidates=(8, 16),
+                               reps=2)
+    assert len(leaf) == len(systems) and set(leaf) <= {8, 16}
+    import math
+    cls = {}
+    for S, lf in zip(systems, leaf):
+        cls.setdefault(math.floor(2 * math.log2(S.N)), set()).add(lf)
+    assert all(len(v) == 1 for v in cls.values())   # one answer per size class
+    B = bid.Batch(systems, 0.1, eps=1e-3, precision="fp32", leaf=leaf)
+    assert B.leaf == leaf
