@@ -27,6 +27,13 @@
  *    allocated per solve or per step: work vectors live in the preconditioner.
  *  - Handles are not thread safe: one thread (and one stream at a time) per
  *    preconditioner handle.
+ *  - The PCG loop of bid_solve / bid_step (and of the batched calls) runs as a
+ *    CUDA graph whose WHILE condition is set on the device, so one solve costs
+ *    one graph launch and one host read.  With the environment variable
+ *    BID_PCG_GRAPH=0 (read once per process) the host launches the same
+ *    kernels in the same order instead and reads the condition after every
+ *    iteration: same results, for profilers that do not see kernels inside
+ *    graphs with conditional nodes.
  */
 #ifndef BID_H
 #define BID_H

@@ -222,7 +222,7 @@ int bbuild_graph(bid_batch* B) {
     BID_CUDA_TRY(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
     int rc = blaunch_lambda(L, 1, g, A, B->ltasks(), B->gamma, B->xs, B->r, B->ytmp, B->sc, B->partials);
     if (rc == BID_OK) rc = blaunch_project(L, g, B->vtasks(), B->r, B->sc, B->partials);
-    if (rc == BID_OK) rc = blaunch_check(L, B->S, B->sc, h, 1);
+    if (rc == BID_OK) rc = blaunch_check(L, B->S, B->sc, h, 1, 1);
     cudaError_t e = cudaStreamEndCapture(B->cap, &pro);
     if (rc != BID_OK) return rc;
     if (e != cudaSuccess) return set_error(BID_ECUDA, "prologue capture: %s", cudaGetErrorString(e));
@@ -246,7 +246,7 @@ int bbuild_graph(bid_batch* B) {
     if (rc == BID_OK)
         rc = blaunch_lambda(L, 0, g, A, B->ltasks(), B->gamma, B->p, B->q, nullptr, B->sc, B->partials);
     if (rc == BID_OK) rc = blaunch_update(L, g, B->vtasks(), B->xs, B->r, B->p, B->q, B->sc, B->partials);
-    if (rc == BID_OK) rc = blaunch_check(L, B->S, B->sc, h, 0);
+    if (rc == BID_OK) rc = blaunch_check(L, B->S, B->sc, h, 1, 0);
     cudaGraph_t body_out = nullptr;
     e = cudaStreamEndCapture(B->cap, &body_out);
     if (rc != BID_OK) return rc;
@@ -274,9 +274,30 @@ int bread(bid_batch* B, cudaStream_t st, HostScal* h) {
     double* hd = static_cast<double*>(B->host_pinned);
     int32_t* hi = reinterpret_cast<int32_t*>(hd + ND * S + 1);
     BID_CUDA_TRY(cudaMemcpyAsync(hd, B->dscal, sizeof(double) * (ND * S + 1), cudaMemcpyDeviceToHost, st));
-    BID_CUDA_TRY(cudaMemcpyAsync(hi, B->iscal, sizeof(int32_t) * NI * S, cudaMemcpyDeviceToHost, st));
+    BID_CUDA_TRY(cudaMemcpyAsync(hi, B->iscal, sizeof(int32_t) * (NI * S + 1), cudaMemcpyDeviceToHost, st));
     BID_CUDA_TRY(cudaStreamSynchronize(st));
     *h = HostScal{hd, hi, S};
+    return BID_OK;
+}
+
+// The loop of bbuild_graph launched from the host (BID_PCG_GRAPH=0).
+int bloop_host(bid_batch* B, const Launch& L, cudaStream_t st, HostScal* h) {
+    const BGeom g = B->geom();
+    const BSell A = B->sell();
+    const int flexible = B->opts.precision != BID_FP64;
+    BID_TRY(blaunch_lambda(L, 1, g, A, B->ltasks(), B->gamma, B->xs, B->r, B->ytmp, B->sc, B->partials));
+    BID_TRY(blaunch_project(L, g, B->vtasks(), B->r, B->sc, B->partials));
+    BID_TRY(blaunch_check(L, B->S, B->sc, 0, 0, 1));
+    BID_TRY(bread(B, st, h));
+    while (h->i[NI * B->S]) {
+        BID_TRY(bprecond(B, L, B->r, B->z));
+        BID_TRY(blaunch_dot_rz(L, g, B->vtasks(), B->r, B->z, B->q, flexible, B->sc, B->partials));
+        BID_TRY(blaunch_pupdate(L, B->vtasks(), B->p, B->z, B->sc));
+        BID_TRY(blaunch_lambda(L, 0, g, A, B->ltasks(), B->gamma, B->p, B->q, nullptr, B->sc, B->partials));
+        BID_TRY(blaunch_update(L, g, B->vtasks(), B->xs, B->r, B->p, B->q, B->sc, B->partials));
+        BID_TRY(blaunch_check(L, B->S, B->sc, 0, 0, 0));
+        BID_TRY(bread(B, st, h));
+    }
     return BID_OK;
 }
 
@@ -288,7 +309,8 @@ int bsolve(bid_batch* B, const double* Y, double* X, double tol, int max_iter,
     const int S = B->S;
     const int64_t n = B->lay.off[S];
     Launch L = blaunch(B, st);
-    BID_TRY(bbuild_graph(B));
+    const bool graph = pcg_graph_enabled();
+    if (graph) BID_TRY(bbuild_graph(B));
     if (Y != B->ytmp) BID_CUDA_TRY(cudaMemcpyAsync(B->ytmp, Y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     if (X != B->xs) BID_CUDA_TRY(cudaMemcpyAsync(B->xs, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     std::vector<bid_solve_info> inf(S);
@@ -300,11 +322,15 @@ int bsolve(bid_batch* B, const double* Y, double* X, double tol, int max_iter,
     for (int attempt = 0; attempt < 2; ++attempt) {
         BID_CUDA_TRY(cudaMemcpyAsync(B->sc.mask, mask.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
         BID_CUDA_TRY(cudaMemcpyAsync(B->sc.maxit, maxit.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
-        BID_CUDA_TRY(cudaGraphLaunch(B->gexec, st));
-        BID_TRY(bread(B, st, &h));
-        int body = 0;
-        for (int s = 0; s < S; ++s) body = std::max(body, mask[s] ? h.iter(s) : 0);
-        count_launches(B->g_prologue + B->g_body * body);
+        if (graph) {
+            BID_CUDA_TRY(cudaGraphLaunch(B->gexec, st));
+            BID_TRY(bread(B, st, &h));
+            int body = 0;
+            for (int s = 0; s < S; ++s) body = std::max(body, mask[s] ? h.iter(s) : 0);
+            count_launches(B->g_prologue + B->g_body * body);
+        } else {
+            BID_TRY(bloop_host(B, L, st, &h));
+        }
         for (int s = 0; s < S; ++s) {
             if (!mask[s]) continue;
             bid_solve_info& f = inf[s];
@@ -444,16 +470,16 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     const int maxcta = std::max(B->nvt, std::max(B->nlt, B->nht));
     if (rc == BID_OK) rc = dalloc(&B->partials, (int64_t)maxcta * 3);
     if (rc == BID_OK) rc = dalloc(&B->dscal, (int64_t)ND * nslices + 1);
-    if (rc == BID_OK) rc = dalloc(&B->iscal, (int64_t)NI * nslices);
+    if (rc == BID_OK) rc = dalloc(&B->iscal, (int64_t)NI * nslices + 1);
     if (rc == BID_OK) rc = dalloc(&B->tickets, 16);
     if (rc == BID_OK &&
-        cudaMallocHost(&B->host_pinned, sizeof(double) * (ND * nslices + 1) + sizeof(int32_t) * NI * nslices) !=
+        cudaMallocHost(&B->host_pinned, sizeof(double) * (ND * nslices + 1) + sizeof(int32_t) * (NI * nslices + 1)) !=
             cudaSuccess)
         rc = set_error(BID_ENOMEM, "pinned host allocation failed");
     if (rc == BID_OK && (cudaMemset(B->hs.tickets, 0, sizeof(unsigned int) * ntk) != cudaSuccess ||
                          cudaMemset(B->tickets, 0, sizeof(unsigned int) * 16) != cudaSuccess ||
                          cudaMemset(B->dscal, 0, sizeof(double) * (ND * nslices + 1)) != cudaSuccess ||
-                         cudaMemset(B->iscal, 0, sizeof(int32_t) * NI * nslices) != cudaSuccess ||
+                         cudaMemset(B->iscal, 0, sizeof(int32_t) * (NI * nslices + 1)) != cudaSuccess ||
                          cudaMemset(B->w, 0, sizeof(double) * n) != cudaSuccess ||
                          cudaMemset(B->p, 0, sizeof(double) * n) != cudaSuccess ||
                          cudaMemset(B->q, 0, sizeof(double) * n) != cudaSuccess ||
@@ -468,7 +494,8 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     double* d = B->dscal;
     B->sc = BScal{d,         d + S,     d + 2 * S, d + 3 * S, d + 4 * S, d + 5 * S,
                   d + 6 * S, d + 7 * S, d + 8 * S, d + 9 * S, d + 10 * S, d + 11 * S,
-                  B->iscal,  B->iscal + S, B->iscal + 2 * S, B->iscal + 3 * S, B->tickets};
+                  B->iscal,  B->iscal + S, B->iscal + 2 * S, B->iscal + 3 * S, B->iscal + 4 * S,
+                  B->tickets};
     bid_precond_stats& st = B->stats;
     st.n1 = h1.n;
     st.nk = hk.n;

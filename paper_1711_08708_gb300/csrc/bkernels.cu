@@ -380,9 +380,10 @@ __global__ void __launch_bounds__(TPB) k_bsub_scalar(BGeom g, BTasks T, double* 
 // slice is active iff mask[s] and it has not converged; otherwise an active
 // slice counts one more iteration and stays active while ||r||^2 > tol^2
 // ||Y||^2, the residual is finite and fewer than maxit[s] iterations are done.
-// The WHILE condition continues while any slice is active.
+// The loop (WHILE condition, or c.go for a host-driven loop) continues while
+// any slice is active.
 __global__ void __launch_bounds__(TPB) k_bcheck(int S, BScal c, cudaGraphConditionalHandle h,
-                                                int first) {
+                                                int use_graph, int first) {
     const double tol2 = c.tol2[0];
     int any = 0;
     for (int s = threadIdx.x; s < S; s += TPB) {
@@ -402,7 +403,10 @@ __global__ void __launch_bounds__(TPB) k_bcheck(int S, BScal c, cudaGraphConditi
         any |= act;
     }
     any = __syncthreads_or(any);
-    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        if (use_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
+        else *c.go = any ? 1 : 0;
+    }
 }
 
 int check(const char* what) {
@@ -484,8 +488,9 @@ int blaunch_normalise(const Launch& L, const BGeom& g, const BTasks& T, double* 
     k_bsub_scalar<<<T.n, TPB, 0, L.st>>>(g, T, X, c);
     return check("bsub_scalar");
 }
-int blaunch_check(const Launch& L, int S, const BScal& c, unsigned long long h, int first) {
-    k_bcheck<<<1, TPB, 0, L.st>>>(S, c, (cudaGraphConditionalHandle)h, first);
+int blaunch_check(const Launch& L, int S, const BScal& c, unsigned long long h, int use_graph,
+                  int first) {
+    k_bcheck<<<1, TPB, 0, L.st>>>(S, c, (cudaGraphConditionalHandle)h, use_graph, first);
     return check("bcheck");
 }
 

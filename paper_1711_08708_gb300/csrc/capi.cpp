@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -19,6 +20,14 @@ static thread_local char g_err[1024] = "";
 static std::atomic<int64_t> g_launches{0};
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool pcg_graph_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("BID_PCG_GRAPH");
+        return !(v && std::strcmp(v, "0") == 0);
+    }();
+    return on;
+}
 
 int set_error(int code, const char* fmt, ...) {
     va_list ap;
@@ -148,7 +157,7 @@ int build_graph(bid_precond* P) {
     int rc = launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp, P->sc,
                            P->partials);
     if (rc == BID_OK) rc = launch_project(L, N, NH, P->r, P->sc, P->partials);
-    if (rc == BID_OK) rc = launch_check(L, P->sc, h, 1);
+    if (rc == BID_OK) rc = launch_check(L, P->sc, h, 1, 1);
     cudaError_t e = cudaStreamEndCapture(P->cap, &pro);
     if (rc != BID_OK) return rc;
     if (e != cudaSuccess) return set_error(BID_ECUDA, "prologue capture: %s", cudaGetErrorString(e));
@@ -173,7 +182,7 @@ int build_graph(bid_precond* P) {
         rc = launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc,
                            P->partials);
     if (rc == BID_OK) rc = launch_update(L, N, NH, P->xs, P->r, P->p, P->q, P->sc, P->partials);
-    if (rc == BID_OK) rc = launch_check(L, P->sc, h, 0);
+    if (rc == BID_OK) rc = launch_check(L, P->sc, h, 1, 0);
     cudaGraph_t body_out = nullptr;
     e = cudaStreamEndCapture(P->cap, &body_out);
     if (rc != BID_OK) return rc;
@@ -185,6 +194,30 @@ int build_graph(bid_precond* P) {
     return BID_OK;
 }
 
+// The PCG loop of build_graph, launched from the host (BID_PCG_GRAPH=0): the
+// same kernels in the same order, the condition read after every iteration.
+int run_loop_host(bid_precond* P, const Launch& L, cudaStream_t st, DevScalars* h) {
+    bid_system* s = P->sys;
+    const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
+    const int flexible = P->opts.precision != BID_FP64;
+    BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp, P->sc,
+                          P->partials));
+    BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+    BID_TRY(launch_check(L, P->sc, 0, 0, 1));
+    BID_TRY(read_scalars(P, st, h));
+    while (h->go) {
+        BID_TRY(precond_apply(P, L, P->r, P->z));
+        BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, -1, P->sc, P->partials));
+        BID_TRY(launch_pupdate(L, n, P->p, P->z, -1, P->sc));
+        BID_TRY(launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc,
+                              P->partials));
+        BID_TRY(launch_update(L, N, NH, P->xs, P->r, P->p, P->q, P->sc, P->partials));
+        BID_TRY(launch_check(L, P->sc, 0, 0, 0));
+        BID_TRY(read_scalars(P, st, h));
+    }
+    return BID_OK;
+}
+
 // Step 2 on X (in: guess, out: solution) for right-hand side Y; X and Y may be
 // the preconditioner's own xs / ytmp (no copy then).
 int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_iter,
@@ -192,7 +225,8 @@ int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_i
     bid_system* s = P->sys;
     const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
     Launch L = launch_of(s, st);
-    BID_TRY(build_graph(P));
+    const bool graph = pcg_graph_enabled();
+    if (graph) BID_TRY(build_graph(P));
     if (Y != P->ytmp) BID_CUDA_TRY(cudaMemcpyAsync(P->ytmp, Y, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     if (X != P->xs) BID_CUDA_TRY(cudaMemcpyAsync(P->xs, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     bid_solve_info inf{};
@@ -207,9 +241,13 @@ int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_i
             int iter, max_iter;
         } lim{tol * tol, 0, max_iter - iters};
         BID_CUDA_TRY(cudaMemcpyAsync(&P->sc->tol2, &lim, sizeof(lim), cudaMemcpyHostToDevice, st));
-        BID_CUDA_TRY(cudaGraphLaunch(P->gexec, st));
-        BID_TRY(read_scalars(P, st, &h));
-        count_launches(P->g_prologue + P->g_body * h.iter);
+        if (graph) {
+            BID_CUDA_TRY(cudaGraphLaunch(P->gexec, st));
+            BID_TRY(read_scalars(P, st, &h));
+            count_launches(P->g_prologue + P->g_body * h.iter);
+        } else {
+            BID_TRY(run_loop_host(P, L, st, &h));
+        }
         iters += h.iter;
         if (attempt == 0) inf.relres_true = h.yy > 0 ? std::sqrt(h.rr / h.yy) : 0.0;
         if (!std::isfinite(h.yy) || !std::isfinite(h.rr)) {

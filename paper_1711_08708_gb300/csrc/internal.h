@@ -267,6 +267,7 @@ struct DevScalars {
     double gen[4];
     double tol2;            // tol^2 of the running solve (device-resident loop)
     int iter, max_iter;     // iterations done / allowed
+    int go, pad0;           // loop condition when the loop runs from the host
     unsigned int ticket[16];
 };
 
@@ -303,10 +304,16 @@ int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, dou
 int launch_normalise(const Launch& L, int64_t N, double* U, const double* m,
                      double msum, DevScalars* sc, double* partials);
 // One-thread convergence check of the device-resident PCG loop: first != 0
-// resets the iteration count, otherwise it is incremented; the WHILE
-// condition `h` is set to continue iff ||r||^2 > tol^2 ||Y||^2, the residual is
-// finite and fewer than max_iter iterations are done.
-int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int first);
+// resets the iteration count, otherwise it is incremented; the loop continues
+// iff ||r||^2 > tol^2 ||Y||^2, the residual is finite and fewer than max_iter
+// iterations are done.  The answer goes to the WHILE condition `h` when
+// use_graph != 0, else to sc->go (host-driven loop).
+int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int use_graph, int first);
+// The PCG loops run as CUDA graphs with a device-side WHILE condition unless
+// the environment sets BID_PCG_GRAPH=0: then the host launches the same
+// kernels in the same order and reads the condition after every iteration
+// (for profilers that do not see kernels inside graphs with conditional nodes).
+bool pcg_graph_enabled();
 // x = P^-1 b over a hierarchical factor: forward pass level by level (leaves
 // first), then backward pass.  The input entries are b[i] - shift_sum*inv_n
 // (shift_sum may be NULL), with the pinned entry set to zero.
@@ -360,6 +367,7 @@ struct BScal {
     double *pq, *sumq, *alpha, *rr, *sumr, *rz, *beta, *yy, *sumb, *gen, *suma;
     double* tol2;          // one value
     int32_t *iter, *active, *mask, *maxit;
+    int32_t* go;           // loop condition when the loop runs from the host
     unsigned int* ticket;  // one per kernel kind
 };
 struct MsParamsB {
@@ -388,7 +396,8 @@ int blaunch_rhs_gate(const Launch& L, const BGeom& g, const BTasks& T, const dou
                      const double* Ist, int stim_on, const bid_params& p, double dt, double* Y);
 int blaunch_normalise(const Launch& L, const BGeom& g, const BTasks& T, double* X, const BScal& c,
                       double* partials);
-int blaunch_check(const Launch& L, int S, const BScal& c, unsigned long long h, int first);
+int blaunch_check(const Launch& L, int S, const BScal& c, unsigned long long h, int use_graph,
+                  int first);
 
 // ---------------------------------------------------------------- handles
 }  // namespace bid

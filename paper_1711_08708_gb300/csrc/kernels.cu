@@ -380,12 +380,13 @@ __global__ void __launch_bounds__(TPB) k_sub_scalar(int N, double* __restrict__ 
         U[i] -= a;
 }
 
-__global__ void k_check(DevScalars* sc, cudaGraphConditionalHandle h, int first) {
+__global__ void k_check(DevScalars* sc, cudaGraphConditionalHandle h, int use_graph, int first) {
     const int it = first ? 0 : sc->iter + 1;
     sc->iter = it;
     const double rr = sc->rr, yy = sc->yy;
     const bool go = yy > 0.0 && isfinite(rr) && rr > sc->tol2 * yy && it < sc->max_iter;
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (use_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
+    else sc->go = go ? 1 : 0;
 }
 
 int check_launch(const char* what) {
@@ -467,8 +468,8 @@ int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, dou
                                                       Y);
     return check_launch("rhs_gate");
 }
-int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int first) {
-    k_check<<<1, 1, 0, L.st>>>(sc, (cudaGraphConditionalHandle)h, first);
+int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int use_graph, int first) {
+    k_check<<<1, 1, 0, L.st>>>(sc, (cudaGraphConditionalHandle)h, use_graph, first);
     return check_launch("check");
 }
 int launch_normalise(const Launch& L, int64_t N, double* U, const double* m, double msum,

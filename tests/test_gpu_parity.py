@@ -252,3 +252,50 @@ def test_full_size_513_properties(bid):
 
 def test_full_size_2049_properties(bid):
     _full_size_properties(bid, 2049, 2, 1e-3, "fp32")
+
+
+_HOST_LOOP_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_08708_gb300 import bid
+from workloads import torso_square_2d, params_2d
+from oracle import bidomain as ob
+mesh, p = torso_square_2d(65), params_2d(0.25)
+S = bid.System(mesh, p)
+P = bid.Precond(S, p["dt"], eps=1e-3, precision="fp32")
+o = ob.build_system(mesh, p)
+Y = ob.rhs(o, p["v_rest"] + 100 * np.random.default_rng(5).random(o.NH), np.ones(o.NH),
+           np.zeros(o.NH), 5.0, p["dt"])
+X = torch.zeros(o.N + o.NH, dtype=torch.float64, device="cuda")
+info = P.solve(torch.tensor(Y, device="cuda"), X, tol=1e-10)
+S2 = bid.System(torso_square_2d(49, semi_axes=(2.0, 3.0)), p)
+B = bid.Batch([S, S2], p["dt"], eps=1e-3, precision="fp32")
+Yb = np.zeros(B.n)
+Yb[:o.N + o.NH] = Y
+Yb[o.N + o.NH + S2.N:] = 10.0 * S2.mH
+Xb = torch.zeros(B.n, dtype=torch.float64, device="cuda")
+binfo, _ = B.solve(torch.tensor(Yb, device="cuda"), Xb, tol=1e-10)
+np.save(sys.argv[2], np.concatenate([X.cpu().numpy(), [info["iters"]], Xb.cpu().numpy(),
+                                     [i["iters"] for i in binfo]]))
+"""
+
+
+@pytest.mark.parametrize("graph", ["1", "0"])
+def test_host_driven_loop_equals_graph_loop(bid, tmp_path, graph):
+    # BID_PCG_GRAPH=0 launches the graph's kernels from the host: the same
+    # iterates, bit for bit
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "s.py"
+    script.write_text(_HOST_LOOP_SCRIPT)
+    out = {}
+    for g in ("1", graph):
+        f = tmp_path / f"x{g}.npy"
+        env = dict(os.environ, BID_PCG_GRAPH=g)
+        subprocess.run([sys.executable, str(script), root, str(f)], check=True, env=env,
+                       timeout=600)
+        out[g] = np.load(f)
+    assert out["1"][-1] >= 1
+    assert np.array_equal(out["1"], out[graph])
