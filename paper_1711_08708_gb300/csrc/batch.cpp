@@ -274,7 +274,7 @@ int bread(bid_batch* B, cudaStream_t st, HostScal* h) {
     double* hd = static_cast<double*>(B->host_pinned);
     int32_t* hi = reinterpret_cast<int32_t*>(hd + ND * S + 1);
     BID_CUDA_TRY(cudaMemcpyAsync(hd, B->dscal, sizeof(double) * (ND * S + 1), cudaMemcpyDeviceToHost, st));
-    BID_CUDA_TRY(cudaMemcpyAsync(hi, B->iscal, sizeof(int32_t) * (NI * S + 1), cudaMemcpyDeviceToHost, st));
+    BID_CUDA_TRY(cudaMemcpyAsync(hi, B->iscal, sizeof(int32_t) * (NI * S + 2), cudaMemcpyDeviceToHost, st));
     BID_CUDA_TRY(cudaStreamSynchronize(st));
     *h = HostScal{hd, hi, S};
     return BID_OK;
@@ -330,6 +330,11 @@ int bsolve(bid_batch* B, const double* Y, double* X, double tol, int max_iter,
             count_launches(B->g_prologue + B->g_body * body);
         } else {
             BID_TRY(bloop_host(B, L, st, &h));
+        }
+        if (h.i[NI * S + 1]) {   // a bounded wait of a factor solve expired
+            BID_CUDA_TRY(cudaMemsetAsync(B->hs.err, 0, sizeof(unsigned int), st));
+            BID_CUDA_TRY(cudaStreamSynchronize(st));
+            return set_error(BID_ETIMEOUT, "a bounded device wait of the factor solve expired");
         }
         for (int s = 0; s < S; ++s) {
             if (!mask[s]) continue;
@@ -461,7 +466,6 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     const int64_t nf = std::max(h1.n, hk.n);
     if (rc == BID_OK) rc = dalloc(&B->hs.ybuf, nf);
     if (rc == BID_OK) rc = dalloc(&B->hs.xp, nf);
-    if (rc == BID_OK) rc = dalloc(&B->hs.inb, std::max(h1.nslots, hk.nslots));
     if (rc == BID_OK) rc = dalloc(&B->hs.vbuf, std::max(h1.vbuf, hk.vbuf));
     if (rc == BID_OK) rc = dalloc(&B->hs.tbuf, std::max(h1.tbuf, hk.tbuf));
     if (rc == BID_OK) rc = dalloc(&B->hs.pbuf, std::max(h1.pbuf, hk.pbuf));
@@ -470,16 +474,16 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     const int maxcta = std::max(B->nvt, std::max(B->nlt, B->nht));
     if (rc == BID_OK) rc = dalloc(&B->partials, (int64_t)maxcta * 3);
     if (rc == BID_OK) rc = dalloc(&B->dscal, (int64_t)ND * nslices + 1);
-    if (rc == BID_OK) rc = dalloc(&B->iscal, (int64_t)NI * nslices + 1);
+    if (rc == BID_OK) rc = dalloc(&B->iscal, (int64_t)NI * nslices + 2);   // + go, error word
     if (rc == BID_OK) rc = dalloc(&B->tickets, 16);
     if (rc == BID_OK &&
-        cudaMallocHost(&B->host_pinned, sizeof(double) * (ND * nslices + 1) + sizeof(int32_t) * (NI * nslices + 1)) !=
+        cudaMallocHost(&B->host_pinned, sizeof(double) * (ND * nslices + 1) + sizeof(int32_t) * (NI * nslices + 2)) !=
             cudaSuccess)
         rc = set_error(BID_ENOMEM, "pinned host allocation failed");
     if (rc == BID_OK && (cudaMemset(B->hs.tickets, 0, sizeof(unsigned int) * ntk) != cudaSuccess ||
                          cudaMemset(B->tickets, 0, sizeof(unsigned int) * 16) != cudaSuccess ||
                          cudaMemset(B->dscal, 0, sizeof(double) * (ND * nslices + 1)) != cudaSuccess ||
-                         cudaMemset(B->iscal, 0, sizeof(int32_t) * (NI * nslices + 1)) != cudaSuccess ||
+                         cudaMemset(B->iscal, 0, sizeof(int32_t) * (NI * nslices + 2)) != cudaSuccess ||
                          cudaMemset(B->w, 0, sizeof(double) * n) != cudaSuccess ||
                          cudaMemset(B->p, 0, sizeof(double) * n) != cudaSuccess ||
                          cudaMemset(B->q, 0, sizeof(double) * n) != cudaSuccess ||
@@ -491,6 +495,7 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
         return rc;
     }
     const int S = nslices;
+    B->hs.err = reinterpret_cast<unsigned int*>(B->iscal + NI * S + 1);
     double* d = B->dscal;
     B->sc = BScal{d,         d + S,     d + 2 * S, d + 3 * S, d + 4 * S, d + 5 * S,
                   d + 6 * S, d + 7 * S, d + 8 * S, d + 9 * S, d + 10 * S, d + 11 * S,

@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(TPB) k_bsub_scalar(BGeom g, BTasks T, double* 
 __global__ void __launch_bounds__(TPB) k_bcheck(int S, BScal c, cudaGraphConditionalHandle h,
                                                 int use_graph, int first) {
     const double tol2 = c.tol2[0];
+    const bool failed = c.go[1] != 0;   // error word of the factor solves
     int any = 0;
     for (int s = threadIdx.x; s < S; s += TPB) {
         const double rr = c.rr[s], yy = c.yy[s];
@@ -399,6 +400,7 @@ __global__ void __launch_bounds__(TPB) k_bcheck(int S, BScal c, cudaGraphConditi
         } else {
             act = 0;
         }
+        if (failed) act = 0;
         c.active[s] = act;
         any |= act;
     }

@@ -249,6 +249,12 @@ int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_i
             BID_TRY(run_loop_host(P, L, st, &h));
         }
         iters += h.iter;
+        if (h.herr) {   // a bounded wait of a factor solve expired: results are invalid
+            const unsigned int zero = 0;
+            BID_CUDA_TRY(cudaMemcpyAsync(&P->sc->herr, &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+            BID_CUDA_TRY(cudaStreamSynchronize(st));
+            return set_error(BID_ETIMEOUT, "a bounded device wait of the factor solve expired");
+        }
         if (attempt == 0) inf.relres_true = h.yy > 0 ? std::sqrt(h.rr / h.yy) : 0.0;
         if (!std::isfinite(h.yy) || !std::isfinite(h.rr)) {
             inf.status = BID_ESTAGNATE;
@@ -416,7 +422,6 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (rc == BID_OK) rc = dalloc(&P->w, N);
     if (rc == BID_OK) rc = dalloc(&P->hs.ybuf, N);
     if (rc == BID_OK) rc = dalloc(&P->hs.xp, N);
-    if (rc == BID_OK) rc = dalloc(&P->hs.inb, std::max(h1.nslots, hk.nslots));
     if (rc == BID_OK) rc = dalloc(&P->hs.vbuf, std::max(h1.vbuf, hk.vbuf));
     if (rc == BID_OK) rc = dalloc(&P->hs.tbuf, std::max(h1.tbuf, hk.tbuf));
     if (rc == BID_OK) rc = dalloc(&P->hs.pbuf, std::max(h1.pbuf, hk.pbuf));
@@ -425,6 +430,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
         rc = set_error(BID_ECUDA, "cudaMemset failed");
     if (rc == BID_OK) rc = dalloc(&P->partials, (int64_t)s->sms * 8 * 4);
     if (rc == BID_OK) rc = dalloc(&P->sc, 1);
+    if (rc == BID_OK) P->hs.err = &P->sc->herr;
     if (rc == BID_OK && cudaMallocHost(&P->host_pinned, sizeof(DevScalars)) != cudaSuccess)
         rc = set_error(BID_ENOMEM, "pinned host allocation failed");
     if (rc == BID_OK && (cudaMemset(P->w, 0, sizeof(double) * N) != cudaSuccess ||

@@ -256,6 +256,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
                 posof[v] = pos++;
             }
             nch[s] = t.nchild;
+            h.nchild = t.nchild;
             depth[s] = t.depth;
             for (int k = 0; k < t.nchild; ++k) {
                 ch[s][k] = sid[t.child[k]];
@@ -510,9 +511,26 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     if (fail) return set_error(BID_EINVAL, "factorisation: non-positive pivot (matrix not SPD)");
 
     // ---------------- pack
+    const int H = maxh + 1;
+    F->height = H;
+    std::vector<std::vector<int>> bylev(H);
+    for (int s = 0; s < nt; ++s) bylev[F->sn[s].height].push_back(s);
+    std::vector<int64_t> blk_end(nt, 0);   // end (elements) of each cluster's data block
     {
-        // every cluster starts on a vec boundary; vec trailing zeros let the last
-        // vector load of the last column stay inside the array
+        // data order: the small clusters level by level, leaves first (the flat
+        // groups of a level are runs of this order, so a group's data is one
+        // contiguous block), then the large clusters.  Every cluster starts on
+        // a vec boundary; 2 vec trailing zeros keep the last vector load of the
+        // last column inside the array.
+        std::vector<int32_t> old_inc(nt);
+        for (int s2 = 0; s2 < nt; ++s2) old_inc[s2] = F->sn[s2].inc_off;
+        std::vector<int> order;
+        order.reserve(nt);
+        for (int L = 0; L < H; ++L)
+            for (int s : bylev[L])
+                if (!F->sn[s].large) order.push_back(s);
+        for (int s = 0; s < nt; ++s)
+            if (F->sn[s].large) order.push_back(s);
         auto up = [vec](int64_t x) { return (x + vec - 1) / vec * vec; };
         int64_t total = 0, nd_rows = 0;
         for (int s = 0; s < nt; ++s) {
@@ -522,7 +540,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         F->data.assign(total + 2 * vec, 0.0);
         F->drows.reserve(nd_rows);
         int64_t off = 0;
-        for (int s = 0; s < nt; ++s) {
+        for (int s : order) {
             SnWork& w = W[s];
             HSnode& h = F->sn[s];
             off = up(off);
@@ -537,88 +555,132 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
                 g.off_v += off;
             }
             off += (int64_t)w.data.size();
+            blk_end[s] = off;
             F->dense_entries += w.dense_e;
             F->lowrank_entries += w.lr_e;
             std::vector<double>().swap(w.data);
         }
+        // update slots in the data order: the slots of a flat group are one
+        // contiguous block; the children's slot indices (uout) and the validity
+        // marks (inc) follow
+        std::vector<int32_t> inc_new(nt);
+        int64_t ioff = 0;
+        for (int s2 : order) {
+            inc_new[s2] = (int32_t)ioff;
+            ioff += 2 * (int64_t)(F->sn[s2].ni + F->sn[s2].nb);
+        }
+        F->inc.assign(ioff, -1);
+        for (int p2 = 0; p2 < nt; ++p2)
+            for (int k = 0; k < nch[p2]; ++k) {
+                const HSnode& hc = F->sn[ch[p2][k]];
+                for (int32_t j = 0; j < hc.nb; ++j) {
+                    int32_t& slot = F->uout[hc.u_off + j];
+                    slot = slot - old_inc[p2] + inc_new[p2];
+                    F->inc[slot] = slot;
+                }
+            }
+        for (int s2 = 0; s2 < nt; ++s2) F->sn[s2].inc_off = inc_new[s2];
+        // pivot positions and boundary lists in the data order too: a flat
+        // group's pivots are one position range and its boundary rows one
+        // range of bidx / uout
+        std::vector<int32_t> pmap(n), first_new(nt), boff_new(nt);
+        int64_t pnext = 0, bnext = 0;
+        for (int s2 : order) {
+            first_new[s2] = (int32_t)pnext;
+            pnext += F->sn[s2].ni;
+            boff_new[s2] = (int32_t)bnext;
+            bnext += F->sn[s2].nb;
+        }
+        for (int s2 = 0; s2 < nt; ++s2)
+            for (int32_t i = 0; i < F->sn[s2].ni; ++i) pmap[F->sn[s2].first + i] = first_new[s2] + i;
+        std::vector<int32_t> pidx_new(n), bidx_new(F->bidx.size()), uout_new(F->uout.size());
+        for (int64_t p2 = 0; p2 < n; ++p2) pidx_new[pmap[p2]] = F->pidx[p2];
+        for (int s2 = 0; s2 < nt; ++s2) {
+            const HSnode& h = F->sn[s2];
+            for (int32_t j = 0; j < h.nb; ++j) {
+                bidx_new[boff_new[s2] + j] = F->pidx[W[s2].B[j]];   // vector index
+                uout_new[boff_new[s2] + j] = F->uout[h.u_off + j];
+            }
+        }
+        F->pidx.swap(pidx_new);
+        F->bidx.swap(bidx_new);
+        F->uout.swap(uout_new);
+        for (int s2 = 0; s2 < nt; ++s2) {
+            F->sn[s2].first = first_new[s2];
+            F->sn[s2].bidx_off = F->sn[s2].u_off = boff_new[s2];
+        }
     }
     // per-level work: flat items of the small clusters, chunked tasks of the
     // large ones
-    const int H = maxh + 1;
-    F->height = H;
-    std::vector<std::vector<int>> bylev(H);
-    for (int s = 0; s < nt; ++s) bylev[F->sn[s].height].push_back(s);
-    F->ff_ptr.assign(1, 0);
-    F->fb_ptr.assign(1, 0);
+    F->fg_ptr.assign(1, 0);
     F->vg_ptr.assign(1, 0);
     F->ulr_ptr.assign(1, 0);
     F->uf_ptr.assign(1, 0);
     F->ub_ptr.assign(1, 0);
     int64_t tbuf = 0, pbuf = 0;
     int32_t tickets = 0;
-    // pack the items of one level into CTAs: <= FLAT_ITEMS items and
-    // <= STAGE_MAX staged values; the splits of one row group (column) sit
-    // in the same CTA, `stride` threads apart
-    auto pack = [&](const std::vector<int>& cl, bool fwd, std::vector<FCta>& ctas,
-                    std::vector<FItem>& items, std::vector<FStage>& stages) {
-        FCta c{};
-        c.it0 = c.it1 = (int32_t)items.size();
-        c.st0 = c.st1 = (int32_t)stages.size();
+    // cut the small clusters of one level into groups: consecutive clusters
+    // (contiguous data) up to STAGE_CL clusters, STAGE_MAX staged values per
+    // pass and GROUP_BYTES of data (a larger cluster forms a group alone)
+    const int esz = vec == 2 ? 8 : vec == 4 ? 4 : 2;
+    auto make_groups = [&](const std::vector<int>& cl) {
+        int32_t most = 0;
+        FGroup g{};
+        bool open = false, kids = false;
+        int64_t end = 0, send = 0;
         auto flush = [&]() {
-            if (c.it1 > c.it0) ctas.push_back(c);
-            c = FCta{};
-            c.it0 = c.it1 = (int32_t)items.size();
-            c.st0 = c.st1 = (int32_t)stages.size();
+            if (!open) return;
+            g.nbytes = (int32_t)(((end - g.dstart) * esz + 15) / 16 * 16);
+            g.sbytes = kids ? (int32_t)((send - g.sstart) * 8) : 0;
+            most = std::max(most, g.nbytes + g.sbytes);
+            g.c1 = (int32_t)F->gcl.size();
+            F->fg.push_back(g);
+            open = false;
         };
         for (int s : cl) {
             const HSnode& h = F->sn[s];
             if (h.ni == 0) continue;
-            const int stage = fwd ? h.ni : h.nd + vec;   // values staged per cluster
-            const int units = fwd ? (h.nd + vec - 1) / vec : h.ni;   // row groups / columns
-            // splits: forward over columns (<= FWD_COLS each), backward over rows
-            const int span = fwd ? h.ni : h.nd;
-            const int per = fwd ? FWD_COLS : BWD_ROWS;
-            const int P = std::min(8, std::max(1, (span + per - 1) / per));
-            int chunk = (span + P - 1) / P;
-            chunk = (chunk + vec - 1) / vec * vec;      // split bounds on vector boundaries
-            const int umax = FLAT_ITEMS / P;             // units per CTA block
-            bool staged = false;
-            int woff = 0, sk = 0;
-            for (int u0 = 0; u0 < units; u0 += umax) {
-                const int u1 = std::min(units, u0 + umax);
-                const int need = P * (u1 - u0);
-                if (c.it1 - c.it0 + need > FLAT_ITEMS ||
-                    (!staged && (c.total + stage > STAGE_MAX || c.st1 - c.st0 == STAGE_CL))) {
-                    flush();
-                    staged = false;
-                }
-                if (!staged) {
-                    FStage g{s, c.total};
-                    stages.push_back(g);
-                    c.st1 = (int32_t)stages.size();
-                    sk = c.st1 - c.st0 - 1;
-                    woff = c.total;
-                    c.total += stage;
-                    staged = true;
-                }
-                for (int p = 0; p < P; ++p)
-                    for (int u = u0; u < u1; ++u) {
-                        FItem it{};
-                        it.s = s;
-                        it.q = fwd ? u * vec : u;
-                        it.woff = woff;
-                        it.sk = sk;
-                        it.c0 = std::min(span, p * chunk);
-                        it.c1 = std::min(span, (p + 1) * chunk);
-                        it.nsplit = P;
-                        it.stride = u1 - u0;
-                        it.lead = p == 0;
-                        items.push_back(it);
-                    }
-                c.it1 = (int32_t)items.size();
+            const int units_f = (h.nd + vec - 1) / vec;
+            if (open && (g.c1 - g.c0 == STAGE_CL || (int)F->gcl.size() - g.c0 == STAGE_CL ||
+                         g.wf + h.ni > STAGE_MAX || g.wb + h.nd + vec > STAGE_MAX ||
+                         (blk_end[s] - g.dstart) * esz > GROUP_BYTES))
+                flush();
+            if (!open) {
+                g = FGroup{};
+                g.dstart = h.data_off;
+                g.sstart = h.inc_off;
+                g.pstart = h.first;
+                g.bstart = h.bidx_off;
+                g.c0 = g.c1 = (int32_t)F->gcl.size();
+                open = true;
+                kids = false;
             }
+            GCl c{};
+            c.first = h.first;
+            c.ni = h.ni;
+            c.nd = h.nd;
+            c.doff = (int32_t)(h.data_off - g.dstart);
+            c.soff = (int32_t)(h.inc_off - g.sstart);
+            c.boff = h.bidx_off - g.bstart;
+            c.nchild = h.nchild;
+            c.s = s;
+            c.woff_f = g.wf;
+            c.woff_b = g.wb;
+            c.uf0 = g.uf;
+            c.ub0 = g.ub;
+            F->gcl.push_back(c);
+            g.c1 = (int32_t)F->gcl.size();
+            g.wf += h.ni;
+            g.wb += h.nd + vec;
+            g.uf += units_f;
+            g.ub += h.ni;
+            g.nbt += h.nb;
+            end = blk_end[s];
+            send = h.inc_off + 2 * (int64_t)(h.ni + h.nb);
+            kids = kids || h.nchild > 0;
         }
         flush();
+        F->fg_bytes.push_back(most);
     };
     for (int L = 0; L < H; ++L) {
         std::vector<int> small;
@@ -641,10 +703,8 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             }
             h.lr_end = (int32_t)F->lr.size();
         }
-        pack(small, true, F->ffc, F->ffi, F->ffs);
-        pack(small, false, F->fbc, F->fbi, F->fbs);
-        F->ff_ptr.push_back((int32_t)F->ffc.size());
-        F->fb_ptr.push_back((int32_t)F->fbc.size());
+        make_groups(small);
+        F->fg_ptr.push_back((int32_t)F->fg.size());
         for (int s : bylev[L]) {
             const HSnode& h = F->sn[s];
             if (!h.large) continue;

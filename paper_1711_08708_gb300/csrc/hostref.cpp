@@ -19,11 +19,13 @@ namespace {
 // x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
 // the same order, as the GPU launches (permuted input, per-level flat items
 // with their splits, large-cluster tasks, parent input slots).
-void replay(const HFactorHost& F, const double* b, double shift, double* x,
+// Returns false when a group's cluster data lies outside the group's block.
+bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             const std::vector<double>* vshift = nullptr) {
     std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
+    const int esz = F.vec == 2 ? 8 : F.vec == 4 ? 4 : 2;   // bytes per stored entry
     for (int64_t i = 0; i < F.n; ++i) {
         const int v = F.pidx[i];
         const bool pinned = v == F.pin || (!F.pinflag.empty() && F.pinflag[v]);
@@ -51,23 +53,24 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x,
     };
     const int H = (int)F.uf_ptr.size() - 1;
     for (int lev = 0; lev < H; ++lev) {
-        // flat items first (all reads of this level's inputs precede the writes
-        // into the parents' slots, as on the GPU where parents sit higher up)
-        std::vector<std::pair<int, double>> rows_out;   // not needed: parents are later levels
-        for (int c = F.ff_ptr[lev]; c < F.ff_ptr[lev + 1]; ++c)
-            for (int it = F.ffc[c].it0; it < F.ffc[c].it1; ++it) {
-                const FItem& f = F.ffi[it];
-                if (!f.lead) continue;
-                const HSnode& s = F.sn[f.s];
-                for (int e = 0; e < F.vec && f.q + e < s.nd; ++e) {
-                    double a = 0.0;
-                    for (int p = 0; p < f.nsplit; ++p) {
-                        const FItem& g = F.ffi[it + p * f.stride];
-                        a += fwd_part(s, f.q + e, g.c0, g.c1);
-                    }
-                    finish(s, drow(s, f.q + e), a);
-                }
+        // flat groups first (their parents sit on later levels): per cluster of
+        // a group, each dense row over all its columns, and the group's data
+        // read inside its bulk-copied block
+        for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g) {
+            const FGroup& G = F.fg[g];
+            const int64_t gend = G.dstart + G.nbytes / esz;
+            for (int c = G.c0; c < G.c1; ++c) {
+                const GCl& d = F.gcl[c];
+                const HSnode& s = F.sn[d.s];
+                if (d.doff != s.data_off - G.dstart || s.data_off + col_start(s.nd, s.ni, F.vec) > gend ||
+                    d.ni != s.ni || d.nd != s.nd || d.nchild != s.nchild ||
+                    d.soff != s.inc_off - G.sstart || d.first != s.first ||
+                    s.first != G.pstart + d.woff_f || s.bidx_off != G.bstart + d.boff ||
+                    (s.nchild && s.inc_off + 2 * s.nd > G.sstart + G.sbytes / 8))
+                    return false;
+                for (int q = 0; q < s.nd; ++q) finish(s, q, fwd_part(s, q, 0, s.ni));
             }
+        }
         for (int ti = F.uf_ptr[lev]; ti < F.uf_ptr[lev + 1]; ++ti) {
             const HTask& k = F.uft[ti];
             if (k.s < 0) {
@@ -125,20 +128,18 @@ void replay(const HFactorHost& F, const double* b, double shift, double* x,
                 xs.push_back({F.pidx[s.first + j], a});
             }
         }
-        for (int c = F.fb_ptr[lev]; c < F.fb_ptr[lev + 1]; ++c)
-            for (int it = F.fbc[c].it0; it < F.fbc[c].it1; ++it) {
-                const FItem& f = F.fbi[it];
-                if (!f.lead) continue;
-                const HSnode& s = F.sn[f.s];
-                double a = 0.0;
-                for (int p = 0; p < f.nsplit; ++p) {
-                    const FItem& g = F.fbi[it + p * f.stride];
-                    for (int q = std::max(g.c0, f.q); q < g.c1; ++q) a += elem(s, q, f.q) * vrow(s, q);
+        for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g)
+            for (int c = F.fg[g].c0; c < F.fg[g].c1; ++c) {
+                const HSnode& s = F.sn[F.gcl[c].s];
+                for (int j = 0; j < s.ni; ++j) {
+                    double a = 0.0;
+                    for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
+                    xs.push_back({F.pidx[s.first + j], a});
                 }
-                xs.push_back({F.pidx[s.first + f.q], a});
             }
         for (auto& pr : xs) x[pr.first] = pr.second;
     }
+    return true;
 }
 
 }  // namespace
@@ -214,7 +215,7 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
                 if (K.col[q] == r) K.val[q] += gamma * a.mH[r];
         BID_TRY(build_hfactor(K, a.coords.data(), a.dim, {}, o, &F));
     }
-    replay(F, b, shift, x);
+    if (!replay(F, b, shift, x)) return set_error(BID_EINVAL, "flat group layout inconsistent");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->n1 = F.n;
@@ -268,7 +269,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
             m /= (double)lay.N[s];
             for (int64_t i = 0; i < lay.N[s]; ++i) vshift[lay.off[s] + i] = m;
         }
-    replay(F, b, 0.0, x, &vshift);
+    if (!replay(F, b, 0.0, x, &vshift)) return set_error(BID_EINVAL, "flat group layout inconsistent");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->n1 = F.n;

@@ -11,8 +11,11 @@
 // Launches of one solve:
 //   k_permute     b (vector order) -> xp (elimination order), shifted, pin zeroed;
 //   per level, leaves first:
-//     k_flat_fwd  small clusters: a thread owns an aligned row group over a
-//                 split of the columns; splits are summed in a fixed order;
+//     k_flat_fwd  small clusters, one CTA per group of clusters: the group's
+//                 factor block is copied into shared memory by one bulk copy
+//                 (cp.async.bulk, mbarrier completion) while the inputs are
+//                 staged; a thread then owns an aligned row group over all
+//                 its columns;
 //     k_up_fwd    large clusters: 64 row groups x 4 column splits per CTA over
 //                 64 columns; column chunks of a row are combined in a fixed
 //                 order by the last CTA (ticket); low-rank groups: one CTA each
@@ -21,13 +24,15 @@
 //     k_bwd_prep  U^T v of the low-rank groups; staging of the large
 //                 clusters' v = [y_s; -x_B] in vbuf;
 //     k_up_bwd    large clusters: 4 warps per column over row quarters;
-//     k_flat_bwd  small clusters: a thread owns a column over a split of rows.
+//     k_flat_bwd  small clusters, same groups and bulk copy: a thread owns a
+//                 column over all its rows.
 // Factors are stored in FP64, FP32 or BF16; FP32/BF16 accumulate in FP32 (the
 // precision form), FP64 in FP64.  All reductions have a fixed order, so the
 // result is bitwise reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "internal.h"
@@ -88,12 +93,8 @@ struct HView {
     const int32_t* __restrict__ vgl;
     const HSnode* __restrict__ sn;
     const HLr* __restrict__ lr;
-    const FCta* __restrict__ ffc;
-    const FCta* __restrict__ fbc;
-    const FItem* __restrict__ ffi;
-    const FItem* __restrict__ fbi;
-    const FStage* __restrict__ ffs;
-    const FStage* __restrict__ fbs;
+    const FGroup* __restrict__ fg;
+    const GCl* __restrict__ gcl;
     const HTask* __restrict__ uft;
     const HTask* __restrict__ ubt;
 };
@@ -123,9 +124,108 @@ __device__ __forceinline__ void finish_row(const HView& v, const HSnode& sn, int
     if (R < sn.ni) {
         ybuf[sn.first + R] = acc;
     } else {
-        const double u = incoming(v, sn, R, inb) - acc;
+        const double u = (sn.nchild ? incoming(v, sn, R, inb) : 0.0) - acc;
         inb[v.uout[sn.u_off + R - sn.ni]] = u;
     }
+}
+
+// ---------------------------------------------------------------- bulk copy
+// Global -> shared copies by the bulk-copy (TMA) engine, completion tracked by
+// an mbarrier transaction count (PTX cp.async.bulk / mbarrier).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// non-blocking test of the phase with the given parity
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase 0 of `bar` (about 2^20 polls with a short sleep
+// between them, well under a second); false when the limit is reached (the
+// caller records the error and gives up).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
+    for (int i = 0; i < (1 << 20); ++i) {
+        if (mbar_test_wait(bar, 0)) return true;
+        if (i >= 8) __nanosleep(64);
+    }
+    return false;
+}
+constexpr int BULK_CHUNK = 16384;   // bytes per bulk-copy instruction
+// dynamic shared memory of a flat launch (the largest group of its level);
+// static shared memory of the flat kernels is at most 44 KB (FP64 staging)
+constexpr int FLAT_DYN_MAX = 176 * 1024;
+
+__device__ __forceinline__ void bulk_region(unsigned char* dst, const void* src, int nbytes,
+                                            uint64_t* bar) {
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    for (int o = 0; o < nbytes; o += BULK_CHUNK)
+        bulk_g2s(dst + o, s + o, (uint32_t)min(BULK_CHUNK, nbytes - o), bar);
+}
+// Thread 0: arm the barrier with the group's byte count and issue its copies:
+// factor data at dst, then (sbytes > 0) the update slots right after it.
+__device__ __forceinline__ void group_load(unsigned char* dst, const void* data, int nbytes,
+                                           const double* slots, int sbytes, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(nbytes + sbytes));
+    bulk_region(dst, data, nbytes, bar);
+    if (sbytes > 0) bulk_region(dst + nbytes, slots, sbytes, bar);
+}
+
+// 16-byte vector from shared memory, widened to the accumulation type
+__device__ __forceinline__ void lds16(const double* p, double (&o)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+}
+__device__ __forceinline__ void lds16(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ void lds16(const __nv_bfloat16* p, float (&o)[8]) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[2 * i] = __uint_as_float(w[i] << 16);
+        o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+// index k of the last cluster of a group whose prefix (field F) is <= x
+template <int F>
+__device__ __forceinline__ int group_owner(const GCl* c, int n, int x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int key = F == 0 ? c[mid].woff_f : F == 1 ? c[mid].woff_b : F == 2 ? c[mid].uf0 : c[mid].ub0;
+        if (key <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q) {
@@ -166,153 +266,148 @@ __global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict
 }
 
 // ------------------------------------------------------------ small clusters
-__device__ __forceinline__ int stage_owner(const int2* st, int nst, int f) {
-    int lo = 0, hi = nst - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (st[mid].y <= f) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
+// Small clusters carry no low-rank groups, so their dense rows are the rows
+// of M_s (dense_row(q) = q).  One CTA per group: thread 0 starts the bulk copy
+// of the group's factor block, all threads stage the cluster descriptors and
+// the inputs, then wait for the copy and compute from shared memory.  A copy
+// that does not complete within the wait limit sets *err and the CTA returns
+// (the result is then invalid and the error is reported by the solve).
+constexpr int FT = FLAT_THREADS;
+
+// both update slots of frontal row f, from the group's copy in shared memory
+__device__ __forceinline__ double incoming_s(const double* ss, const GCl& c, int f) {
+    const double2 val = *reinterpret_cast<const double2*>(ss + c.soff + 2 * f);
+    return val.x + val.y;
 }
 
-// Small clusters carry no low-rank groups, so their dense rows are the rows
-// of M_s (dense_row(q) = q).  A CTA first stages the descriptors and inputs of
-// its clusters in shared memory; the item loop then touches global memory only
-// for the factor data, the update slots of its rows and the result.
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_flat_fwd(HView v, const T* __restrict__ data, int cta0,
-                                                 const double* xp, double* ybuf, double* inb) {
+__global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
+                                                 const double* xp, double* ybuf, double* inb,
+                                                 unsigned int* err) {
     constexpr int VEC = VecOf<T>::N;
-    constexpr int U = VEC == 8 ? 4 : 8;   // columns per load round
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ A w[STAGE_MAX];
-    __shared__ A red[HT][VEC];
-    __shared__ int2 st[STAGE_CL];
-    __shared__ HSnode ssn[STAGE_CL];
-    const FCta c = v.ffc[cta0 + blockIdx.x];
-    const int nst = c.st1 - c.st0;
-    const int it = c.it0 + threadIdx.x;
-    FItem item;
-    item.lead = 0;
-    if (it < c.it1) item = v.ffi[it];   // issued early, used after the barrier
-    for (int k = threadIdx.x; k < nst; k += HT) {
-        const FStage g = v.ffs[c.st0 + k];
-        st[k] = make_int2(g.s, g.woff);
-        ssn[k] = v.sn[g.s];
+    __shared__ GCl scl[STAGE_CL];
+    __shared__ __align__(8) uint64_t bar;
+    const FGroup G = v.fg[g0 + blockIdx.x];
+    const int nc = G.c1 - G.c0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        group_load(dyn_smem, data + G.dstart, G.nbytes, inb + G.sstart, G.sbytes, &bar);
     }
+    // contiguous ranges of the group: descriptors and right-hand side
+    for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+    for (int f = threadIdx.x; f < G.wf; f += FT) w[f] = (A)xp[G.pstart + f];
     __syncthreads();
-    for (int f = threadIdx.x; f < c.total; f += HT) {
-        const int k = stage_owner(st, nst, f);
-        w[f] = (A)gather_w(v, ssn[k], f - st[k].y, xp, inb);
+    if (!mbar_wait_bounded(&bar)) {
+        if (threadIdx.x == 0) atomicOr(err, 1u);
+        return;
     }
-    __syncthreads();
-    A acc[VEC];
+    const double* ss = reinterpret_cast<const double*>(dyn_smem + G.nbytes);
+    if (G.sbytes > 0) {   // add the children's updates (zero where none)
+        for (int f = threadIdx.x; f < G.wf; f += FT) {
+            const GCl& c = scl[group_owner<0>(scl, nc, f)];
+            if (c.nchild) w[f] = (A)((double)w[f] + incoming_s(ss, c, f - c.woff_f));
+        }
+        __syncthreads();
+    }
+    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    for (int u = threadIdx.x; u < G.uf; u += FT) {
+        const GCl& c = scl[group_owner<2>(scl, nc, u)];
+        const int q0 = (u - c.uf0) * VEC;
+        const A* ws = w + c.woff_f;
+        const T* col = sd + c.doff + q0;
+        // a row group of pivot rows stops at its diagonal, others span all columns
+        const int jlast = q0 + VEC - 1 < c.ni ? q0 + VEC : c.ni;
+        A acc[VEC];
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) acc[e] = 0;
-    if (it < c.it1) {
-        const HSnode sn = ssn[item.sk];
-        const int q0 = item.q;
-        const A* ws = w + item.woff;
-        const T* col = data + sn.data_off;
-        const int jend = (q0 + VEC - 1 < sn.ni) ? min(item.c1, q0 + VEC) : item.c1;
-        for (int j0 = item.c0; j0 < jend; j0 += U) {
-            A val[U][VEC];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = j0 + u;
-                if (j < jend) {
-                    ld16(col + col_start(sn.nd, j, VEC) - j + q0, val[u]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) val[u][e] = 0;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = j0 + u;
-                const A wj = j < jend ? ws[j] : (A)0;
+        for (int e = 0; e < VEC; ++e) acc[e] = 0;
+        // column j starts at col_start(nd, j) - j relative to row 0; the
+        // distance to column j + 1 is nd - j rounded so that the next start
+        // stays congruent to its column index modulo VEC
+        int cs = 0;
+        for (int j = 0; j < jlast; ++j) {
+            A val[VEC];
+            lds16(col + cs, val);
+            const A wj = ws[j];
+            if (j > q0) {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e)
-                    if (q0 + e >= j) acc[e] += val[u][e] * wj;
+                    if (q0 + e >= j) acc[e] += val[e] * wj;
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) acc[e] += val[e] * wj;
+            }
+            cs += c.nd - j - 1 + ((j + 1 - c.nd) & (VEC - 1));
+        }
+        const int nrow = min(VEC, c.nd - q0);
+        for (int e = 0; e < nrow; ++e) {
+            const int R = q0 + e;
+            if (R < c.ni) {
+                ybuf[G.pstart + c.woff_f + R] = (double)acc[e];
+            } else {
+                const double u0 = c.nchild ? incoming_s(ss, c, R) : 0.0;
+                inb[v.uout[G.bstart + c.boff + R - c.ni]] = u0 - (double)acc[e];
             }
         }
     }
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) red[threadIdx.x][e] = acc[e];
-    __syncthreads();
-    if (it >= c.it1 || !item.lead) return;
-    const HSnode sn = ssn[item.sk];
-    for (int p = 1; p < item.nsplit; ++p)
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[e] += red[threadIdx.x + p * item.stride][e];
-#pragma unroll
-    for (int e = 0; e < VEC; ++e)
-        if (item.q + e < sn.nd) finish_row(v, sn, item.q + e, (double)acc[e], ybuf, inb);
 }
 
+// Backward: the staged input of a cluster is v = [y_s; -x_B; 0 (vec)]; the
+// group's y are the positions [pstart, pstart + wf) of ybuf and its boundary
+// rows the range [bstart, bstart + nbt) of bidx, both read contiguously.
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_flat_bwd(HView v, const T* __restrict__ data, int cta0,
-                                                 const double* __restrict__ ybuf, double* out) {
+__global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ data, int g0,
+                                                 const double* __restrict__ ybuf, double* out,
+                                                 unsigned int* err) {
     constexpr int VEC = VecOf<T>::N;
-    constexpr int U = VEC == 8 ? 4 : 8;   // vectors per load round
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ A vs[STAGE_MAX];
-    __shared__ A red[HT];
-    __shared__ int2 st[STAGE_CL];
-    __shared__ HSnode ssn[STAGE_CL];
-    const FCta c = v.fbc[cta0 + blockIdx.x];
-    const int nst = c.st1 - c.st0;
-    const int it = c.it0 + threadIdx.x;
-    FItem item;
-    item.lead = 0;
-    if (it < c.it1) item = v.fbi[it];
-    for (int k = threadIdx.x; k < nst; k += HT) {
-        const FStage g = v.fbs[c.st0 + k];
-        st[k] = make_int2(g.s, g.woff);
-        ssn[k] = v.sn[g.s];
+    __shared__ GCl scl[STAGE_CL];
+    __shared__ __align__(8) uint64_t bar;
+    const FGroup G = v.fg[g0 + blockIdx.x];
+    const int nc = G.c1 - G.c0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        group_load(dyn_smem, data + G.dstart, G.nbytes, nullptr, 0, &bar);
     }
+    for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
     __syncthreads();
-    for (int f = threadIdx.x; f < c.total; f += HT) {
-        const int k = stage_owner(st, nst, f);
-        const HSnode& sn = ssn[k];
-        const int q = f - st[k].y;
+    for (int f = threadIdx.x; f < G.wb; f += FT) {
+        const GCl& c = scl[group_owner<1>(scl, nc, f)];
+        const int q = f - c.woff_b;
         double x = 0.0;
-        if (q < sn.nd) x = q < sn.ni ? ybuf[sn.first + q] : -out[v.bidx[sn.bidx_off + q - sn.ni]];
+        if (q < c.ni) x = ybuf[G.pstart + c.woff_f + q];
+        else if (q < c.nd) x = -out[v.bidx[G.bstart + c.boff + q - c.ni]];
         vs[f] = (A)x;
     }
     __syncthreads();
-    A acc = 0;
-    if (it < c.it1) {
-        const HSnode sn = ssn[item.sk];
-        const int j = item.q;
-        const A* vv = vs + item.woff;
-        const T* cj = data + sn.data_off + col_start(sn.nd, j, VEC) - j;
-        const int qend = item.c1;
-        for (int q0 = max(item.c0, j & ~(VEC - 1)); q0 < qend; q0 += U * VEC) {
-            A val[U][VEC];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (q0 + u * VEC < qend) {
-                    ld16(cj + q0 + u * VEC, val[u]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) val[u][e] = 0;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const int q = q0 + u * VEC + e;
-                    if (q >= j && q < qend) acc += val[u][e] * vv[q];
-                }
-        }
+    if (!mbar_wait_bounded(&bar)) {
+        if (threadIdx.x == 0) atomicOr(err, 1u);
+        return;
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (it >= c.it1 || !item.lead) return;
-    for (int p = 1; p < item.nsplit; ++p) acc += red[threadIdx.x + p * item.stride];
-    const HSnode& sn = ssn[item.sk];
-    out[v.pidx[sn.first + item.q]] = (double)acc;
+    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    for (int u = threadIdx.x; u < G.ub; u += FT) {
+        const GCl& c = scl[group_owner<3>(scl, nc, u)];
+        const int j = u - c.ub0;
+        const A* vv = vs + c.woff_b;
+        const T* cj = sd + c.doff + col_start(c.nd, j, VEC) - j;
+        const int q0 = j & ~(VEC - 1);
+        // first vector: the rows from j on
+        A val[VEC];
+        lds16(cj + q0, val);
+        A acc = 0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (q0 + e >= j && q0 + e < c.nd) acc += val[e] * vv[q0 + e];
+        // whole vectors, then the ragged end (staged inputs are zero there)
+        for (int q = q0 + VEC; q < c.nd; q += VEC) {
+            lds16(cj + q, val);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc += val[e] * vv[q + e];
+        }
+        out[v.pidx[G.pstart + u]] = (double)acc;   // u = pivot offset inside the group
+    }
 }
 
 // ------------------------------------------------------------ large clusters
@@ -555,12 +650,8 @@ HView view_of(const HFactorDev& F) {
     v.vgl = F.vgl;
     v.sn = F.sn;
     v.lr = F.lr;
-    v.ffc = F.ffc;
-    v.fbc = F.fbc;
-    v.ffi = F.ffi;
-    v.fbi = F.fbi;
-    v.ffs = F.ffs;
-    v.fbs = F.fbs;
+    v.fg = F.fg;
+    v.gcl = F.gcl;
     v.uft = F.uft;
     v.ubt = F.ubt;
     return v;
@@ -571,6 +662,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         const HScratch& S, double* out) {
     const HView v = view_of(F);
     const T* data = reinterpret_cast<const T*>(F.data);
+    double* inb = S.inb ? S.inb : F.inb;
     int launches = 1;
     {
         int64_t g = (F.n + HT - 1) / HT;
@@ -579,9 +671,10 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
     }
     const int H = (int)F.uf_ptr.size() - 1;
     for (int lev = 0; lev < H; ++lev) {
-        const int nf = F.ff_ptr[lev + 1] - F.ff_ptr[lev];
+        const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
-            k_flat_fwd<T, A><<<nf, HT, 0, L.st>>>(v, data, F.ff_ptr[lev], S.xp, S.ybuf, S.inb);
+            k_flat_fwd<T, A><<<nf, FT, F.fg_bytes[lev], L.st>>>(v, data, F.fg_ptr[lev], S.xp, S.ybuf,
+                                                                 inb, S.err);
             ++launches;
         }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
@@ -589,7 +682,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             const int has_lr = F.ulr_ptr[lev + 1] > F.ulr_ptr[lev];
             const size_t sm = sizeof(A) * (has_lr ? (((F.u_ni_max[lev] + 1) & ~1) + LR_KMAX + 2)
                                                   : (size_t)UP_COLS);
-            k_up_fwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.uf_ptr[lev], S.xp, S.ybuf, S.inb,
+            k_up_fwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.uf_ptr[lev], S.xp, S.ybuf, inb,
                                                  S.tbuf, S.pbuf, S.tickets);
             ++launches;
         }
@@ -607,9 +700,10 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             k_up_bwd<T, A><<<nt, HT, 0, L.st>>>(v, data, F.ub_ptr[lev], S.vbuf, S.tbuf, out);
             ++launches;
         }
-        const int nf = F.fb_ptr[lev + 1] - F.fb_ptr[lev];
+        const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
-            k_flat_bwd<T, A><<<nf, HT, 0, L.st>>>(v, data, F.fb_ptr[lev], S.ybuf, out);
+            k_flat_bwd<T, A><<<nf, FT, F.fg_bytes[lev], L.st>>>(v, data, F.fg_ptr[lev], S.ybuf, out,
+                                                                 S.err);
             ++launches;
         }
     }
@@ -631,6 +725,10 @@ template <typename T, typename A>
 int prepare_one() {
     const int lim = 200 * 1024;
     BID_CUDA_TRY(cudaFuncSetAttribute(k_up_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      FLAT_DYN_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      FLAT_DYN_MAX));
     return BID_OK;
 }
 
@@ -687,6 +785,20 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
             return set_error(BID_EINVAL, "cluster too large for shared memory (ni=%d)", h.u_ni_max[L]);
     for (const HLr& g : h.lr)
         if (g.k > LR_KMAX || g.m > LR_ROWS) return set_error(BID_EINVAL, "low-rank group out of range");
+    {
+        const int esz = precision == BID_FP64 ? 8 : precision == BID_FP32 ? 4 : 2;
+        for (const FGroup& g : h.fg) {
+            // bulk copies: 16-byte aligned source, whole 16-byte chunks inside the array
+            if (g.nbytes <= 0 || g.nbytes % 16 || g.nbytes > FLAT_DYN_MAX || (g.dstart * esz) % 16 ||
+                (g.dstart * esz + g.nbytes) > (int64_t)h.data.size() * esz)
+                return set_error(BID_EINVAL, "flat group out of range (%d bytes)", g.nbytes);
+            if (g.c1 - g.c0 > STAGE_CL || g.wf > STAGE_MAX || g.wb > STAGE_MAX)
+                return set_error(BID_EINVAL, "flat group exceeds its staging limits");
+            if (g.sbytes < 0 || g.sbytes % 16 || g.sstart % 2 || g.nbytes + g.sbytes > FLAT_DYN_MAX ||
+                g.sstart + g.sbytes / 8 > h.nslots)
+                return set_error(BID_EINVAL, "flat group slots out of range");
+        }
+    }
     const int want_vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
     if (h.vec != want_vec) return set_error(BID_EINVAL, "factor layout built for another precision");
     d->n = h.n;
@@ -701,16 +813,12 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.vgl, &d->vgl));
     BID_TRY(upload_vec(h.sn, &d->sn));
     BID_TRY(upload_vec(h.lr, &d->lr));
-    BID_TRY(upload_vec(h.ffc, &d->ffc));
-    BID_TRY(upload_vec(h.fbc, &d->fbc));
-    BID_TRY(upload_vec(h.ffi, &d->ffi));
-    BID_TRY(upload_vec(h.fbi, &d->fbi));
-    BID_TRY(upload_vec(h.ffs, &d->ffs));
-    BID_TRY(upload_vec(h.fbs, &d->fbs));
+    BID_TRY(upload_vec(h.fg, &d->fg));
+    BID_TRY(upload_vec(h.gcl, &d->gcl));
     BID_TRY(upload_vec(h.uft, &d->uft));
     BID_TRY(upload_vec(h.ubt, &d->ubt));
-    d->ff_ptr = h.ff_ptr;
-    d->fb_ptr = h.fb_ptr;
+    d->fg_ptr = h.fg_ptr;
+    d->fg_bytes = h.fg_bytes;
     d->ulr_ptr = h.ulr_ptr;
     d->uf_ptr = h.uf_ptr;
     d->ub_ptr = h.ub_ptr;
@@ -739,6 +847,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
         BID_TRY(upload_vec(f, reinterpret_cast<uint16_t**>(&d->data)));
         esz = 2;
     }
+    BID_CUDA_TRY(cudaMalloc(&d->inb, sizeof(double) * std::max<int64_t>(h.nslots, 2)));
+    BID_CUDA_TRY(cudaMemset(d->inb, 0, sizeof(double) * std::max<int64_t>(h.nslots, 2)));
     d->bytes_pass = 2 * (int64_t)n * esz;
     d->alg_bytes_pass = 2 * (h.dense_entries + h.lowrank_entries) * esz;
     d->vec = h.vec;
@@ -746,8 +856,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 void free_hfactor(HFactorDev* d) {
-    void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout, d->vgl, d->sn, d->lr, d->ffc,
-                    d->fbc, d->ffi, d->fbi, d->ffs, d->fbs, d->uft, d->ubt, d->data};
+    void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout, d->vgl, d->sn,
+                    d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

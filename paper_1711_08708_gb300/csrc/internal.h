@@ -89,7 +89,7 @@ struct HSnode {
     int32_t lr_begin, lr_end;
     int32_t large;      // 1: chunked upper-level tasks (may hold low-rank groups); 0: flat items
     int32_t v_off;      // large clusters: backward input staged at vbuf[v_off ...]
-    int32_t pad2;
+    int32_t nchild;     // children in the cluster tree (0: no incoming updates)
 };
 // Number of stored (nonzero) entries of columns 0 .. j-1 of the dense part.
 BID_HD int64_t col_offset(int64_t nd, int64_t j) { return j * nd - j * (j - 1) / 2; }
@@ -112,26 +112,42 @@ struct HLr {
     int64_t off_u, off_v;
     int32_t t_off, pad;         // slot of V^T w (forward) / U^T v (backward) in tbuf
 };
-// Flat work of the small clusters of one level: one thread per item.
-//  forward item:  rows q .. q+vec-1 (q a multiple of vec) of cluster s over its
-//                 columns [c0, c1); input w_s staged at woff in shared memory;
-//  backward item: column q of cluster s over the rows [c0, c1) of the column;
-//                 v_s = [y_s; -x_B] staged at woff.
-// A row group (or column) is split over nsplit items placed stride threads
-// apart in the same CTA; the split with c0 == lowest (the first) sums the
-// partial results in split order.  A CTA holds up to FLAT_ITEMS items and
-// stages the inputs of its clusters (FStage entries sorted by woff).
-struct FItem {
-    int32_t s, q, woff, c0, c1, nsplit, stride, lead;
-    int32_t sk;         // index of the cluster in its CTA's stage list
+// Positions (elimination order), the boundary lists bidx / uout and the
+// update slots are all numbered in the data order described below.
+// Flat work of the small clusters of one level.  The small clusters of a
+// level are cut into groups of consecutive clusters whose packed data is
+// contiguous in `data` (a group's factor bytes are [dstart, dstart + nbytes)
+// in elements / bytes, 16-byte aligned); one CTA per group copies them into
+// shared memory with one bulk copy, stages the inputs and then computes:
+//  forward:  one unit per aligned row group (vec rows) of a cluster, over all
+//            its columns (uf units per group);
+//  backward: one unit per column of a cluster, over all its rows (ub units).
+// The update slots of a group's clusters are contiguous too (slots are
+// numbered in the same order as the data), and copied by a second bulk copy
+// when some cluster of the group has children.  Slots that no child writes
+// stay zero (each factor owns its zero-initialised slot array), so the flat
+// kernels add both slots of a frontal row without validity checks.
+// A group holds at most STAGE_CL clusters, STAGE_MAX staged values in either
+// pass and, unless it is a single cluster, GROUP_BYTES bytes of data: small
+// CTAs (FLAT_THREADS threads, ~25 KB of shared memory) so that many groups
+// are resident per SM and their load phases overlap.
+struct FGroup {
+    int64_t dstart;                 // element offset of the group's data
+    int64_t sstart;                 // first update slot of the group's clusters
+    int32_t nbytes;                 // data bytes copied (multiple of 16)
+    int32_t sbytes;                 // update-slot bytes copied (0: no cluster has children)
+    int32_t c0, c1;                 // clusters gcl[c0 .. c1)
+    int32_t wf, wb;                 // staged values, forward / backward
+    int32_t uf, ub;                 // units, forward / backward
+    int32_t pstart;                 // first pivot position (the group's pivots: wf positions)
+    int32_t bstart, nbt;            // its boundary rows: bidx / uout [bstart, bstart + nbt)
+    int32_t pad;
 };
-struct FStage {
-    int32_t s, woff;
+struct GCl {                        // a cluster of a group: descriptor and prefixes
+    int32_t first, ni, nd, doff;    // doff: data offset inside the group (elements)
+    int32_t soff, boff, nchild, s;      // slot / boundary-row offsets inside the group; cluster
+    int32_t woff_f, woff_b, uf0, ub0;   // woff_f = uf... pivot offset inside the group
 };
-struct FCta {
-    int32_t it0, it1, st0, st1, total, pad;
-};
-
 // Work item of a large-cluster kernel.
 //  upper forward:   s >= 0: dense rows [a0, a1) x columns [b0, b1); when the
 //                   row chunk is split over nparts column chunks, partial sums
@@ -153,11 +169,11 @@ struct HFactorHost {
     std::vector<int32_t> bidx, inc, drows, uout;
     std::vector<HLr> lr;
     std::vector<double> data;
-    // small clusters: flat items per level
-    std::vector<FCta> ffc, fbc;
-    std::vector<FItem> ffi, fbi;
-    std::vector<FStage> ffs, fbs;
-    std::vector<int32_t> ff_ptr, fb_ptr;       // level -> CTA ranges
+    // small clusters: groups per level
+    std::vector<FGroup> fg;
+    std::vector<GCl> gcl;
+    std::vector<int32_t> fg_ptr;               // level -> group range
+    std::vector<int32_t> fg_bytes;             // level -> largest group data (bytes)
     // large clusters, per level
     std::vector<int32_t> ulr_ptr;              // level -> low-rank groups [ptr, ptr+1)
     std::vector<int32_t> vg_ptr, vgl;          // level -> large clusters (backward staging)
@@ -197,16 +213,15 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
 // Limits shared by the build and the kernels.
 constexpr int SMALL_NI = 64;     // a cluster is small when ni <= SMALL_NI and
 constexpr int SMALL_NF = 320;    // ni + nb <= SMALL_NF (before compression)
-constexpr int FLAT_ITEMS = 256;  // items (threads) of a flat CTA
-constexpr int STAGE_MAX = 4096;  // staged input values of a flat CTA
-constexpr int STAGE_CL = 128;    // staged clusters of a flat CTA
+constexpr int STAGE_MAX = 2048;  // staged input values of a flat CTA
+constexpr int STAGE_CL = 64;     // clusters of a flat group
+constexpr int GROUP_BYTES = 12288;   // factor bytes of a flat group (one cluster may exceed)
+constexpr int FLAT_THREADS = 128;    // threads of a flat CTA
 constexpr int UP_GROUPS = 64;    // row groups (of vec rows) of an upper forward task
 constexpr int UP_SPLIT = 4;      // column splits of an upper forward task (16 columns each)
 constexpr int UP_COLS = 64;      // columns of an upper forward task
 constexpr int UP_BROWS = 512;    // target rows per warp of an upper backward task
 constexpr int UP_THREADS = 256;  // threads of a low-rank group task (one per row)
-constexpr int FWD_COLS = 16;     // columns per flat forward split
-constexpr int BWD_ROWS = 64;     // rows per flat backward split
 constexpr int LR_ROWS = 256;     // max rows of a low-rank group
 constexpr int LR_KMAX = 64;      // largest rank kept in a low-rank group
 
@@ -224,17 +239,14 @@ struct HFactorDev {
     int32_t* vgl = nullptr;
     HSnode* sn = nullptr;
     HLr* lr = nullptr;
-    FCta* ffc = nullptr;
-    FCta* fbc = nullptr;
-    FItem* ffi = nullptr;
-    FItem* fbi = nullptr;
-    FStage* ffs = nullptr;
-    FStage* fbs = nullptr;
+    FGroup* fg = nullptr;
+    GCl* gcl = nullptr;
     HTask* uft = nullptr;
     HTask* ubt = nullptr;
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
-    std::vector<int32_t> ff_ptr, fb_ptr, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max, u_nd_max;
+    double* inb = nullptr;              // update slots (nslots, zero where no child writes)
+    std::vector<int32_t> fg_ptr, fg_bytes, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max, u_nd_max;
     int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0, nslots = 0, vbuf_entries = 0;
     int32_t ntickets = 0;
     int64_t bytes_pass = 0;             // stored factor bytes read by fwd + bwd
@@ -248,11 +260,12 @@ void free_hfactor(HFactorDev* d);
 struct HScratch {
     double* xp = nullptr;      // permuted, shifted input (n)
     double* ybuf = nullptr;    // forward result (n)
-    double* inb = nullptr;     // children's update slots (nslots)
+    double* inb = nullptr;     // update slots (nslots, zeroed); NULL: the factor's own
     double* tbuf = nullptr;    // low-rank products
     double* pbuf = nullptr;    // partial sums of split row chunks
     double* vbuf = nullptr;    // staged backward inputs of the large clusters of a level
     unsigned int* tickets = nullptr;    // zero between solves
+    unsigned int* err = nullptr;        // set (nonzero) when a bounded device wait expired
 };
 
 // ---------------------------------------------------------------- device scalars
@@ -268,6 +281,7 @@ struct DevScalars {
     double tol2;            // tol^2 of the running solve (device-resident loop)
     int iter, max_iter;     // iterations done / allowed
     int go, pad0;           // loop condition when the loop runs from the host
+    unsigned int herr, pad1;    // error word of the factor solves (HScratch::err)
     unsigned int ticket[16];
 };
 
@@ -305,8 +319,8 @@ int launch_normalise(const Launch& L, int64_t N, double* U, const double* m,
                      double msum, DevScalars* sc, double* partials);
 // One-thread convergence check of the device-resident PCG loop: first != 0
 // resets the iteration count, otherwise it is incremented; the loop continues
-// iff ||r||^2 > tol^2 ||Y||^2, the residual is finite and fewer than max_iter
-// iterations are done.  The answer goes to the WHILE condition `h` when
+// iff ||r||^2 > tol^2 ||Y||^2, the residual is finite, fewer than max_iter
+// iterations are done and no factor solve reported an expired wait.  The answer goes to the WHILE condition `h` when
 // use_graph != 0, else to sc->go (host-driven loop).
 int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int use_graph, int first);
 // The PCG loops run as CUDA graphs with a device-side WHILE condition unless

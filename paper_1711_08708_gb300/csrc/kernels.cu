@@ -384,7 +384,8 @@ __global__ void k_check(DevScalars* sc, cudaGraphConditionalHandle h, int use_gr
     const int it = first ? 0 : sc->iter + 1;
     sc->iter = it;
     const double rr = sc->rr, yy = sc->yy;
-    const bool go = yy > 0.0 && isfinite(rr) && rr > sc->tol2 * yy && it < sc->max_iter;
+    const bool go = yy > 0.0 && isfinite(rr) && rr > sc->tol2 * yy && it < sc->max_iter &&
+                    sc->herr == 0;
     if (use_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
     else sc->go = go ? 1 : 0;
 }
