@@ -15,6 +15,10 @@ flush is needed between steps.
 --impl reference times the FP64 CPU oracle on the host cores instead, on a
 bounded sample of the same workload (see cpu_baseline).
 
+--workload slab3d times the 3D slab precision form instead (161 x 161 x 49
+nodes with --n 161; --eps / --precision choose the reduced form, the plain
+form is FP64 exact factors).
+
 --workload batched times the batched form instead: 64 seeded torso slices
 (sides 129 ... 1025 nodes, seed 2026) advanced together, one graph launch of
 the PCG loop per step for all slices, leaf sizes from the tuner; its line
@@ -51,18 +55,40 @@ def parse():
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
-    a.add_argument("--workload", default="slice", choices=["slice", "batched"])
+    a.add_argument("--workload", default="slice", choices=["slice", "batched", "slab3d"])
     a.add_argument("--slices", type=int, default=64)
     a.add_argument("--no-sequential", action="store_true")
     return a.parse_args()
 
 
-def workload(n, seed):
-    from workloads import torso_square_2d, params_2d, stimulus_seeded_disc
+def workload(n, seed, kind="slice"):
+    """kind "slice": the n x n torso slice, dt 0.1 ms, seeded stimulus disc;
+    kind "slab3d": the 1 x 1 x 0.3 cm slab at n x n x nz nodes, nz - 1 the
+    z cells at about the x spacing (65 -> 65 x 65 x 21, 161 -> 161 x 161 x 49),
+    dt 0.05 ms, centre-ball stimulus."""
+    from workloads import (torso_square_2d, params_2d, stimulus_seeded_disc, slab_3d, params_3d,
+                           stimulus_centre_ball)
+    if kind == "slab3d":
+        mesh = slab_3d(n, n, slab_nz(n))
+        return mesh, params_3d(0.05), stimulus_centre_ball(mesh)
     mesh = torso_square_2d(n)
     p = params_2d(0.1)
     stim = stimulus_seeded_disc(mesh, seed=seed)
     return mesh, p, stim
+
+
+def slab_nz(n):
+    return (3 * (n - 1) + 9) // 10 + 1
+
+
+def workload_name(args, N=None, NH=None):
+    sizes = "" if N is None else f" (N={N}, N_H={NH})"
+    if args.workload == "slab3d":
+        n = args.n
+        return (f"3D orthotropic slab {n}x{n}x{slab_nz(n)}{sizes}, fibres -60..+60 deg through "
+                "the depth, isolated heart, dt 0.05 ms, centre-ball stimulus, PCG rel-res 1e-8")
+    return (f"2D torso slice {args.n}^2{sizes}, dt 0.1 ms, seeded stimulus disc, "
+            "PCG rel-res 1e-8")
 
 
 class Clocks:
@@ -121,7 +147,7 @@ def peaks():
         return {}
 
 
-def cpu_baseline(n, budget_s, seed=0):
+def cpu_baseline(n, budget_s, seed=0, kind="slice"):
     """The oracle as it stands, timed on the host cores, on a bounded sample of
     the same workload.  A whole oracle step does not fit the budget at the
     large sizes (its sparse direct solve takes minutes at 2049^2, its plain CG
@@ -132,7 +158,7 @@ def cpu_baseline(n, budget_s, seed=0):
     iterations to reach the timing tolerance at the measured (linear) rate."""
     import math
     from oracle import bidomain as ob
-    mesh, p, stim = workload(n, seed)
+    mesh, p, stim = workload(n, seed, kind)
     s = ob.build_system(mesh, p)
     ist = ob.heart_stimulus(s, stim)
     U, V, h = ob.initial_state(s)
@@ -156,7 +182,7 @@ def cpu_baseline(n, budget_s, seed=0):
     step_s = t_rhs + t_iter * k_need
     cores = len(os.sched_getaffinity(0))
     return {"value": 1.0 / step_s, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"first step of the {n}^2 workload: Step 1+3 ({t_rhs:.2f} s) and {it} "
+            "sample": f"first step of the workload: Step 1+3 ({t_rhs:.2f} s) and {it} "
                       f"iterations of the oracle's plain projected CG ({t_iter * 1e3:.1f} ms "
                       f"each, relres {rel:.2e}); {k_need:.0f} iterations to 1e-8 extrapolated "
                       f"at the measured rate; numpy/scipy threads on {cores} cores"}
@@ -166,13 +192,13 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline(args.n, args.cpu_seconds)
+    cb = cpu_baseline(args.n, args.cpu_seconds, kind=args.workload)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"2D torso slice {args.n}^2, dt 0.1 ms, seeded stimulus",
-                       "solver": "oracle pinned sparse direct"},
+            "config": {"workload": workload_name(args),
+                       "solver": "oracle plain projected CG (bounded sample)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -366,7 +392,7 @@ def main():
     from paper_1711_08708_gb300 import bid
 
     dev = torch.device("cuda", local)
-    mesh, p, stim = workload(args.n, seed=rank)
+    mesh, p, stim = workload(args.n, seed=rank, kind=args.workload)
     S = bid.System(mesh, p)
     NH, N = S.NH, S.N
     ist_h = stim[S.perm[:NH]]
@@ -474,8 +500,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {
-            "workload": f"2D torso slice {args.n}^2 (N={N}, N_H={NH}), dt 0.1 ms, "
-                        "seeded stimulus disc, PCG rel-res 1e-8",
+            "workload": workload_name(args, N, NH),
             "form": {"eps": args.eps, "factor_precision": args.precision},
             "mean_pcg_iters": float(np.mean(chosen["iters"])),
             "l2": "inputs larger than L2 (factor + matrices several GB)",
@@ -501,7 +526,7 @@ def main():
         "clocks": chosen["clocks"],
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds, kind=args.workload)
     if rank == 0:
         print(json.dumps(line))
     if dist:
