@@ -2,12 +2,13 @@
 __graft_entry__.smoke() and bench.py's CPU baseline may use it).
 
 The network maps the last three steps' extracellular and transmembrane
-potentials, sampled on the node grid of a structured slice, to the increment
-of the extracellular potential at the next step; the increment added to the
-last U is the initial guess of PCG (the paper's method is unchanged: the guess
-only changes the iteration count).  Architecture: three 3 x 3 convolutions
-with zero padding ("same" size), 6 -> 32 -> 32 -> 1 channels, ReLU after the
-first two; loss: mean squared error over all grid points.
+potentials, sampled on the node grid of a structured slice, to the increments
+of both potentials at the next step (the next step's solution X = (U, V));
+added to the last state they give the initial guess of PCG (the paper's
+method is unchanged: the guess only changes the iteration count).
+Architecture: three 3 x 3 convolutions with zero padding ("same" size),
+6 -> 32 -> 32 -> 2 channels, ReLU after the first two; loss: mean squared
+error over all grid points and both output channels.
 
 Everything here is plain FP64 numpy written from the definitions:
   conv:  out[i, j, o] = b[o] + sum_{c, ky, kx} W[o, c, ky, kx] x[i + ky - 1, j + kx - 1, c]
@@ -24,7 +25,7 @@ from __future__ import annotations
 
 import numpy as np
 
-LAYERS = ((6, 32), (32, 32), (32, 1))
+LAYERS = ((6, 32), (32, 32), (32, 2))
 
 
 def init_params(seed: int, layers=LAYERS):
@@ -69,7 +70,7 @@ def conv3x3_backward(x, W, dout):
 
 
 def forward(params, x, rnd=None):
-    """Network output (B, H, W) and the per-layer inputs / pre-activations."""
+    """Network output (B, H, W, cout) and the per-layer inputs / pre-activations."""
     r = rnd if rnd is not None else (lambda a: a)
     a = x
     cache = []
@@ -80,16 +81,17 @@ def forward(params, x, rnd=None):
         z = conv3x3(a_in, Wr, b)
         cache.append((a_in, Wr, z))
         a = np.maximum(z, 0.0) if k < n - 1 else z
-    return a[..., 0], cache
+    return a, cache
 
 
 def loss_and_grads(params, x, target, rnd=None):
-    """MSE loss and its gradients [(dW, db), ...] (same structure as params)."""
+    """MSE loss over all outputs (target (B, H, W, cout)) and its gradients
+    [(dW, db), ...] (same structure as params)."""
     y, cache = forward(params, x, rnd)
     P = y.size
     diff = y - target
     loss = float((diff * diff).sum() / P)
-    g = (2.0 / P) * diff[..., None]
+    g = (2.0 / P) * diff
     grads = [None] * len(params)
     for k in range(len(params) - 1, -1, -1):
         a_in, Wr, z = cache[k]

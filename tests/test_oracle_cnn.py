@@ -48,7 +48,7 @@ def test_gradients_match_finite_differences(k):
     params = cnn.init_params(7)
     params = [(W, rng.normal(scale=0.1, size=b.shape)) for W, b in params]
     x = rng.normal(size=(2, 8, 10, 6))
-    t = rng.normal(size=(2, 8, 10))
+    t = rng.normal(size=(2, 8, 10, 2))
     _, grads = cnn.loss_and_grads(params, x, t)
     dW, db = grads[k]
     W = params[k][0]
