@@ -19,6 +19,10 @@ bounded sample of the same workload (see cpu_baseline).
 nodes with --n 161; --eps / --precision choose the reduced form, the plain
 form is FP64 exact factors).
 
+--workload learned times the learned initial guess (config of the learned
+form): online training on plain steps, then held-out steps with and without
+the guess.
+
 --workload batched times the batched form instead: 64 seeded torso slices
 (sides 129 ... 1025 nodes, seed 2026) advanced together, one graph launch of
 the PCG loop per step for all slices, leaf sizes from the tuner; its line
@@ -55,7 +59,12 @@ def parse():
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
-    a.add_argument("--workload", default="slice", choices=["slice", "batched", "slab3d"])
+    a.add_argument("--workload", default="slice", choices=["slice", "batched", "slab3d", "learned"])
+    a.add_argument("--train-runs", type=int, default=3)
+    a.add_argument("--train-steps", type=int, default=60)
+    a.add_argument("--eval-runs", type=int, default=2)
+    a.add_argument("--guess-dv", type=int, default=1)
+    a.add_argument("--guess-policy", type=int, default=1)
     a.add_argument("--slices", type=int, default=64)
     a.add_argument("--no-sequential", action="store_true")
     return a.parse_args()
@@ -372,12 +381,121 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    """Learned initial guess on the 2049^2 slice (chosen form): the network is
+    trained online on plain steps of training stimuli, then held-out stimuli
+    are stepped with the learned guess and with the previous-step guess."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_08708_gb300 import bid
+    from workloads import torso_square_2d, params_2d, stimulus_seeded_disc
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    n, dt = args.n, 0.1
+    mesh, p = torso_square_2d(n), params_2d(dt)
+    S = bid.System(mesh, p)
+    P = bid.Precond(S, dt, eps=args.eps, precision=args.precision)
+    crop, ncrops = 128, 16
+    net = bid.Cnn(ncrops * crop * crop, seed=3)
+    G = bid.Guess(S, net, n, n, max_batch_pixels=ncrops * crop * crop)
+
+    def state(seed):
+        U = torch.zeros(S.N, dtype=torch.float64, device=dev)
+        V = torch.full((S.NH,), p["v_rest"], dtype=torch.float64, device=dev)
+        h = torch.ones(S.NH, dtype=torch.float64, device=dev)
+        I = torch.tensor(stimulus_seeded_disc(mesh, seed=seed)[S.perm[:S.NH]], dtype=torch.float64,
+                         device=dev)
+        return U, V, h, I
+
+    t0 = time.perf_counter()
+    train_steps = 0
+    for seed in range(100, 100 + args.train_runs):
+        U, V, h, I = state(seed)
+        G.reset()
+        G.push(U, V)
+        for k in range(args.train_steps):
+            P.step(U, V, h, I, k * dt, 1, tol=args.tol)
+            G.push(U, V)
+            if k >= 3:
+                G.train(ncrops=ncrops, crop=crop, iters=8, lr=2e-3, seed=seed * 1000 + k)
+            train_steps += 1
+    train_s = time.perf_counter() - t0
+
+    def run(seed, learned):
+        U, V, h, I = state(seed)
+        if learned:
+            G.reset()
+            G.push(U, V)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        l0 = bid.kernel_launches()
+        with Clocks(local) as ck:
+            e0.record(st)
+            if learned:
+                stats = G.step(P, U, V, h, I, 0.0, args.steps, tol=args.tol)
+                its = stats[:, 0]
+            else:
+                stats = None
+                its = P.step(U, V, h, I, 0.0, args.steps, tol=args.tol)
+            e1.record(st)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1), np.asarray(its, dtype=float), stats, \
+            bid.kernel_launches() - l0, ck.summary()
+
+    G.configure(use_dv=bool(args.guess_dv), policy=args.guess_policy)
+    seeds = list(range(200, 200 + args.eval_runs))
+    run(seeds[0], True)            # warm-up of both paths (graphs, buffers)
+    run(seeds[0], False)
+    res_l = [run(sd, True) for sd in seeds]
+    res_p = [run(sd, False) for sd in seeds]
+    ms_l = sum(r[0] for r in res_l)
+    ms_p = sum(r[0] for r in res_p)
+    nsteps = args.steps * len(seeds)
+    stats = np.concatenate([r[2] for r in res_l])
+    warm = stats[np.arange(len(stats)) % args.steps >= 3]
+    ratio = warm[:, 2] / np.maximum(warm[:, 1], 1e-300) if args.guess_policy == 0 else np.array([np.nan])
+    value = nsteps / (ms_l * 1e-3)
+    line = {
+        "metric": "bidomain steps/s at PCG rel-res 1e-8 with the learned initial guess (vs the "
+                  "previous-step guess)",
+        "value": value, "unit": "steps/s", "n_gpus": 1, "steps": nsteps, "warmup": args.steps,
+        "ms_per_step": ms_l / nsteps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {
+            "workload": f"learned form: 2D torso slice {n}^2 (N={S.N}, N_H={S.NH}), dt 0.1 ms; "
+                        f"CNN 6->32->32->2, 3x3, BF16 inference; trained online on "
+                        f"{args.train_runs} x {args.train_steps} plain steps (stimulus seeds 100..), "
+                        f"evaluated on {len(seeds)} x {args.steps} held-out steps (seeds 200..)",
+            "form": {"eps": args.eps, "factor_precision": args.precision},
+            "guess": {"predicts_dV": bool(args.guess_dv),
+                      "policy": ["smaller initial residual", "fewer iterations so far"][args.guess_policy]},
+            "train_seconds": train_s, "train_steps": train_steps,
+            "learned": {"steps_per_s": value, "mean_pcg_iters": float(np.mean(np.concatenate(
+                [r[1] for r in res_l]))), "used_fraction": float(warm[:, 3].mean()),
+                "median_initial_residual_ratio": (float(np.median(ratio)) if args.guess_policy == 0
+                                                  else None)},
+            "previous_step": {"steps_per_s": nsteps / (ms_p * 1e-3), "mean_pcg_iters": float(
+                np.mean(np.concatenate([r[1] for r in res_p])))},
+            "l2": "inputs larger than L2 (factor + matrices several GB)",
+            "parallelism": "single GPU",
+        },
+        "gpu_launches": int(sum(r[3] for r in res_l)),
+        "clocks": res_l[-1][4],
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "learned":
+        return run_learned(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -292,6 +292,86 @@ int bid_tune_batch_leaf(bid_system* const* systems, int nslices, const bid_preco
                         const int32_t* cands, int ncands, int reps, int32_t* leaf_out);
 
 /* ---------------------------------------------------------------------------
+ * Learned initial guess.  A small convolutional network on the node grid of
+ * a structured slice -- three 3 x 3 convolutions, 6 -> 32 -> 32 -> 2
+ * channels, ReLU after the first two, zero padding -- maps the last three
+ * steps' U and V (V - v_rest, zero outside the heart) -- as U^n, its last two
+ * increments, V^n and its last two increments, each over a fixed scale -- to
+ * the scaled increments of U and V at the next step.  PCG then starts from
+ * (U^n + dU, V^n + dV) when that guess has a smaller initial residual than
+ * the previous step (U^n, V^n), which stays the fallback.  The guess changes only the iteration count: the
+ * solve and its stopping rule are those of bid_solve.  (The paper has no
+ * counterpart; the network is trained on solves of the method itself.)
+ * ------------------------------------------------------------------------- */
+typedef struct bid_cnn bid_cnn;
+typedef struct bid_guess bid_guess;
+
+/* Number of network parameters, packed as W1 (32, 6, 3, 3), b1 (32),
+ * W2 (32, 32, 3, 3), b2 (32), W3 (2, 32, 3, 3), b3 (2), row-major. */
+int bid_cnn_nparams(void);
+/* A network with He-style random weights from `seed` (FP32 master copy and
+ * Adam moments on the device) and work buffers for batches of up to
+ * max_pixels grid points.  Blocking. */
+int bid_cnn_create(int max_pixels, uint64_t seed, bid_cnn** out);
+/* Host FP64 arrays of bid_cnn_nparams() entries (stored as FP32; set resets Adam). */
+int bid_cnn_set_params(bid_cnn* C, const double* params);
+int bid_cnn_get_params(const bid_cnn* C, double* params);
+/* Mean squared error of the network on a batch (over all points and both
+ * outputs) and its gradient, computed by the library's own forward and
+ * backward kernels in `precision` (BID_FP64: x, t are double; BID_FP32:
+ * float).  x: device (B, H, W, 6) channels-last; t: device (B, H, W, 2).
+ * loss (host) and grad (host, nparams, may be NULL).  Blocking. */
+int bid_cnn_loss_grad(bid_cnn* C, int precision, const void* x, const void* t, int B, int H, int W,
+                      double* loss, double* grad, void* stream);
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the FP32 gradient of
+ * the batch (x, t float, device).  loss (host) may be NULL.  Blocking. */
+int bid_cnn_train_step(bid_cnn* C, const float* x, const float* t, int B, int H, int W, double lr,
+                       double* loss, void* stream);
+/* Network output y (B, H, W, 2).  precision BID_FP64 (x, y double) or BID_FP32
+ * (float): direct convolutions; BID_BF16: one grid (B = 1), x and y float,
+ * BF16 weights and activations on the tensor cores with FP32 accumulation. */
+int bid_cnn_forward(bid_cnn* C, int precision, const void* x, int B, int H, int W, void* y,
+                    void* stream);
+void bid_cnn_destroy(bid_cnn* C);
+
+/* The guess for system s on an H x W grid: node_pixel (host, one entry per
+ * mesh node) is a bijection of the nodes onto the grid points (row-major).
+ * max_batch_pixels: training batch capacity (ncrops * crop^2).  The network
+ * is borrowed.  Errors: BID_EINVAL (H W != N, not a bijection). */
+int bid_guess_create(bid_system* s, bid_cnn* net, int H, int W, const int32_t* node_pixel,
+                     int max_batch_pixels, bid_guess** out);
+/* Append a solved state (U, V device, library numbering) to the history. */
+int bid_guess_push(bid_guess* G, const double* U, const double* V, void* stream);
+int bid_guess_reset(bid_guess* G);
+/* `iters` Adam steps on random crops (ncrops of crop x crop points, origins
+ * from `seed`) of the newest history entry: inputs the states n-1, n-2, n-3,
+ * targets U^n - U^n-1 and V^n - V^n-1.  The first call fixes the scales (RMS
+ * of U, V - v_rest and of both increments over the grid).  Needs four
+ * states.  Blocking. */
+int bid_guess_train(bid_guess* G, int ncrops, int crop, int iters, double lr, uint64_t seed,
+                    double* loss, void* stream);
+/* scales[4] (host): U, V - v_rest, dU, dV (0 before the first training call). */
+int bid_guess_scales(const bid_guess* G, double* scales);
+/* X0 = (U + dU, V + dV) from the last three history states (device, N + N_H). */
+int bid_guess_predict(bid_guess* G, const double* U, const double* V, double* X0, void* stream);
+/* use_dv: apply the predicted V increment (1, default) or keep V^n (0).
+ * policy 0 (default): each step starts from the guess with the smaller
+ * initial residual; policy 1: from the guess that needed fewer PCG
+ * iterations on average so far (each guess is tried at least twice, and the
+ * other one every 8th step).  Resets the iteration record. */
+int bid_guess_configure(bid_guess* G, int use_dv, int policy);
+/* bid_step with the learned guess (when three states are known; else the
+ * previous step) chosen by the guess's policy; the new state is pushed to
+ * the history.  stats (host, n_steps x 4 or NULL): PCG iterations, relative
+ * initial residual of the previous-step guess and of the learned guess
+ * (policy 0; 0 when not computed), and 1 when the learned guess was used.
+ * Blocking. */
+int bid_step_learned(bid_system* s, bid_precond* P, bid_guess* G, double* U, double* V, double* h,
+                     const double* Ist, double t0, int n_steps, double tol, int max_iter,
+                     double* stats, void* stream);
+void bid_guess_destroy(bid_guess* G);
+
+/* ---------------------------------------------------------------------------
  * Host-only entry points (no GPU needed).  They expose the host half of the
  * library -- the P1 assembly and the hierarchical factor build -- together
  * with a sequential host replay of the factor's level-by-level triangular

@@ -104,6 +104,23 @@ SIGNATURES = {
     "bid_tune_batch_leaf": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, _I, _I, _VP]),
     "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _VP, _VP,
                                          C.POINTER(PrecondStats)]),
+    "bid_cnn_nparams": (_I, []),
+    "bid_cnn_create": (_I, [_I, C.c_uint64, C.POINTER(_VP)]),
+    "bid_cnn_set_params": (_I, [_VP, _VP]),
+    "bid_cnn_get_params": (_I, [_VP, _VP]),
+    "bid_cnn_loss_grad": (_I, [_VP, _I, _VP, _VP, _I, _I, _I, _VP, _VP, _VP]),
+    "bid_cnn_train_step": (_I, [_VP, _VP, _VP, _I, _I, _I, _D, _VP, _VP]),
+    "bid_cnn_forward": (_I, [_VP, _I, _VP, _I, _I, _I, _VP, _VP]),
+    "bid_cnn_destroy": (None, [_VP]),
+    "bid_guess_create": (_I, [_VP, _VP, _I, _I, _VP, _I, C.POINTER(_VP)]),
+    "bid_guess_push": (_I, [_VP, _VP, _VP, _VP]),
+    "bid_guess_reset": (_I, [_VP]),
+    "bid_guess_train": (_I, [_VP, _I, _I, _I, _D, C.c_uint64, _VP, _VP]),
+    "bid_guess_scales": (_I, [_VP, _VP]),
+    "bid_guess_configure": (_I, [_VP, _I, _I]),
+    "bid_guess_predict": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "bid_step_learned": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _D, _I, _D, _I, _VP, _VP]),
+    "bid_guess_destroy": (None, [_VP]),
 }
 
 
@@ -346,6 +363,102 @@ class Batch:
     def __del__(self):
         if getattr(self, "h", None):
             lib.bid_batch_destroy(self.h)
+            self.h = None
+
+
+class Cnn:
+    """bid_cnn: the guess network (3 x 3 convolutions 6 -> 32 -> 32 -> 2)."""
+
+    def __init__(self, max_pixels, seed=0):
+        h = _VP()
+        _check(lib.bid_cnn_create(int(max_pixels), int(seed), C.byref(h)))
+        self.h = h
+        self.nparams = int(lib.bid_cnn_nparams())
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float64)
+        assert flat.size == self.nparams
+        _check(lib.bid_cnn_set_params(self.h, _ptr(flat)))
+
+    def get_params(self):
+        out = np.empty(self.nparams)
+        _check(lib.bid_cnn_get_params(self.h, _ptr(out)))
+        return out
+
+    def loss_grad(self, x, t, precision="fp64", stream=None):
+        """x: device (B, H, W, 6), t: device (B, H, W, 2); returns (loss, grad)."""
+        B, H, W = (int(v) for v in t.shape[:3])
+        loss = np.zeros(1)
+        grad = np.empty(self.nparams)
+        _check(lib.bid_cnn_loss_grad(self.h, PRECISIONS[precision], _ptr(x), _ptr(t), B, H, W,
+                                     _ptr(loss), _ptr(grad), _stream(stream)))
+        return float(loss[0]), grad
+
+    def train_step(self, x, t, lr, stream=None):
+        B, H, W = (int(v) for v in t.shape[:3])
+        loss = np.zeros(1)
+        _check(lib.bid_cnn_train_step(self.h, _ptr(x), _ptr(t), B, H, W, float(lr), _ptr(loss),
+                                      _stream(stream)))
+        return float(loss[0])
+
+    def forward(self, x, y, precision="bf16", stream=None):
+        B, H, W = (int(v) for v in y.shape[:3])
+        _check(lib.bid_cnn_forward(self.h, PRECISIONS[precision], _ptr(x), B, H, W, _ptr(y),
+                                   _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bid_cnn_destroy(self.h)
+            self.h = None
+
+
+class Guess:
+    """bid_guess: history of solved states on the grid + the network."""
+
+    def __init__(self, system: System, net: Cnn, H, W, node_pixel=None, max_batch_pixels=1 << 18):
+        if node_pixel is None:
+            node_pixel = np.arange(H * W, dtype=np.int32)
+        node_pixel = np.ascontiguousarray(node_pixel, dtype=np.int32)
+        h = _VP()
+        _check(lib.bid_guess_create(system.h, net.h, int(H), int(W), _ptr(node_pixel),
+                                    int(max_batch_pixels), C.byref(h)))
+        self.h, self.system, self.net = h, system, net
+
+    def push(self, U, V, stream=None):
+        _check(lib.bid_guess_push(self.h, _ptr(U), _ptr(V), _stream(stream)))
+
+    def reset(self):
+        _check(lib.bid_guess_reset(self.h))
+
+    def configure(self, use_dv=True, policy=0):
+        _check(lib.bid_guess_configure(self.h, int(bool(use_dv)), int(policy)))
+
+    def train(self, ncrops=8, crop=128, iters=1, lr=1e-3, seed=0, stream=None):
+        loss = np.zeros(1)
+        _check(lib.bid_guess_train(self.h, int(ncrops), int(crop), int(iters), float(lr), int(seed),
+                                   _ptr(loss), _stream(stream)))
+        return float(loss[0])
+
+    def scales(self):
+        v = np.zeros(4)
+        _check(lib.bid_guess_scales(self.h, _ptr(v)))
+        return tuple(float(a) for a in v)
+
+    def predict(self, U, V, X0, stream=None):
+        _check(lib.bid_guess_predict(self.h, _ptr(U), _ptr(V), _ptr(X0), _stream(stream)))
+
+    def step(self, P: "Precond", U, V, h, Ist, t0, n_steps, tol=1e-8, max_iter=200, stream=None):
+        """bid_step_learned; returns an (n_steps, 4) array: iterations, initial
+        residual of the previous-step guess, of the learned guess, used flag."""
+        stats = np.zeros((max(n_steps, 1), 4))
+        _check(lib.bid_step_learned(self.system.h, P.h, self.h, _ptr(U), _ptr(V), _ptr(h), _ptr(Ist),
+                                    float(t0), int(n_steps), float(tol), int(max_iter), _ptr(stats),
+                                    _stream(stream)))
+        return stats[:n_steps]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib.bid_guess_destroy(self.h)
             self.h = None
 
 

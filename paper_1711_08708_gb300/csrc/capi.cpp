@@ -553,6 +553,72 @@ int bid_step(bid_system* s, bid_precond* P, double* U, double* V, double* h, con
     return rc;
 }
 
+int bid_step_learned(bid_system* s, bid_precond* P, bid_guess* G, double* U, double* V, double* h,
+                     const double* Ist, double t0, int n_steps, double tol, int max_iter, double* stats,
+                     void* stream) {
+    if (!s || !P || !G || P->sys != s || !U || !V || !h) return set_error(BID_EINVAL, "bad argument");
+    if (n_steps < 0 || !(tol > 0.0) || max_iter < 1) return set_error(BID_EINVAL, "bad step arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
+    const double dt = P->opts.dt;
+    Launch L = launch_of(s, stream);
+    BID_CUDA_TRY(cudaMemcpyAsync(P->xs, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    BID_CUDA_TRY(cudaMemcpyAsync(P->xs + N, V, sizeof(double) * NH, cudaMemcpyDeviceToDevice, st));
+    // relative initial residual ||p(Y - Lambda X0)|| / ||Y|| of a guess
+    auto r0 = [&](const double* X0, double* out) -> int {
+        BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, X0, P->r, P->ytmp, P->sc,
+                              P->partials));
+        BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+        DevScalars hs{};
+        BID_TRY(read_scalars(P, st, &hs));
+        *out = hs.yy > 0.0 ? std::sqrt(hs.rr / hs.yy) : 0.0;
+        return BID_OK;
+    };
+    int rc = BID_OK;
+    for (int k = 0; k < n_steps && rc == BID_OK; ++k) {
+        const double t = t0 + k * dt;
+        const int on = (t >= s->params.stim_t_on && t < s->params.stim_t_off) ? 1 : 0;
+        rc = launch_rhs_gate(L, N, NH, P->xs + N, h, Ist, on, s->mH, s->params, dt, P->ytmp);
+        double rp = 0.0, rl = 0.0;
+        int used = 0;
+        const bool ready = guess_ready(G) != 0;
+        const int policy = guess_policy(G);
+        if (policy == 0) {   // judge by the initial residual
+            if (rc == BID_OK) rc = r0(P->xs, &rp);
+            if (rc == BID_OK && ready) {
+                double* x0 = nullptr;
+                rc = guess_predict(G, P->xs, P->xs + N, &x0, st);
+                if (rc == BID_OK) rc = r0(x0, &rl);
+                if (rc == BID_OK && std::isfinite(rl) && rl < rp) {
+                    used = 1;
+                    if (cudaMemcpyAsync(P->xs, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                        rc = set_error(BID_ECUDA, "copy of the guess failed");
+                }
+            }
+        } else if (ready && rc == BID_OK && guess_choose(G) == 1) {   // judge by iterations
+            double* x0 = nullptr;
+            rc = guess_predict(G, P->xs, P->xs + N, &x0, st);
+            used = 1;
+            if (rc == BID_OK && cudaMemcpyAsync(P->xs, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = set_error(BID_ECUDA, "copy of the guess failed");
+        }
+        bid_solve_info inf{};
+        if (rc == BID_OK) rc = solve_impl(P, P->ytmp, P->xs, tol, max_iter, &inf, st);
+        if (rc == BID_OK && ready && policy == 1) guess_record(G, used, inf.iters);
+        if (rc == BID_OK) rc = guess_push(G, P->xs, P->xs + N, st);
+        if (stats) {
+            stats[4 * k] = inf.iters;
+            stats[4 * k + 1] = rp;
+            stats[4 * k + 2] = rl;
+            stats[4 * k + 3] = used;
+        }
+    }
+    BID_CUDA_TRY(cudaMemcpyAsync(U, P->xs, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    BID_CUDA_TRY(cudaMemcpyAsync(V, P->xs + N, sizeof(double) * NH, cudaMemcpyDeviceToDevice, st));
+    BID_CUDA_TRY(cudaStreamSynchronize(st));
+    return rc;
+}
+
 void bid_destroy_system(bid_system* s) {
     if (!s) return;
     free_sell(&s->S1);

@@ -413,6 +413,15 @@ int blaunch_normalise(const Launch& L, const BGeom& g, const BTasks& T, double* 
 int blaunch_check(const Launch& L, int S, const BScal& c, unsigned long long h, int use_graph,
                   int first);
 
+// ---------------------------------------------------------------- learned guess
+int guess_ready(const bid_guess* G);
+int guess_push(bid_guess* G, const double* U, const double* V, cudaStream_t st);
+// *X0 points at the guess's own buffer (N + N_H)
+int guess_predict(bid_guess* G, const double* U, const double* V, double** X0, cudaStream_t st);
+int guess_policy(const bid_guess* G);
+int guess_choose(bid_guess* G);                    // arm of the next step (policy 1)
+void guess_record(bid_guess* G, int arm, int iters);
+
 // ---------------------------------------------------------------- handles
 }  // namespace bid
 
