@@ -333,6 +333,7 @@ int bsolve(bid_batch* B, const double* Y, double* X, double tol, int max_iter,
         }
         if (h.i[NI * S + 1]) {   // a bounded wait of a factor solve expired
             BID_CUDA_TRY(cudaMemsetAsync(B->hs.err, 0, sizeof(unsigned int), st));
+            BID_CUDA_TRY(cudaMemsetAsync(B->hs.gbar, 0, 2 * sizeof(unsigned int), st));
             BID_CUDA_TRY(cudaStreamSynchronize(st));
             return set_error(BID_ETIMEOUT, "a bounded device wait of the factor solve expired");
         }
@@ -471,6 +472,9 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     if (rc == BID_OK) rc = dalloc(&B->hs.pbuf, std::max(h1.pbuf, hk.pbuf));
     const int ntk = std::max(1, std::max(h1.ntickets, hk.ntickets));
     if (rc == BID_OK) rc = dalloc(&B->hs.tickets, ntk);
+    if (rc == BID_OK) rc = dalloc(&B->hs.gbar, 2);
+    if (rc == BID_OK && cudaMemset(B->hs.gbar, 0, 2 * sizeof(unsigned int)) != cudaSuccess)
+        rc = set_error(BID_ECUDA, "cudaMemset failed");
     const int maxcta = std::max(B->nvt, std::max(B->nlt, B->nht));
     if (rc == BID_OK) rc = dalloc(&B->partials, (int64_t)maxcta * 3);
     if (rc == BID_OK) rc = dalloc(&B->dscal, (int64_t)ND * nslices + 1);
@@ -599,7 +603,7 @@ void bid_batch_destroy(bid_batch* B) {
                     (void*)B->ytmp, (void*)B->z1b, (void*)B->t, (void*)B->w, (void*)B->partials,
                     (void*)B->dscal, (void*)B->iscal, (void*)B->tickets, (void*)B->hs.ybuf,
                     (void*)B->hs.xp, (void*)B->hs.inb, (void*)B->hs.vbuf, (void*)B->hs.tbuf,
-                    (void*)B->hs.pbuf, (void*)B->hs.tickets})
+                    (void*)B->hs.pbuf, (void*)B->hs.tickets, (void*)B->hs.gbar})
         cudaFree(p);
     if (B->host_pinned) cudaFreeHost(B->host_pinned);
     if (B->gexec) cudaGraphExecDestroy(B->gexec);

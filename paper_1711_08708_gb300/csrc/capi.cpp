@@ -252,6 +252,7 @@ int solve_impl(bid_precond* P, const double* Y, double* X, double tol, int max_i
         if (h.herr) {   // a bounded wait of a factor solve expired: results are invalid
             const unsigned int zero = 0;
             BID_CUDA_TRY(cudaMemcpyAsync(&P->sc->herr, &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+            BID_CUDA_TRY(cudaMemsetAsync(P->hs.gbar, 0, 2 * sizeof(unsigned int), st));
             BID_CUDA_TRY(cudaStreamSynchronize(st));
             return set_error(BID_ETIMEOUT, "a bounded device wait of the factor solve expired");
         }
@@ -427,6 +428,9 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (rc == BID_OK) rc = dalloc(&P->hs.pbuf, std::max(h1.pbuf, hk.pbuf));
     if (rc == BID_OK) rc = dalloc(&P->hs.tickets, std::max(h1.ntickets, hk.ntickets));
     if (rc == BID_OK && cudaMemset(P->hs.tickets, 0, sizeof(unsigned int) * std::max(1, std::max(h1.ntickets, hk.ntickets))) != cudaSuccess)
+        rc = set_error(BID_ECUDA, "cudaMemset failed");
+    if (rc == BID_OK) rc = dalloc(&P->hs.gbar, 2);
+    if (rc == BID_OK && cudaMemset(P->hs.gbar, 0, 2 * sizeof(unsigned int)) != cudaSuccess)
         rc = set_error(BID_ECUDA, "cudaMemset failed");
     if (rc == BID_OK) rc = dalloc(&P->partials, (int64_t)s->sms * 8 * 4);
     if (rc == BID_OK) rc = dalloc(&P->sc, 1);
@@ -636,6 +640,7 @@ void bid_destroy_precond(bid_precond* P) {
                       P->hs.xp, P->hs.inb, P->hs.vbuf, P->hs.tbuf, P->hs.pbuf, P->partials})
         cudaFree(p);
     cudaFree(P->hs.tickets);
+    cudaFree(P->hs.gbar);
     cudaFree(P->sc);
     if (P->host_pinned) cudaFreeHost(P->host_pinned);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);

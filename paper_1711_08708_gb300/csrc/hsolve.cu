@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -83,6 +84,15 @@ __device__ __forceinline__ A wsum(A v) {
     return v;
 }
 
+// Programmatic dependent launch (griddepcontrol): the solve's kernels are
+// launched so that the next one may start while the previous one drains; a
+// kernel reads or writes nothing that its predecessors produce or consume
+// before pdl_wait() (only immutable factor data and descriptors, and the bulk
+// copies of factor data into its own shared memory), and every CTA executes
+// pdl_wait() on every path.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 struct HView {
     int32_t pin;
     const int32_t* __restrict__ pidx;
@@ -104,7 +114,9 @@ __device__ __forceinline__ double incoming(const HView& v, const HSnode& sn, int
                                            const double* inb) {
     const int o = sn.inc_off + 2 * f;
     const int2 flags = *reinterpret_cast<const int2*>(v.inc + o);
-    const double2 val = *reinterpret_cast<const double2*>(inb + o);
+    // L2 load: in the persistent upper-level kernels the slots are written by
+    // other CTAs earlier in the same launch (L1 is not coherent across SMs)
+    const double2 val = __ldcg(reinterpret_cast<const double2*>(inb + o));
     double s = 0.0;
     if (flags.x >= 0) s += val.x;
     if (flags.y >= 0) s += val.y;
@@ -183,12 +195,17 @@ __device__ __forceinline__ void bulk_region(unsigned char* dst, const void* src,
     for (int o = 0; o < nbytes; o += BULK_CHUNK)
         bulk_g2s(dst + o, s + o, (uint32_t)min(BULK_CHUNK, nbytes - o), bar);
 }
-// Thread 0: arm the barrier with the group's byte count and issue its copies:
-// factor data at dst, then (sbytes > 0) the update slots right after it.
-__device__ __forceinline__ void group_load(unsigned char* dst, const void* data, int nbytes,
-                                           const double* slots, int sbytes, uint64_t* bar) {
+// Thread 0: arm the barrier with the group's byte count (factor data and
+// update slots) and issue the copy of the factor data (immutable: may run
+// before pdl_wait); the slots, written by the previous levels, are copied
+// after it by group_load_slots.
+__device__ __forceinline__ void group_load(unsigned char* dst, const void* data, int nbytes, int sbytes,
+                                           uint64_t* bar) {
     mbar_arrive_expect_tx(bar, (uint32_t)(nbytes + sbytes));
     bulk_region(dst, data, nbytes, bar);
+}
+__device__ __forceinline__ void group_load_slots(unsigned char* dst, int nbytes, const double* slots,
+                                                 int sbytes, uint64_t* bar) {
     if (sbytes > 0) bulk_region(dst + nbytes, slots, sbytes, bar);
 }
 
@@ -235,7 +252,7 @@ __device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q
 // backward input of dense row q of cluster sn
 __device__ __forceinline__ double vrow(const HView& v, const HSnode& sn, int q,
                                        const double* ybuf, const double* out) {
-    return q < sn.ni ? ybuf[sn.first + q] : -out[v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]];
+    return q < sn.ni ? ybuf[sn.first + q] : -__ldcg(out + v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]);
 }
 
 // Input shift of a solve: one scalar mean, or one mean per segment.
@@ -252,6 +269,8 @@ __global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict
                                                 const uint8_t* __restrict__ pinflag,
                                                 const double* __restrict__ b, HShift sh,
                                                 double* __restrict__ xp) {
+    pdl_wait();
+    pdl_trigger();
     const double shift = sh.sum ? (*sh.sum) * sh.inv_n : 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int vi = pidx[i];
@@ -293,10 +312,13 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
     const int nc = G.c1 - G.c0;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
-        group_load(dyn_smem, data + G.dstart, G.nbytes, inb + G.sstart, G.sbytes, &bar);
+        group_load(dyn_smem, data + G.dstart, G.nbytes, G.sbytes, &bar);
     }
-    // contiguous ranges of the group: descriptors and right-hand side
     for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) group_load_slots(dyn_smem, G.nbytes, inb + G.sstart, G.sbytes, &bar);
+    // contiguous range of the group's right-hand side
     for (int f = threadIdx.x; f < G.wf; f += FT) w[f] = (A)xp[G.pstart + f];
     __syncthreads();
     if (!mbar_wait_bounded(&bar)) {
@@ -369,9 +391,11 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
     const int nc = G.c1 - G.c0;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
-        group_load(dyn_smem, data + G.dstart, G.nbytes, nullptr, 0, &bar);
+        group_load(dyn_smem, data + G.dstart, G.nbytes, 0, &bar);
     }
     for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+    pdl_wait();
+    pdl_trigger();
     __syncthreads();
     for (int f = threadIdx.x; f < G.wb; f += FT) {
         const GCl& c = scl[group_owner<1>(scl, nc, f)];
@@ -417,15 +441,11 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
 // Low-rank task: one CTA per group: t = V^T w_s (all ni columns), then
 // u = incoming - U t for the group's rows.
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ data, int task0,
-                                               const double* xp, double* ybuf, double* inb,
-                                               double* tbuf, double* pbuf,
-                                               unsigned int* tickets) {
+__device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict__ data, const HTask& t,
+                                            const double* xp, double* ybuf, double* inb, double* tbuf,
+                                            double* pbuf, unsigned int* tickets, unsigned char* smem,
+                                            A (&red)[HT][VecOf<T>::N], bool& last) {
     constexpr int VEC = VecOf<T>::N;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ A red[HT][VEC];
-    __shared__ bool last;
-    const HTask t = v.uft[task0 + blockIdx.x];
     const int tid = threadIdx.x;
     if (t.s < 0) {
         const HLr g = v.lr[-1 - t.s];
@@ -537,32 +557,44 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
     if (tid == 0) tickets[t.ticket] = 0u;
 }
 
-// Backward preparation of one level.  CTAs [0, ng): t_g = U_g^T v_g for the
-// low-rank groups; CTAs [ng, ng + nv): staging v = [y_s; -x_B] of a large
-// cluster into vbuf.
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_bwd_prep(HView v, const T* __restrict__ data, int g0,
-                                                 int ng, int vg0, const double* __restrict__ ybuf,
-                                                 const double* out, double* tbuf, double* vbuf) {
-    __shared__ A vv[LR_ROWS];
-    __shared__ A red[HT];
-    if ((int)blockIdx.x >= ng) {
-        const HSnode sn = v.sn[v.vgl[vg0 + blockIdx.x - ng]];
+__global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ data, int task0,
+                                               const double* xp, double* ybuf, double* inb,
+                                               double* tbuf, double* pbuf,
+                                               unsigned int* tickets) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ A red[HT][VecOf<T>::N];
+    __shared__ bool last;
+    const HTask t = v.uft[task0 + blockIdx.x];
+    pdl_wait();
+    pdl_trigger();
+    up_fwd_task<T, A>(v, data, t, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
+}
+
+// Backward preparation of one level, work item i: i < ng: t_g = U_g^T v_g for
+// the low-rank group g0 + i; else staging v = [y_s; -x_B] of the large
+// cluster vgl[vg0 + i - ng] into vbuf.
+template <typename T, typename A>
+__device__ __forceinline__ void prep_task(const HView& v, const T* __restrict__ data, int i, int g0, int ng,
+                                          int vg0, const double* __restrict__ ybuf, const double* out,
+                                          double* tbuf, double* vbuf, A (&vv)[LR_ROWS], A (&red)[HT]) {
+    if (i >= ng) {
+        const HSnode sn = v.sn[v.vgl[vg0 + i - ng]];
         for (int q = threadIdx.x; q < sn.nd + 2 * VecOf<T>::N; q += HT)
             vbuf[sn.v_off + q] = q < sn.nd ? vrow(v, sn, q, ybuf, out) : 0.0;
         return;
     }
-    const HLr g = v.lr[g0 + blockIdx.x];
+    const HLr g = v.lr[g0 + i];
     const HSnode sn = v.sn[g.s];
-    for (int i = threadIdx.x; i < g.m; i += HT)
-        vv[i] = (A)(-out[v.bidx[sn.bidx_off + g.row0 + i - sn.ni]]);
+    for (int r = threadIdx.x; r < g.m; r += HT)
+        vv[r] = (A)(-__ldcg(out + v.bidx[sn.bidx_off + g.row0 + r - sn.ni]));
     __syncthreads();
     const int kp = g.k <= 32 ? 32 : 64, nq = HT / kp;
     const int l = threadIdx.x % kp, grp = threadIdx.x / kp;
     A acc = 0;
     if (l < g.k) {
         const T* U = data + g.off_u;
-        for (int i = grp; i < g.m; i += nq) acc += (A)ldv(U + (int64_t)i * g.k + l) * vv[i];
+        for (int r = grp; r < g.m; r += nq) acc += (A)ldv(U + (int64_t)r * g.k + l) * vv[r];
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -573,17 +605,26 @@ __global__ void __launch_bounds__(HT) k_bwd_prep(HView v, const T* __restrict__ 
     }
 }
 
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_bwd_prep(HView v, const T* __restrict__ data, int g0,
+                                                 int ng, int vg0, const double* __restrict__ ybuf,
+                                                 const double* out, double* tbuf, double* vbuf) {
+    __shared__ A vv[LR_ROWS];
+    __shared__ A red[HT];
+    pdl_wait();
+    pdl_trigger();
+    prep_task<T, A>(v, data, blockIdx.x, g0, ng, vg0, ybuf, out, tbuf, vbuf, vv, red);
+}
+
 // Backward, large clusters: a column is shared by wpc = t.b0 warps (1..8, from
 // the column length), a CTA holds 8 / wpc columns; warp w of a column covers
 // a 1/wpc share of its rows (aligned vectors, v from vbuf).  The wpc partials
 // are summed in order, plus the low-rank terms.
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ data, int task0,
-                                               const double* vbuf, const double* tbuf,
-                                               double* out) {
+__device__ __forceinline__ void up_bwd_task(const HView& v, const T* __restrict__ data, const HTask& t,
+                                            const double* vbuf, const double* tbuf, double* out,
+                                            A (&red)[NW]) {
     constexpr int VEC = VecOf<T>::N;
-    __shared__ A red[NW];
-    const HTask t = v.ubt[task0 + blockIdx.x];
     const HSnode sn = v.sn[t.s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpc = t.b0;
@@ -606,7 +647,7 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
                     const int q = q0 + u * 32 * VEC + e;
-                    if (q >= j && q < r1) acc += val[u][e] * (A)vv[q];
+                    if (q >= j && q < r1) acc += val[u][e] * (A)__ldcg(vv + q);
                 }
         }
         for (; q0 < r1; q0 += 32 * VEC) {
@@ -615,14 +656,14 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
                 const int q = q0 + e;
-                if (q >= j && q < r1) acc += val[e] * (A)vv[q];
+                if (q >= j && q < r1) acc += val[e] * (A)__ldcg(vv + q);
             }
         }
         if (part == 0)
             for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
                 const HLr G = v.lr[g];
                 const T* V = data + G.off_v + (int64_t)j * G.k;
-                for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)tbuf[G.t_off + l];
+                for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)__ldcg(tbuf + G.t_off + l);
             }
     }
     acc = wsum(acc);
@@ -636,6 +677,100 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
             for (int w = 0; w < wpc; ++w) s += red[threadIdx.x * wpc + w];
             out[v.pidx[sn.first + jj]] = (double)s;
         }
+    }
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ data, int task0,
+                                               const double* vbuf, const double* tbuf,
+                                               double* out) {
+    __shared__ A red[NW];
+    const HTask t = v.ubt[task0 + blockIdx.x];
+    pdl_wait();
+    pdl_trigger();
+    up_bwd_task<T, A>(v, data, t, vbuf, tbuf, out, red);
+}
+
+// ------------------------------------------------------------ upper levels, persistent
+// The levels [lev0, lev1) hold only large clusters; one cooperative launch
+// per pass runs them all, the CTAs striding over each level's work items,
+// with a grid barrier between the phases (forward: one phase per level;
+// backward: preparation, then the column products, per level).  The barrier
+// is a generation counter with bounded waits: a wait that runs out sets *err
+// and the kernel carries on (the solve then reports the error).
+struct UpperSched {
+    int lev0, lev1;
+    const int32_t* uf;     // per-level task ranges (device), as uf_ptr / ub_ptr / ulr_ptr / vg_ptr
+    const int32_t* ub;
+    const int32_t* ulr;
+    const int32_t* vg;
+    unsigned int* bar;     // [0] arrivals, [1] generation
+    unsigned int* err;
+};
+
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, unsigned int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            int i = 0;
+            while (*gen == g) {
+                if (++i > (1 << 24)) {   // about a second: give up, record the error
+                    atomicOr(err, 2u);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_upper_fwd(HView v, const T* __restrict__ data, UpperSched sc,
+                                                  const double* xp, double* ybuf, double* inb,
+                                                  double* tbuf, double* pbuf, unsigned int* tickets) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ A red[HT][VecOf<T>::N];
+    __shared__ bool last;
+    for (int lev = sc.lev0; lev < sc.lev1; ++lev) {
+        for (int k = sc.uf[lev] + blockIdx.x; k < sc.uf[lev + 1]; k += gridDim.x) {
+            const HTask t = v.uft[k];
+            up_fwd_task<T, A>(v, data, t, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
+            __syncthreads();
+        }
+        if (lev + 1 < sc.lev1) grid_barrier(sc.bar, sc.err);
+    }
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(HT) k_upper_bwd(HView v, const T* __restrict__ data, UpperSched sc,
+                                                  const double* __restrict__ ybuf, double* out,
+                                                  double* tbuf, double* vbuf) {
+    __shared__ A vv[LR_ROWS];
+    __shared__ A red[HT];
+    __shared__ A redw[NW];
+    for (int lev = sc.lev1 - 1; lev >= sc.lev0; --lev) {
+        const int ng = sc.ulr[lev + 1] - sc.ulr[lev];
+        const int nv = sc.vg[lev + 1] - sc.vg[lev];
+        for (int i = blockIdx.x; i < ng + nv; i += gridDim.x) {
+            prep_task<T, A>(v, data, i, sc.ulr[lev], ng, sc.vg[lev], ybuf, out, tbuf, vbuf, vv, red);
+            __syncthreads();
+        }
+        grid_barrier(sc.bar, sc.err);
+        for (int k = sc.ub[lev] + blockIdx.x; k < sc.ub[lev + 1]; k += gridDim.x) {
+            const HTask t = v.ubt[k];
+            up_bwd_task<T, A>(v, data, t, vbuf, tbuf, out, redw);
+            __syncthreads();
+        }
+        if (lev > sc.lev0) grid_barrier(sc.bar, sc.err);
     }
 }
 
@@ -657,6 +792,86 @@ HView view_of(const HFactorDev& F) {
     return v;
 }
 
+// Launch with programmatic stream serialization (the kernel may start while
+// its predecessor in the stream drains; it synchronises with pdl_wait).
+// BID_PDL=0 in the environment launches the kernels in plain stream order.
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("BID_PDL");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                     cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Cooperative launch of a persistent kernel (all CTAs resident, or the
+// launch fails).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                        cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+__global__ void k_coop_probe(int* flag) {
+    if (flag && threadIdx.x == 0 && blockIdx.x == 0) *flag = 1;
+}
+
+// The persistent upper-level kernels are used only with BID_UPPER=1 in the
+// environment, and then only when a cooperative launch can be captured into
+// a graph and replayed on this device (checked once with an empty kernel).
+// On the 2049^2 slice they measured slower than the per-level launches with
+// programmatic dependent launch (their grid barriers cost more than the
+// overlapped launch gaps they replace), so the per-level launches are the
+// default.
+int g_upper_ok = -1;
+int probe_upper() {
+    const char* e = std::getenv("BID_UPPER");
+    if (!(e && std::strcmp(e, "1") == 0)) return 0;
+    cudaStream_t st = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        const cudaError_t le = launch_coop(k_coop_probe, 2, 32, 0, st, (int*)nullptr);
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        ok = le == cudaSuccess && ce == cudaSuccess && g != nullptr;
+    }
+    ok = ok && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    ok = ok && cudaGraphLaunch(ge, st) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (st) cudaStreamDestroy(st);
+    cudaGetLastError();
+    return ok ? 1 : 0;
+}
+
 template <typename T, typename A>
 int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh,
         const HScratch& S, double* out) {
@@ -667,14 +882,40 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
     {
         int64_t g = (F.n + HT - 1) / HT;
         if (g > (int64_t)L.sms * 8) g = (int64_t)L.sms * 8;
-        k_permute<<<(unsigned)g, HT, 0, L.st>>>((int)F.n, F.pidx, F.pin, F.pinflag, in, sh, S.xp);
+        BID_CUDA_TRY(launch_k(k_permute, (unsigned)g, HT, 0, L.st, (int)F.n, F.pidx, F.pin, F.pinflag, in,
+                              sh, S.xp));
     }
     const int H = (int)F.uf_ptr.size() - 1;
-    for (int lev = 0; lev < H; ++lev) {
+    // upper levels in one persistent launch per pass when possible
+    const int lu = (g_upper_ok == 1 && F.sched && S.gbar && F.lev_upper < H) ? F.lev_upper : H;
+    UpperSched us{};
+    unsigned grid_f = 1, grid_b = 1;
+    if (lu < H) {
+        us.lev0 = lu;
+        us.lev1 = H;
+        us.uf = F.sched;
+        us.ub = F.sched + (H + 1);
+        us.ulr = F.sched + 2 * (H + 1);
+        us.vg = F.sched + 3 * (H + 1);
+        us.bar = S.gbar;
+        us.err = S.err;
+        int nb = 0, most_f = 1, most_b = 1;
+        for (int lev = lu; lev < H; ++lev) {
+            most_f = std::max(most_f, F.uf_ptr[lev + 1] - F.uf_ptr[lev]);
+            most_b = std::max(most_b, std::max(F.ub_ptr[lev + 1] - F.ub_ptr[lev],
+                                               F.ulr_ptr[lev + 1] - F.ulr_ptr[lev] + F.vg_ptr[lev + 1] -
+                                                   F.vg_ptr[lev]));
+        }
+        BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_upper_fwd<T, A>, HT, F.upper_smem));
+        grid_f = (unsigned)std::max(1, std::min(nb * L.sms, most_f));
+        BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_upper_bwd<T, A>, HT, 0));
+        grid_b = (unsigned)std::max(1, std::min(nb * L.sms, most_b));
+    }
+    for (int lev = 0; lev < lu; ++lev) {
         const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
-            k_flat_fwd<T, A><<<nf, FT, F.fg_bytes[lev], L.st>>>(v, data, F.fg_ptr[lev], S.xp, S.ybuf,
-                                                                 inb, S.err);
+            BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, F.fg_bytes[lev], L.st, v, data, F.fg_ptr[lev],
+                                  S.xp, S.ybuf, inb, S.err));
             ++launches;
         }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
@@ -682,28 +923,36 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             const int has_lr = F.ulr_ptr[lev + 1] > F.ulr_ptr[lev];
             const size_t sm = sizeof(A) * (has_lr ? (((F.u_ni_max[lev] + 1) & ~1) + LR_KMAX + 2)
                                                   : (size_t)UP_COLS);
-            k_up_fwd<T, A><<<nt, HT, sm, L.st>>>(v, data, F.uf_ptr[lev], S.xp, S.ybuf, inb,
-                                                 S.tbuf, S.pbuf, S.tickets);
+            BID_CUDA_TRY(launch_k(k_up_fwd<T, A>, nt, HT, sm, L.st, v, data, F.uf_ptr[lev], S.xp, S.ybuf,
+                                  inb, S.tbuf, S.pbuf, S.tickets));
             ++launches;
         }
     }
-    for (int lev = H - 1; lev >= 0; --lev) {
+    if (lu < H) {
+        BID_CUDA_TRY(launch_coop(k_upper_fwd<T, A>, grid_f, HT, F.upper_smem, L.st, v, data, us, S.xp, S.ybuf,
+                                 inb, S.tbuf, S.pbuf, S.tickets));
+        BID_CUDA_TRY(launch_coop(k_upper_bwd<T, A>, grid_b, HT, 0, L.st, v, data, us, S.ybuf, out, S.tbuf,
+                                 S.vbuf));
+        launches += 2;
+    }
+    for (int lev = lu - 1; lev >= 0; --lev) {
         const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
         const int nv = F.vg_ptr[lev + 1] - F.vg_ptr[lev];
         if (ng + nv > 0) {
-            k_bwd_prep<T, A><<<ng + nv, HT, 0, L.st>>>(v, data, F.ulr_ptr[lev], ng, F.vg_ptr[lev],
-                                                       S.ybuf, out, S.tbuf, S.vbuf);
+            BID_CUDA_TRY(launch_k(k_bwd_prep<T, A>, ng + nv, HT, 0, L.st, v, data, F.ulr_ptr[lev], ng,
+                                  F.vg_ptr[lev], S.ybuf, out, S.tbuf, S.vbuf));
             ++launches;
         }
         const int nt = F.ub_ptr[lev + 1] - F.ub_ptr[lev];
         if (nt > 0) {
-            k_up_bwd<T, A><<<nt, HT, 0, L.st>>>(v, data, F.ub_ptr[lev], S.vbuf, S.tbuf, out);
+            BID_CUDA_TRY(launch_k(k_up_bwd<T, A>, nt, HT, 0, L.st, v, data, F.ub_ptr[lev], S.vbuf, S.tbuf,
+                                  out));
             ++launches;
         }
         const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
-            k_flat_bwd<T, A><<<nf, FT, F.fg_bytes[lev], L.st>>>(v, data, F.fg_ptr[lev], S.ybuf, out,
-                                                                 S.err);
+            BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT, F.fg_bytes[lev], L.st, v, data, F.fg_ptr[lev],
+                                  S.ybuf, out, S.err));
             ++launches;
         }
     }
@@ -725,6 +974,7 @@ template <typename T, typename A>
 int prepare_one() {
     const int lim = 200 * 1024;
     BID_CUDA_TRY(cudaFuncSetAttribute(k_up_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_upper_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       FLAT_DYN_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -738,6 +988,7 @@ int hsolve_prepare() {
     BID_TRY((prepare_one<double, double>()));
     BID_TRY((prepare_one<float, float>()));
     BID_TRY((prepare_one<__nv_bfloat16, float>()));
+    if (g_upper_ok < 0) g_upper_ok = probe_upper();
     return BID_OK;
 }
 
@@ -819,6 +1070,18 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.ubt, &d->ubt));
     d->fg_ptr = h.fg_ptr;
     d->fg_bytes = h.fg_bytes;
+    d->lev_upper = h.lev_upper;
+    {
+        std::vector<int32_t> sched;
+        for (const auto* v : {&h.uf_ptr, &h.ub_ptr, &h.ulr_ptr, &h.vg_ptr}) sched.insert(sched.end(), v->begin(), v->end());
+        BID_TRY(upload_vec(sched, &d->sched));
+        const int esz_a = precision == BID_FP64 ? 8 : 4;
+        size_t most = (size_t)esz_a * UP_COLS;
+        for (int L = h.lev_upper; L + 1 < (int)h.ulr_ptr.size(); ++L)
+            if (h.ulr_ptr[L + 1] > h.ulr_ptr[L])
+                most = std::max(most, (size_t)esz_a * (((h.u_ni_max[L] + 1) & ~1) + LR_KMAX + 2));
+        d->upper_smem = most;
+    }
     d->ulr_ptr = h.ulr_ptr;
     d->uf_ptr = h.uf_ptr;
     d->ub_ptr = h.ub_ptr;
@@ -856,8 +1119,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 void free_hfactor(HFactorDev* d) {
-    void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout, d->vgl, d->sn,
-                    d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb};
+    void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout,  d->vgl, d->sn,
+                    d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

@@ -183,6 +183,7 @@ struct HFactorHost {
     int64_t ubuf = 0, tbuf = 0, pbuf = 0, nslots = 0, vbuf = 0;
     int32_t ntickets = 0;
     int32_t vec = 2;
+    int32_t lev_upper = 0;     // levels >= lev_upper hold only large clusters
     int64_t dense_entries = 0, lowrank_entries = 0;   // algorithmic (no padding)
     int64_t nsmall = 0, nlarge = 0, nlr = 0;
 };
@@ -247,6 +248,9 @@ struct HFactorDev {
     int64_t data_elems = 0;
     double* inb = nullptr;              // update slots (nslots, zero where no child writes)
     std::vector<int32_t> fg_ptr, fg_bytes, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max, u_nd_max;
+    int32_t* sched = nullptr;           // device copy of uf_ptr | ub_ptr | ulr_ptr | vg_ptr (H + 1 each)
+    int32_t lev_upper = 0;              // first upper level (only large clusters from there up)
+    size_t upper_smem = 0;              // dynamic shared memory of the upper forward kernel
     int64_t ubuf_entries = 0, tbuf_entries = 0, pbuf_entries = 0, nslots = 0, vbuf_entries = 0;
     int32_t ntickets = 0;
     int64_t bytes_pass = 0;             // stored factor bytes read by fwd + bwd
@@ -266,6 +270,8 @@ struct HScratch {
     double* vbuf = nullptr;    // staged backward inputs of the large clusters of a level
     unsigned int* tickets = nullptr;    // zero between solves
     unsigned int* err = nullptr;        // set (nonzero) when a bounded device wait expired
+    unsigned int* gbar = nullptr;       // grid barrier of the persistent upper-level kernels
+                                        // (2 words, zero initially)
 };
 
 // ---------------------------------------------------------------- device scalars

@@ -4,10 +4,10 @@ and convergence) against the FP64 oracle slice by slice, and against the same
 slices run one at a time through the single-system path.
 
 Tolerances as in test_gpu_parity: solves to relative residual 1e-13 agree with
-the oracle's direct solve within 1e-9 relative per slice; the P_K application
-of a slice inside the batch equals its application alone (same tree, same
-tiles, same summation order) to 1e-14 relative, the P_1 application to 1e-12
-(its input shift, the slice mean, is summed in another order).
+the oracle's direct solve within 1e-9 relative per slice; the factor
+applications of a slice inside the batch equal its applications alone (same
+tree and blocks, possibly another summation order) to 1e-12 relative with FP64
+factors and 1e-6 with FP32 factors.
 """
 import numpy as np
 import pytest
@@ -91,9 +91,11 @@ def test_batch_factor_equals_single(bid, small):
                 xs = torch.zeros(seg.stop - seg.start, dtype=torch.float64, device=DEV)
                 P.apply_factor(which, T(b[seg]), xs)
                 ref = H(xs)
-                # P_K: same tree, tiles and summation order; P_1 also subtracts
-                # the slice mean of b, summed in another order
-                tol = 1e-14 if which == 2 else 1e-12
+                # same tree and blocks; the summation order can differ (the level
+                # from which clusters take the large-cluster kernels is set by
+                # the whole forest; P_1 also subtracts the slice mean, summed in
+                # another order): FP64 to rounding, FP32 storage to FP32 rounding
+                tol = 1e-12 if prec == "fp64" else 1e-6
                 assert np.abs(xb[seg] - ref).max() <= tol * np.abs(ref).max(), (prec, which, k)
 
 
