@@ -45,6 +45,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "bidomain steps/s at PCG rel-res 1e-8 (chosen form); HBM GB/s of the factor solve"
 
+# DRAM bytes per algorithmic byte of one P_1 solve, from the ncu capture of the
+# same kernels at 1025^2 (profiles/p1_solve_dram_1025.md: 568.0 MB over
+# 390.6 MB); the traffic grows with the factor, so the bench's roofline
+# reports this ratio times its own algorithmic bytes for the same form.
+TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 16): 568.0 / 390.6}
+
 
 def parse():
     a = argparse.ArgumentParser()
@@ -55,6 +61,7 @@ def parse():
     a.add_argument("--n", type=int, default=2049)
     a.add_argument("--eps", type=float, default=1e-3)
     a.add_argument("--precision", default="fp32")
+    a.add_argument("--leaf", type=int, default=16)
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
@@ -578,7 +585,7 @@ def main():
         return dict(ms=ms, iters=iters[it0:], launches=launches, clocks=ck.summary(), U=U, V=V, h=h)
 
     # ---- chosen form
-    P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision)
+    P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf)
     chosen_stats = dict(P.stats)
     chosen = time_form(P, "chosen")
 
@@ -644,7 +651,7 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": workload_name(args, N, NH),
-            "form": {"eps": args.eps, "factor_precision": args.precision},
+            "form": {"eps": args.eps, "factor_precision": args.precision, "leaf": args.leaf},
             "mean_pcg_iters": float(np.mean(chosen["iters"])),
             "l2": "inputs larger than L2 (factor + matrices several GB)",
             "parallelism": f"replicas{world}" if world > 1 else "single GPU",
@@ -658,7 +665,12 @@ def main():
             },
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": (TRAFFIC_PER_ALG_BYTE[(args.eps, args.precision, args.leaf)] * alg_bytes
+                                 if args.workload == "slice" and
+                                 (args.eps, args.precision, args.leaf) in TRAFFIC_PER_ALG_BYTE else None),
+                     "traffic_note": "ncu DRAM bytes of the same kernels at 1025^2 scaled by the "
+                                     "algorithmic bytes (profiles/p1_solve_dram_1025.md)",
                      "kernel": "P_1 solve: k_permute, k_flat_fwd, k_up_fwd, k_bwd_prep, "
                                "k_up_bwd, k_flat_bwd over all tree levels",
                      "ms": solve_ms, "algorithmic_bytes": alg_bytes,
