@@ -455,6 +455,7 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     bo.block = o->block;
     bo.threads = o->n_threads;
     bo.vec = o->precision == BID_FP64 ? 2 : o->precision == BID_FP32 ? 4 : 8;
+    bo.upper_levels = hsolve_upper_enabled();
     HFactorHost h1, hk;
     if (rc == BID_OK) rc = build_batch_factor(hosts, L, 1, B->gamma, bo, lf, &h1);
     if (rc == BID_OK) rc = build_batch_factor(hosts, L, 2, B->gamma, bo, lf, &hk);

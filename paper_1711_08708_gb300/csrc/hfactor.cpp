@@ -510,16 +510,18 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         }
     if (fail) return set_error(BID_EINVAL, "factorisation: non-positive pivot (matrix not SPD)");
 
-    // every cluster from the lowest tree level holding a large cluster upwards
-    // takes the large-cluster path, so that those levels form one contiguous
-    // range (the upper levels, solved by one persistent launch per pass)
+    // with o.upper_levels, every cluster from the lowest tree level holding a
+    // large cluster upwards takes the large-cluster path, so that those levels
+    // form one contiguous range (the upper levels, solved by one persistent
+    // launch per pass)
     {
         int lev_upper = maxh + 1;
         for (int s = 0; s < nt; ++s)
             if (F->sn[s].large) lev_upper = std::min(lev_upper, (int)F->sn[s].height);
-        for (int s = 0; s < nt; ++s)
-            if (F->sn[s].height >= lev_upper) F->sn[s].large = 1;
-        F->lev_upper = lev_upper;
+        if (o.upper_levels)
+            for (int s = 0; s < nt; ++s)
+                if (F->sn[s].height >= lev_upper) F->sn[s].large = 1;
+        F->lev_upper = o.upper_levels ? lev_upper : maxh + 1;
     }
 
     // ---------------- pack

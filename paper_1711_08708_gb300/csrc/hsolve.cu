@@ -984,6 +984,8 @@ int prepare_one() {
 
 }  // namespace
 
+bool hsolve_upper_enabled() { return g_upper_ok == 1; }
+
 int hsolve_prepare() {
     BID_TRY((prepare_one<double, double>()));
     BID_TRY((prepare_one<float, float>()));

@@ -203,6 +203,10 @@ struct HBuildOpts {
     // (vmap[i] < vn); empty: the identity.
     std::vector<int32_t> vmap;
     int64_t vn = 0;
+    // route every cluster from the lowest level holding a large cluster
+    // upwards to the large-cluster kernels (needed by the persistent
+    // upper-level path)
+    bool upper_levels = false;
 };
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  Every index in `pins` has its
@@ -345,6 +349,7 @@ int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in,
                       const int16_t* seg, const double* seg_sum, const double* seg_inv_n,
                       const HScratch& S, double* out);
 int hsolve_prepare();   // raise the dynamic shared-memory limit of the kernels
+bool hsolve_upper_enabled();   // persistent upper-level kernels in use (after hsolve_prepare)
 
 // ---------------------------------------------------------------- batched form
 // Slice s of a batch owns the combined-vector segment [off[s], off[s+1]) laid
