@@ -174,6 +174,8 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     if (o.block < 8 || o.block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o.leaf < 4 || o.leaf > 4096) return set_error(BID_EINVAL, "leaf must be in 4..4096");
     if (o.vec != 2 && o.vec != 4 && o.vec != 8) return set_error(BID_EINVAL, "vec must be 2, 4 or 8");
+    if (o.group_bytes < 1024 || o.group_bytes > 65536)
+        return set_error(BID_EINVAL, "group_bytes must be in 1024..65536");
     const int nthreads = o.threads > 0 ? o.threads : omp_get_max_threads();
     std::vector<int64_t> gptr = o.group_ptr;
     if (gptr.empty()) gptr = {0, n};
@@ -638,7 +640,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     // pass and GROUP_BYTES of data (a larger cluster forms a group alone)
     const int esz = vec == 2 ? 8 : vec == 4 ? 4 : 2;
     auto make_groups = [&](const std::vector<int>& cl) {
-        int32_t most = 0;
+        int32_t most = 0, most_nc = 0, most_wf = 0, most_wb = 0;
         FGroup g{};
         bool open = false, kids = false;
         int64_t end = 0, send = 0;
@@ -648,6 +650,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             g.sbytes = kids ? (int32_t)((send - g.sstart) * 8) : 0;
             most = std::max(most, g.nbytes + g.sbytes);
             g.c1 = (int32_t)F->gcl.size();
+            most_nc = std::max(most_nc, g.c1 - g.c0);
+            most_wf = std::max(most_wf, g.wf);
+            most_wb = std::max(most_wb, g.wb);
             F->fg.push_back(g);
             open = false;
         };
@@ -657,7 +662,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             const int units_f = (h.nd + vec - 1) / vec;
             if (open && (g.c1 - g.c0 == STAGE_CL || (int)F->gcl.size() - g.c0 == STAGE_CL ||
                          g.wf + h.ni > STAGE_MAX || g.wb + h.nd + vec > STAGE_MAX ||
-                         (blk_end[s] - g.dstart) * esz > GROUP_BYTES))
+                         (blk_end[s] - g.dstart) * esz > o.group_bytes))
                 flush();
             if (!open) {
                 g = FGroup{};
@@ -695,6 +700,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         }
         flush();
         F->fg_bytes.push_back(most);
+        F->fg_nc.push_back(most_nc);
+        F->fg_wf.push_back(most_wf);
+        F->fg_wb.push_back(most_wb);
     };
     for (int L = 0; L < H; ++L) {
         std::vector<int> small;

@@ -187,7 +187,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
 constexpr int BULK_CHUNK = 16384;   // bytes per bulk-copy instruction
 // dynamic shared memory of a flat launch (the largest group of its level);
 // static shared memory of the flat kernels is at most 44 KB (FP64 staging)
-constexpr int FLAT_DYN_MAX = 176 * 1024;
+constexpr int FLAT_DYN_MAX = 176 * 1024;   // group block (data + slots) of one flat group
+constexpr int FLAT_SMEM_MAX = 224 * 1024;  // with descriptors and staged inputs
 
 __device__ __forceinline__ void bulk_region(unsigned char* dst, const void* src, int nbytes,
                                             uint64_t* bar) {
@@ -299,14 +300,16 @@ __device__ __forceinline__ double incoming_s(const double* ss, const GCl& c, int
     return val.x + val.y;
 }
 
+// Dynamic shared memory of a flat launch: [group block (bytes)] [descriptors
+// (GCl, at sc_off)] [staged inputs (A, at w_off)], sized per level.
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* xp, double* ybuf, double* inb,
-                                                 unsigned int* err) {
+                                                 unsigned int* err, int sc_off, int w_off) {
     constexpr int VEC = VecOf<T>::N;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ A w[STAGE_MAX];
-    __shared__ GCl scl[STAGE_CL];
+    GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
+    A* w = reinterpret_cast<A*>(dyn_smem + w_off);
     __shared__ __align__(8) uint64_t bar;
     const FGroup G = v.fg[g0 + blockIdx.x];
     const int nc = G.c1 - G.c0;
@@ -381,11 +384,11 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* __restrict__ ybuf, double* out,
-                                                 unsigned int* err) {
+                                                 unsigned int* err, int sc_off, int w_off) {
     constexpr int VEC = VecOf<T>::N;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    __shared__ A vs[STAGE_MAX];
-    __shared__ GCl scl[STAGE_CL];
+    GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
+    A* vs = reinterpret_cast<A*>(dyn_smem + w_off);
     __shared__ __align__(8) uint64_t bar;
     const FGroup G = v.fg[g0 + blockIdx.x];
     const int nc = G.c1 - G.c0;
@@ -914,8 +917,11 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
     for (int lev = 0; lev < lu; ++lev) {
         const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
-            BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, F.fg_bytes[lev], L.st, v, data, F.fg_ptr[lev],
-                                  S.xp, S.ybuf, inb, S.err));
+            const int sc_off = (F.fg_bytes[lev] + 15) / 16 * 16;
+            const int w_off = sc_off + F.fg_nc[lev] * (int)sizeof(GCl);
+            const size_t sm = (size_t)w_off + sizeof(A) * F.fg_wf[lev];
+            BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.xp, S.ybuf, inb,
+                                  S.err, sc_off, w_off));
             ++launches;
         }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
@@ -951,8 +957,11 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         }
         const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
-            BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT, F.fg_bytes[lev], L.st, v, data, F.fg_ptr[lev],
-                                  S.ybuf, out, S.err));
+            const int sc_off = (F.fg_bytes[lev] + 15) / 16 * 16;
+            const int w_off = sc_off + F.fg_nc[lev] * (int)sizeof(GCl);
+            const size_t sm = (size_t)w_off + sizeof(A) * F.fg_wb[lev];
+            BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.ybuf, out, S.err,
+                                  sc_off, w_off));
             ++launches;
         }
     }
@@ -976,9 +985,9 @@ int prepare_one() {
     BID_CUDA_TRY(cudaFuncSetAttribute(k_up_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_upper_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      FLAT_DYN_MAX));
+                                      FLAT_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      FLAT_DYN_MAX));
+                                      FLAT_SMEM_MAX));
     return BID_OK;
 }
 
@@ -1072,6 +1081,17 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.ubt, &d->ubt));
     d->fg_ptr = h.fg_ptr;
     d->fg_bytes = h.fg_bytes;
+    d->fg_nc = h.fg_nc;
+    d->fg_wf = h.fg_wf;
+    d->fg_wb = h.fg_wb;
+    {
+        const size_t esz_a = precision == BID_FP64 ? 8 : 4;
+        for (size_t L = 0; L < h.fg_bytes.size(); ++L) {
+            const size_t base = (size_t)(h.fg_bytes[L] + 15) / 16 * 16 + (size_t)h.fg_nc[L] * sizeof(GCl);
+            if (base + esz_a * std::max(h.fg_wf[L], h.fg_wb[L]) > (size_t)FLAT_SMEM_MAX)
+                return set_error(BID_EINVAL, "flat level %zu needs too much shared memory", L);
+        }
+    }
     d->lev_upper = h.lev_upper;
     {
         std::vector<int32_t> sched;

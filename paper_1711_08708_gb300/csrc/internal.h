@@ -128,9 +128,10 @@ struct HLr {
 // stay zero (each factor owns its zero-initialised slot array), so the flat
 // kernels add both slots of a frontal row without validity checks.
 // A group holds at most STAGE_CL clusters, STAGE_MAX staged values in either
-// pass and, unless it is a single cluster, GROUP_BYTES bytes of data: small
-// CTAs (FLAT_THREADS threads, ~25 KB of shared memory) so that many groups
-// are resident per SM and their load phases overlap.
+// pass and, unless it is a single cluster, HBuildOpts::group_bytes bytes of
+// data: small CTAs (FLAT_THREADS threads, the group's data, slots,
+// descriptors and staged inputs in dynamic shared memory sized per level) so
+// that many groups are resident per SM and their load phases overlap.
 struct FGroup {
     int64_t dstart;                 // element offset of the group's data
     int64_t sstart;                 // first update slot of the group's clusters
@@ -173,7 +174,8 @@ struct HFactorHost {
     std::vector<FGroup> fg;
     std::vector<GCl> gcl;
     std::vector<int32_t> fg_ptr;               // level -> group range
-    std::vector<int32_t> fg_bytes;             // level -> largest group data (bytes)
+    std::vector<int32_t> fg_bytes;             // level -> largest group data + slots (bytes)
+    std::vector<int32_t> fg_nc, fg_wf, fg_wb;  // level -> most clusters / staged values of a group
     // large clusters, per level
     std::vector<int32_t> ulr_ptr;              // level -> low-rank groups [ptr, ptr+1)
     std::vector<int32_t> vg_ptr, vgl;          // level -> large clusters (backward staging)
@@ -188,6 +190,7 @@ struct HFactorHost {
     int64_t nsmall = 0, nlarge = 0, nlr = 0;
 };
 
+constexpr int GROUP_BYTES_DEFAULT = 12288;
 struct HBuildOpts {
     double eps = 0.0;
     int leaf = 16;
@@ -207,6 +210,7 @@ struct HBuildOpts {
     // upwards to the large-cluster kernels (needed by the persistent
     // upper-level path)
     bool upper_levels = false;
+    int group_bytes = GROUP_BYTES_DEFAULT;   // factor bytes of a flat group (see FGroup)
 };
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  Every index in `pins` has its
@@ -220,7 +224,6 @@ constexpr int SMALL_NI = 64;     // a cluster is small when ni <= SMALL_NI and
 constexpr int SMALL_NF = 320;    // ni + nb <= SMALL_NF (before compression)
 constexpr int STAGE_MAX = 2048;  // staged input values of a flat CTA
 constexpr int STAGE_CL = 64;     // clusters of a flat group
-constexpr int GROUP_BYTES = 12288;   // factor bytes of a flat group (one cluster may exceed)
 constexpr int FLAT_THREADS = 128;    // threads of a flat CTA
 constexpr int UP_GROUPS = 64;    // row groups (of vec rows) of an upper forward task
 constexpr int UP_SPLIT = 4;      // column splits of an upper forward task (16 columns each)
@@ -251,7 +254,8 @@ struct HFactorDev {
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
     double* inb = nullptr;              // update slots (nslots, zero where no child writes)
-    std::vector<int32_t> fg_ptr, fg_bytes, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max, u_nd_max;
+    std::vector<int32_t> fg_ptr, fg_bytes, fg_nc, fg_wf, fg_wb, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max,
+        u_nd_max;
     int32_t* sched = nullptr;           // device copy of uf_ptr | ub_ptr | ulr_ptr | vg_ptr (H + 1 each)
     int32_t lev_upper = 0;              // first upper level (only large clusters from there up)
     size_t upper_smem = 0;              // dynamic shared memory of the upper forward kernel
