@@ -110,6 +110,11 @@ typedef struct bid_precond_stats {
                                           dense entries and low-rank factors) */
     int64_t lowrank_blocks, dense_blocks;
     double build_seconds;
+    int32_t dataflow_levels1, dataflow_levelsk;  /* levels solved by the two dataflow
+                                          launches per pass (0: one launch per level, the
+                                          default; BID_TREE=1 in the environment turns
+                                          them on) */
+    int32_t dataflow_first1, dataflow_firstk;    /* the first of those levels */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {
@@ -397,16 +402,30 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps,
                           int leaf, int block, int precision, const double* b, double* x,
                           bid_precond_stats* stats);
+/* As bid_host_factor_solve, with the flat groups of a range of levels run in
+ * the order of the dataflow solve kernels (the levels from `from` on whose
+ * largest group needs at most smem_cap bytes of shared memory and that hold
+ * no large cluster; smem_cap 0: level by level): forward, always the
+ * highest-numbered group whose dependencies are complete, backward the
+ * lowest-numbered, so that a missing dependency changes x.  With a complete
+ * schedule x is bit-identical to bid_host_factor_solve's.  sched (5 entries,
+ * may be NULL) receives the schedule's first and end level, groups, forward
+ * and backward dependencies. */
+int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double gamma, double eps,
+                                   int leaf, int block, int precision, int smem_cap, int from,
+                                   const double* b, double* x, bid_precond_stats* stats, int64_t* sched);
 /* The batched factors on the host: the forest over nslices host systems
  * (combined layout as for bid_batch_create, leaf per slice or NULL for
  * `leaf_default`), replayed in FP64: which = 1 writes x_U,s = P_1,s^-1
  * (b_U,s - mean(b_U,s)), which = 2 writes x_V,s = P_K,s^-1 b_V,s (gamma as
  * given); other entries of x are left as they are.  b, x host arrays of the
- * combined length.  stats may be NULL. */
+ * combined length.  smem_cap, from and sched as for
+ * bid_host_factor_solve_dataflow (smem_cap 0: level by level; sched may be
+ * NULL).  stats may be NULL. */
 int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, int which,
                                 double gamma, double eps, const int32_t* leaf, int leaf_default,
-                                int block, int precision, const double* b, double* x,
-                                bid_precond_stats* stats);
+                                int block, int precision, int smem_cap, int from, const double* b,
+                                double* x, bid_precond_stats* stats, int64_t* sched);
 void bid_host_destroy(bid_host_system* h);
 
 #ifdef __cplusplus

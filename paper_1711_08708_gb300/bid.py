@@ -52,7 +52,9 @@ class PrecondStats(C.Structure):
                 ("factor_bytes", C.c_int64), ("bytes_p1", C.c_int64), ("bytes_pk", C.c_int64),
                 ("alg_bytes_p1", C.c_int64), ("alg_bytes_pk", C.c_int64),
                 ("lowrank_blocks", C.c_int64), ("dense_blocks", C.c_int64),
-                ("build_seconds", C.c_double)]
+                ("build_seconds", C.c_double), ("dataflow_levels1", C.c_int32),
+                ("dataflow_levelsk", C.c_int32), ("dataflow_first1", C.c_int32),
+                ("dataflow_firstk", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -91,6 +93,8 @@ SIGNATURES = {
     "bid_host_csr_size": (_I, [_VP, _I, _I64P, _I64P]),
     "bid_host_csr": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "bid_host_factor_solve": (_I, [_VP, _I, _D, _D, _I, _I, _I, _VP, _VP, C.POINTER(PrecondStats)]),
+    "bid_host_factor_solve_dataflow": (_I, [_VP, _I, _D, _D, _I, _I, _I, _I, _I, _VP, _VP,
+                                            C.POINTER(PrecondStats), _I64P]),
     "bid_host_destroy": (None, [_VP]),
     "bid_batch_create": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, C.POINTER(_VP)]),
     "bid_batch_layout": (_I, [_VP, _VP, _VP]),
@@ -102,8 +106,8 @@ SIGNATURES = {
     "bid_batch_destroy": (None, [_VP]),
     "bid_tune_leaf": (_I, [_VP, C.POINTER(PrecondOpts), _VP, _I, _I, _VP, _VP]),
     "bid_tune_batch_leaf": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, _I, _I, _VP]),
-    "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _VP, _VP,
-                                         C.POINTER(PrecondStats)]),
+    "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _I, _I, _VP, _VP,
+                                         C.POINTER(PrecondStats), _I64P]),
     "bid_cnn_nparams": (_I, []),
     "bid_cnn_create": (_I, [_I, C.c_uint64, C.POINTER(_VP)]),
     "bid_cnn_set_params": (_I, [_VP, _VP]),
@@ -500,24 +504,50 @@ class HostSystem:
                                          int(block), prec, _ptr(b), _ptr(x), C.byref(st)))
         return x, st.as_dict()
 
+    def factor_solve_dataflow(self, which, b, smem_cap=32768, first=1, gamma=0.0, eps=0.0, leaf=16,
+                              block=128, precision="fp64"):
+        """factor_solve with the flat levels from `first` on replayed in the
+        dataflow kernels' signal order; returns x, stats and the schedule."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        st = PrecondStats()
+        sched = np.zeros(5, dtype=np.int64)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib.bid_host_factor_solve_dataflow(self.h, int(which), float(gamma), float(eps), int(leaf),
+                                                  int(block), prec, int(smem_cap), int(first), _ptr(b),
+                                                  _ptr(x), C.byref(st), sched.ctypes.data_as(_I64P)))
+        return x, st.as_dict(), _schedule(sched)
+
     def __del__(self):
         if getattr(self, "h", None):
             lib.bid_host_destroy(self.h)
             self.h = None
 
 
+def _schedule(sched):
+    lev0, lev1, groups, df, db = (int(v) for v in sched)
+    return {"first": lev0, "levels": lev1 - lev0, "groups": groups, "deps_fwd": df, "deps_bwd": db}
+
+
 def host_batch_factor_solve(systems, which, b, gamma=0.0, eps=0.0, leaf=16, block=128,
-                            precision="fp64"):
+                            precision="fp64", smem_cap=0, first=1, schedule=False):
     """bid_host_batch_factor_solve over HostSystems (combined layout); the
-    entries of the result outside the factor's block are zero."""
+    entries of the result outside the factor's block are zero.  smem_cap > 0
+    replays the flat levels from `first` on in the dataflow kernels' order; with
+    schedule=True the schedule (levels, groups, forward and backward
+    dependencies) is returned as a third value."""
     S = len(systems)
     arr = (_VP * S)(*[s.h.value for s in systems])
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros_like(b)
     lf = None if np.isscalar(leaf) else np.ascontiguousarray(leaf, dtype=np.int32)
     st = PrecondStats()
+    sched = np.zeros(5, dtype=np.int64)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _check(lib.bid_host_batch_factor_solve(arr, S, int(which), float(gamma), float(eps), _ptr(lf),
                                            int(leaf) if lf is None else 16, int(block), prec,
-                                           _ptr(b), _ptr(x), C.byref(st)))
+                                           int(smem_cap), int(first), _ptr(b), _ptr(x), C.byref(st),
+                                           sched.ctypes.data_as(_I64P)))
+    if schedule:
+        return x, st.as_dict(), _schedule(sched)
     return x, st.as_dict()

@@ -515,6 +515,10 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     st.supernodesk = (int64_t)hk.sn.size();
     st.levels1 = h1.height;
     st.levelsk = hk.height;
+    st.dataflow_levels1 = B->F1.tree_lev1 - B->F1.tree_lev0;
+    st.dataflow_levelsk = B->FK.tree_lev1 - B->FK.tree_lev0;
+    st.dataflow_first1 = B->F1.tree_lev0;
+    st.dataflow_firstk = B->FK.tree_lev0;
     st.dense_entries = h1.dense_entries + hk.dense_entries;
     st.lowrank_entries = h1.lowrank_entries + hk.lowrank_entries;
     st.dense_blocks = h1.nlarge + hk.nlarge;

@@ -455,6 +455,10 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.supernodesk = (int64_t)hk.sn.size();
     st.levels1 = h1.height;
     st.levelsk = hk.height;
+    st.dataflow_levels1 = P->F1.tree_lev1 - P->F1.tree_lev0;
+    st.dataflow_levelsk = P->FK.tree_lev1 - P->FK.tree_lev0;
+    st.dataflow_first1 = P->F1.tree_lev0;
+    st.dataflow_firstk = P->FK.tree_lev0;
     st.dense_entries = h1.dense_entries + hk.dense_entries;
     st.lowrank_entries = h1.lowrank_entries + hk.lowrank_entries;
     st.dense_blocks = h1.nlarge + hk.nlarge;

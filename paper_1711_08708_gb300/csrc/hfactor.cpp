@@ -2,7 +2,7 @@
 // K_m; Sec. 5.3 of the paper: build a hierarchical approximation with accuracy
 // eps, then factorise it, with almost-linear storage and solve cost).
 //
-// Design (GB300-first, see the design doc for the comparison with H-Lib):
+// Design (GB300-first, in place of the paper's H-matrix library):
 //  * cluster tree: geometric nested dissection -- each cluster is split at the
 //    median of its longest axis and the vertex separator (nodes of the lower
 //    half adjacent to the upper half) becomes the parent; leaves hold at most
@@ -809,6 +809,91 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             F->pinflag.swap(pf);
         }
     }
+    return BID_OK;
+}
+
+int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from, TreeHost* T) {
+    *T = TreeHost();
+    const int H = (int)F.uf_ptr.size() - 1;
+    if (H < 1 || (int)F.fg_ptr.size() < H + 1 || from < 0 || from >= H) return BID_OK;
+    auto round16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+    int64_t blk = 0, desc = 0, wmax = 0;
+    int L = from;
+    for (; L < H; ++L) {
+        if (F.uf_ptr[L + 1] != F.uf_ptr[L] || F.ub_ptr[L + 1] != F.ub_ptr[L] ||
+            F.ulr_ptr[L + 1] != F.ulr_ptr[L] || F.vg_ptr[L + 1] != F.vg_ptr[L])
+            break;
+        const int64_t b2 = std::max(blk, round16(F.fg_bytes[L]));
+        const int64_t d2 = std::max(desc, (int64_t)F.fg_nc[L] * (int64_t)sizeof(GCl));
+        const int64_t w2 = std::max(wmax, (int64_t)std::max(F.fg_wf[L], F.fg_wb[L]));
+        if (b2 + d2 + acc_bytes * w2 > smem_cap) break;
+        blk = b2;
+        desc = d2;
+        wmax = w2;
+    }
+    if (L - from < 2) return BID_OK;
+    const int first = F.fg_ptr[from], ntask = F.fg_ptr[L] - first;
+    if (ntask < 1) return BID_OK;
+    // pidx / bidx hold vector indices, which exceed n in a forest's combined
+    // vectors: invert pidx over the largest index it holds
+    int32_t vmax = 0;
+    for (int32_t vi : F.pidx) vmax = std::max(vmax, vi + 1);
+    std::vector<int32_t> slot_owner(std::max<int64_t>(F.nslots, 1), -1), pos_owner(F.n, -1), pos_of(vmax, -1);
+    for (int64_t p = 0; p < F.n; ++p)
+        if (F.pidx[p] >= 0) pos_of[F.pidx[p]] = (int32_t)p;
+    // task numbers (group - first) of the slots and positions the range owns
+    for (int g = 0; g < ntask; ++g)
+        for (int c = F.fg[first + g].c0; c < F.fg[first + g].c1; ++c) {
+            const HSnode& s = F.sn[F.gcl[c].s];
+            for (int64_t k = s.inc_off; k < s.inc_off + 2 * (int64_t)s.nd && k < F.nslots; ++k) slot_owner[k] = g;
+            for (int p = s.first; p < s.first + s.ni; ++p) pos_owner[p] = g;
+        }
+    std::vector<std::vector<int32_t>> sf(ntask), sb(ntask);
+    for (int g = 0; g < ntask; ++g)
+        for (int c = F.fg[first + g].c0; c < F.fg[first + g].c1; ++c) {
+            const HSnode& s = F.sn[F.gcl[c].s];
+            for (int R = s.ni; R < s.nd; ++R) {
+                const int64_t k = s.bidx_off + R - s.ni;
+                const int32_t slot = F.uout[k];
+                if (slot >= 0 && slot < F.nslots && slot_owner[slot] >= 0) {
+                    if (slot_owner[slot] <= g) return BID_OK;   // not bottom-up: no schedule
+                    sf[g].push_back(slot_owner[slot]);
+                }
+                const int32_t vi = F.bidx[k];
+                const int32_t h = (vi >= 0 && vi < vmax && pos_of[vi] >= 0) ? pos_owner[pos_of[vi]] : -1;
+                if (h >= 0) {
+                    if (h <= g) return BID_OK;
+                    sb[h].push_back(g);
+                }
+            }
+        }
+    T->need_f.assign(ntask, 0);
+    T->need_b.assign(ntask, 0);
+    T->ptr_f.assign(1, 0);
+    T->ptr_b.assign(1, 0);
+    for (int g = 0; g < ntask; ++g) {
+        for (auto* v : {&sf[g], &sb[g]}) {
+            std::sort(v->begin(), v->end());
+            v->erase(std::unique(v->begin(), v->end()), v->end());
+        }
+        for (int32_t h : sf[g]) {
+            T->need_f[h]++;
+            T->succ_f.push_back(h);
+        }
+        for (int32_t q : sb[g]) {
+            T->need_b[q]++;
+            T->succ_b.push_back(q);
+        }
+        T->ptr_f.push_back((int32_t)T->succ_f.size());
+        T->ptr_b.push_back((int32_t)T->succ_b.size());
+    }
+    T->lev0 = from;
+    T->lev1 = L;
+    T->first = first;
+    T->ntask = ntask;
+    T->sc_off = (int32_t)blk;
+    T->w_off = (int32_t)(blk + desc);
+    T->smem_f = T->smem_b = (int32_t)(blk + desc + acc_bytes * wmax);
     return BID_OK;
 }
 

@@ -2,6 +2,7 @@
 // replay of the level-by-level triangular passes over the packed factor (the
 // same blocks, tiles, update maps and index lists the GPU kernels read), so
 // that the host logic can be verified without a GPU.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -20,8 +21,14 @@ namespace {
 // the same order, as the GPU launches (permuted input, per-level flat items
 // with their splits, large-cluster tasks, parent input slots).
 // Returns false when a group's cluster data lies outside the group's block.
+// With a dataflow schedule T, the flat groups of its levels run in the order
+// of the dataflow kernels' signals instead of level by level, as early as the
+// schedule allows: forward, always the highest-numbered group whose signals
+// have all arrived (parents before the remaining leaves); backward, the
+// lowest-numbered one.  A missing dependency then reads an input before it is
+// written, so the result differs from the level-by-level replay.
 bool replay(const HFactorHost& F, const double* b, double shift, double* x,
-            const std::vector<double>* vshift = nullptr) {
+            const std::vector<double>* vshift = nullptr, const TreeHost* T = nullptr) {
     std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
@@ -52,25 +59,57 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
         return a;
     };
     const int H = (int)F.uf_ptr.size() - 1;
-    for (int lev = 0; lev < H; ++lev) {
-        // flat groups first (their parents sit on later levels): per cluster of
-        // a group, each dense row over all its columns, and the group's data
-        // read inside its bulk-copied block
-        for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g) {
-            const FGroup& G = F.fg[g];
-            const int64_t gend = G.dstart + G.nbytes / esz;
-            for (int c = G.c0; c < G.c1; ++c) {
-                const GCl& d = F.gcl[c];
-                const HSnode& s = F.sn[d.s];
-                if (d.doff != s.data_off - G.dstart || s.data_off + col_start(s.nd, s.ni, F.vec) > gend ||
-                    d.ni != s.ni || d.nd != s.nd || d.nchild != s.nchild ||
-                    d.soff != s.inc_off - G.sstart || d.first != s.first ||
-                    s.first != G.pstart + d.woff_f || s.bidx_off != G.bstart + d.boff ||
-                    (s.nchild && s.inc_off + 2 * s.nd > G.sstart + G.sbytes / 8))
-                    return false;
-                for (int q = 0; q < s.nd; ++q) finish(s, q, fwd_part(s, q, 0, s.ni));
-            }
+    // forward of a flat group: per cluster, each dense row over all its
+    // columns, and the group's data read inside its bulk-copied block
+    auto fwd_group = [&](int g) {
+        const FGroup& G = F.fg[g];
+        const int64_t gend = G.dstart + G.nbytes / esz;
+        for (int c = G.c0; c < G.c1; ++c) {
+            const GCl& d = F.gcl[c];
+            const HSnode& s = F.sn[d.s];
+            if (d.doff != s.data_off - G.dstart || s.data_off + col_start(s.nd, s.ni, F.vec) > gend ||
+                d.ni != s.ni || d.nd != s.nd || d.nchild != s.nchild || d.soff != s.inc_off - G.sstart ||
+                d.first != s.first || s.first != G.pstart + d.woff_f || s.bidx_off != G.bstart + d.boff ||
+                (s.nchild && s.inc_off + 2 * s.nd > G.sstart + G.sbytes / 8))
+                return false;
+            for (int q = 0; q < s.nd; ++q) finish(s, q, fwd_part(s, q, 0, s.ni));
         }
+        return true;
+    };
+    // groups of the dataflow schedule in signal order; pick() chooses among the ready ones
+    auto dataflow = [&](const std::vector<int32_t>& need, const std::vector<int32_t>& ptr,
+                        const std::vector<int32_t>& succ, bool latest, auto&& run) {
+        std::vector<int32_t> got(T->ntask, 0);
+        std::vector<int32_t> ready;   // a heap of task numbers (group - first)
+        auto before = [&](int32_t a, int32_t c) { return latest ? a < c : a > c; };
+        for (int g = 0; g < T->ntask; ++g)
+            if (need[g] == 0) ready.push_back(g);
+        std::make_heap(ready.begin(), ready.end(), before);
+        int done = 0;
+        while (!ready.empty()) {
+            std::pop_heap(ready.begin(), ready.end(), before);
+            const int g = ready.back();
+            ready.pop_back();
+            if (!run(T->first + g)) return false;
+            ++done;
+            for (int e = ptr[g]; e < ptr[g + 1]; ++e)
+                if (++got[succ[e]] == need[succ[e]]) {
+                    ready.push_back(succ[e]);
+                    std::push_heap(ready.begin(), ready.end(), before);
+                }
+        }
+        return done == T->ntask;
+    };
+    const int l0 = T ? T->lev0 : 0, l1 = T ? T->lev1 : 0;
+    for (int lev = 0; lev < H; ++lev) {
+        if (lev == l0 && l1 > l0) {
+            if (!dataflow(T->need_f, T->ptr_f, T->succ_f, true, fwd_group)) return false;
+            lev = l1 - 1;
+            continue;
+        }
+        // flat groups first (their parents sit on later levels)
+        for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g)
+            if (!fwd_group(g)) return false;
         for (int ti = F.uf_ptr[lev]; ti < F.uf_ptr[lev + 1]; ++ti) {
             const HTask& k = F.uft[ti];
             if (k.s < 0) {
@@ -103,7 +142,29 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
     auto vrow = [&](const HSnode& s, int q) {
         return q < s.ni ? y[s.first + q] : -x[F.bidx[s.bidx_off + drow(s, q) - s.ni]];
     };
+    auto bwd_group = [&](int g, std::vector<std::pair<int32_t, double>>& xs) {
+        for (int c = F.fg[g].c0; c < F.fg[g].c1; ++c) {
+            const HSnode& s = F.sn[F.gcl[c].s];
+            for (int j = 0; j < s.ni; ++j) {
+                double a = 0.0;
+                for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
+                xs.push_back({F.pidx[s.first + j], a});
+            }
+        }
+    };
     for (int lev = H - 1; lev >= 0; --lev) {
+        if (lev == l1 - 1 && l1 > l0) {
+            std::vector<std::pair<int32_t, double>> xs;
+            auto run = [&](int g) {
+                xs.clear();
+                bwd_group(g, xs);
+                for (auto& pr : xs) x[pr.first] = pr.second;
+                return true;
+            };
+            if (!dataflow(T->need_b, T->ptr_b, T->succ_b, false, run)) return false;
+            lev = l0;
+            continue;
+        }
         for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
             const HLr& G = F.lr[g];
             const HSnode& s = F.sn[G.s];
@@ -128,15 +189,7 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 xs.push_back({F.pidx[s.first + j], a});
             }
         }
-        for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g)
-            for (int c = F.fg[g].c0; c < F.fg[g].c1; ++c) {
-                const HSnode& s = F.sn[F.gcl[c].s];
-                for (int j = 0; j < s.ni; ++j) {
-                    double a = 0.0;
-                    for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
-                    xs.push_back({F.pidx[s.first + j], a});
-                }
-            }
+        for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g) bwd_group(g, xs);
         for (auto& pr : xs) x[pr.first] = pr.second;
     }
     return true;
@@ -193,6 +246,13 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps, int leaf,
                           int block, int precision, const double* b, double* x,
                           bid_precond_stats* stats) {
+    return bid_host_factor_solve_dataflow(h, which, gamma, eps, leaf, block, precision, 0, 0, b, x, stats,
+                                          nullptr);
+}
+
+int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double gamma, double eps, int leaf,
+                                   int block, int precision, int smem_cap, int from, const double* b,
+                                   double* x, bid_precond_stats* stats, int64_t* sched) {
     if (!h || !b || !x || (which != 1 && which != 2)) return set_error(BID_EINVAL, "bad argument");
     if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
     if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
@@ -215,7 +275,17 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
                 if (K.col[q] == r) K.val[q] += gamma * a.mH[r];
         BID_TRY(build_hfactor(K, a.coords.data(), a.dim, {}, o, &F));
     }
-    if (!replay(F, b, shift, x)) return set_error(BID_EINVAL, "flat group layout inconsistent");
+    TreeHost T;
+    if (smem_cap > 0) BID_TRY(build_tree_sched(F, precision == BID_FP64 ? 8 : 4, smem_cap, from, &T));
+    if (sched) {
+        sched[0] = T.lev0;
+        sched[1] = T.lev1;
+        sched[2] = T.ntask;
+        sched[3] = (int64_t)T.succ_f.size();
+        sched[4] = (int64_t)T.succ_b.size();
+    }
+    if (!replay(F, b, shift, x, nullptr, smem_cap > 0 ? &T : nullptr))
+        return set_error(BID_EINVAL, "flat group layout or dataflow schedule inconsistent");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->n1 = F.n;
@@ -233,8 +303,8 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
 
 int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, int which,
                                 double gamma, double eps, const int32_t* leaf, int leaf_default,
-                                int block, int precision, const double* b, double* x,
-                                bid_precond_stats* stats) {
+                                int block, int precision, int smem_cap, int from, const double* b,
+                                double* x, bid_precond_stats* stats, int64_t* sched) {
     if (!hs || nslices < 1 || !b || !x || (which != 1 && which != 2))
         return set_error(BID_EINVAL, "bad argument");
     if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
@@ -269,7 +339,17 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
             m /= (double)lay.N[s];
             for (int64_t i = 0; i < lay.N[s]; ++i) vshift[lay.off[s] + i] = m;
         }
-    if (!replay(F, b, 0.0, x, &vshift)) return set_error(BID_EINVAL, "flat group layout inconsistent");
+    TreeHost T;
+    if (smem_cap > 0) BID_TRY(build_tree_sched(F, precision == BID_FP64 ? 8 : 4, smem_cap, from, &T));
+    if (sched) {
+        sched[0] = T.lev0;
+        sched[1] = T.lev1;
+        sched[2] = T.ntask;
+        sched[3] = (int64_t)T.succ_f.size();
+        sched[4] = (int64_t)T.succ_b.size();
+    }
+    if (!replay(F, b, 0.0, x, &vshift, smem_cap > 0 ? &T : nullptr))
+        return set_error(BID_EINVAL, "flat group layout or dataflow schedule inconsistent");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->n1 = F.n;

@@ -174,12 +174,12 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for phase 0 of `bar` (about 2^20 polls with a short sleep
+// Bounded wait for the phase of `bar` with the given parity (about 2^20 polls with a short sleep
 // between them, well under a second); false when the limit is reached (the
 // caller records the error and gives up).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity = 0) {
     for (int i = 0; i < (1 << 20); ++i) {
-        if (mbar_test_wait(bar, 0)) return true;
+        if (mbar_test_wait(bar, parity)) return true;
         if (i >= 8) __nanosleep(64);
     }
     return false;
@@ -189,6 +189,7 @@ constexpr int BULK_CHUNK = 16384;   // bytes per bulk-copy instruction
 // static shared memory of the flat kernels is at most 44 KB (FP64 staging)
 constexpr int FLAT_DYN_MAX = 176 * 1024;   // group block (data + slots) of one flat group
 constexpr int FLAT_SMEM_MAX = 224 * 1024;  // with descriptors and staged inputs
+constexpr int TREE_SMEM_MAX = 96 * 1024;   // a CTA of the dataflow flat kernels
 
 __device__ __forceinline__ void bulk_region(unsigned char* dst, const void* src, int nbytes,
                                             uint64_t* bar) {
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict
 // that does not complete within the wait limit sets *err and the CTA returns
 // (the result is then invalid and the error is reported by the solve).
 constexpr int FT = FLAT_THREADS;
+static_assert(FT >= 64, "the dataflow kernels fetch the next group on the second warp");
 
 // both update slots of frontal row f, from the group's copy in shared memory
 __device__ __forceinline__ double incoming_s(const double* ss, const GCl& c, int f) {
@@ -300,35 +302,13 @@ __device__ __forceinline__ double incoming_s(const double* ss, const GCl& c, int
     return val.x + val.y;
 }
 
-// Dynamic shared memory of a flat launch: [group block (bytes)] [descriptors
-// (GCl, at sc_off)] [staged inputs (A, at w_off)], sized per level.
+// Forward of one flat group from shared memory (its factor block at smem,
+// the children's update slots right after it, descriptors scl, inputs w).
 template <typename T, typename A>
-__global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
-                                                 const double* xp, double* ybuf, double* inb,
-                                                 unsigned int* err, int sc_off, int w_off) {
+__device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, const GCl* scl, int nc,
+                                              const unsigned char* smem, A* w, double* ybuf, double* inb) {
     constexpr int VEC = VecOf<T>::N;
-    extern __shared__ __align__(128) unsigned char dyn_smem[];
-    GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
-    A* w = reinterpret_cast<A*>(dyn_smem + w_off);
-    __shared__ __align__(8) uint64_t bar;
-    const FGroup G = v.fg[g0 + blockIdx.x];
-    const int nc = G.c1 - G.c0;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        group_load(dyn_smem, data + G.dstart, G.nbytes, G.sbytes, &bar);
-    }
-    for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
-    pdl_wait();
-    pdl_trigger();
-    if (threadIdx.x == 0) group_load_slots(dyn_smem, G.nbytes, inb + G.sstart, G.sbytes, &bar);
-    // contiguous range of the group's right-hand side
-    for (int f = threadIdx.x; f < G.wf; f += FT) w[f] = (A)xp[G.pstart + f];
-    __syncthreads();
-    if (!mbar_wait_bounded(&bar)) {
-        if (threadIdx.x == 0) atomicOr(err, 1u);
-        return;
-    }
-    const double* ss = reinterpret_cast<const double*>(dyn_smem + G.nbytes);
+    const double* ss = reinterpret_cast<const double*>(smem + G.nbytes);
     if (G.sbytes > 0) {   // add the children's updates (zero where none)
         for (int f = threadIdx.x; f < G.wf; f += FT) {
             const GCl& c = scl[group_owner<0>(scl, nc, f)];
@@ -336,7 +316,7 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
         }
         __syncthreads();
     }
-    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    const T* sd = reinterpret_cast<const T*>(smem);
     for (int u = threadIdx.x; u < G.uf; u += FT) {
         const GCl& c = scl[group_owner<2>(scl, nc, u)];
         const int q0 = (u - c.uf0) * VEC;
@@ -378,6 +358,66 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
     }
 }
 
+// Dynamic shared memory of a flat launch: [group block (bytes)] [descriptors
+// (GCl, at sc_off)] [staged inputs (A, at w_off)], sized per level.
+template <typename T, typename A>
+__global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
+                                                 const double* xp, double* ybuf, double* inb,
+                                                 unsigned int* err, int sc_off, int w_off) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
+    A* w = reinterpret_cast<A*>(dyn_smem + w_off);
+    __shared__ __align__(8) uint64_t bar;
+    const FGroup G = v.fg[g0 + blockIdx.x];
+    const int nc = G.c1 - G.c0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        group_load(dyn_smem, data + G.dstart, G.nbytes, G.sbytes, &bar);
+    }
+    for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) group_load_slots(dyn_smem, G.nbytes, inb + G.sstart, G.sbytes, &bar);
+    // contiguous range of the group's right-hand side
+    for (int f = threadIdx.x; f < G.wf; f += FT) w[f] = (A)xp[G.pstart + f];
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar)) {
+        if (threadIdx.x == 0) atomicOr(err, 1u);
+        return;
+    }
+    flat_fwd_body<T, A>(v, G, scl, nc, dyn_smem, w, ybuf, inb);
+}
+
+// Backward of one flat group from shared memory (factor block at smem,
+// descriptors scl, staged inputs vs).
+template <typename T, typename A>
+__device__ __forceinline__ void flat_bwd_body(const HView& v, const FGroup& G, const GCl* scl, int nc,
+                                              const unsigned char* smem, const A* vs, double* out) {
+    constexpr int VEC = VecOf<T>::N;
+    const T* sd = reinterpret_cast<const T*>(smem);
+    for (int u = threadIdx.x; u < G.ub; u += FT) {
+        const GCl& c = scl[group_owner<3>(scl, nc, u)];
+        const int j = u - c.ub0;
+        const A* vv = vs + c.woff_b;
+        const T* cj = sd + c.doff + col_start(c.nd, j, VEC) - j;
+        const int q0 = j & ~(VEC - 1);
+        // first vector: the rows from j on
+        A val[VEC];
+        lds16(cj + q0, val);
+        A acc = 0;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (q0 + e >= j && q0 + e < c.nd) acc += val[e] * vv[q0 + e];
+        // whole vectors, then the ragged end (staged inputs are zero there)
+        for (int q = q0 + VEC; q < c.nd; q += VEC) {
+            lds16(cj + q, val);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc += val[e] * vv[q + e];
+        }
+        out[v.pidx[G.pstart + u]] = (double)acc;   // u = pivot offset inside the group
+    }
+}
+
 // Backward: the staged input of a cluster is v = [y_s; -x_B; 0 (vec)]; the
 // group's y are the positions [pstart, pstart + wf) of ybuf and its boundary
 // rows the range [bstart, bstart + nbt) of bidx, both read contiguously.
@@ -385,7 +425,6 @@ template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* __restrict__ ybuf, double* out,
                                                  unsigned int* err, int sc_off, int w_off) {
-    constexpr int VEC = VecOf<T>::N;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
     A* vs = reinterpret_cast<A*>(dyn_smem + w_off);
@@ -413,28 +452,201 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
         if (threadIdx.x == 0) atomicOr(err, 1u);
         return;
     }
-    const T* sd = reinterpret_cast<const T*>(dyn_smem);
-    for (int u = threadIdx.x; u < G.ub; u += FT) {
-        const GCl& c = scl[group_owner<3>(scl, nc, u)];
-        const int j = u - c.ub0;
-        const A* vv = vs + c.woff_b;
-        const T* cj = sd + c.doff + col_start(c.nd, j, VEC) - j;
-        const int q0 = j & ~(VEC - 1);
-        // first vector: the rows from j on
-        A val[VEC];
-        lds16(cj + q0, val);
-        A acc = 0;
-#pragma unroll
-        for (int e = 0; e < VEC; ++e)
-            if (q0 + e >= j && q0 + e < c.nd) acc += val[e] * vv[q0 + e];
-        // whole vectors, then the ragged end (staged inputs are zero there)
-        for (int q = q0 + VEC; q < c.nd; q += VEC) {
-            lds16(cj + q, val);
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) acc += val[e] * vv[q + e];
+    flat_bwd_body<T, A>(v, G, scl, nc, dyn_smem, vs, out);
+}
+
+// ------------------------------------------------------------ dataflow flat levels
+// The flat groups of the levels [tree_lev0, tree_lev1) in one persistent
+// launch per pass instead of one launch per level (the schedule is built on
+// the host, TreeHost; task i is group first + i).  An atomic queue hands the groups out in a fixed
+// order (forward: increasing group index, bottom level first; backward:
+// decreasing); a CTA starts the bulk copy of its group's factor block, thread
+// 0 waits (bounded) until the group has received its signals while thread 32
+// fetches the next group, and after the arithmetic every group signals its
+// successors.  Every dependency of a group is handed out earlier, so the CTA
+// holding the earliest unfinished group can always go on: the kernel does not
+// rely on its CTAs being co-resident.  Data written by other CTAs of the same
+// launch (update slots, x) is read from L2 (ld.cg) after an acquire.  A
+// counter is reset by its group once consumed and the last CTA to leave
+// resets the queue, so the state is zero between solves; after an expired
+// wait (error word set) the last CTA also zeroes every counter.
+struct TreeSched {
+    int32_t first, ntask;
+    const int32_t* __restrict__ need;   // signals a group waits for
+    const int32_t* __restrict__ ptr;    // its successors succ[ptr[g] .. ptr[g + 1])
+    const int32_t* __restrict__ succ;
+    unsigned int* cnt;                  // signals received
+    unsigned int* queue;                // [0] next hand-out, [1] CTAs that have left
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+    return x;
+}
+// order this CTA's earlier shared-memory accesses before a later bulk copy into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Thread 0: wait until the group's counter reaches `need` (about 2^20 polls,
+// about a second; gives up at once when some CTA has recorded an error) and
+// reset it.  False: gave up (the error word is set).
+__device__ __forceinline__ bool tree_wait(unsigned int* cnt, int need, unsigned int* err) {
+    if (need <= 0) return true;
+    for (int i = 0; i < (1 << 20); ++i) {
+        if (ld_acquire_u32(cnt) >= (unsigned int)need) {
+            *cnt = 0u;
+            return true;
         }
-        out[v.pidx[G.pstart + u]] = (double)acc;   // u = pivot offset inside the group
+        if ((i & 31) == 31 && *reinterpret_cast<volatile unsigned int*>(err)) return false;
+        if (i >= 4) __nanosleep(100);
     }
+    atomicOr(err, 4u);
+    return false;
+}
+
+// all threads: make the group's results visible, then signal its successors
+__device__ __forceinline__ void tree_signal(const TreeSched& ts, int g) {
+    __threadfence();
+    __syncthreads();
+    const int e0 = ts.ptr[g], e1 = ts.ptr[g + 1];
+    if (e0 + (int)threadIdx.x < e1) {
+        __threadfence();
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&ts.cnt[ts.succ[e]], 1u);
+    }
+}
+
+// Thread 32 (the second warp): take the next group from the queue and stage
+// its descriptor, while thread 0 waits for the current one.
+__device__ __forceinline__ void tree_fetch(const TreeSched& ts, const FGroup* __restrict__ fg, bool reverse,
+                                           int* s_next, FGroup* s_G) {
+    const int i = (int)atomicAdd(ts.queue, 1u);
+    *s_next = i;
+    if (i < ts.ntask) *s_G = fg[ts.first + (reverse ? ts.ntask - 1 - i : i)];
+}
+
+__device__ __forceinline__ void tree_exit(const TreeSched& ts, unsigned int* err, int* s_last) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *s_last = atomicAdd(ts.queue + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    if (*reinterpret_cast<volatile unsigned int*>(err))
+        for (int i = threadIdx.x; i < ts.ntask; i += blockDim.x) ts.cnt[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ts.queue[0] = 0u;
+        ts.queue[1] = 0u;
+        __threadfence();
+    }
+}
+
+// Shared memory: [group block (factor data, then update slots)] [descriptors
+// at sc_off] [staged inputs at w_off], sized for the largest group.
+template <typename T, typename A>
+__global__ void __launch_bounds__(FT) k_tree_fwd(HView v, const T* __restrict__ data, TreeSched ts,
+                                                 const double* xp, double* ybuf, double* inb,
+                                                 unsigned int* err, int sc_off, int w_off) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
+    A* w = reinterpret_cast<A*>(dyn_smem + w_off);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) FGroup s_G[2];
+    __shared__ int s_next[2], s_fail, s_last;
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        tree_fetch(ts, v.fg, false, &s_next[0], &s_G[0]);
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int g = s_next[it & 1];
+        if (g >= ts.ntask) break;
+        const FGroup G = s_G[it & 1];
+        const int nc = G.c1 - G.c0;
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            group_load(dyn_smem, data + G.dstart, G.nbytes, 0, &bar);
+            s_fail = tree_wait(ts.cnt + g, ts.need[g], err) ? 0 : 1;
+        } else if (threadIdx.x == 32) {
+            tree_fetch(ts, v.fg, false, &s_next[(it + 1) & 1], &s_G[(it + 1) & 1]);
+        }
+        for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+        for (int f = threadIdx.x; f < G.wf; f += FT) w[f] = (A)xp[G.pstart + f];
+        __syncthreads();
+        const bool fail = s_fail != 0;
+        if (!fail && G.sbytes > 0) {   // the children's update slots, written in this launch
+            double2* ss = reinterpret_cast<double2*>(dyn_smem + G.nbytes);
+            const double2* src = reinterpret_cast<const double2*>(inb + G.sstart);
+            for (int k = threadIdx.x; k < G.sbytes / 16; k += FT) ss[k] = __ldcg(src + k);
+        }
+        const bool ok = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+        if (__syncthreads_or(fail || !ok)) {
+            if (threadIdx.x == 0 && !ok) atomicOr(err, 1u);
+            break;
+        }
+        flat_fwd_body<T, A>(v, G, scl, nc, dyn_smem, w, ybuf, inb);
+        tree_signal(ts, g);
+    }
+    tree_exit(ts, err, &s_last);
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(FT) k_tree_bwd(HView v, const T* __restrict__ data, TreeSched ts,
+                                                 const double* __restrict__ ybuf, double* out,
+                                                 unsigned int* err, int sc_off, int w_off) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
+    A* vs = reinterpret_cast<A*>(dyn_smem + w_off);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) FGroup s_G[2];
+    __shared__ int s_next[2], s_fail, s_last;
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        tree_fetch(ts, v.fg, true, &s_next[0], &s_G[0]);
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int i = s_next[it & 1];
+        if (i >= ts.ntask) break;
+        const int g = ts.ntask - 1 - i;
+        const FGroup G = s_G[it & 1];
+        const int nc = G.c1 - G.c0;
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            group_load(dyn_smem, data + G.dstart, G.nbytes, 0, &bar);
+            s_fail = tree_wait(ts.cnt + g, ts.need[g], err) ? 0 : 1;
+        } else if (threadIdx.x == 32) {
+            tree_fetch(ts, v.fg, true, &s_next[(it + 1) & 1], &s_G[(it + 1) & 1]);
+        }
+        for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+        __syncthreads();
+        const bool fail = s_fail != 0;
+        if (!fail)
+            for (int f = threadIdx.x; f < G.wb; f += FT) {
+                const GCl& c = scl[group_owner<1>(scl, nc, f)];
+                const int q = f - c.woff_b;
+                double x = 0.0;
+                if (q < c.ni) x = ybuf[G.pstart + c.woff_f + q];
+                else if (q < c.nd) x = -__ldcg(out + v.bidx[G.bstart + c.boff + q - c.ni]);
+                vs[f] = (A)x;
+            }
+        const bool ok = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+        if (__syncthreads_or(fail || !ok)) {
+            if (threadIdx.x == 0 && !ok) atomicOr(err, 1u);
+            break;
+        }
+        flat_bwd_body<T, A>(v, G, scl, nc, dyn_smem, vs, out);
+        tree_signal(ts, g);
+    }
+    tree_exit(ts, err, &s_last);
 }
 
 // ------------------------------------------------------------ large clusters
@@ -806,6 +1018,39 @@ bool pdl_enabled() {
     return on;
 }
 
+// Dataflow kernels for a range of flat levels, used with BID_TREE=1 in the
+// environment: the range starts at level BID_TREE_FROM (default 1: the leaf
+// level, which carries most of the factor bytes, keeps its own launch at the
+// occupancy of its small groups) and takes the levels whose largest group
+// needs at most BID_TREE_SMEM bytes of shared memory (default 32 KB).  On
+// the 2049^2 slice they measured slower than the per-level launches with
+// programmatic dependent launch (72 against 79 steps/s): a group's serial
+// chain (queue fetch, dependency wait, slot loads, release fence) keeps its
+// CTA's warps waiting at barriers, and that chain, not the launches, bounds
+// these levels.  So the per-level launches are the default.
+bool tree_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("BID_TREE");
+        return e && std::strcmp(e, "1") == 0;
+    }();
+    return on;
+}
+int tree_from() {
+    static const int from = [] {
+        const char* e = std::getenv("BID_TREE_FROM");
+        return e ? std::max(0, std::atoi(e)) : 1;
+    }();
+    return from;
+}
+int tree_smem_cap() {
+    static const int cap = [] {
+        const char* e = std::getenv("BID_TREE_SMEM");
+        const int c = e ? std::atoi(e) : 32 * 1024;
+        return std::max(4096, std::min(c, TREE_SMEM_MAX));
+    }();
+    return cap;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
                      cudaStream_t st, Args... args) {
@@ -914,7 +1159,28 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_upper_bwd<T, A>, HT, 0));
         grid_b = (unsigned)std::max(1, std::min(nb * L.sms, most_b));
     }
+    // flat levels [t0, t1): one dataflow launch per pass
+    const bool tree = F.tree_lev1 > F.tree_lev0 && tree_enabled() && F.tree_lev1 <= lu;
+    const int t0 = tree ? F.tree_lev0 : 0, t1 = tree ? F.tree_lev1 : 0;
+    TreeSched tf{}, tb{};
+    unsigned tgrid_f = 1, tgrid_b = 1;
+    if (tree) {
+        const int32_t* ix = F.tree_idx;
+        tf = TreeSched{F.tree_first, F.tree_ntask, ix + F.tree_off[0], ix + F.tree_off[1], ix + F.tree_off[2],
+                       F.tree_state, F.tree_state + 2 * F.tree_ntask};
+        tb = TreeSched{F.tree_first, F.tree_ntask, ix + F.tree_off[3], ix + F.tree_off[4], ix + F.tree_off[5],
+                       F.tree_state + F.tree_ntask, F.tree_state + 2 * F.tree_ntask + 2};
+        tgrid_f = (unsigned)std::max(1, std::min(F.tree_ntask, F.tree_cta_f * L.sms));
+        tgrid_b = (unsigned)std::max(1, std::min(F.tree_ntask, F.tree_cta_b * L.sms));
+    }
     for (int lev = 0; lev < lu; ++lev) {
+        if (tree && lev == t0) {
+            BID_CUDA_TRY(launch_k(k_tree_fwd<T, A>, tgrid_f, FT, (size_t)F.tree_smem_f, L.st, v, data, tf,
+                                  S.xp, S.ybuf, inb, S.err, F.tree_sc_off, F.tree_w_off));
+            ++launches;
+            lev = t1 - 1;
+            continue;
+        }
         const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
         if (nf > 0) {
             const int sc_off = (F.fg_bytes[lev] + 15) / 16 * 16;
@@ -942,6 +1208,13 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         launches += 2;
     }
     for (int lev = lu - 1; lev >= 0; --lev) {
+        if (tree && lev == t1 - 1) {
+            BID_CUDA_TRY(launch_k(k_tree_bwd<T, A>, tgrid_b, FT, (size_t)F.tree_smem_b, L.st, v, data, tb,
+                                  S.ybuf, out, S.err, F.tree_sc_off, F.tree_w_off));
+            ++launches;
+            lev = t0;
+            continue;
+        }
         const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
         const int nv = F.vg_ptr[lev + 1] - F.vg_ptr[lev];
         if (ng + nv > 0) {
@@ -988,6 +1261,10 @@ int prepare_one() {
                                       FLAT_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       FLAT_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_tree_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TREE_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_tree_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TREE_SMEM_MAX));
     return BID_OK;
 }
 
@@ -1037,6 +1314,54 @@ static int upload_vec(const std::vector<V>& h, V** d) {
     if (h.empty()) return BID_OK;
     BID_CUDA_TRY(cudaMalloc(d, sizeof(V) * h.size()));
     BID_CUDA_TRY(cudaMemcpy(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
+    return BID_OK;
+}
+
+template <typename T, typename A>
+int tree_occupancy(const HFactorDev* d, int* cf, int* cb) {
+    BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(cf, k_tree_fwd<T, A>, FT, d->tree_smem_f));
+    BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(cb, k_tree_bwd<T, A>, FT, d->tree_smem_b));
+    return BID_OK;
+}
+
+// Dataflow schedule of a range of flat levels (none when tree_enabled() is
+// off or the range holds fewer than two levels).
+static int upload_tree(const HFactorHost& h, int precision, HFactorDev* d) {
+    d->tree_lev0 = d->tree_lev1 = 0;
+    if (!tree_enabled()) return BID_OK;
+    TreeHost T;
+    BID_TRY(build_tree_sched(h, precision == BID_FP64 ? 8 : 4, tree_smem_cap(), tree_from(), &T));
+    if (T.lev1 - T.lev0 < 2) return BID_OK;
+    if (T.smem_f > TREE_SMEM_MAX || T.smem_b > TREE_SMEM_MAX || T.sc_off % 16 || T.w_off % 8)
+        return set_error(BID_EINVAL, "dataflow schedule exceeds its shared memory");
+    std::vector<int32_t> idx;
+    const std::vector<int32_t>* parts[6] = {&T.need_f, &T.ptr_f, &T.succ_f, &T.need_b, &T.ptr_b, &T.succ_b};
+    for (int k = 0; k < 6; ++k) {
+        d->tree_off[k] = (int64_t)idx.size();
+        idx.insert(idx.end(), parts[k]->begin(), parts[k]->end());
+    }
+    idx.push_back(0);   // never empty
+    BID_TRY(upload_vec(idx, &d->tree_idx));
+    const size_t nstate = 2 * (size_t)T.ntask + 4;
+    BID_CUDA_TRY(cudaMalloc(&d->tree_state, sizeof(unsigned int) * nstate));
+    BID_CUDA_TRY(cudaMemset(d->tree_state, 0, sizeof(unsigned int) * nstate));
+    d->tree_ntask = T.ntask;
+    d->tree_first = T.first;
+    d->tree_sc_off = T.sc_off;
+    d->tree_w_off = T.w_off;
+    d->tree_smem_f = T.smem_f;
+    d->tree_smem_b = T.smem_b;
+    int cf = 0, cb = 0;
+    switch (precision) {
+        case BID_FP64: BID_TRY((tree_occupancy<double, double>(d, &cf, &cb))); break;
+        case BID_FP32: BID_TRY((tree_occupancy<float, float>(d, &cf, &cb))); break;
+        default: BID_TRY((tree_occupancy<__nv_bfloat16, float>(d, &cf, &cb))); break;
+    }
+    if (cf < 1 || cb < 1) return BID_OK;   // does not fit: per-level launches
+    d->tree_cta_f = cf;
+    d->tree_cta_b = cb;
+    d->tree_lev0 = T.lev0;
+    d->tree_lev1 = T.lev1;
     return BID_OK;
 }
 
@@ -1132,6 +1457,7 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
         BID_TRY(upload_vec(f, reinterpret_cast<uint16_t**>(&d->data)));
         esz = 2;
     }
+    BID_TRY(upload_tree(h, precision, d));
     BID_CUDA_TRY(cudaMalloc(&d->inb, sizeof(double) * std::max<int64_t>(h.nslots, 2)));
     BID_CUDA_TRY(cudaMemset(d->inb, 0, sizeof(double) * std::max<int64_t>(h.nslots, 2)));
     d->bytes_pass = 2 * (int64_t)n * esz;
@@ -1142,7 +1468,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 
 void free_hfactor(HFactorDev* d) {
     void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout,  d->vgl, d->sn,
-                    d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched};
+                    d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
+                    d->tree_idx, d->tree_state};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

@@ -264,7 +264,40 @@ struct HFactorDev {
     int64_t bytes_pass = 0;             // stored factor bytes read by fwd + bwd
     int64_t alg_bytes_pass = 0;         // nonzero entries only (no padding)
     int32_t vec = 2;
+    // dataflow schedule of the flat levels [tree_lev0, tree_lev1) (TreeHost; equal: none)
+    int32_t tree_lev0 = 0, tree_lev1 = 0, tree_first = 0, tree_ntask = 0;
+    int32_t* tree_idx = nullptr;        // need_f | ptr_f | succ_f | need_b | ptr_b | succ_b
+    int64_t tree_off[6] = {0, 0, 0, 0, 0, 0};
+    unsigned int* tree_state = nullptr; // counters f (ntask) | b (ntask) | queue f (2) | queue b (2)
+    int32_t tree_sc_off = 0, tree_w_off = 0, tree_smem_f = 0, tree_smem_b = 0;
+    int32_t tree_cta_f = 0, tree_cta_b = 0;   // resident CTAs per SM
 };
+// Dataflow schedule of the flat groups of the levels [lev0, lev1): the groups
+// first .. first + ntask - 1 (tasks, numbered from 0 in group order = lower
+// level first) that the persistent solve kernels run in two launches instead
+// of one launch per level.  Dependencies on groups outside the range are met
+// by the launches before (forward: lower levels) or after (backward) them.
+//  forward:  group h waits for need_f[h] signals, one from every group g
+//            holding a child of one of its clusters (g writes h's update
+//            slots); g signals succ_f[ptr_f[g] .. ptr_f[g+1]);
+//  backward: group g waits for need_b[g] signals, one from every group h
+//            holding the pivot of a boundary row of one of its clusters (h
+//            writes that entry of x); h signals succ_b[ptr_b[h] .. ptr_b[h+1]).
+// Forward edges go from a lower to a higher group index, backward edges from a
+// higher to a lower one, so handing the groups out in increasing (forward) or
+// decreasing (backward) order never makes a group wait for a later one.
+// The levels are the longest run from level `from` with no large cluster
+// whose largest group fits smem_cap bytes of shared memory; fewer than two
+// levels: no schedule (lev1 = lev0 = 0).
+struct TreeHost {
+    int32_t lev0 = 0, lev1 = 0, first = 0, ntask = 0;
+    std::vector<int32_t> need_f, ptr_f, succ_f, need_b, ptr_b, succ_b;
+    int32_t sc_off = 0;                 // shared memory: group block | descriptors (sc_off)
+    int32_t w_off = 0;                  //   | staged inputs (w_off)
+    int32_t smem_f = 0, smem_b = 0;     // bytes of a forward / backward CTA
+};
+int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from, TreeHost* T);
+
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
 void free_hfactor(HFactorDev* d);
 

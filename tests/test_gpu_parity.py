@@ -299,3 +299,70 @@ def test_host_driven_loop_equals_graph_loop(bid, tmp_path, graph):
         out[g] = np.load(f)
     assert out["1"][-1] >= 1
     assert np.array_equal(out["1"], out[graph])
+
+
+_DATAFLOW_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_08708_gb300 import bid
+from workloads import torso_square_2d, params_2d
+from oracle import bidomain as ob
+p = params_2d(0.1)
+out, levels = [], []
+for prec, leaf in (("fp32", 32), ("fp64", 16), ("bf16", 32)):
+    mesh = torso_square_2d(257)
+    S = bid.System(mesh, p)
+    P = bid.Precond(S, p["dt"], eps=1e-3, precision=prec, leaf=leaf)
+    st = P.stats
+    levels += [st["dataflow_levels1"], st["dataflow_levelsk"]]
+    rng = np.random.default_rng(7)
+    for which, n in ((1, S.N), (2, S.NH)):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        P.apply_factor(which, torch.tensor(rng.normal(size=n), device="cuda"), x)
+        out.append(x.cpu().numpy())
+o = ob.build_system(mesh, p)
+Y = ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"])
+X = torch.zeros(o.N + o.NH, dtype=torch.float64, device="cuda")
+info = P.solve(torch.tensor(Y, device="cuda"), X, tol=1e-10)
+out += [X.cpu().numpy(), [info["iters"]]]
+S2 = bid.System(torso_square_2d(193, semi_axes=(2.0, 3.0)), p)
+B = bid.Batch([S, S2], p["dt"], eps=1e-3, precision="fp32", leaf=32)
+levels += [B.stats["dataflow_levels1"]]
+Yb = np.zeros(B.n)
+Yb[:o.N + o.NH] = Y
+Yb[o.N + o.NH + S2.N:] = 10.0 * S2.mH
+Xb = torch.zeros(B.n, dtype=torch.float64, device="cuda")
+binfo, _ = B.solve(torch.tensor(Yb, device="cuda"), Xb, tol=1e-10)
+out += [Xb.cpu().numpy(), [i["iters"] for i in binfo]]
+np.save(sys.argv[2], np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in out]))
+np.save(sys.argv[3], np.array(levels))
+"""
+
+
+@pytest.mark.parametrize("variant", ["on", "wide", "leaf"])
+def test_dataflow_levels_equal_level_launches(bid, tmp_path, variant):
+    # a range of flat levels in two dataflow launches per pass (BID_TREE=1),
+    # over more levels (BID_TREE_SMEM=65536) or taking in the leaf level
+    # (BID_TREE_FROM=0), gives the same factor solves, PCG iterates and
+    # batched iterates, bit for bit, as one launch per level (the default)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "s.py"
+    script.write_text(_DATAFLOW_SCRIPT)
+    envs = {"default": {}, "on": {"BID_TREE": "1"}, "wide": {"BID_TREE": "1", "BID_TREE_SMEM": "65536"},
+            "leaf": {"BID_TREE": "1", "BID_TREE_FROM": "0"}}
+    res = {}
+    for name in ("default", variant):
+        f, lv = tmp_path / f"x_{name}.npy", tmp_path / f"l_{name}.npy"
+        env = {k: v for k, v in os.environ.items() if not k.startswith("BID_TREE")}
+        env.update(envs[name])
+        subprocess.run([sys.executable, str(script), root, str(f), str(lv)], check=True, env=env,
+                       timeout=900)
+        res[name] = (np.load(f), np.load(lv))
+    x0, l0 = res["default"]
+    x1, l1 = res[variant]
+    assert (l0 == 0).all()
+    assert (l1[[0, 2, 4, 6]] >= 2).all()            # P_1 of every precision and the batch forest
+    assert np.array_equal(x0, x1)

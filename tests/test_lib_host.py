@@ -96,6 +96,35 @@ def test_host_factor_exact_with_upper_levels(bid, n, leaf, block, precision):
     assert st["levels1"] >= 3 and st["dense_blocks"] >= 1   # some large clusters
 
 
+@pytest.mark.parametrize("n,leaf,precision,eps,cap,first", [(161, 16, "fp64", 0.0, 32768, 1),
+                                                            (129, 32, "fp32", 1e-3, 32768, 0),
+                                                            (161, 16, "bf16", 1e-3, 49152, 1),
+                                                            (129, 8, "fp32", 0.0, 65536, 2)])
+def test_dataflow_schedule_is_complete(bid, n, leaf, precision, eps, cap, first):
+    # the bottom flat levels replayed in the order of the dataflow kernels'
+    # signals, each group as early as its dependencies allow (forward the
+    # highest-numbered ready group, backward the lowest): a missing
+    # dependency would read an update slot or an x entry before it is
+    # written, so bit equality with the level-by-level replay checks the
+    # schedule
+    m, p = torso_square_2d(n), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    rng = np.random.default_rng(n + leaf)
+    s = ob.build_system(m, p)
+    g = ob.gamma_of(p, 0.1)
+    for which, size, gam in ((1, s.N, 0.0), (2, s.NH, g)):
+        b = rng.normal(size=size)
+        x0, _ = hs.factor_solve(which, b, gamma=gam, eps=eps, leaf=leaf, precision=precision)
+        x1, _, sch = hs.factor_solve_dataflow(which, b, smem_cap=cap, first=first, gamma=gam, eps=eps,
+                                              leaf=leaf, precision=precision)
+        assert sch["first"] == first and sch["levels"] >= 2 and sch["groups"] > 10
+        assert sch["deps_fwd"] > 0 and sch["deps_bwd"] >= sch["deps_fwd"]
+        assert np.array_equal(x0, x1)
+    # a cap below any group: no schedule, plain level order
+    _, _, sch = hs.factor_solve_dataflow(1, rng.normal(size=s.N), smem_cap=64, leaf=leaf, precision=precision)
+    assert sch["levels"] == 0
+
+
 def test_host_factor_3d_exact():
     import __graft_entry__
     __graft_entry__.build()
@@ -205,6 +234,29 @@ def test_host_batch_factor_forest(bid, precision, leaf):
         xo2 = spla.spsolve(ob.monodomain_matrix(s, g).tocsc(), bv)
         assert np.abs(x2[o + s.N:off[k + 1]] - xo2).max() <= 1e-12 * np.abs(xo2).max()
         assert not x2[o:o + s.N].any()
+
+
+@pytest.mark.parametrize("precision,cap,first", [("fp32", 32768, 1), ("fp64", 65536, 0),
+                                                  ("bf16", 49152, 2)])
+def test_host_batch_dataflow_schedule_is_complete(bid, precision, cap, first):
+    # the forest's bottom flat levels in the dataflow order (vector indices of
+    # the combined layout, one tree per slice) equal the level-by-level replay
+    sl = _slices(3, 7, 6, 10, 16)
+    hs = [bid.HostSystem(m, p) for m, p in sl]
+    ss = [ob.build_system(m, p) for m, p in sl]
+    n = sum(s.N + s.NH for s in ss)
+    rng = np.random.default_rng(11)
+    g = ob.gamma_of(sl[0][1], 0.1)
+    for which in (1, 2):
+        b = rng.normal(size=n)
+        x0, _ = bid.host_batch_factor_solve(hs, which, b, gamma=g, eps=1e-3, leaf=[32, 16, 32],
+                                            precision=precision)
+        x1, _, sch = bid.host_batch_factor_solve(hs, which, b, gamma=g, eps=1e-3, leaf=[32, 16, 32],
+                                                 precision=precision, smem_cap=cap, first=first,
+                                                 schedule=True)
+        assert sch["first"] == first and sch["levels"] >= 2
+        assert sch["deps_fwd"] > 0 and sch["deps_bwd"] > 0
+        assert np.array_equal(x0, x1)
 
 
 def test_host_batch_factor_errors(bid):
