@@ -185,6 +185,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 constexpr int BULK_CHUNK = 16384;   // bytes per bulk-copy instruction
+constexpr int LR_UNROLL = 8;        // low-rank products: loads issued ahead of their products
 // dynamic shared memory of a flat launch (the largest group of its level);
 // static shared memory of the flat kernels is at most 44 KB (FP64 staging)
 constexpr int FLAT_DYN_MAX = 176 * 1024;   // group block (data + slots) of one flat group
@@ -674,7 +675,15 @@ __device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict_
         A a = 0;
         if (l < g.k) {
             const T* V = data + g.off_v;
-            for (int j = grp; j < sn.ni; j += ng) a += (A)ldv(V + (int64_t)j * g.k + l) * w[j];
+            int j = grp;
+            for (; j + (LR_UNROLL - 1) * ng < sn.ni; j += LR_UNROLL * ng) {   // loads first, products in order
+                A x[LR_UNROLL];
+    #pragma unroll
+                for (int e = 0; e < LR_UNROLL; ++e) x[e] = (A)ldv(V + (int64_t)(j + e * ng) * g.k + l);
+    #pragma unroll
+                for (int e = 0; e < LR_UNROLL; ++e) a += x[e] * w[j + e * ng];
+            }
+            for (; j < sn.ni; j += ng) a += (A)ldv(V + (int64_t)j * g.k + l) * w[j];
         }
         red[tid][0] = a;
         __syncthreads();
@@ -689,7 +698,15 @@ __device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict_
         if (i < t.a1) {
             const T* U = data + g.off_u + (int64_t)i * g.k;
             A acc = 0;
-            for (int q = 0; q < g.k; ++q) acc += (A)ldv(U + q) * tl[q];
+            int q = 0;
+            for (; q + LR_UNROLL <= g.k; q += LR_UNROLL) {   // loads first, products in order
+                A u[LR_UNROLL];
+    #pragma unroll
+                for (int e = 0; e < LR_UNROLL; ++e) u[e] = (A)ldv(U + q + e);
+    #pragma unroll
+                for (int e = 0; e < LR_UNROLL; ++e) acc += u[e] * tl[q + e];
+            }
+            for (; q < g.k; ++q) acc += (A)ldv(U + q) * tl[q];
             finish_row(v, sn, g.row0 + i, (double)acc, ybuf, inb);
         }
         return;
@@ -809,7 +826,15 @@ __device__ __forceinline__ void prep_task(const HView& v, const T* __restrict__ 
     A acc = 0;
     if (l < g.k) {
         const T* U = data + g.off_u;
-        for (int r = grp; r < g.m; r += nq) acc += (A)ldv(U + (int64_t)r * g.k + l) * vv[r];
+        int r = grp;
+        for (; r + (LR_UNROLL - 1) * nq < g.m; r += LR_UNROLL * nq) {   // loads first, products in order
+            A u[LR_UNROLL];
+#pragma unroll
+            for (int e = 0; e < LR_UNROLL; ++e) u[e] = (A)ldv(U + (int64_t)(r + e * nq) * g.k + l);
+#pragma unroll
+            for (int e = 0; e < LR_UNROLL; ++e) acc += u[e] * vv[r + e * nq];
+        }
+        for (; r < g.m; r += nq) acc += (A)ldv(U + (int64_t)r * g.k + l) * vv[r];
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -829,6 +854,54 @@ __global__ void __launch_bounds__(HT) k_bwd_prep(HView v, const T* __restrict__ 
     pdl_wait();
     pdl_trigger();
     prep_task<T, A>(v, data, blockIdx.x, g0, ng, vg0, ybuf, out, tbuf, vbuf, vv, red);
+}
+
+// Low-rank terms of column j of cluster sn: acc += V_g(j, :) t_g over the
+// cluster's groups in order (LR_KMAX <= 64: lanes l and l + 32).  The group
+// descriptors are read one per lane and broadcast, and the loads of LR_BATCH
+// groups are issued before their products, so a cluster's groups cost a few
+// dependent loads instead of two per group.
+constexpr int LR_BATCH = 2;
+static_assert(LR_KMAX <= 64, "two entries of a low-rank row per lane");
+
+template <typename T, typename A>
+__device__ __forceinline__ void up_bwd_lr(const HView& v, const T* __restrict__ data, const HSnode& sn, int j,
+                                          int lane, const double* tbuf, A& acc) {
+    for (int g0 = sn.lr_begin; g0 < sn.lr_end; g0 += 32) {
+        const int n = min(32, sn.lr_end - g0);
+        int k = 0, to = 0;
+        int64_t ov = 0;
+        if (lane < n) {
+            const HLr G = v.lr[g0 + lane];
+            k = G.k;
+            ov = G.off_v;
+            to = G.t_off;
+        }
+        for (int b = 0; b < n; b += LR_BATCH) {
+            A vv[LR_BATCH][2], tt[LR_BATCH][2];
+            int kk[LR_BATCH];
+#pragma unroll
+            for (int u = 0; u < LR_BATCH; ++u) {
+                const int q = b + u < n ? b + u : 0;
+                const int kq = __shfl_sync(0xffffffffu, k, q);
+                const int64_t oq = __shfl_sync(0xffffffffu, ov, q);
+                const int tq = __shfl_sync(0xffffffffu, to, q);
+                kk[u] = b + u < n ? kq : 0;
+                const T* V = data + oq + (int64_t)j * kq;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int l = lane + 32 * h;
+                    vv[u][h] = l < kk[u] ? (A)ldv(V + l) : (A)0;
+                    tt[u][h] = l < kk[u] ? (A)__ldcg(tbuf + tq + l) : (A)0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < LR_BATCH; ++u)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (lane + 32 * h < kk[u]) acc += vv[u][h] * tt[u][h];
+        }
+    }
 }
 
 // Backward, large clusters: a column is shared by wpc = t.b0 warps (1..8, from
@@ -874,12 +947,7 @@ __device__ __forceinline__ void up_bwd_task(const HView& v, const T* __restrict_
                 if (q >= j && q < r1) acc += val[e] * (A)__ldcg(vv + q);
             }
         }
-        if (part == 0)
-            for (int g = sn.lr_begin; g < sn.lr_end; ++g) {
-                const HLr G = v.lr[g];
-                const T* V = data + G.off_v + (int64_t)j * G.k;
-                for (int l = lane; l < G.k; l += 32) acc += (A)ldv(V + l) * (A)__ldcg(tbuf + G.t_off + l);
-            }
+        if (part == 0) up_bwd_lr<T, A>(v, data, sn, j, lane, tbuf, acc);
     }
     acc = wsum(acc);
     if (lane == 0) red[warp] = acc;
