@@ -186,6 +186,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 constexpr int BULK_CHUNK = 16384;   // bytes per bulk-copy instruction
 constexpr int LR_UNROLL = 8;        // low-rank products: loads issued ahead of their products
+constexpr int PREP_BATCH = 4;       // backward staging: entries per thread whose loads go together
 // dynamic shared memory of a flat launch (the largest group of its level);
 // static shared memory of the flat kernels is at most 44 KB (FP64 staging)
 constexpr int FLAT_DYN_MAX = 176 * 1024;   // group block (data + slots) of one flat group
@@ -250,12 +251,6 @@ __device__ __forceinline__ int group_owner(const GCl* c, int n, int x) {
 
 __device__ __forceinline__ int dense_row(const HView& v, const HSnode& sn, int q) {
     return q < sn.ni ? q : v.drows[sn.drow_off + q - sn.ni];
-}
-
-// backward input of dense row q of cluster sn
-__device__ __forceinline__ double vrow(const HView& v, const HSnode& sn, int q,
-                                       const double* ybuf, const double* out) {
-    return q < sn.ni ? ybuf[sn.first + q] : -__ldcg(out + v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni]);
 }
 
 // Input shift of a solve: one scalar mean, or one mean per segment.
@@ -780,8 +775,18 @@ __device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict_
         for (int e = 0; e < VEC; ++e) {
             const int q = q0 + e;
             if (q < t.a1) {
+                // the column chunks' partial sums in order, loads issued ahead
+                const double* pp = pbuf + t.part + (q - t.a0);
                 double s = 0.0;
-                for (int k = 0; k < t.nparts; ++k) s += __ldcg(&pbuf[t.part + (int64_t)k * rows + (q - t.a0)]);
+                int k = 0;
+                for (; k + LR_UNROLL <= t.nparts; k += LR_UNROLL) {
+                    double x[LR_UNROLL];
+#pragma unroll
+                    for (int u = 0; u < LR_UNROLL; ++u) x[u] = __ldcg(pp + (int64_t)(k + u) * rows);
+#pragma unroll
+                    for (int u = 0; u < LR_UNROLL; ++u) s += x[u];
+                }
+                for (; k < t.nparts; ++k) s += __ldcg(pp + (int64_t)k * rows);
                 finish_row(v, sn, dense_row(v, sn, q), s, ybuf, inb);
             }
         }
@@ -811,9 +816,25 @@ __device__ __forceinline__ void prep_task(const HView& v, const T* __restrict__ 
                                           int vg0, const double* __restrict__ ybuf, const double* out,
                                           double* tbuf, double* vbuf, A (&vv)[LR_ROWS], A (&red)[HT]) {
     if (i >= ng) {
+        // batches of PREP_BATCH entries per thread: indices, then values, then stores
         const HSnode sn = v.sn[v.vgl[vg0 + i - ng]];
-        for (int q = threadIdx.x; q < sn.nd + 2 * VecOf<T>::N; q += HT)
-            vbuf[sn.v_off + q] = q < sn.nd ? vrow(v, sn, q, ybuf, out) : 0.0;
+        const int n = sn.nd + 2 * VecOf<T>::N;
+        for (int q0 = threadIdx.x; q0 < n; q0 += PREP_BATCH * HT) {
+            int src[PREP_BATCH];
+#pragma unroll
+            for (int b = 0; b < PREP_BATCH; ++b) {
+                const int q = q0 + b * HT;
+                src[b] = q >= sn.nd ? -1 : q < sn.ni ? sn.first + q
+                                                     : -2 - v.bidx[sn.bidx_off + dense_row(v, sn, q) - sn.ni];
+            }
+            double x[PREP_BATCH];
+#pragma unroll
+            for (int b = 0; b < PREP_BATCH; ++b)
+                x[b] = src[b] >= 0 ? ybuf[src[b]] : src[b] == -1 ? 0.0 : -__ldcg(out + (-2 - src[b]));
+#pragma unroll
+            for (int b = 0; b < PREP_BATCH; ++b)
+                if (q0 + b * HT < n) vbuf[sn.v_off + q0 + b * HT] = x[b];
+        }
         return;
     }
     const HLr g = v.lr[g0 + i];
