@@ -651,16 +651,24 @@ __global__ void __launch_bounds__(FT) k_tree_bwd(HView v, const T* __restrict__ 
 // order; split column chunks of a row chunk are combined by the last CTA.
 // Low-rank task: one CTA per group: t = V^T w_s (all ni columns), then
 // u = incoming - U t for the group's rows.
+// the cluster of a forward task (and, for a low-rank task, its group); the
+// launch kernel reads them before pdl_wait (immutable)
+__device__ __forceinline__ HSnode up_fwd_node(const HView& v, const HTask& t, HLr& g) {
+    if (t.s < 0) {
+        g = v.lr[-1 - t.s];
+        return v.sn[g.s];
+    }
+    return v.sn[t.s];
+}
+
 template <typename T, typename A>
 __device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict__ data, const HTask& t,
-                                            const double* xp, double* ybuf, double* inb, double* tbuf,
-                                            double* pbuf, unsigned int* tickets, unsigned char* smem,
-                                            A (&red)[HT][VecOf<T>::N], bool& last) {
+                                            const HLr& g, const HSnode& sn, const double* xp, double* ybuf,
+                                            double* inb, double* tbuf, double* pbuf, unsigned int* tickets,
+                                            unsigned char* smem, A (&red)[HT][VecOf<T>::N], bool& last) {
     constexpr int VEC = VecOf<T>::N;
     const int tid = threadIdx.x;
     if (t.s < 0) {
-        const HLr g = v.lr[-1 - t.s];
-        const HSnode sn = v.sn[g.s];
         A* w = reinterpret_cast<A*>(smem);
         A* tl = w + ((sn.ni + 1) & ~1);
         for (int i = tid; i < sn.ni; i += HT) w[i] = (A)gather_w(v, sn, i, xp, inb);
@@ -706,7 +714,6 @@ __device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict_
         }
         return;
     }
-    const HSnode sn = v.sn[t.s];
     A* w = reinterpret_cast<A*>(smem);
     for (int j = t.b0 + tid; j < t.b1; j += HT) w[j - t.b0] = (A)gather_w(v, sn, j, xp, inb);
     __syncthreads();
@@ -803,9 +810,11 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
     __shared__ A red[HT][VecOf<T>::N];
     __shared__ bool last;
     const HTask t = v.uft[task0 + blockIdx.x];
+    HLr g;
+    const HSnode sn = up_fwd_node(v, t, g);
     pdl_wait();
     pdl_trigger();
-    up_fwd_task<T, A>(v, data, t, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
+    up_fwd_task<T, A>(v, data, t, g, sn, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
 }
 
 // Backward preparation of one level, work item i: i < ng: t_g = U_g^T v_g for
@@ -931,10 +940,9 @@ __device__ __forceinline__ void up_bwd_lr(const HView& v, const T* __restrict__ 
 // are summed in order, plus the low-rank terms.
 template <typename T, typename A>
 __device__ __forceinline__ void up_bwd_task(const HView& v, const T* __restrict__ data, const HTask& t,
-                                            const double* vbuf, const double* tbuf, double* out,
-                                            A (&red)[NW]) {
+                                            const HSnode& sn, int dst, const double* vbuf, const double* tbuf,
+                                            double* out, A (&red)[NW]) {
     constexpr int VEC = VecOf<T>::N;
-    const HSnode sn = v.sn[t.s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpc = t.b0;
     const int j = t.a0 + warp / wpc, part = warp % wpc;
@@ -973,15 +981,18 @@ __device__ __forceinline__ void up_bwd_task(const HView& v, const T* __restrict_
     acc = wsum(acc);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
-    const int ncol = NW / wpc;
-    if ((int)threadIdx.x < ncol) {
-        const int jj = t.a0 + threadIdx.x;
-        if (jj < t.a1) {
-            A s = 0;
-            for (int w = 0; w < wpc; ++w) s += red[threadIdx.x * wpc + w];
-            out[v.pidx[sn.first + jj]] = (double)s;
-        }
+    if (dst >= 0) {
+        A s = 0;
+        for (int w = 0; w < wpc; ++w) s += red[threadIdx.x * wpc + w];
+        out[dst] = (double)s;
     }
+}
+
+// the output index of column t.a0 + threadIdx.x of a backward task, or -1
+// (immutable: read before pdl_wait by the launch kernel)
+__device__ __forceinline__ int up_bwd_dst(const HView& v, const HTask& t, const HSnode& sn) {
+    const int jj = t.a0 + (int)threadIdx.x;
+    return ((int)threadIdx.x < NW / t.b0 && jj < t.a1) ? v.pidx[sn.first + jj] : -1;
 }
 
 template <typename T, typename A>
@@ -990,9 +1001,11 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
                                                double* out) {
     __shared__ A red[NW];
     const HTask t = v.ubt[task0 + blockIdx.x];
+    const HSnode sn = v.sn[t.s];
+    const int dst = up_bwd_dst(v, t, sn);
     pdl_wait();
     pdl_trigger();
-    up_bwd_task<T, A>(v, data, t, vbuf, tbuf, out, red);
+    up_bwd_task<T, A>(v, data, t, sn, dst, vbuf, tbuf, out, red);
 }
 
 // ------------------------------------------------------------ upper levels, persistent
@@ -1047,7 +1060,9 @@ __global__ void __launch_bounds__(HT) k_upper_fwd(HView v, const T* __restrict__
     for (int lev = sc.lev0; lev < sc.lev1; ++lev) {
         for (int k = sc.uf[lev] + blockIdx.x; k < sc.uf[lev + 1]; k += gridDim.x) {
             const HTask t = v.uft[k];
-            up_fwd_task<T, A>(v, data, t, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
+            HLr g;
+            const HSnode sn = up_fwd_node(v, t, g);
+            up_fwd_task<T, A>(v, data, t, g, sn, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
             __syncthreads();
         }
         if (lev + 1 < sc.lev1) grid_barrier(sc.bar, sc.err);
@@ -1071,7 +1086,8 @@ __global__ void __launch_bounds__(HT) k_upper_bwd(HView v, const T* __restrict__
         grid_barrier(sc.bar, sc.err);
         for (int k = sc.ub[lev] + blockIdx.x; k < sc.ub[lev + 1]; k += gridDim.x) {
             const HTask t = v.ubt[k];
-            up_bwd_task<T, A>(v, data, t, vbuf, tbuf, out, redw);
+            const HSnode sn = v.sn[t.s];
+            up_bwd_task<T, A>(v, data, t, sn, up_bwd_dst(v, t, sn), vbuf, tbuf, out, redw);
             __syncthreads();
         }
         if (lev > sc.lev0) grid_barrier(sc.bar, sc.err);
