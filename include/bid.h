@@ -414,6 +414,15 @@ int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, dou
 int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double gamma, double eps,
                                    int leaf, int block, int precision, int smem_cap, int from,
                                    const double* b, double* x, bid_precond_stats* stats, int64_t* sched);
+/* bid_host_factor_solve for which = 1 (P_1 of S_1) with b zero outside the
+ * heart nodes (indices N_H .. N-1; EINVAL otherwise), replayed as the masked
+ * solve: every cluster whose subtree holds no heart node sees the constant
+ * input -mean(b) alone, so its forward results are -mean(b) times those of
+ * the all-ones input, which the replay computes first and then copies
+ * scaled.  Equal to bid_host_factor_solve's x up to rounding.  ndead (2
+ * entries, may be NULL): dead clusters, all clusters. */
+int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf, int block, int precision,
+                                 const double* b, double* x, int64_t* ndead);
 /* The batched factors on the host: the forest over nslices host systems
  * (combined layout as for bid_batch_create, leaf per slice or NULL for
  * `leaf_default`), replayed in FP64: which = 1 writes x_U,s = P_1,s^-1

@@ -95,6 +95,7 @@ SIGNATURES = {
     "bid_host_factor_solve": (_I, [_VP, _I, _D, _D, _I, _I, _I, _VP, _VP, C.POINTER(PrecondStats)]),
     "bid_host_factor_solve_dataflow": (_I, [_VP, _I, _D, _D, _I, _I, _I, _I, _I, _VP, _VP,
                                             C.POINTER(PrecondStats), _I64P]),
+    "bid_host_factor_solve_masked": (_I, [_VP, _D, _I, _I, _I, _VP, _VP, _I64P]),
     "bid_host_destroy": (None, [_VP]),
     "bid_batch_create": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, C.POINTER(_VP)]),
     "bid_batch_layout": (_I, [_VP, _VP, _VP]),
@@ -503,6 +504,17 @@ class HostSystem:
         _check(lib.bid_host_factor_solve(self.h, int(which), float(gamma), float(eps), int(leaf),
                                          int(block), prec, _ptr(b), _ptr(x), C.byref(st)))
         return x, st.as_dict()
+
+    def factor_solve_masked(self, b, eps=0.0, leaf=16, block=128, precision="fp64"):
+        """P_1 replay as the masked solve (b zero outside the heart nodes);
+        returns x and (dead clusters, clusters)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        nd = np.zeros(2, dtype=np.int64)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib.bid_host_factor_solve_masked(self.h, float(eps), int(leaf), int(block), prec, _ptr(b),
+                                                _ptr(x), nd.ctypes.data_as(_I64P)))
+        return x, (int(nd[0]), int(nd[1]))
 
     def factor_solve_dataflow(self, which, b, smem_cap=32768, first=1, gamma=0.0, eps=0.0, leaf=16,
                               block=128, precision="fp64"):

@@ -120,8 +120,8 @@ int precond_apply(bid_precond* P, const Launch& L, const double* r, double* z) {
     BID_TRY(launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->hs, z + N));
     // W = Pi^T S_i Z2 (zero on the torso), sum(W)
     BID_TRY(launch_si_apply_sum(L, N, NH, s->Si, z + N, P->w, P->sc, P->partials));
-    // Z1 -= P_1^-1 p W
-    BID_TRY(launch_hsolve(L, P->F1, P->w, &P->sc->sum_b, invN, P->hs, P->z1b));
+    // Z1 -= P_1^-1 p W (W is zero outside the heart: the masked solve)
+    BID_TRY(launch_hsolve_masked(L, P->F1, P->w, &P->sc->sum_b, invN, P->hs, P->z1b));
     BID_TRY(launch_axpy_sub(L, N, z, P->z1b));
     return BID_OK;
 }
@@ -444,6 +444,10 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
                          cudaMemset(P->p, 0, sizeof(double) * n) != cudaSuccess ||
                          cudaMemset(P->q, 0, sizeof(double) * n) != cudaSuccess))
         rc = set_error(BID_ECUDA, "cudaMemset failed");
+    // the masked P_1 solve of the preconditioner's second P_1 application: its
+    // input is zero outside the heart nodes (vector indices < N_H)
+    if (rc == BID_OK && hsolve_mask_enabled()) rc = upload_liveness(h1, (int32_t)NH, &P->F1);
+    if (rc == BID_OK && hsolve_mask_enabled()) rc = hsolve_ones(launch_of(s, nullptr), &P->F1, P->hs);
     if (rc != BID_OK) {
         bid_destroy_precond(P);
         return rc;

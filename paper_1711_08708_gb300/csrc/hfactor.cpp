@@ -812,6 +812,29 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     return BID_OK;
 }
 
+void cluster_liveness(const HFactorHost& F, int32_t nlive, std::vector<uint8_t>* live) {
+    const int nc = (int)F.sn.size();
+    live->assign(nc, 0);
+    std::vector<int32_t> owner(std::max<int64_t>(F.nslots, 1), -1), order(nc);
+    for (int s = 0; s < nc; ++s) {
+        const HSnode& h = F.sn[s];
+        for (int64_t k = h.inc_off; k < h.inc_off + 2 * (int64_t)(h.ni + h.nb) && k < F.nslots; ++k)
+            if (k >= 0) owner[k] = s;
+        for (int i = 0; i < h.ni; ++i)
+            if (F.pidx[h.first + i] < nlive) (*live)[s] = 1;
+        order[s] = s;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return F.sn[a].height < F.sn[b].height; });
+    for (int s : order) {
+        if (!(*live)[s]) continue;
+        const HSnode& h = F.sn[s];
+        for (int r = 0; r < h.nb; ++r) {
+            const int32_t slot = F.uout[h.u_off + r];
+            if (slot >= 0 && slot < F.nslots && owner[slot] >= 0) (*live)[owner[slot]] = 1;
+        }
+    }
+}
+
 int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from, TreeHost* T) {
     *T = TreeHost();
     const int H = (int)F.uf_ptr.size() - 1;

@@ -27,9 +27,28 @@ namespace {
 // have all arrived (parents before the remaining leaves); backward, the
 // lowest-numbered one.  A missing dependency then reads an input before it is
 // written, so the result differs from the level-by-level replay.
+// With a mask (the masked solve), a flat group whose clusters are all dead,
+// and a dead large cluster, write c times the all-ones forward results
+// (y1 / y1slot) instead of computing.  fwd_y / fwd_slots (if given) receive
+// the forward results.
+struct ReplayMask {
+    const std::vector<uint8_t>* live = nullptr;
+    const double* y1 = nullptr;
+    const double* y1slot = nullptr;
+    double c = 0.0;
+};
 bool replay(const HFactorHost& F, const double* b, double shift, double* x,
-            const std::vector<double>* vshift = nullptr, const TreeHost* T = nullptr) {
+            const std::vector<double>* vshift = nullptr, const TreeHost* T = nullptr,
+            const ReplayMask* mask = nullptr, std::vector<double>* fwd_y = nullptr,
+            std::vector<double>* fwd_slots = nullptr) {
     std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
+    auto scaled_copy = [&](const HSnode& s) {   // a dead cluster's forward results
+        for (int i = 0; i < s.ni; ++i) y[s.first + i] = mask->c * mask->y1[s.first + i];
+        for (int r = 0; r < s.nb; ++r) {
+            const int32_t slot = F.uout[s.u_off + r];
+            inb[slot] = mask->c * mask->y1slot[slot];
+        }
+    };
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
     const int esz = F.vec == 2 ? 8 : F.vec == 4 ? 4 : 2;   // bytes per stored entry
@@ -63,6 +82,14 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
     // columns, and the group's data read inside its bulk-copied block
     auto fwd_group = [&](int g) {
         const FGroup& G = F.fg[g];
+        if (mask) {
+            bool any = false;
+            for (int c = G.c0; c < G.c1; ++c) any = any || (*mask->live)[F.gcl[c].s];
+            if (!any) {
+                for (int c = G.c0; c < G.c1; ++c) scaled_copy(F.sn[F.gcl[c].s]);
+                return true;
+            }
+        }
         const int64_t gend = G.dstart + G.nbytes / esz;
         for (int c = G.c0; c < G.c1; ++c) {
             const GCl& d = F.gcl[c];
@@ -110,8 +137,14 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
         // flat groups first (their parents sit on later levels)
         for (int g = F.fg_ptr[lev]; g < F.fg_ptr[lev + 1]; ++g)
             if (!fwd_group(g)) return false;
+        if (mask)
+            for (size_t si = 0; si < F.sn.size(); ++si) {
+                const HSnode& s = F.sn[si];
+                if (s.large && s.height == lev && !(*mask->live)[si]) scaled_copy(s);
+            }
         for (int ti = F.uf_ptr[lev]; ti < F.uf_ptr[lev + 1]; ++ti) {
             const HTask& k = F.uft[ti];
+            if (mask && !(*mask->live)[k.s < 0 ? F.lr[-1 - k.s].s : k.s]) continue;
             if (k.s < 0) {
                 const HLr& G = F.lr[-1 - k.s];
                 const HSnode& s = F.sn[G.s];
@@ -139,6 +172,8 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             }
         }
     }
+    if (fwd_y) *fwd_y = y;
+    if (fwd_slots) *fwd_slots = inb;
     auto vrow = [&](const HSnode& s, int q) {
         return q < s.ni ? y[s.first + q] : -x[F.bidx[s.bidx_off + drow(s, q) - s.ni]];
     };
@@ -298,6 +333,43 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
     }
+    return BID_OK;
+}
+
+int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf, int block, int precision,
+                                 const double* b, double* x, int64_t* ndead) {
+    if (!h || !b || !x) return set_error(BID_EINVAL, "bad argument");
+    if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
+    if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
+    const AssembledHost& a = h->a;
+    for (int64_t i = a.NH; i < a.N; ++i)
+        if (b[i] != 0.0) return set_error(BID_EINVAL, "b must be zero outside the heart nodes");
+    HBuildOpts o;
+    o.eps = eps;
+    o.leaf = leaf;
+    o.block = block;
+    o.vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
+    HFactorHost F;
+    BID_TRY(build_hfactor(a.S1, a.coords.data(), a.dim, {(int32_t)(a.N - 1)}, o, &F));
+    std::vector<uint8_t> live;
+    cluster_liveness(F, (int32_t)a.NH, &live);
+    if (ndead) {
+        ndead[0] = (int64_t)std::count(live.begin(), live.end(), 0);
+        ndead[1] = (int64_t)live.size();
+    }
+    // all-ones forward results, then the solve with the dead clusters scaled
+    std::vector<double> ones(a.N, 1.0), xo(a.N), y1, y1slot;
+    if (!replay(F, ones.data(), 0.0, xo.data(), nullptr, nullptr, nullptr, &y1, &y1slot))
+        return set_error(BID_EINVAL, "flat group layout inconsistent");
+    double shift = 0.0;
+    for (int64_t i = 0; i < a.N; ++i) shift += b[i];
+    shift /= (double)a.N;
+    ReplayMask m;
+    m.live = &live;
+    m.y1 = y1.data();
+    m.y1slot = y1slot.data();
+    m.c = -shift;
+    if (!replay(F, b, shift, x, nullptr, nullptr, &m)) return set_error(BID_EINVAL, "flat group layout inconsistent");
     return BID_OK;
 }
 

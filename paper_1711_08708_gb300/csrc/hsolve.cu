@@ -262,6 +262,18 @@ struct HShift {
     const double* seg_inv_n = nullptr;
 };
 
+// Masked solve: a group or task with live[i] == 0 writes c times the
+// all-ones forward results (c = -shift) instead of computing; live NULL:
+// every group computes.
+struct MaskArgs {
+    const uint8_t* live = nullptr;
+    const double* csum = nullptr;    // c = -(*csum) * cinv
+    double cinv = 0.0;
+    const double* y1 = nullptr;      // all-ones forward results: ybuf ...
+    const double* y1slot = nullptr;  // ... and update slots
+};
+__device__ __forceinline__ double mask_c(const MaskArgs& mk) { return mk.csum ? -(*mk.csum) * mk.cinv : 0.0; }
+
 // xp[pos] = b[pidx[pos]] - shift, pinned entries 0
 __global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict__ pidx, int pin,
                                                 const uint8_t* __restrict__ pinflag,
@@ -359,12 +371,23 @@ __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, c
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* xp, double* ybuf, double* inb,
-                                                 unsigned int* err, int sc_off, int w_off) {
+                                                 unsigned int* err, int sc_off, int w_off, MaskArgs mk) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
     A* w = reinterpret_cast<A*>(dyn_smem + w_off);
     __shared__ __align__(8) uint64_t bar;
     const FGroup G = v.fg[g0 + blockIdx.x];
+    if (mk.live && !mk.live[g0 + blockIdx.x]) {   // constant input -c: scaled all-ones results
+        pdl_wait();
+        pdl_trigger();
+        const double c = mask_c(mk);
+        for (int f = threadIdx.x; f < G.wf; f += FT) ybuf[G.pstart + f] = c * mk.y1[G.pstart + f];
+        for (int k = threadIdx.x; k < G.nbt; k += FT) {
+            const int32_t slot = v.uout[G.bstart + k];
+            inb[slot] = c * mk.y1slot[slot];
+        }
+        return;
+    }
     const int nc = G.c1 - G.c0;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -805,7 +828,7 @@ template <typename T, typename A>
 __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ data, int task0,
                                                const double* xp, double* ybuf, double* inb,
                                                double* tbuf, double* pbuf,
-                                               unsigned int* tickets) {
+                                               unsigned int* tickets, MaskArgs mk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ A red[HT][VecOf<T>::N];
     __shared__ bool last;
@@ -814,6 +837,20 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
     const HSnode sn = up_fwd_node(v, t, g);
     pdl_wait();
     pdl_trigger();
+    if (mk.live && !mk.live[task0 + blockIdx.x]) {   // constant input -c: scaled all-ones results
+        if (t.s >= 0 && t.b0 != 0) return;            // the first column chunk writes the rows
+        const double c = mask_c(mk);
+        for (int q = t.a0 + (int)threadIdx.x; q < t.a1; q += HT) {
+            const int R = t.s < 0 ? g.row0 + q : dense_row(v, sn, q);
+            if (R < sn.ni) {
+                ybuf[sn.first + R] = c * mk.y1[sn.first + R];
+            } else {
+                const int32_t slot = v.uout[sn.u_off + R - sn.ni];
+                inb[slot] = c * mk.y1slot[slot];
+            }
+        }
+        return;
+    }
     up_fwd_task<T, A>(v, data, t, g, sn, xp, ybuf, inb, tbuf, pbuf, tickets, smem, red, last);
 }
 
@@ -1227,7 +1264,7 @@ int probe_upper() {
 
 template <typename T, typename A>
 int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh,
-        const HScratch& S, double* out) {
+        const HScratch& S, double* out, bool masked) {
     const HView v = view_of(F);
     const T* data = reinterpret_cast<const T*>(F.data);
     double* inb = S.inb ? S.inb : F.inb;
@@ -1239,6 +1276,15 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                               sh, S.xp));
     }
     const int H = (int)F.uf_ptr.size() - 1;
+    MaskArgs mf{}, mu{};
+    if (masked && F.ones_ready && hsolve_mask_enabled()) {
+        mf.csum = mu.csum = sh.sum;
+        mf.cinv = mu.cinv = sh.inv_n;
+        mf.y1 = mu.y1 = F.y1;
+        mf.y1slot = mu.y1slot = F.y1slot;
+        mf.live = F.fg_live;
+        mu.live = F.uf_live;
+    }
     // upper levels in one persistent launch per pass when possible
     const int lu = (g_upper_ok == 1 && F.sched && S.gbar && F.lev_upper < H) ? F.lev_upper : H;
     UpperSched us{};
@@ -1292,7 +1338,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             const int w_off = sc_off + F.fg_nc[lev] * (int)sizeof(GCl);
             const size_t sm = (size_t)w_off + sizeof(A) * F.fg_wf[lev];
             BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.xp, S.ybuf, inb,
-                                  S.err, sc_off, w_off));
+                                  S.err, sc_off, w_off, mf));
             ++launches;
         }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
@@ -1301,7 +1347,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             const size_t sm = sizeof(A) * (has_lr ? (((F.u_ni_max[lev] + 1) & ~1) + LR_KMAX + 2)
                                                   : (size_t)UP_COLS);
             BID_CUDA_TRY(launch_k(k_up_fwd<T, A>, nt, HT, sm, L.st, v, data, F.uf_ptr[lev], S.xp, S.ybuf,
-                                  inb, S.tbuf, S.pbuf, S.tickets));
+                                  inb, S.tbuf, S.pbuf, S.tickets, mu));
             ++launches;
         }
     }
@@ -1386,13 +1432,62 @@ int hsolve_prepare() {
 }
 
 static int dispatch(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh,
-                    const HScratch& S, double* out) {
+                    const HScratch& S, double* out, bool masked = false) {
     switch (F.precision) {
-        case BID_FP64: return run<double, double>(L, F, in, sh, S, out);
-        case BID_FP32: return run<float, float>(L, F, in, sh, S, out);
-        case BID_BF16: return run<__nv_bfloat16, float>(L, F, in, sh, S, out);
+        case BID_FP64: return run<double, double>(L, F, in, sh, S, out, masked);
+        case BID_FP32: return run<float, float>(L, F, in, sh, S, out, masked);
+        case BID_BF16: return run<__nv_bfloat16, float>(L, F, in, sh, S, out, masked);
         default: return set_error(BID_EINVAL, "bad factor precision");
     }
+}
+
+int launch_hsolve_masked(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
+                         double inv_n, const HScratch& S, double* out) {
+    HShift sh;
+    sh.sum = shift_sum;
+    sh.inv_n = inv_n;
+    return dispatch(L, F, in, sh, S, out, true);
+}
+
+// BID_MASK=0 in the environment: the masked solves compute every group
+bool hsolve_mask_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("BID_MASK");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    return on;
+}
+
+__global__ void k_fill(int64_t n, double v, double* x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S) {
+    F->ones_ready = false;
+    if (!F->fg_live || !F->uf_live || !F->y1 || !F->y1slot) return BID_OK;
+    double *ones = nullptr, *x = nullptr;
+    const int64_t n = std::max<int64_t>(F->n, 1);
+    if (cudaMalloc(&ones, sizeof(double) * n) != cudaSuccess || cudaMalloc(&x, sizeof(double) * n) != cudaSuccess) {
+        cudaFree(ones);
+        cudaGetLastError();
+        return set_error(BID_ENOMEM, "cudaMalloc failed");
+    }
+    int rc = BID_OK;
+    k_fill<<<L.sms * 4, 256, 0, L.st>>>(F->n, 1.0, ones);
+    count_launches(1);
+    rc = launch_hsolve(L, *F, ones, nullptr, 0.0, S, x);
+    const double* inb = S.inb ? S.inb : F->inb;
+    if (rc == BID_OK &&
+        (cudaMemcpyAsync(F->y1, S.ybuf, sizeof(double) * F->n, cudaMemcpyDeviceToDevice, L.st) != cudaSuccess ||
+         cudaMemcpyAsync(F->y1slot, inb, sizeof(double) * std::max<int64_t>(F->nslots, 1),
+                         cudaMemcpyDeviceToDevice, L.st) != cudaSuccess ||
+         cudaStreamSynchronize(L.st) != cudaSuccess))
+        rc = set_error(BID_ECUDA, "all-ones forward results: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(ones);
+    cudaFree(x);
+    if (rc == BID_OK) F->ones_ready = true;
+    return rc;
 }
 
 int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
@@ -1467,6 +1562,25 @@ static int upload_tree(const HFactorHost& h, int precision, HFactorDev* d) {
     d->tree_cta_b = cb;
     d->tree_lev0 = T.lev0;
     d->tree_lev1 = T.lev1;
+    return BID_OK;
+}
+
+int upload_liveness(const HFactorHost& h, int32_t nlive, HFactorDev* d) {
+    std::vector<uint8_t> live, fl(h.fg.size(), 0), ul(h.uft.size(), 0);
+    cluster_liveness(h, nlive, &live);
+    for (size_t g = 0; g < h.fg.size(); ++g)
+        for (int c = h.fg[g].c0; c < h.fg[g].c1; ++c) fl[g] |= live[h.gcl[c].s];
+    for (size_t k = 0; k < h.uft.size(); ++k) {
+        const HTask& t = h.uft[k];
+        ul[k] = live[t.s < 0 ? h.lr[-1 - t.s].s : t.s];
+    }
+    fl.push_back(1);   // never empty
+    ul.push_back(1);
+    BID_TRY(upload_vec(fl, &d->fg_live));
+    BID_TRY(upload_vec(ul, &d->uf_live));
+    BID_CUDA_TRY(cudaMalloc(&d->y1, sizeof(double) * std::max<int64_t>(h.n, 1)));
+    BID_CUDA_TRY(cudaMalloc(&d->y1slot, sizeof(double) * std::max<int64_t>(h.nslots, 1)));
+    d->ones_ready = false;
     return BID_OK;
 }
 
@@ -1574,7 +1688,7 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 void free_hfactor(HFactorDev* d) {
     void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout,  d->vgl, d->sn,
                     d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
-                    d->tree_idx, d->tree_state};
+                    d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

@@ -271,6 +271,14 @@ struct HFactorDev {
     unsigned int* tree_state = nullptr; // counters f (ntask) | b (ntask) | queue f (2) | queue b (2)
     int32_t tree_sc_off = 0, tree_w_off = 0, tree_smem_f = 0, tree_smem_b = 0;
     int32_t tree_cta_f = 0, tree_cta_b = 0;   // resident CTAs per SM
+    // masked solve (upload_liveness): live flags per flat group / upper forward
+    // task, and the forward results of the all-ones input (y1: ybuf, y1slot:
+    // update slots), filled by hsolve_ones
+    uint8_t* fg_live = nullptr;
+    uint8_t* uf_live = nullptr;
+    double* y1 = nullptr;
+    double* y1slot = nullptr;
+    bool ones_ready = false;
 };
 // Dataflow schedule of the flat groups of the levels [lev0, lev1): the groups
 // first .. first + ntask - 1 (tasks, numbered from 0 in group order = lower
@@ -298,7 +306,18 @@ struct TreeHost {
 };
 int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from, TreeHost* T);
 
+// Clusters whose subtree holds a pivot with vector index < nlive: their own
+// pivots, then upwards through the update slots (a child's boundary rows
+// write its parent's slots).  In a solve whose input is zero on every other
+// index, up to a constant shift c, every other cluster sees the constant
+// input -c alone, so its forward results are -c times those of the all-ones
+// input (masked solve).
+void cluster_liveness(const HFactorHost& F, int32_t nlive, std::vector<uint8_t>* live);
+
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
+// Flags of the masked solve (cluster_liveness with nlive) for the flat groups
+// and the upper forward tasks, and room for the all-ones forward results.
+int upload_liveness(const HFactorHost& h, int32_t nlive, HFactorDev* d);
 void free_hfactor(HFactorDev* d);
 
 // Scratch of one triangular solve (sized by the factor; reused by every solve).
@@ -382,6 +401,15 @@ int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in,
                   const double* shift_sum, double inv_n, const HScratch& S, double* out);
 // Same with one shift per segment (block-diagonal systems): input entry of
 // vector index i is b[i] - seg_sum[seg[i]] * seg_inv_n[seg[i]].
+// x = P^-1 (b - shift) for an input b that is zero outside the live clusters
+// (upload_liveness): the other clusters' forward results are scaled copies of
+// the all-ones results (needs hsolve_ones first).  Same result as
+// launch_hsolve up to rounding.
+int launch_hsolve_masked(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
+                         double inv_n, const HScratch& S, double* out);
+// the all-ones forward results of a factor with liveness flags (blocking)
+int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S);
+bool hsolve_mask_enabled();   // BID_MASK=0 in the environment: plain solves
 int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in,
                       const int16_t* seg, const double* seg_sum, const double* seg_inv_n,
                       const HScratch& S, double* out);

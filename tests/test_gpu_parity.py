@@ -366,3 +366,58 @@ def test_dataflow_levels_equal_level_launches(bid, tmp_path, variant):
     assert (l0 == 0).all()
     assert (l1[[0, 2, 4, 6]] >= 2).all()            # P_1 of every precision and the batch forest
     assert np.array_equal(x0, x1)
+
+
+_MASK_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_08708_gb300 import bid
+from workloads import torso_square_2d, params_2d
+from oracle import bidomain as ob
+p = params_2d(0.1)
+mesh = torso_square_2d(257)
+S = bid.System(mesh, p)
+o = ob.build_system(mesh, p)
+out = []
+for prec in ("fp64", "fp32", "bf16"):
+    P = bid.Precond(S, p["dt"], eps=1e-3, precision=prec, leaf=32)
+    rng = np.random.default_rng(3)
+    r = torch.tensor(rng.normal(size=S.N + S.NH), device="cuda")
+    z = torch.zeros_like(r)
+    P.apply(r, z)
+    Y = ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"])
+    X = torch.zeros(o.N + o.NH, dtype=torch.float64, device="cuda")
+    info = P.solve(torch.tensor(Y, device="cuda"), X, tol=1e-10)
+    out += [z.cpu().numpy(), X.cpu().numpy(), [info["iters"]]]
+np.save(sys.argv[2], np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in out]))
+"""
+
+
+def test_masked_second_solve_matches_full_solve(bid, tmp_path):
+    # the preconditioner's second P_1 solve takes the clusters without heart
+    # nodes as scaled all-ones results (default) or computes them (BID_MASK=0):
+    # the same P_Lambda^-1 r up to the factor's rounding, the same PCG
+    # iteration counts and solutions within the solve tolerance
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "s.py"
+    script.write_text(_MASK_SCRIPT)
+    res = {}
+    for name, extra in (("masked", {}), ("full", {"BID_MASK": "0"})):
+        f = tmp_path / f"x_{name}.npy"
+        env = {k: v for k, v in os.environ.items() if k != "BID_MASK"}
+        env.update(extra)
+        subprocess.run([sys.executable, str(script), root, str(f)], check=True, env=env, timeout=900)
+        res[name] = np.load(f)
+    n = 257 * 257
+    nh = (res["masked"].size // 3 - 1) // 2 - n
+    a, b = res["masked"], res["full"]
+    step = 2 * (n + nh) + 1
+    for k, tol in enumerate((1e-12, 1e-5, 1e-2)):   # fp64, fp32, bf16 factors
+        za, zb = a[k * step:k * step + n + nh], b[k * step:k * step + n + nh]
+        xa, xb = a[k * step + n + nh:k * step + 2 * (n + nh)], b[k * step + n + nh:k * step + 2 * (n + nh)]
+        assert np.abs(za - zb).max() <= tol * np.abs(zb).max()
+        assert np.linalg.norm(xa - xb) <= 1e-7 * np.linalg.norm(xb)
+        assert abs(a[(k + 1) * step - 1] - b[(k + 1) * step - 1]) <= 1

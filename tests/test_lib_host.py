@@ -125,6 +125,28 @@ def test_dataflow_schedule_is_complete(bid, n, leaf, precision, eps, cap, first)
     assert sch["levels"] == 0
 
 
+@pytest.mark.parametrize("n,leaf,precision,eps", [(129, 16, "fp64", 0.0), (161, 32, "fp32", 1e-3),
+                                                  (257, 32, "bf16", 1e-3)])
+def test_masked_solve_equals_full_replay(bid, n, leaf, precision, eps):
+    # P_1 applied to an input that is zero off the heart (the preconditioner's
+    # second P_1 solve): the clusters whose subtree holds no heart node see the
+    # constant -mean(b) alone and are replaced by scaled all-ones results;
+    # equal to the full replay up to rounding.  A cluster wrongly taken as
+    # dead (a live child missed) changes x at O(1).
+    m, p = torso_square_2d(n), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    o = ob.build_system(m, p)
+    b = np.zeros(o.N)
+    b[:o.NH] = np.random.default_rng(n).normal(size=o.NH)
+    x0, _ = hs.factor_solve(1, b, eps=eps, leaf=leaf, precision=precision)
+    x1, (dead, total) = hs.factor_solve_masked(b, eps=eps, leaf=leaf, precision=precision)
+    assert dead > total // 2
+    assert np.abs(x1 - x0).max() <= 1e-12 * np.abs(x0).max()
+    b[-5] = 1.0
+    with pytest.raises(bid.BidError):
+        hs.factor_solve_masked(b, eps=eps, leaf=leaf, precision=precision)
+
+
 def test_host_factor_3d_exact():
     import __graft_entry__
     __graft_entry__.build()
