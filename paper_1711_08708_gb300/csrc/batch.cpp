@@ -457,7 +457,8 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     bo.threads = o->n_threads;
     bo.vec = o->precision == BID_FP64 ? 2 : o->precision == BID_FP32 ? 4 : 8;
     bo.upper_levels = hsolve_upper_enabled();
-    if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knob
+    if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knobs
+    if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
     HFactorHost h1, hk;
     if (rc == BID_OK) rc = build_batch_factor(hosts, L, 1, B->gamma, bo, lf, &h1);
     if (rc == BID_OK) rc = build_batch_factor(hosts, L, 2, B->gamma, bo, lf, &hk);

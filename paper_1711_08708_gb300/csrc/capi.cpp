@@ -396,7 +396,8 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     bo.threads = o->n_threads;
     bo.vec = o->precision == BID_FP64 ? 2 : o->precision == BID_FP32 ? 4 : 8;
     bo.upper_levels = hsolve_upper_enabled();
-    if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knob
+    if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knobs
+    if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
     HFactorHost h1, hk;
     // P_1: S_1 with the last U unknown pinned (pseudo-inverse on 1^perp)
     BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, {(int32_t)(H.N - 1)}, bo, &h1));

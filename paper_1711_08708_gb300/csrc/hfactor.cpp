@@ -174,7 +174,8 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     if (o.block < 8 || o.block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o.leaf < 4 || o.leaf > 4096) return set_error(BID_EINVAL, "leaf must be in 4..4096");
     if (o.vec != 2 && o.vec != 4 && o.vec != 8) return set_error(BID_EINVAL, "vec must be 2, 4 or 8");
-    if (o.group_bytes < 1024 || o.group_bytes > 65536)
+    if (o.group_bytes < 1024 || o.group_bytes > 65536 ||
+        (o.group_bytes_leaf != 0 && (o.group_bytes_leaf < 1024 || o.group_bytes_leaf > 65536)))
         return set_error(BID_EINVAL, "group_bytes must be in 1024..65536");
     const int nthreads = o.threads > 0 ? o.threads : omp_get_max_threads();
     std::vector<int64_t> gptr = o.group_ptr;
@@ -639,7 +640,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     // (contiguous data) up to STAGE_CL clusters, STAGE_MAX staged values per
     // pass and GROUP_BYTES of data (a larger cluster forms a group alone)
     const int esz = vec == 2 ? 8 : vec == 4 ? 4 : 2;
-    auto make_groups = [&](const std::vector<int>& cl) {
+    auto make_groups = [&](const std::vector<int>& cl, int budget) {
         int32_t most = 0, most_nc = 0, most_wf = 0, most_wb = 0;
         FGroup g{};
         bool open = false, kids = false;
@@ -662,7 +663,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             const int units_f = (h.nd + vec - 1) / vec;
             if (open && (g.c1 - g.c0 == STAGE_CL || (int)F->gcl.size() - g.c0 == STAGE_CL ||
                          g.wf + h.ni > STAGE_MAX || g.wb + h.nd + vec > STAGE_MAX ||
-                         (blk_end[s] - g.dstart) * esz > o.group_bytes))
+                         (blk_end[s] - g.dstart) * esz > budget))
                 flush();
             if (!open) {
                 g = FGroup{};
@@ -725,7 +726,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             }
             h.lr_end = (int32_t)F->lr.size();
         }
-        make_groups(small);
+        make_groups(small, L == 0 && o.group_bytes_leaf > 0 ? o.group_bytes_leaf : o.group_bytes);
         F->fg_ptr.push_back((int32_t)F->fg.size());
         for (int s : bylev[L]) {
             const HSnode& h = F->sn[s];

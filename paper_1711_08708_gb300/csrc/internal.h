@@ -211,6 +211,7 @@ struct HBuildOpts {
     // upper-level path)
     bool upper_levels = false;
     int group_bytes = GROUP_BYTES_DEFAULT;   // factor bytes of a flat group (see FGroup)
+    int group_bytes_leaf = 0;                // the same for the leaf level (0: group_bytes)
 };
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  Every index in `pins` has its
