@@ -69,6 +69,10 @@ extern "C" int bid_apply_factor_noalloc(bid_precond* P, int which, const double*
     S.ybuf = base;
     S.xp = S.ybuf + F.n;
     S.inb = S.xp + F.n;
+    // the update slots are read as 16-byte pairs and bulk-copied (2n doubles
+    // after the 256-byte aligned base keep them on a 16-byte boundary)
+    if (reinterpret_cast<uintptr_t>(S.inb) % 16 != 0)
+        return set_error(BID_EINVAL, "scratch update slots not 16-byte aligned");
     S.vbuf = S.inb + F.nslots;
     S.tbuf = S.vbuf + F.vbuf_entries;
     S.pbuf = S.tbuf + F.tbuf_entries;
