@@ -46,11 +46,11 @@ sys.path.insert(0, ROOT)
 METRIC = "bidomain steps/s at PCG rel-res 1e-8 (chosen form); HBM GB/s of the factor solve"
 
 # DRAM bytes per algorithmic byte of one P_1 solve, from an ncu capture of the
-# same kernels at 1025^2 (profiles/p1_solve_dram_1025.md: 601.5 MB over
+# same kernels at 1025^2 (profiles/p1_solve_dram_1025.md: 601.6 MB over
 # 464.1 MB at leaf 32); the traffic grows with the factor, so the bench's
 # roofline reports this ratio times its own algorithmic bytes for the same
 # form (other forms: null, no capture of the current kernels).
-TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 601.5 / 464.06}
+TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 601.6 / 464.06}
 
 
 def parse():
