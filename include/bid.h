@@ -34,6 +34,21 @@
  *    kernels in the same order instead and reads the condition after every
  *    iteration: same results, for profilers that do not see kernels inside
  *    graphs with conditional nodes.
+ *  - Other switches, read once per process (defaults are the measured best):
+ *    BID_MASK=0      the preconditioner's second P_1 solve computes every
+ *                    cluster instead of taking the clusters without heart
+ *                    nodes from the all-ones forward results (equal up to
+ *                    rounding);
+ *    BID_PDL=0       the factor-solve kernels launch in plain stream order
+ *                    instead of with programmatic dependent launch;
+ *    BID_TREE=1      a range of flat levels runs in two dataflow launches per
+ *                    solve (BID_TREE_FROM first level, default 1;
+ *                    BID_TREE_SMEM shared-memory cap, default 32768);
+ *    BID_UPPER=1     the top levels run in persistent cooperative launches;
+ *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
+ *                    (1024..65536, default 12288), read at preconditioner build.
+ *    Results are the same with every setting (bit for bit except BID_MASK,
+ *    which changes rounding).
  */
 #ifndef BID_H
 #define BID_H
