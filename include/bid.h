@@ -47,8 +47,10 @@
  *    BID_UPPER=1     the top levels run in persistent cooperative launches;
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
- *    Results are the same with every setting (bit for bit except BID_MASK,
- *    which changes rounding).
+ *    Results are the same with every setting: bit for bit, except that the
+ *    masked solve's clusters computed in full (all of them with BID_MASK=0,
+ *    those of the levels that BID_TREE or BID_UPPER take over) round
+ *    differently.
  */
 #ifndef BID_H
 #define BID_H
