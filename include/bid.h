@@ -447,11 +447,13 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
  * given); other entries of x are left as they are.  b, x host arrays of the
  * combined length.  smem_cap, from and sched as for
  * bid_host_factor_solve_dataflow (smem_cap 0: level by level; sched may be
- * NULL).  stats may be NULL. */
+ * NULL).  masked != 0 (which = 1 only; b zero on every slice's torso nodes,
+ * EINVAL otherwise): replayed as the masked forest solve, as in
+ * bid_host_factor_solve_masked with each tree's own mean.  stats may be NULL. */
 int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, int which,
                                 double gamma, double eps, const int32_t* leaf, int leaf_default,
-                                int block, int precision, int smem_cap, int from, const double* b,
-                                double* x, bid_precond_stats* stats, int64_t* sched);
+                                int block, int precision, int smem_cap, int from, int masked,
+                                const double* b, double* x, bid_precond_stats* stats, int64_t* sched);
 void bid_host_destroy(bid_host_system* h);
 
 #ifdef __cplusplus

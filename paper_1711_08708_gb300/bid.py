@@ -107,7 +107,7 @@ SIGNATURES = {
     "bid_batch_destroy": (None, [_VP]),
     "bid_tune_leaf": (_I, [_VP, C.POINTER(PrecondOpts), _VP, _I, _I, _VP, _VP]),
     "bid_tune_batch_leaf": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, _I, _I, _VP]),
-    "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _I, _I, _VP, _VP,
+    "bid_host_batch_factor_solve": (_I, [_VP, _I, _I, _D, _D, _VP, _I, _I, _I, _I, _I, _I, _VP, _VP,
                                          C.POINTER(PrecondStats), _I64P]),
     "bid_cnn_nparams": (_I, []),
     "bid_cnn_create": (_I, [_I, C.c_uint64, C.POINTER(_VP)]),
@@ -542,12 +542,13 @@ def _schedule(sched):
 
 
 def host_batch_factor_solve(systems, which, b, gamma=0.0, eps=0.0, leaf=16, block=128,
-                            precision="fp64", smem_cap=0, first=1, schedule=False):
+                            precision="fp64", smem_cap=0, first=1, masked=False, schedule=False):
     """bid_host_batch_factor_solve over HostSystems (combined layout); the
     entries of the result outside the factor's block are zero.  smem_cap > 0
-    replays the flat levels from `first` on in the dataflow kernels' order; with
-    schedule=True the schedule (levels, groups, forward and backward
-    dependencies) is returned as a third value."""
+    replays the flat levels from `first` on in the dataflow kernels' order;
+    masked=True (which = 1, b zero on the torso nodes) replays the masked
+    forest solve; with schedule=True the schedule (levels, groups, forward and
+    backward dependencies) is returned as a third value."""
     S = len(systems)
     arr = (_VP * S)(*[s.h.value for s in systems])
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -558,7 +559,8 @@ def host_batch_factor_solve(systems, which, b, gamma=0.0, eps=0.0, leaf=16, bloc
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _check(lib.bid_host_batch_factor_solve(arr, S, int(which), float(gamma), float(eps), _ptr(lf),
                                            int(leaf) if lf is None else 16, int(block), prec,
-                                           int(smem_cap), int(first), _ptr(b), _ptr(x), C.byref(st),
+                                           int(smem_cap), int(first), int(bool(masked)), _ptr(b), _ptr(x),
+                                           C.byref(st),
                                            sched.ctypes.data_as(_I64P)))
     if schedule:
         return x, st.as_dict(), _schedule(sched)

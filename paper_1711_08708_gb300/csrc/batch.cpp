@@ -204,7 +204,8 @@ int bprecond(bid_batch* B, const Launch& L, const double* r, double* z) {
     BID_TRY(blaunch_si_residual(L, g, A, B->htasks(), r, z, B->t));
     BID_TRY(launch_hsolve(L, B->FK, B->t, nullptr, 0.0, B->hs, z));
     BID_TRY(blaunch_si_apply_sum(L, g, A, B->htasks(), z, B->w, B->sc, B->partials));
-    BID_TRY(launch_hsolve_seg(L, B->F1, B->w, B->seg, B->sc.sumb, B->d_invN, B->hs, B->z1b));
+    // W is zero outside the hearts: the masked solve
+    BID_TRY(launch_hsolve_seg_masked(L, B->F1, B->w, B->seg, B->sc.sumb, B->d_invN, B->hs, B->z1b));
     return blaunch_axpy_sub_u(L, g, B->vtasks(), z, B->z1b);
 }
 
@@ -509,6 +510,20 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
                   d + 6 * S, d + 7 * S, d + 8 * S, d + 9 * S, d + 10 * S, d + 11 * S,
                   B->iscal,  B->iscal + S, B->iscal + 2 * S, B->iscal + 3 * S, B->iscal + 4 * S,
                   B->tickets};
+    // the masked P_1 forest solve of the preconditioner's second P_1
+    // application: its input is zero outside every slice's heart nodes
+    // (U_s heart-first: combined indices off_s .. off_s + N_H,s)
+    if (hsolve_mask_enabled()) {
+        std::vector<uint8_t> vlive(n, 0);
+        for (int s = 0; s < S; ++s)
+            std::fill(vlive.begin() + L.off[s], vlive.begin() + L.off[s] + L.NH[s], (uint8_t)1);
+        rc = upload_liveness(h1, vlive, &B->F1);
+        if (rc == BID_OK) rc = hsolve_ones(blaunch(B, nullptr), &B->F1, B->hs, n);
+        if (rc != BID_OK) {
+            bid_batch_destroy(B);
+            return rc;
+        }
+    }
     bid_precond_stats& st = B->stats;
     st.n1 = h1.n;
     st.nk = hk.n;

@@ -447,8 +447,12 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
         rc = set_error(BID_ECUDA, "cudaMemset failed");
     // the masked P_1 solve of the preconditioner's second P_1 application: its
     // input is zero outside the heart nodes (vector indices < N_H)
-    if (rc == BID_OK && hsolve_mask_enabled()) rc = upload_liveness(h1, (int32_t)NH, &P->F1);
-    if (rc == BID_OK && hsolve_mask_enabled()) rc = hsolve_ones(launch_of(s, nullptr), &P->F1, P->hs);
+    if (rc == BID_OK && hsolve_mask_enabled()) {
+        std::vector<uint8_t> vlive(N, 0);
+        std::fill(vlive.begin(), vlive.begin() + NH, (uint8_t)1);
+        rc = upload_liveness(h1, vlive, &P->F1);
+    }
+    if (rc == BID_OK && hsolve_mask_enabled()) rc = hsolve_ones(launch_of(s, nullptr), &P->F1, P->hs, N);
     if (rc != BID_OK) {
         bid_destroy_precond(P);
         return rc;

@@ -813,7 +813,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     return BID_OK;
 }
 
-void cluster_liveness(const HFactorHost& F, int32_t nlive, std::vector<uint8_t>* live) {
+void cluster_liveness(const HFactorHost& F, const std::vector<uint8_t>& vlive, std::vector<uint8_t>* live) {
     const int nc = (int)F.sn.size();
     live->assign(nc, 0);
     std::vector<int32_t> owner(std::max<int64_t>(F.nslots, 1), -1), order(nc);
@@ -821,8 +821,10 @@ void cluster_liveness(const HFactorHost& F, int32_t nlive, std::vector<uint8_t>*
         const HSnode& h = F.sn[s];
         for (int64_t k = h.inc_off; k < h.inc_off + 2 * (int64_t)(h.ni + h.nb) && k < F.nslots; ++k)
             if (k >= 0) owner[k] = s;
-        for (int i = 0; i < h.ni; ++i)
-            if (F.pidx[h.first + i] < nlive) (*live)[s] = 1;
+        for (int i = 0; i < h.ni; ++i) {
+            const int32_t vi = F.pidx[h.first + i];
+            if (vi >= 0 && vi < (int64_t)vlive.size() && vlive[vi]) (*live)[s] = 1;
+        }
         order[s] = s;
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return F.sn[a].height < F.sn[b].height; });

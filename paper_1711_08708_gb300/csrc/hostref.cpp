@@ -36,6 +36,8 @@ struct ReplayMask {
     const double* y1 = nullptr;
     const double* y1slot = nullptr;
     double c = 0.0;
+    const std::vector<double>* vshift = nullptr;   // per vector index: c = -vshift[index]
+    double at(int32_t vi) const { return vshift ? -(*vshift)[vi] : c; }
 };
 bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             const std::vector<double>* vshift = nullptr, const TreeHost* T = nullptr,
@@ -43,10 +45,10 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             std::vector<double>* fwd_slots = nullptr) {
     std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
     auto scaled_copy = [&](const HSnode& s) {   // a dead cluster's forward results
-        for (int i = 0; i < s.ni; ++i) y[s.first + i] = mask->c * mask->y1[s.first + i];
+        for (int i = 0; i < s.ni; ++i) y[s.first + i] = mask->at(F.pidx[s.first + i]) * mask->y1[s.first + i];
         for (int r = 0; r < s.nb; ++r) {
             const int32_t slot = F.uout[s.u_off + r];
-            inb[slot] = mask->c * mask->y1slot[slot];
+            inb[slot] = mask->at(F.bidx[s.bidx_off + r]) * mask->y1slot[slot];
         }
     };
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
@@ -351,8 +353,9 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
     o.vec = precision == BID_FP64 ? 2 : precision == BID_FP32 ? 4 : 8;
     HFactorHost F;
     BID_TRY(build_hfactor(a.S1, a.coords.data(), a.dim, {(int32_t)(a.N - 1)}, o, &F));
-    std::vector<uint8_t> live;
-    cluster_liveness(F, (int32_t)a.NH, &live);
+    std::vector<uint8_t> live, vlive(a.N, 0);
+    std::fill(vlive.begin(), vlive.begin() + a.NH, (uint8_t)1);
+    cluster_liveness(F, vlive, &live);
     if (ndead) {
         ndead[0] = (int64_t)std::count(live.begin(), live.end(), 0);
         ndead[1] = (int64_t)live.size();
@@ -375,8 +378,8 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
 
 int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, int which,
                                 double gamma, double eps, const int32_t* leaf, int leaf_default,
-                                int block, int precision, int smem_cap, int from, const double* b,
-                                double* x, bid_precond_stats* stats, int64_t* sched) {
+                                int block, int precision, int smem_cap, int from, int masked,
+                                const double* b, double* x, bid_precond_stats* stats, int64_t* sched) {
     if (!hs || nslices < 1 || !b || !x || (which != 1 && which != 2))
         return set_error(BID_EINVAL, "bad argument");
     if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
@@ -420,7 +423,27 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         sched[3] = (int64_t)T.succ_f.size();
         sched[4] = (int64_t)T.succ_b.size();
     }
-    if (!replay(F, b, 0.0, x, &vshift, smem_cap > 0 ? &T : nullptr))
+    ReplayMask m;
+    std::vector<uint8_t> live;
+    std::vector<double> y1, y1slot;
+    if (masked) {   // which = 1, b zero outside the hearts: the masked forest solve
+        if (which != 1) return set_error(BID_EINVAL, "the masked solve is the P_1 solve (which = 1)");
+        std::vector<uint8_t> vlive(lay.off[nslices], 0);
+        for (int s = 0; s < nslices; ++s) {
+            for (int64_t i = lay.NH[s]; i < lay.N[s]; ++i)
+                if (b[lay.off[s] + i] != 0.0) return set_error(BID_EINVAL, "b must be zero outside the hearts");
+            std::fill(vlive.begin() + lay.off[s], vlive.begin() + lay.off[s] + lay.NH[s], (uint8_t)1);
+        }
+        cluster_liveness(F, vlive, &live);
+        std::vector<double> ones(lay.off[nslices], 1.0), xo(lay.off[nslices], 0.0);
+        if (!replay(F, ones.data(), 0.0, xo.data(), nullptr, nullptr, nullptr, &y1, &y1slot))
+            return set_error(BID_EINVAL, "flat group layout inconsistent");
+        m.live = &live;
+        m.y1 = y1.data();
+        m.y1slot = y1slot.data();
+        m.vshift = &vshift;
+    }
+    if (!replay(F, b, 0.0, x, &vshift, smem_cap > 0 ? &T : nullptr, masked ? &m : nullptr))
         return set_error(BID_EINVAL, "flat group layout or dataflow schedule inconsistent");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));

@@ -267,12 +267,22 @@ struct HShift {
 // every group computes.
 struct MaskArgs {
     const uint8_t* live = nullptr;
-    const double* csum = nullptr;    // c = -(*csum) * cinv
+    const double* csum = nullptr;    // c = -(*csum) * cinv ...
     double cinv = 0.0;
+    const int16_t* seg = nullptr;    // ... or per segment (a forest's trees): c(vi) =
+    const double* seg_sum = nullptr;  //   -seg_sum[seg[vi]] * seg_inv_n[seg[vi]]
+    const double* seg_inv_n = nullptr;
     const double* y1 = nullptr;      // all-ones forward results: ybuf ...
     const double* y1slot = nullptr;  // ... and update slots
 };
-__device__ __forceinline__ double mask_c(const MaskArgs& mk) { return mk.csum ? -(*mk.csum) * mk.cinv : 0.0; }
+// c for a row whose node (a pivot, or a boundary node of the same tree) has
+// vector index vi; c0 = the scalar c when there are no segments
+__device__ __forceinline__ double mask_c0(const MaskArgs& mk) { return mk.csum ? -(*mk.csum) * mk.cinv : 0.0; }
+__device__ __forceinline__ double mask_c(const MaskArgs& mk, double c0, int vi) {
+    if (!mk.seg) return c0;
+    const int g = mk.seg[vi];
+    return -mk.seg_sum[g] * mk.seg_inv_n[g];
+}
 
 // xp[pos] = b[pidx[pos]] - shift, pinned entries 0
 __global__ void __launch_bounds__(HT) k_permute(int n, const int32_t* __restrict__ pidx, int pin,
@@ -380,11 +390,12 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
     if (mk.live && !mk.live[g0 + blockIdx.x]) {   // constant input -c: scaled all-ones results
         pdl_wait();
         pdl_trigger();
-        const double c = mask_c(mk);
-        for (int f = threadIdx.x; f < G.wf; f += FT) ybuf[G.pstart + f] = c * mk.y1[G.pstart + f];
+        const double c0 = mask_c0(mk);
+        for (int f = threadIdx.x; f < G.wf; f += FT)
+            ybuf[G.pstart + f] = mask_c(mk, c0, mk.seg ? v.pidx[G.pstart + f] : 0) * mk.y1[G.pstart + f];
         for (int k = threadIdx.x; k < G.nbt; k += FT) {
             const int32_t slot = v.uout[G.bstart + k];
-            inb[slot] = c * mk.y1slot[slot];
+            inb[slot] = mask_c(mk, c0, mk.seg ? v.bidx[G.bstart + k] : 0) * mk.y1slot[slot];
         }
         return;
     }
@@ -839,13 +850,15 @@ __global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ da
     pdl_trigger();
     if (mk.live && !mk.live[task0 + blockIdx.x]) {   // constant input -c: scaled all-ones results
         if (t.s >= 0 && t.b0 != 0) return;            // the first column chunk writes the rows
-        const double c = mask_c(mk);
+        const double c0 = mask_c0(mk);
         for (int q = t.a0 + (int)threadIdx.x; q < t.a1; q += HT) {
             const int R = t.s < 0 ? g.row0 + q : dense_row(v, sn, q);
             if (R < sn.ni) {
+                const double c = mask_c(mk, c0, mk.seg ? v.pidx[sn.first + R] : 0);
                 ybuf[sn.first + R] = c * mk.y1[sn.first + R];
             } else {
                 const int32_t slot = v.uout[sn.u_off + R - sn.ni];
+                const double c = mask_c(mk, c0, mk.seg ? v.bidx[sn.bidx_off + R - sn.ni] : 0);
                 inb[slot] = c * mk.y1slot[slot];
             }
         }
@@ -1280,6 +1293,9 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
     if (masked && F.ones_ready && hsolve_mask_enabled()) {
         mf.csum = mu.csum = sh.sum;
         mf.cinv = mu.cinv = sh.inv_n;
+        mf.seg = mu.seg = sh.seg;
+        mf.seg_sum = mu.seg_sum = sh.seg_sum;
+        mf.seg_inv_n = mu.seg_inv_n = sh.seg_inv_n;
         mf.y1 = mu.y1 = F.y1;
         mf.y1slot = mu.y1slot = F.y1slot;
         mf.live = F.fg_live;
@@ -1449,6 +1465,15 @@ int launch_hsolve_masked(const Launch& L, const HFactorDev& F, const double* in,
     return dispatch(L, F, in, sh, S, out, true);
 }
 
+int launch_hsolve_seg_masked(const Launch& L, const HFactorDev& F, const double* in, const int16_t* seg,
+                             const double* seg_sum, const double* seg_inv_n, const HScratch& S, double* out) {
+    HShift sh;
+    sh.seg = seg;
+    sh.seg_sum = seg_sum;
+    sh.seg_inv_n = seg_inv_n;
+    return dispatch(L, F, in, sh, S, out, true);
+}
+
 // BID_MASK=0 in the environment: the masked solves compute every group
 bool hsolve_mask_enabled() {
     static const bool on = [] {
@@ -1463,18 +1488,19 @@ __global__ void k_fill(int64_t n, double v, double* x) {
         x[i] = v;
 }
 
-int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S) {
+int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S, int64_t vn) {
     F->ones_ready = false;
     if (!F->fg_live || !F->uf_live || !F->y1 || !F->y1slot) return BID_OK;
+    if (vn < F->n) return set_error(BID_EINVAL, "vector length below the factor size");
     double *ones = nullptr, *x = nullptr;
-    const int64_t n = std::max<int64_t>(F->n, 1);
+    const int64_t n = std::max<int64_t>(vn, 1);
     if (cudaMalloc(&ones, sizeof(double) * n) != cudaSuccess || cudaMalloc(&x, sizeof(double) * n) != cudaSuccess) {
         cudaFree(ones);
         cudaGetLastError();
         return set_error(BID_ENOMEM, "cudaMalloc failed");
     }
     int rc = BID_OK;
-    k_fill<<<L.sms * 4, 256, 0, L.st>>>(F->n, 1.0, ones);
+    k_fill<<<L.sms * 4, 256, 0, L.st>>>(n, 1.0, ones);
     count_launches(1);
     rc = launch_hsolve(L, *F, ones, nullptr, 0.0, S, x);
     const double* inb = S.inb ? S.inb : F->inb;
@@ -1565,9 +1591,9 @@ static int upload_tree(const HFactorHost& h, int precision, HFactorDev* d) {
     return BID_OK;
 }
 
-int upload_liveness(const HFactorHost& h, int32_t nlive, HFactorDev* d) {
+int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFactorDev* d) {
     std::vector<uint8_t> live, fl(h.fg.size(), 0), ul(h.uft.size(), 0);
-    cluster_liveness(h, nlive, &live);
+    cluster_liveness(h, vlive, &live);
     for (size_t g = 0; g < h.fg.size(); ++g)
         for (int c = h.fg[g].c0; c < h.fg[g].c1; ++c) fl[g] |= live[h.gcl[c].s];
     for (size_t k = 0; k < h.uft.size(); ++k) {

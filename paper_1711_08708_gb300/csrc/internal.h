@@ -307,18 +307,19 @@ struct TreeHost {
 };
 int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from, TreeHost* T);
 
-// Clusters whose subtree holds a pivot with vector index < nlive: their own
-// pivots, then upwards through the update slots (a child's boundary rows
-// write its parent's slots).  In a solve whose input is zero on every other
-// index, up to a constant shift c, every other cluster sees the constant
+// Clusters whose subtree holds a pivot with a live vector index
+// (vlive[index] != 0; indices beyond vlive are dead): their own pivots, then
+// upwards through the update slots (a child's boundary rows write its
+// parent's slots).  In a solve whose input is zero on every other index, up
+// to a shift c constant on each tree, every other cluster sees the constant
 // input -c alone, so its forward results are -c times those of the all-ones
 // input (masked solve).
-void cluster_liveness(const HFactorHost& F, int32_t nlive, std::vector<uint8_t>* live);
+void cluster_liveness(const HFactorHost& F, const std::vector<uint8_t>& vlive, std::vector<uint8_t>* live);
 
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
-// Flags of the masked solve (cluster_liveness with nlive) for the flat groups
+// Flags of the masked solve (cluster_liveness with vlive) for the flat groups
 // and the upper forward tasks, and room for the all-ones forward results.
-int upload_liveness(const HFactorHost& h, int32_t nlive, HFactorDev* d);
+int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFactorDev* d);
 void free_hfactor(HFactorDev* d);
 
 // Scratch of one triangular solve (sized by the factor; reused by every solve).
@@ -408,8 +409,12 @@ int launch_hsolve(const Launch& L, const HFactorDev& F, const double* in,
 // launch_hsolve up to rounding.
 int launch_hsolve_masked(const Launch& L, const HFactorDev& F, const double* in, const double* shift_sum,
                          double inv_n, const HScratch& S, double* out);
-// the all-ones forward results of a factor with liveness flags (blocking)
-int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S);
+// the all-ones forward results of a factor with liveness flags (blocking);
+// vn: length of the vectors the factor's indices point into
+int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S, int64_t vn);
+// launch_hsolve_masked with one shift per segment (the batched forests)
+int launch_hsolve_seg_masked(const Launch& L, const HFactorDev& F, const double* in, const int16_t* seg,
+                             const double* seg_sum, const double* seg_inv_n, const HScratch& S, double* out);
 bool hsolve_mask_enabled();   // BID_MASK=0 in the environment: plain solves
 int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in,
                       const int16_t* seg, const double* seg_sum, const double* seg_inv_n,

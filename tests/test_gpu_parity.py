@@ -378,7 +378,7 @@ p = params_2d(0.1)
 mesh = torso_square_2d(257)
 S = bid.System(mesh, p)
 o = ob.build_system(mesh, p)
-out = []
+out = {}
 for prec in ("fp64", "fp32", "bf16"):
     P = bid.Precond(S, p["dt"], eps=1e-3, precision=prec, leaf=32)
     rng = np.random.default_rng(3)
@@ -388,8 +388,21 @@ for prec in ("fp64", "fp32", "bf16"):
     Y = ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"])
     X = torch.zeros(o.N + o.NH, dtype=torch.float64, device="cuda")
     info = P.solve(torch.tensor(Y, device="cuda"), X, tol=1e-10)
-    out += [z.cpu().numpy(), X.cpu().numpy(), [info["iters"]]]
-np.save(sys.argv[2], np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in out]))
+    out[prec + "_z"], out[prec + "_x"], out[prec + "_it"] = z.cpu().numpy(), X.cpu().numpy(), info["iters"]
+S2 = bid.System(torso_square_2d(193, semi_axes=(2.0, 3.0)), p)
+B = bid.Batch([S, S2], p["dt"], eps=1e-3, precision="fp32", leaf=32)
+rng = np.random.default_rng(4)
+rb = torch.tensor(rng.normal(size=B.n), device="cuda")
+zb = torch.zeros_like(rb)
+B.apply_precond(rb, zb)
+Yb = np.zeros(B.n)
+Yb[:o.N + o.NH] = ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"])
+Yb[o.N + o.NH + S2.N:] = 10.0 * S2.mH
+Xb = torch.zeros(B.n, dtype=torch.float64, device="cuda")
+binfo, _ = B.solve(torch.tensor(Yb, device="cuda"), Xb, tol=1e-10)
+out["batch_z"], out["batch_x"] = zb.cpu().numpy(), Xb.cpu().numpy()
+out["batch_it"] = np.array([i["iters"] for i in binfo])
+np.savez(sys.argv[2], **out)
 """
 
 
@@ -397,7 +410,8 @@ def test_masked_second_solve_matches_full_solve(bid, tmp_path):
     # the preconditioner's second P_1 solve takes the clusters without heart
     # nodes as scaled all-ones results (default) or computes them (BID_MASK=0):
     # the same P_Lambda^-1 r up to the factor's rounding, the same PCG
-    # iteration counts and solutions within the solve tolerance
+    # iteration counts and solutions within the solve tolerance, for one slice
+    # (each factor precision) and for a two-slice batch (each tree its own shift)
     import os
     import subprocess
     import sys
@@ -406,18 +420,14 @@ def test_masked_second_solve_matches_full_solve(bid, tmp_path):
     script.write_text(_MASK_SCRIPT)
     res = {}
     for name, extra in (("masked", {}), ("full", {"BID_MASK": "0"})):
-        f = tmp_path / f"x_{name}.npy"
+        f = tmp_path / f"x_{name}.npz"
         env = {k: v for k, v in os.environ.items() if k != "BID_MASK"}
         env.update(extra)
         subprocess.run([sys.executable, str(script), root, str(f)], check=True, env=env, timeout=900)
-        res[name] = np.load(f)
-    n = 257 * 257
-    nh = (res["masked"].size // 3 - 1) // 2 - n
+        res[name] = dict(np.load(f))
     a, b = res["masked"], res["full"]
-    step = 2 * (n + nh) + 1
-    for k, tol in enumerate((1e-12, 1e-5, 1e-2)):   # fp64, fp32, bf16 factors
-        za, zb = a[k * step:k * step + n + nh], b[k * step:k * step + n + nh]
-        xa, xb = a[k * step + n + nh:k * step + 2 * (n + nh)], b[k * step + n + nh:k * step + 2 * (n + nh)]
-        assert np.abs(za - zb).max() <= tol * np.abs(zb).max()
-        assert np.linalg.norm(xa - xb) <= 1e-7 * np.linalg.norm(xb)
-        assert abs(a[(k + 1) * step - 1] - b[(k + 1) * step - 1]) <= 1
+    for key, tol in (("fp64", 1e-12), ("fp32", 1e-5), ("bf16", 1e-2), ("batch", 1e-5)):
+        za, zb = a[key + "_z"], b[key + "_z"]
+        assert np.abs(za - zb).max() <= tol * np.abs(zb).max(), key
+        assert np.linalg.norm(a[key + "_x"] - b[key + "_x"]) <= 1e-7 * np.linalg.norm(b[key + "_x"]), key
+        assert np.abs(np.asarray(a[key + "_it"]) - np.asarray(b[key + "_it"])).max() <= 1, key

@@ -281,6 +281,29 @@ def test_host_batch_dataflow_schedule_is_complete(bid, precision, cap, first):
         assert np.array_equal(x0, x1)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_host_batch_masked_solve_equals_full_replay(bid, precision):
+    # the batched preconditioner's second P_1 forest solve: input zero on
+    # every slice's torso nodes, each tree shifted by its own mean; the dead
+    # clusters take their tree's scaled all-ones results
+    sl = _slices(3, 5, 6, 10, 16)
+    hs = [bid.HostSystem(m, p) for m, p in sl]
+    ss = [ob.build_system(m, p) for m, p in sl]
+    off = np.cumsum([0] + [s.N + s.NH for s in ss])
+    rng = np.random.default_rng(21)
+    b = np.zeros(off[-1])
+    for k, s in enumerate(ss):
+        b[off[k]:off[k] + s.NH] = rng.normal(size=s.NH)
+    kw = dict(eps=1e-3, leaf=[32, 16, 32], precision=precision)
+    x0, _ = bid.host_batch_factor_solve(hs, 1, b, **kw)
+    x1, _ = bid.host_batch_factor_solve(hs, 1, b, masked=True, **kw)
+    assert np.abs(x1 - x0).max() <= 1e-12 * np.abs(x0).max()
+    b2 = b.copy()
+    b2[off[1] + ss[1].N - 1] = 1.0                   # a torso node of slice 1
+    with pytest.raises(bid.BidError):
+        bid.host_batch_factor_solve(hs, 1, b2, masked=True, **kw)
+
+
 def test_host_batch_factor_errors(bid):
     sl = _slices(2, 3, 3, 4, 8)
     hs = [bid.HostSystem(m, p) for m, p in sl]
