@@ -161,6 +161,35 @@ def test_host_factor_3d_exact():
     assert np.abs(x - xo).max() <= 1e-11 * np.abs(xo).max()
 
 
+@pytest.mark.parametrize("precision,eps,first", [("fp64", 0.0, 1), ("fp32", 1e-2, 0), ("bf16", 1e-2, 2)])
+def test_3d_dataflow_schedule_and_masked_solve(bid, precision, eps, first):
+    # 3D slab (isolated heart: every node is a heart node, deeper separators,
+    # low-rank groups at eps > 0): the dataflow order equals the level order bit
+    # for bit, and the masked replay has no dead cluster and equals the full one
+    m, p = slab_3d(17, 17, 7), params_3d(0.05)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    assert s.NH == s.N
+    b = np.random.default_rng(31).normal(size=s.N)
+    x0, _ = hs.factor_solve(1, b, eps=eps, leaf=16, precision=precision)
+    x1, _, sch = hs.factor_solve_dataflow(1, b, smem_cap=65536, first=first, eps=eps, leaf=16,
+                                          precision=precision)
+    assert sch["levels"] >= 2 and sch["deps_fwd"] > 0
+    assert np.array_equal(x0, x1)
+    x2, (dead, total) = hs.factor_solve_masked(b, eps=eps, leaf=16, precision=precision)
+    assert dead == 0 and total > 10
+    assert np.array_equal(x0, x2)
+
+
+def test_masked_solve_without_heart_input(bid):
+    # b = 0 everywhere: mean 0, every result zero, on either path
+    m, p = torso_square_2d(65), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    s = ob.build_system(m, p)
+    x, (dead, total) = hs.factor_solve_masked(np.zeros(s.N), eps=1e-3, leaf=16, precision="fp32")
+    assert not x.any() and 0 < dead < total
+
+
 def test_host_factor_truncation_error_tracks_eps(bid):
     m, p = torso_square_2d(257), params_2d(0.1)
     hs = bid.HostSystem(m, p)
