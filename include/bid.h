@@ -170,8 +170,14 @@ void bid_precond_opts_default(bid_precond_opts* o);
  * BID_ECUDA. */
 int bid_precond_build(bid_system* s, double dt, double eps, int precision,
                       bid_precond** out);
+/* The same with every option (leaf size, low-rank block rows, host threads);
+ * defaults from bid_precond_opts_default.  The build also takes the all-ones
+ * forward results of P_1 used by the masked second P_1 solve (one extra solve,
+ * skipped with BID_MASK=0). */
 int bid_precond_build_ex(bid_system* s, const bid_precond_opts* opts,
                          bid_precond** out);
+/* Factor statistics of P (host struct, filled at build; no device work).
+ * Errors: BID_EINVAL (NULL argument). */
 int bid_precond_get_stats(const bid_precond* P, bid_precond_stats* st);
 
 /* y = Lambda(gamma) x (eq. system); x, y device, N + N_H each, distinct. */
@@ -391,6 +397,7 @@ int bid_guess_configure(bid_guess* G, int use_dv, int policy);
 int bid_step_learned(bid_system* s, bid_precond* P, bid_guess* G, double* U, double* V, double* h,
                      const double* Ist, double t0, int n_steps, double tol, int max_iter,
                      double* stats, void* stream);
+/* Frees the guess's device buffers (not the network it was created with). */
 void bid_guess_destroy(bid_guess* G);
 
 /* ---------------------------------------------------------------------------
@@ -454,6 +461,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
                                 double gamma, double eps, const int32_t* leaf, int leaf_default,
                                 int block, int precision, int smem_cap, int from, int masked,
                                 const double* b, double* x, bid_precond_stats* stats, int64_t* sched);
+/* Frees a host system (NULL is ignored). */
 void bid_host_destroy(bid_host_system* h);
 
 #ifdef __cplusplus
