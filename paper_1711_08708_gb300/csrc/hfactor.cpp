@@ -419,6 +419,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         // rank-revealing QR reaches eps with k (m + ni) <= m ni / 2
         std::vector<char> in_lr(nb, 0);
         if (eps > 0.0 && h.large && ni >= 16) {
+            std::vector<std::pair<int, int>> runs;   // candidate groups [j, e), in row order
             int j = 0;
             while (j < nb) {
                 int a = parent[s];
@@ -427,28 +428,36 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
                     a = parent[a];
                 int e = j + 1;
                 while (e < nb && e - j < lrows && w.B[e] < F->sn[a].first + F->sn[a].ni) ++e;
-                const int m = e - j;
-                if (m >= 16) {
-                    const int kmax = std::min(LR_KMAX, (m * ni) / (2 * (m + ni)));
-                    std::vector<double> Ub, Vt;
-                    int k = dense::rrqr(m, ni, &M[(size_t)(ni + j) * ni], ni, eps, kmax, Ub, Vt);
-                    if (k >= 0) {
-                        HLr g{};
-                        g.s = s;
-                        g.row0 = ni + j;
-                        g.m = m;
-                        g.k = k;
-                        g.off_u = (int64_t)w.data.size();
-                        w.data.insert(w.data.end(), Ub.begin(), Ub.end());
-                        g.off_v = (int64_t)w.data.size();
-                        for (int c = 0; c < ni; ++c)          // V = Vt^T, row-major ni x k
-                            for (int l = 0; l < k; ++l) w.data.push_back(Vt[(size_t)l * ni + c]);
-                        w.lr.push_back(g);
-                        w.lr_e += (int64_t)k * (m + ni);
-                        for (int r = j; r < e; ++r) in_lr[r] = 1;
-                    }
-                }
+                if (e - j >= 16) runs.push_back({j, e});
                 j = e;
+            }
+            // the groups' truncated QRs are independent: computed side by side,
+            // then appended in row order
+            std::vector<std::vector<double>> Us(runs.size()), Vts(runs.size());
+            std::vector<int> ks(runs.size(), -1);
+#pragma omp parallel for schedule(dynamic, 1) if (par && runs.size() > 1)
+            for (size_t r = 0; r < runs.size(); ++r) {
+                const int j0 = runs[r].first, m = runs[r].second - j0;
+                const int kmax = std::min(LR_KMAX, (m * ni) / (2 * (m + ni)));
+                ks[r] = dense::rrqr(m, ni, &M[(size_t)(ni + j0) * ni], ni, eps, kmax, Us[r], Vts[r]);
+            }
+            for (size_t r = 0; r < runs.size(); ++r) {
+                const int k = ks[r];
+                if (k < 0) continue;
+                const int j0 = runs[r].first, e = runs[r].second, m = e - j0;
+                HLr g{};
+                g.s = s;
+                g.row0 = ni + j0;
+                g.m = m;
+                g.k = k;
+                g.off_u = (int64_t)w.data.size();
+                w.data.insert(w.data.end(), Us[r].begin(), Us[r].end());
+                g.off_v = (int64_t)w.data.size();
+                for (int c = 0; c < ni; ++c)          // V = Vt^T, row-major ni x k
+                    for (int l = 0; l < k; ++l) w.data.push_back(Vts[r][(size_t)l * ni + c]);
+                w.lr.push_back(g);
+                w.lr_e += (int64_t)k * (m + ni);
+                for (int q = j0; q < e; ++q) in_lr[q] = 1;
             }
         }
         // packed dense columns over the dense rows
@@ -503,14 +512,43 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         }
     }
     fail = pfail.load();
-    if (!fail)
-        for (int s : upper) {   // ascending post-order = children first
-            int bad = factor_one(s, true);
-            if (bad) {
-                fail = bad;
-                break;
+    // clusters above the cut, deepest first (children before parents); the
+    // clusters of one depth are independent, so they run side by side, each
+    // with an equal share of the threads for its dense kernels (the `par`
+    // flag splits loops without changing any summation order, so the factors
+    // do not depend on this schedule)
+    if (!fail && !upper.empty()) {
+        int dmax = 0;
+        for (int s : upper) dmax = std::max(dmax, depth[s]);
+        std::vector<std::vector<int>> bydepth(dmax + 1);
+        for (int s : upper) bydepth[depth[s]].push_back(s);
+        const int levels_before = omp_get_max_active_levels();
+        omp_set_max_active_levels(2);
+        for (int d = dmax; d >= 0 && !fail; --d) {
+            const std::vector<int>& cl = bydepth[d];
+            const int conc = std::min((int)cl.size(), nthreads_eff);
+            if (conc <= 1) {
+                for (int s : cl) {
+                    int bad = factor_one(s, true);
+                    if (bad) {
+                        fail = bad;
+                        break;
+                    }
+                }
+                continue;
             }
+            const int inner = std::max(1, nthreads_eff / conc);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(conc)
+            for (size_t i = 0; i < cl.size(); ++i) {
+                if (pfail.load() != 0) continue;
+                omp_set_num_threads(inner);
+                int bad = factor_one(cl[i], inner > 1);
+                if (bad) pfail.store(bad);
+            }
+            fail = pfail.load();
         }
+        omp_set_max_active_levels(levels_before);
+    }
     if (fail) return set_error(BID_EINVAL, "factorisation: non-positive pivot (matrix not SPD)");
 
     // with o.upper_levels, every cluster from the lowest tree level holding a
