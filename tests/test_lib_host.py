@@ -38,6 +38,19 @@ def test_exports_every_declared_symbol(bid):
         assert n in bid.SIGNATURES, n
 
 
+def test_binding_arity_matches_header(bid):
+    # every prototype's parameter count equals the binding's argument list
+    src = open(os.path.join(ROOT, "include", "bid.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = {}
+    for m in re.finditer(r"\b(bid_\w+)\s*\(([^;{]*?)\)\s*;", src):
+        params = m.group(2).strip()
+        decls[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    assert len(decls) >= 50
+    for name, n in decls.items():
+        assert len(bid.SIGNATURES[name][1]) == n, name
+
+
 def test_library_is_the_in_tree_build(bid):
     assert os.path.dirname(bid.LIB_PATH) == os.path.join(ROOT, "paper_1711_08708_gb300")
 
