@@ -212,7 +212,12 @@ int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void
  * calls and keeps the last call's contents (the tickets it needs at zero are
  * cleared on each call), so calls that overlap on the GPU -- on different
  * streams, or from different threads -- race: serialise them.  Device
- * pointers, stream semantics and which / b / x as for bid_apply_factor. */
+ * pointers, stream semantics and which / b / x as for bid_apply_factor; as
+ * there, an expired bounded device wait is recorded in P's error word (built
+ * with P, so nothing is allocated) and reported as BID_ETIMEOUT by the next
+ * bid_solve / bid_step on P.  The cached address belongs to the device's
+ * current context: after a device reset (which also invalidates every handle
+ * of this library) do not call this entry point again in the process. */
 int bid_apply_factor_noalloc(bid_precond* P, int which, const double* b, double* x,
                              void* stream);
 

@@ -57,7 +57,7 @@ extern "C" int bid_apply_factor_noalloc(bid_precond* P, int which, const double*
     const int64_t red = (int64_t)P->sys->sms * 8 + 2;      // block partials + sum + ticket
     const int64_t tick = (F.ntickets + 2) / 2;              // tickets packed two per double
     const int64_t need = 2 * F.n + F.nslots + F.vbuf_entries + F.tbuf_entries + F.pbuf_entries +
-                         tick + red + 2;   // + error word, grid barrier
+                         tick + red + 1;   // + grid barrier
     if (need > (int64_t)NOALLOC_DOUBLES)
         return set_error(BID_EINVAL,
                          "factor needs %lld scratch values; the static scratch holds %lld "
@@ -80,14 +80,17 @@ extern "C" int bid_apply_factor_noalloc(bid_precond* P, int which, const double*
     double* partials = S.pbuf + F.pbuf_entries + tick;
     double* sum = partials + (red - 2);
     unsigned int* sum_ticket = reinterpret_cast<unsigned int*>(sum + 1);
-    S.err = reinterpret_cast<unsigned int*>(sum + 2);
-    S.gbar = reinterpret_cast<unsigned int*>(sum + 3);
+    // an expired bounded wait is recorded in the preconditioner's own error
+    // word (allocated at build), which the next bid_solve / bid_step reports as
+    // BID_ETIMEOUT, exactly as after bid_apply_factor
+    S.err = &P->sc->herr;
+    S.gbar = reinterpret_cast<unsigned int*>(sum + 2);
     cudaStream_t st = (cudaStream_t)stream;
     // tickets must start at zero; the array keeps whatever the last call left
     BID_CUDA_TRY(cudaMemsetAsync(S.tickets, 0, sizeof(double) * tick, st));
     // update slots that no child writes must read as zero
     BID_CUDA_TRY(cudaMemsetAsync(S.inb, 0, sizeof(double) * F.nslots, st));
-    BID_CUDA_TRY(cudaMemsetAsync(sum_ticket, 0, 3 * sizeof(double), st));   // ticket, error word, barrier
+    BID_CUDA_TRY(cudaMemsetAsync(sum_ticket, 0, 2 * sizeof(double), st));   // ticket, grid barrier
     Launch L;
     L.sms = P->sys->sms;
     L.st = st;
