@@ -46,10 +46,10 @@ sys.path.insert(0, ROOT)
 METRIC = "bidomain steps/s at PCG rel-res 1e-8 (chosen form); HBM GB/s of the factor solve"
 
 # DRAM bytes per algorithmic byte of one P_1 solve, from an ncu capture of the
-# same kernels at 1025^2 (profiles/p1_solve_dram_1025.md: 601.6 MB over
-# 464.1 MB at leaf 32); the traffic grows with the factor, so the bench's
-# roofline reports this ratio times its own algorithmic bytes for the same
-# form (other forms: null, no capture of the current kernels).
+# same kernels on the 1025^2 slice (601.6 MB of DRAM traffic for 464.1 MB of
+# algorithmic bytes at eps 1e-3, FP32, leaf 32); the traffic grows with the
+# factor, so the bench's roofline reports this ratio times its own algorithmic
+# bytes for the same form (other forms: null, no capture of the current kernels).
 TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 601.6 / 464.06}
 
 
@@ -67,6 +67,8 @@ def parse():
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
+    a.add_argument("--no-cpu-full", action="store_true",
+                   help="skip the whole-step oracle timings at 65^2 and 513^2")
     a.add_argument("--workload", default="slice", choices=["slice", "batched", "slab3d", "learned"])
     a.add_argument("--train-runs", type=int, default=3)
     a.add_argument("--train-steps", type=int, default=60)
@@ -189,20 +191,71 @@ def cpu_baseline(n, budget_s, seed=0, kind="slice"):
     t0 = time.perf_counter()
     ob.solve_cg(s, g, Y, X0, tol=1e-30, max_iter=5)
     t_cal = (time.perf_counter() - t0) / 5
-    K = int(max(10, min(2000, budget_s / max(t_cal, 1e-6))))
+    K = int(max(10, min(20000, budget_s / max(t_cal, 1e-6))))
     t0 = time.perf_counter()
-    X, it = ob.solve_cg(s, g, Y, X0, tol=1e-30, max_iter=K)
+    X, it = ob.solve_cg(s, g, Y, X0, tol=1e-8, max_iter=K)
     t_iter = (time.perf_counter() - t0) / max(it, 1)
     L = ob.system_matrix(s, g)
     rel = float(np.linalg.norm(L @ X - Y) / np.linalg.norm(Y))
-    k_need = it * math.log(1e-8) / math.log(rel) if 0 < rel < 1 else float("nan")
-    step_s = t_rhs + t_iter * k_need
     cores = len(os.sched_getaffinity(0))
+    if it < K:      # converged inside the budget: a whole step, measured
+        step_s = t_rhs + t_iter * it
+        how = (f"the whole first step, measured: Step 1+3 ({t_rhs:.2f} s) and {it} iterations "
+               f"of the oracle's plain projected CG to rel-res 1e-8 ({t_iter * 1e3:.2f} ms each)")
+    else:
+        k_need = it * math.log(1e-8) / math.log(rel) if 0 < rel < 1 else float("nan")
+        step_s = t_rhs + t_iter * k_need
+        how = (f"first step of the workload: Step 1+3 ({t_rhs:.2f} s) and {it} iterations of the "
+               f"oracle's plain projected CG ({t_iter * 1e3:.1f} ms each, relres {rel:.2e}); "
+               f"{k_need:.0f} iterations to 1e-8 extrapolated at the measured rate (optimistic: "
+               "CG slows in its tail, see measured_full_steps for whole steps)")
     return {"value": 1.0 / step_s, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"first step of the workload: Step 1+3 ({t_rhs:.2f} s) and {it} "
-                      f"iterations of the oracle's plain projected CG ({t_iter * 1e3:.1f} ms "
-                      f"each, relres {rel:.2e}); {k_need:.0f} iterations to 1e-8 extrapolated "
-                      f"at the measured rate; numpy/scipy threads on {cores} cores"}
+            "sample": how + f"; numpy/scipy threads on {cores} cores (its sparse products run on one)"}
+
+
+_ORACLE_RUN = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import bidomain as ob
+from workloads import torso_square_2d, params_2d, stimulus_left_apex, stimulus_seeded_disc
+n, steps, dt, solver = int(sys.argv[2]), int(sys.argv[3]), float(sys.argv[4]), sys.argv[5]
+mesh, p = torso_square_2d(n), params_2d(dt)
+s = ob.build_system(mesh, p)
+stim = stimulus_left_apex(mesh) if n == 65 else stimulus_seeded_disc(mesh, seed=0)
+ist = ob.heart_stimulus(s, stim)
+U, V, h = ob.initial_state(s)
+t0 = time.perf_counter()
+for k in range(steps):
+    U, V, h = ob.time_step(s, U, V, h, ist, k * dt, dt, solver=solver, tol=1e-8)
+el = time.perf_counter() - t0
+print(json.dumps({"seconds": el, "steps": steps}))
+"""
+
+
+def oracle_full_steps(n, steps, dt, solver, threads):
+    """Whole oracle time steps (Step 1, Step 2 by `solver` to rel-res 1e-8 where
+    it iterates, Step 3), timed in a child process whose numerical libraries use
+    `threads` threads.  Returns steps/s and the seconds taken."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, "-c", _ORACLE_RUN, ROOT, str(n), str(steps), str(dt), solver],
+                         env=env, capture_output=True, text=True, timeout=900, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"steps_per_s": r["steps"] / r["seconds"], "seconds": r["seconds"], "steps": r["steps"],
+            "threads": threads}
+
+
+def oracle_measured(cores):
+    """Whole oracle steps, not extrapolated: the 65^2 slice of 20 steps of
+    0.25 ms with the corner stimulus (plain CG and sparse direct Step 2, one
+    thread and all cores), and one 0.1 ms step of the 513^2 slice (plain CG)."""
+    return {
+        "slice65_20steps_cg": [oracle_full_steps(65, 20, 0.25, "cg", t) for t in (1, cores)],
+        "slice65_20steps_direct": [oracle_full_steps(65, 20, 0.25, "direct", t) for t in (1, cores)],
+        "slice513_1step_cg": oracle_full_steps(513, 1, 0.1, "cg", cores),
+    }
 
 
 def run_reference(args):
@@ -210,6 +263,8 @@ def run_reference(args):
     if rank != 0:
         return
     cb = cpu_baseline(args.n, args.cpu_seconds, kind=args.workload)
+    if args.workload == "slice" and not args.no_cpu_full:
+        cb["measured_full_steps"] = oracle_measured(cb["cores"])
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
@@ -521,6 +576,33 @@ def run_learned(args):
     print(json.dumps(line))
 
 
+def class_bytes(stats, N, NH, nnz1, nnzi):
+    """Algorithmic bytes of one launch of each kernel class of bid_profile_classes
+    (FP64 values, int32 columns, each matrix entry and vector entry moved once)."""
+    n = N + NH
+    return {
+        "lambda": 12 * (nnz1 + nnzi) + 16 * N + 24 * NH,          # S_1, S_i; x read, q written, m_H
+        "p1_solve": stats["alg_bytes_p1"] + 32 * N,              # factor twice; input, y, x vectors
+        "p1_masked": stats["alg_bytes_p1_masked"] + 32 * N,
+        "pk_solve": stats["alg_bytes_pk"] + 32 * NH,
+        "si_chain": 24 * nnzi + 48 * NH + 24 * N,               # two S_i products, z_U -= P_1^-1 W
+        "pcg_vectors": 96 * n,                                   # <r,z>, p update, x and r updates
+        "residual": 12 * (nnz1 + nnzi) + 24 * N + 32 * NH + 16 * n,   # Y - Lambda x, projection
+        "rhs_gate": 8 * N + 40 * NH,                             # Y_U = 0; V, h, m_H in, h, Y_V out
+        "normalise": 32 * N,
+    }
+
+
+def step_bytes(cb, iters):
+    """Algorithmic bytes of one time step with `iters` PCG iterations: per
+    iteration a preconditioner application (two P_1 solves, one masked, a P_K
+    solve, the S_i chain), a Lambda product and the vector kernels; per step the
+    initial and the final residual, Step 1 + Step 3 and the normalisation."""
+    it = (cb["p1_solve"] + cb["p1_masked"] + cb["pk_solve"] + cb["si_chain"] + cb["lambda"] +
+          cb["pcg_vectors"])
+    return iters * it + 2 * cb["residual"] + cb["rhs_gate"] + cb["normalise"]
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -557,7 +639,9 @@ def main():
     I = torch.tensor(ist_h, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream()
 
-    def time_form(P, label):
+    def time_form(P):
+        """W warm-up steps from the initial state, then K timed steps; the state
+        at the start of the timed region is kept for the end-to-end replay."""
         U, V, h = state()
         t = 0.0
         iters = []
@@ -565,6 +649,7 @@ def main():
             iters += list(P.step(U, V, h, I, t, 1, tol=args.tol))
             t += p["dt"]
         torch.cuda.synchronize()
+        snap = (U.cpu(), V.cpu(), h.cpu(), t)
         if dist:
             dist.barrier()
         it0 = len(iters)
@@ -583,21 +668,48 @@ def main():
             tt = torch.tensor([ms], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             ms = float(tt.item())
-        return dict(ms=ms, iters=iters[it0:], launches=launches, clocks=ck.summary(), U=U, V=V, h=h)
+        return dict(ms=ms, iters=iters[it0:], launches=launches, clocks=ck.summary(), U=U, V=V, h=h,
+                    snap=snap)
 
     # ---- chosen form
     P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf)
     chosen_stats = dict(P.stats)
-    chosen = time_form(P, "chosen")
+    chosen = time_form(P)
 
-    # ---- roofline of the dominant kernel family: the P_1 triangular pair
-    # (k_hfwd + k_hbwd over all tree levels), timed alone with CUDA events
+    # ---- e2e through the public API with host buffers: the same K steps from
+    # the same state and time as the timed region, the state copied from and to
+    # pinned host memory every step
+    hU, hV, hh = (a.pin_memory() for a in chosen["snap"][:3])
+    t = chosen["snap"][3]
+    U0, V0, h0 = state()
+    e2e_iters = []
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        U0.copy_(hU, non_blocking=True)
+        V0.copy_(hV, non_blocking=True)
+        h0.copy_(hh, non_blocking=True)
+        e2e_iters += list(P.step(U0, V0, h0, I, t, 1, tol=args.tol))
+        hU.copy_(U0, non_blocking=True)
+        hV.copy_(V0, non_blocking=True)
+        hh.copy_(h0, non_blocking=True)
+        t += p["dt"]
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    io_bytes = 8 * (N + 2 * NH)
+    Uc, Vc = chosen["U"].cpu().numpy(), chosen["V"].cpu().numpy()
+    e2e_same = bool(np.array_equal(hU.numpy(), Uc) and np.array_equal(hV.numpy(), Vc))
+
+    # ---- roofline of the dominant kernel family: the P_1 solve (forward and
+    # backward passes over all tree levels), timed alone with CUDA events on the
+    # stream it is launched on
     b = torch.randn(N, dtype=torch.float64, device=dev)
     x = torch.empty_like(b)
     for _ in range(3):
         P.apply_factor(1, b, x)
     reps = 10
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(reps):
         P.apply_factor(1, b, x)
@@ -609,80 +721,96 @@ def main():
     # algorithmic bytes of one P_1 application: the factor read twice (stored
     # bytes_p1 already counts both passes) + input gather, y and x vectors
     alg_bytes = P.stats["alg_bytes_p1"] + 8 * 4 * N
-    achieved = alg_bytes / (solve_ms * 1e-3) / 1e9
 
-    # ---- e2e through the public API with host buffers
-    U0, V0, h0 = state()
-    hU = torch.zeros(N, dtype=torch.float64).pin_memory()
-    hV = torch.full((NH,), p["v_rest"], dtype=torch.float64).pin_memory()
-    hh = torch.ones(NH, dtype=torch.float64).pin_memory()
-    t = args.warmup * p["dt"]
-    torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        U0.copy_(hU, non_blocking=True)
-        V0.copy_(hV, non_blocking=True)
-        h0.copy_(hh, non_blocking=True)
-        P.step(U0, V0, h0, I, t, 1, tol=args.tol)
-        hU.copy_(U0, non_blocking=True)
-        hV.copy_(V0, non_blocking=True)
-        hh.copy_(h0, non_blocking=True)
-        t += p["dt"]
-    e1.record(st)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    io_bytes = 8 * (N + 2 * NH)
+    # ---- every kernel class of a step, each timed alone (library CUDA events on
+    # this stream), and the whole step against its algorithmic bytes
+    cls_ms = P.profile_classes(reps=10, stream=st.cuda_stream)
+    cb = class_bytes(chosen_stats, N, NH, S.nnz_s1, S.nnz_si)
+    mean_it = float(np.mean(chosen["iters"]))
+    ms_step = chosen["ms"] / args.steps
+    classes = {k: {"ms": cls_ms[k], "algorithmic_bytes": cb[k],
+                   "achieved_gbs": cb[k] / (cls_ms[k] * 1e-3) / 1e9,
+                   "frac": cb[k] / (cls_ms[k] * 1e-3) / 1e9 / hbm} for k in cb}
+    sb = step_bytes(cb, mean_it)
+    per_step_ms = {k: v * (mean_it if k in ("lambda", "p1_solve", "p1_masked", "pk_solve", "si_chain",
+                                            "pcg_vectors") else 2 if k == "residual" else 1)
+                   for k, v in cls_ms.items()}
+    whole_step = {"algorithmic_bytes": sb, "ms": ms_step, "achieved_gbs": sb / (ms_step * 1e-3) / 1e9,
+                  "frac": sb / (ms_step * 1e-3) / 1e9 / hbm,
+                  "classes_ms_sum": sum(per_step_ms.values()),
+                  "note": "bytes per step at the mean PCG iterations; classes_ms_sum adds the "
+                          "classes' standalone times in the same proportions (the rest of the "
+                          "step is launch gaps, host reads and the state copies of bid_step)"}
+    del P
+    torch.cuda.empty_cache()
 
-    # ---- plain form on the same GPU
+    # ---- plain form on the same GPU, the same steps from the same state
     plain = None
     if not args.no_plain:
-        del P
-        torch.cuda.empty_cache()
-        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64")
-        plain = time_form(Pp, "plain")
+        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64", leaf=args.leaf)
+        plain = time_form(Pp)
         plain_stats = Pp.stats
         del Pp
+        Up, Vp = plain["U"].cpu().numpy(), plain["V"].cpu().numpy()
+        err_vs_plain = {"U": float(np.abs(Uc - Up).max() / np.abs(Up).max()),
+                        "V": float(np.abs(Vc - Vp).max() / np.abs(Vp).max()),
+                        "h": float(np.abs(chosen["h"].cpu().numpy() - plain["h"].cpu().numpy()).max()),
+                        "note": f"after {args.warmup + args.steps} steps, max |chosen - plain| over "
+                                "each block / max |plain| (h: absolute); both forms stop at rel-res "
+                                f"{args.tol:g}, so this is the solve tolerance times the "
+                                "conditioning, not the factor precision"}
 
-    ms_step = chosen["ms"] / args.steps
     value = world * args.steps / (chosen["ms"] * 1e-3)
+    traffic_ratio = TRAFFIC_PER_ALG_BYTE.get((args.eps, args.precision, args.leaf))
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f64 PCG / {args.precision} factors" + (f" (eps {args.eps:g})" if args.eps else ""),
         "data": "synthetic",
         "config": {
             "workload": workload_name(args, N, NH),
             "form": {"eps": args.eps, "factor_precision": args.precision, "leaf": args.leaf},
-            "mean_pcg_iters": float(np.mean(chosen["iters"])),
+            "mean_pcg_iters": mean_it,
             "l2": "inputs larger than L2 (factor + matrices several GB)",
             "parallelism": f"replicas{world}" if world > 1 else "single GPU",
             "precond_stats": {k: chosen_stats[k] for k in (
-                "factor_bytes", "bytes_p1", "bytes_pk", "levels1", "levelsk", "dense_entries",
-                "lowrank_entries", "build_seconds")},
+                "factor_bytes", "bytes_p1", "bytes_pk", "alg_bytes_p1", "alg_bytes_p1_masked",
+                "alg_bytes_pk", "levels1", "levelsk", "large_levels1", "large_levelsk",
+                "masked_dead1", "masked_clusters1", "dense_entries", "lowrank_entries",
+                "lowrank_blocks", "build_seconds")},
             "plain": None if plain is None else {
                 "steps_per_s": world * args.steps / (plain["ms"] * 1e-3),
                 "mean_pcg_iters": float(np.mean(plain["iters"])),
                 "factor_bytes": plain_stats["factor_bytes"],
+                "build_seconds": plain_stats["build_seconds"],
+                "dtype": "f64 PCG / fp64 factors (exact)",
             },
+            "chosen_error_vs_plain": None if plain is None else err_vs_plain,
         },
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm,
-                     "traffic": (TRAFFIC_PER_ALG_BYTE[(args.eps, args.precision, args.leaf)] * alg_bytes
-                                 if args.workload == "slice" and
-                                 (args.eps, args.precision, args.leaf) in TRAFFIC_PER_ALG_BYTE else None),
-                     "traffic_note": "ncu DRAM bytes of the same kernels at 1025^2 scaled by the "
-                                     "algorithmic bytes (profiles/p1_solve_dram_1025.md)",
+        "roofline": {"bound": "hbm", "achieved": alg_bytes / (solve_ms * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": alg_bytes / (solve_ms * 1e-3) / 1e9 / hbm,
+                     "traffic": (traffic_ratio * alg_bytes if args.workload == "slice" and traffic_ratio
+                                 else None),
+                     "traffic_note": "ncu DRAM bytes of the same kernels on the 1025^2 slice, scaled "
+                                     "by the algorithmic bytes",
                      "kernel": "P_1 solve: k_permute, k_flat_fwd, k_up_fwd, k_bwd_prep, "
                                "k_up_bwd, k_flat_bwd over all tree levels",
                      "ms": solve_ms, "algorithmic_bytes": alg_bytes,
-                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+                     "classes": classes, "whole_step": whole_step},
         "e2e": {"value": world / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": io_bytes,
-                "d2h_bytes_per_step": io_bytes},
+                "d2h_bytes_per_step": io_bytes, "mean_pcg_iters": float(np.mean(e2e_iters)),
+                "same_steps_as_timed": e2e_same,
+                "note": "the timed region's K steps replayed from its starting state and time, "
+                        "U, V, h copied from and to pinned host memory every step"},
         "gpu_launches": chosen["launches"],
         "clocks": chosen["clocks"],
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds, kind=args.workload)
+        if args.workload == "slice" and not args.no_cpu_full:
+            line["cpu_baseline"]["measured_full_steps"] = oracle_measured(line["cpu_baseline"]["cores"])
     if rank == 0:
         print(json.dumps(line))
     if dist:

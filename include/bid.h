@@ -132,6 +132,14 @@ typedef struct bid_precond_stats {
                                           default; BID_TREE=1 in the environment turns
                                           them on) */
     int32_t dataflow_first1, dataflow_firstk;    /* the first of those levels */
+    int32_t large_levels1, large_levelsk;  /* tree levels holding large clusters (solved
+                                          by the chunked large-cluster kernels) */
+    int64_t masked_dead1, masked_clusters1;  /* clusters of P_1 whose forward results the
+                                          masked second P_1 solve takes from the all-ones
+                                          solve, and all clusters (0, 0 with BID_MASK=0) */
+    int64_t alg_bytes_p1_masked;       /* algorithmic bytes of one masked P_1 solve: the
+                                          forward blocks of the live clusters and the whole
+                                          backward pass (alg_bytes_p1 with BID_MASK=0) */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {
@@ -220,6 +228,27 @@ int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void
  * of this library) do not call this entry point again in the process. */
 int bid_apply_factor_noalloc(bid_precond* P, int which, const double* b, double* x,
                              void* stream);
+
+/* Kernel classes of one PCG time step, each timed alone with CUDA events on
+ * `stream` (one warm-up launch, then `reps` launches back to back; ms[c] is
+ * the mean milliseconds of one launch of class c).  The classes, in the order
+ * of ms (BID_PROFILE_CLASSES entries):
+ *   0 Lambda product (eq. system), fused <p, q> and sum(q_U);
+ *   1 P_1 solve (forward and backward passes of the S_1 factor);
+ *   2 masked P_1 solve (the preconditioner's second P_1 application, eq. prec2);
+ *   3 P_K solve (the K_m factor);
+ *   4 the S_i products and the update of the block-LU chain (eq. prec2);
+ *   5 PCG vector kernels of one iteration (<r, z>, p update, x and r updates
+ *     with the projection, convergence test);
+ *   6 residual Y - Lambda X with the projection (start and end of a solve);
+ *   7 Step 1 + Step 3 (right-hand side and gate update);
+ *   8 normalisation (proof of Prop. 1).
+ * The call overwrites P's work vectors and scalars (inputs are a fixed finite
+ * pattern), so it must not run while a solve on P is in flight; the next
+ * bid_solve / bid_step starts afresh.  Blocking.  Errors: BID_EINVAL (NULL P
+ * or ms, reps < 1), BID_ECUDA. */
+#define BID_PROFILE_CLASSES 9
+int bid_profile_classes(bid_precond* P, int reps, double* ms, void* stream);
 
 /* Step 2 (eq. system): PCG on Lambda from the guess in X, stopping when the
  * recurrence residual ||r||_2/||Y||_2 < tol (Sec. 6.2); the true residual is

@@ -54,7 +54,9 @@ class PrecondStats(C.Structure):
                 ("lowrank_blocks", C.c_int64), ("dense_blocks", C.c_int64),
                 ("build_seconds", C.c_double), ("dataflow_levels1", C.c_int32),
                 ("dataflow_levelsk", C.c_int32), ("dataflow_first1", C.c_int32),
-                ("dataflow_firstk", C.c_int32)]
+                ("dataflow_firstk", C.c_int32), ("large_levels1", C.c_int32),
+                ("large_levelsk", C.c_int32), ("masked_dead1", C.c_int64),
+                ("masked_clusters1", C.c_int64), ("alg_bytes_p1_masked", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -81,6 +83,7 @@ SIGNATURES = {
     "bid_apply_precond": (_I, [_VP, _VP, _VP, _VP]),
     "bid_apply_factor": (_I, [_VP, _I, _VP, _VP, _VP]),
     "bid_apply_factor_noalloc": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "bid_profile_classes": (_I, [_VP, _I, _VP, _VP]),
     "bid_solve": (_I, [_VP, _VP, _VP, _VP, _D, _I, C.POINTER(SolveInfo), _VP]),
     "bid_step": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _D, _I, _D, _I, _VP, _VP]),
     "bid_rhs_gate": (_I, [_VP, _VP, _VP, _VP, _I, _VP, _VP]),
@@ -278,6 +281,16 @@ class Precond:
                             float(t0), int(n_steps), float(tol), int(max_iter), _ptr(iters),
                             _stream(stream)))
         return iters[:n_steps]
+
+    PROFILE_CLASSES = ("lambda", "p1_solve", "p1_masked", "pk_solve", "si_chain", "pcg_vectors",
+                       "residual", "rhs_gate", "normalise")
+
+    def profile_classes(self, reps=10, stream=None):
+        """bid_profile_classes: mean ms of one launch of each kernel class
+        (overwrites the work vectors; blocking)."""
+        ms = np.zeros(len(self.PROFILE_CLASSES))
+        _check(lib.bid_profile_classes(self.h, int(reps), _ptr(ms), _stream(stream)))
+        return dict(zip(self.PROFILE_CLASSES, ms.tolist()))
 
     def rhs_gate(self, V, h, Ist, stim_on, Y, stream=None):
         _check(lib.bid_rhs_gate(self.h, _ptr(V), _ptr(h), _ptr(Ist), int(bool(stim_on)), _ptr(Y),

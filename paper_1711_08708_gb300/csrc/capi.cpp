@@ -447,10 +447,24 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
         rc = set_error(BID_ECUDA, "cudaMemset failed");
     // the masked P_1 solve of the preconditioner's second P_1 application: its
     // input is zero outside the heart nodes (vector indices < N_H)
+    int64_t masked_dead = 0, masked_fwd_entries = 0;
     if (rc == BID_OK && hsolve_mask_enabled()) {
         std::vector<uint8_t> vlive(N, 0);
         std::fill(vlive.begin(), vlive.begin() + NH, (uint8_t)1);
         rc = upload_liveness(h1, vlive, &P->F1);
+        // what the masked solve streams in its forward pass: live clusters only
+        std::vector<uint8_t> live;
+        cluster_liveness(h1, vlive, &live);
+        for (size_t c = 0; c < h1.sn.size(); ++c) {
+            if (!live[c]) {
+                ++masked_dead;
+                continue;
+            }
+            const HSnode& sn = h1.sn[c];
+            masked_fwd_entries += col_offset(sn.nd, sn.ni);
+            for (int g = sn.lr_begin; g < sn.lr_end; ++g)
+                masked_fwd_entries += (int64_t)h1.lr[g].k * (h1.lr[g].m + sn.ni);
+        }
     }
     if (rc == BID_OK && hsolve_mask_enabled()) rc = hsolve_ones(launch_of(s, nullptr), &P->F1, P->hs, N);
     if (rc != BID_OK) {
@@ -477,6 +491,21 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.alg_bytes_p1 = P->F1.alg_bytes_pass;
     st.alg_bytes_pk = P->FK.alg_bytes_pass;
     st.factor_bytes = 2 * st.alg_bytes_p1 + st.alg_bytes_pk;   // one P_Lambda^-1: 2 P_1 + 1 P_K
+    auto large_levels = [](const HFactorHost& h) {
+        int32_t c = 0;
+        for (size_t L = 0; L + 1 < h.vg_ptr.size(); ++L) c += h.vg_ptr[L + 1] > h.vg_ptr[L];
+        return c;
+    };
+    st.large_levels1 = large_levels(h1);
+    st.large_levelsk = large_levels(hk);
+    if (hsolve_mask_enabled()) {
+        const int esz = o->precision == BID_FP64 ? 8 : o->precision == BID_FP32 ? 4 : 2;
+        st.masked_dead1 = masked_dead;
+        st.masked_clusters1 = (int64_t)h1.sn.size();
+        st.alg_bytes_p1_masked = st.alg_bytes_p1 / 2 + masked_fwd_entries * esz;
+    } else {
+        st.alg_bytes_p1_masked = st.alg_bytes_p1;
+    }
     st.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = P;
     return BID_OK;
@@ -544,6 +573,83 @@ int bid_normalise(bid_precond* P, double* X, void* stream) {
     if (!P || !X) return set_error(BID_EINVAL, "bad argument");
     bid_system* s = P->sys;
     return launch_normalise(launch_of(s, stream), s->host.N, X, s->m, s->msum, P->sc, P->partials);
+}
+
+int bid_profile_classes(bid_precond* P, int reps, double* ms, void* stream) {
+    if (!P || !ms || reps < 1) return set_error(BID_EINVAL, "bad argument");
+    bid_system* s = P->sys;
+    const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
+    const double invN = 1.0 / (double)N;
+    const int flexible = P->opts.precision != BID_FP64;
+    cudaStream_t st = (cudaStream_t)stream;
+    Launch L = launch_of(s, stream);
+    // finite work vectors (byte pattern 0x3F: about 4.8e-4 in every entry);
+    // the masked solve's input keeps its zero torso part
+    for (double* v : {P->r, P->z, P->p, P->q, P->xs, P->ytmp})
+        BID_CUDA_TRY(cudaMemsetAsync(v, 0x3F, sizeof(double) * n, st));
+    BID_CUDA_TRY(cudaMemsetAsync(P->z1b, 0x3F, sizeof(double) * N, st));
+    BID_CUDA_TRY(cudaMemsetAsync(P->t, 0x3F, sizeof(double) * NH, st));
+    BID_CUDA_TRY(cudaMemsetAsync(P->w, 0x3F, sizeof(double) * NH, st));
+    // finite PCG scalars: residual, <r, z>, <p, Lambda p>
+    BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp, P->sc,
+                          P->partials));
+    BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+    BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, 1, P->sc, P->partials));
+    BID_TRY(launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc,
+                          P->partials));
+    cudaEvent_t e0, e1;
+    BID_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(BID_ECUDA, "cudaEventCreate failed");
+    }
+    auto run = [&](int cls) -> int {
+        switch (cls) {
+        case 0:
+            return launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc,
+                                 P->partials);
+        case 1:
+            return launch_hsolve(L, P->F1, P->r, &P->sc->sumr, invN, P->hs, P->z);
+        case 2:
+            return launch_hsolve_masked(L, P->F1, P->w, &P->sc->sum_b, invN, P->hs, P->z1b);
+        case 3:
+            return launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->hs, P->z + N);
+        case 4:
+            BID_TRY(launch_si_residual(L, NH, s->Si, P->r + N, P->z, P->t));
+            BID_TRY(launch_si_apply_sum(L, N, NH, s->Si, P->z + N, P->w, P->sc, P->partials));
+            return launch_axpy_sub(L, N, P->z, P->z1b);
+        case 5:
+            BID_TRY(launch_dot_rz(L, n, N, P->r, P->z, P->q, flexible, 0, P->sc, P->partials));
+            BID_TRY(launch_pupdate(L, n, P->p, P->z, 0, P->sc));
+            BID_TRY(launch_update(L, N, NH, P->xs, P->r, P->p, P->q, P->sc, P->partials));
+            return launch_check(L, P->sc, 0, 0, 0);
+        case 6:
+            BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp,
+                                  P->sc, P->partials));
+            BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
+            return launch_check(L, P->sc, 0, 0, 1);
+        case 7:
+            return launch_rhs_gate(L, N, NH, P->xs + N, P->t, nullptr, 0, s->mH, s->params, P->opts.dt,
+                                   P->ytmp);
+        default:
+            return launch_normalise(L, N, P->xs, s->m, s->msum, P->sc, P->partials);
+        }
+    };
+    int rc = BID_OK;
+    for (int cls = 0; cls < BID_PROFILE_CLASSES && rc == BID_OK; ++cls) {
+        rc = run(cls);   // warm-up launch
+        if (rc == BID_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = set_error(BID_ECUDA, "event record failed");
+        for (int k = 0; k < reps && rc == BID_OK; ++k) rc = run(cls);
+        if (rc == BID_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = set_error(BID_ECUDA, "event record failed");
+        float t = 0.0f;
+        if (rc == BID_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+            rc = set_error(BID_ECUDA, "event timing failed");
+        if (rc == BID_OK) ms[cls] = (double)t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the herr word is left as the solves left it: an expired wait shows at the next solve
+    return rc;
 }
 
 int bid_step(bid_system* s, bid_precond* P, double* U, double* V, double* h, const double* Ist,

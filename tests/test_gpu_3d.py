@@ -3,9 +3,10 @@
 The 1 x 1 x 0.3 cm orthotropic slab with the fibre angle rotating from -60 to
 +60 degrees through the depth, isolated heart (Pi = Id, N_H = N).  At
 65 x 65 x 21 nodes every factor precision is compared with the oracle's FP64
-solve (plain projected CG to relative residual 1e-13): the solution agrees
-within 1e-9 relative whatever the factor storage, because PCG stops on the
-FP64 residual.  At 161 x 161 x 49 nodes (N = 1 270 129) the BF16 form is
+solve (plain projected CG to relative residual 1e-14): U and V each agree
+within 1e-9 of the oracle's, relative to the oracle block's largest entry,
+whatever the factor storage, because PCG stops on the FP64 residual (1e-14 on
+both sides; see test_gpu_parity for why not 1e-13).  At 161 x 161 x 49 nodes (N = 1 270 129) the BF16 form is
 checked by properties: the true residual against the oracle's Lambda and the
 normalisation.
 """
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 from oracle import bidomain as ob
+from potentials import assert_potentials_close
 from workloads import slab_3d, params_3d, stimulus_centre_ball
 
 pytestmark = pytest.mark.gpu
@@ -51,7 +53,7 @@ def slab65(bid):
     Y = ob.rhs(o, V, rng.random(o.NH), np.zeros(o.NH), 5.0, p["dt"])
     g = ob.gamma_of(p, p["dt"])
     X0 = np.concatenate([np.zeros(o.N), V])
-    Xo, _ = ob.solve_cg(o, g, Y, X0, tol=1e-13, max_iter=20000)
+    Xo, _ = ob.solve_cg(o, g, Y, X0, tol=1e-14, max_iter=40000)
     Xo = ob.normalise(o, Xo)
     return mesh, p, S, o, Y, Xo
 
@@ -62,11 +64,10 @@ def test_slab65_precision_forms_match_oracle(bid, slab65, eps, prec):
     mesh, p, S, o, Y, Xo = slab65
     P = bid.Precond(S, p["dt"], eps=eps, precision=prec)
     X = torch.zeros(o.N + o.NH, dtype=torch.float64, device=DEV)
-    info = P.solve(T(Y), X, tol=1e-13, max_iter=500)
+    info = P.solve(T(Y), X, tol=1e-14, max_iter=800)
     Xg = H(X)
-    err = np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)
-    assert err <= 1e-9, (err, info)
-    assert info["relres_true"] < 1e-13
+    assert_potentials_close(Xg, Xo, o.N, 1e-9, info)
+    assert info["relres_true"] <= 1e-14
     # exact factors still leave the monodomain approximation K_m != K (the slab's
     # anisotropy ratios differ), so a few iterations remain
     assert 1 <= info["iters"] <= 200
@@ -75,7 +76,7 @@ def test_slab65_precision_forms_match_oracle(bid, slab65, eps, prec):
 
 def test_slab65_steps_match_oracle(bid, slab65):
     # five steps with the centre-ball stimulus, BF16 factors: per step the oracle
-    # (plain CG, 1e-13) is fed the GPU's state
+    # (plain CG, 1e-14) is fed the GPU's state
     mesh, p, S, o, _, _ = slab65
     P = bid.Precond(S, p["dt"], eps=1e-2, precision="bf16")
     ist = ob.heart_stimulus(o, stimulus_centre_ball(mesh))
@@ -84,11 +85,11 @@ def test_slab65_steps_match_oracle(bid, slab65):
     dt = p["dt"]
     for k in range(5):
         Ug, Vg, hg = H(U), H(V), H(h)
-        its = P.step(U, V, h, I, k * dt, 1, tol=1e-13, max_iter=500)
-        U1, V1, h1 = ob.time_step(o, Ug, Vg, hg, ist, k * dt, dt, solver="cg", tol=1e-13)
+        its = P.step(U, V, h, I, k * dt, 1, tol=1e-14, max_iter=800)
+        U1, V1, h1 = ob.time_step(o, Ug, Vg, hg, ist, k * dt, dt, solver="cg", tol=1e-14)
         X1 = np.concatenate([U1, V1])
         Xg = np.concatenate([H(U), H(V)])
-        assert np.linalg.norm(Xg - X1) <= 1e-8 * np.linalg.norm(X1), k
+        assert_potentials_close(Xg, X1, o.N, 1e-9, k)
         assert np.abs(H(h) - h1).max() <= 1e-13
         assert its[0] >= 1
 

@@ -3,8 +3,9 @@ one launch per phase (combined layout, forest factors, per-slice PCG scalars
 and convergence) against the FP64 oracle slice by slice, and against the same
 slices run one at a time through the single-system path.
 
-Tolerances as in test_gpu_parity: solves to relative residual 1e-13 agree with
-the oracle's direct solve within 1e-9 relative per slice; the factor
+Tolerances as in test_gpu_parity: solves to relative residual 1e-14 agree with
+the oracle's direct solve within 1e-9 per slice, U and V each relative to the
+oracle block's largest entry; the factor
 applications of a slice inside the batch equal its applications alone (same
 tree and blocks, possibly another summation order) to 1e-12 relative with FP64
 factors and 1e-6 with FP32 factors.
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 from oracle import bidomain as ob
+from potentials import assert_potentials_close
 from workloads import batched_slices, torso_square_2d, params_2d, stimulus_seeded_disc
 
 pytestmark = pytest.mark.gpu
@@ -136,12 +138,12 @@ def test_batch_solve_matches_oracle(bid, small, kw):
         Y[B.off[k]:B.off[k + 1]] = Yk
         ref.append(ob.solve_direct(o, ob.gamma_of(p, p["dt"]), Yk))
     X = torch.zeros(B.n, dtype=torch.float64, device=DEV)
-    info, _ = B.solve(T(Y), X, tol=1e-13, max_iter=400)
+    info, _ = B.solve(T(Y), X, tol=1e-14, max_iter=600)
     Xg = H(X)
     for k, Xo in enumerate(ref):
         Xk = Xg[B.off[k]:B.off[k + 1]]
-        assert np.linalg.norm(Xk - Xo) <= 1e-9 * np.linalg.norm(Xo), (k, info[k])
-        assert info[k]["relres_true"] < 1e-13
+        assert_potentials_close(Xk, Xo, systems[k].N, 1e-9, (k, info[k]))
+        assert info[k]["relres_true"] <= 1e-14
 
 
 def test_batch_step_matches_oracle_and_single(bid, small):
@@ -161,7 +163,7 @@ def test_batch_step_matches_oracle_and_single(bid, small):
                         T(h0[B.hoff[k]:B.hoff[k + 1]]), T(ist[B.hoff[k]:B.hoff[k + 1]])))
     for step in range(4):
         Xb, hb = H(X), H(h)
-        its = B.step(X, h, I, step * dt, 1, tol=1e-12, max_iter=200)
+        its = B.step(X, h, I, step * dt, 1, tol=1e-14, max_iter=400)
         Xa, ha = H(X), H(h)
         for k, o in os_.items():
             a, e = int(B.off[k]), int(B.off[k + 1])
@@ -169,16 +171,16 @@ def test_batch_step_matches_oracle_and_single(bid, small):
             U1, V1, h1 = ob.time_step(o, Xb[a:a + o.N], Xb[a + o.N:e], hb[hs:he], ist[hs:he],
                                       step * dt, dt)
             X1 = np.concatenate([U1, V1])
-            assert np.linalg.norm(Xa[a:e] - X1) <= 1e-8 * np.linalg.norm(X1), (step, k)
+            assert_potentials_close(Xa[a:e], X1, o.N, 1e-9, (step, k))
             assert np.abs(ha[hs:he] - h1).max() <= 1e-13
             P, U, V, hh, Ik = singles[k]
-            it1 = P.step(U, V, hh, Ik, step * dt, 1, tol=1e-12, max_iter=200)
+            it1 = P.step(U, V, hh, Ik, step * dt, 1, tol=1e-14, max_iter=400)
             # same iteration up to summation order: the counts agree unless a
             # residual sits within rounding of tol
             assert abs(int(it1[0]) - int(its[0, k])) <= 1, (step, k, it1, its[0])
             if it1[0] == its[0, k]:
                 Xs = np.concatenate([H(U), H(V)])
-                assert np.linalg.norm(Xa[a:e] - Xs) <= 1e-9 * np.linalg.norm(Xs), (step, k)
+                assert_potentials_close(Xa[a:e], Xs, o.N, 1e-9, (step, k))
             else:   # continue the single run from the batch's state
                 U.copy_(T(Xa[a:a + o.N]))
                 V.copy_(T(Xa[a + o.N:e]))

@@ -1,18 +1,22 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances: FP64 element-wise results (Lambda product, Step 1 + Step 3) within
-1e-13 relative to the largest entry (rounding order only); solves compared
-after a PCG run to relative residual 1e-13, where the solution error is at
-most cond * 1e-13, within 1e-9 relative (the bound stated for the
-transmembrane and extracellular potentials); every factor precision (FP64,
-FP32, BF16, eps > 0) reaches the same bound because PCG stops on the FP64
-residual.
+1e-13 relative to the largest entry (rounding order only).  Solves are
+compared potential by potential: U and V each within 1e-9 of the oracle's,
+relative to the largest entry of the oracle's block (tests/potentials.py).
+The solution error is at most cond * (relative residual), and a run to
+relative residual 1e-13 leaves errors of up to about 1e-9 in U (the oracle's
+own CG at 1e-13 against its direct solve, 97^2 and 129^2 slices), so parity
+solves run to 1e-14 on both sides, which leaves about 1e-10.  Every factor
+precision (FP64, FP32, BF16, eps > 0) reaches the same bound because PCG stops
+on the FP64 residual.
 """
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import bidomain as ob
+from potentials import assert_potentials_close
 from workloads import (torso_square_2d, slab_3d, params_2d, params_3d, stimulus_left_apex,
                        stimulus_seeded_disc)
 
@@ -152,12 +156,11 @@ def test_solve_matches_oracle(bid, case, kw):
     h = rng.random(o.NH)
     Y = ob.rhs(o, V, h, np.zeros(o.NH), 5.0, p["dt"])
     X = T(np.concatenate([np.zeros(o.N), V]))
-    info = P.solve(T(Y), X, tol=1e-13, max_iter=400)
+    info = P.solve(T(Y), X, tol=1e-14, max_iter=600)
     Xo = ob.solve_direct(o, g, Y)
     Xg = H(X)
-    err = np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)
-    assert err <= 1e-9, (err, info)
-    assert info["relres_true"] < 1e-13
+    assert_potentials_close(Xg, Xo, o.N, 1e-9, info)
+    assert info["relres_true"] <= 1e-14
     assert abs(Xg[:o.N] @ o.M.diagonal()) <= 1e-12 * np.abs(Xg).max() * o.M.sum()
 
 
@@ -172,17 +175,21 @@ def test_step_trajectory_matches_oracle(bid):
     dt = p["dt"]
     for k in range(20):
         Ug, Vg, hg = H(U), H(V), H(h)
-        its = P.step(U, V, h, I, k * dt, 1, tol=1e-13, max_iter=400)
+        its = P.step(U, V, h, I, k * dt, 1, tol=1e-14, max_iter=600)
         U1, V1, h1 = ob.time_step(o, Ug, Vg, hg, ist, k * dt, dt)
         Xg = np.concatenate([H(U), H(V)])
         X1 = np.concatenate([U1, V1])
-        assert np.linalg.norm(Xg - X1) <= 1e-9 * np.linalg.norm(X1), k
+        assert_potentials_close(Xg, X1, o.N, 1e-9, k)
         assert np.abs(H(h) - h1).max() <= 1e-13
         Uo, Vo, ho = ob.time_step(o, Uo, Vo, ho, ist, k * dt, dt)
         assert its[0] >= 1
+    # the two trajectories, each run on its own, agree at the end as well (the
+    # per-step errors do not grow: the oracle's CG trajectory at 1e-14 stays
+    # within 1e-10 of its direct one over these 20 steps)
     Xo = np.concatenate([Uo, Vo])
     Xg = np.concatenate([H(U), H(V)])
-    assert np.linalg.norm(Xg - Xo) <= 1e-8 * np.linalg.norm(Xo)
+    assert_potentials_close(Xg, Xo, o.N, 1e-9, "end")
+    assert np.abs(H(h) - ho).max() <= 1e-12
     assert H(V).max() > -60.0                # the stimulus depolarised the site
 
 
@@ -244,6 +251,41 @@ def _full_size_properties(bid, n, steps, eps, precision):
         idx = rng.choice(o.NH, 2000, replace=False)
         _, gg = ob.ms_reaction(Vb[idx], hb[idx], p)
         np.testing.assert_allclose(H(h)[idx], hb[idx] + p["dt"] * gg, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_513_step_matches_oracle(bid, precision):
+    # the 513^2 slice (N = 263 169, N_H = 49 925) in the bench's form (eps 1e-3,
+    # leaf 32): low-rank groups accepted, several levels of large clusters and
+    # the masked second P_1 solve all take part.  Five steps at rel-res 1e-8
+    # bring the stimulated state away from rest; then one step at 1e-14 from
+    # that state is compared with the oracle's step (sparse direct solve) from
+    # the same state, U and V each to 1e-9, h exactly up to rounding
+    mesh = torso_square_2d(513)
+    p = params_2d(0.1)
+    S = bid.System(mesh, p)
+    assert (S.N, S.NH) == (263169, 49925)
+    P = bid.Precond(S, p["dt"], eps=1e-3, precision=precision, leaf=32)
+    st = P.stats
+    assert st["lowrank_blocks"] > 0 and st["lowrank_entries"] > 0
+    assert st["large_levels1"] >= 3 and st["large_levelsk"] >= 2, st
+    assert 0 < st["masked_dead1"] < st["masked_clusters1"], st
+    assert st["alg_bytes_p1_masked"] < st["alg_bytes_p1"]
+    o = ob.build_system(mesh, p)
+    assert (S.perm == o.order).all()
+    ist = ob.heart_stimulus(o, stimulus_seeded_disc(mesh, seed=0))
+    U0, V0, h0 = ob.initial_state(o)
+    U, V, h, I = T(U0), T(V0), T(h0), T(ist)
+    dt = p["dt"]
+    P.step(U, V, h, I, 0.0, 5, tol=1e-8, max_iter=200)
+    Ug, Vg, hg = H(U), H(V), H(h)
+    assert Vg.max() > p["v_rest"] + 1.0       # the stimulus has moved the state
+    its = P.step(U, V, h, I, 5 * dt, 1, tol=1e-14, max_iter=800)
+    U1, V1, h1 = ob.time_step(o, Ug, Vg, hg, ist, 5 * dt, dt)
+    assert_potentials_close(np.concatenate([H(U), H(V)]), np.concatenate([U1, V1]), o.N, 1e-9,
+                            (precision, int(its[0])))
+    assert np.abs(H(h) - h1).max() <= 1e-13
+    assert abs(H(U) @ o.M.diagonal()) <= 1e-12 * np.abs(H(U)).max() * o.M.sum()
 
 
 def test_full_size_513_properties(bid):
