@@ -12,7 +12,9 @@ Contents (paper sections in brackets):
                 direct factorisation, by plain CG or by dense pseudo-inverse
                 [Prop. 1], the normalisation [proof of Prop. 1], and the
                 block-LU preconditioner at its exact limit P_1 = S_1,
-                P_K = K_m [Def. 5.1, eq. prec2, Sec. 5.2].
+                P_K = K_m [Def. 5.1, eq. prec2, Sec. 5.2]; the Crank-Nicolson and
+                Strang-splitting time schemes [Remark on the time discretisation]
+                with Heun's method for the reaction half steps.
   algebra.py    dense matrices of Props. 2-3 and Remark K (tiny meshes only).
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against

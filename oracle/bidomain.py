@@ -322,3 +322,94 @@ def precond_apply_exact(sys: System, gamma: float, r: np.ndarray) -> np.ndarray:
     w[:NH] = sys.Si @ z2
     z1 = z1 - s1_pseudo_inverse_apply(sys, w)
     return np.concatenate([z1, z2])
+
+
+# --------------------------------------------------------------------------
+# Other time schemes (Remark "About the time discretisation"): a scheme
+# changes the right-hand side of Step 1 and the coefficient of M_H in Lambda
+# (hence in K); Lambda keeps its structure (symmetric PSD, kernel [1; 0]).
+# Both schemes below treat the diffusion by Crank-Nicolson, so Lambda carries
+# 2 gamma = 2 chi Cm / dt.
+# --------------------------------------------------------------------------
+
+def scheme_gamma(params: dict, dt: float, scheme: str) -> float:
+    """Coefficient of M_H in Lambda: gamma (semi-implicit Euler, Sec. 3.2) or
+    2 gamma (Crank-Nicolson diffusion, in the "cn" and "strang" schemes)."""
+    g = gamma_of(params, dt)
+    return g if scheme == "euler" else 2.0 * g
+
+
+def rhs_cn(sys: System, U, V, h, ist, t: float, dt: float):
+    """Step 1 of the Crank-Nicolson scheme, reaction explicit at t^n.  The
+    parabolic equation averaged between t^n and t^n+1,
+      chi Cm M_H (V' - V)/dt + chi M_H (I_ion - I_st)
+          = -1/2 S_i (Pi U' + V') - 1/2 S_i (Pi U + V),
+    with the elliptic equation S_1 U' + Pi^T S_i V' = 0 at t^n+1, is
+    Lambda(2 gamma) X' = [0; M_H (2 gamma V - 2 chi (I_ion - I_st)) - S_i (Pi U + V)]."""
+    p = sys.params
+    g = gamma_of(p, dt)
+    i_ion, _ = ms_reaction(V, h, p)
+    i_st = ist if stimulus_on(t, p) else np.zeros_like(V)
+    y2 = sys.MH @ (2.0 * g * V - 2.0 * p["chi"] * (i_ion - i_st)) - sys.Si @ (U[:sys.NH] + V)
+    return np.concatenate([np.zeros(sys.N), y2])
+
+
+def reaction_heun(sys: System, V, h, ist, t0: float, t1: float):
+    """The reaction ODEs  Cm dv/dt = -(I_ion(v, h) - I_st(t)),  dh/dt = g(v, h)
+    at every heart node over [t0, t1] by Heun's method (explicit trapezoidal
+    rule, second order): with tau = t1 - t0, k1 = F(y, t0),
+    k2 = F(y + tau k1, t1), y <- y + tau (k1 + k2)/2."""
+    p = sys.params
+    tau, t = t1 - t0, t0
+
+    def F(v, hh, tt):
+        i_ion, gg = ms_reaction(v, hh, p)
+        i_st = ist if stimulus_on(tt, p) else np.zeros_like(v)
+        return -(i_ion - i_st) / p["Cm"], gg
+
+    dv1, dh1 = F(V, h, t)
+    dv2, dh2 = F(V + tau * dv1, h + tau * dh1, t1)
+    return V + 0.5 * tau * (dv1 + dv2), h + 0.5 * tau * (dh1 + dh2)
+
+
+def _solve(sys: System, gamma: float, Y, X0, solver: str, tol: float):
+    if solver == "direct":
+        return solve_direct(sys, gamma, Y)
+    if solver == "cg":
+        return solve_cg(sys, gamma, Y, X0, tol=tol)[0]
+    if solver == "dense":
+        return solve_dense(sys, gamma, Y)
+    raise ValueError(solver)
+
+
+def time_step_cn(sys: System, U, V, h, ist, t: float, dt: float, solver: str = "direct",
+                 tol: float = 1e-13):
+    """One step of the Crank-Nicolson scheme (rhs_cn): returns (U, V, h) at
+    t + dt; U must satisfy the elliptic equation with V (it does after any
+    step, and for the resting initial state).  The gate takes its explicit
+    Euler step from (V^n, W^n), as in Step 3."""
+    Y = rhs_cn(sys, U, V, h, ist, t, dt)
+    X = _solve(sys, scheme_gamma(sys.params, dt, "cn"), Y, np.concatenate([U, V]), solver, tol)
+    return X[:sys.N], X[sys.N:], gate_update(sys, V, h, dt)
+
+
+def time_step_strang(sys: System, U, V, h, ist, t: float, dt: float, solver: str = "direct",
+                     tol: float = 1e-13):
+    """One step of Strang splitting, reaction half step / diffusion step /
+    reaction half step.  The reaction half steps are reaction_heun over
+    [t, t + dt/2] and [t + dt/2, t + dt].  The diffusion step is
+    Crank-Nicolson on the reaction-free bidomain system from V*: its midpoint
+    Z = (X* + X')/2 solves Lambda(2 gamma) Z = [0; 2 gamma M_H V*] (the
+    elliptic equation holds at both ends, so it holds for Z), and
+    V' = 2 Z_V - V*.  The returned U is Z_U, the extracellular potential at
+    the middle of the step, t + dt/2 (U at the step's end would need one more
+    elliptic solve).  Returns (U_mid, V, h) with V and h at t + dt."""
+    p = sys.params
+    mid = t + 0.5 * dt
+    Vs, hs = reaction_heun(sys, V, h, ist, t, mid)
+    g2 = scheme_gamma(p, dt, "strang")
+    Y = np.concatenate([np.zeros(sys.N), sys.MH @ (g2 * Vs)])
+    Z = _solve(sys, g2, Y, np.concatenate([U, Vs]), solver, tol)
+    V2 = 2.0 * Z[sys.N:] - Vs
+    V3, h3 = reaction_heun(sys, V2, hs, ist, mid, t + dt)
+    return Z[:sys.N], V3, h3
