@@ -63,6 +63,8 @@ def parse():
     a.add_argument("--eps", type=float, default=1e-3)
     a.add_argument("--precision", default="fp32")
     a.add_argument("--leaf", type=int, default=32)
+    a.add_argument("--scheme", default="euler", choices=["euler", "cn", "strang"],
+                   help="time scheme of the slice and slab workloads")
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
@@ -106,7 +108,9 @@ def workload_name(args, N=None, NH=None):
         n = args.n
         return (f"3D orthotropic slab {n}x{n}x{slab_nz(n)}{sizes}, fibres -60..+60 deg through "
                 "the depth, isolated heart, dt 0.05 ms, centre-ball stimulus, PCG rel-res 1e-8")
-    return (f"2D torso slice {args.n}^2{sizes}, dt 0.1 ms, seeded stimulus disc, "
+    scheme = {"euler": "", "cn": ", Crank-Nicolson scheme",
+              "strang": ", Strang splitting"}[getattr(args, "scheme", "euler")]
+    return (f"2D torso slice {args.n}^2{sizes}, dt 0.1 ms, seeded stimulus disc{scheme}, "
             "PCG rel-res 1e-8")
 
 
@@ -672,7 +676,8 @@ def main():
                     snap=snap)
 
     # ---- chosen form
-    P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf)
+    P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf,
+                    scheme=args.scheme)
     chosen_stats = dict(P.stats)
     chosen = time_form(P)
 
@@ -747,7 +752,7 @@ def main():
     # ---- plain form on the same GPU, the same steps from the same state
     plain = None
     if not args.no_plain:
-        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64", leaf=args.leaf)
+        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64", leaf=args.leaf, scheme=args.scheme)
         plain = time_form(Pp)
         plain_stats = Pp.stats
         del Pp
@@ -770,7 +775,8 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": workload_name(args, N, NH),
-            "form": {"eps": args.eps, "factor_precision": args.precision, "leaf": args.leaf},
+            "form": {"eps": args.eps, "factor_precision": args.precision, "leaf": args.leaf,
+                     "scheme": args.scheme},
             "mean_pcg_iters": mean_it,
             "l2": "inputs larger than L2 (factor + matrices several GB)",
             "parallelism": f"replicas{world}" if world > 1 else "single GPU",

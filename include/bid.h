@@ -75,6 +75,20 @@ extern "C" {
 #define BID_FP32 1
 #define BID_BF16 2
 
+/* time schemes of bid_step (Sec. 3.2 and the remark on the time
+ * discretisation: a scheme changes Step 1 and the coefficient of M_H in
+ * Lambda, which keeps its structure) */
+#define BID_SCHEME_EULER 0   /* semi-implicit Euler of the resolution algorithm
+                                (Sec. 3.2): Lambda with gamma = chi Cm / dt */
+#define BID_SCHEME_CN 1      /* Crank-Nicolson diffusion, reaction explicit at t^n:
+                                Lambda(2 gamma) X^{n+1} = [0; M_H (2 gamma V^n -
+                                2 chi (I_ion - I_st)) - S_i (Pi U^n + V^n)] */
+#define BID_SCHEME_STRANG 2  /* Strang splitting: Heun reaction half step, Crank-
+                                Nicolson diffusion step (its midpoint Z solves
+                                Lambda(2 gamma) Z = [0; 2 gamma M_H V*], V = 2 Z_V -
+                                V*), Heun reaction half step; U returned is Z_U, the
+                                extracellular potential at the middle of the step */
+
 /* Mesh of Omega with the heart sub-mesh (Sec. 3.1, hypothesis H1).  All arrays
  * are HOST memory, borrowed for the duration of bid_assemble only. */
 typedef struct bid_mesh {
@@ -112,6 +126,9 @@ typedef struct bid_precond_opts {
     int32_t leaf_size;        /* nested-dissection leaf: max nodes per leaf cluster (4..4096) */
     int32_t block;            /* rows of a low-rank boundary group (8..256) */
     int32_t n_threads;        /* host threads for the build (0 = all) */
+    int32_t scheme;           /* BID_SCHEME_*: time scheme of bid_step; the factors and
+                                 bid_solve use gamma = chi Cm / dt (EULER) or twice
+                                 that (CN, STRANG) */
 } bid_precond_opts;
 
 typedef struct bid_precond_stats {
@@ -265,7 +282,15 @@ int bid_solve(bid_system* s, bid_precond* P, const double* Y, double* X,
  * Step 2 by bid_solve with guess (U^n, V^n).  U (N), V (N_H), h (N_H) device,
  * updated in place.  Ist: device per-heart-node stimulus amplitude (uA/cm^2)
  * applied while t in [stim_t_on, stim_t_off), or NULL.  iters_out: host array
- * of n_steps PCG iteration counts, or NULL.  Blocking. */
+ * of n_steps PCG iteration counts, or NULL.  Blocking.
+ * The preconditioner's scheme (bid_precond_opts.scheme) selects the time
+ * scheme: BID_SCHEME_CN replaces Step 1 by its Crank-Nicolson right-hand side
+ * (one fused kernel, which reads U^n: U must satisfy the elliptic equation
+ * with V, as it does after any step and for the resting state U = 0,
+ * V = v_rest); BID_SCHEME_STRANG runs the reaction half steps (stimulus
+ * sampled at t, t + dt/2 and t + dt) around the Crank-Nicolson diffusion
+ * solve and returns in U the extracellular potential at t + dt/2 (U on input
+ * is only the solve's initial guess). */
 int bid_step(bid_system* s, bid_precond* P, double* U, double* V, double* h,
              const double* Ist, double t0, int n_steps, double tol, int max_iter,
              int* iters_out, void* stream);

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbid.so")
 OK, EINVAL, ENOCONV, ESTAGNATE, ECUDA, ETIMEOUT, ENOMEM = range(7)
 FP64, FP32, BF16 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+SCHEMES = {"euler": 0, "cn": 1, "strang": 2}
 
 
 class BidError(RuntimeError):
@@ -42,7 +43,8 @@ class Params(C.Structure):
 
 class PrecondOpts(C.Structure):
     _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("precision", C.c_int32),
-                ("leaf_size", C.c_int32), ("block", C.c_int32), ("n_threads", C.c_int32)]
+                ("leaf_size", C.c_int32), ("block", C.c_int32), ("n_threads", C.c_int32),
+                ("scheme", C.c_int32)]
 
 
 class PrecondStats(C.Structure):
@@ -228,12 +230,13 @@ class System:
             self.h = None
 
 
-def _opts(dt, eps, precision, leaf, block, threads):
+def _opts(dt, eps, precision, leaf, block, threads, scheme="euler"):
     o = PrecondOpts()
     lib.bid_precond_opts_default(C.byref(o))
     o.dt, o.eps = float(dt), float(eps)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.leaf_size, o.block, o.n_threads = int(leaf), int(block), int(threads)
+    o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     return o
 
 
@@ -241,8 +244,8 @@ class Precond:
     """bid_precond: P_Lambda for one time step dt, plus the PCG work vectors."""
 
     def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=16, block=128,
-                 threads=0):
-        o = _opts(dt, eps, precision, leaf, block, threads)
+                 threads=0, scheme="euler"):
+        o = _opts(dt, eps, precision, leaf, block, threads, scheme)
         h = _VP()
         _check(lib.bid_precond_build_ex(system.h, C.byref(o), C.byref(h)))
         self.h, self.system, self.dt = h, system, float(dt)
@@ -336,10 +339,11 @@ class Batch:
     """bid_batch: independent slices advanced together (combined layout:
     slice s owns X[off[s]:off[s+1]] = [U_s | V_s] and h[hoff[s]:hoff[s+1]])."""
 
-    def __init__(self, systems, dt, eps=0.0, precision="fp64", leaf=16, block=128, threads=0):
+    def __init__(self, systems, dt, eps=0.0, precision="fp64", leaf=16, block=128, threads=0,
+                 scheme="euler"):
         self.systems = list(systems)
         S = len(self.systems)
-        o = _opts(dt, eps, precision, leaf if np.isscalar(leaf) else 16, block, threads)
+        o = _opts(dt, eps, precision, leaf if np.isscalar(leaf) else 16, block, threads, scheme)
         arr = (_VP * S)(*[s.h.value for s in self.systems])
         lf = None if np.isscalar(leaf) else np.ascontiguousarray(leaf, dtype=np.int32)
         h = _VP()

@@ -415,6 +415,8 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     if (!(o->eps >= 0.0) || o->eps >= 1.0) return set_error(BID_EINVAL, "eps must be in [0, 1)");
     if (o->precision < BID_FP64 || o->precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
     if (o->block < 8 || o->block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
+    if (o->scheme != BID_SCHEME_EULER)
+        return set_error(BID_EINVAL, "the batched form steps the semi-implicit Euler scheme only");
     std::vector<int32_t> lf(nslices, o->leaf_size);
     if (leaf) lf.assign(leaf, leaf + nslices);
     for (int32_t v : lf)
@@ -641,7 +643,9 @@ int bid_tune_leaf(bid_system* s, const bid_precond_opts* o, const int32_t* cands
     for (int c = 0; c < ncands; ++c)
         if (cands[c] < 4 || cands[c] > 4096) return set_error(BID_EINVAL, "leaf candidates must be in 4..4096");
     const AssembledHost& H = s->host;
-    TuneKey key{H.N, H.NH, H.S1.nnz(), H.Si.nnz(), H.dim, o->precision, o->block, o->eps, o->dt,
+    // the factors depend on dt through gamma only (Crank-Nicolson schemes: 2 chi Cm / dt)
+    const double dt_gamma = o->scheme == BID_SCHEME_EULER ? o->dt : 0.5 * o->dt;
+    TuneKey key{H.N, H.NH, H.S1.nnz(), H.Si.nnz(), H.dim, o->precision, o->block, o->eps, dt_gamma,
                 std::vector<int32_t>(cands, cands + ncands)};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);

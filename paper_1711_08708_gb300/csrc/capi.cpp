@@ -366,6 +366,7 @@ void bid_precond_opts_default(bid_precond_opts* o) {
     o->leaf_size = 16;
     o->block = 128;
     o->n_threads = 0;
+    o->scheme = BID_SCHEME_EULER;
 }
 
 int bid_precond_build(bid_system* s, double dt, double eps, int precision, bid_precond** out) {
@@ -385,10 +386,12 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (o->precision < BID_FP64 || o->precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
     if (o->block < 8 || o->block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o->leaf_size < 4 || o->leaf_size > 4096) return set_error(BID_EINVAL, "leaf_size must be in 4..4096");
+    if (o->scheme < BID_SCHEME_EULER || o->scheme > BID_SCHEME_STRANG) return set_error(BID_EINVAL, "bad scheme");
     auto t0 = std::chrono::steady_clock::now();
     BID_TRY(hsolve_prepare());
     const AssembledHost& H = s->host;
-    const double gamma = s->params.chi * s->params.Cm / o->dt;
+    // Crank-Nicolson diffusion (CN, Strang) doubles the coefficient of M_H
+    const double gamma = (o->scheme == BID_SCHEME_EULER ? 1.0 : 2.0) * s->params.chi * s->params.Cm / o->dt;
     HBuildOpts bo;
     bo.eps = o->eps;
     bo.leaf = o->leaf_size;
@@ -424,6 +427,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (rc == BID_OK) rc = dalloc(&P->z1b, N);
     if (rc == BID_OK) rc = dalloc(&P->t, NH);
     if (rc == BID_OK) rc = dalloc(&P->w, N);
+    if (rc == BID_OK && o->scheme == BID_SCHEME_STRANG) rc = dalloc(&P->vstar, NH);
     if (rc == BID_OK) rc = dalloc(&P->hs.ybuf, N);
     if (rc == BID_OK) rc = dalloc(&P->hs.xp, N);
     if (rc == BID_OK) rc = dalloc(&P->hs.vbuf, std::max(h1.vbuf, hk.vbuf));
@@ -662,15 +666,37 @@ int bid_step(bid_system* s, bid_precond* P, double* U, double* V, double* h, con
     BID_CUDA_TRY(cudaMemcpyAsync(P->xs, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     BID_CUDA_TRY(cudaMemcpyAsync(P->xs + N, V, sizeof(double) * NH, cudaMemcpyDeviceToDevice, st));
     int rc = BID_OK;
+    const Launch L = launch_of(s, stream);
+    auto stim_on = [&](double t) {
+        return (t >= s->params.stim_t_on && t < s->params.stim_t_off) ? 1 : 0;
+    };
+    const int scheme = P->opts.scheme;
     for (int k = 0; k < n_steps; ++k) {
         const double t = t0 + k * dt;
-        const int on = (t >= s->params.stim_t_on && t < s->params.stim_t_off) ? 1 : 0;
-        rc = launch_rhs_gate(launch_of(s, stream), N, NH, P->xs + N, h, Ist, on, s->mH, s->params, dt, P->ytmp);
+        const int on = stim_on(t);
+        if (scheme == BID_SCHEME_CN) {
+            rc = launch_rhs_gate_cn(L, N, NH, s->Si, P->xs, P->xs + N, h, Ist, on, s->mH, s->params, dt,
+                                    P->ytmp);
+        } else if (scheme == BID_SCHEME_STRANG) {
+            // reaction over [t, t + dt/2]; the diffusion solve then starts from (U, V*)
+            const double mid = t + 0.5 * dt;
+            rc = launch_react_heun(L, 0, N, NH, P->xs + N, h, P->vstar, Ist, on, stim_on(mid), mid - t,
+                                   P->gamma, s->mH, s->params, dt, P->ytmp);
+        } else {
+            rc = launch_rhs_gate(L, N, NH, P->xs + N, h, Ist, on, s->mH, s->params, dt, P->ytmp);
+        }
         if (rc != BID_OK) break;
         bid_solve_info inf{};
         rc = solve_impl(P, P->ytmp, P->xs, tol, max_iter, &inf, st);
         if (iters_out) iters_out[k] = inf.iters;
         if (rc != BID_OK) break;
+        if (scheme == BID_SCHEME_STRANG) {
+            // V = 2 Z_V - V*, then the reaction over [t + dt/2, t + dt]; U keeps Z_U
+            const double mid = t + 0.5 * dt, end = t + dt;
+            rc = launch_react_heun(L, 1, N, NH, P->xs + N, h, P->vstar, Ist, stim_on(mid), stim_on(end),
+                                   end - mid, P->gamma, s->mH, s->params, dt, P->ytmp);
+            if (rc != BID_OK) break;
+        }
     }
     BID_CUDA_TRY(cudaMemcpyAsync(U, P->xs, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     BID_CUDA_TRY(cudaMemcpyAsync(V, P->xs + N, sizeof(double) * NH, cudaMemcpyDeviceToDevice, st));
@@ -683,6 +709,8 @@ int bid_step_learned(bid_system* s, bid_precond* P, bid_guess* G, double* U, dou
                      void* stream) {
     if (!s || !P || !G || P->sys != s || !U || !V || !h) return set_error(BID_EINVAL, "bad argument");
     if (n_steps < 0 || !(tol > 0.0) || max_iter < 1) return set_error(BID_EINVAL, "bad step arguments");
+    if (P->opts.scheme != BID_SCHEME_EULER)
+        return set_error(BID_EINVAL, "the learned guess steps the semi-implicit Euler scheme only");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
     const double dt = P->opts.dt;
@@ -757,7 +785,7 @@ void bid_destroy_precond(bid_precond* P) {
     if (!P) return;
     free_hfactor(&P->F1);
     free_hfactor(&P->FK);
-    for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->hs.ybuf,
+    for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->vstar, P->hs.ybuf,
                       P->hs.xp, P->hs.inb, P->hs.vbuf, P->hs.tbuf, P->hs.pbuf, P->partials})
         cudaFree(p);
     cudaFree(P->hs.tickets);

@@ -383,6 +383,17 @@ int launch_axpy_sub(const Launch& L, int64_t n, double* a, const double* b);
 int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, double* h,
                     const double* Ist, int stim_on, const double* mH, const bid_params& p,
                     double dt, double* Y);
+// Crank-Nicolson Step 1 + Step 3 (S_i (Pi U + V) fused in): Y = [0; m_H (2 gamma V -
+// 2 chi (I_ion - I_st)) - S_i (Pi U + V)], h += dt g(V, h); gamma = chi Cm / dt.
+int launch_rhs_gate_cn(const Launch& L, int64_t N, int64_t NH, const SellDev& Si, const double* U,
+                       const double* V, double* h, const double* Ist, int stim_on, const double* mH,
+                       const bid_params& p, double dt, double* Y);
+// Strang reaction half step by Heun's method (mode 0: before the diffusion
+// step, V -> V* (also to vstar) and Y = [0; g2 m_H V*]; mode 1: after it, from
+// 2 Z_V - V* with Z_V in V).
+int launch_react_heun(const Launch& L, int mode, int64_t N, int64_t NH, double* V, double* h,
+                      double* vstar, const double* Ist, int on0, int on1, double tau, double g2,
+                      const double* mH, const bid_params& p, double dt, double* Y);
 int launch_normalise(const Launch& L, int64_t N, double* U, const double* m,
                      double msum, DevScalars* sc, double* partials);
 // One-thread convergence check of the device-resident PCG loop: first != 0
@@ -525,6 +536,7 @@ struct bid_precond {
     // work vectors (device)
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double *z1b = nullptr, *t = nullptr, *w = nullptr, *ytmp = nullptr, *xs = nullptr;
+    double* vstar = nullptr;                  // Strang scheme: V after the first reaction half step
     bid::HScratch hs;
     double* partials = nullptr;
     bid::DevScalars* sc = nullptr;

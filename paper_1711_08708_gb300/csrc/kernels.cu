@@ -1,13 +1,17 @@
 // FP64 vector kernels of the PCG on Lambda (Sec. 5.1, 6.2), the fused
 // Lambda product (eq. system), the S_i products of the block-LU chain
-// (eq. prec2), the fused Step 1 + Step 3 kernel (Sec. 3.2) and the
-// normalisation (proof of Prop. 1).
+// (eq. prec2), the fused Step 1 + Step 3 kernel (Sec. 3.2), its
+// Crank-Nicolson form and the Heun reaction half steps of Strang splitting
+// (remark on the time discretisation), and the normalisation (proof of
+// Prop. 1).
 //
 // All reductions are deterministic: each CTA reduces in a fixed tree, writes
 // its partial, and the last CTA to finish (ticket counter) sums the partials
 // in index order and updates the PCG scalars in device memory.  No kernel
 // needs a host round trip.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "internal.h"
 
@@ -363,6 +367,90 @@ __global__ void __launch_bounds__(TPB) k_rhs_gate(int N, int NH, const double* _
     }
 }
 
+__device__ __forceinline__ double ms_iion(const MsParams& P, double v, double hj) {
+    const double w = (v - P.v_rest) / P.span;
+    const double jin = hj * w * w * (1.0 - w) / P.tau_in;
+    const double jout = -w / P.tau_out;
+    return -P.Cm * P.span * (jin + jout);
+}
+__device__ __forceinline__ double ms_gate(const MsParams& P, double v, double hj) {
+    const double w = (v - P.v_rest) / P.span;
+    return (w < P.v_gate) ? (1.0 - hj) / P.tau_open : -hj / P.tau_close;
+}
+
+// Step 1 + Step 3 of the Crank-Nicolson scheme (remark on the time
+// discretisation), reaction explicit at t^n:
+//   Y_V = m_H (2 gamma v - 2 chi (I_ion - I_st)) - (S_i (Pi U + V))_r,  Y_U = 0,
+//   h <- h + dt g(v, h).
+// One warp per 32-row slice of S_i (heart rows); every thread also zeroes a
+// share of Y_U.
+__global__ void __launch_bounds__(TPB) k_rhs_gate_cn(int N, int NH, SellView Si,
+                                                     const double* __restrict__ U,
+                                                     const double* __restrict__ V,
+                                                     double* __restrict__ h,
+                                                     const double* __restrict__ Ist, int stim_on,
+                                                     const double* __restrict__ mH, MsParams P,
+                                                     double* __restrict__ Y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        Y[i] = 0.0;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int sl = gw; sl < Si.nslices; sl += nwarps) {
+        const int r = sl * 32 + lane;
+        const int b = Si.sptr[sl], w = (Si.sptr[sl + 1] - b) >> 5;
+        double a = 0.0;
+        for (int k = 0; k < w; ++k) {
+            const int idx = b + k * 32 + lane;
+            const int j = Si.col[idx];
+            a += Si.val[idx] * (U[j] + V[j]);
+        }
+        if (r >= NH) continue;
+        const double v = V[r], hj = h[r];
+        const double ist = (stim_on && Ist) ? Ist[r] : 0.0;
+        const double iion = ms_iion(P, v, hj);
+        Y[N + r] = mH[r] * (2.0 * P.gamma * v - 2.0 * P.chi * (iion - ist)) - a;
+        h[r] = hj + P.dt * ms_gate(P, v, hj);
+    }
+}
+
+// Reaction half step of Strang splitting: Heun's method on
+//   Cm dv/dt = -(I_ion(v, h) - I_st),  dh/dt = g(v, h)
+// over a window of length tau, the stimulus on at its start (on0) and at its
+// end (on1): k1 = F(y, t0), k2 = F(y + tau k1, t1), y <- y + tau (k1 + k2)/2.
+//  mode 0 (before the diffusion step): v = V; writes V* to vstar and to V (the
+//         guess of the diffusion solve), h, and Y = [0; g2 m_H V*];
+//  mode 1 (after it): v = 2 Z_V - V* (Z_V read from V); writes V and h.
+__global__ void __launch_bounds__(TPB) k_react_heun(int mode, int N, int NH, double* __restrict__ V,
+                                                    double* __restrict__ h,
+                                                    double* __restrict__ vstar,
+                                                    const double* __restrict__ Ist, int on0, int on1,
+                                                    double tau, double g2,
+                                                    const double* __restrict__ mH, MsParams P,
+                                                    double* __restrict__ Y) {
+    if (mode == 0)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+            Y[i] = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < NH; j += gridDim.x * blockDim.x) {
+        const double v = mode == 0 ? V[j] : 2.0 * V[j] - vstar[j];
+        const double hj = h[j];
+        const double i0 = (on0 && Ist) ? Ist[j] : 0.0;
+        const double i1 = (on1 && Ist) ? Ist[j] : 0.0;
+        const double dv1 = -(ms_iion(P, v, hj) - i0) / P.Cm;
+        const double dh1 = ms_gate(P, v, hj);
+        const double v1 = v + tau * dv1, h1 = hj + tau * dh1;
+        const double dv2 = -(ms_iion(P, v1, h1) - i1) / P.Cm;
+        const double dh2 = ms_gate(P, v1, h1);
+        const double vn = v + 0.5 * tau * (dv1 + dv2);
+        h[j] = hj + 0.5 * tau * (dh1 + dh2);
+        V[j] = vn;
+        if (mode == 0) {
+            vstar[j] = vn;
+            Y[N + j] = mH[j] * (g2 * vn);
+        }
+    }
+}
+
 // alpha = (M U, 1) / (M 1, 1) (lumped M), then U -= alpha.
 __global__ void __launch_bounds__(TPB) k_mass_dot(int N, const double* __restrict__ U,
                                                   const double* __restrict__ m, double msum,
@@ -468,6 +556,36 @@ int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, dou
     k_rhs_gate<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, V, h, Ist, stim_on, mH, P,
                                                       Y);
     return check_launch("rhs_gate");
+}
+static MsParams ms_params(const bid_params& p, double dt) {
+    MsParams P;
+    P.v_rest = p.v_rest;
+    P.span = p.v_peak - p.v_rest;
+    P.tau_in = p.tau_in;
+    P.tau_out = p.tau_out;
+    P.tau_open = p.tau_open;
+    P.tau_close = p.tau_close;
+    P.v_gate = p.v_gate;
+    P.Cm = p.Cm;
+    P.chi = p.chi;
+    P.gamma = p.chi * p.Cm / dt;
+    P.dt = dt;
+    return P;
+}
+int launch_rhs_gate_cn(const Launch& L, int64_t N, int64_t NH, const SellDev& Si, const double* U,
+                       const double* V, double* h, const double* Ist, int stim_on, const double* mH,
+                       const bid_params& p, double dt, double* Y) {
+    const int g = grid_for(L, std::max<int64_t>((int64_t)Si.nslices * 32, N));
+    k_rhs_gate_cn<<<g, TPB, 0, L.st>>>((int)N, (int)NH, view(Si), U, V, h, Ist, stim_on, mH,
+                                       ms_params(p, dt), Y);
+    return check_launch("rhs_gate_cn");
+}
+int launch_react_heun(const Launch& L, int mode, int64_t N, int64_t NH, double* V, double* h,
+                      double* vstar, const double* Ist, int on0, int on1, double tau, double g2,
+                      const double* mH, const bid_params& p, double dt, double* Y) {
+    k_react_heun<<<grid_for(L, mode == 0 ? N : NH), TPB, 0, L.st>>>(
+        mode, (int)N, (int)NH, V, h, vstar, Ist, on0, on1, tau, g2, mH, ms_params(p, dt), Y);
+    return check_launch("react_heun");
 }
 int launch_check(const Launch& L, DevScalars* sc, unsigned long long h, int use_graph, int first) {
     k_check<<<1, 1, 0, L.st>>>(sc, (cudaGraphConditionalHandle)h, use_graph, first);
