@@ -65,6 +65,9 @@ def parse():
     a.add_argument("--leaf", type=int, default=32)
     a.add_argument("--scheme", default="euler", choices=["euler", "cn", "strang"],
                    help="time scheme of the slice and slab workloads")
+    a.add_argument("--elliptic", default="hchol", choices=["hchol", "mg"],
+                   help="P_1 / P_K by hierarchical Cholesky factors or multigrid V-cycles "
+                        "(mg: FP64, --eps and --precision not used)")
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
@@ -676,8 +679,10 @@ def main():
                     snap=snap)
 
     # ---- chosen form
+    if args.elliptic == "mg":
+        args.eps, args.precision = 0.0, "fp64"
     P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf,
-                    scheme=args.scheme)
+                    scheme=args.scheme, elliptic=args.elliptic)
     chosen_stats = dict(P.stats)
     chosen = time_form(P)
 
@@ -771,12 +776,13 @@ def main():
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": f"f64 PCG / {args.precision} factors" + (f" (eps {args.eps:g})" if args.eps else ""),
+        "dtype": ("f64 PCG / f64 multigrid V-cycles" if args.elliptic == "mg" else
+                  f"f64 PCG / {args.precision} factors" + (f" (eps {args.eps:g})" if args.eps else "")),
         "data": "synthetic",
         "config": {
             "workload": workload_name(args, N, NH),
             "form": {"eps": args.eps, "factor_precision": args.precision, "leaf": args.leaf,
-                     "scheme": args.scheme},
+                     "scheme": args.scheme, "elliptic": args.elliptic},
             "mean_pcg_iters": mean_it,
             "l2": "inputs larger than L2 (factor + matrices several GB)",
             "parallelism": f"replicas{world}" if world > 1 else "single GPU",
@@ -800,8 +806,10 @@ def main():
                                  else None),
                      "traffic_note": "ncu DRAM bytes of the same kernels on the 1025^2 slice, scaled "
                                      "by the algorithmic bytes",
-                     "kernel": "P_1 solve: k_permute, k_flat_fwd, k_up_fwd, k_bwd_prep, "
-                               "k_up_bwd, k_flat_bwd over all tree levels",
+                     "kernel": ("P_1 solve: k_permute, k_flat_fwd, k_up_fwd, k_bwd_prep, "
+                                "k_up_bwd, k_flat_bwd over all tree levels" if args.elliptic == "hchol"
+                                else "P_1 multigrid V-cycle: k_mg_first, k_mg_cheb, k_mg_resid, "
+                                     "k_mg_apply over all levels, k_mg_dense"),
                      "ms": solve_ms, "algorithmic_bytes": alg_bytes,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
                      "classes": classes, "whole_step": whole_step},

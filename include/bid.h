@@ -75,6 +75,21 @@ extern "C" {
 #define BID_FP32 1
 #define BID_BF16 2
 
+/* elliptic solvers of P_1 and P_K (the block-LU preconditioner admits any
+ * good preconditioners of S_1 and K, Sec. 5.2) */
+#define BID_ELLIPTIC_HCHOL 0 /* hierarchical (nested-dissection, eps-compressed)
+                                Cholesky factors (Sec. 5.3) */
+#define BID_ELLIPTIC_MG 1    /* one geometric-multigrid V-cycle: the mesh nodes must
+                                be the points of a regular lattice and its
+                                simplices the Kuhn simplices of the cells (2D:
+                                squares cut along the (+1, +1) diagonal; 3D: six
+                                tetrahedra around the (+1, +1, +1) diagonal); coarse
+                                level = points with all indices even, P1
+                                interpolation, Galerkin coarse operators,
+                                Chebyshev smoothing of degree 2 before and after
+                                the correction, dense inverse on the coarsest
+                                level; FP64; eps, leaf and block are not used */
+
 /* time schemes of bid_step (Sec. 3.2 and the remark on the time
  * discretisation: a scheme changes Step 1 and the coefficient of M_H in
  * Lambda, which keeps its structure) */
@@ -129,6 +144,7 @@ typedef struct bid_precond_opts {
     int32_t scheme;           /* BID_SCHEME_*: time scheme of bid_step; the factors and
                                  bid_solve use gamma = chi Cm / dt (EULER) or twice
                                  that (CN, STRANG) */
+    int32_t elliptic;         /* BID_ELLIPTIC_*: how P_1 and P_K are applied */
 } bid_precond_opts;
 
 typedef struct bid_precond_stats {
@@ -195,8 +211,13 @@ void bid_precond_opts_default(bid_precond_opts* o);
  * BID_ECUDA. */
 int bid_precond_build(bid_system* s, double dt, double eps, int precision,
                       bid_precond** out);
-/* The same with every option (leaf size, low-rank block rows, host threads);
- * defaults from bid_precond_opts_default.  The build also takes the all-ones
+/* The same with every option (leaf size, low-rank block rows, host threads,
+ * time scheme, elliptic solver); defaults from bid_precond_opts_default.
+ * With BID_ELLIPTIC_MG the build makes the multigrid hierarchies instead of
+ * the factors (EINVAL when the mesh is not a Kuhn lattice or precision is not
+ * BID_FP64); the stats then give the hierarchies' levels (levels1, levelsk),
+ * their stored matrix entries (dense_entries) and the algorithmic bytes of
+ * one V-cycle (alg_bytes_p1, alg_bytes_pk).  The build also takes the all-ones
  * forward results of P_1 used by the masked second P_1 solve (one extra solve,
  * skipped with BID_MASK=0). */
 int bid_precond_build_ex(bid_system* s, const bid_precond_opts* opts,
@@ -520,6 +541,14 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
                                 double gamma, double eps, const int32_t* leaf, int leaf_default,
                                 int block, int precision, int smem_cap, int from, int masked,
                                 const double* b, double* x, bid_precond_stats* stats, int64_t* sched);
+/* The multigrid V-cycle of BID_ELLIPTIC_MG on the host, in FP64 and in the
+ * order of operations of the GPU kernels: which = 1: x = V_1(b - mean(b))
+ * for S_1 (its hierarchy is singular: constants are its kernel), which = 2:
+ * x = V_K(b) for K_m = gamma M_H + S_m.  b and x host arrays (N or N_H).
+ * levels (may be NULL): the hierarchy's levels.  Errors: BID_EINVAL (bad
+ * argument, mesh not a Kuhn lattice). */
+int bid_host_mg_solve(const bid_host_system* h, int which, double gamma, const double* b, double* x,
+                      int32_t* levels);
 /* Frees a host system (NULL is ignored). */
 void bid_host_destroy(bid_host_system* h);
 

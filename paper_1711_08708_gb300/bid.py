@@ -19,6 +19,7 @@ OK, EINVAL, ENOCONV, ESTAGNATE, ECUDA, ETIMEOUT, ENOMEM = range(7)
 FP64, FP32, BF16 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 SCHEMES = {"euler": 0, "cn": 1, "strang": 2}
+ELLIPTIC = {"hchol": 0, "mg": 1}
 
 
 class BidError(RuntimeError):
@@ -44,7 +45,7 @@ class Params(C.Structure):
 class PrecondOpts(C.Structure):
     _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("precision", C.c_int32),
                 ("leaf_size", C.c_int32), ("block", C.c_int32), ("n_threads", C.c_int32),
-                ("scheme", C.c_int32)]
+                ("scheme", C.c_int32), ("elliptic", C.c_int32)]
 
 
 class PrecondStats(C.Structure):
@@ -101,6 +102,7 @@ SIGNATURES = {
     "bid_host_factor_solve_dataflow": (_I, [_VP, _I, _D, _D, _I, _I, _I, _I, _I, _VP, _VP,
                                             C.POINTER(PrecondStats), _I64P]),
     "bid_host_factor_solve_masked": (_I, [_VP, _D, _I, _I, _I, _VP, _VP, _I64P]),
+    "bid_host_mg_solve": (_I, [_VP, _I, _D, _VP, _VP, _VP]),
     "bid_host_destroy": (None, [_VP]),
     "bid_batch_create": (_I, [_VP, _I, C.POINTER(PrecondOpts), _VP, C.POINTER(_VP)]),
     "bid_batch_layout": (_I, [_VP, _VP, _VP]),
@@ -230,13 +232,14 @@ class System:
             self.h = None
 
 
-def _opts(dt, eps, precision, leaf, block, threads, scheme="euler"):
+def _opts(dt, eps, precision, leaf, block, threads, scheme="euler", elliptic="hchol"):
     o = PrecondOpts()
     lib.bid_precond_opts_default(C.byref(o))
     o.dt, o.eps = float(dt), float(eps)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.leaf_size, o.block, o.n_threads = int(leaf), int(block), int(threads)
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    o.elliptic = ELLIPTIC[elliptic] if isinstance(elliptic, str) else int(elliptic)
     return o
 
 
@@ -244,8 +247,8 @@ class Precond:
     """bid_precond: P_Lambda for one time step dt, plus the PCG work vectors."""
 
     def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=16, block=128,
-                 threads=0, scheme="euler"):
-        o = _opts(dt, eps, precision, leaf, block, threads, scheme)
+                 threads=0, scheme="euler", elliptic="hchol"):
+        o = _opts(dt, eps, precision, leaf, block, threads, scheme, elliptic)
         h = _VP()
         _check(lib.bid_precond_build_ex(system.h, C.byref(o), C.byref(h)))
         self.h, self.system, self.dt = h, system, float(dt)
@@ -340,10 +343,10 @@ class Batch:
     slice s owns X[off[s]:off[s+1]] = [U_s | V_s] and h[hoff[s]:hoff[s+1]])."""
 
     def __init__(self, systems, dt, eps=0.0, precision="fp64", leaf=16, block=128, threads=0,
-                 scheme="euler"):
+                 scheme="euler", elliptic="hchol"):
         self.systems = list(systems)
         S = len(self.systems)
-        o = _opts(dt, eps, precision, leaf if np.isscalar(leaf) else 16, block, threads, scheme)
+        o = _opts(dt, eps, precision, leaf if np.isscalar(leaf) else 16, block, threads, scheme, elliptic)
         arr = (_VP * S)(*[s.h.value for s in self.systems])
         lf = None if np.isscalar(leaf) else np.ascontiguousarray(leaf, dtype=np.int32)
         h = _VP()
@@ -521,6 +524,15 @@ class HostSystem:
         _check(lib.bid_host_factor_solve(self.h, int(which), float(gamma), float(eps), int(leaf),
                                          int(block), prec, _ptr(b), _ptr(x), C.byref(st)))
         return x, st.as_dict()
+
+    def mg_solve(self, which, b, gamma=0.0):
+        """bid_host_mg_solve: one multigrid V-cycle of S_1 (which = 1, on b minus
+        its mean) or of K_m (which = 2) on the host; returns x and the levels."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        lv = C.c_int32()
+        _check(lib.bid_host_mg_solve(self.h, int(which), float(gamma), _ptr(b), _ptr(x), C.byref(lv)))
+        return x, int(lv.value)
 
     def factor_solve_masked(self, b, eps=0.0, leaf=16, block=128, precision="fp64"):
         """P_1 replay as the masked solve (b zero outside the heart nodes);

@@ -417,6 +417,8 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     if (o->block < 8 || o->block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o->scheme != BID_SCHEME_EULER)
         return set_error(BID_EINVAL, "the batched form steps the semi-implicit Euler scheme only");
+    if (o->elliptic != BID_ELLIPTIC_HCHOL)
+        return set_error(BID_EINVAL, "the batched form uses the hierarchical factors only");
     std::vector<int32_t> lf(nslices, o->leaf_size);
     if (leaf) lf.assign(leaf, leaf + nslices);
     for (int32_t v : lf)

@@ -37,9 +37,7 @@ int set_error(int code, const char* fmt, ...) {
     return code;
 }
 
-namespace {
-
-int upload_sell(const CsrHost& A, SellDev* d) {
+int upload_sell(const CsrHost& A, SellDev* d, int64_t ncols) {
     const int64_t n = A.n;
     const int32_t ns = (int32_t)((n + 31) / 32);
     std::vector<int32_t> sptr(ns + 1, 0);
@@ -63,7 +61,7 @@ int upload_sell(const CsrHost& A, SellDev* d) {
                     col[idx] = A.col[A.ptr[r] + k];
                     val[idx] = A.val[A.ptr[r] + k];
                 } else {
-                    col[idx] = r < n ? (int32_t)r : 0;
+                    col[idx] = (r < n && (ncols < 0 || r < ncols)) ? (int32_t)r : 0;
                 }
             }
         }
@@ -89,6 +87,8 @@ void free_sell(SellDev* d) {
     *d = SellDev();
 }
 
+namespace {
+
 template <typename T>
 int dalloc(T** p, int64_t n) {
     *p = nullptr;
@@ -106,22 +106,44 @@ Launch launch_of(const bid_system* s, void* stream) {
     return L;
 }
 
+}  // namespace
+
+// The elliptic solves of P_Lambda: the hierarchical Cholesky factors, or one
+// multigrid V-cycle (BID_ELLIPTIC_MG).  P_1 acts on the input minus
+// shift_sum / N.
+int apply_p1(bid_precond* P, const Launch& L, const double* in, const double* shift_sum, double* out) {
+    const double invN = 1.0 / (double)P->sys->host.N;
+    if (P->mg) return launch_mg(L, P->M1, in, shift_sum, invN, out);
+    return launch_hsolve(L, P->F1, in, shift_sum, invN, P->hs, out);
+}
+// the second P_1 application of eq. prec2 (input zero outside the heart)
+int apply_p1_masked(bid_precond* P, const Launch& L, const double* in, const double* shift_sum, double* out) {
+    const double invN = 1.0 / (double)P->sys->host.N;
+    if (P->mg) return launch_mg(L, P->M1, in, shift_sum, invN, out);
+    return launch_hsolve_masked(L, P->F1, in, shift_sum, invN, P->hs, out);
+}
+int apply_pk(bid_precond* P, const Launch& L, const double* in, double* out) {
+    if (P->mg) return launch_mg(L, P->MK, in, nullptr, 0.0, out);
+    return launch_hsolve(L, P->FK, in, nullptr, 0.0, P->hs, out);
+}
+
+namespace {
+
 // z = P_Lambda^-1 r (eq. prec2).  The shift of the first P_1 input is
 // sc->sumr / N (sum of r_U), of the second sc->sum_b / N.
 int precond_apply(bid_precond* P, const Launch& L, const double* r, double* z) {
     bid_system* s = P->sys;
     const int64_t N = s->host.N, NH = s->host.NH;
-    const double invN = 1.0 / (double)N;
     // Z1 = P_1^-1 p r_U
-    BID_TRY(launch_hsolve(L, P->F1, r, &P->sc->sumr, invN, P->hs, z));
+    BID_TRY(apply_p1(P, L, r, &P->sc->sumr, z));
     // T = r_V - S_i Pi Z1
     BID_TRY(launch_si_residual(L, NH, s->Si, r + N, z, P->t));
     // Z2 = P_K^-1 T
-    BID_TRY(launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->hs, z + N));
+    BID_TRY(apply_pk(P, L, P->t, z + N));
     // W = Pi^T S_i Z2 (zero on the torso), sum(W)
     BID_TRY(launch_si_apply_sum(L, N, NH, s->Si, z + N, P->w, P->sc, P->partials));
     // Z1 -= P_1^-1 p W (W is zero outside the heart: the masked solve)
-    BID_TRY(launch_hsolve_masked(L, P->F1, P->w, &P->sc->sum_b, invN, P->hs, P->z1b));
+    BID_TRY(apply_p1_masked(P, L, P->w, &P->sc->sum_b, P->z1b));
     BID_TRY(launch_axpy_sub(L, N, z, P->z1b));
     return BID_OK;
 }
@@ -144,7 +166,7 @@ int build_graph(bid_precond* P) {
     if (P->gexec) return BID_OK;
     bid_system* s = P->sys;
     const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
-    const int flexible = P->opts.precision != BID_FP64;
+    const int flexible = P->opts.precision != BID_FP64 || P->mg;
     BID_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
     BID_CUDA_TRY(cudaGraphCreate(&P->graph, 0));
     cudaGraphConditionalHandle h;
@@ -199,7 +221,7 @@ int build_graph(bid_precond* P) {
 int run_loop_host(bid_precond* P, const Launch& L, cudaStream_t st, DevScalars* h) {
     bid_system* s = P->sys;
     const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
-    const int flexible = P->opts.precision != BID_FP64;
+    const int flexible = P->opts.precision != BID_FP64 || P->mg;
     BID_TRY(launch_lambda(L, 1, N, NH, s->S1, s->Si, s->mH, P->gamma, P->xs, P->r, P->ytmp, P->sc,
                           P->partials));
     BID_TRY(launch_project(L, N, NH, P->r, P->sc, P->partials));
@@ -367,6 +389,7 @@ void bid_precond_opts_default(bid_precond_opts* o) {
     o->block = 128;
     o->n_threads = 0;
     o->scheme = BID_SCHEME_EULER;
+    o->elliptic = BID_ELLIPTIC_HCHOL;
 }
 
 int bid_precond_build(bid_system* s, double dt, double eps, int precision, bid_precond** out) {
@@ -387,6 +410,10 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (o->block < 8 || o->block > 256) return set_error(BID_EINVAL, "block must be in 8..256");
     if (o->leaf_size < 4 || o->leaf_size > 4096) return set_error(BID_EINVAL, "leaf_size must be in 4..4096");
     if (o->scheme < BID_SCHEME_EULER || o->scheme > BID_SCHEME_STRANG) return set_error(BID_EINVAL, "bad scheme");
+    if (o->elliptic != BID_ELLIPTIC_HCHOL && o->elliptic != BID_ELLIPTIC_MG)
+        return set_error(BID_EINVAL, "bad elliptic solver");
+    const bool mg = o->elliptic == BID_ELLIPTIC_MG;
+    if (mg && o->precision != BID_FP64) return set_error(BID_EINVAL, "the multigrid preconditioner runs in FP64 only");
     auto t0 = std::chrono::steady_clock::now();
     BID_TRY(hsolve_prepare());
     const AssembledHost& H = s->host;
@@ -402,21 +429,37 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knobs
     if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
     HFactorHost h1, hk;
-    // P_1: S_1 with the last U unknown pinned (pseudo-inverse on 1^perp)
-    BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, {(int32_t)(H.N - 1)}, bo, &h1));
+    MgHost m1, mk;
     // P_K: K_m = gamma M_H + S_m (Sec. 5.2)
     CsrHost Km = H.Sm;
     for (int64_t r = 0; r < Km.n; ++r)
         for (int64_t q = Km.ptr[r]; q < Km.ptr[r + 1]; ++q)
             if (Km.col[q] == r) Km.val[q] += gamma * H.mH[r];
-    BID_TRY(build_hfactor(Km, H.coords.data(), H.dim, {}, bo, &hk));
+    if (mg) {
+        // multigrid hierarchies of S_1 (singular, Neumann) and K_m on the mesh lattice
+        Lattice lat;
+        BID_TRY(lattice_of(H.coords.data(), H.N, H.dim, &lat));
+        BID_TRY(build_mg(H.S1, H.coords.data(), lat, true, &m1));
+        BID_TRY(build_mg(Km, H.coords.data(), lat, false, &mk));
+    } else {
+        // P_1: S_1 with the last U unknown pinned (pseudo-inverse on 1^perp)
+        BID_TRY(build_hfactor(H.S1, H.coords.data(), H.dim, {(int32_t)(H.N - 1)}, bo, &h1));
+        BID_TRY(build_hfactor(Km, H.coords.data(), H.dim, {}, bo, &hk));
+    }
     bid_precond* P = new (std::nothrow) bid_precond();
     if (!P) return set_error(BID_ENOMEM, "host allocation failed");
     P->sys = s;
     P->opts = *o;
     P->gamma = gamma;
-    int rc = upload_hfactor(h1, o->precision, &P->F1);
-    if (rc == BID_OK) rc = upload_hfactor(hk, o->precision, &P->FK);
+    P->mg = mg;
+    int rc = BID_OK;
+    if (mg) {
+        rc = upload_mg(m1, &P->M1);
+        if (rc == BID_OK) rc = upload_mg(mk, &P->MK);
+    } else {
+        rc = upload_hfactor(h1, o->precision, &P->F1);
+        if (rc == BID_OK) rc = upload_hfactor(hk, o->precision, &P->FK);
+    }
     const int64_t N = H.N, NH = H.NH, n = N + NH;
     if (rc == BID_OK) rc = dalloc(&P->r, n);
     if (rc == BID_OK) rc = dalloc(&P->z, n);
@@ -452,7 +495,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     // the masked P_1 solve of the preconditioner's second P_1 application: its
     // input is zero outside the heart nodes (vector indices < N_H)
     int64_t masked_dead = 0, masked_fwd_entries = 0;
-    if (rc == BID_OK && hsolve_mask_enabled()) {
+    if (rc == BID_OK && !mg && hsolve_mask_enabled()) {
         std::vector<uint8_t> vlive(N, 0);
         std::fill(vlive.begin(), vlive.begin() + NH, (uint8_t)1);
         rc = upload_liveness(h1, vlive, &P->F1);
@@ -470,7 +513,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
                 masked_fwd_entries += (int64_t)h1.lr[g].k * (h1.lr[g].m + sn.ni);
         }
     }
-    if (rc == BID_OK && hsolve_mask_enabled()) rc = hsolve_ones(launch_of(s, nullptr), &P->F1, P->hs, N);
+    if (rc == BID_OK && !mg && hsolve_mask_enabled()) rc = hsolve_ones(launch_of(s, nullptr), &P->F1, P->hs, N);
     if (rc != BID_OK) {
         bid_destroy_precond(P);
         return rc;
@@ -502,7 +545,23 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     };
     st.large_levels1 = large_levels(h1);
     st.large_levelsk = large_levels(hk);
-    if (hsolve_mask_enabled()) {
+    if (mg) {
+        // multigrid: levels of the two hierarchies, stored matrix entries, and
+        // the algorithmic bytes of one V-cycle in place of the factor passes
+        auto entries = [](const MgHost& m) {
+            int64_t e = (int64_t)m.G.size();
+            for (const MgLevelHost& l : m.lev) e += l.A.nnz() + l.P.nnz() + l.R.nnz();
+            return e;
+        };
+        st.n1 = N;
+        st.nk = NH;
+        st.levels1 = (int32_t)m1.lev.size();
+        st.levelsk = (int32_t)mk.lev.size();
+        st.dense_entries = entries(m1) + entries(mk);
+        st.bytes_p1 = st.alg_bytes_p1 = st.alg_bytes_p1_masked = P->M1.alg_bytes;
+        st.bytes_pk = st.alg_bytes_pk = P->MK.alg_bytes;
+        st.factor_bytes = 2 * st.alg_bytes_p1 + st.alg_bytes_pk;
+    } else if (hsolve_mask_enabled()) {
         const int esz = o->precision == BID_FP64 ? 8 : o->precision == BID_FP32 ? 4 : 2;
         st.masked_dead1 = masked_dead;
         st.masked_clusters1 = (int64_t)h1.sn.size();
@@ -552,9 +611,9 @@ int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void
     Launch L = launch_of(P->sys, stream);
     if (which == 1) {
         BID_TRY(launch_sum(L, P->sys->host.N, b, &P->sc->sum_a, &P->sc->ticket[5], P->partials));
-        return launch_hsolve(L, P->F1, b, &P->sc->sum_a, 1.0 / (double)P->sys->host.N, P->hs, x);
+        return apply_p1(P, L, b, &P->sc->sum_a, x);
     }
-    if (which == 2) return launch_hsolve(L, P->FK, b, nullptr, 0.0, P->hs, x);
+    if (which == 2) return apply_pk(P, L, b, x);
     return set_error(BID_EINVAL, "which must be 1 or 2");
 }
 
@@ -583,8 +642,7 @@ int bid_profile_classes(bid_precond* P, int reps, double* ms, void* stream) {
     if (!P || !ms || reps < 1) return set_error(BID_EINVAL, "bad argument");
     bid_system* s = P->sys;
     const int64_t N = s->host.N, NH = s->host.NH, n = N + NH;
-    const double invN = 1.0 / (double)N;
-    const int flexible = P->opts.precision != BID_FP64;
+    const int flexible = P->opts.precision != BID_FP64 || P->mg;
     cudaStream_t st = (cudaStream_t)stream;
     Launch L = launch_of(s, stream);
     // finite work vectors (byte pattern 0x3F: about 4.8e-4 in every entry);
@@ -613,11 +671,11 @@ int bid_profile_classes(bid_precond* P, int reps, double* ms, void* stream) {
             return launch_lambda(L, 0, N, NH, s->S1, s->Si, s->mH, P->gamma, P->p, P->q, nullptr, P->sc,
                                  P->partials);
         case 1:
-            return launch_hsolve(L, P->F1, P->r, &P->sc->sumr, invN, P->hs, P->z);
+            return apply_p1(P, L, P->r, &P->sc->sumr, P->z);
         case 2:
-            return launch_hsolve_masked(L, P->F1, P->w, &P->sc->sum_b, invN, P->hs, P->z1b);
+            return apply_p1_masked(P, L, P->w, &P->sc->sum_b, P->z1b);
         case 3:
-            return launch_hsolve(L, P->FK, P->t, nullptr, 0.0, P->hs, P->z + N);
+            return apply_pk(P, L, P->t, P->z + N);
         case 4:
             BID_TRY(launch_si_residual(L, NH, s->Si, P->r + N, P->z, P->t));
             BID_TRY(launch_si_apply_sum(L, N, NH, s->Si, P->z + N, P->w, P->sc, P->partials));
@@ -785,6 +843,8 @@ void bid_destroy_precond(bid_precond* P) {
     if (!P) return;
     free_hfactor(&P->F1);
     free_hfactor(&P->FK);
+    free_mg(&P->M1);
+    free_mg(&P->MK);
     for (double* p : {P->r, P->z, P->p, P->q, P->xs, P->ytmp, P->z1b, P->t, P->w, P->vstar, P->hs.ybuf,
                       P->hs.xp, P->hs.inb, P->hs.vbuf, P->hs.tbuf, P->hs.pbuf, P->partials})
         cudaFree(p);

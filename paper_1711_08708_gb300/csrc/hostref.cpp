@@ -280,6 +280,27 @@ int bid_host_csr(const bid_host_system* h, int which, int64_t* ptr, int32_t* col
     return BID_OK;
 }
 
+int bid_host_mg_solve(const bid_host_system* h, int which, double gamma, const double* b, double* x,
+                      int32_t* levels) {
+    if (!h || !b || !x || (which != 1 && which != 2)) return set_error(BID_EINVAL, "bad argument");
+    const AssembledHost& a = h->a;
+    Lattice lat;
+    BID_TRY(lattice_of(a.coords.data(), a.N, a.dim, &lat));
+    MgHost M;
+    if (which == 1) {
+        BID_TRY(build_mg(a.S1, a.coords.data(), lat, true, &M));
+    } else {
+        CsrHost K = a.Sm;
+        for (int64_t r = 0; r < K.n; ++r)
+            for (int64_t q = K.ptr[r]; q < K.ptr[r + 1]; ++q)
+                if (K.col[q] == r) K.val[q] += gamma * a.mH[r];
+        BID_TRY(build_mg(K, a.coords.data(), lat, false, &M));
+    }
+    mg_vcycle_host(M, b, which == 1, x);
+    if (levels) *levels = (int32_t)M.lev.size();
+    return BID_OK;
+}
+
 int bid_host_factor_solve(const bid_host_system* h, int which, double gamma, double eps, int leaf,
                           int block, int precision, const double* b, double* x,
                           bid_precond_stats* stats) {

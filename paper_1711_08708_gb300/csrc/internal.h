@@ -51,6 +51,12 @@ struct SellDev {
     int64_t stored = 0;        // stored entries including padding
 };
 
+// Upload a CSR matrix as sliced ELLPACK (32-row slices) / free it.  Padding
+// entries read column = their row, or column 0 for rows at or beyond ncols
+// (rectangular matrices with fewer columns than rows; ncols < 0: square).
+int upload_sell(const CsrHost& A, SellDev* d, int64_t ncols = -1);
+void free_sell(SellDev* d);
+
 // ---------------------------------------------------------------- assembly
 struct AssembledHost {
     int dim = 0;
@@ -336,6 +342,82 @@ struct HScratch {
                                         // (2 words, zero initially)
 };
 
+// ---------------------------------------------------------------- geometric multigrid
+// Alternative elliptic solver for P_1 and P_K (the paper admits any
+// preconditioner of S_1 and K there): one V-cycle of geometric multigrid on a
+// mesh whose nodes form a regular lattice and whose simplices are the Kuhn
+// (Freudenthal) simplices of its cells (2D: every square cut along its "/"
+// diagonal; 3D: six tetrahedra around the main diagonal).  Coarse level =
+// the lattice points with all indices even; prolongation = P1 interpolation
+// (a fine point with odd indices is the midpoint of the coarse points
+// floor(i/2) and floor(i/2) + (i mod 2), an edge of the coarse Kuhn
+// triangulation), entries whose coarse point is missing from the node set are
+// dropped (the heart sub-lattice of P_K); coarse operators A_c = P^T A P
+// (Galerkin, symmetrised); smoother: Chebyshev polynomial of degree MG_DEGREE
+// in D^-1 A on [MG_LOW lmax, MG_HIGH lmax], lmax from MG_POWER power
+// iterations; coarsest level (at most MG_COARSEST points): explicit dense
+// inverse, or for the singular S_1 the pseudo-inverse (I - J) E A_pin^-1 E (I - J)
+// (last point pinned, E zeroes it, J the mean).
+constexpr int MG_DEGREE = 2;
+constexpr double MG_LOW = 0.3, MG_HIGH = 1.1;
+constexpr int MG_POWER = 20;
+constexpr int MG_COARSEST = 512;
+constexpr int MG_MAX_LEVELS = 24;
+
+struct MgLevelHost {
+    int64_t n = 0;
+    CsrHost A;                   // level operator (symmetric)
+    std::vector<double> dinv;    // 1 / diag(A)
+    CsrHost P, R;                // prolongation (n x n_coarse) and its transpose (absent on the coarsest)
+    double lmax = 0.0;           // power-iteration estimate of the largest eigenvalue of D^-1 A
+};
+struct MgHost {
+    std::vector<MgLevelHost> lev;
+    std::vector<double> G;       // coarsest-level inverse (nc x nc, row-major)
+    int64_t nc = 0;
+    bool singular = false;
+};
+// Lattice of the mesh nodes (coordinates of all N nodes, library order).
+struct Lattice {
+    int dim = 0;
+    double x0[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+};
+int lattice_of(const double* coords, int64_t n, int dim, Lattice* L);
+// Hierarchy for A (rows = the first A.n nodes of the mesh, coords in library
+// order); singular: A is the Neumann S_1 (kernel = constants).  EINVAL when
+// the nodes are not lattice points or A couples points that are not Kuhn
+// neighbours.
+int build_mg(const CsrHost& A, const double* coords, const Lattice& L, bool singular, MgHost* out);
+// One V-cycle on the host in FP64, the device algorithm's order of operations
+// per entry (reference for tests): x = V(b - shift) with shift = mean(b) when
+// `project`, x projected onto 1^perp for the singular hierarchy.
+void mg_vcycle_host(const MgHost& M, const double* b, bool project, double* x);
+// Chebyshev coefficients of level lmax: theta, and (c1, c2) of step 2.
+void mg_cheb_coeffs(double lmax, double* theta, double* c1, double* c2);
+
+struct MgLevelDev {
+    int64_t n = 0;
+    SellDev A, P, R;
+    double* dinv = nullptr;
+    double lmax = 0.0;
+    double *x = nullptr, *y = nullptr, *b = nullptr, *r = nullptr, *d = nullptr;   // work vectors
+    double* e = nullptr;         // this level's V-cycle result (the coarse correction of the level above)
+};
+struct MgDev {
+    std::vector<MgLevelDev> lev;
+    double* G = nullptr;
+    int64_t nc = 0;
+    bool singular = false;
+    int64_t alg_bytes = 0;       // algorithmic bytes of one V-cycle
+};
+struct Launch;
+int upload_mg(const MgHost& h, MgDev* d);
+void free_mg(MgDev* d);
+// x = V-cycle(in - shift), shift = *shift_sum * inv_n when shift_sum != NULL;
+// singular hierarchies return x with zero mean.
+int launch_mg(const Launch& L, const MgDev& M, const double* in, const double* shift_sum, double inv_n,
+              double* x);
+
 // ---------------------------------------------------------------- device scalars
 // Scalars of the PCG recurrences, kept on the device so that no kernel needs a
 // host round trip.  Reductions are deterministic (fixed order).
@@ -537,6 +619,8 @@ struct bid_precond {
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double *z1b = nullptr, *t = nullptr, *w = nullptr, *ytmp = nullptr, *xs = nullptr;
     double* vstar = nullptr;                  // Strang scheme: V after the first reaction half step
+    bool mg = false;                          // P_1, P_K by multigrid V-cycles (M1, MK), not F1, FK
+    bid::MgDev M1, MK;
     bid::HScratch hs;
     double* partials = nullptr;
     bid::DevScalars* sc = nullptr;

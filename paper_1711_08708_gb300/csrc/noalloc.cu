@@ -53,6 +53,7 @@ extern "C" int bid_apply_factor_noalloc(bid_precond* P, int which, const double*
                                         void* stream) {
     if (!P || !b || !x || b == x) return set_error(BID_EINVAL, "bad argument");
     if (which != 1 && which != 2) return set_error(BID_EINVAL, "which must be 1 or 2");
+    if (P->mg) return set_error(BID_EINVAL, "the allocation-free solve applies hierarchical factors only");
     const HFactorDev& F = which == 1 ? P->F1 : P->FK;
     const int64_t red = (int64_t)P->sys->sms * 8 + 2;      // block partials + sum + ticket
     const int64_t tick = (F.ntickets + 2) / 2;              // tickets packed two per double
