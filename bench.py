@@ -67,7 +67,7 @@ def parse():
                    help="time scheme of the slice and slab workloads")
     a.add_argument("--elliptic", default="hchol", choices=["hchol", "mg"],
                    help="P_1 / P_K by hierarchical Cholesky factors or multigrid V-cycles "
-                        "(mg: FP64, --eps and --precision not used)")
+                        "(mg: --precision fp64 or fp32 storage, --eps not used)")
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
@@ -680,7 +680,7 @@ def main():
 
     # ---- chosen form
     if args.elliptic == "mg":
-        args.eps, args.precision = 0.0, "fp64"
+        args.eps = 0.0
     P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf,
                     scheme=args.scheme, elliptic=args.elliptic)
     chosen_stats = dict(P.stats)
@@ -776,7 +776,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f64 PCG / f64 multigrid V-cycles" if args.elliptic == "mg" else
+        "dtype": (f"f64 PCG / {args.precision} multigrid V-cycles" if args.elliptic == "mg" else
                   f"f64 PCG / {args.precision} factors" + (f" (eps {args.eps:g})" if args.eps else "")),
         "data": "synthetic",
         "config": {

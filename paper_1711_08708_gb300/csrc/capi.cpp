@@ -413,7 +413,8 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (o->elliptic != BID_ELLIPTIC_HCHOL && o->elliptic != BID_ELLIPTIC_MG)
         return set_error(BID_EINVAL, "bad elliptic solver");
     const bool mg = o->elliptic == BID_ELLIPTIC_MG;
-    if (mg && o->precision != BID_FP64) return set_error(BID_EINVAL, "the multigrid preconditioner runs in FP64 only");
+    if (mg && o->precision == BID_BF16)
+        return set_error(BID_EINVAL, "the multigrid preconditioner stores FP64 or FP32 only");
     auto t0 = std::chrono::steady_clock::now();
     BID_TRY(hsolve_prepare());
     const AssembledHost& H = s->host;
@@ -454,8 +455,8 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     P->mg = mg;
     int rc = BID_OK;
     if (mg) {
-        rc = upload_mg(m1, &P->M1);
-        if (rc == BID_OK) rc = upload_mg(mk, &P->MK);
+        rc = upload_mg(m1, o->precision, &P->M1);
+        if (rc == BID_OK) rc = upload_mg(mk, o->precision, &P->MK);
     } else {
         rc = upload_hfactor(h1, o->precision, &P->F1);
         if (rc == BID_OK) rc = upload_hfactor(hk, o->precision, &P->FK);

@@ -395,23 +395,35 @@ void mg_vcycle_host(const MgHost& M, const double* b, bool project, double* x);
 // Chebyshev coefficients of level lmax: theta, and (c1, c2) of step 2.
 void mg_cheb_coeffs(double lmax, double* theta, double* c1, double* c2);
 
+// A level matrix in sliced ELLPACK (32-row slices) with values in the
+// hierarchy's storage type (double or float).
+struct MgMat {
+    int32_t n = 0, nslices = 0;
+    int32_t* sptr = nullptr;
+    int32_t* col = nullptr;
+    void* val = nullptr;
+};
+// Device hierarchy; matrices, 1/diag, the coarsest inverse and the work
+// vectors are stored (and the products accumulated) in FP64 or FP32
+// (`precision`); the cycle's input and output vectors are FP64.
 struct MgLevelDev {
     int64_t n = 0;
-    SellDev A, P, R;
-    double* dinv = nullptr;
+    MgMat A, P, R;
+    void* dinv = nullptr;
     double lmax = 0.0;
-    double *x = nullptr, *y = nullptr, *b = nullptr, *r = nullptr, *d = nullptr;   // work vectors
-    double* e = nullptr;         // this level's V-cycle result (the coarse correction of the level above)
+    void *x = nullptr, *y = nullptr, *b = nullptr, *r = nullptr, *d = nullptr;   // work vectors
+    void* e = nullptr;           // this level's V-cycle result (the coarse correction of the level above)
 };
 struct MgDev {
     std::vector<MgLevelDev> lev;
-    double* G = nullptr;
+    void* G = nullptr;
     int64_t nc = 0;
     bool singular = false;
+    int precision = BID_FP64;    // BID_FP64 or BID_FP32
     int64_t alg_bytes = 0;       // algorithmic bytes of one V-cycle
 };
 struct Launch;
-int upload_mg(const MgHost& h, MgDev* d);
+int upload_mg(const MgHost& h, int precision, MgDev* d);
 void free_mg(MgDev* d);
 // x = V-cycle(in - shift), shift = *shift_sum * inv_n when shift_sum != NULL;
 // singular hierarchies return x with zero mean.

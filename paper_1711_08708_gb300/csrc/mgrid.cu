@@ -4,9 +4,12 @@
 // coarse correction, the prolongation x += P e and a Chebyshev post-smoothing
 // of degree 2 with the same polynomial (so the cycle is a symmetric operator);
 // the coarsest level applies its dense inverse.  Every matrix is sliced
-// ELLPACK (32-row slices, one warp per slice), FP64; every kernel is a plain
+// ELLPACK (32-row slices, one warp per slice); every kernel is a plain
 // bandwidth-bound pass (HBM roofline), launched in stream order so that the
-// PCG loop captures the whole cycle in its graph.
+// PCG loop captures the whole cycle in its graph.  Matrices and work vectors
+// are stored, and products accumulated, in the hierarchy's type V (FP64, or
+// FP32 for the precision form, which halves the vector bytes and cuts the
+// matrix bytes by a third); the cycle's input and output are FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,18 +22,23 @@ namespace {
 
 constexpr int MT = 256;
 
-struct SView {
+template <typename V>
+struct MView {
     int32_t n, nslices;
     const int32_t* __restrict__ sptr;
     const int32_t* __restrict__ col;
-    const double* __restrict__ val;
+    const V* __restrict__ val;
 };
-SView sview(const SellDev& s) { return SView{s.n, s.nslices, s.sptr, s.col, s.val}; }
+template <typename V>
+MView<V> mview(const MgMat& m) {
+    return MView<V>{m.n, m.nslices, m.sptr, m.col, static_cast<const V*>(m.val)};
+}
 
-// row r = 32 sl + lane of A times x
-__device__ __forceinline__ double row_dot(const SView& A, int sl, int lane, const double* __restrict__ x) {
+// row 32 sl + lane of A times x
+template <typename V>
+__device__ __forceinline__ V row_dot(const MView<V>& A, int sl, int lane, const V* __restrict__ x) {
     const int b = A.sptr[sl], w = (A.sptr[sl + 1] - b) >> 5;
-    double s = 0.0;
+    V s = 0;
     for (int k = 0; k < w; ++k) {
         const int idx = b + k * 32 + lane;
         s += A.val[idx] * x[A.col[idx]];
@@ -38,17 +46,24 @@ __device__ __forceinline__ double row_dot(const SView& A, int sl, int lane, cons
     return s;
 }
 
-// first Chebyshev step from x = 0: b = in - shift (level 0 writes b), d = D^-1 b / theta, x = d
-__global__ void __launch_bounds__(MT) k_mg_first(int n, const double* __restrict__ in,
+// First Chebyshev step from x = 0: d = D^-1 b / theta, x = d.  At level 0
+// the right-hand side is the FP64 input minus the shift, stored into b
+// (in0 != NULL); below, b is the restricted residual.
+template <typename V>
+__global__ void __launch_bounds__(MT) k_mg_first(int n, const double* __restrict__ in0,
                                                  const double* __restrict__ shift_sum, double inv_n,
-                                                 const double* __restrict__ dinv, double inv_theta,
-                                                 double* __restrict__ b, double* __restrict__ x,
-                                                 double* __restrict__ d) {
+                                                 const V* __restrict__ dinv, V inv_theta, V* b,
+                                                 V* __restrict__ x, V* __restrict__ d) {
     const double sh = shift_sum ? *shift_sum * inv_n : 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double bi = in[i] - sh;
-        if (b != in) b[i] = bi;
-        const double di = inv_theta * (dinv[i] * bi);
+        V bi;
+        if (in0) {
+            bi = (V)(in0[i] - sh);
+            b[i] = bi;
+        } else {
+            bi = b[i];
+        }
+        const V di = inv_theta * (dinv[i] * bi);
         d[i] = di;
         x[i] = di;
     }
@@ -56,63 +71,66 @@ __global__ void __launch_bounds__(MT) k_mg_first(int n, const double* __restrict
 
 // Chebyshev step: d = c1 d + c2 D^-1 (b - A xin), xout = xin + d (c1 = 0: d's
 // old value unused)
-__global__ void __launch_bounds__(MT) k_mg_cheb(SView A, const double* __restrict__ dinv,
-                                                const double* __restrict__ b, const double* __restrict__ xin,
-                                                double* __restrict__ xout, double* __restrict__ d, double c1,
-                                                double c2) {
+template <typename V, typename O>
+__global__ void __launch_bounds__(MT) k_mg_cheb(MView<V> A, const V* __restrict__ dinv, const V* __restrict__ b,
+                                                const V* __restrict__ xin, O* __restrict__ xout,
+                                                V* __restrict__ d, V c1, V c2) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int sl = gw; sl < A.nslices; sl += nw) {
-        const double ax = row_dot(A, sl, lane, xin);
+        const V ax = row_dot(A, sl, lane, xin);
         const int r = sl * 32 + lane;
         if (r >= A.n) continue;
-        const double res = b[r] - ax;
-        const double dn = (c1 != 0.0 ? c1 * d[r] : 0.0) + c2 * (dinv[r] * res);
+        const V res = b[r] - ax;
+        const V dn = (c1 != (V)0 ? c1 * d[r] : (V)0) + c2 * (dinv[r] * res);
         d[r] = dn;
-        xout[r] = xin[r] + dn;
+        xout[r] = (O)(xin[r] + dn);
     }
 }
 
 // r = b - A x
-__global__ void __launch_bounds__(MT) k_mg_resid(SView A, const double* __restrict__ b,
-                                                 const double* __restrict__ x, double* __restrict__ r) {
+template <typename V>
+__global__ void __launch_bounds__(MT) k_mg_resid(MView<V> A, const V* __restrict__ b, const V* __restrict__ x,
+                                                 V* __restrict__ r) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int sl = gw; sl < A.nslices; sl += nw) {
-        const double ax = row_dot(A, sl, lane, x);
+        const V ax = row_dot(A, sl, lane, x);
         const int i = sl * 32 + lane;
         if (i < A.n) r[i] = b[i] - ax;
     }
 }
 
-// y = M x (mode 0) or y += M x (mode 1): the restriction (M = P^T) and the
+// y = M x (add = 0) or y += M x (add = 1): the restriction (M = P^T) and the
 // prolongation (M = P)
-__global__ void __launch_bounds__(MT) k_mg_apply(SView M, const double* __restrict__ x, double* __restrict__ y,
+template <typename V>
+__global__ void __launch_bounds__(MT) k_mg_apply(MView<V> M, const V* __restrict__ x, V* __restrict__ y,
                                                  int add) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int sl = gw; sl < M.nslices; sl += nw) {
-        const double s = row_dot(M, sl, lane, x);
+        const V s = row_dot(M, sl, lane, x);
         const int i = sl * 32 + lane;
         if (i < M.n) y[i] = add ? y[i] + s : s;
     }
 }
 
 // coarsest level: x = G b (one warp per row)
-__global__ void __launch_bounds__(MT) k_mg_dense(int n, const double* __restrict__ G, const double* __restrict__ b,
-                                                 double* __restrict__ x) {
+template <typename V, typename O>
+__global__ void __launch_bounds__(MT) k_mg_dense(int n, const V* __restrict__ G, const V* __restrict__ b,
+                                                 O* __restrict__ x) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = gw; i < n; i += nw) {
-        double s = 0.0;
+        V s = 0;
         for (int j = lane; j < n; j += 32) s += G[(size_t)i * n + j] * b[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) x[i] = s;
+        if (lane == 0) x[i] = (O)s;
     }
 }
 
@@ -129,41 +147,144 @@ int checked(const char* what) {
     return BID_OK;
 }
 
-// V-cycle at level l on b, result in out (distinct from the level's buffers).
-int vcycle(const Launch& L, const MgDev& M, size_t l, const double* in, const double* shift_sum,
-           double inv_n, double* out) {
-    const MgLevelDev& V = M.lev[l];
-    const int n = (int)V.n;
+// V-cycle at level l.  Level 0 reads the FP64 input in0 (minus the shift) and
+// writes the FP64 result out0; a coarser level reads its b (the restricted
+// residual) and writes its e.
+template <typename V>
+int vcycle(const Launch& L, const MgDev& M, size_t l, const double* in0, const double* shift_sum,
+           double inv_n, double* out0) {
+    const MgLevelDev& W = M.lev[l];
+    const int n = (int)W.n;
+    V* b = static_cast<V*>(W.b);
+    V* x = static_cast<V*>(W.x);
+    V* y = static_cast<V*>(W.y);
+    V* d = static_cast<V*>(W.d);
+    V* e = static_cast<V*>(W.e);
+    const V* dinv = static_cast<const V*>(W.dinv);
     if (l + 1 == M.lev.size()) {
-        if (shift_sum) {   // a one-level hierarchy: shift into b first
-            k_mg_first<<<grid_of(L, n), MT, 0, L.st>>>(n, in, shift_sum, inv_n, V.dinv, 0.0, V.b, V.x, V.d);
+        if (in0) {   // a one-level hierarchy: the shifted input into b first
+            k_mg_first<V><<<grid_of(L, n), MT, 0, L.st>>>(n, in0, shift_sum, inv_n, dinv, (V)0, b, x, d);
             BID_TRY(checked("mg_first"));
-            in = V.b;
         }
-        k_mg_dense<<<grid_of(L, (int64_t)n * 32), MT, 0, L.st>>>(n, M.G, in, out);
+        const V* G = static_cast<const V*>(M.G);
+        if (out0) k_mg_dense<V, double><<<grid_of(L, (int64_t)n * 32), MT, 0, L.st>>>(n, G, b, out0);
+        else k_mg_dense<V, V><<<grid_of(L, (int64_t)n * 32), MT, 0, L.st>>>(n, G, b, e);
         return checked("mg_dense");
     }
     double th, c1, c2;
-    mg_cheb_coeffs(V.lmax, &th, &c1, &c2);
-    const SView A = sview(V.A);
-    const int gs = grid_of(L, (int64_t)V.A.nslices * 32);
-    double* b = l == 0 ? V.b : const_cast<double*>(in);
-    k_mg_first<<<grid_of(L, n), MT, 0, L.st>>>(n, in, shift_sum, inv_n, V.dinv, 1.0 / th, b, V.x, V.d);
+    mg_cheb_coeffs(W.lmax, &th, &c1, &c2);
+    const MView<V> A = mview<V>(W.A);
+    const int gs = grid_of(L, (int64_t)W.A.nslices * 32);
+    k_mg_first<V><<<grid_of(L, n), MT, 0, L.st>>>(n, in0, shift_sum, inv_n, dinv, (V)(1.0 / th), b, x, d);
     BID_TRY(checked("mg_first"));
-    k_mg_cheb<<<gs, MT, 0, L.st>>>(A, V.dinv, b, V.x, V.y, V.d, c1, c2);
+    k_mg_cheb<V, V><<<gs, MT, 0, L.st>>>(A, dinv, b, x, y, d, (V)c1, (V)c2);
     BID_TRY(checked("mg_cheb"));
-    k_mg_resid<<<gs, MT, 0, L.st>>>(A, b, V.y, V.r);
+    k_mg_resid<V><<<gs, MT, 0, L.st>>>(A, b, y, static_cast<V*>(W.r));
     BID_TRY(checked("mg_resid"));
     const MgLevelDev& C = M.lev[l + 1];
-    k_mg_apply<<<grid_of(L, (int64_t)V.R.nslices * 32), MT, 0, L.st>>>(sview(V.R), V.r, C.b, 0);
+    k_mg_apply<V><<<grid_of(L, (int64_t)W.R.nslices * 32), MT, 0, L.st>>>(mview<V>(W.R), static_cast<V*>(W.r),
+                                                                          static_cast<V*>(C.b), 0);
     BID_TRY(checked("mg_restrict"));
-    BID_TRY(vcycle(L, M, l + 1, C.b, nullptr, 0.0, C.e));
-    k_mg_apply<<<grid_of(L, (int64_t)V.P.nslices * 32), MT, 0, L.st>>>(sview(V.P), C.e, V.y, 1);
+    BID_TRY(vcycle<V>(L, M, l + 1, nullptr, nullptr, 0.0, nullptr));
+    k_mg_apply<V><<<grid_of(L, (int64_t)W.P.nslices * 32), MT, 0, L.st>>>(mview<V>(W.P), static_cast<V*>(C.e),
+                                                                          y, 1);
     BID_TRY(checked("mg_prolong"));
-    k_mg_cheb<<<gs, MT, 0, L.st>>>(A, V.dinv, b, V.y, V.x, V.d, 0.0, 1.0 / th);
+    k_mg_cheb<V, V><<<gs, MT, 0, L.st>>>(A, dinv, b, y, x, d, (V)0, (V)(1.0 / th));
     BID_TRY(checked("mg_cheb"));
-    k_mg_cheb<<<gs, MT, 0, L.st>>>(A, V.dinv, b, V.x, out, V.d, c1, c2);
+    if (out0) k_mg_cheb<V, double><<<gs, MT, 0, L.st>>>(A, dinv, b, x, out0, d, (V)c1, (V)c2);
+    else k_mg_cheb<V, V><<<gs, MT, 0, L.st>>>(A, dinv, b, x, e, d, (V)c1, (V)c2);
     return checked("mg_cheb");
+}
+
+// Sliced ELLPACK of a CSR matrix with values of type V.  Padding entries have
+// value 0 and read column = their row (square) or column 0 (rows at or beyond
+// ncols), always inside the vector they multiply.
+template <typename V>
+int upload_mat(const CsrHost& A, int64_t ncols, MgMat* d) {
+    const int64_t n = A.n;
+    const int32_t ns = (int32_t)((n + 31) / 32);
+    std::vector<int32_t> sptr(ns + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) {
+        int64_t w = 0;
+        for (int64_t r = (int64_t)s * 32; r < std::min<int64_t>(n, (int64_t)s * 32 + 32); ++r)
+            w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
+        if ((int64_t)sptr[s] + w * 32 > INT32_MAX) return set_error(BID_EINVAL, "multigrid matrix too large");
+        sptr[s + 1] = sptr[s] + (int32_t)(w * 32);
+    }
+    std::vector<int32_t> col(std::max<int32_t>(sptr[ns], 1), 0);
+    std::vector<V> val(std::max<int32_t>(sptr[ns], 1), (V)0);
+    for (int32_t s = 0; s < ns; ++s) {
+        const int32_t w = (sptr[s + 1] - sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t r = (int64_t)s * 32 + l;
+            const int64_t len = r < n ? A.ptr[r + 1] - A.ptr[r] : 0;
+            for (int k = 0; k < w; ++k) {
+                const int64_t idx = sptr[s] + (int64_t)k * 32 + l;
+                if (k < len) {
+                    col[idx] = A.col[A.ptr[r] + k];
+                    val[idx] = (V)A.val[A.ptr[r] + k];
+                } else {
+                    col[idx] = (r < n && r < ncols) ? (int32_t)r : 0;
+                }
+            }
+        }
+    }
+    d->n = (int32_t)n;
+    d->nslices = ns;
+    BID_CUDA_TRY(cudaMalloc(&d->sptr, sizeof(int32_t) * (ns + 1)));
+    BID_CUDA_TRY(cudaMalloc(&d->col, sizeof(int32_t) * col.size()));
+    BID_CUDA_TRY(cudaMalloc(&d->val, sizeof(V) * val.size()));
+    BID_CUDA_TRY(cudaMemcpy(d->sptr, sptr.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice));
+    BID_CUDA_TRY(cudaMemcpy(d->col, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice));
+    BID_CUDA_TRY(cudaMemcpy(d->val, val.data(), sizeof(V) * val.size(), cudaMemcpyHostToDevice));
+    return BID_OK;
+}
+
+template <typename V>
+int upload_vals(const std::vector<double>& h, void** d) {
+    std::vector<V> v(std::max<size_t>(h.size(), 1), (V)0);
+    for (size_t i = 0; i < h.size(); ++i) v[i] = (V)h[i];
+    BID_CUDA_TRY(cudaMalloc(d, sizeof(V) * v.size()));
+    BID_CUDA_TRY(cudaMemcpy(*d, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice));
+    return BID_OK;
+}
+
+template <typename V>
+int upload_typed(const MgHost& h, MgDev* d) {
+    constexpr int64_t E = sizeof(V), M = 4 + sizeof(V);   // vector entry, matrix entry (value + column)
+    int64_t bytes = 0;
+    for (size_t l = 0; l < h.lev.size(); ++l) {
+        const MgLevelHost& H = h.lev[l];
+        d->lev.emplace_back();
+        MgLevelDev& D = d->lev.back();
+        D.n = H.n;
+        D.lmax = H.lmax;
+        BID_TRY(upload_mat<V>(H.A, H.n, &D.A));
+        const bool last = l + 1 == h.lev.size();
+        if (!last) {
+            BID_TRY(upload_mat<V>(H.P, h.lev[l + 1].n, &D.P));
+            BID_TRY(upload_mat<V>(H.R, H.n, &D.R));
+        }
+        BID_TRY(upload_vals<V>(H.dinv, &D.dinv));
+        for (void** p : {&D.x, &D.y, &D.b, &D.r, &D.d, &D.e})
+            BID_CUDA_TRY(cudaMalloc(p, sizeof(V) * std::max<int64_t>(H.n, 1)));
+        // algorithmic bytes: every matrix entry (value and column) and vector
+        // entry moved once per kernel; the cycle's input and output in FP64
+        const int64_t n = H.n, a = M * H.A.nnz();
+        if (!last) {
+            const int64_t nc = h.lev[l + 1].n;
+            bytes += (l == 0 ? 8 + 4 * E : 4 * E) * n;                // first step
+            bytes += 3 * a + (l == 0 ? 17 * E + 8 : 18 * E) * n;      // three Chebyshev steps
+            bytes += a + 3 * E * n;                                   // residual
+            bytes += M * H.R.nnz() + E * (n + nc);                    // restriction
+            bytes += M * H.P.nnz() + E * (nc + 2 * n);                // prolongation
+        } else {
+            bytes += E * n * n + 2 * E * n + (l == 0 ? 16 * n : 0);   // dense inverse
+        }
+    }
+    BID_TRY(upload_vals<V>(h.G, &d->G));
+    d->alg_bytes = bytes;
+    return BID_OK;
 }
 
 }  // namespace
@@ -171,56 +292,28 @@ int vcycle(const Launch& L, const MgDev& M, size_t l, const double* in, const do
 int launch_mg(const Launch& L, const MgDev& M, const double* in, const double* shift_sum, double inv_n,
               double* x) {
     if (M.lev.empty()) return set_error(BID_EINVAL, "empty multigrid hierarchy");
-    return vcycle(L, M, 0, in, shift_sum, inv_n, x);
+    if (M.precision == BID_FP32) return vcycle<float>(L, M, 0, in, shift_sum, inv_n, x);
+    return vcycle<double>(L, M, 0, in, shift_sum, inv_n, x);
 }
 
-int upload_mg(const MgHost& h, MgDev* d) {
+int upload_mg(const MgHost& h, int precision, MgDev* d) {
     *d = MgDev();
     d->singular = h.singular;
     d->nc = h.nc;
-    int64_t bytes = 0;
-    for (size_t l = 0; l < h.lev.size(); ++l) {
-        const MgLevelHost& H = h.lev[l];
-        MgLevelDev V;
-        V.n = H.n;
-        V.lmax = H.lmax;
-        d->lev.push_back(V);
-        MgLevelDev& D = d->lev.back();
-        BID_TRY(upload_sell(H.A, &D.A));
-        if (l + 1 < h.lev.size()) {
-            BID_TRY(upload_sell(H.P, &D.P, h.lev[l + 1].n));
-            BID_TRY(upload_sell(H.R, &D.R));
-        }
-        const size_t vb = sizeof(double) * std::max<int64_t>(H.n, 1);
-        for (double** p : {&D.dinv, &D.x, &D.y, &D.b, &D.r, &D.d, &D.e})
-            BID_CUDA_TRY(cudaMalloc(p, vb));
-        BID_CUDA_TRY(cudaMemcpy(D.dinv, H.dinv.data(), sizeof(double) * H.n, cudaMemcpyHostToDevice));
-        // algorithmic bytes: FP64 values + int32 columns of every matrix pass,
-        // vectors read or written once per kernel
-        const int64_t n = H.n, a = 12 * H.A.nnz();
-        if (l + 1 < h.lev.size()) {
-            const int64_t nc = h.lev[l + 1].n;
-            bytes += (l == 0 ? 48 : 40) * n;                 // first step
-            bytes += 3 * (a + 48 * n);                       // three Chebyshev steps
-            bytes += a + 24 * n;                             // residual
-            bytes += 12 * H.R.nnz() + 8 * n + 8 * nc;        // restriction
-            bytes += 12 * H.P.nnz() + 8 * nc + 16 * n;       // prolongation
-        } else {
-            bytes += 8 * n * n + 16 * n;                     // dense inverse
-        }
-    }
-    BID_CUDA_TRY(cudaMalloc(&d->G, sizeof(double) * std::max<size_t>(h.G.size(), 1)));
-    BID_CUDA_TRY(cudaMemcpy(d->G, h.G.data(), sizeof(double) * h.G.size(), cudaMemcpyHostToDevice));
-    d->alg_bytes = bytes;
-    return BID_OK;
+    d->precision = precision;
+    if (precision == BID_FP32) return upload_typed<float>(h, d);
+    if (precision == BID_FP64) return upload_typed<double>(h, d);
+    return set_error(BID_EINVAL, "multigrid storage must be FP64 or FP32");
 }
 
 void free_mg(MgDev* d) {
     for (MgLevelDev& V : d->lev) {
-        free_sell(&V.A);
-        free_sell(&V.P);
-        free_sell(&V.R);
-        for (double* p : {V.dinv, V.x, V.y, V.b, V.r, V.d, V.e}) cudaFree(p);
+        for (MgMat* m : {&V.A, &V.P, &V.R}) {
+            cudaFree(m->sptr);
+            cudaFree(m->col);
+            cudaFree(m->val);
+        }
+        for (void* p : {V.dinv, V.x, V.y, V.b, V.r, V.d, V.e}) cudaFree(p);
     }
     cudaFree(d->G);
     *d = MgDev();
