@@ -45,6 +45,9 @@
  *                    solve (BID_TREE_FROM first level, default 1;
  *                    BID_TREE_SMEM shared-memory cap, default 32768);
  *    BID_UPPER=1     the top levels run in persistent cooperative launches;
+ *    BID_FLATP=0     one CTA per flat group on every level instead of persistent
+ *                    double-buffered launches on the levels with more groups
+ *                    than resident CTAs;
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the
@@ -173,6 +176,9 @@ typedef struct bid_precond_stats {
     int64_t alg_bytes_p1_masked;       /* algorithmic bytes of one masked P_1 solve: the
                                           forward blocks of the live clusters and the whole
                                           backward pass (alg_bytes_p1 with BID_MASK=0) */
+    int32_t flatp_levels1, flatp_levelsk;  /* flat levels solved by persistent double-
+                                          buffered launches (more groups than resident
+                                          CTAs), forward pass; 0 with BID_FLATP=0 */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {

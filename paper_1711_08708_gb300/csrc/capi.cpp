@@ -546,6 +546,14 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     };
     st.large_levels1 = large_levels(h1);
     st.large_levelsk = large_levels(hk);
+    auto flatp_levels = [](const HFactorDev& d) {
+        int32_t c = 0;
+        if (hsolve_flatp_enabled())
+            for (int32_t g : d.fgp_grid_f) c += g > 0;
+        return c;
+    };
+    st.flatp_levels1 = flatp_levels(P->F1);
+    st.flatp_levelsk = flatp_levels(P->FK);
     if (mg) {
         // multigrid: levels of the two hierarchies, stored matrix entries, and
         // the algorithmic bytes of one V-cycle in place of the factor passes

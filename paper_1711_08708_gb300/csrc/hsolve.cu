@@ -192,6 +192,7 @@ constexpr int PREP_BATCH = 4;       // backward staging: entries per thread whos
 constexpr int FLAT_DYN_MAX = 176 * 1024;   // group block (data + slots) of one flat group
 constexpr int FLAT_SMEM_MAX = 224 * 1024;  // with descriptors and staged inputs
 constexpr int TREE_SMEM_MAX = 96 * 1024;   // a CTA of the dataflow flat kernels
+constexpr int FLATP_BUF_MAX = 48 * 1024;   // one buffer of a persistent flat CTA (two per CTA)
 
 __device__ __forceinline__ void bulk_region(unsigned char* dst, const void* src, int nbytes,
                                             uint64_t* bar) {
@@ -483,6 +484,143 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
         return;
     }
     flat_bwd_body<T, A>(v, G, scl, nc, dyn_smem, vs, out);
+}
+
+// ------------------------------------------------------------ flat levels, persistent
+// Levels with more flat groups than resident CTAs: each CTA walks the groups
+// g = blockIdx.x, + gridDim.x, ... with two shared-memory buffers, so that the
+// bulk copy of its next group (factor block and, forward, the update slots,
+// which the lower levels wrote before this launch's pdl_wait) is in flight
+// while it computes the current one.  Per group the staging and the
+// arithmetic are those of k_flat_fwd / k_flat_bwd, so the results are the
+// same bit for bit.  Buffer layout (bufsz bytes each): group block, cluster
+// descriptors at sc_off, staged inputs at w_off.  An expired wait sets *err,
+// waits (bounded) for the other buffer's copy in flight, and returns.
+template <typename T, typename A>
+__global__ void __launch_bounds__(FT) k_flat_fwd_pb(HView v, const T* __restrict__ data, int g0, int nf,
+                                                    const double* xp, double* ybuf, double* inb,
+                                                    unsigned int* err, int bufsz, int sc_off, int w_off,
+                                                    MaskArgs mk) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int stride = gridDim.x;
+    int g = blockIdx.x;
+    uint32_t pend = 0u;   // bit b: a copy was issued into buffer b and not yet waited for
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    if (g < nf && (!mk.live || mk.live[g0 + g])) {
+        const FGroup G = v.fg[g0 + g];
+        if (threadIdx.x == 0) group_load(dyn_smem, data + G.dstart, G.nbytes, G.sbytes, &bar[0]);
+        pend = 1u;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if ((pend & 1u) && threadIdx.x == 0) {
+        const FGroup G = v.fg[g0 + g];
+        group_load_slots(dyn_smem, G.nbytes, inb + G.sstart, G.sbytes, &bar[0]);
+    }
+    __syncthreads();
+    uint32_t ph = 0u;     // bit b: phase parity of buffer b's barrier
+    for (int buf = 0; g < nf; g += stride, buf ^= 1) {
+        unsigned char* sm = dyn_smem + buf * bufsz;
+        const int gn = g + stride;
+        if (gn < nf && (!mk.live || mk.live[g0 + gn])) {   // prefetch the next group
+            if (threadIdx.x == 0) {
+                const FGroup Gn = v.fg[g0 + gn];
+                unsigned char* dn = dyn_smem + (buf ^ 1) * bufsz;
+                group_load(dn, data + Gn.dstart, Gn.nbytes, Gn.sbytes, &bar[buf ^ 1]);
+                group_load_slots(dn, Gn.nbytes, inb + Gn.sstart, Gn.sbytes, &bar[buf ^ 1]);
+            }
+            pend |= 1u << (buf ^ 1);
+        }
+        const FGroup G = v.fg[g0 + g];
+        if (mk.live && !mk.live[g0 + g]) {   // constant input -c: scaled all-ones results
+            const double c0 = mask_c0(mk);
+            for (int f = threadIdx.x; f < G.wf; f += FT)
+                ybuf[G.pstart + f] = mask_c(mk, c0, mk.seg ? v.pidx[G.pstart + f] : 0) * mk.y1[G.pstart + f];
+            for (int k = threadIdx.x; k < G.nbt; k += FT) {
+                const int32_t slot = v.uout[G.bstart + k];
+                inb[slot] = mask_c(mk, c0, mk.seg ? v.bidx[G.bstart + k] : 0) * mk.y1slot[slot];
+            }
+            continue;
+        }
+        GCl* scl = reinterpret_cast<GCl*>(sm + sc_off);
+        A* w = reinterpret_cast<A*>(sm + w_off);
+        const int nc = G.c1 - G.c0;
+        for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+        for (int f = threadIdx.x; f < G.wf; f += FT) w[f] = (A)xp[G.pstart + f];
+        __syncthreads();
+        if (!mbar_wait_bounded(&bar[buf], (ph >> buf) & 1u)) {
+            if (threadIdx.x == 0) atomicOr(err, 1u);
+            if ((pend >> (buf ^ 1)) & 1u) mbar_wait_bounded(&bar[buf ^ 1], (ph >> (buf ^ 1)) & 1u);
+            return;
+        }
+        ph ^= 1u << buf;
+        pend &= ~(1u << buf);
+        flat_fwd_body<T, A>(v, G, scl, nc, sm, w, ybuf, inb);
+        __syncthreads();   // the buffer is refilled two groups later
+    }
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(FT) k_flat_bwd_pb(HView v, const T* __restrict__ data, int g0, int nf,
+                                                    const double* __restrict__ ybuf, double* out,
+                                                    unsigned int* err, int bufsz, int sc_off, int w_off) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int stride = gridDim.x;
+    int g = blockIdx.x;
+    uint32_t pend = 0u;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        if (g < nf) {
+            const FGroup G = v.fg[g0 + g];
+            group_load(dyn_smem, data + G.dstart, G.nbytes, 0, &bar[0]);
+        }
+    }
+    pend = g < nf ? 1u : 0u;
+    pdl_wait();
+    pdl_trigger();
+    __syncthreads();
+    uint32_t ph = 0u;     // bit b: phase parity of buffer b's barrier
+    for (int buf = 0; g < nf; g += stride, buf ^= 1) {
+        unsigned char* sm = dyn_smem + buf * bufsz;
+        const int gn = g + stride;
+        if (gn < nf) {   // prefetch the next group's factor block
+            if (threadIdx.x == 0) {
+                const FGroup Gn = v.fg[g0 + gn];
+                group_load(dyn_smem + (buf ^ 1) * bufsz, data + Gn.dstart, Gn.nbytes, 0, &bar[buf ^ 1]);
+            }
+            pend |= 1u << (buf ^ 1);
+        }
+        const FGroup G = v.fg[g0 + g];
+        GCl* scl = reinterpret_cast<GCl*>(sm + sc_off);
+        A* vs = reinterpret_cast<A*>(sm + w_off);
+        const int nc = G.c1 - G.c0;
+        for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+        __syncthreads();
+        for (int f = threadIdx.x; f < G.wb; f += FT) {
+            const GCl& c = scl[group_owner<1>(scl, nc, f)];
+            const int q = f - c.woff_b;
+            double x = 0.0;
+            if (q < c.ni) x = ybuf[G.pstart + c.woff_f + q];
+            else if (q < c.nd) x = -out[v.bidx[G.bstart + c.boff + q - c.ni]];
+            vs[f] = (A)x;
+        }
+        __syncthreads();
+        if (!mbar_wait_bounded(&bar[buf], (ph >> buf) & 1u)) {
+            if (threadIdx.x == 0) atomicOr(err, 1u);
+            if ((pend >> (buf ^ 1)) & 1u) mbar_wait_bounded(&bar[buf ^ 1], (ph >> (buf ^ 1)) & 1u);
+            return;
+        }
+        ph ^= 1u << buf;
+        pend &= ~(1u << buf);
+        flat_bwd_body<T, A>(v, G, scl, nc, sm, vs, out);
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------ dataflow flat levels
@@ -1206,6 +1344,16 @@ int tree_smem_cap() {
     return cap;
 }
 
+// BID_FLATP=0 in the environment: one CTA per flat group on every level
+// (the persistent double-buffered launches give the same results bit for bit)
+bool flatp_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("BID_FLATP");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    return on;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
                      cudaStream_t st, Args... args) {
@@ -1353,8 +1501,15 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             const int sc_off = (F.fg_bytes[lev] + 15) / 16 * 16;
             const int w_off = sc_off + F.fg_nc[lev] * (int)sizeof(GCl);
             const size_t sm = (size_t)w_off + sizeof(A) * F.fg_wf[lev];
-            BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.xp, S.ybuf, inb,
-                                  S.err, sc_off, w_off, mf));
+            const int pg = flatp_enabled() && lev < (int)F.fgp_grid_f.size() ? F.fgp_grid_f[lev] : 0;
+            if (pg > 0) {
+                const int bs = F.fgp_buf_f[lev];
+                BID_CUDA_TRY(launch_k(k_flat_fwd_pb<T, A>, pg, FT, (size_t)2 * bs, L.st, v, data, F.fg_ptr[lev], nf,
+                                      S.xp, S.ybuf, inb, S.err, bs, sc_off, w_off, mf));
+            } else {
+                BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.xp, S.ybuf,
+                                      inb, S.err, sc_off, w_off, mf));
+            }
             ++launches;
         }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
@@ -1400,8 +1555,15 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             const int sc_off = (F.fg_bytes[lev] + 15) / 16 * 16;
             const int w_off = sc_off + F.fg_nc[lev] * (int)sizeof(GCl);
             const size_t sm = (size_t)w_off + sizeof(A) * F.fg_wb[lev];
-            BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.ybuf, out, S.err,
-                                  sc_off, w_off));
+            const int pg = flatp_enabled() && lev < (int)F.fgp_grid_b.size() ? F.fgp_grid_b[lev] : 0;
+            if (pg > 0) {
+                const int bs = F.fgp_buf_b[lev];
+                BID_CUDA_TRY(launch_k(k_flat_bwd_pb<T, A>, pg, FT, (size_t)2 * bs, L.st, v, data, F.fg_ptr[lev], nf,
+                                      S.ybuf, out, S.err, bs, sc_off, w_off));
+            } else {
+                BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.ybuf, out,
+                                      S.err, sc_off, w_off));
+            }
             ++launches;
         }
     }
@@ -1428,6 +1590,10 @@ int prepare_one() {
                                       FLAT_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       FLAT_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_fwd_pb<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * FLATP_BUF_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_flat_bwd_pb<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      2 * FLATP_BUF_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_tree_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       TREE_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_tree_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1438,6 +1604,7 @@ int prepare_one() {
 }  // namespace
 
 bool hsolve_upper_enabled() { return g_upper_ok == 1; }
+bool hsolve_flatp_enabled() { return flatp_enabled(); }
 
 int hsolve_prepare() {
     BID_TRY((prepare_one<double, double>()));
@@ -1610,6 +1777,40 @@ int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFa
     return BID_OK;
 }
 
+// Persistent double-buffered flat launches, level by level: used where the
+// level has more groups than CTAs fit on the GPU at once and two buffers of
+// its largest group fit FLATP_BUF_MAX each; grid = resident CTAs.
+template <typename T, typename A>
+static int flat_persistent_grids(HFactorDev* d) {
+    BID_TRY(hsolve_prepare());
+    int dev = 0, sms = 0;
+    BID_CUDA_TRY(cudaGetDevice(&dev));
+    BID_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int H = (int)d->fg_ptr.size() - 1;
+    for (auto* v : {&d->fgp_grid_f, &d->fgp_grid_b, &d->fgp_buf_f, &d->fgp_buf_b}) v->assign(std::max(H, 0), 0);
+    for (int lev = 0; lev < H; ++lev) {
+        const int nf = d->fg_ptr[lev + 1] - d->fg_ptr[lev];
+        if (nf <= 0) continue;
+        const int sc_off = (d->fg_bytes[lev] + 15) / 16 * 16;
+        const int w_off = sc_off + d->fg_nc[lev] * (int)sizeof(GCl);
+        for (int dir = 0; dir < 2; ++dir) {
+            const int w = dir == 0 ? d->fg_wf[lev] : d->fg_wb[lev];
+            const int bs = (w_off + (int)sizeof(A) * w + 127) / 128 * 128;
+            if (bs > FLATP_BUF_MAX) continue;
+            int nb = 0;
+            if (dir == 0)
+                BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_flat_fwd_pb<T, A>, FT, 2 * bs));
+            else
+                BID_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_flat_bwd_pb<T, A>, FT, 2 * bs));
+            const int grid = nb * sms;
+            if (nb < 1 || nf <= grid) continue;
+            (dir == 0 ? d->fgp_grid_f : d->fgp_grid_b)[lev] = grid;
+            (dir == 0 ? d->fgp_buf_f : d->fgp_buf_b)[lev] = bs;
+        }
+    }
+    return BID_OK;
+}
+
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     const int esz_acc = precision == BID_FP64 ? 8 : 4;
     for (size_t L = 0; L < h.u_ni_max.size(); ++L)
@@ -1703,6 +1904,9 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
         esz = 2;
     }
     BID_TRY(upload_tree(h, precision, d));
+    if (precision == BID_FP64) BID_TRY((flat_persistent_grids<double, double>(d)));
+    else if (precision == BID_FP32) BID_TRY((flat_persistent_grids<float, float>(d)));
+    else BID_TRY((flat_persistent_grids<__nv_bfloat16, float>(d)));
     BID_CUDA_TRY(cudaMalloc(&d->inb, sizeof(double) * std::max<int64_t>(h.nslots, 2)));
     BID_CUDA_TRY(cudaMemset(d->inb, 0, sizeof(double) * std::max<int64_t>(h.nslots, 2)));
     d->bytes_pass = 2 * (int64_t)n * esz;

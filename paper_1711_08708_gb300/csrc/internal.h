@@ -286,6 +286,9 @@ struct HFactorDev {
     double* y1 = nullptr;
     double* y1slot = nullptr;
     bool ones_ready = false;
+    // persistent double-buffered flat launches (k_flat_fwd_pb / k_flat_bwd_pb):
+    // per level the grid (0: one CTA per group instead) and the buffer size
+    std::vector<int32_t> fgp_grid_f, fgp_grid_b, fgp_buf_f, fgp_buf_b;
 };
 // Dataflow schedule of the flat groups of the levels [lev0, lev1): the groups
 // first .. first + ntask - 1 (tasks, numbered from 0 in group order = lower
@@ -521,6 +524,7 @@ int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S, int64_t vn);
 int launch_hsolve_seg_masked(const Launch& L, const HFactorDev& F, const double* in, const int16_t* seg,
                              const double* seg_sum, const double* seg_inv_n, const HScratch& S, double* out);
 bool hsolve_mask_enabled();   // BID_MASK=0 in the environment: plain solves
+bool hsolve_flatp_enabled();  // BID_FLATP=0 in the environment: one CTA per flat group
 int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in,
                       const int16_t* seg, const double* seg_sum, const double* seg_inv_n,
                       const HScratch& S, double* out);

@@ -473,3 +473,60 @@ def test_masked_second_solve_matches_full_solve(bid, tmp_path):
         assert np.abs(za - zb).max() <= tol * np.abs(zb).max(), key
         assert np.linalg.norm(a[key + "_x"] - b[key + "_x"]) <= 1e-7 * np.linalg.norm(b[key + "_x"]), key
         assert np.abs(np.asarray(a[key + "_it"]) - np.asarray(b[key + "_it"])).max() <= 1, key
+
+
+_FLATP_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_08708_gb300 import bid
+from workloads import torso_square_2d, params_2d
+from oracle import bidomain as ob
+p = params_2d(0.1)
+mesh = torso_square_2d(1025)
+S = bid.System(mesh, p)
+o = ob.build_system(mesh, p)
+out, levels = {}, []
+for prec in ("fp64", "fp32", "bf16"):
+    P = bid.Precond(S, p["dt"], eps=1e-3, precision=prec, leaf=32)
+    levels += [P.stats["flatp_levels1"], P.stats["flatp_levelsk"]]
+    rng = np.random.default_rng(9)
+    for which, n in ((1, S.N), (2, S.NH)):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        P.apply_factor(which, torch.tensor(rng.normal(size=n), device="cuda"), x)
+        out[f"{prec}_f{which}"] = x.cpu().numpy()
+    r = torch.tensor(rng.normal(size=S.N + S.NH), device="cuda")
+    z = torch.zeros_like(r)
+    P.apply(r, z)
+    out[prec + "_z"] = z.cpu().numpy()
+    Y = ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"])
+    X = torch.zeros(o.N + o.NH, dtype=torch.float64, device="cuda")
+    info = P.solve(torch.tensor(Y, device="cuda"), X, tol=1e-10)
+    out[prec + "_x"], out[prec + "_it"] = X.cpu().numpy(), np.array([info["iters"]])
+    del P
+np.savez(sys.argv[2], levels=np.array(levels), **out)
+"""
+
+
+def test_persistent_flat_levels_equal_one_cta_per_group(bid, tmp_path):
+    # the persistent double-buffered flat launches (default, on the levels with
+    # more groups than resident CTAs) and one CTA per group (BID_FLATP=0) give
+    # the same factor solves, masked preconditioner and PCG iterates, bit for
+    # bit, in every storage precision
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "s.py"
+    script.write_text(_FLATP_SCRIPT)
+    res = {}
+    for name, extra in (("pb", {}), ("plain", {"BID_FLATP": "0"})):
+        f = tmp_path / f"x_{name}.npz"
+        env = {k: v for k, v in os.environ.items() if k != "BID_FLATP"}
+        env.update(extra)
+        subprocess.run([sys.executable, str(script), root, str(f)], check=True, env=env, timeout=900)
+        res[name] = dict(np.load(f))
+    assert (res["pb"]["levels"][0::2] >= 1).all(), res["pb"]["levels"]    # P_1 of every precision
+    assert (res["plain"]["levels"] == 0).all()
+    for k in res["pb"]:
+        if k != "levels":
+            assert np.array_equal(res["pb"][k], res["plain"][k]), k
