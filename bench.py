@@ -71,6 +71,8 @@ def parse():
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
+    a.add_argument("--no-mg", action="store_true",
+                   help="skip the multigrid comparison (P_1, P_K by FP32 multigrid V-cycles)")
     a.add_argument("--no-cpu", action="store_true")
     a.add_argument("--no-cpu-full", action="store_true",
                    help="skip the whole-step oracle timings at 65^2 and 513^2")
@@ -770,6 +772,37 @@ def main():
                                 f"{args.tol:g}, so this is the solve tolerance times the "
                                 "conditioning, not the factor precision"}
 
+    # ---- the multigrid alternative for P_1 and P_K on the same GPU, same steps
+    mgres = None
+    if not args.no_mg and args.elliptic == "hchol":
+        Pm = bid.Precond(S, p["dt"], precision="fp32", scheme=args.scheme, elliptic="mg")
+        mg_form = time_form(Pm)
+        b = torch.randn(N, dtype=torch.float64, device=dev)
+        x = torch.empty_like(b)
+        for _ in range(3):
+            Pm.apply_factor(1, b, x)
+        e0.record(st)
+        for _ in range(10):
+            Pm.apply_factor(1, b, x)
+        e1.record(st)
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / 10
+        vb = Pm.stats["alg_bytes_p1"] + 16 * N      # V-cycle bytes plus the mean-sum pass
+        Um, Vm = mg_form["U"].cpu().numpy(), mg_form["V"].cpu().numpy()
+        mgres = {"steps_per_s": world * args.steps / (mg_form["ms"] * 1e-3),
+                 "mean_pcg_iters": float(np.mean(mg_form["iters"])),
+                 "build_seconds": Pm.stats["build_seconds"],
+                 "levels": [Pm.stats["levels1"], Pm.stats["levelsk"]],
+                 "dtype": "f64 PCG / fp32 multigrid V-cycles",
+                 "p1_vcycle": {"ms": vms, "algorithmic_bytes": vb,
+                               "achieved_gbs": vb / (vms * 1e-3) / 1e9,
+                               "frac": vb / (vms * 1e-3) / 1e9 / hbm},
+                 "error_vs_chosen": {"U": float(np.abs(Um - Uc).max() / np.abs(Uc).max()),
+                                     "V": float(np.abs(Vm - Vc).max() / np.abs(Vc).max())},
+                 "note": "the same block-LU preconditioner with P_1 and P_K applied by one "
+                         "geometric-multigrid V-cycle each instead of the hierarchical factors"}
+        del Pm
+
     value = world * args.steps / (chosen["ms"] * 1e-3)
     traffic_ratio = TRAFFIC_PER_ALG_BYTE.get((args.eps, args.precision, args.leaf))
     line = {
@@ -799,6 +832,7 @@ def main():
                 "dtype": "f64 PCG / fp64 factors (exact)",
             },
             "chosen_error_vs_plain": None if plain is None else err_vs_plain,
+            "multigrid": mgres,
         },
         "roofline": {"bound": "hbm", "achieved": alg_bytes / (solve_ms * 1e-3) / 1e9, "peak": hbm,
                      "unit": "GB/s", "frac": alg_bytes / (solve_ms * 1e-3) / 1e9 / hbm,

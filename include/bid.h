@@ -45,9 +45,9 @@
  *                    solve (BID_TREE_FROM first level, default 1;
  *                    BID_TREE_SMEM shared-memory cap, default 32768);
  *    BID_UPPER=1     the top levels run in persistent cooperative launches;
- *    BID_FLATP=0     one CTA per flat group on every level instead of persistent
- *                    double-buffered launches on the levels with more groups
- *                    than resident CTAs;
+ *    BID_FLATP=1     persistent double-buffered launches on the flat levels
+ *                    with more groups than resident CTAs instead of one CTA
+ *                    per group;
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the
@@ -178,7 +178,7 @@ typedef struct bid_precond_stats {
                                           backward pass (alg_bytes_p1 with BID_MASK=0) */
     int32_t flatp_levels1, flatp_levelsk;  /* flat levels solved by persistent double-
                                           buffered launches (more groups than resident
-                                          CTAs), forward pass; 0 with BID_FLATP=0 */
+                                          CTAs), forward pass; 0 unless BID_FLATP=1 */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {

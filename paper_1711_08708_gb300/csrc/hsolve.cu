@@ -1344,12 +1344,16 @@ int tree_smem_cap() {
     return cap;
 }
 
-// BID_FLATP=0 in the environment: one CTA per flat group on every level
-// (the persistent double-buffered launches give the same results bit for bit)
+// BID_FLATP=1 in the environment: persistent double-buffered launches on
+// the flat levels with more groups than resident CTAs (same results bit for
+// bit).  On the 2049^2 slice they measured slower than one CTA per group
+// (P_1 solve 1.82 against 1.11 ms): a persistent CTA stages, waits for and
+// computes its groups one after another, so fewer groups are in flight per
+// SM than with independent CTAs, and the copy it hides was not the bound.
 bool flatp_enabled() {
     static const bool on = [] {
         const char* e = std::getenv("BID_FLATP");
-        return !(e && std::strcmp(e, "0") == 0);
+        return e && std::strcmp(e, "1") == 0;
     }();
     return on;
 }

@@ -508,10 +508,10 @@ np.savez(sys.argv[2], levels=np.array(levels), **out)
 
 
 def test_persistent_flat_levels_equal_one_cta_per_group(bid, tmp_path):
-    # the persistent double-buffered flat launches (default, on the levels with
-    # more groups than resident CTAs) and one CTA per group (BID_FLATP=0) give
-    # the same factor solves, masked preconditioner and PCG iterates, bit for
-    # bit, in every storage precision
+    # the persistent double-buffered flat launches (BID_FLATP=1, on the levels
+    # with more groups than resident CTAs) and one CTA per group (the default)
+    # give the same factor solves, masked preconditioner and PCG iterates, bit
+    # for bit, in every storage precision
     import os
     import subprocess
     import sys
@@ -519,7 +519,7 @@ def test_persistent_flat_levels_equal_one_cta_per_group(bid, tmp_path):
     script = tmp_path / "s.py"
     script.write_text(_FLATP_SCRIPT)
     res = {}
-    for name, extra in (("pb", {}), ("plain", {"BID_FLATP": "0"})):
+    for name, extra in (("pb", {"BID_FLATP": "1"}), ("plain", {})):
         f = tmp_path / f"x_{name}.npz"
         env = {k: v for k, v in os.environ.items() if k != "BID_FLATP"}
         env.update(extra)
