@@ -973,8 +973,11 @@ __device__ __forceinline__ void up_fwd_task(const HView& v, const T* __restrict_
     if (tid == 0) tickets[t.ticket] = 0u;
 }
 
+// resident CTAs per SM the large-cluster forward kernel is compiled for
+constexpr int UP_FWD_MINB = 6;
+
 template <typename T, typename A>
-__global__ void __launch_bounds__(HT) k_up_fwd(HView v, const T* __restrict__ data, int task0,
+__global__ void __launch_bounds__(HT, UP_FWD_MINB) k_up_fwd(HView v, const T* __restrict__ data, int task0,
                                                const double* xp, double* ybuf, double* inb,
                                                double* tbuf, double* pbuf,
                                                unsigned int* tickets, MaskArgs mk) {
