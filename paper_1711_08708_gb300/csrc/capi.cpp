@@ -429,6 +429,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     bo.upper_levels = hsolve_upper_enabled();
     if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knobs
     if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
+    if (const char* ub = std::getenv("BID_UP_BROWS")) bo.up_brows = std::max(32, std::atoi(ub));
     HFactorHost h1, hk;
     MgHost m1, mk;
     // P_K: K_m = gamma M_H + S_m (Sec. 5.2)

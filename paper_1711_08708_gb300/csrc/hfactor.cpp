@@ -803,9 +803,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
                 F->uft.push_back(k);
             }
             // backward: a column is shared by wpc warps so that each warp reads
-            // about UP_BROWS rows; a CTA holds 8 / wpc columns
+            // about o.up_brows rows; a CTA holds 8 / wpc columns
             int wpc = 1;
-            while (wpc < 8 && (int64_t)wpc * UP_BROWS < h.nd) wpc *= 2;
+            while (wpc < 8 && (int64_t)wpc * o.up_brows < h.nd) wpc *= 2;
             const int cpc = 8 / wpc;
             for (int a = 0; a < h.ni; a += cpc) {
                 HTask k{};

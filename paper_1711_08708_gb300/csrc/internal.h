@@ -218,6 +218,7 @@ struct HBuildOpts {
     bool upper_levels = false;
     int group_bytes = GROUP_BYTES_DEFAULT;   // factor bytes of a flat group (see FGroup)
     int group_bytes_leaf = 0;                // the same for the leaf level (0: group_bytes)
+    int up_brows = 512;                      // target rows per warp of a large-cluster backward task
 };
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  Every index in `pins` has its
@@ -235,7 +236,6 @@ constexpr int FLAT_THREADS = 128;    // threads of a flat CTA
 constexpr int UP_GROUPS = 64;    // row groups (of vec rows) of an upper forward task
 constexpr int UP_SPLIT = 4;      // column splits of an upper forward task (16 columns each)
 constexpr int UP_COLS = 64;      // columns of an upper forward task
-constexpr int UP_BROWS = 512;    // target rows per warp of an upper backward task
 constexpr int UP_THREADS = 256;  // threads of a low-rank group task (one per row)
 constexpr int LR_ROWS = 256;     // max rows of a low-rank group
 constexpr int LR_KMAX = 64;      // largest rank kept in a low-rank group
