@@ -35,24 +35,6 @@ MView<V> mview(const MgMat& m) {
     return MView<V>{m.n, m.nslices, m.sptr, m.col, static_cast<const V*>(m.val)};
 }
 
-// Arithmetic with explicit rounding (no contraction left to the compiler), so
-// that the per-level kernels and the fused coarse kernel round alike.
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-
-// Chebyshev update of one row: d' = c1 d + c2 (dinv (b - ax)) (c1 = 0: d unused)
-template <typename V>
-__device__ __forceinline__ V cheb_d(V c1, V d, V c2, V dinv, V b, V ax) {
-    const V t = mul_rn(c2, mul_rn(dinv, sub_rn(b, ax)));
-    return c1 != (V)0 ? add_rn(mul_rn(c1, d), t) : t;
-}
-
 // row 32 sl + lane of A times x
 template <typename V>
 __device__ __forceinline__ V row_dot(const MView<V>& A, int sl, int lane, const V* __restrict__ x) {
@@ -60,7 +42,7 @@ __device__ __forceinline__ V row_dot(const MView<V>& A, int sl, int lane, const 
     V s = 0;
     for (int k = 0; k < w; ++k) {
         const int idx = b + k * 32 + lane;
-        s = fma_rn(A.val[idx], x[A.col[idx]], s);
+        s += A.val[idx] * x[A.col[idx]];
     }
     return s;
 }
@@ -82,7 +64,7 @@ __global__ void __launch_bounds__(MT) k_mg_first(int n, const double* __restrict
         } else {
             bi = b[i];
         }
-        const V di = mul_rn(inv_theta, mul_rn(dinv[i], bi));
+        const V di = inv_theta * (dinv[i] * bi);
         d[i] = di;
         x[i] = di;
     }
@@ -101,9 +83,10 @@ __global__ void __launch_bounds__(MT) k_mg_cheb(MView<V> A, const V* __restrict_
         const V ax = row_dot(A, sl, lane, xin);
         const int r = sl * 32 + lane;
         if (r >= A.n) continue;
-        const V dn = cheb_d(c1, c1 != (V)0 ? d[r] : (V)0, c2, dinv[r], b[r], ax);
+        const V res = b[r] - ax;
+        const V dn = (c1 != (V)0 ? c1 * d[r] : (V)0) + c2 * (dinv[r] * res);
         d[r] = dn;
-        xout[r] = (O)add_rn(xin[r], dn);
+        xout[r] = (O)(xin[r] + dn);
     }
 }
 
@@ -117,7 +100,7 @@ __global__ void __launch_bounds__(MT) k_mg_resid(MView<V> A, const V* __restrict
     for (int sl = gw; sl < A.nslices; sl += nw) {
         const V ax = row_dot(A, sl, lane, x);
         const int i = sl * 32 + lane;
-        if (i < A.n) r[i] = sub_rn(b[i], ax);
+        if (i < A.n) r[i] = b[i] - ax;
     }
 }
 
@@ -132,7 +115,7 @@ __global__ void __launch_bounds__(MT) k_mg_apply(MView<V> M, const V* __restrict
     for (int sl = gw; sl < M.nslices; sl += nw) {
         const V s = row_dot(M, sl, lane, x);
         const int i = sl * 32 + lane;
-        if (i < M.n) y[i] = add ? add_rn(y[i], s) : s;
+        if (i < M.n) y[i] = add ? y[i] + s : s;
     }
 }
 
@@ -145,9 +128,9 @@ __global__ void __launch_bounds__(MT) k_mg_dense(int n, const V* __restrict__ G,
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = gw; i < n; i += nw) {
         V s = 0;
-        for (int j = lane; j < n; j += 32) s = fma_rn(G[(size_t)i * n + j], b[j], s);
+        for (int j = lane; j < n; j += 32) s += G[(size_t)i * n + j] * b[j];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s = add_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) x[i] = (O)s;
     }
 }
@@ -176,7 +159,7 @@ __device__ __forceinline__ V row_dot_cg(const int32_t* __restrict__ sptr, const 
     V s = 0;
     for (int k = 0; k < w; ++k) {
         const int idx = b + k * 32 + lane;
-        s = fma_rn(val[idx], __ldcg(x + col[idx]), s);
+        s += val[idx] * __ldcg(x + col[idx]);
     }
     return s;
 }
@@ -193,9 +176,10 @@ __device__ __forceinline__ void fused_cheb(const MgFuseLev& L, const V* xin, V* 
         const V ax = row_dot_cg<V>(L.sA, L.cA, val, sl, lane, xin);
         const int r = sl * 32 + lane;
         if (r >= L.n) continue;
-        const V dn = cheb_d(c1, c1 != (V)0 ? __ldcg(d + r) : (V)0, c2, dinv[r], __ldcg(b + r), ax);
+        const V res = __ldcg(b + r) - ax;
+        const V dn = (c1 != (V)0 ? c1 * __ldcg(d + r) : (V)0) + c2 * (dinv[r] * res);
         d[r] = dn;
-        xout[r] = add_rn(__ldcg(xin + r), dn);
+        xout[r] = __ldcg(xin + r) + dn;
     }
 }
 
@@ -212,7 +196,7 @@ __global__ void __launch_bounds__(FT_MG) k_mg_coarse(const MgFuseLev* __restrict
         V* d = static_cast<V*>(L.d);
         const V it = (V)L.inv_theta;
         for (int i = threadIdx.x; i < L.n; i += FT_MG) {
-            const V di = mul_rn(it, mul_rn(dinv[i], __ldcg(b + i)));
+            const V di = it * (dinv[i] * __ldcg(b + i));
             d[i] = di;
             x[i] = di;
         }
@@ -225,7 +209,7 @@ __global__ void __launch_bounds__(FT_MG) k_mg_coarse(const MgFuseLev* __restrict
         for (int sl = warp; sl < L.nsA; sl += FT_MG / 32) {
             const V ax = row_dot_cg<V>(L.sA, L.cA, vA, sl, lane, y);
             const int i = sl * 32 + lane;
-            if (i < L.n) r[i] = sub_rn(__ldcg(b + i), ax);
+            if (i < L.n) r[i] = __ldcg(b + i) - ax;
         }
         __syncthreads();
         V* bc = static_cast<V*>(levs[l + 1].b);
@@ -245,9 +229,9 @@ __global__ void __launch_bounds__(FT_MG) k_mg_coarse(const MgFuseLev* __restrict
         V* e = static_cast<V*>(L.e);
         for (int i = warp; i < nc; i += FT_MG / 32) {
             V s = 0;
-            for (int j = lane; j < nc; j += 32) s = fma_rn(G[(size_t)i * nc + j], __ldcg(b + j), s);
+            for (int j = lane; j < nc; j += 32) s += G[(size_t)i * nc + j] * __ldcg(b + j);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s = add_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if (lane == 0) e[i] = s;
         }
         __syncthreads();
@@ -261,7 +245,7 @@ __global__ void __launch_bounds__(FT_MG) k_mg_coarse(const MgFuseLev* __restrict
         for (int sl = warp; sl < L.nsP; sl += FT_MG / 32) {
             const V s = row_dot_cg<V>(L.sP, L.cP, vP, sl, lane, ec);
             const int i = sl * 32 + lane;
-            if (i < L.n) y[i] = add_rn(__ldcg(y + i), s);
+            if (i < L.n) y[i] = __ldcg(y + i) + s;
         }
         __syncthreads();
         fused_cheb<V>(L, y, static_cast<V*>(L.x), (V)0, (V)L.inv_theta);
