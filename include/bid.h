@@ -48,8 +48,6 @@
  *    BID_FLATP=1     persistent double-buffered launches on the flat levels
  *                    with more groups than resident CTAs instead of one CTA
  *                    per group;
- *    BID_MG_FUSE=0   every multigrid level in its own launches instead of the
- *                    levels below 24576 points in one single-CTA launch;
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the

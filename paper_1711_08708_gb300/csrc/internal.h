@@ -424,12 +424,7 @@ struct MgDev {
     bool singular = false;
     int precision = BID_FP64;    // BID_FP64 or BID_FP32
     int64_t alg_bytes = 0;       // algorithmic bytes of one V-cycle
-    // levels [fuse_from, end) run in one single-CTA launch per cycle (their
-    // per-level launches would be latency-bound); fuse_from = lev.size(): none
-    int fuse_from = 0;
-    void* fuse_desc = nullptr;   // device array of the fused levels' descriptors
 };
-constexpr int MG_FUSE_ROWS = 24576;   // levels at most this large run fused
 struct Launch;
 int upload_mg(const MgHost& h, int precision, MgDev* d);
 void free_mg(MgDev* d);

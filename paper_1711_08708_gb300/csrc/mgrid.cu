@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cstdlib>
 
 #include "internal.h"
 
@@ -135,135 +134,6 @@ __global__ void __launch_bounds__(MT) k_mg_dense(int n, const V* __restrict__ G,
     }
 }
 
-// ---------------------------------------------------------------- fused coarse levels
-// The levels from fuse_from down run in one launch of a single CTA (FT_MG
-// threads): the same passes as the per-level kernels, in the same order and
-// with the same per-row arithmetic (so the same results bit for bit), with a
-// block barrier between passes instead of a kernel boundary.  Vectors
-// written inside the launch are read through L2 (ld.global.cg), never
-// through the read-only path.
-constexpr int FT_MG = 1024;
-
-struct MgFuseLev {           // one level's pointers (device), values of type V
-    int32_t n, nsA, nsP, nsR;
-    const int32_t *sA, *cA, *sP, *cP, *sR, *cR;
-    const void *vA, *vP, *vR, *dinv;
-    void *x, *y, *b, *r, *d, *e;
-    double inv_theta, c1, c2;
-};
-
-template <typename V>
-__device__ __forceinline__ V row_dot_cg(const int32_t* __restrict__ sptr, const int32_t* __restrict__ col,
-                                        const V* __restrict__ val, int sl, int lane, const V* x) {
-    const int b = sptr[sl], w = (sptr[sl + 1] - b) >> 5;
-    V s = 0;
-    for (int k = 0; k < w; ++k) {
-        const int idx = b + k * 32 + lane;
-        s += val[idx] * __ldcg(x + col[idx]);
-    }
-    return s;
-}
-
-// Chebyshev step of one level inside the fused launch (as k_mg_cheb)
-template <typename V>
-__device__ __forceinline__ void fused_cheb(const MgFuseLev& L, const V* xin, V* xout, V c1, V c2) {
-    const V* val = static_cast<const V*>(L.vA);
-    const V* dinv = static_cast<const V*>(L.dinv);
-    const V* b = static_cast<const V*>(L.b);
-    V* d = static_cast<V*>(L.d);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int sl = warp; sl < L.nsA; sl += FT_MG / 32) {
-        const V ax = row_dot_cg<V>(L.sA, L.cA, val, sl, lane, xin);
-        const int r = sl * 32 + lane;
-        if (r >= L.n) continue;
-        const V res = __ldcg(b + r) - ax;
-        const V dn = (c1 != (V)0 ? c1 * __ldcg(d + r) : (V)0) + c2 * (dinv[r] * res);
-        d[r] = dn;
-        xout[r] = __ldcg(xin + r) + dn;
-    }
-}
-
-template <typename V>
-__global__ void __launch_bounds__(FT_MG) k_mg_coarse(const MgFuseLev* __restrict__ levs, int nlev,
-                                                     const V* __restrict__ G, int nc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // down: first step, Chebyshev step, residual, restriction
-    for (int l = 0; l + 1 < nlev; ++l) {
-        const MgFuseLev L = levs[l];
-        const V* dinv = static_cast<const V*>(L.dinv);
-        const V* b = static_cast<const V*>(L.b);
-        V* x = static_cast<V*>(L.x);
-        V* d = static_cast<V*>(L.d);
-        const V it = (V)L.inv_theta;
-        for (int i = threadIdx.x; i < L.n; i += FT_MG) {
-            const V di = it * (dinv[i] * __ldcg(b + i));
-            d[i] = di;
-            x[i] = di;
-        }
-        __syncthreads();
-        fused_cheb<V>(L, x, static_cast<V*>(L.y), (V)L.c1, (V)L.c2);
-        __syncthreads();
-        const V* vA = static_cast<const V*>(L.vA);
-        const V* y = static_cast<const V*>(L.y);
-        V* r = static_cast<V*>(L.r);
-        for (int sl = warp; sl < L.nsA; sl += FT_MG / 32) {
-            const V ax = row_dot_cg<V>(L.sA, L.cA, vA, sl, lane, y);
-            const int i = sl * 32 + lane;
-            if (i < L.n) r[i] = __ldcg(b + i) - ax;
-        }
-        __syncthreads();
-        V* bc = static_cast<V*>(levs[l + 1].b);
-        const V* vR = static_cast<const V*>(L.vR);
-        const int nr = levs[l + 1].n;
-        for (int sl = warp; sl < L.nsR; sl += FT_MG / 32) {
-            const V s = row_dot_cg<V>(L.sR, L.cR, vR, sl, lane, r);
-            const int i = sl * 32 + lane;
-            if (i < nr) bc[i] = s;
-        }
-        __syncthreads();
-    }
-    // coarsest: e = G b (one warp per row)
-    {
-        const MgFuseLev L = levs[nlev - 1];
-        const V* b = static_cast<const V*>(L.b);
-        V* e = static_cast<V*>(L.e);
-        for (int i = warp; i < nc; i += FT_MG / 32) {
-            V s = 0;
-            for (int j = lane; j < nc; j += 32) s += G[(size_t)i * nc + j] * __ldcg(b + j);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) e[i] = s;
-        }
-        __syncthreads();
-    }
-    // up: prolongation, two Chebyshev steps (the second writes the level's e)
-    for (int l = nlev - 2; l >= 0; --l) {
-        const MgFuseLev L = levs[l];
-        V* y = static_cast<V*>(L.y);
-        const V* ec = static_cast<const V*>(levs[l + 1].e);
-        const V* vP = static_cast<const V*>(L.vP);
-        for (int sl = warp; sl < L.nsP; sl += FT_MG / 32) {
-            const V s = row_dot_cg<V>(L.sP, L.cP, vP, sl, lane, ec);
-            const int i = sl * 32 + lane;
-            if (i < L.n) y[i] = __ldcg(y + i) + s;
-        }
-        __syncthreads();
-        fused_cheb<V>(L, y, static_cast<V*>(L.x), (V)0, (V)L.inv_theta);
-        __syncthreads();
-        fused_cheb<V>(L, static_cast<const V*>(L.x), static_cast<V*>(L.e), (V)L.c1, (V)L.c2);
-        __syncthreads();
-    }
-}
-
-// BID_MG_FUSE=0 in the environment: every level in its own launches
-bool mg_fuse_enabled() {
-    static const bool on = [] {
-        const char* e = std::getenv("BID_MG_FUSE");
-        return !(e && e[0] == '0' && e[1] == 0);
-    }();
-    return on;
-}
-
 int grid_of(const Launch& L, int64_t threads) {
     int64_t g = (threads + MT - 1) / MT;
     g = std::min<int64_t>(g, (int64_t)L.sms * 8);
@@ -283,11 +153,6 @@ int checked(const char* what) {
 template <typename V>
 int vcycle(const Launch& L, const MgDev& M, size_t l, const double* in0, const double* shift_sum,
            double inv_n, double* out0) {
-    if ((int)l == M.fuse_from && l > 0) {   // this level and all below in one launch: b in, e out
-        k_mg_coarse<V><<<1, FT_MG, 0, L.st>>>(static_cast<const MgFuseLev*>(M.fuse_desc) + l,
-                                              (int)(M.lev.size() - l), static_cast<const V*>(M.G), (int)M.nc);
-        return checked("mg_coarse");
-    }
     const MgLevelDev& W = M.lev[l];
     const int n = (int)W.n;
     V* b = static_cast<V*>(W.b);
@@ -419,48 +284,6 @@ int upload_typed(const MgHost& h, MgDev* d) {
     }
     BID_TRY(upload_vals<V>(h.G, &d->G));
     d->alg_bytes = bytes;
-    // fused coarse levels: from the first level below the top with at most
-    // MG_FUSE_ROWS points that is not the coarsest
-    const int nl = (int)d->lev.size();
-    d->fuse_from = nl;
-    if (mg_fuse_enabled())
-        for (int l = 1; l + 1 < nl; ++l)
-            if (d->lev[l].n <= MG_FUSE_ROWS) {
-                d->fuse_from = l;
-                break;
-            }
-    std::vector<MgFuseLev> desc(nl);
-    for (int l = 0; l < nl; ++l) {
-        const MgLevelDev& D = d->lev[l];
-        MgFuseLev& f = desc[l];
-        f.n = (int32_t)D.n;
-        f.nsA = D.A.nslices;
-        f.nsP = D.P.nslices;
-        f.nsR = D.R.nslices;
-        f.sA = D.A.sptr;
-        f.cA = D.A.col;
-        f.sP = D.P.sptr;
-        f.cP = D.P.col;
-        f.sR = D.R.sptr;
-        f.cR = D.R.col;
-        f.vA = D.A.val;
-        f.vP = D.P.val;
-        f.vR = D.R.val;
-        f.dinv = D.dinv;
-        f.x = D.x;
-        f.y = D.y;
-        f.b = D.b;
-        f.r = D.r;
-        f.d = D.d;
-        f.e = D.e;
-        double th = 1.0, c1 = 0.0, c2 = 0.0;
-        if (l + 1 < nl) mg_cheb_coeffs(D.lmax, &th, &c1, &c2);
-        f.inv_theta = 1.0 / th;
-        f.c1 = c1;
-        f.c2 = c2;
-    }
-    BID_CUDA_TRY(cudaMalloc(&d->fuse_desc, sizeof(MgFuseLev) * nl));
-    BID_CUDA_TRY(cudaMemcpy(d->fuse_desc, desc.data(), sizeof(MgFuseLev) * nl, cudaMemcpyHostToDevice));
     return BID_OK;
 }
 
@@ -493,7 +316,6 @@ void free_mg(MgDev* d) {
         for (void* p : {V.dinv, V.x, V.y, V.b, V.r, V.d, V.e}) cudaFree(p);
     }
     cudaFree(d->G);
-    cudaFree(d->fuse_desc);
     *d = MgDev();
 }
 

@@ -137,50 +137,3 @@ def test_multigrid_rejections(bid):
     with pytest.raises(bid.BidError) as e:
         bid.Batch([S], 0.1, elliptic="mg")
     assert e.value.code == bid.EINVAL
-
-
-_FUSE_SCRIPT = r"""
-import sys, numpy as np, torch
-sys.path.insert(0, sys.argv[1])
-from paper_1711_08708_gb300 import bid
-from workloads import torso_square_2d, params_2d
-from oracle import bidomain as ob
-p = params_2d(0.1)
-mesh = torso_square_2d(513)
-S = bid.System(mesh, p)
-o = ob.build_system(mesh, p)
-out = {}
-for prec in ("fp64", "fp32"):
-    P = bid.Precond(S, p["dt"], elliptic="mg", precision=prec)
-    rng = np.random.default_rng(4)
-    for which, n in ((1, S.N), (2, S.NH)):
-        x = torch.zeros(n, dtype=torch.float64, device="cuda")
-        P.apply_factor(which, torch.tensor(rng.normal(size=n), device="cuda"), x)
-        out[f"{prec}_{which}"] = x.cpu().numpy()
-    Y = ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"])
-    X = torch.zeros(o.N + o.NH, dtype=torch.float64, device="cuda")
-    info = P.solve(torch.tensor(Y, device="cuda"), X, tol=1e-10)
-    out[prec + "_x"], out[prec + "_it"] = X.cpu().numpy(), np.array([info["iters"]])
-np.savez(sys.argv[2], **out)
-"""
-
-
-def test_fused_coarse_levels_equal_per_level_launches(bid, tmp_path):
-    # the coarse levels in one single-CTA launch (default) and in their own
-    # launches (BID_MG_FUSE=0) run the same per-row arithmetic in the same
-    # order: V-cycles and PCG iterates equal bit for bit
-    import os
-    import subprocess
-    import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    script = tmp_path / "s.py"
-    script.write_text(_FUSE_SCRIPT)
-    res = {}
-    for name, extra in (("fused", {}), ("levels", {"BID_MG_FUSE": "0"})):
-        f = tmp_path / f"x_{name}.npz"
-        env = {k: v for k, v in os.environ.items() if k != "BID_MG_FUSE"}
-        env.update(extra)
-        subprocess.run([sys.executable, str(script), root, str(f)], check=True, env=env, timeout=900)
-        res[name] = dict(np.load(f))
-    for k in res["fused"]:
-        assert np.array_equal(res["fused"][k], res["levels"][k]), k
