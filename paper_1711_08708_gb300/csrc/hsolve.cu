@@ -1612,6 +1612,7 @@ int prepare_one() {
 
 bool hsolve_upper_enabled() { return g_upper_ok == 1; }
 bool hsolve_flatp_enabled() { return flatp_enabled(); }
+bool hsolve_pdl_enabled() { return pdl_enabled(); }
 
 int hsolve_prepare() {
     BID_TRY((prepare_one<double, double>()));

@@ -524,7 +524,8 @@ int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S, int64_t vn);
 int launch_hsolve_seg_masked(const Launch& L, const HFactorDev& F, const double* in, const int16_t* seg,
                              const double* seg_sum, const double* seg_inv_n, const HScratch& S, double* out);
 bool hsolve_mask_enabled();   // BID_MASK=0 in the environment: plain solves
-bool hsolve_flatp_enabled();  // BID_FLATP=0 in the environment: one CTA per flat group
+bool hsolve_flatp_enabled();  // BID_FLATP=1 in the environment: persistent flat launches
+bool hsolve_pdl_enabled();    // BID_PDL=0 in the environment: plain stream order
 int launch_hsolve_seg(const Launch& L, const HFactorDev& F, const double* in,
                       const int16_t* seg, const double* seg_sum, const double* seg_inv_n,
                       const HScratch& S, double* out);

@@ -22,6 +22,26 @@ namespace {
 
 constexpr int MT = 256;
 
+// Programmatic dependent launch: each kernel of the cycle may be scheduled
+// while its predecessor drains; it touches no memory before pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kern)(KArgs...), int grid, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(MT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = hsolve_pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename V>
 struct MView {
     int32_t n, nslices;
@@ -54,6 +74,8 @@ __global__ void __launch_bounds__(MT) k_mg_first(int n, const double* __restrict
                                                  const double* __restrict__ shift_sum, double inv_n,
                                                  const V* __restrict__ dinv, V inv_theta, V* b,
                                                  V* __restrict__ x, V* __restrict__ d) {
+    pdl_wait();
+    pdl_trigger();
     const double sh = shift_sum ? *shift_sum * inv_n : 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         V bi;
@@ -75,6 +97,8 @@ template <typename V, typename O>
 __global__ void __launch_bounds__(MT) k_mg_cheb(MView<V> A, const V* __restrict__ dinv, const V* __restrict__ b,
                                                 const V* __restrict__ xin, O* __restrict__ xout,
                                                 V* __restrict__ d, V c1, V c2) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -93,6 +117,8 @@ __global__ void __launch_bounds__(MT) k_mg_cheb(MView<V> A, const V* __restrict_
 template <typename V>
 __global__ void __launch_bounds__(MT) k_mg_resid(MView<V> A, const V* __restrict__ b, const V* __restrict__ x,
                                                  V* __restrict__ r) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -108,6 +134,8 @@ __global__ void __launch_bounds__(MT) k_mg_resid(MView<V> A, const V* __restrict
 template <typename V>
 __global__ void __launch_bounds__(MT) k_mg_apply(MView<V> M, const V* __restrict__ x, V* __restrict__ y,
                                                  int add) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -122,6 +150,8 @@ __global__ void __launch_bounds__(MT) k_mg_apply(MView<V> M, const V* __restrict
 template <typename V, typename O>
 __global__ void __launch_bounds__(MT) k_mg_dense(int n, const V* __restrict__ G, const V* __restrict__ b,
                                                  O* __restrict__ x) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -140,9 +170,9 @@ int grid_of(const Launch& L, int64_t threads) {
     return (int)std::max<int64_t>(g, 1);
 }
 
-int checked(const char* what) {
+int checked(cudaError_t e, const char* what) {
     count_launches(1);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(BID_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
     return BID_OK;
 }
@@ -153,6 +183,7 @@ int checked(const char* what) {
 template <typename V>
 int vcycle(const Launch& L, const MgDev& M, size_t l, const double* in0, const double* shift_sum,
            double inv_n, double* out0) {
+    cudaError_t lerr = cudaSuccess;
     const MgLevelDev& W = M.lev[l];
     const int n = (int)W.n;
     V* b = static_cast<V*>(W.b);
@@ -163,37 +194,37 @@ int vcycle(const Launch& L, const MgDev& M, size_t l, const double* in0, const d
     const V* dinv = static_cast<const V*>(W.dinv);
     if (l + 1 == M.lev.size()) {
         if (in0) {   // a one-level hierarchy: the shifted input into b first
-            k_mg_first<V><<<grid_of(L, n), MT, 0, L.st>>>(n, in0, shift_sum, inv_n, dinv, (V)0, b, x, d);
-            BID_TRY(checked("mg_first"));
+            lerr = launch(k_mg_first<V>, grid_of(L, n), L.st, n, in0, shift_sum, inv_n, dinv, (V)0, b, x, d);
+            BID_TRY(checked(lerr, "mg_first"));
         }
         const V* G = static_cast<const V*>(M.G);
-        if (out0) k_mg_dense<V, double><<<grid_of(L, (int64_t)n * 32), MT, 0, L.st>>>(n, G, b, out0);
-        else k_mg_dense<V, V><<<grid_of(L, (int64_t)n * 32), MT, 0, L.st>>>(n, G, b, e);
-        return checked("mg_dense");
+        if (out0) lerr = launch(k_mg_dense<V, double>, grid_of(L, (int64_t)n * 32), L.st, n, G, b, out0);
+        else lerr = launch(k_mg_dense<V, V>, grid_of(L, (int64_t)n * 32), L.st, n, G, b, e);
+        return checked(lerr, "mg_dense");
     }
     double th, c1, c2;
     mg_cheb_coeffs(W.lmax, &th, &c1, &c2);
     const MView<V> A = mview<V>(W.A);
     const int gs = grid_of(L, (int64_t)W.A.nslices * 32);
-    k_mg_first<V><<<grid_of(L, n), MT, 0, L.st>>>(n, in0, shift_sum, inv_n, dinv, (V)(1.0 / th), b, x, d);
-    BID_TRY(checked("mg_first"));
-    k_mg_cheb<V, V><<<gs, MT, 0, L.st>>>(A, dinv, b, x, y, d, (V)c1, (V)c2);
-    BID_TRY(checked("mg_cheb"));
-    k_mg_resid<V><<<gs, MT, 0, L.st>>>(A, b, y, static_cast<V*>(W.r));
-    BID_TRY(checked("mg_resid"));
+    lerr = launch(k_mg_first<V>, grid_of(L, n), L.st, n, in0, shift_sum, inv_n, dinv, (V)(1.0 / th), b, x, d);
+    BID_TRY(checked(lerr, "mg_first"));
+    lerr = launch(k_mg_cheb<V, V>, gs, L.st, A, dinv, b, x, y, d, (V)c1, (V)c2);
+    BID_TRY(checked(lerr, "mg_cheb"));
+    lerr = launch(k_mg_resid<V>, gs, L.st, A, b, y, static_cast<V*>(W.r));
+    BID_TRY(checked(lerr, "mg_resid"));
     const MgLevelDev& C = M.lev[l + 1];
-    k_mg_apply<V><<<grid_of(L, (int64_t)W.R.nslices * 32), MT, 0, L.st>>>(mview<V>(W.R), static_cast<V*>(W.r),
+    lerr = launch(k_mg_apply<V>, grid_of(L, (int64_t)W.R.nslices * 32), L.st, mview<V>(W.R), static_cast<V*>(W.r),
                                                                           static_cast<V*>(C.b), 0);
-    BID_TRY(checked("mg_restrict"));
+    BID_TRY(checked(lerr, "mg_restrict"));
     BID_TRY(vcycle<V>(L, M, l + 1, nullptr, nullptr, 0.0, nullptr));
-    k_mg_apply<V><<<grid_of(L, (int64_t)W.P.nslices * 32), MT, 0, L.st>>>(mview<V>(W.P), static_cast<V*>(C.e),
+    lerr = launch(k_mg_apply<V>, grid_of(L, (int64_t)W.P.nslices * 32), L.st, mview<V>(W.P), static_cast<V*>(C.e),
                                                                           y, 1);
-    BID_TRY(checked("mg_prolong"));
-    k_mg_cheb<V, V><<<gs, MT, 0, L.st>>>(A, dinv, b, y, x, d, (V)0, (V)(1.0 / th));
-    BID_TRY(checked("mg_cheb"));
-    if (out0) k_mg_cheb<V, double><<<gs, MT, 0, L.st>>>(A, dinv, b, x, out0, d, (V)c1, (V)c2);
-    else k_mg_cheb<V, V><<<gs, MT, 0, L.st>>>(A, dinv, b, x, e, d, (V)c1, (V)c2);
-    return checked("mg_cheb");
+    BID_TRY(checked(lerr, "mg_prolong"));
+    lerr = launch(k_mg_cheb<V, V>, gs, L.st, A, dinv, b, y, x, d, (V)0, (V)(1.0 / th));
+    BID_TRY(checked(lerr, "mg_cheb"));
+    if (out0) lerr = launch(k_mg_cheb<V, double>, gs, L.st, A, dinv, b, x, out0, d, (V)c1, (V)c2);
+    else lerr = launch(k_mg_cheb<V, V>, gs, L.st, A, dinv, b, x, e, d, (V)c1, (V)c2);
+    return checked(lerr, "mg_cheb");
 }
 
 // Sliced ELLPACK of a CSR matrix with values of type V.  Padding entries have
