@@ -46,11 +46,11 @@ sys.path.insert(0, ROOT)
 METRIC = "bidomain steps/s at PCG rel-res 1e-8 (chosen form); HBM GB/s of the factor solve"
 
 # DRAM bytes per algorithmic byte of one P_1 solve, from an ncu capture of the
-# same kernels on the 1025^2 slice (601.6 MB of DRAM traffic for 464.1 MB of
+# same kernels on the 1025^2 slice (601.7 MB of DRAM traffic for 464.1 MB of
 # algorithmic bytes at eps 1e-3, FP32, leaf 32); the traffic grows with the
 # factor, so the bench's roofline reports this ratio times its own algorithmic
 # bytes for the same form (other forms: null, no capture of the current kernels).
-TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 601.6 / 464.06}
+TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 601.7 / 464.06}
 
 
 def parse():
