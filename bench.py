@@ -71,6 +71,8 @@ def parse():
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
+    a.add_argument("--gpu-build", type=int, default=0,
+                   help="1: factor the large fronts on the GPU (bid_precond_opts.gpu_build)")
     a.add_argument("--no-mg", action="store_true",
                    help="skip the multigrid comparison (P_1, P_K by FP32 multigrid V-cycles)")
     a.add_argument("--no-cpu", action="store_true")
@@ -684,7 +686,7 @@ def main():
     if args.elliptic == "mg":
         args.eps = 0.0
     P = bid.Precond(S, p["dt"], eps=args.eps, precision=args.precision, leaf=args.leaf,
-                    scheme=args.scheme, elliptic=args.elliptic)
+                    scheme=args.scheme, elliptic=args.elliptic, gpu_build=args.gpu_build)
     chosen_stats = dict(P.stats)
     chosen = time_form(P)
 
@@ -759,7 +761,8 @@ def main():
     # ---- plain form on the same GPU, the same steps from the same state
     plain = None
     if not args.no_plain:
-        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64", leaf=args.leaf, scheme=args.scheme)
+        Pp = bid.Precond(S, p["dt"], eps=0.0, precision="fp64", leaf=args.leaf, scheme=args.scheme,
+                         gpu_build=args.gpu_build)
         plain = time_form(Pp)
         plain_stats = Pp.stats
         del Pp
@@ -815,7 +818,7 @@ def main():
         "config": {
             "workload": workload_name(args, N, NH),
             "form": {"eps": args.eps, "factor_precision": args.precision, "leaf": args.leaf,
-                     "scheme": args.scheme, "elliptic": args.elliptic},
+                     "scheme": args.scheme, "elliptic": args.elliptic, "gpu_build": args.gpu_build},
             "mean_pcg_iters": mean_it,
             "l2": "inputs larger than L2 (factor + matrices several GB)",
             "parallelism": f"replicas{world}" if world > 1 else "single GPU",

@@ -45,7 +45,7 @@ class Params(C.Structure):
 class PrecondOpts(C.Structure):
     _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("precision", C.c_int32),
                 ("leaf_size", C.c_int32), ("block", C.c_int32), ("n_threads", C.c_int32),
-                ("scheme", C.c_int32), ("elliptic", C.c_int32)]
+                ("scheme", C.c_int32), ("elliptic", C.c_int32), ("gpu_build", C.c_int32)]
 
 
 class PrecondStats(C.Structure):
@@ -233,7 +233,7 @@ class System:
             self.h = None
 
 
-def _opts(dt, eps, precision, leaf, block, threads, scheme="euler", elliptic="hchol"):
+def _opts(dt, eps, precision, leaf, block, threads, scheme="euler", elliptic="hchol", gpu_build=None):
     o = PrecondOpts()
     lib.bid_precond_opts_default(C.byref(o))
     o.dt, o.eps = float(dt), float(eps)
@@ -241,6 +241,8 @@ def _opts(dt, eps, precision, leaf, block, threads, scheme="euler", elliptic="hc
     o.leaf_size, o.block, o.n_threads = int(leaf), int(block), int(threads)
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     o.elliptic = ELLIPTIC[elliptic] if isinstance(elliptic, str) else int(elliptic)
+    if gpu_build is not None:
+        o.gpu_build = int(bool(gpu_build))
     return o
 
 
@@ -248,8 +250,8 @@ class Precond:
     """bid_precond: P_Lambda for one time step dt, plus the PCG work vectors."""
 
     def __init__(self, system: System, dt, eps=0.0, precision="fp64", leaf=16, block=128,
-                 threads=0, scheme="euler", elliptic="hchol"):
-        o = _opts(dt, eps, precision, leaf, block, threads, scheme, elliptic)
+                 threads=0, scheme="euler", elliptic="hchol", gpu_build=None):
+        o = _opts(dt, eps, precision, leaf, block, threads, scheme, elliptic, gpu_build)
         h = _VP()
         _check(lib.bid_precond_build_ex(system.h, C.byref(o), C.byref(h)))
         self.h, self.system, self.dt = h, system, float(dt)

@@ -390,6 +390,7 @@ void bid_precond_opts_default(bid_precond_opts* o) {
     o->n_threads = 0;
     o->scheme = BID_SCHEME_EULER;
     o->elliptic = BID_ELLIPTIC_HCHOL;
+    o->gpu_build = 0;
 }
 
 int bid_precond_build(bid_system* s, double dt, double eps, int precision, bid_precond** out) {
@@ -430,6 +431,8 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knobs
     if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
     if (const char* ub = std::getenv("BID_UP_BROWS")) bo.up_brows = std::max(32, std::atoi(ub));
+    bo.gpu_front = o->gpu_build != 0;
+    if (const char* gf = std::getenv("BID_GPU_FRONT_NF")) bo.gpu_front_nf = std::max(16, std::atoi(gf));
     HFactorHost h1, hk;
     MgHost m1, mk;
     // P_K: K_m = gamma M_H + S_m (Sec. 5.2)

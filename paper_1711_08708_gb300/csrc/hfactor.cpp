@@ -391,29 +391,41 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
                     Fm[(size_t)rel[i] * nf + rel[j]] += Uc[(size_t)i * nbc + j];
             std::vector<double>().swap(W[c].Ustore);
         }
-        if (ni > 0) {
-            int bad = dense::potrf_partial(nf, ni, Fm.data(), nf, par);
-            if (bad) return bad;
-        }
-        if (nb > 0) {   // update matrix for the parent
+        std::vector<double> M;
+        if (o.gpu_front && ni > 0 && nf >= o.gpu_front_nf) {
+            // the dense work of a large front on the GPU: the same M_s and update matrix
+            M.resize((size_t)nf * ni);
             w.Ustore.assign((size_t)nb * nb, 0.0);
-            for (int i = 0; i < nb; ++i)
-                std::memcpy(&w.Ustore[(size_t)i * nb], &Fm[(size_t)(ni + i) * nf + ni],
-                            sizeof(double) * (i + 1));
-            if (ni > 0)
-                dense::syrk_lower_sub(nb, ni, &Fm[(size_t)ni * nf], nf, w.Ustore.data(), nb, par);
+            int bad = 0;
+            const int rc = gpu_front_factor(nf, ni, Fm.data(), M.data(), nb > 0 ? w.Ustore.data() : nullptr, &bad);
+            if (rc != BID_OK) return -rc;
+            if (bad) return bad;
+            std::vector<double>().swap(Fm);
+        } else {
+            if (ni > 0) {
+                int bad = dense::potrf_partial(nf, ni, Fm.data(), nf, par);
+                if (bad) return bad;
+            }
+            if (nb > 0) {   // update matrix for the parent
+                w.Ustore.assign((size_t)nb * nb, 0.0);
+                for (int i = 0; i < nb; ++i)
+                    std::memcpy(&w.Ustore[(size_t)i * nb], &Fm[(size_t)(ni + i) * nf + ni],
+                                sizeof(double) * (i + 1));
+                if (ni > 0)
+                    dense::syrk_lower_sub(nb, ni, &Fm[(size_t)ni * nf], nf, w.Ustore.data(), nb, par);
+            }
+            if (ni == 0) {
+                w.nd = 0;
+                return 0;
+            }
+            // M_s = [L_ss^-1 ; L_Bs L_ss^-1]  (nf x ni, row-major)
+            M.resize((size_t)nf * ni);
+            dense::trtri_lower(ni, Fm.data(), nf, M.data(), ni, par);
+            if (nb > 0)
+                dense::trmm_right_lower(nb, ni, &Fm[(size_t)ni * nf], nf, M.data(), ni,
+                                        &M[(size_t)ni * ni], ni, par);
+            std::vector<double>().swap(Fm);
         }
-        if (ni == 0) {
-            w.nd = 0;
-            return 0;
-        }
-        // M_s = [L_ss^-1 ; L_Bs L_ss^-1]  (nf x ni, row-major)
-        std::vector<double> M((size_t)nf * ni);
-        dense::trtri_lower(ni, Fm.data(), nf, M.data(), ni, par);
-        if (nb > 0)
-            dense::trmm_right_lower(nb, ni, &Fm[(size_t)ni * nf], nf, M.data(), ni,
-                                    &M[(size_t)ni * ni], ni, par);
-        std::vector<double>().swap(Fm);
         // low-rank groups: boundary rows of an upper cluster, in runs owned by one
         // ancestor separator, chunked to `lrows` rows; kept when the truncated
         // rank-revealing QR reaches eps with k (m + ni) <= m ni / 2
@@ -549,6 +561,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         }
         omp_set_max_active_levels(levels_before);
     }
+    if (fail < 0) return set_error(BID_ECUDA, "factorisation: the GPU front factorisation failed (CUDA error)");
     if (fail) return set_error(BID_EINVAL, "factorisation: non-positive pivot (matrix not SPD)");
 
     // with o.upper_levels, every cluster from the lowest tree level holding a

@@ -219,7 +219,16 @@ struct HBuildOpts {
     int group_bytes = GROUP_BYTES_DEFAULT;   // factor bytes of a flat group (see FGroup)
     int group_bytes_leaf = 0;                // the same for the leaf level (0: group_bytes)
     int up_brows = 512;                      // target rows per warp of a large-cluster backward task
+    // fronts with at least gpu_front_nf rows factorised on the GPU (gpu_front_factor)
+    bool gpu_front = false;
+    int gpu_front_nf = 1024;
 };
+// Dense numeric work of one front on the GPU (FP64): F (nf x nf, row-major,
+// lower part used) -> M = [L_ss^-1 ; L_Bs L_ss^-1] (nf x ni, row-major) and
+// the update matrix U = F_BB - L_Bs L_Bs^T (nb x nb, row-major, lower part
+// meaningful), nb = nf - ni.  *bad: 0, or 1 + the index of a non-positive
+// pivot.  One front at a time per process (serialised).
+int gpu_front_factor(int nf, int ni, const double* F, double* M, double* U, int* bad);
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  Every index in `pins` has its
 // row and column replaced by the identity and its input entry set to zero
