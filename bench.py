@@ -71,8 +71,8 @@ def parse():
     a.add_argument("--tol", type=float, default=1e-8)
     a.add_argument("--cpu-seconds", type=float, default=20.0)
     a.add_argument("--no-plain", action="store_true")
-    a.add_argument("--gpu-build", type=int, default=0,
-                   help="1: factor the large fronts on the GPU (bid_precond_opts.gpu_build)")
+    a.add_argument("--gpu-build", type=int, default=1,
+                   help="1: factor the large fronts on the GPU (bid_precond_opts.gpu_build); 0: host")
     a.add_argument("--no-mg", action="store_true",
                    help="skip the multigrid comparison (P_1, P_K by FP32 multigrid V-cycles)")
     a.add_argument("--no-cpu", action="store_true")

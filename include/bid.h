@@ -148,11 +148,12 @@ typedef struct bid_precond_opts {
                                  bid_solve use gamma = chi Cm / dt (EULER) or twice
                                  that (CN, STRANG) */
     int32_t elliptic;         /* BID_ELLIPTIC_*: how P_1 and P_K are applied */
-    int32_t gpu_build;        /* 1: the dense work of the large fronts (at least 1024
-                                 rows; BID_GPU_FRONT_NF overrides) of the hierarchical
-                                 factors runs on the GPU (FP64 Cholesky, inverse and
-                                 products; the symbolic tree, the small fronts and the
-                                 low-rank compression stay on the host); 0: host only */
+    int32_t gpu_build;        /* 1 (default): the dense work of the large fronts (at
+                                 least 1024 rows; BID_GPU_FRONT_NF overrides) of the
+                                 hierarchical factors runs on the GPU (FP64 Cholesky,
+                                 inverse and products, the same factors up to rounding);
+                                 the symbolic tree, the small fronts and the low-rank
+                                 compression stay on the host; 0: host only */
 } bid_precond_opts;
 
 typedef struct bid_precond_stats {

@@ -390,7 +390,7 @@ void bid_precond_opts_default(bid_precond_opts* o) {
     o->n_threads = 0;
     o->scheme = BID_SCHEME_EULER;
     o->elliptic = BID_ELLIPTIC_HCHOL;
-    o->gpu_build = 0;
+    o->gpu_build = 1;
 }
 
 int bid_precond_build(bid_system* s, double dt, double eps, int precision, bid_precond** out) {
