@@ -44,9 +44,15 @@ def test_noalloc_matches_allocating_entry_point(bid, precision, eps):
         r = ref.cpu().numpy()
         for call in range(2):
             x = torch.full((n,), np.nan, dtype=torch.float64, device=DEV)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
             rc = bid.lib.bid_apply_factor_noalloc(P.h, which, b.data_ptr(), x.data_ptr(), stream)
             assert rc == bid.OK, bid.lib.bid_last_error()
             torch.cuda.synchronize()
+            if call > 0:
+                # after the first call (which may load the module that holds the
+                # static array) a call takes no device memory at all
+                assert torch.cuda.mem_get_info()[0] == free0, which
             xn = x.cpu().numpy()
             assert np.isfinite(xn).all()
             assert np.abs(xn - r).max() <= 1e-12 * np.abs(r).max(), (which, call)
