@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <array>
 #include <atomic>
@@ -37,10 +38,77 @@ namespace {
 
 struct TNode {
     std::vector<int32_t> sep;   // vector indices eliminated at this cluster
-    int child[2] = {-1, -1};
+    int child[MAX_CHILDREN] = {-1, -1, -1, -1};
     int nchild = 0;
     int depth = 0;
 };
+
+// Merge pass over a nested-dissection tree: top-down, a node whose subtree
+// holds at least min_nodes nodes and whose two children both have children
+// absorbs the children's separators (eliminated first, then its own) and
+// adopts their children (up to four), which are visited in turn, so the
+// upper part of the tree has about half as many levels.  Returns the
+// compacted tree (reachable nodes only) and its roots.
+void merge_upper_levels(std::vector<TNode>& T, std::vector<int>& roots, int64_t min_nodes) {
+    const int n0 = (int)T.size();
+    std::vector<int64_t> size(n0, 0);
+    std::function<int64_t(int)> count = [&](int t) {
+        int64_t c = (int64_t)T[t].sep.size();
+        for (int k = 0; k < T[t].nchild; ++k) c += count(T[t].child[k]);
+        return size[t] = c;
+    };
+    for (int r : roots) count(r);
+    std::vector<int> stack(roots.begin(), roots.end());
+    while (!stack.empty()) {
+        const int t = stack.back();
+        stack.pop_back();
+        TNode& n = T[t];
+        if (n.nchild == 2 && size[t] >= min_nodes && T[n.child[0]].nchild > 0 && T[n.child[1]].nchild > 0) {
+            const int c0 = n.child[0], c1 = n.child[1];
+            std::vector<int32_t> sep;
+            sep.reserve(T[c0].sep.size() + T[c1].sep.size() + n.sep.size());
+            for (int c : {c0, c1}) sep.insert(sep.end(), T[c].sep.begin(), T[c].sep.end());
+            sep.insert(sep.end(), n.sep.begin(), n.sep.end());
+            n.sep.swap(sep);
+            int kids[MAX_CHILDREN], nk = 0;
+            for (int c : {c0, c1})
+                for (int k = 0; k < T[c].nchild; ++k) kids[nk++] = T[c].child[k];
+            n.nchild = nk;
+            for (int k = 0; k < nk; ++k) n.child[k] = kids[k];
+            T[c0].nchild = T[c1].nchild = 0;
+            T[c0].sep.clear();
+            T[c1].sep.clear();
+        }
+        for (int k = 0; k < n.nchild; ++k) stack.push_back(n.child[k]);
+    }
+    // compact: the nodes reachable from the roots, children remapped
+    std::vector<int> newid(n0, -1);
+    std::vector<TNode> C;
+    C.reserve(n0);
+    std::vector<int> order;
+    for (int r : roots) {
+        std::vector<int> st{r};
+        while (!st.empty()) {
+            const int t = st.back();
+            st.pop_back();
+            newid[t] = (int)order.size();
+            order.push_back(t);
+            for (int k = 0; k < T[t].nchild; ++k) st.push_back(T[t].child[k]);
+        }
+    }
+    for (int t : order) {
+        TNode m = T[t];
+        for (int k = 0; k < m.nchild; ++k) m.child[k] = newid[m.child[k]];
+        C.push_back(std::move(m));
+    }
+    for (int& r : roots) r = newid[r];
+    // depths of the merged tree (the build schedule picks subtrees by depth);
+    // a node comes before its children in `order`
+    for (int r : roots) C[r].depth = 0;
+    for (size_t i = 0; i < C.size(); ++i)
+        for (int k = 0; k < C[i].nchild; ++k) C[C[i].child[k]].depth = C[i].depth + 1;
+    T.swap(C);
+}
 
 struct NDBuilder {
     const CsrHost& A;
@@ -212,6 +280,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         troots.push_back(nd.build(all, 0));
     }
     std::vector<TNode>& T = nd.T;
+    int64_t merge_min = o.merge_min;
+    if (const char* e = std::getenv("BID_MERGE_MIN")) merge_min = std::max<int64_t>(0, std::atoll(e));
+    if (merge_min > 0) merge_upper_levels(T, troots, merge_min);
     const int nt = (int)T.size();
 
     // post-order, tree after tree
@@ -244,7 +315,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     F->pidx.resize(n);
     F->sn.resize(nt);
     std::vector<int32_t> posof(n);
-    std::vector<std::array<int, 2>> ch(nt, {-1, -1});
+    std::vector<std::array<int, MAX_CHILDREN>> ch(nt, {-1, -1, -1, -1});
     std::vector<int> nch(nt, 0), parent(nt, -1), depth(nt, 0);
     {
         int32_t pos = 0;
@@ -306,7 +377,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             h.inc_off = (int32_t)ioff;
             boff += h.nb;
             uoff += h.nb;
-            ioff += 2 * (int64_t)(h.ni + h.nb);
+            ioff += slot_stride(h) * (int64_t)(h.ni + h.nb);
         }
         if (ioff > INT32_MAX || boff > INT32_MAX)
             return set_error(BID_EINVAL, "factor index space exceeds 2^31");
@@ -333,7 +404,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             const HSnode& hc = F->sn[c];
             for (int32_t j = 0; j < hc.nb; ++j) {
                 const int32_t f = front_index(s, W[c].B[j]);
-                const int32_t slot = F->sn[s].inc_off + 2 * f + k;
+                const int32_t slot = F->sn[s].inc_off + slot_stride(F->sn[s]) * f + k;
                 F->inc[slot] = slot;
                 F->uout[hc.u_off + j] = slot;
             }
@@ -349,7 +420,9 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     }
     for (int s = 0; s < nt; ++s) {
         HSnode& h = F->sn[s];
-        h.large = (h.ni > SMALL_NI || h.ni + h.nb > SMALL_NF) ? 1 : 0;
+        // clusters with more than two children (merged upper levels) always
+        // take the large-cluster kernels (the flat kernels read two slots per row)
+        h.large = (h.ni > SMALL_NI || h.ni + h.nb > SMALL_NF || h.nchild > 2) ? 1 : 0;
     }
 
     // ---------------- numeric factorisation
@@ -635,7 +708,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         int64_t ioff = 0;
         for (int s2 : order) {
             inc_new[s2] = (int32_t)ioff;
-            ioff += 2 * (int64_t)(F->sn[s2].ni + F->sn[s2].nb);
+            ioff += slot_stride(F->sn[s2]) * (int64_t)(F->sn[s2].ni + F->sn[s2].nb);
         }
         F->inc.assign(ioff, -1);
         for (int p2 = 0; p2 < nt; ++p2)
@@ -747,7 +820,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             g.ub += h.ni;
             g.nbt += h.nb;
             end = blk_end[s];
-            send = h.inc_off + 2 * (int64_t)(h.ni + h.nb);
+            send = h.inc_off + slot_stride(h) * (int64_t)(h.ni + h.nb);
             kids = kids || h.nchild > 0;
         }
         flush();
@@ -870,7 +943,7 @@ void cluster_liveness(const HFactorHost& F, const std::vector<uint8_t>& vlive, s
     std::vector<int32_t> owner(std::max<int64_t>(F.nslots, 1), -1), order(nc);
     for (int s = 0; s < nc; ++s) {
         const HSnode& h = F.sn[s];
-        for (int64_t k = h.inc_off; k < h.inc_off + 2 * (int64_t)(h.ni + h.nb) && k < F.nslots; ++k)
+        for (int64_t k = h.inc_off; k < h.inc_off + slot_stride(h) * (int64_t)(h.ni + h.nb) && k < F.nslots; ++k)
             if (k >= 0) owner[k] = s;
         for (int i = 0; i < h.ni; ++i) {
             const int32_t vi = F.pidx[h.first + i];

@@ -60,8 +60,11 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
         xp[i] = pinned ? 0.0 : b[v] - (vshift ? (*vshift)[v] : shift);
     }
     auto incoming = [&](const HSnode& s, int f) {
-        const int o = s.inc_off + 2 * f;
-        return (F.inc[o] >= 0 ? inb[o] : 0.0) + (F.inc[o + 1] >= 0 ? inb[o + 1] : 0.0);
+        const int st = slot_stride(s);
+        const int o = s.inc_off + st * f;
+        double v = (F.inc[o] >= 0 ? inb[o] : 0.0) + (F.inc[o + 1] >= 0 ? inb[o + 1] : 0.0);
+        for (int k = 2; k < st; ++k) v += F.inc[o + k] >= 0 ? inb[o + k] : 0.0;
+        return v;
     };
     auto gather = [&](const HSnode& s, int i) { return xp[s.first + i] + incoming(s, i); };
     auto finish = [&](const HSnode& s, int R, double acc) {

@@ -109,10 +109,12 @@ struct HView {
     const HTask* __restrict__ ubt;
 };
 
-// sum of the (up to two) children's contributions to frontal row f
+// sum of the children's contributions to frontal row f (two slots per row,
+// four for a merged cluster), in slot order
 __device__ __forceinline__ double incoming(const HView& v, const HSnode& sn, int f,
                                            const double* inb) {
-    const int o = sn.inc_off + 2 * f;
+    const int st = slot_stride(sn);
+    const int o = sn.inc_off + st * f;
     const int2 flags = *reinterpret_cast<const int2*>(v.inc + o);
     // L2 load: in the persistent upper-level kernels the slots are written by
     // other CTAs earlier in the same launch (L1 is not coherent across SMs)
@@ -120,6 +122,12 @@ __device__ __forceinline__ double incoming(const HView& v, const HSnode& sn, int
     double s = 0.0;
     if (flags.x >= 0) s += val.x;
     if (flags.y >= 0) s += val.y;
+    if (st > 2) {
+        const int2 f2 = *reinterpret_cast<const int2*>(v.inc + o + 2);
+        const double2 v2 = __ldcg(reinterpret_cast<const double2*>(inb + o + 2));
+        if (f2.x >= 0) s += v2.x;
+        if (f2.y >= 0) s += v2.y;
+    }
     return s;
 }
 

@@ -87,7 +87,7 @@ struct HSnode {
     int32_t first, ni, nb, nd;
     int32_t bidx_off;   // B_s entries (vector indices) at bidx[bidx_off ...]
     int32_t u_off;      // uout[u_off + j]: slot of update row j in the parent's inputs
-    int32_t inc_off;    // 2 input slots per frontal row at inb[inc_off + 2f + k]
+    int32_t inc_off;    // slot_stride input slots per frontal row at inb[inc_off + stride f + k]
                         // (child k's contribution), valid iff inc[...] >= 0
     int32_t height;
     int64_t data_off;   // packed dense columns
@@ -95,8 +95,12 @@ struct HSnode {
     int32_t lr_begin, lr_end;
     int32_t large;      // 1: chunked upper-level tasks (may hold low-rank groups); 0: flat items
     int32_t v_off;      // large clusters: backward input staged at vbuf[v_off ...]
-    int32_t nchild;     // children in the cluster tree (0: no incoming updates)
+    int32_t nchild;     // children in the cluster tree (0: no incoming updates; up to 4 for a
+                        // cluster merged with its two children's separators)
 };
+// Update slots per frontal row of a cluster: one per child, two or four.
+BID_HD int slot_stride(const HSnode& s) { return s.nchild > 2 ? 4 : 2; }
+constexpr int MAX_CHILDREN = 4;
 // Number of stored (nonzero) entries of columns 0 .. j-1 of the dense part.
 BID_HD int64_t col_offset(int64_t nd, int64_t j) { return j * nd - j * (j - 1) / 2; }
 // Start of column j inside the cluster's dense data.  Column c holds rows
@@ -219,6 +223,9 @@ struct HBuildOpts {
     int group_bytes = GROUP_BYTES_DEFAULT;   // factor bytes of a flat group (see FGroup)
     int group_bytes_leaf = 0;                // the same for the leaf level (0: group_bytes)
     int up_brows = 512;                      // target rows per warp of a large-cluster backward task
+    // merge pass over the cluster tree (merge_upper_levels): subtrees of at
+    // least merge_min nodes have their levels merged in pairs; 0: off
+    int64_t merge_min = 0;
     // fronts with at least gpu_front_nf rows factorised on the GPU (gpu_front_factor)
     bool gpu_front = false;
     int gpu_front_nf = 1024;
