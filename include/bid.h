@@ -48,6 +48,12 @@
  *    BID_FLATP=1     persistent double-buffered launches on the flat levels
  *                    with more groups than resident CTAs instead of one CTA
  *                    per group;
+ *    BID_MERGE_MIN=n in the cluster tree, every subtree of at least n nodes has
+ *                    its separator merged with its two children's (half as many
+ *                    upper levels; read at preconditioner build);
+ *    BID_UP_BROWS=n  target rows per warp of the large-cluster backward tasks
+ *                    (default 512; read at preconditioner build);
+ *    BID_GPU_FRONT_NF=n  smallest front factorised on the GPU (default 1024);
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the
