@@ -260,10 +260,10 @@ int bid_apply_factor(bid_precond* P, int which, const double* b, double* x, void
 
 /* Same result as bid_apply_factor, but the call allocates nothing.  (The paper
  * has no counterpart: this is a library service.)  It is meant for callers
- * that cannot call cudaMalloc at the moment they solve: code running under a
- * stream capture in the global capture mode, where the allocator is illegal;
- * a real-time loop that must not pay for the allocator's implicit device
- * synchronisation; or a host that gives the library a fixed memory budget.
+ * that cannot call cudaMalloc at the moment they solve: a real-time loop that
+ * must not pay for the allocator's implicit device synchronisation, or a host
+ * application that hands the library a fixed memory budget up front and
+ * forbids device allocations afterwards.
  * bid_apply_factor itself only uses buffers made by bid_precond_build, but
  * this variant takes its scratch (the forward-pass, update, rank, partial-sum
  * and ticket buffers) from one static device array of 2^21 doubles (16 MiB)

@@ -268,8 +268,8 @@ class Precond:
     def apply_factor_noalloc(self, which, b, x, stream=None, check=True):
         """bid_apply_factor without any allocation: scratch comes from the
         library's static 16 MiB device array (for callers that cannot call
-        cudaMalloc, e.g. inside a global-mode stream capture).  Returns the
-        status code."""
+        cudaMalloc when they solve, e.g. a real-time loop or a fixed memory
+        budget).  Returns the status code."""
         rc = lib.bid_apply_factor_noalloc(self.h, int(which), _ptr(b), _ptr(x), _stream(stream))
         if check:
             _check(rc)

@@ -1,10 +1,10 @@
 """The allocation-free factor solve (bid_apply_factor_noalloc) gives the same
 result as bid_apply_factor, called twice in a row through the C ABI.
 
-It exists for callers that cannot call cudaMalloc when they solve (inside a
-global-mode stream capture, in a real-time loop that must avoid the
-allocator's implicit synchronisation, or under a fixed memory budget), so its
-scratch lives in one static device array.  This file is collected last so that
+It exists for callers that cannot call cudaMalloc when they solve (a
+real-time loop that must avoid the allocator's implicit synchronisation, or an
+application that gives the library a fixed memory budget and forbids device
+allocations afterwards), so its scratch lives in one static device array.  This file is collected last so that
 a run stopping at the first failure has run every other test already; it
 passes both alone in a fresh process and after the rest of the suite.
 """
