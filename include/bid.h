@@ -53,13 +53,18 @@
  *                    upper levels; read at preconditioner build);
  *    BID_UP_BROWS=n  target rows per warp of the large-cluster backward tasks
  *                    (default 512; read at preconditioner build);
+ *    BID_MID_BYTES=n largest block (bytes) of a large cluster solved by one CTA
+ *                    with its whole block in shared memory (default 98304; 0:
+ *                    every large cluster takes the chunked kernels; read at
+ *                    preconditioner build);
  *    BID_GPU_FRONT_NF=n  smallest front factorised on the GPU (default 1024);
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the
  *    masked solve's clusters computed in full (all of them with BID_MASK=0,
  *    those of the levels that BID_TREE or BID_UPPER take over) round
- *    differently.
+ *    differently, and that BID_MID_BYTES changes the summation order of the
+ *    large clusters it moves between the two kinds of kernels.
  */
 #ifndef BID_H
 #define BID_H
@@ -191,6 +196,11 @@ typedef struct bid_precond_stats {
     int32_t flatp_levels1, flatp_levelsk;  /* flat levels solved by persistent double-
                                           buffered launches (more groups than resident
                                           CTAs), forward pass; 0 unless BID_FLATP=1 */
+    int64_t mid_clusters1, mid_clustersk;  /* large clusters solved by one CTA each with
+                                          their whole block in shared memory (at most
+                                          BID_MID_BYTES bytes, default 96 KiB; 0 turns
+                                          them off); the other large clusters take the
+                                          chunked kernels */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {

@@ -431,6 +431,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (const char* gb = std::getenv("BID_GROUP_BYTES")) bo.group_bytes = std::atoi(gb);   // tuning knobs
     if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
     if (const char* ub = std::getenv("BID_UP_BROWS")) bo.up_brows = std::max(32, std::atoi(ub));
+    if (const char* mb = std::getenv("BID_MID_BYTES")) bo.mid_bytes = std::max(0, std::atoi(mb));
     bo.gpu_front = o->gpu_build != 0;
     if (const char* gf = std::getenv("BID_GPU_FRONT_NF")) bo.gpu_front_nf = std::max(16, std::atoi(gf));
     HFactorHost h1, hk;
@@ -545,11 +546,14 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.factor_bytes = 2 * st.alg_bytes_p1 + st.alg_bytes_pk;   // one P_Lambda^-1: 2 P_1 + 1 P_K
     auto large_levels = [](const HFactorHost& h) {
         int32_t c = 0;
-        for (size_t L = 0; L + 1 < h.vg_ptr.size(); ++L) c += h.vg_ptr[L + 1] > h.vg_ptr[L];
+        for (size_t L = 0; L + 1 < h.vg_ptr.size(); ++L)
+            c += h.vg_ptr[L + 1] > h.vg_ptr[L] || h.mid_ptr[L + 1] > h.mid_ptr[L];
         return c;
     };
     st.large_levels1 = large_levels(h1);
     st.large_levelsk = large_levels(hk);
+    st.mid_clusters1 = (int64_t)h1.mid.size();
+    st.mid_clustersk = (int64_t)hk.mid.size();
     auto flatp_levels = [](const HFactorDev& d) {
         int32_t c = 0;
         if (hsolve_flatp_enabled())

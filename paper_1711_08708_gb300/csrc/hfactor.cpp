@@ -657,6 +657,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     std::vector<std::vector<int>> bylev(H);
     for (int s = 0; s < nt; ++s) bylev[F->sn[s].height].push_back(s);
     std::vector<int64_t> blk_end(nt, 0);   // end (elements) of each cluster's data block
+    std::vector<int64_t> blk_beg(nt, 0);   // its start (a vec boundary)
     {
         // data order: the small clusters level by level, leaves first (the flat
         // groups of a level are runs of this order, so a group's data is one
@@ -685,6 +686,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             SnWork& w = W[s];
             HSnode& h = F->sn[s];
             off = up(off);
+            blk_beg[s] = off;
             std::memcpy(F->data.data() + off, w.data.data(), w.data.size() * sizeof(double));
             h.nd = w.nd;
             h.data_off = off + w.dense_off;
@@ -758,12 +760,40 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
     F->ulr_ptr.assign(1, 0);
     F->uf_ptr.assign(1, 0);
     F->ub_ptr.assign(1, 0);
+    F->mid_ptr.assign(1, 0);
+    F->ulr_mid.clear();
+    F->mid.clear();
+    // mid clusters (MidCl): large clusters whose block fits one CTA's shared
+    // memory (not with the persistent upper-level path, whose schedule covers
+    // every large cluster by tasks)
+    std::vector<char> is_mid(nt, 0);
+    const int esz = 16 / vec;   // bytes per stored entry
+    auto mid_block_bytes = [&](int s) {   // the block and two trailing vectors
+        return ((blk_end[s] + vec - 1) / vec * vec - blk_beg[s] + 2 * (int64_t)vec) * esz;
+    };
+    for (int s = 0; s < nt; ++s) {
+        const HSnode& h = F->sn[s];
+        if (o.mid_bytes <= 0 || o.upper_levels || !h.large || h.ni == 0 || h.ni > MID_NI ||
+            h.nb > MID_NB || h.nd > MID_ND || mid_block_bytes(s) > o.mid_bytes)
+            continue;
+        int npair = 0;
+        for (const HLr& g : W[s].lr) npair += g.k;
+        is_mid[s] = npair <= MID_PAIRS && (int)W[s].lr.size() <= MID_GROUPS;
+    }
+    // a level takes the mid kernels only when all its large clusters fit (one
+    // launch per level and pass instead of two)
+    {
+        std::vector<char> all(H, 1);
+        for (int s = 0; s < nt; ++s)
+            if (F->sn[s].large && !is_mid[s]) all[F->sn[s].height] = 0;
+        for (int s = 0; s < nt; ++s)
+            if (!all[F->sn[s].height]) is_mid[s] = 0;
+    }
     int64_t tbuf = 0, pbuf = 0;
     int32_t tickets = 0;
     // cut the small clusters of one level into groups: consecutive clusters
     // (contiguous data) up to STAGE_CL clusters, STAGE_MAX staged values per
     // pass and GROUP_BYTES of data (a larger cluster forms a group alone)
-    const int esz = vec == 2 ? 8 : vec == 4 ? 4 : 2;
     auto make_groups = [&](const std::vector<int>& cl, int budget) {
         int32_t most = 0, most_nc = 0, most_wf = 0, most_wb = 0;
         FGroup g{};
@@ -843,18 +873,38 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             F->nlarge++;
             ni_max = std::max(ni_max, h.ni);
             nd_max = std::max(nd_max, h.nd);
-            for (HLr g : W[s].lr) {
-                g.t_off = (int32_t)tbuf;
-                tbuf += g.k;
-                F->lr.push_back(g);
+        }
+        // low-rank groups: the task clusters' first, then the mid clusters'
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) F->ulr_mid.push_back((int32_t)F->lr.size());
+            for (int s : bylev[L]) {
+                HSnode& h = F->sn[s];
+                if (!h.large || is_mid[s] != pass) continue;
+                h.lr_begin = (int32_t)F->lr.size();
+                for (HLr g : W[s].lr) {
+                    g.t_off = (int32_t)tbuf;
+                    tbuf += g.k;
+                    F->lr.push_back(g);
+                }
+                h.lr_end = (int32_t)F->lr.size();
             }
-            h.lr_end = (int32_t)F->lr.size();
         }
         make_groups(small, L == 0 && o.group_bytes_leaf > 0 ? o.group_bytes_leaf : o.group_bytes);
         F->fg_ptr.push_back((int32_t)F->fg.size());
         for (int s : bylev[L]) {
             const HSnode& h = F->sn[s];
             if (!h.large) continue;
+            if (is_mid[s]) {
+                MidCl m{};
+                m.blk = blk_beg[s];
+                m.s = s;
+                m.nbytes = (int32_t)mid_block_bytes(s);
+                m.dense = (int32_t)(h.data_off - blk_beg[s]);
+                for (int g = h.lr_begin; g < h.lr_end; ++g) m.npair += F->lr[g].k;
+                m.ng = h.lr_end - h.lr_begin;
+                F->mid.push_back(m);
+                continue;
+            }
             const int up_rows = UP_GROUPS * vec;   // a thread owns vec consecutive rows
             for (int a = 0; a < h.nd; a += up_rows) {
                 const int a1 = std::min(h.nd, a + up_rows);
@@ -906,7 +956,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             int64_t voff = 0;
             for (int s : bylev[L]) {
                 HSnode& h = F->sn[s];
-                if (!h.large || h.ni == 0) continue;
+                if (!h.large || h.ni == 0 || is_mid[s]) continue;
                 h.v_off = (int32_t)voff;
                 voff += h.nd + 2 * vec;
                 F->vgl.push_back(s);
@@ -919,6 +969,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         F->ulr_ptr.push_back((int32_t)F->lr.size());
         F->uf_ptr.push_back((int32_t)F->uft.size());
         F->ub_ptr.push_back((int32_t)F->ubt.size());
+        F->mid_ptr.push_back((int32_t)F->mid.size());
     }
     F->tbuf = tbuf;
     F->pbuf = pbuf;
@@ -971,7 +1022,8 @@ int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from
     int L = from;
     for (; L < H; ++L) {
         if (F.uf_ptr[L + 1] != F.uf_ptr[L] || F.ub_ptr[L + 1] != F.ub_ptr[L] ||
-            F.ulr_ptr[L + 1] != F.ulr_ptr[L] || F.vg_ptr[L + 1] != F.vg_ptr[L])
+            F.ulr_ptr[L + 1] != F.ulr_ptr[L] || F.vg_ptr[L + 1] != F.vg_ptr[L] ||
+            F.mid_ptr[L + 1] != F.mid_ptr[L])
             break;
         const int64_t b2 = std::max(blk, round16(F.fg_bytes[L]));
         const int64_t d2 = std::max(desc, (int64_t)F.fg_nc[L] * (int64_t)sizeof(GCl));

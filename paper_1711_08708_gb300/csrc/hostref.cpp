@@ -4,6 +4,7 @@
 // that the host logic can be verified without a GPU.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -17,9 +18,16 @@ struct bid_host_system {
 namespace bid {
 namespace {
 
+// BID_MID_BYTES in the environment: largest block of a mid cluster (as for
+// the device factors; 0 turns mid clusters off)
+int mid_bytes_env() {
+    const char* e = std::getenv("BID_MID_BYTES");
+    return e ? std::max(0, std::atoi(e)) : MID_BYTES_DEFAULT;
+}
+
 // x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
 // the same order, as the GPU launches (permuted input, per-level flat items
-// with their splits, large-cluster tasks, parent input slots).
+// with their splits, mid clusters, large-cluster tasks, parent input slots).
 // Returns false when a group's cluster data lies outside the group's block.
 // With a dataflow schedule T, the flat groups of its levels run in the order
 // of the dataflow kernels' signals instead of level by level, as early as the
@@ -83,6 +91,25 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
         return a;
     };
     const int H = (int)F.uf_ptr.size() - 1;
+    // a mid cluster's block: aligned, inside the array, and holding its dense
+    // columns (up to the last vector read) and its low-rank groups
+    auto mid_block_ok = [&](const MidCl& m) {
+        const HSnode& s = F.sn[m.s];
+        const int64_t end = m.blk + m.nbytes / esz;
+        if (m.blk % F.vec || m.nbytes % 16 || m.nbytes <= 0 || end > (int64_t)F.data.size() ||
+            m.dense != s.data_off - m.blk || s.data_off + col_start(s.nd, s.ni, F.vec) + 2 * F.vec > end ||
+            m.ng != s.lr_end - s.lr_begin || !s.large)
+            return false;
+        int npair = 0;
+        for (int g = s.lr_begin; g < s.lr_end; ++g) {
+            const HLr& G = F.lr[g];
+            npair += G.k;
+            if (G.s != m.s || G.off_u < m.blk || G.off_u + (int64_t)G.m * G.k > end || G.off_v < m.blk ||
+                G.off_v + (int64_t)s.ni * G.k > end)
+                return false;
+        }
+        return npair == m.npair;
+    };
     // forward of a flat group: per cluster, each dense row over all its
     // columns, and the group's data read inside its bulk-copied block
     auto fwd_group = [&](int g) {
@@ -147,6 +174,27 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 const HSnode& s = F.sn[si];
                 if (s.large && s.height == lev && !(*mask->live)[si]) scaled_copy(s);
             }
+        // mid clusters: the whole block in one CTA's shared memory
+        for (int mi = F.mid_ptr[lev]; mi < F.mid_ptr[lev + 1]; ++mi) {
+            const MidCl& m = F.mid[mi];
+            if (!mid_block_ok(m)) return false;
+            if (mask && !(*mask->live)[m.s]) continue;
+            const HSnode& s = F.sn[m.s];
+            for (int q = 0; q < s.nd; ++q) finish(s, drow(s, q), fwd_part(s, q, 0, s.ni));
+            for (int g = s.lr_begin; g < s.lr_end; ++g) {
+                const HLr& G = F.lr[g];
+                for (int l = 0; l < G.k; ++l) {
+                    double a = 0.0;
+                    for (int j = 0; j < s.ni; ++j) a += D[G.off_v + (int64_t)j * G.k + l] * gather(s, j);
+                    t[G.t_off + l] = a;
+                }
+                for (int i = 0; i < G.m; ++i) {
+                    double a = 0.0;
+                    for (int l = 0; l < G.k; ++l) a += D[G.off_u + (int64_t)i * G.k + l] * t[G.t_off + l];
+                    finish(s, G.row0 + i, a);
+                }
+            }
+        }
         for (int ti = F.uf_ptr[lev]; ti < F.uf_ptr[lev + 1]; ++ti) {
             const HTask& k = F.uft[ti];
             if (mask && !(*mask->live)[k.s < 0 ? F.lr[-1 - k.s].s : k.s]) continue;
@@ -220,6 +268,18 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             const HTask& k = F.ubt[ti];
             const HSnode& s = F.sn[k.s];
             for (int j = k.a0; j < k.a1; ++j) {
+                double a = 0.0;
+                for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
+                for (int g = s.lr_begin; g < s.lr_end; ++g) {
+                    const HLr& G = F.lr[g];
+                    for (int l = 0; l < G.k; ++l) a += D[G.off_v + (int64_t)j * G.k + l] * t[G.t_off + l];
+                }
+                xs.push_back({F.pidx[s.first + j], a});
+            }
+        }
+        for (int mi = F.mid_ptr[lev]; mi < F.mid_ptr[lev + 1]; ++mi) {
+            const HSnode& s = F.sn[F.mid[mi].s];
+            for (int j = 0; j < s.ni; ++j) {
                 double a = 0.0;
                 for (int q = j; q < s.nd; ++q) a += elem(s, q, j) * vrow(s, q);
                 for (int g = s.lr_begin; g < s.lr_end; ++g) {
@@ -318,6 +378,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
     if (precision < BID_FP64 || precision > BID_BF16) return set_error(BID_EINVAL, "bad precision");
     if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
     HBuildOpts o;
+    o.mid_bytes = mid_bytes_env();
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
@@ -356,6 +417,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
         stats->lowrank_entries = F.lowrank_entries;
         stats->dense_blocks = F.nlarge;
         stats->lowrank_blocks = F.nlr;
+        stats->mid_clusters1 = (int64_t)F.mid.size();
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
     }
@@ -371,6 +433,7 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
     for (int64_t i = a.NH; i < a.N; ++i)
         if (b[i] != 0.0) return set_error(BID_EINVAL, "b must be zero outside the heart nodes");
     HBuildOpts o;
+    o.mid_bytes = mid_bytes_env();
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
@@ -422,6 +485,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         lay.hoff.push_back(lay.hoff.back() + hs[s]->a.NH);
     }
     HBuildOpts o;
+    o.mid_bytes = mid_bytes_env();
     o.eps = eps;
     o.leaf = leaf_default;
     o.block = block;

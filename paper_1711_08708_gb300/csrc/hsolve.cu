@@ -107,6 +107,7 @@ struct HView {
     const GCl* __restrict__ gcl;
     const HTask* __restrict__ uft;
     const HTask* __restrict__ ubt;
+    const MidCl* __restrict__ mid;
 };
 
 // sum of the children's contributions to frontal row f (two slots per row,
@@ -1207,6 +1208,351 @@ __global__ void __launch_bounds__(HT) k_up_bwd(HView v, const T* __restrict__ da
     up_bwd_task<T, A>(v, data, t, sn, dst, vbuf, tbuf, out, red);
 }
 
+// ------------------------------------------------------------ mid clusters
+// One CTA of MID_THREADS threads per mid cluster (MidCl) and pass.  Before the
+// dependency wait, thread 0 starts the bulk copy of the cluster's block (its
+// low-rank U and V, then its dense columns: immutable data) and the CTA
+// stages the group descriptors, a table of the low-rank product entries and
+// the output indices; after the wait it stages the inputs, waits for the copy
+// and computes from shared memory:
+//  forward:  each dense row over its columns (threads = row groups of vec
+//            rows x column chunks) and t_g = V_g^T w of every low-rank group
+//            (threads = product entries x row chunks), the chunks summed in
+//            order; then every low-rank row U_g(i, :) t_g (one thread per
+//            row); pivot rows go to y, boundary rows to the parent's update
+//            slots;
+//  backward: t_g = U_g^T v_g (entries x row chunks), then every column
+//            (threads = columns x chunks of its dense rows and of the
+//            low-rank entries), the chunks summed in order.
+// No partial sums leave the CTA, so a mid level needs no tickets and no
+// backward preparation launch.
+constexpr int MT = MID_THREADS;
+static_assert(MT >= 2 * MID_PAIRS && MT >= 2 * MID_NI, "a thread per product entry / column");
+
+__device__ __forceinline__ float lds1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float lds1(const float* p) { return *p; }
+__device__ __forceinline__ double lds1(const double* p) { return *p; }
+
+// sum of the update slots of frontal row f in slot order (a slot no child
+// writes holds zero, so the sum equals incoming())
+__device__ __forceinline__ double slot_sum(const HSnode& sn, int f, const double* inb) {
+    const int st = slot_stride(sn);
+    const double* p = inb + sn.inc_off + st * f;
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    double s = a.x + a.y;
+    if (st > 2) {
+        const double2 b = __ldcg(reinterpret_cast<const double2*>(p + 2));
+        s += b.x;
+        s += b.y;
+    }
+    return s;
+}
+
+// product entry p of a mid cluster's low-rank groups (entries numbered group
+// by group): offsets of V(0, l) and U(0, l) inside the block, rank, rows
+__device__ __forceinline__ MidPair mid_pair(const HLr* gd, int ng, int p, int64_t blk, int ni) {
+    int g = 0, pb = 0;
+    while (g < ng - 1 && pb + gd[g].k <= p) {
+        pb += gd[g].k;
+        ++g;
+    }
+    const int l = p - pb;
+    MidPair r{};
+    r.voff = (int)(gd[g].off_v - blk) + l;
+    r.uoff = (int)(gd[g].off_u - blk) + l;
+    r.k = gd[g].k;
+    r.rb = gd[g].row0 - ni;
+    r.m = gd[g].m;
+    return r;
+}
+
+// largest power of two c <= cmax with n * c <= MT (chunks per item)
+__device__ __forceinline__ int mid_chunks(int n, int cmax) {
+    int c = 1;
+    while (c < cmax && n * c * 2 <= MT) c *= 2;
+    return c;
+}
+
+// Work before the dependency wait (immutable data only): thread 0 arms the
+// barrier and starts the block's bulk copy (when `copy`); the CTA stages the
+// group descriptors and the product-entry table.  The first barrier makes the
+// mbarrier's initialisation and the staged descriptors visible to every
+// thread, the second the table.
+template <typename T>
+__device__ __forceinline__ void mid_start(const HView& v, const T* __restrict__ data, const MidCl& c,
+                                          const HSnode& sn, const MidLayout& lay, unsigned char* smem,
+                                          uint64_t* bar, bool copy) {
+    if (copy && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, (uint32_t)c.nbytes);
+        bulk_region(smem, data + c.blk, c.nbytes, bar);
+    }
+    HLr* gd = reinterpret_cast<HLr*>(smem + lay.gd);
+    for (int g = threadIdx.x; g < c.ng; g += MT) gd[g] = v.lr[sn.lr_begin + g];
+    __syncthreads();
+    MidPair* pt = reinterpret_cast<MidPair*>(smem + lay.pt);
+    for (int p = threadIdx.x; p < c.npair; p += MT) pt[p] = mid_pair(gd, c.ng, p, c.blk, sn.ni);
+    __syncthreads();
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(MT) k_mid_fwd(HView v, const T* __restrict__ data, int m0, MidLayout lay,
+                                                const double* xp, double* ybuf, double* inb,
+                                                unsigned int* err, MaskArgs mk) {
+    constexpr int VEC = VecOf<T>::N;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x;
+    const MidCl c = v.mid[m0 + blockIdx.x];
+    const HSnode sn = v.sn[c.s];
+    const int ni = sn.ni, nd = sn.nd, nb = sn.nb;
+    const bool dead = mk.live && !mk.live[m0 + blockIdx.x];
+    int32_t* us = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);   // update slot of boundary row r
+    int32_t* dr = reinterpret_cast<int32_t*>(dyn_smem + lay.dr);   // dense boundary row q - ni, minus ni
+    if (!dead) {
+        for (int r = tid; r < nb; r += MT) us[r] = v.uout[sn.u_off + r];
+        for (int q = tid; q < nd - ni; q += MT) dr[q] = v.drows[sn.drow_off + q] - ni;
+    }
+    mid_start<T>(v, data, c, sn, lay, dyn_smem, &bar, !dead);
+    pdl_wait();
+    pdl_trigger();
+    if (dead) {   // constant input -c: scaled all-ones results
+        const double c0 = mask_c0(mk);
+        for (int i = tid; i < ni; i += MT)
+            ybuf[sn.first + i] = mask_c(mk, c0, mk.seg ? v.pidx[sn.first + i] : 0) * mk.y1[sn.first + i];
+        for (int r = tid; r < nb; r += MT) {
+            const int32_t slot = v.uout[sn.u_off + r];
+            inb[slot] = mask_c(mk, c0, mk.seg ? v.bidx[sn.bidx_off + r] : 0) * mk.y1slot[slot];
+        }
+        return;
+    }
+    A* w = reinterpret_cast<A*>(dyn_smem + lay.w);
+    double* ib = reinterpret_cast<double*>(dyn_smem + lay.ib);
+    for (int i = tid; i < ni; i += MT) w[i] = (A)(xp[sn.first + i] + (sn.nchild ? slot_sum(sn, i, inb) : 0.0));
+    for (int r = tid; r < nb; r += MT) ib[r] = sn.nchild ? slot_sum(sn, ni + r, inb) : 0.0;
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar)) {
+        if (tid == 0) atomicOr(err, 1u);
+        return;
+    }
+    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    A* red = reinterpret_cast<A*>(dyn_smem + lay.red);
+    A* tl = reinterpret_cast<A*>(dyn_smem + lay.tl);
+    A* tp = reinterpret_cast<A*>(dyn_smem + lay.tp);
+    const MidPair* pt = reinterpret_cast<const MidPair*>(dyn_smem + lay.pt);
+    // dense rows: thread = (row group rg of VEC rows, column chunk cs)
+    const int RG = (nd + VEC - 1) / VEC;
+    const int CS = mid_chunks(RG, 16), RGP = MT / CS;
+    {
+        const int rg = tid % RGP, cs = tid / RGP;
+        A acc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = 0;
+        if (rg < RG) {
+            const int q0 = rg * VEC;
+            // a row group of pivot rows stops at its diagonal, others span all columns
+            const int jlast = q0 + VEC - 1 < ni ? q0 + VEC : ni;
+            const int chunk = (ni + CS - 1) / CS;
+            const int j0 = cs * chunk, j1 = min(jlast, j0 + chunk);
+            if (j0 < j1) {
+                const T* base = sd + c.dense + q0;
+                int off = (int)col_start(nd, j0, VEC) - j0;
+                int j = j0;
+                for (; j + 1 < j1; j += 2) {   // two columns' loads ahead of their products
+                    const int off1 = off + nd - j - 1 + ((j + 1 - nd) & (VEC - 1));
+                    A v0[VEC], v1[VEC];
+                    lds16(base + off, v0);
+                    lds16(base + off1, v1);
+                    const A w0 = w[j], w1 = w[j + 1];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        if (q0 + e >= j) acc[e] += v0[e] * w0;
+                        if (q0 + e >= j + 1) acc[e] += v1[e] * w1;
+                    }
+                    off = off1 + nd - j - 2 + ((j + 2 - nd) & (VEC - 1));
+                }
+                if (j < j1) {
+                    A v0[VEC];
+                    lds16(base + off, v0);
+                    const A w0 = w[j];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e)
+                        if (q0 + e >= j) acc[e] += v0[e] * w0;
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) red[tid * VEC + e] = acc[e];
+    }
+    // low-rank: thread = (product entry p, row chunk jc) of t = V^T w
+    const int P = c.npair;
+    const int JC = P > 0 ? mid_chunks(P, 16) : 1, PP = MT / JC;
+    if (P > 0) {
+        const int p = tid % PP, jc = tid / PP;
+        A a = 0;
+        if (p < P) {
+            const MidPair e = pt[p];
+            const int chunk = (ni + JC - 1) / JC;
+            const int j0 = jc * chunk, j1 = min(ni, j0 + chunk);
+            for (int j = j0; j < j1; ++j) a += lds1(sd + e.voff + j * e.k) * w[j];
+        }
+        tp[tid] = a;
+    }
+    __syncthreads();
+    if (tid < RG) {   // RG <= MT / 2: the dense rows on the first half of the CTA
+        A s[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) s[e] = red[tid * VEC + e];
+        for (int k = 1; k < CS; ++k)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) s[e] += red[(k * RGP + tid) * VEC + e];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const int q = tid * VEC + e;
+            if (q < nd) {
+                if (q < ni) {
+                    ybuf[sn.first + q] = (double)s[e];
+                } else {
+                    const int r = dr[q - ni];
+                    inb[us[r]] = ib[r] - (double)s[e];
+                }
+            }
+        }
+    }
+    if (tid >= MT / 2 && tid - MT / 2 < P) {   // P <= MT / 2: the products on the second half
+        const int p = tid - MT / 2;
+        A s = tp[p];
+        for (int k = 1; k < JC; ++k) s += tp[k * PP + p];
+        tl[p] = s;
+    }
+    __syncthreads();
+    // low-rank rows, one thread per row: u = incoming - U_g(i, :) t_g
+    const HLr* gd = reinterpret_cast<const HLr*>(dyn_smem + lay.gd);
+    for (int r = tid;; r += MT) {
+        int g = 0, rb = 0, pb = 0;
+        while (g < c.ng && r >= rb + gd[g].m) {
+            rb += gd[g].m;
+            pb += gd[g].k;
+            ++g;
+        }
+        if (g >= c.ng) break;
+        const int i = r - rb, k = gd[g].k;
+        const T* U = sd + (gd[g].off_u - c.blk) + i * k;
+        A a = 0;
+        for (int l = 0; l < k; ++l) a += lds1(U + l) * tl[pb + l];
+        const int rr = gd[g].row0 - ni + i;
+        inb[us[rr]] = ib[rr] - (double)a;
+    }
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(MT) k_mid_bwd(HView v, const T* __restrict__ data, int m0, MidLayout lay,
+                                                const double* __restrict__ ybuf, double* out,
+                                                unsigned int* err) {
+    constexpr int VEC = VecOf<T>::N;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x;
+    const MidCl c = v.mid[m0 + blockIdx.x];
+    const HSnode sn = v.sn[c.s];
+    const int ni = sn.ni, nd = sn.nd, nb = sn.nb;
+    int32_t* bi = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);   // vector index of boundary row r
+    int32_t* dr = reinterpret_cast<int32_t*>(dyn_smem + lay.dr);
+    int32_t* po = reinterpret_cast<int32_t*>(dyn_smem + lay.po);   // vector index of pivot j
+    for (int r = tid; r < nb; r += MT) bi[r] = v.bidx[sn.bidx_off + r];
+    for (int q = tid; q < nd - ni; q += MT) dr[q] = v.drows[sn.drow_off + q] - ni;
+    for (int j = tid; j < ni; j += MT) po[j] = v.pidx[sn.first + j];
+    mid_start<T>(v, data, c, sn, lay, dyn_smem, &bar, true);
+    pdl_wait();
+    pdl_trigger();
+    A* vd = reinterpret_cast<A*>(dyn_smem + lay.w);    // v at the dense rows, zero tail of VEC
+    A* xb = reinterpret_cast<A*>(dyn_smem + lay.ib);   // -x_B (all boundary rows)
+    for (int q = tid; q < ni; q += MT) vd[q] = (A)ybuf[sn.first + q];
+    for (int r = tid; r < nb; r += MT) xb[r] = (A)(-out[bi[r]]);
+    for (int q = nd + tid; q < nd + VEC; q += MT) vd[q] = (A)0;
+    __syncthreads();
+    for (int q = ni + tid; q < nd; q += MT) vd[q] = xb[dr[q - ni]];
+    if (!mbar_wait_bounded(&bar)) {
+        if (tid == 0) atomicOr(err, 1u);
+        return;
+    }
+    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    A* red = reinterpret_cast<A*>(dyn_smem + lay.red);
+    A* tl = reinterpret_cast<A*>(dyn_smem + lay.tl);
+    A* tp = reinterpret_cast<A*>(dyn_smem + lay.tp);
+    const MidPair* pt = reinterpret_cast<const MidPair*>(dyn_smem + lay.pt);
+    // low-rank: thread = (product entry p, row chunk rc) of t = U^T v
+    const int P = c.npair;
+    const int RC = P > 0 ? mid_chunks(P, 16) : 1, PP = MT / RC;
+    if (P > 0) {
+        const int p = tid % PP, rc = tid / PP;
+        A a = 0;
+        if (p < P) {
+            const MidPair e = pt[p];
+            const int chunk = (e.m + RC - 1) / RC;
+            const int i0 = rc * chunk, i1 = min(e.m, i0 + chunk);
+            for (int i = i0; i < i1; ++i) a += lds1(sd + e.uoff + i * e.k) * xb[e.rb + i];
+        }
+        tp[tid] = a;
+    }
+    __syncthreads();
+    if (tid < P) {
+        A s = tp[tid];
+        for (int k = 1; k < RC; ++k) s += tp[k * PP + tid];
+        tl[tid] = s;
+    }
+    __syncthreads();
+    // columns: thread = (column j, chunk cc of its dense row vectors and of the
+    // low-rank entries)
+    const int CC = mid_chunks(ni, 16);
+    {
+        const int j = tid / CC, cc = tid % CC;
+        A acc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = 0;
+        if (j < ni) {
+            const T* cj = sd + c.dense + (int)col_start(nd, j, VEC) - j;
+            const int qa = j & ~(VEC - 1);
+            const int nv = (nd - qa + VEC - 1) / VEC;
+            const int per = (nv + CC - 1) / CC;
+            const int v0 = cc * per, v1 = min(nv, v0 + per);
+            int t = v0;
+            for (; t + 1 < v1; t += 2) {   // two vectors' loads ahead of their products
+                const int q0 = qa + t * VEC;
+                A a0[VEC], a1[VEC];
+                lds16(cj + q0, a0);
+                lds16(cj + q0 + VEC, a1);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    if (q0 + e >= j) acc[e] += a0[e] * vd[q0 + e];
+                    acc[e] += a1[e] * vd[q0 + VEC + e];
+                }
+            }
+            if (t < v1) {
+                const int q0 = qa + t * VEC;
+                A a0[VEC];
+                lds16(cj + q0, a0);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (q0 + e >= j) acc[e] += a0[e] * vd[q0 + e];
+            }
+            const int pper = (P + CC - 1) / CC;
+            const int p0 = cc * pper, p1 = min(P, p0 + pper);
+            for (int p = p0; p < p1; ++p) acc[0] += lds1(sd + pt[p].voff + j * pt[p].k) * tl[p];
+        }
+        A s = acc[0];
+#pragma unroll
+        for (int e = 1; e < VEC; ++e) s += acc[e];
+        red[tid] = s;
+    }
+    __syncthreads();
+    if (tid < ni) {
+        A s = red[tid * CC];
+        for (int k = 1; k < CC; ++k) s += red[tid * CC + k];
+        out[po[tid]] = (double)s;
+    }
+}
+
 // ------------------------------------------------------------ upper levels, persistent
 // The levels [lev0, lev1) hold only large clusters; one cooperative launch
 // per pass runs them all, the CTAs striding over each level's work items,
@@ -1308,6 +1654,7 @@ HView view_of(const HFactorDev& F) {
     v.gcl = F.gcl;
     v.uft = F.uft;
     v.ubt = F.ubt;
+    v.mid = F.mid;
     return v;
 }
 
@@ -1452,7 +1799,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                               sh, S.xp));
     }
     const int H = (int)F.uf_ptr.size() - 1;
-    MaskArgs mf{}, mu{};
+    MaskArgs mf{}, mu{}, mm{};
     if (masked && F.ones_ready && hsolve_mask_enabled()) {
         mf.csum = mu.csum = sh.sum;
         mf.cinv = mu.cinv = sh.inv_n;
@@ -1463,6 +1810,8 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         mf.y1slot = mu.y1slot = F.y1slot;
         mf.live = F.fg_live;
         mu.live = F.uf_live;
+        mm = mu;
+        mm.live = F.mid_live;
     }
     // upper levels in one persistent launch per pass when possible
     const int lu = (g_upper_ok == 1 && F.sched && S.gbar && F.lev_upper < H) ? F.lev_upper : H;
@@ -1527,6 +1876,13 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             }
             ++launches;
         }
+        const int nm = F.mid_ptr[lev + 1] - F.mid_ptr[lev];
+        if (nm > 0) {
+            const MidLayout& ly = F.mid_lay[lev];
+            BID_CUDA_TRY(launch_k(k_mid_fwd<T, A>, nm, MT, (size_t)ly.total, L.st, v, data, F.mid_ptr[lev], ly,
+                                  S.xp, S.ybuf, inb, S.err, mm));
+            ++launches;
+        }
         const int nt = F.uf_ptr[lev + 1] - F.uf_ptr[lev];
         if (nt > 0) {
             const int has_lr = F.ulr_ptr[lev + 1] > F.ulr_ptr[lev];
@@ -1552,7 +1908,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             lev = t0;
             continue;
         }
-        const int ng = F.ulr_ptr[lev + 1] - F.ulr_ptr[lev];
+        const int ng = F.ulr_mid[lev] - F.ulr_ptr[lev];   // the task clusters' low-rank groups
         const int nv = F.vg_ptr[lev + 1] - F.vg_ptr[lev];
         if (ng + nv > 0) {
             BID_CUDA_TRY(launch_k(k_bwd_prep<T, A>, ng + nv, HT, 0, L.st, v, data, F.ulr_ptr[lev], ng,
@@ -1563,6 +1919,13 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         if (nt > 0) {
             BID_CUDA_TRY(launch_k(k_up_bwd<T, A>, nt, HT, 0, L.st, v, data, F.ub_ptr[lev], S.vbuf, S.tbuf,
                                   out));
+            ++launches;
+        }
+        const int nm = F.mid_ptr[lev + 1] - F.mid_ptr[lev];
+        if (nm > 0) {
+            const MidLayout& ly = F.mid_lay[lev];
+            BID_CUDA_TRY(launch_k(k_mid_bwd<T, A>, nm, MT, (size_t)ly.total, L.st, v, data, F.mid_ptr[lev], ly,
+                                  S.ybuf, out, S.err));
             ++launches;
         }
         const int nf = F.fg_ptr[lev + 1] - F.fg_ptr[lev];
@@ -1613,6 +1976,10 @@ int prepare_one() {
                                       TREE_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_tree_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       TREE_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_mid_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      MID_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_mid_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      MID_SMEM_MAX));
     return BID_OK;
 }
 
@@ -1775,8 +2142,9 @@ static int upload_tree(const HFactorHost& h, int precision, HFactorDev* d) {
 }
 
 int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFactorDev* d) {
-    std::vector<uint8_t> live, fl(h.fg.size(), 0), ul(h.uft.size(), 0);
+    std::vector<uint8_t> live, fl(h.fg.size(), 0), ul(h.uft.size(), 0), ml(h.mid.size(), 0);
     cluster_liveness(h, vlive, &live);
+    for (size_t k = 0; k < h.mid.size(); ++k) ml[k] = live[h.mid[k].s];
     for (size_t g = 0; g < h.fg.size(); ++g)
         for (int c = h.fg[g].c0; c < h.fg[g].c1; ++c) fl[g] |= live[h.gcl[c].s];
     for (size_t k = 0; k < h.uft.size(); ++k) {
@@ -1785,8 +2153,10 @@ int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFa
     }
     fl.push_back(1);   // never empty
     ul.push_back(1);
+    ml.push_back(1);
     BID_TRY(upload_vec(fl, &d->fg_live));
     BID_TRY(upload_vec(ul, &d->uf_live));
+    BID_TRY(upload_vec(ml, &d->mid_live));
     BID_CUDA_TRY(cudaMalloc(&d->y1, sizeof(double) * std::max<int64_t>(h.n, 1)));
     BID_CUDA_TRY(cudaMalloc(&d->y1slot, sizeof(double) * std::max<int64_t>(h.nslots, 1)));
     d->ones_ready = false;
@@ -1825,6 +2195,71 @@ static int flat_persistent_grids(HFactorDev* d) {
         }
     }
     return BID_OK;
+}
+
+// Mid clusters: descriptors, and per level the shared-memory layout of its
+// launches, sized by the level's largest block, rows, groups and products.
+static int upload_mid(const HFactorHost& h, int precision, HFactorDev* d) {
+    const int H = (int)h.mid_ptr.size() - 1;
+    if (H < 0 || (int)h.ulr_mid.size() != H || (int)h.ulr_ptr.size() != H + 1)
+        return set_error(BID_EINVAL, "mid-cluster lists out of range");
+    const int esz = precision == BID_FP64 ? 8 : precision == BID_FP32 ? 4 : 2;
+    const int esz_a = precision == BID_FP64 ? 8 : 4;
+    const int vec = 16 / esz;
+    d->mid_ptr = h.mid_ptr;
+    d->ulr_mid = h.ulr_mid;
+    d->mid_lay.assign(H, MidLayout{});
+    for (int L = 0; L < H; ++L) {
+        if (h.ulr_mid[L] < h.ulr_ptr[L] || h.ulr_mid[L] > h.ulr_ptr[L + 1])
+            return set_error(BID_EINVAL, "mid-cluster groups out of range");
+        int64_t nbytes = 0;
+        int ni = 0, nd = 0, nb = 0, ndb = 0, np = 0, ng = 0;
+        for (int i = h.mid_ptr[L]; i < h.mid_ptr[L + 1]; ++i) {
+            const MidCl& m = h.mid[i];
+            const HSnode& s = h.sn[m.s];
+            // bulk copy: 16-byte aligned source, whole 16-byte chunks inside the array
+            if (m.nbytes <= 0 || m.nbytes % 16 || (m.blk * esz) % 16 ||
+                m.blk * esz + m.nbytes > (int64_t)h.data.size() * esz || s.ni > MID_NI || s.nb > MID_NB ||
+                s.nd > MID_ND || m.npair > MID_PAIRS || m.ng > MID_GROUPS || m.ng != s.lr_end - s.lr_begin ||
+                s.lr_begin < h.ulr_mid[L] || s.lr_end > h.ulr_ptr[L + 1] || (s.inc_off % 2))
+                return set_error(BID_EINVAL, "mid cluster out of range");
+            nbytes = std::max<int64_t>(nbytes, m.nbytes);
+            ni = std::max(ni, s.ni);
+            nd = std::max(nd, s.nd);
+            nb = std::max(nb, s.nb);
+            ndb = std::max(ndb, s.nd - s.ni);
+            np = std::max(np, m.npair);
+            ng = std::max(ng, m.ng);
+        }
+        if (h.mid_ptr[L + 1] == h.mid_ptr[L]) continue;
+        auto r16 = [](int64_t x) { return (x + 15) / 16 * 16; };
+        MidLayout y{};
+        int64_t o = (nbytes + 127) / 128 * 128;
+        y.w = (int32_t)o;
+        o += r16((int64_t)esz_a * (nd + vec));
+        y.ib = (int32_t)o;
+        o += r16(8LL * std::max(nb, 1));
+        y.red = (int32_t)o;
+        o += r16((int64_t)esz_a * MID_THREADS * vec);
+        y.tl = (int32_t)o;
+        o += r16((int64_t)esz_a * std::max(np, 1));
+        y.tp = (int32_t)o;
+        o += r16((int64_t)esz_a * MID_THREADS);
+        y.gd = (int32_t)o;
+        o += r16((int64_t)sizeof(HLr) * std::max(ng, 1));
+        y.pt = (int32_t)o;
+        o += r16((int64_t)sizeof(MidPair) * std::max(np, 1));
+        y.bi = (int32_t)o;
+        o += r16(4LL * std::max(nb, 1));
+        y.dr = (int32_t)o;
+        o += r16(4LL * std::max(ndb, 1));
+        y.po = (int32_t)o;
+        o += r16(4LL * std::max(ni, 1));
+        if (o > MID_SMEM_MAX) return set_error(BID_EINVAL, "mid level %d needs too much shared memory", L);
+        y.total = (int32_t)o;
+        d->mid_lay[L] = y;
+    }
+    return upload_vec(h.mid, &d->mid);
 }
 
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
@@ -1866,6 +2301,7 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.gcl, &d->gcl));
     BID_TRY(upload_vec(h.uft, &d->uft));
     BID_TRY(upload_vec(h.ubt, &d->ubt));
+    BID_TRY(upload_mid(h, precision, d));
     d->fg_ptr = h.fg_ptr;
     d->fg_bytes = h.fg_bytes;
     d->fg_nc = h.fg_nc;
@@ -1934,7 +2370,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
 void free_hfactor(HFactorDev* d) {
     void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout,  d->vgl, d->sn,
                     d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
-                    d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot};
+                    d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot,
+                    d->mid, d->mid_live};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

@@ -169,6 +169,42 @@ struct GCl {                        // a cluster of a group: descriptor and pref
 struct HTask {
     int32_t s, a0, a1, b0, b1, part, ticket, nparts;
 };
+// A large cluster whose whole block (its low-rank groups' U and V, then its
+// dense columns) fits one CTA's shared memory.  Such a cluster has no tasks:
+// one CTA per cluster and pass (k_mid_fwd / k_mid_bwd) copies the block with
+// bulk copies, stages its inputs and computes every row (forward) or column
+// (backward), the low-rank products included, with the partial sums of a row
+// or column combined in shared memory in a fixed order.  Its low-rank groups
+// follow the task clusters' groups of the same level (HFactorHost::ulr_mid),
+// so the backward preparation launch covers only the task clusters.
+struct MidCl {
+    int64_t blk;        // element offset of the block in `data` (16-byte aligned)
+    int32_t s;          // the cluster
+    int32_t nbytes;     // bytes copied: the block and two trailing vectors (multiple of 16)
+    int32_t dense;      // element offset of the dense columns inside the block
+    int32_t npair;      // sum of the ranks of its low-rank groups
+    int32_t ng;         // its low-rank groups
+    int32_t pad;
+};
+// Dynamic shared memory of a mid launch, per level (byte offsets): the block
+// at 0, then w (forward input / backward dense-row input, nd + vec values),
+// ib (forward: incoming updates of the boundary rows, FP64; backward: -x_B),
+// red (partial sums), tl / tp (low-rank products and their partial sums),
+// gd (group descriptors), pt (one MidPair per low-rank product entry),
+// bi (forward: the boundary rows' update slots; backward: their vector
+// indices), dr (dense boundary rows, minus ni), po (backward: the pivots'
+// vector indices).
+struct MidLayout {
+    int32_t w, ib, red, tl, tp, gd, pt, bi, dr, po, total;
+};
+struct MidPair {    // entry l of the low-rank group holding product entry p
+    int32_t voff, uoff, k, rb;   // V(0, l), U(0, l) inside the block; rank; first row - ni
+    int32_t m, pad0, pad1, pad2;
+};
+constexpr int MID_BYTES_DEFAULT = 96 * 1024;   // largest block of a mid cluster (bytes)
+constexpr int MID_THREADS = 512;
+constexpr int MID_NI = 256, MID_NB = 1024, MID_ND = 512, MID_PAIRS = 256, MID_GROUPS = 32;
+constexpr int MID_SMEM_MAX = 224 * 1024;
 
 struct HFactorHost {
     int64_t n = 0;
@@ -192,6 +228,9 @@ struct HFactorHost {
     std::vector<int32_t> uf_ptr, ub_ptr;       // level -> task ranges
     std::vector<HTask> uft, ubt;
     std::vector<int32_t> u_ni_max, u_nd_max;   // level -> max ni / nd (shared memory)
+    std::vector<int32_t> ulr_mid;              // level -> first low-rank group of its mid clusters
+    std::vector<MidCl> mid;                    // mid clusters, level by level
+    std::vector<int32_t> mid_ptr;              // level -> mid cluster range
     int64_t ubuf = 0, tbuf = 0, pbuf = 0, nslots = 0, vbuf = 0;
     int32_t ntickets = 0;
     int32_t vec = 2;
@@ -223,6 +262,7 @@ struct HBuildOpts {
     int group_bytes = GROUP_BYTES_DEFAULT;   // factor bytes of a flat group (see FGroup)
     int group_bytes_leaf = 0;                // the same for the leaf level (0: group_bytes)
     int up_brows = 512;                      // target rows per warp of a large-cluster backward task
+    int mid_bytes = MID_BYTES_DEFAULT;       // largest block of a mid cluster (MidCl); 0: none
     // merge pass over the cluster tree (merge_upper_levels): subtrees of at
     // least merge_min nodes have their levels merged in pairs; 0: off
     int64_t merge_min = 0;
@@ -274,6 +314,9 @@ struct HFactorDev {
     GCl* gcl = nullptr;
     HTask* uft = nullptr;
     HTask* ubt = nullptr;
+    MidCl* mid = nullptr;
+    std::vector<int32_t> mid_ptr, ulr_mid;
+    std::vector<MidLayout> mid_lay;     // per level (mid clusters' shared memory)
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
     double* inb = nullptr;              // update slots (nslots, zero where no child writes)
@@ -295,10 +338,11 @@ struct HFactorDev {
     int32_t tree_sc_off = 0, tree_w_off = 0, tree_smem_f = 0, tree_smem_b = 0;
     int32_t tree_cta_f = 0, tree_cta_b = 0;   // resident CTAs per SM
     // masked solve (upload_liveness): live flags per flat group / upper forward
-    // task, and the forward results of the all-ones input (y1: ybuf, y1slot:
+    // task / mid cluster, and the forward results of the all-ones input (y1: ybuf, y1slot:
     // update slots), filled by hsolve_ones
     uint8_t* fg_live = nullptr;
     uint8_t* uf_live = nullptr;
+    uint8_t* mid_live = nullptr;
     double* y1 = nullptr;
     double* y1slot = nullptr;
     bool ones_ready = false;

@@ -271,6 +271,7 @@ def test_513_step_matches_oracle(bid, precision):
     assert st["large_levels1"] >= 3 and st["large_levelsk"] >= 2, st
     assert 0 < st["masked_dead1"] < st["masked_clusters1"], st
     assert st["alg_bytes_p1_masked"] < st["alg_bytes_p1"]
+    assert st["mid_clusters1"] > 0 and st["mid_clustersk"] > 0, st
     o = ob.build_system(mesh, p)
     assert (S.perm == o.order).all()
     ist = ob.heart_stimulus(o, stimulus_seeded_disc(mesh, seed=0))
@@ -286,6 +287,45 @@ def test_513_step_matches_oracle(bid, precision):
                             (precision, int(its[0])))
     assert np.abs(H(h) - h1).max() <= 1e-13
     assert abs(H(U) @ o.M.diagonal()) <= 1e-12 * np.abs(H(U)).max() * o.M.sum()
+
+
+@pytest.mark.parametrize("precision,leaf", [("fp32", 32), ("bf16", 32), ("fp64", 16)])
+def test_mid_clusters_equal_chunked_kernels(bid, monkeypatch, precision, leaf):
+    # the large clusters whose block fits one CTA's shared memory (one CTA per
+    # cluster, the default) against the chunked task kernels (BID_MID_BYTES=0)
+    # on the 513^2 slice with eps 1e-3: the same P_1, P_K and P_Lambda^-1
+    # applications up to the accumulation precision's rounding (FP32: 1e-5,
+    # FP64: 1e-12 of the largest entry), and PCG solves to rel-res 1e-13 that
+    # agree potential by potential to 1e-8 within one iteration of each other
+    mesh, p = torso_square_2d(513), params_2d(0.1)
+    S = bid.System(mesh, p)
+    o = ob.build_system(mesh, p)
+    rng = np.random.default_rng(513)
+    b1, bk, r = T(rng.normal(size=S.N)), T(rng.normal(size=S.NH)), T(rng.normal(size=S.N + S.NH))
+    Y = T(ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"]))
+    out = {}
+    for mb in ("0", None):
+        if mb is None:
+            monkeypatch.delenv("BID_MID_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("BID_MID_BYTES", mb)
+        P = bid.Precond(S, p["dt"], eps=1e-3, precision=precision, leaf=leaf)
+        x1, xk, z = torch.zeros_like(b1), torch.zeros_like(bk), torch.zeros_like(r)
+        P.apply_factor(1, b1, x1)
+        P.apply_factor(2, bk, xk)
+        P.apply(r, z)
+        X = torch.zeros_like(r)
+        info = P.solve(Y, X, tol=1e-13, max_iter=800)
+        out[mb] = (H(x1), H(xk), H(z), H(X), info["iters"], P.stats["mid_clusters1"],
+                   P.stats["mid_clustersk"])
+        del P
+    assert out["0"][5] == 0 and out[None][5] > 0 and out[None][6] > 0
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for a, c in zip(out["0"][:3], out[None][:3]):
+        assert np.isfinite(c).all()
+        assert np.abs(a - c).max() <= tol * np.abs(a).max()
+    assert abs(out["0"][4] - out[None][4]) <= 1, (out["0"][4], out[None][4])
+    assert_potentials_close(out[None][3], out["0"][3], o.N, 1e-8, precision)
 
 
 def test_full_size_513_properties(bid):

@@ -160,6 +160,38 @@ def test_masked_solve_equals_full_replay(bid, n, leaf, precision, eps):
         hs.factor_solve_masked(b, eps=eps, leaf=leaf, precision=precision)
 
 
+@pytest.mark.parametrize("precision,leaf", [("fp32", 32), ("fp64", 16), ("bf16", 32)])
+def test_mid_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
+    # large clusters whose block fits one CTA's shared memory (BID_MID_BYTES,
+    # default 96 KiB) are solved as one unit: every dense row, then each
+    # low-rank group's V^T w and U t (backward U^T v, then the columns); the
+    # chunked task replay (BID_MID_BYTES=0) gives the same P_1 and P_K solves
+    # and the same masked solve up to rounding.  A dropped low-rank group or a
+    # wrong row of the block changes x at O(1).
+    m, p = torso_square_2d(257), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    o = ob.build_system(m, p)
+    rng = np.random.default_rng(257)
+    b1, bk = rng.normal(size=o.N), rng.normal(size=o.NH)
+    bm = np.zeros(o.N)
+    bm[:o.NH] = rng.normal(size=o.NH)
+    g = p["chi"] * p["Cm"] / p["dt"]
+    out = {}
+    for mb in ("0", None):
+        if mb is None:
+            monkeypatch.delenv("BID_MID_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("BID_MID_BYTES", mb)
+        x1, st = hs.factor_solve(1, b1, eps=1e-3, leaf=leaf, precision=precision)
+        xk, _ = hs.factor_solve(2, bk, gamma=g, eps=1e-3, leaf=leaf, precision=precision)
+        xm, _ = hs.factor_solve_masked(bm, eps=1e-3, leaf=leaf, precision=precision)
+        out[mb] = (x1, xk, xm, st)
+    assert out["0"][3]["mid_clusters1"] == 0
+    assert out[None][3]["mid_clusters1"] >= 4 and out[None][3]["lowrank_blocks"] > 0
+    for a, c in zip(out["0"][:3], out[None][:3]):
+        assert np.abs(a - c).max() <= 1e-12 * np.abs(a).max()
+
+
 def test_host_factor_3d_exact():
     import __graft_entry__
     __graft_entry__.build()
