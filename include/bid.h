@@ -57,14 +57,17 @@
  *                    with its whole block in shared memory (default 98304; 0:
  *                    every large cluster takes the chunked kernels; read at
  *                    preconditioner build);
+ *    BID_WIDE_BYTES=n factor bytes per CTA of a large cluster split in column
+ *                    slices over a thread-block cluster (default 163840; 0:
+ *                    none; read at preconditioner build);
  *    BID_GPU_FRONT_NF=n  smallest front factorised on the GPU (default 1024);
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the
  *    masked solve's clusters computed in full (all of them with BID_MASK=0,
  *    those of the levels that BID_TREE or BID_UPPER take over) round
- *    differently, and that BID_MID_BYTES changes the summation order of the
- *    large clusters it moves between the two kinds of kernels.
+ *    differently, and that BID_MID_BYTES and BID_WIDE_BYTES change the
+ *    summation order of the large clusters they move between kinds of kernels.
  */
 #ifndef BID_H
 #define BID_H
@@ -201,6 +204,12 @@ typedef struct bid_precond_stats {
                                           BID_MID_BYTES bytes, default 96 KiB; 0 turns
                                           them off); the other large clusters take the
                                           chunked kernels */
+    int64_t wide_clusters1, wide_clustersk;  /* large clusters solved by a thread-block
+                                          cluster of CTAs, each holding a column slice of
+                                          the block in shared memory (at most
+                                          BID_WIDE_BYTES bytes per CTA, default 160 KiB; 0
+                                          turns them off); counted where the device runs
+                                          them (the host replay: where they are built) */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {

@@ -432,6 +432,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (const char* gb = std::getenv("BID_GROUP_BYTES_LEAF")) bo.group_bytes_leaf = std::atoi(gb);
     if (const char* ub = std::getenv("BID_UP_BROWS")) bo.up_brows = std::max(32, std::atoi(ub));
     if (const char* mb = std::getenv("BID_MID_BYTES")) bo.mid_bytes = std::max(0, std::atoi(mb));
+    if (const char* wb = std::getenv("BID_WIDE_BYTES")) bo.wide_bytes = std::max(0, std::atoi(wb));
     bo.gpu_front = o->gpu_build != 0;
     if (const char* gf = std::getenv("BID_GPU_FRONT_NF")) bo.gpu_front_nf = std::max(16, std::atoi(gf));
     HFactorHost h1, hk;
@@ -554,6 +555,14 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     st.large_levelsk = large_levels(hk);
     st.mid_clusters1 = (int64_t)h1.mid.size();
     st.mid_clustersk = (int64_t)hk.mid.size();
+    auto wide_run = [](const HFactorHost& h, const HFactorDev& d) {   // on levels running the wide kernels
+        int64_t c = 0;
+        for (size_t L = 0; L < d.wide_c.size(); ++L)
+            if (d.wide_c[L] > 0) c += h.wide_ptr[L + 1] - h.wide_ptr[L];
+        return c;
+    };
+    st.wide_clusters1 = wide_run(h1, P->F1);
+    st.wide_clustersk = wide_run(hk, P->FK);
     auto flatp_levels = [](const HFactorDev& d) {
         int32_t c = 0;
         if (hsolve_flatp_enabled())

@@ -971,6 +971,140 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         F->ub_ptr.push_back((int32_t)F->ubt.size());
         F->mid_ptr.push_back((int32_t)F->mid.size());
     }
+    // wide clusters (WideCl): on a level whose large clusters are all task
+    // clusters, each split into C column slices of at most o.wide_bytes bytes
+    // (C the level's largest need, at most WIDE_MAX_CTAS); the tasks stay
+    F->wide.clear();
+    F->wslice.clear();
+    F->wpiece.clear();
+    F->wadj.clear();
+    F->wide_ptr.assign(1, 0);
+    F->wide_c.assign(H, 0);
+    {
+        auto fl = [vec](int64_t x) { return x / vec * vec; };
+        auto cl = [vec](int64_t x) { return (x + vec - 1) / vec * vec; };
+        // slices of cluster s over C CTAs; false when one exceeds the budget
+        auto partition = [&](int s, int C, bool commit) {
+            const HSnode& h = F->sn[s];
+            const int ni = h.ni, nd = h.nd, ng = h.lr_end - h.lr_begin;
+            int ksum = 0;
+            for (int g = h.lr_begin; g < h.lr_end; ++g) ksum += F->lr[g].k;
+            int64_t tot = 0;
+            for (int j = 0; j < ni; ++j) tot += (nd - j) + ksum;
+            std::vector<int> jb(C + 1, ni);
+            jb[0] = 0;
+            {
+                int64_t acc = 0;
+                int c = 1;
+                for (int j = 0; j < ni && c < C; j += vec) {
+                    for (int jj = j; jj < std::min(ni, j + vec); ++jj) acc += (nd - jj) + ksum;
+                    if (acc * C >= tot * c) jb[c++] = std::min(ni, j + vec);
+                }
+            }
+            // pieces: dense columns, V rows, then the U of the groups it owns
+            std::vector<int64_t> bytes(C, 0);
+            auto piece_bytes = [&](int64_t a, int64_t b) { return (cl(b) - fl(a)) * esz; };
+            for (int c = 0; c < C; ++c) {
+                if (jb[c + 1] <= jb[c]) continue;
+                bytes[c] += piece_bytes(h.data_off + col_start(nd, jb[c], vec),
+                                        h.data_off + col_start(nd, jb[c + 1], vec) + 2 * vec);
+                for (int g = h.lr_begin; g < h.lr_end; ++g) {
+                    const HLr& G = F->lr[g];
+                    if (G.k > 0) bytes[c] += piece_bytes(G.off_v + (int64_t)jb[c] * G.k, G.off_v + (int64_t)jb[c + 1] * G.k);
+                }
+            }
+            std::vector<int> owner(ng, 0);
+            for (int g = 0; g < ng; ++g) {
+                const HLr& G = F->lr[h.lr_begin + g];
+                int best = 0;
+                for (int c = 1; c < C; ++c)
+                    if (bytes[c] < bytes[best]) best = c;
+                owner[g] = best;
+                if (G.k > 0) bytes[best] += piece_bytes(G.off_u, G.off_u + (int64_t)G.m * G.k);
+            }
+            for (int c = 0; c < C; ++c)
+                if (bytes[c] > o.wide_bytes) return false;
+            if (!commit) return true;
+            WideCl w{};
+            w.blk = blk_beg[s];
+            w.s = s;
+            w.slice0 = (int32_t)F->wslice.size();
+            F->wide.push_back(w);
+            for (int c = 0; c < C; ++c) {
+                WideSlice sl{};
+                sl.j0 = jb[c];
+                sl.j1 = jb[c + 1];
+                sl.q0 = (int32_t)((int64_t)nd * c / C);
+                sl.q1 = (int32_t)((int64_t)nd * (c + 1) / C);
+                sl.piece0 = (int32_t)F->wpiece.size();
+                sl.adj0 = (int32_t)F->wadj.size();
+                int64_t dst = 0;
+                auto add = [&](int64_t a, int64_t b) {   // elements [a, b) -> shared bytes dst
+                    WidePiece pc{};
+                    pc.src = fl(a);
+                    pc.dst = (int32_t)dst;
+                    pc.bytes = (int32_t)((cl(b) - fl(a)) * esz);
+                    F->wpiece.push_back(pc);
+                    dst += pc.bytes;
+                    return pc;
+                };
+                std::vector<WideAdj> adj(ng, WideAdj{});
+                if (sl.j1 > sl.j0) {
+                    const int64_t a = h.data_off + col_start(nd, sl.j0, vec);
+                    const WidePiece pc = add(a, h.data_off + col_start(nd, sl.j1, vec) + 2 * vec);
+                    sl.dbase = pc.dst / esz - col_start(nd, sl.j0, vec) + (a - pc.src);
+                    for (int g = 0; g < ng; ++g) {
+                        const HLr& G = F->lr[h.lr_begin + g];
+                        if (G.k == 0) continue;
+                        const int64_t va = G.off_v + (int64_t)sl.j0 * G.k;
+                        const WidePiece pv = add(va, G.off_v + (int64_t)sl.j1 * G.k);
+                        adj[g].vadj = (int32_t)(pv.dst / esz + (G.off_v - pv.src));
+                    }
+                }
+                for (int g = 0; g < ng; ++g) {
+                    const HLr& G = F->lr[h.lr_begin + g];
+                    adj[g].owner = owner[g];
+                    adj[g].uadj = -1;
+                    if (owner[g] == c && G.k > 0) {
+                        const WidePiece pu = add(G.off_u, G.off_u + (int64_t)G.m * G.k);
+                        adj[g].uadj = (int32_t)(pu.dst / esz + (G.off_u - pu.src));
+                    }
+                }
+                sl.npiece = (int32_t)F->wpiece.size() - sl.piece0;
+                sl.nbytes = (int32_t)dst;
+                F->wadj.insert(F->wadj.end(), adj.begin(), adj.end());
+                F->wslice.push_back(sl);
+            }
+            return true;
+        };
+        for (int L = 0; L < H; ++L) {
+            std::vector<int> lc;
+            bool ok = o.wide_bytes > 0 && !o.upper_levels;
+            for (int s : bylev[L]) {
+                const HSnode& h = F->sn[s];
+                if (!h.large) continue;
+                int ksum = 0;
+                for (int g = h.lr_begin; g < h.lr_end; ++g) ksum += F->lr[g].k;
+                if (is_mid[s] || h.ni < 2 * vec || h.nd > WIDE_ND || h.nb > WIDE_NB || ksum > MID_PAIRS ||
+                    h.lr_end - h.lr_begin > MID_GROUPS || h.inc_off % 2)
+                    ok = false;
+                lc.push_back(s);
+            }
+            int C = 0;
+            for (size_t i = 0; ok && i < lc.size(); ++i) {
+                int c = 2;
+                while (c <= WIDE_MAX_CTAS && !partition(lc[i], c, false)) ++c;
+                if (c > WIDE_MAX_CTAS) ok = false;
+                C = std::max(C, c);
+            }
+            if (ok && !lc.empty()) {
+                for (int s : lc)
+                    if (!partition(s, C, true)) return set_error(BID_EINVAL, "wide cluster partition");
+                F->wide_c[L] = C;
+            }
+            F->wide_ptr.push_back((int32_t)F->wide.size());
+        }
+    }
     F->tbuf = tbuf;
     F->pbuf = pbuf;
     F->ntickets = tickets;

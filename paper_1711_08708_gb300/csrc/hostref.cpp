@@ -25,9 +25,17 @@ int mid_bytes_env() {
     return e ? std::max(0, std::atoi(e)) : MID_BYTES_DEFAULT;
 }
 
+// BID_WIDE_BYTES in the environment: factor bytes per CTA of a wide cluster
+// (0 turns wide clusters off)
+int wide_bytes_env() {
+    const char* e = std::getenv("BID_WIDE_BYTES");
+    return e ? std::max(0, std::atoi(e)) : WIDE_DATA_MAX;
+}
+
 // x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
 // the same order, as the GPU launches (permuted input, per-level flat items
-// with their splits, mid clusters, large-cluster tasks, parent input slots).
+// with their splits, mid and wide clusters, large-cluster tasks, parent input
+// slots).
 // Returns false when a group's cluster data lies outside the group's block.
 // With a dataflow schedule T, the flat groups of its levels run in the order
 // of the dataflow kernels' signals instead of level by level, as early as the
@@ -110,6 +118,32 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
         }
         return npair == m.npair;
     };
+    // Wide clusters: each CTA's shared-memory image, built from its bulk
+    // copies exactly as the kernels lay it out; every entry below is read
+    // through the image with the kernels' index arithmetic (a wrong offset
+    // reads outside its piece or the wrong entry and fails the comparison).
+    auto wide_images = [&](const WideCl& wc, int C, std::vector<std::vector<double>>& sm) {
+        for (int c = 0; c < C; ++c) {
+            const WideSlice& sl = F.wslice[wc.slice0 + c];
+            if (sl.nbytes < 0 || sl.nbytes % 16) return false;
+            sm[c].assign(sl.nbytes / esz, std::nan(""));
+            for (int k = sl.piece0; k < sl.piece0 + sl.npiece; ++k) {
+                const WidePiece& pc = F.wpiece[k];
+                if (pc.src % F.vec || pc.dst % 16 || pc.bytes % 16 || pc.dst + pc.bytes > sl.nbytes ||
+                    pc.src + pc.bytes / esz > (int64_t)F.data.size())
+                    return false;
+                for (int e = 0; e < pc.bytes / esz; ++e) sm[c][pc.dst / esz + e] = D[pc.src + e];
+            }
+        }
+        return true;
+    };
+    auto at = [](const std::vector<double>& v, int64_t i, bool& bad) {
+        if (i < 0 || i >= (int64_t)v.size() || std::isnan(v[i])) {
+            bad = true;
+            return 0.0;
+        }
+        return v[i];
+    };
     // forward of a flat group: per cluster, each dense row over all its
     // columns, and the group's data read inside its bulk-copied block
     auto fwd_group = [&](int g) {
@@ -174,6 +208,66 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 const HSnode& s = F.sn[si];
                 if (s.large && s.height == lev && !(*mask->live)[si]) scaled_copy(s);
             }
+        if (F.wide_c[lev] > 0) {   // wide clusters: C column slices, partials combined by rank
+            const int C = F.wide_c[lev];
+            for (int wi = F.wide_ptr[lev]; wi < F.wide_ptr[lev + 1]; ++wi) {
+                const WideCl& wc = F.wide[wi];
+                if (mask && !(*mask->live)[wc.s]) continue;
+                const HSnode& s = F.sn[wc.s];
+                std::vector<std::vector<double>> sm(C);
+                if (!wide_images(wc, C, sm)) return false;
+                bool bad = false;
+                const int ng = s.lr_end - s.lr_begin;
+                std::vector<std::vector<double>> part(C, std::vector<double>(s.nd, 0.0));
+                std::vector<std::vector<std::vector<double>>> tpart(C, std::vector<std::vector<double>>(ng));
+                for (int c = 0; c < C; ++c) {
+                    const WideSlice& sl = F.wslice[wc.slice0 + c];
+                    for (int q = sl.j0; q < s.nd; ++q) {
+                        const int jend = q < s.ni ? std::min(sl.j1, q + 1) : sl.j1;
+                        double a = 0.0;
+                        for (int j = sl.j0; j < jend; ++j)
+                            a += at(sm[c], sl.dbase + col_start(s.nd, j, F.vec) - j + q, bad) * gather(s, j);
+                        part[c][q] = a;
+                    }
+                    for (int g = 0; g < ng; ++g) {
+                        const HLr& G = F.lr[s.lr_begin + g];
+                        const WideAdj& ad = F.wadj[sl.adj0 + g];
+                        tpart[c][g].assign(G.k, 0.0);
+                        for (int l = 0; l < G.k; ++l)
+                            for (int j = sl.j0; j < sl.j1; ++j)
+                                tpart[c][g][l] += at(sm[c], (int64_t)ad.vadj + (int64_t)j * G.k + l, bad) * gather(s, j);
+                    }
+                }
+                std::vector<int> cov(s.nd, 0);
+                for (int c = 0; c < C; ++c) {
+                    const WideSlice& sl = F.wslice[wc.slice0 + c];
+                    for (int q = sl.q0; q < sl.q1 && q < s.nd; ++q) {
+                        double a = 0.0;
+                        for (int c2 = 0; c2 < C; ++c2) a += part[c2][q];
+                        ++cov[q];
+                        finish(s, drow(s, q), a);
+                    }
+                }
+                for (int q = 0; q < s.nd; ++q)
+                    if (cov[q] != 1) return false;
+                for (int g = 0; g < ng; ++g) {
+                    const HLr& G = F.lr[s.lr_begin + g];
+                    const int o = F.wadj[F.wslice[wc.slice0].adj0 + g].owner;
+                    if (o < 0 || o >= C) return false;
+                    const WideAdj& ad = F.wadj[F.wslice[wc.slice0 + o].adj0 + g];
+                    std::vector<double> tg(G.k, 0.0);
+                    for (int l = 0; l < G.k; ++l)
+                        for (int c = 0; c < C; ++c) tg[l] += tpart[c][g][l];
+                    for (int i = 0; i < G.m; ++i) {
+                        double a = 0.0;
+                        for (int l = 0; l < G.k; ++l) a += at(sm[o], (int64_t)ad.uadj + (int64_t)i * G.k + l, bad) * tg[l];
+                        finish(s, G.row0 + i, a);
+                    }
+                }
+                if (bad) return false;
+            }
+            continue;
+        }
         // mid clusters: the whole block in one CTA's shared memory
         for (int mi = F.mid_ptr[lev]; mi < F.mid_ptr[lev + 1]; ++mi) {
             const MidCl& m = F.mid[mi];
@@ -253,7 +347,51 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             lev = l0;
             continue;
         }
-        for (int g = F.ulr_ptr[lev]; g < F.ulr_ptr[lev + 1]; ++g) {
+        std::vector<std::pair<int32_t, double>> xs;   // outputs of this level, written after
+        if (F.wide_c[lev] > 0) {
+            const int C = F.wide_c[lev];
+            for (int wi = F.wide_ptr[lev]; wi < F.wide_ptr[lev + 1]; ++wi) {
+                const WideCl& wc = F.wide[wi];
+                const HSnode& s = F.sn[wc.s];
+                std::vector<std::vector<double>> sm(C);
+                if (!wide_images(wc, C, sm)) return false;
+                bool bad = false;
+                const int ng = s.lr_end - s.lr_begin;
+                std::vector<std::vector<double>> tg(ng);
+                for (int g = 0; g < ng; ++g) {   // t = U^T v by the owner
+                    const HLr& G = F.lr[s.lr_begin + g];
+                    const int o = F.wadj[F.wslice[wc.slice0].adj0 + g].owner;
+                    if (o < 0 || o >= C) return false;
+                    const WideAdj& ad = F.wadj[F.wslice[wc.slice0 + o].adj0 + g];
+                    tg[g].assign(G.k, 0.0);
+                    for (int l = 0; l < G.k; ++l)
+                        for (int i = 0; i < G.m; ++i)
+                            tg[g][l] += at(sm[o], (int64_t)ad.uadj + (int64_t)i * G.k + l, bad) *
+                                        -x[F.bidx[s.bidx_off + G.row0 + i - s.ni]];
+                }
+                std::vector<int> cov(s.ni, 0);
+                for (int c = 0; c < C; ++c) {
+                    const WideSlice& sl = F.wslice[wc.slice0 + c];
+                    for (int j = sl.j0; j < sl.j1; ++j) {
+                        double a = 0.0;
+                        for (int q = j; q < s.nd; ++q)
+                            a += at(sm[c], sl.dbase + col_start(s.nd, j, F.vec) - j + q, bad) * vrow(s, q);
+                        for (int g = 0; g < ng; ++g) {
+                            const HLr& G = F.lr[s.lr_begin + g];
+                            const WideAdj& ad = F.wadj[sl.adj0 + g];
+                            for (int l = 0; l < G.k; ++l)
+                                a += at(sm[c], (int64_t)ad.vadj + (int64_t)j * G.k + l, bad) * tg[g][l];
+                        }
+                        ++cov[j];
+                        xs.push_back({F.pidx[s.first + j], a});
+                    }
+                }
+                for (int j = 0; j < s.ni; ++j)
+                    if (cov[j] != 1) return false;
+                if (bad) return false;
+            }
+        }
+        for (int g = F.ulr_ptr[lev]; F.wide_c[lev] == 0 && g < F.ulr_ptr[lev + 1]; ++g) {
             const HLr& G = F.lr[g];
             const HSnode& s = F.sn[G.s];
             for (int l = 0; l < G.k; ++l) {
@@ -263,8 +401,7 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 t[G.t_off + l] = a;
             }
         }
-        std::vector<std::pair<int32_t, double>> xs;   // outputs of this level, written after
-        for (int ti = F.ub_ptr[lev]; ti < F.ub_ptr[lev + 1]; ++ti) {
+        for (int ti = F.ub_ptr[lev]; F.wide_c[lev] == 0 && ti < F.ub_ptr[lev + 1]; ++ti) {
             const HTask& k = F.ubt[ti];
             const HSnode& s = F.sn[k.s];
             for (int j = k.a0; j < k.a1; ++j) {
@@ -379,6 +516,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
     if (!(eps >= 0.0) || block < 8 || block > 256) return set_error(BID_EINVAL, "bad eps/block");
     HBuildOpts o;
     o.mid_bytes = mid_bytes_env();
+    o.wide_bytes = wide_bytes_env();
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
@@ -418,6 +556,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
         stats->dense_blocks = F.nlarge;
         stats->lowrank_blocks = F.nlr;
         stats->mid_clusters1 = (int64_t)F.mid.size();
+        stats->wide_clusters1 = (int64_t)F.wide.size();
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
     }
@@ -434,6 +573,7 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
         if (b[i] != 0.0) return set_error(BID_EINVAL, "b must be zero outside the heart nodes");
     HBuildOpts o;
     o.mid_bytes = mid_bytes_env();
+    o.wide_bytes = wide_bytes_env();
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
@@ -486,6 +626,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
     }
     HBuildOpts o;
     o.mid_bytes = mid_bytes_env();
+    o.wide_bytes = wide_bytes_env();
     o.eps = eps;
     o.leaf = leaf_default;
     o.block = block;
@@ -542,6 +683,8 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         stats->lowrank_entries = F.lowrank_entries;
         stats->dense_blocks = F.nlarge;
         stats->lowrank_blocks = F.nlr;
+        stats->mid_clusters1 = (int64_t)F.mid.size();
+        stats->wide_clusters1 = (int64_t)F.wide.size();
     }
     return BID_OK;
 }

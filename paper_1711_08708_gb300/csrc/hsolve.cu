@@ -29,6 +29,7 @@
 // Factors are stored in FP64, FP32 or BF16; FP32/BF16 accumulate in FP32 (the
 // precision form), FP64 in FP64.  All reductions have a fixed order, so the
 // result is bitwise reproducible.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -108,6 +109,10 @@ struct HView {
     const HTask* __restrict__ uft;
     const HTask* __restrict__ ubt;
     const MidCl* __restrict__ mid;
+    const WideCl* __restrict__ wide;
+    const WideSlice* __restrict__ wslice;
+    const WidePiece* __restrict__ wpiece;
+    const WideAdj* __restrict__ wadj;
 };
 
 // sum of the children's contributions to frontal row f (two slots per row,
@@ -1553,6 +1558,349 @@ __global__ void __launch_bounds__(MT) k_mid_bwd(HView v, const T* __restrict__ d
     }
 }
 
+// ------------------------------------------------------------ wide clusters
+// One thread-block cluster of C CTAs (MID_THREADS threads each) per wide
+// cluster (WideCl) and pass; CTA `rank` holds the slice wslice[slice0 + rank]
+// in its shared memory (bulk copies started before the dependency wait).
+// The partial sums that cross CTAs are read through distributed shared memory
+// in rank order, between cluster barriers, so the results are reproducible.
+namespace cg = cooperative_groups;
+
+// Before the dependency wait: barrier armed and the slice's pieces copied
+// (when `copy`), descriptors, the slice's group table and the product-entry
+// table staged.  Ends with a CTA barrier.
+template <typename T>
+__device__ __forceinline__ void wide_start(const HView& v, const T* __restrict__ data, const WideSlice& sl,
+                                           const HSnode& sn, const MidLayout& lay, unsigned char* smem,
+                                           uint64_t* bar, bool copy) {
+    const int ng = sn.lr_end - sn.lr_begin;
+    if (copy && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, (uint32_t)sl.nbytes);
+        for (int k = sl.piece0; k < sl.piece0 + sl.npiece; ++k) {
+            const WidePiece pc = v.wpiece[k];
+            bulk_region(smem + pc.dst, data + pc.src, pc.bytes, bar);
+        }
+    }
+    HLr* gd = reinterpret_cast<HLr*>(smem + lay.gd);
+    WideAdj* ad = reinterpret_cast<WideAdj*>(smem + lay.ad);
+    for (int g = threadIdx.x; g < ng; g += MT) {
+        gd[g] = v.lr[sn.lr_begin + g];
+        ad[g] = v.wadj[sl.adj0 + g];
+    }
+    __syncthreads();
+    MidPair* pt = reinterpret_cast<MidPair*>(smem + lay.pt);
+    int P = 0;
+    for (int g = 0; g < ng; ++g) P += gd[g].k;
+    for (int p = threadIdx.x; p < P; p += MT) {
+        int g = 0, pb = 0;
+        while (g < ng - 1 && pb + gd[g].k <= p) {
+            pb += gd[g].k;
+            ++g;
+        }
+        const int l = p - pb;
+        MidPair r{};
+        r.voff = ad[g].vadj + l;
+        r.uoff = ad[g].uadj + l;
+        r.k = gd[g].k;
+        r.rb = gd[g].row0 - sn.ni;
+        r.m = gd[g].m;
+        r.pad0 = ad[g].owner;
+        pt[p] = r;
+    }
+    __syncthreads();
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(MT) k_wide_fwd(HView v, const T* __restrict__ data, int w0, MidLayout lay,
+                                                 const double* xp, double* ybuf, double* inb,
+                                                 unsigned int* err, MaskArgs mk) {
+    constexpr int VEC = VecOf<T>::N;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tid = threadIdx.x;
+    const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const int wi = w0 + (int)blockIdx.x / C;
+    const WideCl wc = v.wide[wi];
+    const WideSlice sl = v.wslice[wc.slice0 + rank];
+    const HSnode sn = v.sn[wc.s];
+    const int ni = sn.ni, nd = sn.nd, nb = sn.nb, ng = sn.lr_end - sn.lr_begin;
+    const bool dead = mk.live && !mk.live[wi];   // the same for every CTA of the cluster
+    int32_t* us = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);
+    int32_t* dr = reinterpret_cast<int32_t*>(dyn_smem + lay.dr);
+    if (!dead) {
+        for (int r = tid; r < nb; r += MT) us[r] = v.uout[sn.u_off + r];
+        for (int q = tid; q < nd - ni; q += MT) dr[q] = v.drows[sn.drow_off + q] - ni;
+    }
+    wide_start<T>(v, data, sl, sn, lay, dyn_smem, &bar, !dead);
+    pdl_wait();
+    pdl_trigger();
+    if (dead) {   // constant input -c: scaled all-ones results, shared out by rank
+        const double c0 = mask_c0(mk);
+        for (int i = rank * MT + tid; i < ni; i += C * MT)
+            ybuf[sn.first + i] = mask_c(mk, c0, mk.seg ? v.pidx[sn.first + i] : 0) * mk.y1[sn.first + i];
+        for (int r = rank * MT + tid; r < nb; r += C * MT) {
+            const int32_t slot = v.uout[sn.u_off + r];
+            inb[slot] = mask_c(mk, c0, mk.seg ? v.bidx[sn.bidx_off + r] : 0) * mk.y1slot[slot];
+        }
+        return;
+    }
+    const int j0 = sl.j0, j1 = sl.j1, ncol = j1 - j0;
+    A* w = reinterpret_cast<A*>(dyn_smem + lay.w);          // w[j - j0], the slice's columns
+    double* ib = reinterpret_cast<double*>(dyn_smem + lay.ib);
+    for (int j = j0 + tid; j < j1; j += MT) w[j - j0] = (A)(xp[sn.first + j] + (sn.nchild ? slot_sum(sn, j, inb) : 0.0));
+    for (int r = tid; r < nb; r += MT) ib[r] = sn.nchild ? slot_sum(sn, ni + r, inb) : 0.0;
+    __syncthreads();
+    // an expired wait records the error and carries on (results invalid), so
+    // that every CTA of the cluster still reaches the cluster barriers
+    if (!mbar_wait_bounded(&bar) && tid == 0) atomicOr(err, 1u);
+    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    A* red = reinterpret_cast<A*>(dyn_smem + lay.red);
+    A* tp = reinterpret_cast<A*>(dyn_smem + lay.tp);
+    A* tl = reinterpret_cast<A*>(dyn_smem + lay.tl);
+    A* pa = reinterpret_cast<A*>(dyn_smem + lay.pa);   // row partials over this slice (nd)
+    A* tq = reinterpret_cast<A*>(dyn_smem + lay.tq);   // product partials over this slice (P)
+    const MidPair* pt = reinterpret_cast<const MidPair*>(dyn_smem + lay.pt);
+    for (int q = tid; q < (ncol > 0 ? min(j0, nd) : nd); q += MT) pa[q] = 0;
+    // dense rows [j0, nd) over the slice's columns: item = (row group, column chunk)
+    const int r0 = j0 / VEC, NR = ncol > 0 ? (nd + VEC - 1) / VEC - r0 : 0;
+    const int CS = NR > 0 ? mid_chunks(NR, 16) : 1;
+    for (int it = tid; it < NR * CS; it += MT) {
+        const int rg = r0 + it % NR, cs = it / NR;
+        const int q0 = rg * VEC;
+        A acc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = 0;
+        const int jlast = q0 + VEC - 1 < ni ? q0 + VEC : ni;
+        const int chunk = (ncol + CS - 1) / CS;
+        const int ja = j0 + cs * chunk, jb = min(min(jlast, j1), ja + chunk);
+        if (ja < jb) {
+            const T* base = sd + sl.dbase + q0;
+            int off = (int)col_start(nd, ja, VEC) - ja;
+            int j = ja;
+            for (; j + 1 < jb; j += 2) {
+                const int off1 = off + nd - j - 1 + ((j + 1 - nd) & (VEC - 1));
+                A v0[VEC], v1[VEC];
+                lds16(base + off, v0);
+                lds16(base + off1, v1);
+                const A w0 = w[j - j0], w1 = w[j + 1 - j0];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    if (q0 + e >= j) acc[e] += v0[e] * w0;
+                    if (q0 + e >= j + 1) acc[e] += v1[e] * w1;
+                }
+                off = off1 + nd - j - 2 + ((j + 2 - nd) & (VEC - 1));
+            }
+            if (j < jb) {
+                A v0[VEC];
+                lds16(base + off, v0);
+                const A w0 = w[j - j0];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (q0 + e >= j) acc[e] += v0[e] * w0;
+            }
+        }
+        if (CS == 1) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (q0 + e < nd) pa[q0 + e] = acc[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) red[it * VEC + e] = acc[e];
+        }
+    }
+    // product partials t = V^T w over the slice: item = (entry, column chunk)
+    int P = 0;
+    for (int g = 0; g < ng; ++g) P += reinterpret_cast<const HLr*>(dyn_smem + lay.gd)[g].k;
+    const int JC = P > 0 ? mid_chunks(P, 16) : 1, PP = MT / JC;
+    if (P > 0) {
+        const int p = tid % PP, jc = tid / PP;
+        A a = 0;
+        if (p < P && ncol > 0) {
+            const MidPair e = pt[p];
+            const int chunk = (ncol + JC - 1) / JC;
+            const int ja = j0 + jc * chunk, jb = min(j1, ja + chunk);
+            for (int j = ja; j < jb; ++j) a += lds1(sd + e.voff + j * e.k) * w[j - j0];
+        }
+        tp[tid] = a;
+    }
+    __syncthreads();
+    if (CS > 1)
+        for (int rg = tid; rg < NR; rg += MT) {
+            A s[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) s[e] = red[rg * VEC + e];
+            for (int k = 1; k < CS; ++k)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) s[e] += red[(k * NR + rg) * VEC + e];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if ((r0 + rg) * VEC + e < nd) pa[(r0 + rg) * VEC + e] = s[e];
+        }
+    for (int p = tid; p < P; p += MT) {
+        A s = tp[p];
+        for (int k = 1; k < JC; ++k) s += tp[k * PP + p];
+        tq[p] = s;
+    }
+    cluster.sync();
+    // this CTA's rows: the C slices' partials in rank order
+    for (int q = sl.q0 + tid; q < sl.q1; q += MT) {
+        A s = 0;
+        for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(pa, r)[q];
+        if (q < ni) {
+            ybuf[sn.first + q] = (double)s;
+        } else {
+            const int rr = dr[q - ni];
+            inb[us[rr]] = ib[rr] - (double)s;
+        }
+    }
+    // the products of the groups it owns
+    for (int p = tid; p < P; p += MT)
+        if (pt[p].pad0 == rank) {
+            A s = 0;
+            for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(tq, r)[p];
+            tl[p] = s;
+        }
+    __syncthreads();
+    // the low-rank rows of the groups it owns: u = incoming - U_g(i, :) t_g
+    const HLr* gd = reinterpret_cast<const HLr*>(dyn_smem + lay.gd);
+    const WideAdj* ad = reinterpret_cast<const WideAdj*>(dyn_smem + lay.ad);
+    for (int r = tid;; r += MT) {
+        int g = 0, rb = 0, pb = 0;
+        while (g < ng && r >= rb + gd[g].m) {
+            rb += gd[g].m;
+            pb += gd[g].k;
+            ++g;
+        }
+        if (g >= ng) break;
+        if (ad[g].owner != rank) continue;
+        const int i = r - rb, k = gd[g].k;
+        A a = 0;
+        for (int l = 0; l < k; ++l) a += lds1(sd + ad[g].uadj + i * k + l) * tl[pb + l];
+        const int rr = gd[g].row0 - ni + i;
+        inb[us[rr]] = ib[rr] - (double)a;
+    }
+    cluster.sync();   // no CTA leaves while another still reads its partials
+}
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(MT) k_wide_bwd(HView v, const T* __restrict__ data, int w0, MidLayout lay,
+                                                 const double* __restrict__ ybuf, double* out,
+                                                 unsigned int* err) {
+    constexpr int VEC = VecOf<T>::N;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tid = threadIdx.x;
+    const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const WideCl wc = v.wide[w0 + (int)blockIdx.x / C];
+    const WideSlice sl = v.wslice[wc.slice0 + rank];
+    const HSnode sn = v.sn[wc.s];
+    const int ni = sn.ni, nd = sn.nd, nb = sn.nb, ng = sn.lr_end - sn.lr_begin;
+    const int j0 = sl.j0, j1 = sl.j1, ncol = j1 - j0;
+    int32_t* bi = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);
+    int32_t* dr = reinterpret_cast<int32_t*>(dyn_smem + lay.dr);
+    int32_t* po = reinterpret_cast<int32_t*>(dyn_smem + lay.po);
+    for (int r = tid; r < nb; r += MT) bi[r] = v.bidx[sn.bidx_off + r];
+    for (int q = tid; q < nd - ni; q += MT) dr[q] = v.drows[sn.drow_off + q] - ni;
+    for (int j = tid; j < ncol; j += MT) po[j] = v.pidx[sn.first + j0 + j];
+    wide_start<T>(v, data, sl, sn, lay, dyn_smem, &bar, true);
+    pdl_wait();
+    pdl_trigger();
+    A* vd = reinterpret_cast<A*>(dyn_smem + lay.w);    // v at the dense rows (from j0), zero tail
+    A* xb = reinterpret_cast<A*>(dyn_smem + lay.ib);   // -x_B
+    for (int q = j0 + tid; q < ni; q += MT) vd[q] = (A)ybuf[sn.first + q];
+    for (int r = tid; r < nb; r += MT) xb[r] = (A)(-out[bi[r]]);
+    for (int q = nd + tid; q < nd + VEC; q += MT) vd[q] = (A)0;
+    __syncthreads();
+    for (int q = max(ni, j0) + tid; q < nd; q += MT) vd[q] = xb[dr[q - ni]];
+    // an expired wait records the error and carries on (results invalid), so
+    // that every CTA of the cluster still reaches the cluster barriers
+    if (!mbar_wait_bounded(&bar) && tid == 0) atomicOr(err, 1u);
+    const T* sd = reinterpret_cast<const T*>(dyn_smem);
+    A* red = reinterpret_cast<A*>(dyn_smem + lay.red);
+    A* tp = reinterpret_cast<A*>(dyn_smem + lay.tp);
+    A* tl = reinterpret_cast<A*>(dyn_smem + lay.tl);   // t of the owned groups
+    A* tf = reinterpret_cast<A*>(dyn_smem + lay.tq);   // all t, read from their owners
+    const MidPair* pt = reinterpret_cast<const MidPair*>(dyn_smem + lay.pt);
+    int P = 0;
+    for (int g = 0; g < ng; ++g) P += reinterpret_cast<const HLr*>(dyn_smem + lay.gd)[g].k;
+    // t = U^T v of the owned groups: item = (entry, row chunk)
+    const int RC = P > 0 ? mid_chunks(P, 16) : 1, PP = MT / RC;
+    if (P > 0) {
+        const int p = tid % PP, rc = tid / PP;
+        A a = 0;
+        if (p < P && pt[p].pad0 == rank) {
+            const MidPair e = pt[p];
+            const int chunk = (e.m + RC - 1) / RC;
+            const int i0 = rc * chunk, i1 = min(e.m, i0 + chunk);
+            for (int i = i0; i < i1; ++i) a += lds1(sd + e.uoff + i * e.k) * xb[e.rb + i];
+        }
+        tp[tid] = a;
+    }
+    __syncthreads();
+    for (int p = tid; p < P; p += MT)
+        if (pt[p].pad0 == rank) {
+            A s = tp[p];
+            for (int k = 1; k < RC; ++k) s += tp[k * PP + p];
+            tl[p] = s;
+        }
+    cluster.sync();
+    for (int p = tid; p < P; p += MT) tf[p] = cluster.map_shared_rank(tl, pt[p].pad0)[p];
+    cluster.sync();   // every remote read done before any CTA moves on (and leaves)
+    // the slice's columns: item = (column, chunk of its dense row vectors and
+    // of the low-rank entries)
+    const int CC = ncol > 0 ? mid_chunks(ncol, 16) : 1;
+    for (int it = tid; it < ncol * CC; it += MT) {
+        const int j = j0 + it / CC, cc = it % CC;
+        A acc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[e] = 0;
+        const T* cj = sd + sl.dbase + (int)col_start(nd, j, VEC) - j;
+        const int qa = j & ~(VEC - 1);
+        const int nv = (nd - qa + VEC - 1) / VEC;
+        const int per = (nv + CC - 1) / CC;
+        const int v0 = cc * per, v1 = min(nv, v0 + per);
+        int t = v0;
+        for (; t + 1 < v1; t += 2) {
+            const int q0 = qa + t * VEC;
+            A a0[VEC], a1[VEC];
+            lds16(cj + q0, a0);
+            lds16(cj + q0 + VEC, a1);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                if (q0 + e >= j) acc[e] += a0[e] * vd[q0 + e];
+                acc[e] += a1[e] * vd[q0 + VEC + e];
+            }
+        }
+        if (t < v1) {
+            const int q0 = qa + t * VEC;
+            A a0[VEC];
+            lds16(cj + q0, a0);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (q0 + e >= j) acc[e] += a0[e] * vd[q0 + e];
+        }
+        const int pper = (P + CC - 1) / CC;
+        const int p0 = cc * pper, p1 = min(P, p0 + pper);
+        for (int p = p0; p < p1; ++p) acc[0] += lds1(sd + pt[p].voff + j * pt[p].k) * tf[p];
+        A s = acc[0];
+#pragma unroll
+        for (int e = 1; e < VEC; ++e) s += acc[e];
+        if (CC == 1) out[po[j - j0]] = (double)s;
+        else red[it] = s;
+    }
+    if (CC > 1) {
+        __syncthreads();
+        for (int jj = tid; jj < ncol; jj += MT) {
+            A s = red[jj * CC];
+            for (int k = 1; k < CC; ++k) s += red[jj * CC + k];
+            out[po[jj]] = (double)s;
+        }
+    }
+}
+
 // ------------------------------------------------------------ upper levels, persistent
 // The levels [lev0, lev1) hold only large clusters; one cooperative launch
 // per pass runs them all, the CTAs striding over each level's work items,
@@ -1655,6 +2003,10 @@ HView view_of(const HFactorDev& F) {
     v.uft = F.uft;
     v.ubt = F.ubt;
     v.mid = F.mid;
+    v.wide = F.wide;
+    v.wslice = F.wslice;
+    v.wpiece = F.wpiece;
+    v.wadj = F.wadj;
     return v;
 }
 
@@ -1750,6 +2102,28 @@ cudaError_t launch_coop(void (*kern)(KArgs...), unsigned grid, unsigned block, s
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// Launch as thread-block clusters of `cl` CTAs (with programmatic stream
+// serialization unless BID_PDL=0).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cl(void (*kern)(KArgs...), unsigned grid, unsigned cl, unsigned block, size_t smem,
+                      cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 __global__ void k_coop_probe(int* flag) {
     if (flag && threadIdx.x == 0 && blockIdx.x == 0) *flag = 1;
 }
@@ -1799,7 +2173,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                               sh, S.xp));
     }
     const int H = (int)F.uf_ptr.size() - 1;
-    MaskArgs mf{}, mu{}, mm{};
+    MaskArgs mf{}, mu{}, mm{}, mw{};
     if (masked && F.ones_ready && hsolve_mask_enabled()) {
         mf.csum = mu.csum = sh.sum;
         mf.cinv = mu.cinv = sh.inv_n;
@@ -1812,6 +2186,8 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         mu.live = F.uf_live;
         mm = mu;
         mm.live = F.mid_live;
+        mw = mu;
+        mw.live = F.wide_live;
     }
     // upper levels in one persistent launch per pass when possible
     const int lu = (g_upper_ok == 1 && F.sched && S.gbar && F.lev_upper < H) ? F.lev_upper : H;
@@ -1876,6 +2252,15 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             }
             ++launches;
         }
+        const int wcn = F.wide_c[lev];
+        if (wcn > 0) {   // wide level: one cluster of wcn CTAs per large cluster, no tasks
+            const MidLayout& ly = F.wide_lay[lev];
+            const int nw = F.wide_ptr[lev + 1] - F.wide_ptr[lev];
+            BID_CUDA_TRY(launch_cl(k_wide_fwd<T, A>, nw * wcn, wcn, MT, (size_t)ly.total, L.st, v, data,
+                                   F.wide_ptr[lev], ly, S.xp, S.ybuf, inb, S.err, mw));
+            ++launches;
+            continue;
+        }
         const int nm = F.mid_ptr[lev + 1] - F.mid_ptr[lev];
         if (nm > 0) {
             const MidLayout& ly = F.mid_lay[lev];
@@ -1908,14 +2293,22 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             lev = t0;
             continue;
         }
-        const int ng = F.ulr_mid[lev] - F.ulr_ptr[lev];   // the task clusters' low-rank groups
-        const int nv = F.vg_ptr[lev + 1] - F.vg_ptr[lev];
+        const int wcn = F.wide_c[lev];
+        const int ng = wcn > 0 ? 0 : F.ulr_mid[lev] - F.ulr_ptr[lev];   // the task clusters' low-rank groups
+        const int nv = wcn > 0 ? 0 : F.vg_ptr[lev + 1] - F.vg_ptr[lev];
+        if (wcn > 0) {
+            const MidLayout& ly = F.wide_lay[lev];
+            const int nw = F.wide_ptr[lev + 1] - F.wide_ptr[lev];
+            BID_CUDA_TRY(launch_cl(k_wide_bwd<T, A>, nw * wcn, wcn, MT, (size_t)ly.total, L.st, v, data,
+                                   F.wide_ptr[lev], ly, S.ybuf, out, S.err));
+            ++launches;
+        }
         if (ng + nv > 0) {
             BID_CUDA_TRY(launch_k(k_bwd_prep<T, A>, ng + nv, HT, 0, L.st, v, data, F.ulr_ptr[lev], ng,
                                   F.vg_ptr[lev], S.ybuf, out, S.tbuf, S.vbuf));
             ++launches;
         }
-        const int nt = F.ub_ptr[lev + 1] - F.ub_ptr[lev];
+        const int nt = wcn > 0 ? 0 : F.ub_ptr[lev + 1] - F.ub_ptr[lev];
         if (nt > 0) {
             BID_CUDA_TRY(launch_k(k_up_bwd<T, A>, nt, HT, 0, L.st, v, data, F.ub_ptr[lev], S.vbuf, S.tbuf,
                                   out));
@@ -1980,6 +2373,12 @@ int prepare_one() {
                                       MID_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_mid_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       MID_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_fwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      MID_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      MID_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_fwd<T, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_bwd<T, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return BID_OK;
 }
 
@@ -2145,6 +2544,10 @@ int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFa
     std::vector<uint8_t> live, fl(h.fg.size(), 0), ul(h.uft.size(), 0), ml(h.mid.size(), 0);
     cluster_liveness(h, vlive, &live);
     for (size_t k = 0; k < h.mid.size(); ++k) ml[k] = live[h.mid[k].s];
+    std::vector<uint8_t> wl(h.wide.size(), 0);
+    for (size_t k = 0; k < h.wide.size(); ++k) wl[k] = live[h.wide[k].s];
+    wl.push_back(1);
+    BID_TRY(upload_vec(wl, &d->wide_live));
     for (size_t g = 0; g < h.fg.size(); ++g)
         for (int c = h.fg[g].c0; c < h.fg[g].c1; ++c) fl[g] |= live[h.gcl[c].s];
     for (size_t k = 0; k < h.uft.size(); ++k) {
@@ -2262,6 +2665,127 @@ static int upload_mid(const HFactorHost& h, int precision, HFactorDev* d) {
     return upload_vec(h.mid, &d->mid);
 }
 
+// How many clusters of C CTAs of both wide kernels, with `smem` bytes of
+// dynamic shared memory each, the device holds at once (0: none).
+template <typename T, typename A>
+static int wide_cluster_fits(int C, size_t smem) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(MT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nf = 0, nb = 0;
+    const cudaError_t ef = cudaOccupancyMaxActiveClusters(&nf, k_wide_fwd<T, A>, &cfg);
+    const cudaError_t eb = cudaOccupancyMaxActiveClusters(&nb, k_wide_bwd<T, A>, &cfg);
+    if (ef != cudaSuccess || eb != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::min(nf, nb);
+}
+
+// Wide clusters: descriptors, slices, pieces and group tables; per level the
+// shared-memory layout (the largest slice's pieces, then the staging), and
+// whether the level runs the wide kernels (wide_c > 0) or its tasks: the
+// tasks when the layout exceeds the shared memory or the device cannot hold
+// all the level's clusters at once (a second wave of slices, each copying
+// its whole slice before computing, was measured slower than the tasks).
+static int upload_wide(const HFactorHost& h, int precision, HFactorDev* d) {
+    const int H = (int)h.wide_ptr.size() - 1;
+    if (H < 0 || (int)h.wide_c.size() != H || (int)h.uf_ptr.size() != H + 1)
+        return set_error(BID_EINVAL, "wide-cluster lists out of range");
+    BID_TRY(hsolve_prepare());
+    const int esz = precision == BID_FP64 ? 8 : precision == BID_FP32 ? 4 : 2;
+    const int esz_a = precision == BID_FP64 ? 8 : 4;
+    const int vec = 16 / esz;
+    d->wide_ptr = h.wide_ptr;
+    d->wide_c.assign(H, 0);
+    d->wide_lay.assign(H, MidLayout{});
+    for (int L = 0; L < H; ++L) {
+        const int C = h.wide_c[L];
+        if (C <= 0 || h.wide_ptr[L + 1] == h.wide_ptr[L]) continue;
+        if (C > WIDE_MAX_CTAS) return set_error(BID_EINVAL, "wide cluster of %d CTAs", C);
+        int64_t nbytes = 0;
+        int ncol = 0, nd = 0, nb = 0, ndb = 0, np = 0, ng = 0;
+        for (int wi = h.wide_ptr[L]; wi < h.wide_ptr[L + 1]; ++wi) {
+            const WideCl& w = h.wide[wi];
+            const HSnode& s = h.sn[w.s];
+            const int g = s.lr_end - s.lr_begin;
+            int P = 0;
+            for (int k = s.lr_begin; k < s.lr_end; ++k) P += h.lr[k].k;
+            if (!s.large || s.height != L || w.slice0 < 0 || w.slice0 + C > (int)h.wslice.size() || s.nd > WIDE_ND ||
+                s.nb > WIDE_NB || P > MID_PAIRS || g > MID_GROUPS || s.inc_off % 2)
+                return set_error(BID_EINVAL, "wide cluster out of range");
+            for (int c = 0; c < C; ++c) {
+                const WideSlice& sl = h.wslice[w.slice0 + c];
+                if (sl.j0 < 0 || sl.j0 > sl.j1 || sl.j1 > s.ni || (sl.j1 > sl.j0 && sl.j0 % vec) || sl.q0 < 0 ||
+                    sl.q0 > sl.q1 || sl.q1 > s.nd || sl.nbytes < 0 || sl.nbytes % 16 || sl.piece0 < 0 ||
+                    sl.piece0 + sl.npiece > (int)h.wpiece.size() || sl.adj0 < 0 || sl.adj0 + g > (int)h.wadj.size())
+                    return set_error(BID_EINVAL, "wide slice out of range");
+                for (int k = sl.piece0; k < sl.piece0 + sl.npiece; ++k) {
+                    const WidePiece& pc = h.wpiece[k];
+                    // bulk copy: 16-byte aligned source and destination, whole 16-byte chunks
+                    if ((pc.src * esz) % 16 || pc.dst % 16 || pc.bytes <= 0 || pc.bytes % 16 ||
+                        pc.dst + pc.bytes > sl.nbytes || pc.src * esz + pc.bytes > (int64_t)h.data.size() * esz)
+                        return set_error(BID_EINVAL, "wide piece out of range");
+                }
+                for (int k = 0; k < g; ++k)
+                    if (h.wadj[sl.adj0 + k].owner < 0 || h.wadj[sl.adj0 + k].owner >= C)
+                        return set_error(BID_EINVAL, "wide group owner out of range");
+                nbytes = std::max<int64_t>(nbytes, sl.nbytes);
+                ncol = std::max(ncol, sl.j1 - sl.j0);
+            }
+            nd = std::max(nd, s.nd);
+            nb = std::max(nb, s.nb);
+            ndb = std::max(ndb, s.nd - s.ni);
+            np = std::max(np, P);
+            ng = std::max(ng, g);
+        }
+        auto r16 = [](int64_t x) { return (x + 15) / 16 * 16; };
+        MidLayout y{};
+        int64_t o = (nbytes + 127) / 128 * 128;
+        auto take = [&](int32_t* f, int64_t b) {
+            *f = (int32_t)o;
+            o += r16(b);
+        };
+        take(&y.w, (int64_t)esz_a * (nd + vec));
+        take(&y.ib, 8LL * std::max(nb, 1));
+        take(&y.red, (int64_t)esz_a * MID_THREADS * vec);
+        take(&y.tl, (int64_t)esz_a * std::max(np, 1));
+        take(&y.tp, (int64_t)esz_a * MID_THREADS);
+        take(&y.gd, (int64_t)sizeof(HLr) * std::max(ng, 1));
+        take(&y.ad, (int64_t)sizeof(WideAdj) * std::max(ng, 1));
+        take(&y.pt, (int64_t)sizeof(MidPair) * std::max(np, 1));
+        take(&y.bi, 4LL * std::max(nb, 1));
+        take(&y.dr, 4LL * std::max(ndb, 1));
+        take(&y.po, 4LL * std::max(ncol, 1));
+        take(&y.pa, (int64_t)esz_a * (nd + vec));
+        take(&y.tq, (int64_t)esz_a * std::max(np, 1));
+        if (o > MID_SMEM_MAX) continue;   // the tasks solve this level
+        y.total = (int32_t)o;
+        int held = 0;
+        switch (precision) {
+            case BID_FP64: held = wide_cluster_fits<double, double>(C, (size_t)o); break;
+            case BID_FP32: held = wide_cluster_fits<float, float>(C, (size_t)o); break;
+            default: held = wide_cluster_fits<__nv_bfloat16, float>(C, (size_t)o); break;
+        }
+        if (held < 1 || h.wide_ptr[L + 1] - h.wide_ptr[L] > held) continue;
+        d->wide_lay[L] = y;
+        d->wide_c[L] = C;
+    }
+    BID_TRY(upload_vec(h.wide, &d->wide));
+    BID_TRY(upload_vec(h.wslice, &d->wslice));
+    BID_TRY(upload_vec(h.wpiece, &d->wpiece));
+    BID_TRY(upload_vec(h.wadj, &d->wadj));
+    return BID_OK;
+}
+
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     const int esz_acc = precision == BID_FP64 ? 8 : 4;
     for (size_t L = 0; L < h.u_ni_max.size(); ++L)
@@ -2302,6 +2826,7 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.uft, &d->uft));
     BID_TRY(upload_vec(h.ubt, &d->ubt));
     BID_TRY(upload_mid(h, precision, d));
+    BID_TRY(upload_wide(h, precision, d));
     d->fg_ptr = h.fg_ptr;
     d->fg_bytes = h.fg_bytes;
     d->fg_nc = h.fg_nc;
@@ -2371,7 +2896,7 @@ void free_hfactor(HFactorDev* d) {
     void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout,  d->vgl, d->sn,
                     d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
                     d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot,
-                    d->mid, d->mid_live};
+                    d->mid, d->mid_live, d->wide, d->wslice, d->wpiece, d->wadj, d->wide_live};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

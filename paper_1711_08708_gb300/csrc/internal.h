@@ -196,11 +196,49 @@ struct MidCl {
 // vector indices).
 struct MidLayout {
     int32_t w, ib, red, tl, tp, gd, pt, bi, dr, po, total;
+    int32_t pa, tq, ad, pad;   // wide clusters: row partials, product partials, WideAdj table
 };
 struct MidPair {    // entry l of the low-rank group holding product entry p
     int32_t voff, uoff, k, rb;   // V(0, l), U(0, l) inside the block; rank; first row - ni
     int32_t m, pad0, pad1, pad2;
 };
+// A large cluster too big for one CTA but within WIDE_MAX_CTAS CTAs' shared
+// memory ("wide"): one thread-block cluster of C CTAs per tree cluster and
+// pass (k_wide_fwd / k_wide_bwd).  CTA c holds a column slice [j0, j1) of
+// the dense block and the same rows of every low-rank V, plus the whole U of
+// the groups it owns, each piece bulk-copied into its shared memory.  Forward:
+// every CTA forms the partial sums of the dense rows and of t = V^T w over its
+// columns; after a cluster barrier, CTA c sums the C partials of its rows
+// [q0, q1) and of its groups' t (distributed shared memory, rank order) and
+// writes y, the update slots and its groups' low-rank rows.  Backward: each
+// CTA computes its groups' t = U^T v; after a cluster barrier every CTA reads
+// all t from their owners and computes its columns.  A wide cluster keeps its
+// chunked tasks as well: a level runs the wide kernels when all its large
+// clusters are wide and the device can co-schedule the level's cluster size.
+struct WideCl {
+    int64_t blk;        // block start (elements)
+    int32_t s;          // the tree cluster
+    int32_t slice0;     // its slices: wslice[slice0 .. slice0 + C of the level)
+};
+struct WideSlice {      // one CTA of a wide cluster
+    int32_t j0, j1;     // dense columns (j0 a multiple of vec)
+    int32_t q0, q1;     // dense rows it finishes (forward)
+    int32_t piece0, npiece;   // its bulk copies: wpiece[piece0 ..)
+    int32_t nbytes;     // shared-memory bytes of its pieces
+    int32_t adj0;       // per low-rank group of the cluster: wadj[adj0 + g]
+    int64_t dbase;      // shared-memory element of dense entry (q, j) = dbase + col_start(j) - j + q
+};
+struct WidePiece {      // a bulk copy of elements [src, src + bytes / esz) to shared byte dst
+    int64_t src;
+    int32_t dst, bytes;
+};
+struct WideAdj {        // shared-memory element of V(j, l) = vadj + j k + l; of U(i, l) = uadj + i k + l
+    int32_t vadj, uadj; // uadj < 0: the group's U is held by CTA `owner`
+    int32_t owner, pad;
+};
+constexpr int WIDE_MAX_CTAS = 16;
+constexpr int WIDE_ND = 4096, WIDE_NB = 4096;   // largest dense rows / boundary rows
+constexpr int WIDE_DATA_MAX = 160 * 1024;   // factor bytes of one CTA of a wide cluster
 constexpr int MID_BYTES_DEFAULT = 96 * 1024;   // largest block of a mid cluster (bytes)
 constexpr int MID_THREADS = 512;
 constexpr int MID_NI = 256, MID_NB = 1024, MID_ND = 512, MID_PAIRS = 256, MID_GROUPS = 32;
@@ -231,6 +269,12 @@ struct HFactorHost {
     std::vector<int32_t> ulr_mid;              // level -> first low-rank group of its mid clusters
     std::vector<MidCl> mid;                    // mid clusters, level by level
     std::vector<int32_t> mid_ptr;              // level -> mid cluster range
+    std::vector<WideCl> wide;                  // wide clusters, level by level
+    std::vector<int32_t> wide_ptr;             // level -> wide cluster range
+    std::vector<int32_t> wide_c;               // level -> CTAs per wide cluster (0: none)
+    std::vector<WideSlice> wslice;
+    std::vector<WidePiece> wpiece;
+    std::vector<WideAdj> wadj;
     int64_t ubuf = 0, tbuf = 0, pbuf = 0, nslots = 0, vbuf = 0;
     int32_t ntickets = 0;
     int32_t vec = 2;
@@ -263,6 +307,7 @@ struct HBuildOpts {
     int group_bytes_leaf = 0;                // the same for the leaf level (0: group_bytes)
     int up_brows = 512;                      // target rows per warp of a large-cluster backward task
     int mid_bytes = MID_BYTES_DEFAULT;       // largest block of a mid cluster (MidCl); 0: none
+    int wide_bytes = WIDE_DATA_MAX;          // factor bytes per CTA of a wide cluster (WideCl); 0: none
     // merge pass over the cluster tree (merge_upper_levels): subtrees of at
     // least merge_min nodes have their levels merged in pairs; 0: off
     int64_t merge_min = 0;
@@ -317,6 +362,12 @@ struct HFactorDev {
     MidCl* mid = nullptr;
     std::vector<int32_t> mid_ptr, ulr_mid;
     std::vector<MidLayout> mid_lay;     // per level (mid clusters' shared memory)
+    WideCl* wide = nullptr;
+    WideSlice* wslice = nullptr;
+    WidePiece* wpiece = nullptr;
+    WideAdj* wadj = nullptr;
+    std::vector<int32_t> wide_ptr, wide_c;   // wide_c[L] > 0: level L runs the wide kernels
+    std::vector<MidLayout> wide_lay;    // per level: staging after the largest slice's pieces
     void* data = nullptr;               // double / float / __nv_bfloat16
     int64_t data_elems = 0;
     double* inb = nullptr;              // update slots (nslots, zero where no child writes)
@@ -343,6 +394,7 @@ struct HFactorDev {
     uint8_t* fg_live = nullptr;
     uint8_t* uf_live = nullptr;
     uint8_t* mid_live = nullptr;
+    uint8_t* wide_live = nullptr;
     double* y1 = nullptr;
     double* y1slot = nullptr;
     bool ones_ready = false;

@@ -328,6 +328,44 @@ def test_mid_clusters_equal_chunked_kernels(bid, monkeypatch, precision, leaf):
     assert_potentials_close(out[None][3], out["0"][3], o.N, 1e-8, precision)
 
 
+@pytest.mark.parametrize("precision,leaf", [("fp32", 32), ("bf16", 32), ("fp64", 16)])
+def test_wide_clusters_equal_chunked_kernels(bid, monkeypatch, precision, leaf):
+    # the large clusters split in column slices over a thread-block cluster
+    # (partial sums combined through distributed shared memory; the default)
+    # against the chunked task kernels (BID_WIDE_BYTES=0) on the 513^2 slice
+    # with eps 1e-3: the same P_1, P_K and P_Lambda^-1 applications up to the
+    # accumulation precision's rounding, the same masked solve, and PCG solves
+    # that agree potential by potential to 1e-8 within one iteration
+    mesh, p = torso_square_2d(513), params_2d(0.1)
+    S = bid.System(mesh, p)
+    o = ob.build_system(mesh, p)
+    rng = np.random.default_rng(514)
+    b1, bk, r = T(rng.normal(size=S.N)), T(rng.normal(size=S.NH)), T(rng.normal(size=S.N + S.NH))
+    Y = T(ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"]))
+    out = {}
+    for wb in ("0", None):
+        if wb is None:
+            monkeypatch.delenv("BID_WIDE_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("BID_WIDE_BYTES", wb)
+        P = bid.Precond(S, p["dt"], eps=1e-3, precision=precision, leaf=leaf)
+        x1, xk, z = torch.zeros_like(b1), torch.zeros_like(bk), torch.zeros_like(r)
+        P.apply_factor(1, b1, x1)
+        P.apply_factor(2, bk, xk)
+        P.apply(r, z)
+        X = torch.zeros_like(r)
+        info = P.solve(Y, X, tol=1e-13, max_iter=800)
+        out[wb] = (H(x1), H(xk), H(z), H(X), info["iters"], P.stats["wide_clusters1"])
+        del P
+    assert out["0"][5] == 0 and out[None][5] > 0, (out["0"][5], out[None][5])
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for a, c in zip(out["0"][:3], out[None][:3]):
+        assert np.isfinite(c).all()
+        assert np.abs(a - c).max() <= tol * np.abs(a).max()
+    assert abs(out["0"][4] - out[None][4]) <= 1, (out["0"][4], out[None][4])
+    assert_potentials_close(out[None][3], out["0"][3], o.N, 1e-8, precision)
+
+
 def test_full_size_513_properties(bid):
     _full_size_properties(bid, 513, 3, 1e-3, "fp64")
 

@@ -192,6 +192,38 @@ def test_mid_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
         assert np.abs(a - c).max() <= 1e-12 * np.abs(a).max()
 
 
+@pytest.mark.parametrize("precision,leaf", [("fp32", 32), ("fp64", 16), ("bf16", 32)])
+def test_wide_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
+    # large clusters split in column slices over a thread-block cluster: the
+    # replay builds each CTA's shared-memory image from its bulk copies and
+    # reads every factor entry through the kernels' index arithmetic (dense
+    # columns, V rows of its slice, U of its groups), combining the partial
+    # sums by rank; it equals the chunked task replay (BID_WIDE_BYTES=0) up to
+    # rounding in the P_1, P_K and masked solves.  An entry read outside its
+    # piece, a row or column covered twice or not at all fails the replay.
+    m, p = torso_square_2d(513), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    o = ob.build_system(m, p)
+    rng = np.random.default_rng(513)
+    b1, bk = rng.normal(size=o.N), rng.normal(size=o.NH)
+    bm = np.zeros(o.N)
+    bm[:o.NH] = rng.normal(size=o.NH)
+    g = p["chi"] * p["Cm"] / p["dt"]
+    out = {}
+    for wb in ("0", None):
+        if wb is None:
+            monkeypatch.delenv("BID_WIDE_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("BID_WIDE_BYTES", wb)
+        x1, st = hs.factor_solve(1, b1, eps=1e-3, leaf=leaf, precision=precision)
+        xk, stk = hs.factor_solve(2, bk, gamma=g, eps=1e-3, leaf=leaf, precision=precision)
+        xm, _ = hs.factor_solve_masked(bm, eps=1e-3, leaf=leaf, precision=precision)
+        out[wb] = (x1, xk, xm, st["wide_clusters1"] + stk["wide_clusters1"])
+    assert out["0"][3] == 0 and out[None][3] >= 1
+    for a, c in zip(out["0"][:3], out[None][:3]):
+        assert np.abs(a - c).max() <= 1e-12 * np.abs(a).max()
+
+
 def test_host_factor_3d_exact():
     import __graft_entry__
     __graft_entry__.build()
