@@ -339,7 +339,8 @@ __device__ __forceinline__ double incoming_s(const double* ss, const GCl& c, int
 // the children's update slots right after it, descriptors scl, inputs w).
 template <typename T, typename A>
 __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, const GCl* scl, int nc,
-                                              const unsigned char* smem, A* w, double* ybuf, double* inb) {
+                                              const unsigned char* smem, A* w, double* ybuf, double* inb,
+                                              const int32_t* uo = nullptr) {
     constexpr int VEC = VecOf<T>::N;
     const double* ss = reinterpret_cast<const double*>(smem + G.nbytes);
     if (G.sbytes > 0) {   // add the children's updates (zero where none)
@@ -385,7 +386,8 @@ __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, c
                 ybuf[G.pstart + c.woff_f + R] = (double)acc[e];
             } else {
                 const double u0 = c.nchild ? incoming_s(ss, c, R) : 0.0;
-                inb[v.uout[G.bstart + c.boff + R - c.ni]] = u0 - (double)acc[e];
+                const int k = c.boff + R - c.ni;
+                inb[uo ? uo[k] : v.uout[G.bstart + k]] = u0 - (double)acc[e];
             }
         }
     }
@@ -396,10 +398,12 @@ __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, c
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* xp, double* ybuf, double* inb,
-                                                 unsigned int* err, int sc_off, int w_off, MaskArgs mk) {
+                                                 unsigned int* err, int sc_off, int w_off, int ix_off,
+                                                 MaskArgs mk) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
     A* w = reinterpret_cast<A*>(dyn_smem + w_off);
+    int32_t* uo = reinterpret_cast<int32_t*>(dyn_smem + ix_off);   // update slots of the boundary rows
     __shared__ __align__(8) uint64_t bar;
     const FGroup G = v.fg[g0 + blockIdx.x];
     if (mk.live && !mk.live[g0 + blockIdx.x]) {   // constant input -c: scaled all-ones results
@@ -420,6 +424,7 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
         group_load(dyn_smem, data + G.dstart, G.nbytes, G.sbytes, &bar);
     }
     for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+    for (int k = threadIdx.x; k < G.nbt; k += FT) uo[k] = v.uout[G.bstart + k];   // immutable
     pdl_wait();
     pdl_trigger();
     if (threadIdx.x == 0) group_load_slots(dyn_smem, G.nbytes, inb + G.sstart, G.sbytes, &bar);
@@ -430,14 +435,15 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
         if (threadIdx.x == 0) atomicOr(err, 1u);
         return;
     }
-    flat_fwd_body<T, A>(v, G, scl, nc, dyn_smem, w, ybuf, inb);
+    flat_fwd_body<T, A>(v, G, scl, nc, dyn_smem, w, ybuf, inb, uo);
 }
 
 // Backward of one flat group from shared memory (factor block at smem,
 // descriptors scl, staged inputs vs).
 template <typename T, typename A>
 __device__ __forceinline__ void flat_bwd_body(const HView& v, const FGroup& G, const GCl* scl, int nc,
-                                              const unsigned char* smem, const A* vs, double* out) {
+                                              const unsigned char* smem, const A* vs, double* out,
+                                              const int32_t* po = nullptr) {
     constexpr int VEC = VecOf<T>::N;
     const T* sd = reinterpret_cast<const T*>(smem);
     for (int u = threadIdx.x; u < G.ub; u += FT) {
@@ -459,7 +465,7 @@ __device__ __forceinline__ void flat_bwd_body(const HView& v, const FGroup& G, c
 #pragma unroll
             for (int e = 0; e < VEC; ++e) acc += val[e] * vv[q + e];
         }
-        out[v.pidx[G.pstart + u]] = (double)acc;   // u = pivot offset inside the group
+        out[po ? po[u] : v.pidx[G.pstart + u]] = (double)acc;   // u = pivot offset inside the group
     }
 }
 
@@ -469,7 +475,7 @@ __device__ __forceinline__ void flat_bwd_body(const HView& v, const FGroup& G, c
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* __restrict__ ybuf, double* out,
-                                                 unsigned int* err, int sc_off, int w_off) {
+                                                 unsigned int* err, int sc_off, int w_off, int ix_off) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
     A* vs = reinterpret_cast<A*>(dyn_smem + w_off);
@@ -481,6 +487,11 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
         group_load(dyn_smem, data + G.dstart, G.nbytes, 0, &bar);
     }
     for (int k = threadIdx.x; k < nc; k += FT) scl[k] = v.gcl[G.c0 + k];
+    // immutable indices: the boundary rows' vector indices, then the pivots'
+    int32_t* bo = reinterpret_cast<int32_t*>(dyn_smem + ix_off);
+    int32_t* po = bo + G.nbt;
+    for (int k = threadIdx.x; k < G.nbt; k += FT) bo[k] = v.bidx[G.bstart + k];
+    for (int k = threadIdx.x; k < G.wf; k += FT) po[k] = v.pidx[G.pstart + k];
     pdl_wait();
     pdl_trigger();
     __syncthreads();
@@ -489,7 +500,7 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
         const int q = f - c.woff_b;
         double x = 0.0;
         if (q < c.ni) x = ybuf[G.pstart + c.woff_f + q];
-        else if (q < c.nd) x = -out[v.bidx[G.bstart + c.boff + q - c.ni]];
+        else if (q < c.nd) x = -out[bo[c.boff + q - c.ni]];
         vs[f] = (A)x;
     }
     __syncthreads();
@@ -497,7 +508,7 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
         if (threadIdx.x == 0) atomicOr(err, 1u);
         return;
     }
-    flat_bwd_body<T, A>(v, G, scl, nc, dyn_smem, vs, out);
+    flat_bwd_body<T, A>(v, G, scl, nc, dyn_smem, vs, out, po);
 }
 
 // ------------------------------------------------------------ flat levels, persistent
@@ -2247,8 +2258,9 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                 BID_CUDA_TRY(launch_k(k_flat_fwd_pb<T, A>, pg, FT, (size_t)2 * bs, L.st, v, data, F.fg_ptr[lev], nf,
                                       S.xp, S.ybuf, inb, S.err, bs, sc_off, w_off, mf));
             } else {
-                BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.xp, S.ybuf,
-                                      inb, S.err, sc_off, w_off, mf));
+                const int ix_off = (int)((sm + 15) / 16 * 16);
+                BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, (size_t)ix_off + 4 * (size_t)F.fg_nbt[lev], L.st, v,
+                                      data, F.fg_ptr[lev], S.xp, S.ybuf, inb, S.err, sc_off, w_off, ix_off, mf));
             }
             ++launches;
         }
@@ -2332,8 +2344,10 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                 BID_CUDA_TRY(launch_k(k_flat_bwd_pb<T, A>, pg, FT, (size_t)2 * bs, L.st, v, data, F.fg_ptr[lev], nf,
                                       S.ybuf, out, S.err, bs, sc_off, w_off));
             } else {
-                BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT, sm, L.st, v, data, F.fg_ptr[lev], S.ybuf, out,
-                                      S.err, sc_off, w_off));
+                const int ix_off = (int)((sm + 15) / 16 * 16);
+                BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT,
+                                      (size_t)ix_off + 4 * (size_t)(F.fg_nbt[lev] + F.fg_wf[lev]), L.st, v, data,
+                                      F.fg_ptr[lev], S.ybuf, out, S.err, sc_off, w_off, ix_off));
             }
             ++launches;
         }
@@ -2834,9 +2848,14 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     d->fg_wb = h.fg_wb;
     {
         const size_t esz_a = precision == BID_FP64 ? 8 : 4;
+        d->fg_nbt.assign(h.fg_bytes.size(), 0);
+        for (size_t L = 0; L < h.fg_bytes.size() && L + 1 < h.fg_ptr.size(); ++L)
+            for (int g = h.fg_ptr[L]; g < h.fg_ptr[L + 1]; ++g) d->fg_nbt[L] = std::max(d->fg_nbt[L], h.fg[g].nbt);
         for (size_t L = 0; L < h.fg_bytes.size(); ++L) {
             const size_t base = (size_t)(h.fg_bytes[L] + 15) / 16 * 16 + (size_t)h.fg_nc[L] * sizeof(GCl);
-            if (base + esz_a * std::max(h.fg_wf[L], h.fg_wb[L]) > (size_t)FLAT_SMEM_MAX)
+            // staged inputs, then (16-byte aligned) the staged indices
+            const size_t ix = (base + esz_a * std::max(h.fg_wf[L], h.fg_wb[L]) + 15) / 16 * 16;
+            if (ix + 4 * (size_t)(d->fg_nbt[L] + h.fg_wf[L]) > (size_t)FLAT_SMEM_MAX)
                 return set_error(BID_EINVAL, "flat level %zu needs too much shared memory", L);
         }
     }

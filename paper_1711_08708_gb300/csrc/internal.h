@@ -373,6 +373,7 @@ struct HFactorDev {
     double* inb = nullptr;              // update slots (nslots, zero where no child writes)
     std::vector<int32_t> fg_ptr, fg_bytes, fg_nc, fg_wf, fg_wb, ulr_ptr, uf_ptr, ub_ptr, vg_ptr, u_ni_max,
         u_nd_max;
+    std::vector<int32_t> fg_nbt;        // level -> most boundary rows of a flat group
     int32_t* sched = nullptr;           // device copy of uf_ptr | ub_ptr | ulr_ptr | vg_ptr (H + 1 each)
     int32_t lev_upper = 0;              // first upper level (only large clusters from there up)
     size_t upper_smem = 0;              // dynamic shared memory of the upper forward kernel
