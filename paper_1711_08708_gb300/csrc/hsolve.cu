@@ -363,20 +363,34 @@ __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, c
         for (int e = 0; e < VEC; ++e) acc[e] = 0;
         // column j starts at col_start(nd, j) - j relative to row 0; the
         // distance to column j + 1 is nd - j rounded so that the next start
-        // stays congruent to its column index modulo VEC
+        // stays congruent to its column index modulo VEC.  Four columns' loads
+        // are issued ahead of their products, which are added in column order.
         int cs = 0;
-        for (int j = 0; j < jlast; ++j) {
+        int j = 0;
+        for (; j + 3 < jlast; j += 4) {
+            int o[4];
+            o[0] = cs;
+#pragma unroll
+            for (int u = 1; u < 4; ++u) o[u] = o[u - 1] + c.nd - (j + u) + ((j + u - c.nd) & (VEC - 1));
+            A val[4][VEC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) lds16(col + o[u], val[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const A wj = ws[j + u];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (q0 + e >= j + u) acc[e] += val[u][e] * wj;
+            }
+            cs = o[3] + c.nd - (j + 4) + ((j + 4 - c.nd) & (VEC - 1));
+        }
+        for (; j < jlast; ++j) {
             A val[VEC];
             lds16(col + cs, val);
             const A wj = ws[j];
-            if (j > q0) {
 #pragma unroll
-                for (int e = 0; e < VEC; ++e)
-                    if (q0 + e >= j) acc[e] += val[e] * wj;
-            } else {
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) acc[e] += val[e] * wj;
-            }
+            for (int e = 0; e < VEC; ++e)
+                if (q0 + e >= j) acc[e] += val[e] * wj;
             cs += c.nd - j - 1 + ((j + 1 - c.nd) & (VEC - 1));
         }
         const int nrow = min(VEC, c.nd - q0);
@@ -459,8 +473,19 @@ __device__ __forceinline__ void flat_bwd_body(const HView& v, const FGroup& G, c
 #pragma unroll
         for (int e = 0; e < VEC; ++e)
             if (q0 + e >= j && q0 + e < c.nd) acc += val[e] * vv[q0 + e];
-        // whole vectors, then the ragged end (staged inputs are zero there)
-        for (int q = q0 + VEC; q < c.nd; q += VEC) {
+        // whole vectors, then the ragged end (staged inputs are zero there);
+        // four vectors' loads ahead of their products, added in row order
+        int q = q0 + VEC;
+        for (; q + 3 * VEC < c.nd; q += 4 * VEC) {
+            A v4[4][VEC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) lds16(cj + q + u * VEC, v4[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) acc += v4[u][e] * vv[q + u * VEC + e];
+        }
+        for (; q < c.nd; q += VEC) {
             lds16(cj + q, val);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) acc += val[e] * vv[q + e];
@@ -1289,20 +1314,24 @@ __device__ __forceinline__ int mid_chunks(int n, int cmax) {
     return c;
 }
 
-// Work before the dependency wait (immutable data only): thread 0 arms the
-// barrier and starts the block's bulk copy (when `copy`); the CTA stages the
-// group descriptors and the product-entry table.  The first barrier makes the
-// mbarrier's initialisation and the staged descriptors visible to every
-// thread, the second the table.
+// Work before the dependency wait (immutable data only): mid_copy, first,
+// arms the barrier and starts the block's bulk copy (thread 0, when `copy`);
+// mid_start stages the group descriptors and the product-entry table.  Its
+// first barrier makes the mbarrier's initialisation and the staged
+// descriptors visible to every thread, the second the table.
 template <typename T>
-__device__ __forceinline__ void mid_start(const HView& v, const T* __restrict__ data, const MidCl& c,
-                                          const HSnode& sn, const MidLayout& lay, unsigned char* smem,
-                                          uint64_t* bar, bool copy) {
+__device__ __forceinline__ void mid_copy(const T* __restrict__ data, const MidCl& c, unsigned char* smem,
+                                         uint64_t* bar, bool copy) {
     if (copy && threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, (uint32_t)c.nbytes);
         bulk_region(smem, data + c.blk, c.nbytes, bar);
     }
+}
+template <typename T>
+__device__ __forceinline__ void mid_start(const HView& v, const T* __restrict__ data, const MidCl& c,
+                                          const HSnode& sn, const MidLayout& lay, unsigned char* smem,
+                                          uint64_t* bar, bool copy) {
     HLr* gd = reinterpret_cast<HLr*>(smem + lay.gd);
     for (int g = threadIdx.x; g < c.ng; g += MT) gd[g] = v.lr[sn.lr_begin + g];
     __syncthreads();
@@ -1320,9 +1349,10 @@ __global__ void __launch_bounds__(MT) k_mid_fwd(HView v, const T* __restrict__ d
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
     const MidCl c = v.mid[m0 + blockIdx.x];
+    const bool dead = mk.live && !mk.live[m0 + blockIdx.x];
+    mid_copy<T>(data, c, dyn_smem, &bar, !dead);
     const HSnode sn = v.sn[c.s];
     const int ni = sn.ni, nd = sn.nd, nb = sn.nb;
-    const bool dead = mk.live && !mk.live[m0 + blockIdx.x];
     int32_t* us = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);   // update slot of boundary row r
     int32_t* dr = reinterpret_cast<int32_t*>(dyn_smem + lay.dr);   // dense boundary row q - ni, minus ni
     if (!dead) {
@@ -1470,6 +1500,7 @@ __global__ void __launch_bounds__(MT) k_mid_bwd(HView v, const T* __restrict__ d
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
     const MidCl c = v.mid[m0 + blockIdx.x];
+    mid_copy<T>(data, c, dyn_smem, &bar, true);
     const HSnode sn = v.sn[c.s];
     const int ni = sn.ni, nd = sn.nd, nb = sn.nb;
     int32_t* bi = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);   // vector index of boundary row r
@@ -1577,22 +1608,30 @@ __global__ void __launch_bounds__(MT) k_mid_bwd(HView v, const T* __restrict__ d
 // in rank order, between cluster barriers, so the results are reproducible.
 namespace cg = cooperative_groups;
 
-// Before the dependency wait: barrier armed and the slice's pieces copied
-// (when `copy`), descriptors, the slice's group table and the product-entry
-// table staged.  Ends with a CTA barrier.
+// Before the dependency wait, first: thread 0 initialises and arms the
+// barrier with the slice's bytes; after a CTA barrier the slice's pieces are
+// copied, one piece per thread (the copies of a CTA are issued together, not
+// one descriptor load after another).
 template <typename T>
-__device__ __forceinline__ void wide_start(const HView& v, const T* __restrict__ data, const WideSlice& sl,
-                                           const HSnode& sn, const MidLayout& lay, unsigned char* smem,
-                                           uint64_t* bar, bool copy) {
-    const int ng = sn.lr_end - sn.lr_begin;
+__device__ __forceinline__ void wide_copy(const HView& v, const T* __restrict__ data, const WideSlice& sl,
+                                          unsigned char* smem, uint64_t* bar, bool copy) {
     if (copy && threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, (uint32_t)sl.nbytes);
-        for (int k = sl.piece0; k < sl.piece0 + sl.npiece; ++k) {
-            const WidePiece pc = v.wpiece[k];
+    }
+    __syncthreads();
+    if (copy)
+        for (int k = threadIdx.x; k < sl.npiece; k += MT) {
+            const WidePiece pc = v.wpiece[sl.piece0 + k];
             bulk_region(smem + pc.dst, data + pc.src, pc.bytes, bar);
         }
-    }
+}
+
+// Then (still before the wait): the group descriptors, the slice's group
+// table and the product-entry table.  Ends with a CTA barrier.
+__device__ __forceinline__ void wide_tables(const HView& v, const WideSlice& sl, const HSnode& sn,
+                                            const MidLayout& lay, unsigned char* smem) {
+    const int ng = sn.lr_end - sn.lr_begin;
     HLr* gd = reinterpret_cast<HLr*>(smem + lay.gd);
     WideAdj* ad = reinterpret_cast<WideAdj*>(smem + lay.ad);
     for (int g = threadIdx.x; g < ng; g += MT) {
@@ -1633,18 +1672,19 @@ __global__ void __launch_bounds__(MT) k_wide_fwd(HView v, const T* __restrict__ 
     const int tid = threadIdx.x;
     const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     const int wi = w0 + (int)blockIdx.x / C;
+    const bool dead = mk.live && !mk.live[wi];   // the same for every CTA of the cluster
     const WideCl wc = v.wide[wi];
     const WideSlice sl = v.wslice[wc.slice0 + rank];
+    wide_copy<T>(v, data, sl, dyn_smem, &bar, !dead);
     const HSnode sn = v.sn[wc.s];
     const int ni = sn.ni, nd = sn.nd, nb = sn.nb, ng = sn.lr_end - sn.lr_begin;
-    const bool dead = mk.live && !mk.live[wi];   // the same for every CTA of the cluster
     int32_t* us = reinterpret_cast<int32_t*>(dyn_smem + lay.bi);
     int32_t* dr = reinterpret_cast<int32_t*>(dyn_smem + lay.dr);
     if (!dead) {
         for (int r = tid; r < nb; r += MT) us[r] = v.uout[sn.u_off + r];
         for (int q = tid; q < nd - ni; q += MT) dr[q] = v.drows[sn.drow_off + q] - ni;
     }
-    wide_start<T>(v, data, sl, sn, lay, dyn_smem, &bar, !dead);
+    wide_tables(v, sl, sn, lay, dyn_smem);
     pdl_wait();
     pdl_trigger();
     if (dead) {   // constant input -c: scaled all-ones results, shared out by rank
@@ -1661,7 +1701,20 @@ __global__ void __launch_bounds__(MT) k_wide_fwd(HView v, const T* __restrict__ 
     A* w = reinterpret_cast<A*>(dyn_smem + lay.w);          // w[j - j0], the slice's columns
     double* ib = reinterpret_cast<double*>(dyn_smem + lay.ib);
     for (int j = j0 + tid; j < j1; j += MT) w[j - j0] = (A)(xp[sn.first + j] + (sn.nchild ? slot_sum(sn, j, inb) : 0.0));
-    for (int r = tid; r < nb; r += MT) ib[r] = sn.nchild ? slot_sum(sn, ni + r, inb) : 0.0;
+    {   // incoming updates of the boundary rows this CTA finishes: its dense rows, its groups' rows
+        const HLr* gd0 = reinterpret_cast<const HLr*>(dyn_smem + lay.gd);
+        const WideAdj* ad0 = reinterpret_cast<const WideAdj*>(dyn_smem + lay.ad);
+        for (int q = max(sl.q0, ni) + tid; q < sl.q1; q += MT) {
+            const int r = dr[q - ni];
+            ib[r] = sn.nchild ? slot_sum(sn, ni + r, inb) : 0.0;
+        }
+        for (int g = 0; g < ng; ++g)
+            if (ad0[g].owner == rank)
+                for (int i = tid; i < gd0[g].m; i += MT) {
+                    const int r = gd0[g].row0 - ni + i;
+                    ib[r] = sn.nchild ? slot_sum(sn, ni + r, inb) : 0.0;
+                }
+    }
     __syncthreads();
     // an expired wait records the error and carries on (results invalid), so
     // that every CTA of the cluster still reaches the cluster barriers
@@ -1807,6 +1860,7 @@ __global__ void __launch_bounds__(MT) k_wide_bwd(HView v, const T* __restrict__ 
     const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     const WideCl wc = v.wide[w0 + (int)blockIdx.x / C];
     const WideSlice sl = v.wslice[wc.slice0 + rank];
+    wide_copy<T>(v, data, sl, dyn_smem, &bar, true);
     const HSnode sn = v.sn[wc.s];
     const int ni = sn.ni, nd = sn.nd, nb = sn.nb, ng = sn.lr_end - sn.lr_begin;
     const int j0 = sl.j0, j1 = sl.j1, ncol = j1 - j0;
@@ -1816,16 +1870,25 @@ __global__ void __launch_bounds__(MT) k_wide_bwd(HView v, const T* __restrict__ 
     for (int r = tid; r < nb; r += MT) bi[r] = v.bidx[sn.bidx_off + r];
     for (int q = tid; q < nd - ni; q += MT) dr[q] = v.drows[sn.drow_off + q] - ni;
     for (int j = tid; j < ncol; j += MT) po[j] = v.pidx[sn.first + j0 + j];
-    wide_start<T>(v, data, sl, sn, lay, dyn_smem, &bar, true);
+    wide_tables(v, sl, sn, lay, dyn_smem);
     pdl_wait();
     pdl_trigger();
     A* vd = reinterpret_cast<A*>(dyn_smem + lay.w);    // v at the dense rows (from j0), zero tail
-    A* xb = reinterpret_cast<A*>(dyn_smem + lay.ib);   // -x_B
+    A* xb = reinterpret_cast<A*>(dyn_smem + lay.ib);   // -x_B of the rows of the groups it owns
     for (int q = j0 + tid; q < ni; q += MT) vd[q] = (A)ybuf[sn.first + q];
-    for (int r = tid; r < nb; r += MT) xb[r] = (A)(-out[bi[r]]);
+    for (int q = max(ni, j0) + tid; q < nd; q += MT) vd[q] = (A)(-out[bi[dr[q - ni]]]);
     for (int q = nd + tid; q < nd + VEC; q += MT) vd[q] = (A)0;
+    {
+        const HLr* gd0 = reinterpret_cast<const HLr*>(dyn_smem + lay.gd);
+        const WideAdj* ad0 = reinterpret_cast<const WideAdj*>(dyn_smem + lay.ad);
+        for (int g = 0; g < ng; ++g)
+            if (ad0[g].owner == rank)
+                for (int i = tid; i < gd0[g].m; i += MT) {
+                    const int r = gd0[g].row0 - ni + i;
+                    xb[r] = (A)(-out[bi[r]]);
+                }
+    }
     __syncthreads();
-    for (int q = max(ni, j0) + tid; q < nd; q += MT) vd[q] = xb[dr[q - ni]];
     // an expired wait records the error and carries on (results invalid), so
     // that every CTA of the cluster still reaches the cluster barriers
     if (!mbar_wait_bounded(&bar) && tid == 0) atomicOr(err, 1u);
