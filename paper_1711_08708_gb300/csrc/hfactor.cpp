@@ -1147,6 +1147,30 @@ void cluster_liveness(const HFactorHost& F, const std::vector<uint8_t>& vlive, s
     }
 }
 
+void cluster_frontier(const HFactorHost& F, const std::vector<uint8_t>& live, std::vector<uint8_t>* send) {
+    const int nc = (int)F.sn.size();
+    send->assign(nc, 0);
+    std::vector<int32_t> owner(std::max<int64_t>(F.nslots, 1), -1);
+    for (int s = 0; s < nc; ++s) {
+        const HSnode& h = F.sn[s];
+        for (int64_t k = h.inc_off; k < h.inc_off + slot_stride(h) * (int64_t)(h.ni + h.nb) && k < F.nslots; ++k)
+            if (k >= 0) owner[k] = s;
+    }
+    for (int s = 0; s < nc; ++s) {
+        if (s < (int)live.size() && live[s]) {
+            (*send)[s] = 1;
+            continue;
+        }
+        const HSnode& h = F.sn[s];
+        for (int r = 0; r < h.nb && !(*send)[s]; ++r) {
+            const int32_t slot = F.uout[h.u_off + r];
+            if (slot >= 0 && slot < F.nslots && owner[slot] >= 0 && owner[slot] < (int)live.size() &&
+                live[owner[slot]])
+                (*send)[s] = 1;
+        }
+    }
+}
+
 int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from, TreeHost* T) {
     *T = TreeHost();
     const int H = (int)F.uf_ptr.size() - 1;

@@ -43,12 +43,15 @@ int wide_bytes_env() {
 // have all arrived (parents before the remaining leaves); backward, the
 // lowest-numbered one.  A missing dependency then reads an input before it is
 // written, so the result differs from the level-by-level replay.
-// With a mask (the masked solve), a flat group whose clusters are all dead,
-// and a dead large cluster, write c times the all-ones forward results
-// (y1 / y1slot) instead of computing.  fwd_y / fwd_slots (if given) receive
-// the forward results.
+// With a mask (the masked solve), every dead cluster (flat or large) takes c
+// times the all-ones forward results (y1 / y1slot) instead of computing; a
+// dead flat cluster writes its update slots only when its parent reads them
+// (cluster_frontier) and NaN otherwise, so a live cluster reading a slot that
+// the GPU's masked launch leaves unwritten makes the result NaN.  fwd_y /
+// fwd_slots (if given) receive the forward results.
 struct ReplayMask {
     const std::vector<uint8_t>* live = nullptr;
+    const std::vector<uint8_t>* send = nullptr;   // cluster_frontier of live
     const double* y1 = nullptr;
     const double* y1slot = nullptr;
     double c = 0.0;
@@ -60,12 +63,15 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             const ReplayMask* mask = nullptr, std::vector<double>* fwd_y = nullptr,
             std::vector<double>* fwd_slots = nullptr) {
     std::vector<double> xp(F.n), y(F.n, 0.0), inb(std::max<int64_t>(F.nslots, 2), 0.0);
-    auto scaled_copy = [&](const HSnode& s) {   // a dead cluster's forward results
+    auto scaled_copy = [&](const HSnode& s, bool slots = true) {   // a dead cluster's forward results
         for (int i = 0; i < s.ni; ++i) y[s.first + i] = mask->at(F.pidx[s.first + i]) * mask->y1[s.first + i];
         for (int r = 0; r < s.nb; ++r) {
             const int32_t slot = F.uout[s.u_off + r];
-            inb[slot] = mask->at(F.bidx[s.bidx_off + r]) * mask->y1slot[slot];
+            inb[slot] = slots ? mask->at(F.bidx[s.bidx_off + r]) * mask->y1slot[slot] : std::nan("");
         }
+    };
+    auto flat_dead = [&](int si) {   // a dead flat cluster: slots only where its parent reads them
+        scaled_copy(F.sn[si], !mask->send || (*mask->send)[si]);
     };
     std::vector<double> t(std::max<int64_t>(F.tbuf, 1), 0.0);
     const double* D = F.data.data();
@@ -152,7 +158,7 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             bool any = false;
             for (int c = G.c0; c < G.c1; ++c) any = any || (*mask->live)[F.gcl[c].s];
             if (!any) {
-                for (int c = G.c0; c < G.c1; ++c) scaled_copy(F.sn[F.gcl[c].s]);
+                for (int c = G.c0; c < G.c1; ++c) flat_dead(F.gcl[c].s);
                 return true;
             }
         }
@@ -165,6 +171,10 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 d.first != s.first || s.first != G.pstart + d.woff_f || s.bidx_off != G.bstart + d.boff ||
                 (s.nchild && s.inc_off + 2 * s.nd > G.sstart + G.sbytes / 8))
                 return false;
+            if (mask && !(*mask->live)[d.s]) {   // a dead cluster of a live group
+                flat_dead(d.s);
+                continue;
+            }
             for (int q = 0; q < s.nd; ++q) finish(s, q, fwd_part(s, q, 0, s.ni));
         }
         return true;
@@ -594,8 +604,11 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
     double shift = 0.0;
     for (int64_t i = 0; i < a.N; ++i) shift += b[i];
     shift /= (double)a.N;
+    std::vector<uint8_t> send;
+    cluster_frontier(F, live, &send);
     ReplayMask m;
     m.live = &live;
+    m.send = &send;
     m.y1 = y1.data();
     m.y1slot = y1slot.data();
     m.c = -shift;
@@ -653,7 +666,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         sched[4] = (int64_t)T.succ_b.size();
     }
     ReplayMask m;
-    std::vector<uint8_t> live;
+    std::vector<uint8_t> live, send;
     std::vector<double> y1, y1slot;
     if (masked) {   // which = 1, b zero outside the hearts: the masked forest solve
         if (which != 1) return set_error(BID_EINVAL, "the masked solve is the P_1 solve (which = 1)");
@@ -667,7 +680,9 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         std::vector<double> ones(lay.off[nslices], 1.0), xo(lay.off[nslices], 0.0);
         if (!replay(F, ones.data(), 0.0, xo.data(), nullptr, nullptr, nullptr, &y1, &y1slot))
             return set_error(BID_EINVAL, "flat group layout inconsistent");
+        cluster_frontier(F, live, &send);
         m.live = &live;
+        m.send = &send;
         m.y1 = y1.data();
         m.y1slot = y1slot.data();
         m.vshift = &vshift;

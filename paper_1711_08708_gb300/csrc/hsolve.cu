@@ -282,6 +282,7 @@ struct HShift {
 // every group computes.
 struct MaskArgs {
     const uint8_t* live = nullptr;
+    const uint8_t* clive = nullptr;   // per cluster (flat kernels: a dead cluster of a launched group)
     const double* csum = nullptr;    // c = -(*csum) * cinv ...
     double cinv = 0.0;
     const int16_t* seg = nullptr;    // ... or per segment (a forest's trees): c(vi) =
@@ -340,7 +341,7 @@ __device__ __forceinline__ double incoming_s(const double* ss, const GCl& c, int
 template <typename T, typename A>
 __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, const GCl* scl, int nc,
                                               const unsigned char* smem, A* w, double* ybuf, double* inb,
-                                              const int32_t* uo = nullptr) {
+                                              const int32_t* uo = nullptr, const MaskArgs* mk = nullptr) {
     constexpr int VEC = VecOf<T>::N;
     const double* ss = reinterpret_cast<const double*>(smem + G.nbytes);
     if (G.sbytes > 0) {   // add the children's updates (zero where none)
@@ -351,9 +352,24 @@ __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, c
         __syncthreads();
     }
     const T* sd = reinterpret_cast<const T*>(smem);
+    const double c0 = mk ? mask_c0(*mk) : 0.0;
     for (int u = threadIdx.x; u < G.uf; u += FT) {
         const GCl& c = scl[group_owner<2>(scl, nc, u)];
         const int q0 = (u - c.uf0) * VEC;
+        if (mk && mk->clive && !mk->clive[c.s]) {   // dead cluster of a launched group: scaled all-ones results
+            for (int e = 0; e < min(VEC, c.nd - q0); ++e) {
+                const int R = q0 + e;
+                if (R < c.ni) {
+                    const int p = G.pstart + c.woff_f + R;
+                    ybuf[p] = mask_c(*mk, c0, mk->seg ? v.pidx[p] : 0) * mk->y1[p];
+                } else {
+                    const int k = c.boff + R - c.ni;
+                    const int32_t slot = uo ? uo[k] : v.uout[G.bstart + k];
+                    inb[slot] = mask_c(*mk, c0, mk->seg ? v.bidx[G.bstart + k] : 0) * mk->y1slot[slot];
+                }
+            }
+            continue;
+        }
         const A* ws = w + c.woff_f;
         const T* col = sd + c.doff + q0;
         // a row group of pivot rows stops at its diagonal, others span all columns
@@ -411,16 +427,18 @@ __device__ __forceinline__ void flat_fwd_body(const HView& v, const FGroup& G, c
 // (GCl, at sc_off)] [staged inputs (A, at w_off)], sized per level.
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ data, int g0,
-                                                 const double* xp, double* ybuf, double* inb,
-                                                 unsigned int* err, int sc_off, int w_off, int ix_off,
+                                                 const int32_t* __restrict__ gl, const double* xp, double* ybuf,
+                                                 double* inb, unsigned int* err, int sc_off, int w_off, int ix_off,
                                                  MaskArgs mk) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
     A* w = reinterpret_cast<A*>(dyn_smem + w_off);
     int32_t* uo = reinterpret_cast<int32_t*>(dyn_smem + ix_off);   // update slots of the boundary rows
     __shared__ __align__(8) uint64_t bar;
-    const FGroup G = v.fg[g0 + blockIdx.x];
-    if (mk.live && !mk.live[g0 + blockIdx.x]) {   // constant input -c: scaled all-ones results
+    // group: the level's g0 + blockIdx.x, or the masked solve's launch list
+    const int gi = gl ? gl[blockIdx.x] : g0 + (int)blockIdx.x;
+    const FGroup G = v.fg[gi];
+    if (mk.live && !mk.live[gi]) {   // constant input -c: scaled all-ones results
         pdl_wait();
         pdl_trigger();
         const double c0 = mask_c0(mk);
@@ -449,7 +467,7 @@ __global__ void __launch_bounds__(FT) k_flat_fwd(HView v, const T* __restrict__ 
         if (threadIdx.x == 0) atomicOr(err, 1u);
         return;
     }
-    flat_fwd_body<T, A>(v, G, scl, nc, dyn_smem, w, ybuf, inb, uo);
+    flat_fwd_body<T, A>(v, G, scl, nc, dyn_smem, w, ybuf, inb, uo, mk.clive ? &mk : nullptr);
 }
 
 // Backward of one flat group from shared memory (factor block at smem,
@@ -500,7 +518,8 @@ __device__ __forceinline__ void flat_bwd_body(const HView& v, const FGroup& G, c
 template <typename T, typename A>
 __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ data, int g0,
                                                  const double* __restrict__ ybuf, double* out,
-                                                 unsigned int* err, int sc_off, int w_off, int ix_off) {
+                                                 unsigned int* err, int sc_off, int w_off, int ix_off,
+                                                 MaskArgs mk) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     GCl* scl = reinterpret_cast<GCl*>(dyn_smem + sc_off);
     A* vs = reinterpret_cast<A*>(dyn_smem + w_off);
@@ -520,12 +539,19 @@ __global__ void __launch_bounds__(FT) k_flat_bwd(HView v, const T* __restrict__ 
     pdl_wait();
     pdl_trigger();
     __syncthreads();
+    // masked solve: a dead cluster's y is c times the all-ones y (its group
+    // may not have been launched in the forward pass)
+    const double c0 = mk.clive ? mask_c0(mk) : 0.0;
     for (int f = threadIdx.x; f < G.wb; f += FT) {
         const GCl& c = scl[group_owner<1>(scl, nc, f)];
         const int q = f - c.woff_b;
         double x = 0.0;
-        if (q < c.ni) x = ybuf[G.pstart + c.woff_f + q];
-        else if (q < c.nd) x = -out[bo[c.boff + q - c.ni]];
+        if (q < c.ni) {
+            const int p = G.pstart + c.woff_f + q;
+            x = (mk.clive && !mk.clive[c.s]) ? mask_c(mk, c0, mk.seg ? po[c.woff_f + q] : 0) * mk.y1[p] : ybuf[p];
+        } else if (q < c.nd) {
+            x = -out[bo[c.boff + q - c.ni]];
+        }
         vs[f] = (A)x;
     }
     __syncthreads();
@@ -2259,6 +2285,11 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         mf.live = F.fg_live;
         mu.live = F.uf_live;
         mm = mu;
+        // per-cluster flags and the compacted launch list of the flat levels (not
+        // with the dataflow or persistent flat launches, which launch every group
+        // and compute every cluster of a live group)
+        if (F.cl_live && F.fg_mlist && !(F.tree_lev1 > F.tree_lev0 && tree_enabled()) && !flatp_enabled())
+            mf.clive = F.cl_live;
         mm.live = F.mid_live;
         mw = mu;
         mw.live = F.wide_live;
@@ -2322,8 +2353,14 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                                       S.xp, S.ybuf, inb, S.err, bs, sc_off, w_off, mf));
             } else {
                 const int ix_off = (int)((sm + 15) / 16 * 16);
-                BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, nf, FT, (size_t)ix_off + 4 * (size_t)F.fg_nbt[lev], L.st, v,
-                                      data, F.fg_ptr[lev], S.xp, S.ybuf, inb, S.err, sc_off, w_off, ix_off, mf));
+                // masked solve: only the groups holding a live cluster or a dead one
+                // whose parent reads its update slots
+                const int32_t* gl = mf.clive ? F.fg_mlist + F.fg_mptr[lev] : nullptr;
+                const int ng = mf.clive ? F.fg_mptr[lev + 1] - F.fg_mptr[lev] : nf;
+                if (ng > 0)
+                    BID_CUDA_TRY(launch_k(k_flat_fwd<T, A>, ng, FT, (size_t)ix_off + 4 * (size_t)F.fg_nbt[lev], L.st,
+                                          v, data, F.fg_ptr[lev], gl, S.xp, S.ybuf, inb, S.err, sc_off, w_off, ix_off,
+                                          mf));
             }
             ++launches;
         }
@@ -2410,7 +2447,8 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
                 const int ix_off = (int)((sm + 15) / 16 * 16);
                 BID_CUDA_TRY(launch_k(k_flat_bwd<T, A>, nf, FT,
                                       (size_t)ix_off + 4 * (size_t)(F.fg_nbt[lev] + F.fg_wf[lev]), L.st, v, data,
-                                      F.fg_ptr[lev], S.ybuf, out, S.err, sc_off, w_off, ix_off));
+                                      F.fg_ptr[lev], S.ybuf, out, S.err, sc_off, w_off, ix_off,
+                                      mf.clive ? mf : MaskArgs{}));
             }
             ++launches;
         }
@@ -2625,6 +2663,24 @@ int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFa
     for (size_t k = 0; k < h.wide.size(); ++k) wl[k] = live[h.wide[k].s];
     wl.push_back(1);
     BID_TRY(upload_vec(wl, &d->wide_live));
+    {   // per cluster, and the flat groups each level's masked forward launches
+        std::vector<uint8_t> send, cl(live);
+        cluster_frontier(h, live, &send);
+        cl.push_back(1);
+        BID_TRY(upload_vec(cl, &d->cl_live));
+        std::vector<int32_t> list;
+        d->fg_mptr.assign(1, 0);
+        for (size_t L = 0; L + 1 < h.fg_ptr.size(); ++L) {
+            for (int g = h.fg_ptr[L]; g < h.fg_ptr[L + 1]; ++g) {
+                bool any = false;
+                for (int c = h.fg[g].c0; c < h.fg[g].c1 && !any; ++c) any = send[h.gcl[c].s] != 0;
+                if (any) list.push_back(g);
+            }
+            d->fg_mptr.push_back((int32_t)list.size());
+        }
+        list.push_back(0);   // never empty
+        BID_TRY(upload_vec(list, &d->fg_mlist));
+    }
     for (size_t g = 0; g < h.fg.size(); ++g)
         for (int c = h.fg[g].c0; c < h.fg[g].c1; ++c) fl[g] |= live[h.gcl[c].s];
     for (size_t k = 0; k < h.uft.size(); ++k) {
@@ -2978,7 +3034,8 @@ void free_hfactor(HFactorDev* d) {
     void* ptrs[] = {d->pinflag, d->pidx, d->bidx, d->inc, d->drows, d->uout,  d->vgl, d->sn,
                     d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
                     d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot,
-                    d->mid, d->mid_live, d->wide, d->wslice, d->wpiece, d->wadj, d->wide_live};
+                    d->mid, d->mid_live, d->wide, d->wslice, d->wpiece, d->wadj, d->wide_live,
+                    d->cl_live, d->fg_mlist};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

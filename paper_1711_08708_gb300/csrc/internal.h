@@ -396,6 +396,9 @@ struct HFactorDev {
     uint8_t* uf_live = nullptr;
     uint8_t* mid_live = nullptr;
     uint8_t* wide_live = nullptr;
+    uint8_t* cl_live = nullptr;         // per cluster
+    int32_t* fg_mlist = nullptr;        // flat groups of the masked forward launches, level by level
+    std::vector<int32_t> fg_mptr;       // level -> range of fg_mlist
     double* y1 = nullptr;
     double* y1slot = nullptr;
     bool ones_ready = false;
@@ -437,10 +440,18 @@ int build_tree_sched(const HFactorHost& F, int acc_bytes, int smem_cap, int from
 // input -c alone, so its forward results are -c times those of the all-ones
 // input (masked solve).
 void cluster_liveness(const HFactorHost& F, const std::vector<uint8_t>& vlive, std::vector<uint8_t>* live);
+// Clusters whose update slots the masked solve reads: the live ones and the
+// dead ones with a live parent (the owner of one of their boundary slots).  A
+// dead cluster whose parent is dead writes nothing in the masked forward
+// pass: its parent takes the scaled all-ones results without reading slots,
+// and the backward pass forms its y as c times the all-ones y.
+void cluster_frontier(const HFactorHost& F, const std::vector<uint8_t>& live, std::vector<uint8_t>* send);
 
 int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d);
-// Flags of the masked solve (cluster_liveness with vlive) for the flat groups
-// and the upper forward tasks, and room for the all-ones forward results.
+// Flags of the masked solve (cluster_liveness with vlive) for the clusters,
+// the flat groups and the upper forward tasks, the flat groups each level's
+// masked forward launch covers (those holding a cluster of cluster_frontier),
+// and room for the all-ones forward results.
 int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFactorDev* d);
 void free_hfactor(HFactorDev* d);
 
