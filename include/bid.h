@@ -60,14 +60,18 @@
  *    BID_WIDE_BYTES=n factor bytes per CTA of a large cluster split in column
  *                    slices over a thread-block cluster (default 163840; 0:
  *                    none; read at preconditioner build);
+ *    BID_ROOT_GRAM=0 the root cluster keeps its forward and backward passes
+ *                    instead of one product with its Gram matrix (read at
+ *                    preconditioner build);
  *    BID_GPU_FRONT_NF=n  smallest front factorised on the GPU (default 1024);
  *    BID_GROUP_BYTES / BID_GROUP_BYTES_LEAF  flat group size in bytes
  *                    (1024..65536, default 12288), read at preconditioner build.
  *    Results are the same with every setting: bit for bit, except that the
  *    masked solve's clusters computed in full (all of them with BID_MASK=0,
  *    those of the levels that BID_TREE or BID_UPPER take over) round
- *    differently, and that BID_MID_BYTES and BID_WIDE_BYTES change the
- *    summation order of the large clusters they move between kinds of kernels.
+ *    differently, and that BID_MID_BYTES, BID_WIDE_BYTES and BID_ROOT_GRAM
+ *    change the summation order of the large clusters they move between kinds
+ *    of kernels.
  */
 #ifndef BID_H
 #define BID_H
@@ -210,6 +214,10 @@ typedef struct bid_precond_stats {
                                           BID_WIDE_BYTES bytes per CTA, default 160 KiB; 0
                                           turns them off); counted where the device runs
                                           them (the host replay: where they are built) */
+    int64_t gram_pivots1, gram_pivotsk;  /* pivots of the root cluster whose forward and
+                                          backward passes are one product with its Gram
+                                          matrix M^T M (0: none; BID_ROOT_GRAM=0 turns it
+                                          off) */
 } bid_precond_stats;
 
 typedef struct bid_solve_info {

@@ -62,7 +62,8 @@ class PrecondStats(C.Structure):
                 ("masked_clusters1", C.c_int64), ("alg_bytes_p1_masked", C.c_int64),
                 ("flatp_levels1", C.c_int32), ("flatp_levelsk", C.c_int32),
                 ("mid_clusters1", C.c_int64), ("mid_clustersk", C.c_int64),
-                ("wide_clusters1", C.c_int64), ("wide_clustersk", C.c_int64)]
+                ("wide_clusters1", C.c_int64), ("wide_clustersk", C.c_int64),
+                ("gram_pivots1", C.c_int64), ("gram_pivotsk", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

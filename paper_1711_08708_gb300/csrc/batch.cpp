@@ -467,6 +467,7 @@ int bid_batch_create(bid_system* const* systems, int nslices, const bid_precond_
     if (const char* ub = std::getenv("BID_UP_BROWS")) bo.up_brows = std::max(32, std::atoi(ub));
     if (const char* mb = std::getenv("BID_MID_BYTES")) bo.mid_bytes = std::max(0, std::atoi(mb));
     if (const char* wb = std::getenv("BID_WIDE_BYTES")) bo.wide_bytes = std::max(0, std::atoi(wb));
+    if (const char* rg = std::getenv("BID_ROOT_GRAM")) bo.root_gram = std::strcmp(rg, "0") != 0;
     HFactorHost h1, hk;
     if (rc == BID_OK) rc = build_batch_factor(hosts, L, 1, B->gamma, bo, lf, &h1);
     if (rc == BID_OK) rc = build_batch_factor(hosts, L, 2, B->gamma, bo, lf, &hk);

@@ -433,6 +433,7 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     if (const char* ub = std::getenv("BID_UP_BROWS")) bo.up_brows = std::max(32, std::atoi(ub));
     if (const char* mb = std::getenv("BID_MID_BYTES")) bo.mid_bytes = std::max(0, std::atoi(mb));
     if (const char* wb = std::getenv("BID_WIDE_BYTES")) bo.wide_bytes = std::max(0, std::atoi(wb));
+    if (const char* rg = std::getenv("BID_ROOT_GRAM")) bo.root_gram = std::strcmp(rg, "0") != 0;
     bo.gpu_front = o->gpu_build != 0;
     if (const char* gf = std::getenv("BID_GPU_FRONT_NF")) bo.gpu_front_nf = std::max(16, std::atoi(gf));
     HFactorHost h1, hk;
@@ -563,6 +564,8 @@ int bid_precond_build_ex(bid_system* s, const bid_precond_opts* o, bid_precond**
     };
     st.wide_clusters1 = wide_run(h1, P->F1);
     st.wide_clustersk = wide_run(hk, P->FK);
+    st.gram_pivots1 = P->F1.gram ? P->F1.gram_ni : 0;
+    st.gram_pivotsk = P->FK.gram ? P->FK.gram_ni : 0;
     auto flatp_levels = [](const HFactorDev& d) {
         int32_t c = 0;
         if (hsolve_flatp_enabled())

@@ -971,6 +971,17 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         F->ub_ptr.push_back((int32_t)F->ubt.size());
         F->mid_ptr.push_back((int32_t)F->mid.size());
     }
+    // root Gram candidate (HFactorHost::gram): the top level's only cluster,
+    // large, without boundary or low-rank groups; its level takes neither the
+    // mid nor the wide kernels
+    int gram_root = -1;
+    if (o.root_gram && !o.upper_levels && H > 0 && bylev[H - 1].size() == 1) {
+        const int r = bylev[H - 1][0];
+        const HSnode& h = F->sn[r];
+        if (h.large && h.nb == 0 && h.lr_end == h.lr_begin && h.ni >= GRAM_NI_MIN && h.ni <= GRAM_NI_MAX &&
+            h.nd == h.ni && !is_mid[r])
+            gram_root = r;
+    }
     // wide clusters (WideCl): on a level whose large clusters are all task
     // clusters, each split into C column slices of at most o.wide_bytes bytes
     // (C the level's largest need, at most WIDE_MAX_CTAS); the tasks stay
@@ -1079,7 +1090,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         };
         for (int L = 0; L < H; ++L) {
             std::vector<int> lc;
-            bool ok = o.wide_bytes > 0 && !o.upper_levels;
+            bool ok = o.wide_bytes > 0 && !o.upper_levels && !(gram_root >= 0 && L == H - 1);
             for (int s : bylev[L]) {
                 const HSnode& h = F->sn[s];
                 if (!h.large) continue;
@@ -1103,6 +1114,24 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
                 F->wide_c[L] = C;
             }
             F->wide_ptr.push_back((int32_t)F->wide.size());
+        }
+    }
+    // root Gram matrix G = M_r^T M_r (row-major, FP64; M_r = L_rr^-1 unpacked)
+    F->gram_s = F->gram_lev = -1;
+    F->gram.clear();
+    if (gram_root >= 0) {
+        const int root = gram_root;
+        const HSnode* h = &F->sn[root];
+        {
+            const int ni = h->ni;
+            std::vector<double> Mt((size_t)ni * ni, 0.0);   // Mt[j][q] = M[q][j]
+            for (int j = 0; j < ni; ++j)
+                for (int q = j; q < ni; ++q)
+                    Mt[(size_t)j * ni + q] = F->data[h->data_off + col_start(ni, j, vec) - j + q];
+            F->gram.assign((size_t)ni * ni, 0.0);
+            dense::gemm_nt(ni, ni, ni, 1.0, Mt.data(), ni, Mt.data(), ni, F->gram.data(), ni, true);
+            F->gram_s = root;
+            F->gram_lev = H - 1;
         }
     }
     F->tbuf = tbuf;

@@ -32,6 +32,12 @@ int wide_bytes_env() {
     return e ? std::max(0, std::atoi(e)) : WIDE_DATA_MAX;
 }
 
+// BID_ROOT_GRAM=0 in the environment: no root Gram product
+bool root_gram_env() {
+    const char* e = std::getenv("BID_ROOT_GRAM");
+    return !(e && std::strcmp(e, "0") == 0);
+}
+
 // x = P^-1 (b - shift) with the pinned entry zeroed: the same work items, in
 // the same order, as the GPU launches (permuted input, per-level flat items
 // with their splits, mid and wide clusters, large-cluster tasks, parent input
@@ -218,6 +224,8 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 const HSnode& s = F.sn[si];
                 if (s.large && s.height == lev && !(*mask->live)[si]) scaled_copy(s);
             }
+        if (lev == F.gram_lev && F.gram_s >= 0 && (mask ? (*mask->live)[F.gram_s] != 0 : !fwd_y))
+            continue;   // the root: its forward and backward are one product with G in the backward pass
         if (F.wide_c[lev] > 0) {   // wide clusters: C column slices, partials combined by rank
             const int C = F.wide_c[lev];
             for (int wi = F.wide_ptr[lev]; wi < F.wide_ptr[lev + 1]; ++wi) {
@@ -358,6 +366,18 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             continue;
         }
         std::vector<std::pair<int32_t, double>> xs;   // outputs of this level, written after
+        if (lev == F.gram_lev && F.gram_s >= 0 && (mask ? (*mask->live)[F.gram_s] != 0 : !fwd_y)) {
+            // root Gram product: x_r = G w_r, w_r the root's input and its children's updates
+            const HSnode& s = F.sn[F.gram_s];
+            std::vector<double> wr(s.ni);
+            for (int j = 0; j < s.ni; ++j) wr[j] = gather(s, j);
+            for (int i = 0; i < s.ni; ++i) {
+                double a = 0.0;
+                for (int j = 0; j < s.ni; ++j) a += F.gram[(size_t)i * s.ni + j] * wr[j];
+                x[F.pidx[s.first + i]] = a;
+            }
+            continue;
+        }
         if (F.wide_c[lev] > 0) {
             const int C = F.wide_c[lev];
             for (int wi = F.wide_ptr[lev]; wi < F.wide_ptr[lev + 1]; ++wi) {
@@ -527,6 +547,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
     HBuildOpts o;
     o.mid_bytes = mid_bytes_env();
     o.wide_bytes = wide_bytes_env();
+    o.root_gram = root_gram_env();
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
@@ -567,6 +588,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
         stats->lowrank_blocks = F.nlr;
         stats->mid_clusters1 = (int64_t)F.mid.size();
         stats->wide_clusters1 = (int64_t)F.wide.size();
+        stats->gram_pivots1 = F.gram_s >= 0 ? F.sn[F.gram_s].ni : 0;
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
     }
@@ -584,6 +606,7 @@ int bid_host_factor_solve_masked(const bid_host_system* h, double eps, int leaf,
     HBuildOpts o;
     o.mid_bytes = mid_bytes_env();
     o.wide_bytes = wide_bytes_env();
+    o.root_gram = root_gram_env();
     o.eps = eps;
     o.leaf = leaf;
     o.block = block;
@@ -640,6 +663,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
     HBuildOpts o;
     o.mid_bytes = mid_bytes_env();
     o.wide_bytes = wide_bytes_env();
+    o.root_gram = root_gram_env();
     o.eps = eps;
     o.leaf = leaf_default;
     o.block = block;
@@ -700,6 +724,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         stats->lowrank_blocks = F.nlr;
         stats->mid_clusters1 = (int64_t)F.mid.size();
         stats->wide_clusters1 = (int64_t)F.wide.size();
+        stats->gram_pivots1 = F.gram_s >= 0 ? F.sn[F.gram_s].ni : 0;
     }
     return BID_OK;
 }

@@ -77,6 +77,10 @@ template <typename T>
 struct VecOf {
     static constexpr int N = 16 / sizeof(T);
 };
+template <typename T>
+constexpr size_t precision_size() {
+    return sizeof(T);
+}
 
 template <typename A>
 __device__ __forceinline__ A wsum(A v) {
@@ -2001,6 +2005,56 @@ __global__ void __launch_bounds__(MT) k_wide_bwd(HView v, const T* __restrict__ 
     }
 }
 
+// ------------------------------------------------------------ root Gram product
+// x_r = G w_r for the root cluster (HFactorHost::gram): CTA b holds rows
+// [b R, b R + R) of G (row stride ld, zero padded), bulk-copied before the
+// dependency wait; after it the CTA gathers w_r (the root's input and its
+// children's updates) and one warp per row forms the product, summed by the
+// warp in a fixed order.
+template <typename T, typename A>
+__global__ void __launch_bounds__(MT) k_gram(HView v, const T* __restrict__ G, int ld, int rows, int s,
+                                             const double* xp, const double* inb, double* out,
+                                             unsigned int* err) {
+    constexpr int VEC = VecOf<T>::N;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int32_t po[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const HSnode sn = v.sn[s];
+    const int ni = sn.ni;
+    const int r0 = blockIdx.x * rows, nr = min(rows, ni - r0);
+    const int gbytes = nr * ld * (int)sizeof(T);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, (uint32_t)gbytes);
+        bulk_region(dyn_smem, G + (int64_t)r0 * ld, gbytes, &bar);
+    }
+    if (tid < nr) po[tid] = v.pidx[sn.first + r0 + tid];
+    A* w = reinterpret_cast<A*>(dyn_smem + ((size_t)rows * ld * sizeof(T) + 15) / 16 * 16);
+    __syncthreads();
+    pdl_wait();
+    pdl_trigger();
+    for (int j = tid; j < ld; j += blockDim.x)
+        w[j] = j < ni ? (A)(xp[sn.first + j] + (sn.nchild ? slot_sum(sn, j, inb) : 0.0)) : (A)0;
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar)) {
+        if (tid == 0) atomicOr(err, 1u);
+        return;
+    }
+    if (warp < nr) {
+        const T* g = reinterpret_cast<const T*>(dyn_smem) + (size_t)warp * ld;
+        A acc = 0;
+        for (int j = VEC * lane; j < ld; j += 32 * VEC) {
+            A val[VEC];
+            lds16(g + j, val);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc += val[e] * w[j + e];
+        }
+        acc = wsum(acc);
+        if (lane == 0) out[po[warp]] = (double)acc;
+    }
+}
+
 // ------------------------------------------------------------ upper levels, persistent
 // The levels [lev0, lev1) hold only large clusters; one cooperative launch
 // per pass runs them all, the CTAs striding over each level's work items,
@@ -2364,6 +2418,17 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             }
             ++launches;
         }
+        if (lev == F.gram_lev && F.gram && (!mu.live || F.gram_masked)) {   // the root: one Gram product
+            const int rows = F.gram_rows;
+            const size_t sm = ((size_t)rows * F.gram_ld * (precision_size<T>()) + 15) / 16 * 16 +
+                              sizeof(A) * (size_t)F.gram_ld;
+            const int ni = F.gram_ni;
+            BID_CUDA_TRY(launch_k(k_gram<T, A>, (ni + rows - 1) / rows, 32 * rows, sm, L.st, v,
+                                  reinterpret_cast<const T*>(F.gram), F.gram_ld, rows, F.gram_s, S.xp, inb, out,
+                                  S.err));
+            ++launches;
+            continue;
+        }
         const int wcn = F.wide_c[lev];
         if (wcn > 0) {   // wide level: one cluster of wcn CTAs per large cluster, no tasks
             const MidLayout& ly = F.wide_lay[lev];
@@ -2405,6 +2470,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             lev = t0;
             continue;
         }
+        if (lev == F.gram_lev && F.gram && (!mu.live || F.gram_masked)) continue;   // done by k_gram
         const int wcn = F.wide_c[lev];
         const int ng = wcn > 0 ? 0 : F.ulr_mid[lev] - F.ulr_ptr[lev];   // the task clusters' low-rank groups
         const int nv = wcn > 0 ? 0 : F.vg_ptr[lev + 1] - F.vg_ptr[lev];
@@ -2492,6 +2558,7 @@ int prepare_one() {
                                       MID_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       MID_SMEM_MAX));
+    BID_CUDA_TRY(cudaFuncSetAttribute(k_gram<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_fwd<T, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_bwd<T, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return BID_OK;
@@ -2566,7 +2633,12 @@ int hsolve_ones(const Launch& L, HFactorDev* F, const HScratch& S, int64_t vn) {
     int rc = BID_OK;
     k_fill<<<L.sms * 4, 256, 0, L.st>>>(n, 1.0, ones);
     count_launches(1);
+    // the root's own passes, not its Gram product, so that its y is there for a
+    // masked solve in which the root is dead
+    const int gram_lev = F->gram_lev;
+    if (!F->gram_masked) F->gram_lev = -1;
     rc = launch_hsolve(L, *F, ones, nullptr, 0.0, S, x);
+    F->gram_lev = gram_lev;
     const double* inb = S.inb ? S.inb : F->inb;
     if (rc == BID_OK &&
         (cudaMemcpyAsync(F->y1, S.ybuf, sizeof(double) * F->n, cudaMemcpyDeviceToDevice, L.st) != cudaSuccess ||
@@ -2663,6 +2735,7 @@ int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFa
     for (size_t k = 0; k < h.wide.size(); ++k) wl[k] = live[h.wide[k].s];
     wl.push_back(1);
     BID_TRY(upload_vec(wl, &d->wide_live));
+    d->gram_masked = d->gram_s >= 0 && live[d->gram_s];
     {   // per cluster, and the flat groups each level's masked forward launches
         std::vector<uint8_t> send, cl(live);
         cluster_frontier(h, live, &send);
@@ -2960,6 +3033,42 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_vec(h.ubt, &d->ubt));
     BID_TRY(upload_mid(h, precision, d));
     BID_TRY(upload_wide(h, precision, d));
+    d->gram = nullptr;
+    d->gram_s = d->gram_lev = -1;
+    if (h.gram_s >= 0) {   // root Gram matrix in the storage precision, rows padded to whole vectors
+        const int ni = h.sn[h.gram_s].ni;
+        const int vec = want_vec;
+        const int ld = (ni + vec - 1) / vec * vec;
+        const int esz = precision == BID_FP64 ? 8 : precision == BID_FP32 ? 4 : 2;
+        if ((int64_t)h.gram.size() != (int64_t)ni * ni) return set_error(BID_EINVAL, "root Gram matrix size");
+        int rows = GRAM_ROWS;   // rows per CTA: whole rows within the shared memory, with w
+        while (rows > 1 && (size_t)rows * ld * esz + 16 + (size_t)(precision == BID_FP64 ? 8 : 4) * ld >
+                               (size_t)MID_SMEM_MAX)
+            rows /= 2;
+        if ((size_t)ld * esz + 16 + (size_t)8 * ld <= (size_t)MID_SMEM_MAX) {
+            if (precision == BID_FP64) {
+                std::vector<double> g((size_t)ni * ld, 0.0);
+                for (int i = 0; i < ni; ++i)
+                    for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = h.gram[(size_t)i * ni + j];
+                BID_TRY(upload_vec(g, reinterpret_cast<double**>(&d->gram)));
+            } else if (precision == BID_FP32) {
+                std::vector<float> g((size_t)ni * ld, 0.0f);
+                for (int i = 0; i < ni; ++i)
+                    for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = (float)h.gram[(size_t)i * ni + j];
+                BID_TRY(upload_vec(g, reinterpret_cast<float**>(&d->gram)));
+            } else {
+                std::vector<uint16_t> g((size_t)ni * ld, 0);
+                for (int i = 0; i < ni; ++i)
+                    for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = to_bf16((float)h.gram[(size_t)i * ni + j]);
+                BID_TRY(upload_vec(g, reinterpret_cast<uint16_t**>(&d->gram)));
+            }
+            d->gram_s = h.gram_s;
+            d->gram_lev = h.gram_lev;
+            d->gram_ld = ld;
+            d->gram_ni = ni;
+            d->gram_rows = rows;
+        }
+    }
     d->fg_ptr = h.fg_ptr;
     d->fg_bytes = h.fg_bytes;
     d->fg_nc = h.fg_nc;
@@ -3035,7 +3144,7 @@ void free_hfactor(HFactorDev* d) {
                     d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
                     d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot,
                     d->mid, d->mid_live, d->wide, d->wslice, d->wpiece, d->wadj, d->wide_live,
-                    d->cl_live, d->fg_mlist};
+                    d->cl_live, d->fg_mlist, d->gram};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

@@ -237,6 +237,8 @@ struct WideAdj {        // shared-memory element of V(j, l) = vadj + j k + l; of
     int32_t owner, pad;
 };
 constexpr int WIDE_MAX_CTAS = 16;
+constexpr int GRAM_NI_MIN = 1024, GRAM_NI_MAX = 4096;   // root sizes that take the Gram product
+constexpr int GRAM_ROWS = 16;                           // rows of G per CTA (one per warp)
 constexpr int WIDE_ND = 4096, WIDE_NB = 4096;   // largest dense rows / boundary rows
 constexpr int WIDE_DATA_MAX = 160 * 1024;   // factor bytes of one CTA of a wide cluster
 constexpr int MID_BYTES_DEFAULT = 96 * 1024;   // largest block of a mid cluster (bytes)
@@ -280,6 +282,13 @@ struct HFactorHost {
     int32_t vec = 2;
     int32_t lev_upper = 0;     // levels >= lev_upper hold only large clusters
     int64_t dense_entries = 0, lowrank_entries = 0;   // algorithmic (no padding)
+    // Root Gram matrix: when the top level holds one large cluster r with no
+    // boundary and no low-rank groups (its forward and backward passes are
+    // x_r = M_r^T (M_r w_r) with nothing in between), G = M_r^T M_r (ni x ni,
+    // row-major, FP64) replaces both passes by one product x_r = G w_r.
+    int32_t gram_s = -1;                       // the root cluster, or -1
+    int32_t gram_lev = -1;                     // its level
+    std::vector<double> gram;
     int64_t nsmall = 0, nlarge = 0, nlr = 0;
 };
 
@@ -312,6 +321,7 @@ struct HBuildOpts {
     // least merge_min nodes have their levels merged in pairs; 0: off
     int64_t merge_min = 0;
     // fronts with at least gpu_front_nf rows factorised on the GPU (gpu_front_factor)
+    bool root_gram = true;                   // G = M^T M of the root (HFactorHost::gram) when it applies
     bool gpu_front = false;
     int gpu_front_nf = 1024;
 };
@@ -397,6 +407,9 @@ struct HFactorDev {
     uint8_t* mid_live = nullptr;
     uint8_t* wide_live = nullptr;
     uint8_t* cl_live = nullptr;         // per cluster
+    void* gram = nullptr;               // root Gram matrix (storage precision, row stride gram_ld), or NULL
+    int32_t gram_s = -1, gram_lev = -1, gram_ld = 0, gram_ni = 0, gram_rows = 1;
+    bool gram_masked = false;           // the masked solve may use it too (the root is live)
     int32_t* fg_mlist = nullptr;        // flat groups of the masked forward launches, level by level
     std::vector<int32_t> fg_mptr;       // level -> range of fg_mlist
     double* y1 = nullptr;

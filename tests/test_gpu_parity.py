@@ -366,6 +366,43 @@ def test_wide_clusters_equal_chunked_kernels(bid, monkeypatch, precision, leaf):
     assert_potentials_close(out[None][3], out["0"][3], o.N, 1e-8, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_root_gram_equals_root_passes(bid, monkeypatch, precision):
+    # the root's two passes replaced by one product with G = M_r^T M_r (the
+    # default where the root has no boundary, no low-rank groups and 1024 to
+    # 4096 pivots) against the passes themselves (BID_ROOT_GRAM=0), 1025^2
+    # slice: the same P_1 and P_Lambda^-1 applications up to the storage
+    # precision's rounding, and PCG solves within one iteration that agree
+    # potential by potential to 1e-8
+    mesh, p = torso_square_2d(1025), params_2d(0.1)
+    S = bid.System(mesh, p)
+    o = ob.build_system(mesh, p)
+    rng = np.random.default_rng(1026)
+    b1, r = T(rng.normal(size=S.N)), T(rng.normal(size=S.N + S.NH))
+    Y = T(ob.rhs(o, p["v_rest"] + 100 * rng.random(o.NH), np.ones(o.NH), np.zeros(o.NH), 5.0, p["dt"]))
+    out = {}
+    for rg in ("0", None):
+        if rg is None:
+            monkeypatch.delenv("BID_ROOT_GRAM", raising=False)
+        else:
+            monkeypatch.setenv("BID_ROOT_GRAM", rg)
+        P = bid.Precond(S, p["dt"], eps=1e-3 if precision == "fp32" else 0.0, precision=precision, leaf=32)
+        x1, z = torch.zeros_like(b1), torch.zeros_like(r)
+        P.apply_factor(1, b1, x1)
+        P.apply(r, z)
+        X = torch.zeros_like(r)
+        info = P.solve(Y, X, tol=1e-13, max_iter=800)
+        out[rg] = (H(x1), H(z), H(X), info["iters"], P.stats["gram_pivots1"])
+        del P
+    assert out["0"][4] == 0 and out[None][4] == 1025, (out["0"][4], out[None][4])
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    for a, c in zip(out["0"][:2], out[None][:2]):
+        assert np.isfinite(c).all()
+        assert np.abs(a - c).max() <= tol * np.abs(a).max()
+    assert abs(out["0"][3] - out[None][3]) <= 1, (out["0"][3], out[None][3])
+    assert_potentials_close(out[None][2], out["0"][2], o.N, 1e-8, precision)
+
+
 def test_full_size_513_properties(bid):
     _full_size_properties(bid, 513, 3, 1e-3, "fp64")
 

@@ -224,6 +224,32 @@ def test_wide_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
         assert np.abs(a - c).max() <= 1e-12 * np.abs(a).max()
 
 
+def test_root_gram_equals_root_passes(bid, monkeypatch):
+    # the root cluster (no boundary, no low-rank groups) solved as one product
+    # x_r = G w_r with G = M_r^T M_r formed at build, against its forward and
+    # backward passes (BID_ROOT_GRAM=0): the same P_1 and masked P_1 solves up
+    # to rounding on the 1025^2 slice, whose root separator has 1025 pivots
+    m, p = torso_square_2d(1025), params_2d(0.1)
+    hs = bid.HostSystem(m, p)
+    o = ob.build_system(m, p)
+    rng = np.random.default_rng(1025)
+    b1 = rng.normal(size=o.N)
+    bm = np.zeros(o.N)
+    bm[:o.NH] = rng.normal(size=o.NH)
+    out = {}
+    for rg in ("0", None):
+        if rg is None:
+            monkeypatch.delenv("BID_ROOT_GRAM", raising=False)
+        else:
+            monkeypatch.setenv("BID_ROOT_GRAM", rg)
+        x1, st = hs.factor_solve(1, b1, eps=1e-3, leaf=32, precision="fp32")
+        xm, _ = hs.factor_solve_masked(bm, eps=1e-3, leaf=32, precision="fp32")
+        out[rg] = (x1, xm, st["gram_pivots1"])
+    assert out["0"][2] == 0 and out[None][2] == 1025
+    for a, c in zip(out["0"][:2], out[None][:2]):
+        assert np.abs(a - c).max() <= 1e-12 * np.abs(a).max()
+
+
 def test_host_factor_3d_exact():
     import __graft_entry__
     __graft_entry__.build()
