@@ -237,7 +237,7 @@ struct WideAdj {        // shared-memory element of V(j, l) = vadj + j k + l; of
     int32_t owner, pad;
 };
 constexpr int WIDE_MAX_CTAS = 16;
-constexpr int GRAM_NI_MIN = 1024, GRAM_NI_MAX = 4096;   // root sizes that take the Gram product
+constexpr int GRAM_NI_MIN = 128, GRAM_NI_MAX = 4096;    // root sizes that take the Gram product
 constexpr int GRAM_ROWS = 16;                           // rows of G per CTA (one per warp)
 constexpr int WIDE_ND = 4096, WIDE_NB = 4096;   // largest dense rows / boundary rows
 constexpr int WIDE_DATA_MAX = 160 * 1024;   // factor bytes of one CTA of a wide cluster

@@ -209,6 +209,7 @@ def test_wide_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
     bm = np.zeros(o.N)
     bm[:o.NH] = rng.normal(size=o.NH)
     g = p["chi"] * p["Cm"] / p["dt"]
+    monkeypatch.setenv("BID_ROOT_GRAM", "0")   # the root stays a wide cluster here
     out = {}
     for wb in ("0", None):
         if wb is None:
