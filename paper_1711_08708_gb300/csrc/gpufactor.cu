@@ -261,3 +261,31 @@ int gpu_front_factor(int nf, int ni, const double* Fh, double* Mh, double* Uh, i
 }
 
 }  // namespace bid
+
+namespace bid {
+
+int gpu_gram_nt(int n, const double* Ah, double* Gh) {
+    if (n <= 0) return set_error(BID_EINVAL, "gpu gram: bad size");
+    std::lock_guard<std::mutex> lock(g_gf_mu);
+    double *A = nullptr, *G = nullptr;
+    cudaStream_t st = nullptr;
+    const size_t sz = sizeof(double) * (size_t)n * n;
+    int rc = BID_OK;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&A, sz) != cudaSuccess || cudaMalloc(&G, sz) != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(BID_ENOMEM, "gpu gram: device allocation of %d x %d failed", n, n);
+    }
+    if (rc == BID_OK && cudaMemcpyAsync(A, Ah, sz, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = set_error(BID_ECUDA, "gpu gram upload: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == BID_OK) rc = gemm<true, false>(n, n, n, 1.0, A, n, A, n, 0, G, n, st);
+    if (rc == BID_OK && (cudaMemcpyAsync(Gh, G, sz, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess))
+        rc = set_error(BID_ECUDA, "gpu gram: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(A);
+    cudaFree(G);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
+}  // namespace bid

@@ -971,16 +971,31 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         F->ub_ptr.push_back((int32_t)F->ubt.size());
         F->mid_ptr.push_back((int32_t)F->mid.size());
     }
-    // root Gram candidate (HFactorHost::gram): the top level's only cluster,
-    // large, without boundary or low-rank groups; its level takes neither the
-    // mid nor the wide kernels
-    int gram_root = -1;
+    // top block (HFactorHost::gram): the top level's only cluster r, large,
+    // without boundary or low-rank groups, and its children when the level
+    // below holds exactly them (large, two update slots per row, boundary
+    // within r's pivots); the block's levels take neither the mid nor the wide
+    // kernels
+    int gram_root = -1, top_k = 0;
     if (o.root_gram && !o.upper_levels && H > 0 && bylev[H - 1].size() == 1) {
         const int r = bylev[H - 1][0];
         const HSnode& h = F->sn[r];
         if (h.large && h.nb == 0 && h.lr_end == h.lr_begin && h.ni >= GRAM_NI_MIN && h.ni <= GRAM_NI_MAX &&
-            h.nd == h.ni && !is_mid[r])
+            h.nd == h.ni && !is_mid[r] && slot_stride(h) == 2) {
             gram_root = r;
+            top_k = 1;
+            if (H > 1 && (int)bylev[H - 2].size() == nch[r] && nch[r] > 0) {
+                std::vector<int32_t> rpiv(h.first, h.first + h.ni);   // positions of r's pivots
+                bool ok = true;
+                int64_t ntop = h.ni;
+                for (int s : bylev[H - 2]) {
+                    const HSnode& c = F->sn[s];
+                    ntop += c.ni;
+                    if (parent[s] != r || !c.large || is_mid[s] || slot_stride(c) != 2 || c.ni == 0) ok = false;
+                }
+                if (ok && ntop <= TOP_N_MAX) top_k = 2;
+            }
+        }
     }
     // wide clusters (WideCl): on a level whose large clusters are all task
     // clusters, each split into C column slices of at most o.wide_bytes bytes
@@ -1090,7 +1105,7 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
         };
         for (int L = 0; L < H; ++L) {
             std::vector<int> lc;
-            bool ok = o.wide_bytes > 0 && !o.upper_levels && !(gram_root >= 0 && L == H - 1);
+            bool ok = o.wide_bytes > 0 && !o.upper_levels && !(gram_root >= 0 && L >= H - top_k);
             for (int s : bylev[L]) {
                 const HSnode& h = F->sn[s];
                 if (!h.large) continue;
@@ -1116,23 +1131,116 @@ int build_hfactor(const CsrHost& A, const double* coords, int dim,
             F->wide_ptr.push_back((int32_t)F->wide.size());
         }
     }
-    // root Gram matrix G = M_r^T M_r (row-major, FP64; M_r = L_rr^-1 unpacked)
+    // top-block Gram matrix G = M_top^T M_top (row-major, FP64), M_top = L_top^-1
+    // assembled from the stored blocks: the children's L_cc^-1, r's L_rr^-1,
+    // and -L_rr^-1 (L_rc L_cc^-1) below the children (their boundary rows,
+    // low-rank groups expanded, placed at r's pivots)
     F->gram_s = F->gram_lev = -1;
     F->gram.clear();
-    if (gram_root >= 0) {
+    F->top_cl.clear();
+    F->top_pos.clear();
+    F->top_sptr.assign(1, 0);
+    F->top_slot.clear();
+    while (gram_root >= 0) {
         const int root = gram_root;
-        const HSnode* h = &F->sn[root];
-        {
-            const int ni = h->ni;
-            std::vector<double> Mt((size_t)ni * ni, 0.0);   // Mt[j][q] = M[q][j]
-            for (int j = 0; j < ni; ++j)
-                for (int q = j; q < ni; ++q)
-                    Mt[(size_t)j * ni + q] = F->data[h->data_off + col_start(ni, j, vec) - j + q];
-            F->gram.assign((size_t)ni * ni, 0.0);
-            dense::gemm_nt(ni, ni, ni, 1.0, Mt.data(), ni, Mt.data(), ni, F->gram.data(), ni, true);
-            F->gram_s = root;
-            F->gram_lev = H - 1;
+        const HSnode& hr = F->sn[root];
+        std::vector<int> cls;
+        if (top_k == 2)
+            for (int s : bylev[H - 2]) cls.push_back(s);
+        // rows: the children's pivots, then r's
+        std::vector<int> off(cls.size() + 1, 0);
+        for (size_t k = 0; k < cls.size(); ++k) off[k + 1] = off[k] + F->sn[cls[k]].ni;
+        const int offr = off.back(), n = offr + hr.ni;
+        // root-local index of each of r's pivot nodes (vector index -> a)
+        std::vector<std::pair<int32_t, int32_t>> rmap;
+        for (int a = 0; a < hr.ni; ++a) rmap.push_back({F->pidx[hr.first + a], a});
+        std::sort(rmap.begin(), rmap.end());
+        auto rlocal = [&](int32_t vi) {
+            auto it = std::lower_bound(rmap.begin(), rmap.end(), std::make_pair(vi, (int32_t)-1));
+            return (it != rmap.end() && it->first == vi) ? it->second : -1;
+        };
+        auto M = [&](const HSnode& h, int q, int j) { return F->data[h.data_off + col_start(h.nd, j, vec) - j + q]; };
+        std::vector<double> Mt((size_t)n * n, 0.0);   // Mt[i][q] = M_top[q][i]
+        for (int j = 0; j < hr.ni; ++j)
+            for (int q = j; q < hr.ni; ++q) Mt[(size_t)(offr + j) * n + offr + q] = M(hr, q, j);
+        std::vector<double> Mr((size_t)hr.ni * hr.ni, 0.0);   // L_rr^-1, row-major
+        for (int j = 0; j < hr.ni; ++j)
+            for (int q = j; q < hr.ni; ++q) Mr[(size_t)q * hr.ni + j] = M(hr, q, j);
+        bool ok = true;
+        for (size_t k = 0; k < cls.size() && ok; ++k) {
+            const HSnode& c = F->sn[cls[k]];
+            for (int j = 0; j < c.ni; ++j)
+                for (int q = j; q < c.ni; ++q) Mt[(size_t)(off[k] + j) * n + off[k] + q] = M(c, q, j);
+            // B = L_rc L_cc^-1 at r's pivots (hr.ni x c.ni, row-major)
+            std::vector<double> B((size_t)hr.ni * c.ni, 0.0);
+            for (int q = c.ni; q < c.nd && ok; ++q) {   // dense boundary rows
+                const int R = F->drows[c.drow_off + q - c.ni];
+                const int a = rlocal(F->bidx[c.bidx_off + R - c.ni]);
+                if (a < 0) ok = false;
+                else
+                    for (int j = 0; j < c.ni; ++j) B[(size_t)a * c.ni + j] = M(c, q, j);
+            }
+            for (int g = c.lr_begin; g < c.lr_end && ok; ++g) {   // low-rank rows U V^T
+                const HLr& G = F->lr[g];
+                for (int i = 0; i < G.m && ok; ++i) {
+                    const int a = rlocal(F->bidx[c.bidx_off + G.row0 + i - c.ni]);
+                    if (a < 0) {
+                        ok = false;
+                        break;
+                    }
+                    for (int j = 0; j < c.ni; ++j) {
+                        double v = 0.0;
+                        for (int l = 0; l < G.k; ++l)
+                            v += F->data[G.off_u + (int64_t)i * G.k + l] * F->data[G.off_v + (int64_t)j * G.k + l];
+                        B[(size_t)a * c.ni + j] = v;
+                    }
+                }
+            }
+            if (!ok) break;
+            std::vector<double> P((size_t)hr.ni * c.ni, 0.0);   // L_rr^-1 B
+            dense::gemm_nn(hr.ni, c.ni, hr.ni, 1.0, Mr.data(), hr.ni, B.data(), c.ni, P.data(), c.ni, true);
+            for (int a = 0; a < hr.ni; ++a)
+                for (int j = 0; j < c.ni; ++j) Mt[(size_t)(off[k] + j) * n + offr + a] = -P[(size_t)a * c.ni + j];
         }
+        if (!ok) {   // a child's boundary outside r: the root alone
+            if (top_k == 2) {
+                top_k = 1;
+                continue;
+            }
+            break;
+        }
+        F->gram.assign((size_t)n * n, 0.0);
+        if (o.gpu_front && n >= 1024) {
+            const int e = gpu_gram_nt(n, Mt.data(), F->gram.data());
+            if (e != BID_OK) return e;
+        } else {
+            dense::gemm_nt(n, n, n, 1.0, Mt.data(), n, Mt.data(), n, F->gram.data(), n, true);
+        }
+        // rows: position and input slots
+        for (size_t k = 0; k < cls.size(); ++k) {
+            const HSnode& c = F->sn[cls[k]];
+            F->top_cl.push_back(cls[k]);
+            for (int i = 0; i < c.ni; ++i) {
+                F->top_pos.push_back(c.first + i);
+                F->top_slot.push_back(c.inc_off + 2 * i);
+                F->top_sptr.push_back((int32_t)F->top_slot.size());
+            }
+        }
+        F->top_cl.push_back(root);
+        std::vector<std::vector<int32_t>> rs(hr.ni);   // r's pivot a <- children's boundary rows
+        for (int s : cls) {
+            const HSnode& c = F->sn[s];
+            for (int r = 0; r < c.nb; ++r) rs[rlocal(F->bidx[c.bidx_off + r])].push_back(c.inc_off + 2 * (c.ni + r));
+        }
+        for (int a = 0; a < hr.ni; ++a) {
+            F->top_pos.push_back(hr.first + a);
+            if (cls.empty()) F->top_slot.push_back(hr.inc_off + 2 * a);   // the root alone: its own slots
+            for (int32_t sl : rs[a]) F->top_slot.push_back(sl);
+            F->top_sptr.push_back((int32_t)F->top_slot.size());
+        }
+        F->gram_s = root;
+        F->gram_lev = H - top_k;
+        break;
     }
     F->tbuf = tbuf;
     F->pbuf = pbuf;

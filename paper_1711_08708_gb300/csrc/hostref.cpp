@@ -111,6 +111,12 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
         return a;
     };
     const int H = (int)F.uf_ptr.size() - 1;
+    // the top block's Gram product: with every block cluster live in a masked
+    // solve, and not when the forward results are asked for
+    bool use_gram = F.gram_s >= 0 && (int64_t)F.gram.size() == (int64_t)F.top_pos.size() * (int64_t)F.top_pos.size();
+    if (use_gram && mask)
+        for (int c : F.top_cl) use_gram = use_gram && (*mask->live)[c];
+    if (use_gram && !mask && fwd_y) use_gram = false;
     // a mid cluster's block: aligned, inside the array, and holding its dense
     // columns (up to the last vector read) and its low-rank groups
     auto mid_block_ok = [&](const MidCl& m) {
@@ -224,8 +230,8 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
                 const HSnode& s = F.sn[si];
                 if (s.large && s.height == lev && !(*mask->live)[si]) scaled_copy(s);
             }
-        if (lev == F.gram_lev && F.gram_s >= 0 && (mask ? (*mask->live)[F.gram_s] != 0 : !fwd_y))
-            continue;   // the root: its forward and backward are one product with G in the backward pass
+        if (use_gram && lev >= F.gram_lev)
+            continue;   // the top block: its forward and backward are one product with G in the backward pass
         if (F.wide_c[lev] > 0) {   // wide clusters: C column slices, partials combined by rank
             const int C = F.wide_c[lev];
             for (int wi = F.wide_ptr[lev]; wi < F.wide_ptr[lev + 1]; ++wi) {
@@ -366,15 +372,20 @@ bool replay(const HFactorHost& F, const double* b, double shift, double* x,
             continue;
         }
         std::vector<std::pair<int32_t, double>> xs;   // outputs of this level, written after
-        if (lev == F.gram_lev && F.gram_s >= 0 && (mask ? (*mask->live)[F.gram_s] != 0 : !fwd_y)) {
-            // root Gram product: x_r = G w_r, w_r the root's input and its children's updates
-            const HSnode& s = F.sn[F.gram_s];
-            std::vector<double> wr(s.ni);
-            for (int j = 0; j < s.ni; ++j) wr[j] = gather(s, j);
-            for (int i = 0; i < s.ni; ++i) {
+        if (use_gram && lev >= F.gram_lev) {
+            if (lev > F.gram_lev) continue;
+            // top-block Gram product: x_top = G w_top, w_top each row's input and listed update slots
+            const int n = (int)F.top_pos.size();
+            std::vector<double> wt(n);
+            for (int t = 0; t < n; ++t) {
+                double a = xp[F.top_pos[t]];
+                for (int e = F.top_sptr[t]; e < F.top_sptr[t + 1]; ++e) a += inb[F.top_slot[e]] + inb[F.top_slot[e] + 1];
+                wt[t] = a;
+            }
+            for (int i = 0; i < n; ++i) {
                 double a = 0.0;
-                for (int j = 0; j < s.ni; ++j) a += F.gram[(size_t)i * s.ni + j] * wr[j];
-                x[F.pidx[s.first + i]] = a;
+                for (int j = 0; j < n; ++j) a += F.gram[(size_t)i * n + j] * wt[j];
+                x[F.pidx[F.top_pos[i]]] = a;
             }
             continue;
         }
@@ -588,7 +599,7 @@ int bid_host_factor_solve_dataflow(const bid_host_system* h, int which, double g
         stats->lowrank_blocks = F.nlr;
         stats->mid_clusters1 = (int64_t)F.mid.size();
         stats->wide_clusters1 = (int64_t)F.wide.size();
-        stats->gram_pivots1 = F.gram_s >= 0 ? F.sn[F.gram_s].ni : 0;
+        stats->gram_pivots1 = F.gram_s >= 0 ? (int64_t)F.top_pos.size() : 0;
         stats->bytes_p1 = 2 * (int64_t)F.data.size() * 8;
         stats->alg_bytes_p1 = 2 * (F.dense_entries + F.lowrank_entries) * 8;
     }
@@ -724,7 +735,7 @@ int bid_host_batch_factor_solve(const bid_host_system* const* hs, int nslices, i
         stats->lowrank_blocks = F.nlr;
         stats->mid_clusters1 = (int64_t)F.mid.size();
         stats->wide_clusters1 = (int64_t)F.wide.size();
-        stats->gram_pivots1 = F.gram_s >= 0 ? F.sn[F.gram_s].ni : 0;
+        stats->gram_pivots1 = F.gram_s >= 0 ? (int64_t)F.top_pos.size() : 0;
     }
     return BID_OK;
 }

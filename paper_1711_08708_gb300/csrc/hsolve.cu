@@ -2005,37 +2005,45 @@ __global__ void __launch_bounds__(MT) k_wide_bwd(HView v, const T* __restrict__ 
     }
 }
 
-// ------------------------------------------------------------ root Gram product
-// x_r = G w_r for the root cluster (HFactorHost::gram): CTA b holds rows
+// ------------------------------------------------------------ top-block Gram product
+// x_top = G w_top for the top block (HFactorHost::gram): CTA b holds rows
 // [b R, b R + R) of G (row stride ld, zero padded), bulk-copied before the
-// dependency wait; after it the CTA gathers w_r (the root's input and its
-// children's updates) and one warp per row forms the product, summed by the
-// warp in a fixed order.
+// dependency wait; after it the CTA gathers w_top (each row's input and its
+// listed update-slot pairs) and one warp per row forms the product, summed by
+// the warp in a fixed order.
 template <typename T, typename A>
-__global__ void __launch_bounds__(MT) k_gram(HView v, const T* __restrict__ G, int ld, int rows, int s,
-                                             const double* xp, const double* inb, double* out,
-                                             unsigned int* err) {
+__global__ void __launch_bounds__(MT) k_gram(HView v, const T* __restrict__ G, int ld, int rows, int n,
+                                             const int32_t* __restrict__ tpos, const int32_t* __restrict__ tsptr,
+                                             const int32_t* __restrict__ tslot, const double* xp, const double* inb,
+                                             double* out, unsigned int* err) {
     constexpr int VEC = VecOf<T>::N;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int32_t po[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const HSnode sn = v.sn[s];
-    const int ni = sn.ni;
-    const int r0 = blockIdx.x * rows, nr = min(rows, ni - r0);
+    const int r0 = blockIdx.x * rows, nr = min(rows, n - r0);
     const int gbytes = nr * ld * (int)sizeof(T);
     if (tid == 0) {
         mbar_init(&bar, 1);
         mbar_arrive_expect_tx(&bar, (uint32_t)gbytes);
         bulk_region(dyn_smem, G + (int64_t)r0 * ld, gbytes, &bar);
     }
-    if (tid < nr) po[tid] = v.pidx[sn.first + r0 + tid];
+    if (tid < nr) po[tid] = v.pidx[tpos[r0 + tid]];
     A* w = reinterpret_cast<A*>(dyn_smem + ((size_t)rows * ld * sizeof(T) + 15) / 16 * 16);
     __syncthreads();
     pdl_wait();
     pdl_trigger();
-    for (int j = tid; j < ld; j += blockDim.x)
-        w[j] = j < ni ? (A)(xp[sn.first + j] + (sn.nchild ? slot_sum(sn, j, inb) : 0.0)) : (A)0;
+    for (int j = tid; j < ld; j += blockDim.x) {
+        double a = 0.0;
+        if (j < n) {
+            a = xp[tpos[j]];
+            for (int e = tsptr[j]; e < tsptr[j + 1]; ++e) {
+                const double2 sv = __ldcg(reinterpret_cast<const double2*>(inb + tslot[e]));
+                a += sv.x + sv.y;
+            }
+        }
+        w[j] = (A)a;
+    }
     __syncthreads();
     if (!mbar_wait_bounded(&bar)) {
         if (tid == 0) atomicOr(err, 1u);
@@ -2418,15 +2426,17 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             }
             ++launches;
         }
-        if (lev == F.gram_lev && F.gram && (!mu.live || F.gram_masked)) {   // the root: one Gram product
-            const int rows = F.gram_rows;
-            const size_t sm = ((size_t)rows * F.gram_ld * (precision_size<T>()) + 15) / 16 * 16 +
-                              sizeof(A) * (size_t)F.gram_ld;
-            const int ni = F.gram_ni;
-            BID_CUDA_TRY(launch_k(k_gram<T, A>, (ni + rows - 1) / rows, 32 * rows, sm, L.st, v,
-                                  reinterpret_cast<const T*>(F.gram), F.gram_ld, rows, F.gram_s, S.xp, inb, out,
-                                  S.err));
-            ++launches;
+        if (F.gram && (!mu.live || F.gram_masked) && lev >= F.gram_lev) {   // the top block: one Gram product
+            if (lev == F.gram_lev) {
+                const int rows = F.gram_rows;
+                const size_t sm = ((size_t)rows * F.gram_ld * (precision_size<T>()) + 15) / 16 * 16 +
+                                  sizeof(A) * (size_t)F.gram_ld;
+                const int n = F.gram_ni;
+                BID_CUDA_TRY(launch_k(k_gram<T, A>, (n + rows - 1) / rows, 32 * rows, sm, L.st, v,
+                                      reinterpret_cast<const T*>(F.gram), F.gram_ld, rows, n, F.top_pos, F.top_sptr,
+                                      F.top_slot, S.xp, inb, out, S.err));
+                ++launches;
+            }
             continue;
         }
         const int wcn = F.wide_c[lev];
@@ -2470,7 +2480,7 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
             lev = t0;
             continue;
         }
-        if (lev == F.gram_lev && F.gram && (!mu.live || F.gram_masked)) continue;   // done by k_gram
+        if (F.gram && (!mu.live || F.gram_masked) && lev >= F.gram_lev) continue;   // done by k_gram
         const int wcn = F.wide_c[lev];
         const int ng = wcn > 0 ? 0 : F.ulr_mid[lev] - F.ulr_ptr[lev];   // the task clusters' low-rank groups
         const int nv = wcn > 0 ? 0 : F.vg_ptr[lev + 1] - F.vg_ptr[lev];
@@ -2735,7 +2745,8 @@ int upload_liveness(const HFactorHost& h, const std::vector<uint8_t>& vlive, HFa
     for (size_t k = 0; k < h.wide.size(); ++k) wl[k] = live[h.wide[k].s];
     wl.push_back(1);
     BID_TRY(upload_vec(wl, &d->wide_live));
-    d->gram_masked = d->gram_s >= 0 && live[d->gram_s];
+    d->gram_masked = d->gram_s >= 0;
+    for (int c : h.top_cl) d->gram_masked = d->gram_masked && live[c];
     {   // per cluster, and the flat groups each level's masked forward launches
         std::vector<uint8_t> send, cl(live);
         cluster_frontier(h, live, &send);
@@ -3035,8 +3046,8 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     BID_TRY(upload_wide(h, precision, d));
     d->gram = nullptr;
     d->gram_s = d->gram_lev = -1;
-    if (h.gram_s >= 0) {   // root Gram matrix in the storage precision, rows padded to whole vectors
-        const int ni = h.sn[h.gram_s].ni;
+    if (h.gram_s >= 0) {   // top-block Gram matrix in the storage precision, rows padded to whole vectors
+        const int ni = (int)h.top_pos.size();
         const int vec = want_vec;
         const int ld = (ni + vec - 1) / vec * vec;
         const int esz = precision == BID_FP64 ? 8 : precision == BID_FP32 ? 4 : 2;
@@ -3062,6 +3073,15 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
                     for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = to_bf16((float)h.gram[(size_t)i * ni + j]);
                 BID_TRY(upload_vec(g, reinterpret_cast<uint16_t**>(&d->gram)));
             }
+            if ((int)h.top_sptr.size() != ni + 1 || h.top_sptr.back() != (int)h.top_slot.size())
+                return set_error(BID_EINVAL, "top-block slot lists out of range");
+            for (int32_t sl : h.top_slot)
+                if (sl < 0 || sl % 2 || sl + 2 > h.nslots) return set_error(BID_EINVAL, "top-block slot out of range");
+            for (int32_t ps : h.top_pos)
+                if (ps < 0 || ps >= h.n) return set_error(BID_EINVAL, "top-block position out of range");
+            BID_TRY(upload_vec(h.top_pos, &d->top_pos));
+            BID_TRY(upload_vec(h.top_sptr, &d->top_sptr));
+            BID_TRY(upload_vec(h.top_slot.empty() ? std::vector<int32_t>{0} : h.top_slot, &d->top_slot));
             d->gram_s = h.gram_s;
             d->gram_lev = h.gram_lev;
             d->gram_ld = ld;
@@ -3144,7 +3164,7 @@ void free_hfactor(HFactorDev* d) {
                     d->lr,      d->fg,   d->gcl,  d->uft, d->ubt,   d->data, d->inb, d->sched,
                     d->tree_idx, d->tree_state, d->fg_live, d->uf_live, d->y1, d->y1slot,
                     d->mid, d->mid_live, d->wide, d->wslice, d->wpiece, d->wadj, d->wide_live,
-                    d->cl_live, d->fg_mlist, d->gram};
+                    d->cl_live, d->fg_mlist, d->gram, d->top_pos, d->top_sptr, d->top_slot};
     for (void* p : ptrs) cudaFree(p);
     *d = HFactorDev();
 }

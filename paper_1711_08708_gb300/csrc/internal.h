@@ -238,6 +238,8 @@ struct WideAdj {        // shared-memory element of V(j, l) = vadj + j k + l; of
 };
 constexpr int WIDE_MAX_CTAS = 16;
 constexpr int GRAM_NI_MIN = 128, GRAM_NI_MAX = 4096;    // root sizes that take the Gram product
+constexpr int TOP_N_MAX = 2560;   // largest top block with the children (its dense G grows as n^2: 4097 rows
+                                  // of the 2049^2 slice read 4x the bytes of the blocks they replace)
 constexpr int GRAM_ROWS = 16;                           // rows of G per CTA (one per warp)
 constexpr int WIDE_ND = 4096, WIDE_NB = 4096;   // largest dense rows / boundary rows
 constexpr int WIDE_DATA_MAX = 160 * 1024;   // factor bytes of one CTA of a wide cluster
@@ -282,13 +284,21 @@ struct HFactorHost {
     int32_t vec = 2;
     int32_t lev_upper = 0;     // levels >= lev_upper hold only large clusters
     int64_t dense_entries = 0, lowrank_entries = 0;   // algorithmic (no padding)
-    // Root Gram matrix: when the top level holds one large cluster r with no
-    // boundary and no low-rank groups (its forward and backward passes are
-    // x_r = M_r^T (M_r w_r) with nothing in between), G = M_r^T M_r (ni x ni,
-    // row-major, FP64) replaces both passes by one product x_r = G w_r.
+    // Top-block Gram matrix.  When the top level holds one large cluster r with
+    // no boundary and no low-rank groups, the forward and backward passes of the
+    // top block -- r, and its children when the level below holds exactly them
+    // -- are x_top = M_top^T (M_top w_top) with nothing in between, M_top =
+    // L_top^-1 the inverse of the block's Cholesky factor (children's pivots,
+    // then r's): G = M_top^T M_top (n_top x n_top, row-major, FP64) replaces
+    // them by one product x_top = G w_top.  w_top of a top row is its xp entry
+    // plus the update slots listed for it: a child's pivot, its own frontal row;
+    // a pivot of r, the children's frontal boundary rows holding that node.
     int32_t gram_s = -1;                       // the root cluster, or -1
-    int32_t gram_lev = -1;                     // its level
+    int32_t gram_lev = -1;                     // the lowest level of the block
     std::vector<double> gram;
+    std::vector<int32_t> top_cl;               // the block's clusters
+    std::vector<int32_t> top_pos;              // per top row: its elimination position
+    std::vector<int32_t> top_sptr, top_slot;   // per top row: slot pairs at top_slot[sptr[t] .. sptr[t+1])
     int64_t nsmall = 0, nlarge = 0, nlr = 0;
 };
 
@@ -331,6 +341,8 @@ struct HBuildOpts {
 // meaningful), nb = nf - ni.  *bad: 0, or 1 + the index of a non-positive
 // pivot.  One front at a time per process (serialised).
 int gpu_front_factor(int nf, int ni, const double* F, double* M, double* U, int* bad);
+// G = A A^T for A n x n (row-major, FP64) on the GPU (the tiled product kernel).
+int gpu_gram_nt(int n, const double* A, double* G);
 // A: symmetric CSR (full pattern).  coords: dim values per row (geometry of
 // the unknowns, used by the nested dissection).  Every index in `pins` has its
 // row and column replaced by the identity and its input entry set to zero
@@ -407,8 +419,11 @@ struct HFactorDev {
     uint8_t* mid_live = nullptr;
     uint8_t* wide_live = nullptr;
     uint8_t* cl_live = nullptr;         // per cluster
-    void* gram = nullptr;               // root Gram matrix (storage precision, row stride gram_ld), or NULL
+    void* gram = nullptr;               // top-block Gram matrix (storage precision, row stride gram_ld), or NULL
     int32_t gram_s = -1, gram_lev = -1, gram_ld = 0, gram_ni = 0, gram_rows = 1;
+    int32_t* top_pos = nullptr;         // HFactorHost::top_pos / top_sptr / top_slot
+    int32_t* top_sptr = nullptr;
+    int32_t* top_slot = nullptr;
     bool gram_masked = false;           // the masked solve may use it too (the root is live)
     int32_t* fg_mlist = nullptr;        // flat groups of the masked forward launches, level by level
     std::vector<int32_t> fg_mptr;       // level -> range of fg_mlist

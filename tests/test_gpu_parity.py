@@ -369,9 +369,9 @@ def test_wide_clusters_equal_chunked_kernels(bid, monkeypatch, precision, leaf):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_root_gram_equals_root_passes(bid, monkeypatch, precision):
-    # the root's two passes replaced by one product with G = M_r^T M_r (the
-    # default where the root has no boundary, no low-rank groups and 1024 to
-    # 4096 pivots) against the passes themselves (BID_ROOT_GRAM=0), 1025^2
+    # the top block's passes (the root and its two children) replaced by one
+    # product with G = M^T M (the default where the root has no boundary or
+    # low-rank groups) against the passes themselves (BID_ROOT_GRAM=0), 1025^2
     # slice: the same P_1 and P_Lambda^-1 applications up to the storage
     # precision's rounding, and PCG solves within one iteration that agree
     # potential by potential to 1e-8
@@ -395,7 +395,7 @@ def test_root_gram_equals_root_passes(bid, monkeypatch, precision):
         info = P.solve(Y, X, tol=1e-13, max_iter=800)
         out[rg] = (H(x1), H(z), H(X), info["iters"], P.stats["gram_pivots1"])
         del P
-    assert out["0"][4] == 0 and out[None][4] == 1025, (out["0"][4], out[None][4])
+    assert out["0"][4] == 0 and out[None][4] == 1025 + 2 * 512, (out["0"][4], out[None][4])
     tol = 1e-11 if precision == "fp64" else 1e-5
     for a, c in zip(out["0"][:2], out[None][:2]):
         assert np.isfinite(c).all()

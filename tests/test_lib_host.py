@@ -226,10 +226,13 @@ def test_wide_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
 
 
 def test_root_gram_equals_root_passes(bid, monkeypatch):
-    # the root cluster (no boundary, no low-rank groups) solved as one product
-    # x_r = G w_r with G = M_r^T M_r formed at build, against its forward and
-    # backward passes (BID_ROOT_GRAM=0): the same P_1 and masked P_1 solves up
-    # to rounding on the 1025^2 slice, whose root separator has 1025 pivots
+    # the top block (the root, without boundary or low-rank groups, and its two
+    # children, whose boundary rows -- low-rank groups expanded -- lie on the
+    # root) solved as one product x = G w with G = M^T M, M the inverse of the
+    # block's Cholesky factor assembled at build, against the blocks' forward
+    # and backward passes (BID_ROOT_GRAM=0): the same P_1 and masked P_1 solves
+    # up to rounding on the 1025^2 slice (root separator of 1025 pivots,
+    # children of 512)
     m, p = torso_square_2d(1025), params_2d(0.1)
     hs = bid.HostSystem(m, p)
     o = ob.build_system(m, p)
@@ -246,7 +249,7 @@ def test_root_gram_equals_root_passes(bid, monkeypatch):
         x1, st = hs.factor_solve(1, b1, eps=1e-3, leaf=32, precision="fp32")
         xm, _ = hs.factor_solve_masked(bm, eps=1e-3, leaf=32, precision="fp32")
         out[rg] = (x1, xm, st["gram_pivots1"])
-    assert out["0"][2] == 0 and out[None][2] == 1025
+    assert out["0"][2] == 0 and out[None][2] == 1025 + 2 * 512   # the root and its two children
     for a, c in zip(out["0"][:2], out[None][:2]):
         assert np.abs(a - c).max() <= 1e-12 * np.abs(a).max()
 
