@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 
@@ -2428,12 +2429,15 @@ int run(const Launch& L, const HFactorDev& F, const double* in, const HShift& sh
         }
         if (F.gram && (!mu.live || F.gram_masked) && lev >= F.gram_lev) {   // the top block: one Gram product
             if (lev == F.gram_lev) {
+                // G in FP64 for FP64 factors, else FP32 (BF16 would spoil a product whose
+                // matrix has the squared condition of the blocks it replaces)
+                using TG = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
                 const int rows = F.gram_rows;
-                const size_t sm = ((size_t)rows * F.gram_ld * (precision_size<T>()) + 15) / 16 * 16 +
+                const size_t sm = ((size_t)rows * F.gram_ld * sizeof(TG) + 15) / 16 * 16 +
                                   sizeof(A) * (size_t)F.gram_ld;
                 const int n = F.gram_ni;
-                BID_CUDA_TRY(launch_k(k_gram<T, A>, (n + rows - 1) / rows, 32 * rows, sm, L.st, v,
-                                      reinterpret_cast<const T*>(F.gram), F.gram_ld, rows, n, F.top_pos, F.top_sptr,
+                BID_CUDA_TRY(launch_k(k_gram<TG, A>, (n + rows - 1) / rows, 32 * rows, sm, L.st, v,
+                                      reinterpret_cast<const TG*>(F.gram), F.gram_ld, rows, n, F.top_pos, F.top_sptr,
                                       F.top_slot, S.xp, inb, out, S.err));
                 ++launches;
             }
@@ -2568,7 +2572,10 @@ int prepare_one() {
                                       MID_SMEM_MAX));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_bwd<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       MID_SMEM_MAX));
-    BID_CUDA_TRY(cudaFuncSetAttribute(k_gram<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM_MAX));
+    {
+        using TG = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+        BID_CUDA_TRY(cudaFuncSetAttribute(k_gram<TG, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM_MAX));
+    }
     BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_fwd<T, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     BID_CUDA_TRY(cudaFuncSetAttribute(k_wide_bwd<T, A>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return BID_OK;
@@ -3048,9 +3055,9 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
     d->gram_s = d->gram_lev = -1;
     if (h.gram_s >= 0) {   // top-block Gram matrix in the storage precision, rows padded to whole vectors
         const int ni = (int)h.top_pos.size();
-        const int vec = want_vec;
+        const int esz = precision == BID_FP64 ? 8 : 4;   // FP64, else FP32 (also for BF16 factors)
+        const int vec = 16 / esz;
         const int ld = (ni + vec - 1) / vec * vec;
-        const int esz = precision == BID_FP64 ? 8 : precision == BID_FP32 ? 4 : 2;
         if ((int64_t)h.gram.size() != (int64_t)ni * ni) return set_error(BID_EINVAL, "root Gram matrix size");
         int rows = GRAM_ROWS;   // rows per CTA: whole rows within the shared memory, with w
         while (rows > 1 && (size_t)rows * ld * esz + 16 + (size_t)(precision == BID_FP64 ? 8 : 4) * ld >
@@ -3062,16 +3069,11 @@ int upload_hfactor(const HFactorHost& h, int precision, HFactorDev* d) {
                 for (int i = 0; i < ni; ++i)
                     for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = h.gram[(size_t)i * ni + j];
                 BID_TRY(upload_vec(g, reinterpret_cast<double**>(&d->gram)));
-            } else if (precision == BID_FP32) {
+            } else {
                 std::vector<float> g((size_t)ni * ld, 0.0f);
                 for (int i = 0; i < ni; ++i)
                     for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = (float)h.gram[(size_t)i * ni + j];
                 BID_TRY(upload_vec(g, reinterpret_cast<float**>(&d->gram)));
-            } else {
-                std::vector<uint16_t> g((size_t)ni * ld, 0);
-                for (int i = 0; i < ni; ++i)
-                    for (int j = 0; j < ni; ++j) g[(size_t)i * ld + j] = to_bf16((float)h.gram[(size_t)i * ni + j]);
-                BID_TRY(upload_vec(g, reinterpret_cast<uint16_t**>(&d->gram)));
             }
             if ((int)h.top_sptr.size() != ni + 1 || h.top_sptr.back() != (int)h.top_slot.size())
                 return set_error(BID_EINVAL, "top-block slot lists out of range");

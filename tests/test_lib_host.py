@@ -176,6 +176,7 @@ def test_mid_clusters_equal_chunked_replay(bid, monkeypatch, precision, leaf):
     bm = np.zeros(o.N)
     bm[:o.NH] = rng.normal(size=o.NH)
     g = p["chi"] * p["Cm"] / p["dt"]
+    monkeypatch.setenv("BID_ROOT_GRAM", "0")   # the same top levels in both runs
     out = {}
     for mb in ("0", None):
         if mb is None:
