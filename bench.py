@@ -46,11 +46,11 @@ sys.path.insert(0, ROOT)
 METRIC = "bidomain steps/s at PCG rel-res 1e-8 (chosen form); HBM GB/s of the factor solve"
 
 # DRAM bytes per algorithmic byte of one P_1 solve, from an ncu capture of the
-# same kernels on the 1025^2 slice (600.1 MB of DRAM traffic for 464.1 MB of
+# same kernels on the 1025^2 slice (610.8 MB of DRAM traffic for 464.1 MB of
 # algorithmic bytes at eps 1e-3, FP32, leaf 32); the traffic grows with the
 # factor, so the bench's roofline reports this ratio times its own algorithmic
 # bytes for the same form (other forms: null, no capture of the current kernels).
-TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 600.1 / 464.06}
+TRAFFIC_PER_ALG_BYTE = {(1e-3, "fp32", 32): 610.8 / 464.06}
 
 
 def parse():
@@ -465,8 +465,8 @@ def run_batched(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "kernel": "P_1 forest solve of all slices (k_permute, k_flat_fwd, k_mid_fwd, "
-                               "k_wide_fwd, k_up_fwd, k_bwd_prep, k_up_bwd, k_wide_bwd, k_mid_bwd, "
-                               "k_flat_bwd over all levels)",
+                               "k_wide_fwd, k_gram, k_up_fwd, k_bwd_prep, k_up_bwd, k_wide_bwd, "
+                               "k_mid_bwd, k_flat_bwd over all levels)",
                      "ms": solve_ms, "algorithmic_bytes": alg_bytes,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"},
         "e2e": {"value": world / (e2e_ms / args.steps * 1e-3), "unit": "batch steps/s",
@@ -828,7 +828,7 @@ def main():
                 "alg_bytes_pk", "levels1", "levelsk", "large_levels1", "large_levelsk",
                 "masked_dead1", "masked_clusters1", "dense_entries", "lowrank_entries",
                 "lowrank_blocks", "mid_clusters1", "mid_clustersk", "wide_clusters1", "wide_clustersk",
-                "build_seconds")},
+                "gram_pivots1", "gram_pivotsk", "build_seconds")},
             "plain": None if plain is None else {
                 "steps_per_s": world * args.steps / (plain["ms"] * 1e-3),
                 "mean_pcg_iters": float(np.mean(plain["iters"])),
@@ -845,9 +845,9 @@ def main():
                                  else None),
                      "traffic_note": "ncu DRAM bytes of the same kernels on the 1025^2 slice, scaled "
                                      "by the algorithmic bytes",
-                     "kernel": ("P_1 solve: k_permute, k_flat_fwd, k_mid_fwd, k_wide_fwd, k_up_fwd, "
-                                "k_bwd_prep, k_up_bwd, k_wide_bwd, k_mid_bwd, k_flat_bwd over all tree "
-                                "levels" if args.elliptic == "hchol"
+                     "kernel": ("P_1 solve: k_permute, k_flat_fwd, k_mid_fwd, k_wide_fwd, k_gram, "
+                                "k_up_fwd, k_bwd_prep, k_up_bwd, k_wide_bwd, k_mid_bwd, k_flat_bwd over "
+                                "all tree levels" if args.elliptic == "hchol"
                                 else "P_1 multigrid V-cycle: k_mg_first, k_mg_cheb, k_mg_resid, "
                                      "k_mg_apply over all levels, k_mg_dense"),
                      "ms": solve_ms, "algorithmic_bytes": alg_bytes,
