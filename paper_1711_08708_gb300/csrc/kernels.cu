@@ -11,6 +11,9 @@
 // needs a host round trip.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <initializer_list>
+
 #include <algorithm>
 
 #include "internal.h"
@@ -203,25 +206,46 @@ __global__ void __launch_bounds__(TPB) k_project(int N, int NH, double* __restri
 }
 
 // x += alpha p; r -= alpha q; r_U projected onto 1^perp in the same pass (the
-// new mean is known from the tracked sums); ||r||^2 and sum(r_U).
+// new mean is known from the tracked sums); ||r||^2 and sum(r_U).  vec: all
+// four vectors 16-byte aligned, entries taken two at a time (one 16-byte load
+// each), the U/V boundary handled entry by entry.
+__device__ __forceinline__ void update_one(int i, int N, double alpha, double mean, double& xv, double& rv,
+                                           double pv, double qv, double& rr, double& s) {
+    xv += alpha * pv;
+    double v = rv - alpha * qv;
+    if (i < N) {
+        v -= mean;
+        s += v;
+    }
+    rv = v;
+    rr += v * v;
+}
 __global__ void __launch_bounds__(TPB) k_update(int N, int NH, double* __restrict__ x,
                                                 double* __restrict__ r,
                                                 const double* __restrict__ p,
-                                                const double* __restrict__ q, DevScalars* sc,
+                                                const double* __restrict__ q, int vec, DevScalars* sc,
                                                 double* partials) {
     const double alpha = sc->alpha;
     const double mean = (sc->sumr - alpha * sc->sumq) / N;
     double rr = 0.0, s = 0.0;
     const int n = N + NH;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        x[i] += alpha * p[i];
-        double v = r[i] - alpha * q[i];
-        if (i < N) {
-            v -= mean;
-            s += v;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    if (vec) {
+        double2* x2 = reinterpret_cast<double2*>(x);
+        double2* r2 = reinterpret_cast<double2*>(r);
+        const double2* p2 = reinterpret_cast<const double2*>(p);
+        const double2* q2 = reinterpret_cast<const double2*>(q);
+        for (int k = t0; k < n / 2; k += st) {
+            double2 xv = x2[k], rv = r2[k];
+            const double2 pv = p2[k], qv = q2[k];
+            update_one(2 * k, N, alpha, mean, xv.x, rv.x, pv.x, qv.x, rr, s);
+            update_one(2 * k + 1, N, alpha, mean, xv.y, rv.y, pv.y, qv.y, rr, s);
+            x2[k] = xv;
+            r2[k] = rv;
         }
-        r[i] = v;
-        rr += v * v;
+        if ((n & 1) && t0 == 0) update_one(n - 1, N, alpha, mean, x[n - 1], r[n - 1], p[n - 1], q[n - 1], rr, s);
+    } else {
+        for (int i = t0; i < n; i += st) update_one(i, N, alpha, mean, x[i], r[i], p[i], q[i], rr, s);
     }
     double v2[2] = {rr, s}, tot[2];
     if (grid_reduce<2>(v2, partials, &sc->ticket[TK_UPDATE], tot)) {
@@ -232,22 +256,38 @@ __global__ void __launch_bounds__(TPB) k_update(int N, int NH, double* __restric
 
 // rz_new = <r, z>; qz = <q, p z> (q against the U-projected z).  first: rz = rz_new.
 // otherwise beta = rz_new / rz (standard) or -alpha qz / rz (flexible,
-// Polak-Ribiere form, since r_{k+1} - r_k = -alpha p q_k).
+// Polak-Ribiere form, since r_{k+1} - r_k = -alpha p q_k).  vec as k_update.
+__device__ __forceinline__ void dot_one(int i, int N, bool fq, double ri, double zi, double qi, double& rz,
+                                        double& qz, double& sz) {
+    rz += ri * zi;
+    if (fq) {
+        qz += qi * zi;
+        if (i < N) sz += zi;
+    }
+}
 __global__ void __launch_bounds__(TPB) k_dot_rz(int n, int N, const double* __restrict__ r,
                                                 const double* __restrict__ z,
                                                 const double* __restrict__ q, int flexible,
-                                                int first_arg, DevScalars* sc, double* partials) {
+                                                int first_arg, int vec, DevScalars* sc, double* partials) {
     // first_arg < 0: inside the device-resident loop, the first iteration is
     // the one that starts with no iteration done
     const bool first = first_arg < 0 ? sc->iter == 0 : first_arg != 0;
+    const bool fq = flexible && !first;
     double rz = 0.0, qz = 0.0, sz = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double zi = z[i];
-        rz += r[i] * zi;
-        if (flexible && !first) {
-            qz += q[i] * zi;
-            if (i < N) sz += zi;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    if (vec) {
+        const double2* r2 = reinterpret_cast<const double2*>(r);
+        const double2* z2 = reinterpret_cast<const double2*>(z);
+        const double2* q2 = reinterpret_cast<const double2*>(q);
+        for (int k = t0; k < n / 2; k += st) {
+            const double2 rv = r2[k], zv = z2[k];
+            const double2 qv = fq ? q2[k] : make_double2(0.0, 0.0);
+            dot_one(2 * k, N, fq, rv.x, zv.x, qv.x, rz, qz, sz);
+            dot_one(2 * k + 1, N, fq, rv.y, zv.y, qv.y, rz, qz, sz);
         }
+        if ((n & 1) && t0 == 0) dot_one(n - 1, N, fq, r[n - 1], z[n - 1], fq ? q[n - 1] : 0.0, rz, qz, sz);
+    } else {
+        for (int i = t0; i < n; i += st) dot_one(i, N, fq, r[i], z[i], fq ? q[i] : 0.0, rz, qz, sz);
     }
     double v[3] = {rz, qz, sz}, tot[3];
     if (grid_reduce<3>(v, partials, &sc->ticket[TK_DOT], tot)) {
@@ -266,12 +306,30 @@ __global__ void __launch_bounds__(TPB) k_dot_rz(int n, int N, const double* __re
 }
 
 __global__ void __launch_bounds__(TPB) k_pupdate(int n, double* __restrict__ p,
-                                                 const double* __restrict__ z, int first_arg,
+                                                 const double* __restrict__ z, int first_arg, int vec,
                                                  const DevScalars* sc) {
     const bool first = first_arg < 0 ? sc->iter == 0 : first_arg != 0;
     const double beta = first ? 0.0 : sc->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        p[i] = first ? z[i] : z[i] + beta * p[i];
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    if (vec) {
+        double2* p2 = reinterpret_cast<double2*>(p);
+        const double2* z2 = reinterpret_cast<const double2*>(z);
+        for (int k = t0; k < n / 2; k += st) {
+            const double2 zv = z2[k];
+            double2 pv;
+            if (first) {
+                pv = zv;
+            } else {
+                pv = p2[k];
+                pv.x = zv.x + beta * pv.x;
+                pv.y = zv.y + beta * pv.y;
+            }
+            p2[k] = pv;
+        }
+        if ((n & 1) && t0 == 0) p[n - 1] = first ? z[n - 1] : z[n - 1] + beta * p[n - 1];
+    } else {
+        for (int i = t0; i < n; i += st) p[i] = first ? z[i] : z[i] + beta * p[i];
+    }
 }
 
 // t = r_V - S_i z1[0:N_H]
@@ -330,9 +388,22 @@ __global__ void __launch_bounds__(TPB) k_sum(int n, const double* __restrict__ x
 }
 
 __global__ void __launch_bounds__(TPB) k_axpy_sub(int n, double* __restrict__ a,
-                                                  const double* __restrict__ b) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        a[i] -= b[i];
+                                                  const double* __restrict__ b, int vec) {
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    if (vec) {
+        double2* a2 = reinterpret_cast<double2*>(a);
+        const double2* b2 = reinterpret_cast<const double2*>(b);
+        for (int k = t0; k < n / 2; k += st) {
+            double2 av = a2[k];
+            const double2 bv = b2[k];
+            av.x -= bv.x;
+            av.y -= bv.y;
+            a2[k] = av;
+        }
+        if ((n & 1) && t0 == 0) a[n - 1] -= b[n - 1];
+    } else {
+        for (int i = t0; i < n; i += st) a[i] -= b[i];
+    }
 }
 
 // Step 1 + Step 3 (Sec. 3.2) with the Mitchell-Schaeffer model:
@@ -500,20 +571,30 @@ int launch_project(const Launch& L, int64_t N, int64_t NH, double* r, DevScalars
     k_project<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, r, sc, partials);
     return check_launch("project");
 }
+// 1 when every pointer is 16-byte aligned (the kernels then take two entries per load)
+static int aligned16(std::initializer_list<const void*> ps) {
+    for (const void* q : ps)
+        if (reinterpret_cast<uintptr_t>(q) & 15) return 0;
+    return 1;
+}
 int launch_update(const Launch& L, int64_t N, int64_t NH, double* x, double* r, const double* p,
                   const double* q, DevScalars* sc, double* partials) {
-    k_update<<<grid_for(L, N + NH), TPB, 0, L.st>>>((int)N, (int)NH, x, r, p, q, sc, partials);
+    const int vec = aligned16({x, r, p, q});
+    k_update<<<grid_for(L, vec ? (N + NH + 1) / 2 : N + NH), TPB, 0, L.st>>>((int)N, (int)NH, x, r, p, q, vec,
+                                                                             sc, partials);
     return check_launch("update");
 }
 int launch_dot_rz(const Launch& L, int64_t n, int64_t N, const double* r, const double* z,
                     const double* q, int flexible, int first, DevScalars* sc, double* partials) {
-    k_dot_rz<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, (int)N, r, z, q, flexible, first, sc,
-                                               partials);
+    const int vec = aligned16({r, z, q});
+    k_dot_rz<<<grid_for(L, vec ? (n + 1) / 2 : n), TPB, 0, L.st>>>((int)n, (int)N, r, z, q, flexible, first, vec,
+                                                                   sc, partials);
     return check_launch("dot_rz");
 }
 int launch_pupdate(const Launch& L, int64_t n, double* p, const double* z, int first,
                    const DevScalars* sc) {
-    k_pupdate<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, p, z, first, sc);
+    const int vec = aligned16({p, z});
+    k_pupdate<<<grid_for(L, vec ? (n + 1) / 2 : n), TPB, 0, L.st>>>((int)n, p, z, first, vec, sc);
     return check_launch("pupdate");
 }
 int launch_si_residual(const Launch& L, int64_t NH, const SellDev& Si, const double* rV,
@@ -535,7 +616,8 @@ int launch_sum(const Launch& L, int64_t n, const double* x, double* dst, unsigne
     return check_launch("sum");
 }
 int launch_axpy_sub(const Launch& L, int64_t n, double* a, const double* b) {
-    k_axpy_sub<<<grid_for(L, n), TPB, 0, L.st>>>((int)n, a, b);
+    const int vec = aligned16({a, b});
+    k_axpy_sub<<<grid_for(L, vec ? (n + 1) / 2 : n), TPB, 0, L.st>>>((int)n, a, b, vec);
     return check_launch("axpy_sub");
 }
 int launch_rhs_gate(const Launch& L, int64_t N, int64_t NH, const double* V, double* h,
