@@ -85,6 +85,9 @@ def parse():
     a.add_argument("--guess-dv", type=int, default=1)
     a.add_argument("--guess-policy", type=int, default=1)
     a.add_argument("--slices", type=int, default=64)
+    a.add_argument("--seeds", default="",
+                   help="slice workload: comma-separated stimulus seeds; the chosen form is also "
+                        "timed from the resting state once per seed (mean/min/max in the line)")
     a.add_argument("--no-sequential", action="store_true")
     return a.parse_args()
 
@@ -651,7 +654,7 @@ def main():
     I = torch.tensor(ist_h, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream()
 
-    def time_form(P):
+    def time_form(P, I=I):
         """W warm-up steps from the initial state, then K timed steps; the state
         at the start of the timed region is kept for the end-to-end replay."""
         U, V, h = state()
@@ -716,6 +719,31 @@ def main():
     io_bytes = 8 * (N + 2 * NH)
     Uc, Vc = chosen["U"].cpu().numpy(), chosen["V"].cpu().numpy()
     e2e_same = bool(np.array_equal(hU.numpy(), Uc) and np.array_equal(hV.numpy(), Vc))
+
+    # ---- the same form from the resting state for each stimulus seed asked for
+    sweep = None
+    seeds = [int(x) for x in args.seeds.split(",") if x.strip()] if args.workload == "slice" else []
+    if seeds:
+        from workloads import stimulus_seeded_disc
+        runs = []
+        for sd in seeds:
+            Is = torch.tensor(stimulus_seeded_disc(mesh, seed=sd)[S.perm[:NH]], dtype=torch.float64,
+                              device=dev)
+            r = time_form(P, Is)
+            runs.append({"seed": sd, "steps_per_s": world * args.steps / (r["ms"] * 1e-3),
+                         "mean_pcg_iters": float(np.mean(r["iters"])),
+                         "max_pcg_iters": int(np.max(r["iters"]))})
+            del r
+        sps = [r["steps_per_s"] for r in runs]
+        its = [r["mean_pcg_iters"] for r in runs]
+        sweep = {"seeds": seeds, "runs": runs,
+                 "steps_per_s": {"mean": float(np.mean(sps)), "min": float(np.min(sps)),
+                                 "max": float(np.max(sps))},
+                 "mean_pcg_iters": {"mean": float(np.mean(its)), "min": float(np.min(its)),
+                                    "max": float(np.max(its))},
+                 "note": f"the chosen form, {args.warmup} warm-up + {args.steps} timed steps from the "
+                         "resting state per stimulus seed (the line's value is seed "
+                         f"{rank})"}
 
     # ---- roofline of the dominant kernel family: the P_1 solve (forward and
     # backward passes over all tree levels), timed alone with CUDA events on the
@@ -838,6 +866,7 @@ def main():
             },
             "chosen_error_vs_plain": None if plain is None else err_vs_plain,
             "multigrid": mgres,
+            "seed_sweep": sweep,
         },
         "roofline": {"bound": "hbm", "achieved": alg_bytes / (solve_ms * 1e-3) / 1e9, "peak": hbm,
                      "unit": "GB/s", "frac": alg_bytes / (solve_ms * 1e-3) / 1e9 / hbm,
